@@ -1,0 +1,484 @@
+/*
+ * jd_oracle.c -- plain FP64 CPU oracle (TEST INFRASTRUCTURE ONLY; see jd_oracle.h).
+ *
+ * Written for readability: one path at a time, the paper's order of operations,
+ * no blocking, fusion or reordering.  Threads only split the path range; every
+ * sum is taken in a fixed order so results do not depend on the thread count.
+ */
+#include "jd_oracle.h"
+
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10, as published by Salmon et al. (SC'11): ten rounds of two     */
+/* 32x32->64 multiplies, the key bumped by the Weyl constants between rounds.  */
+/* ------------------------------------------------------------------------- */
+void orc_philox4x32_10(const uint32_t key[2], const uint32_t ctr[4], uint32_t out[4]) {
+  const uint32_t MUL0 = 0xD2511F53u, MUL1 = 0xCD9E8D57u;
+  const uint32_t WEYL0 = 0x9E3779B9u, WEYL1 = 0xBB67AE85u;
+  uint32_t k0 = key[0], k1 = key[1];
+  uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += WEYL0;
+      k1 += WEYL1;
+    }
+    uint64_t prod0 = (uint64_t)MUL0 * (uint64_t)x0;
+    uint64_t prod1 = (uint64_t)MUL1 * (uint64_t)x2;
+    uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+    uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+    uint32_t y0 = hi1 ^ x1 ^ k0;
+    uint32_t y1 = lo1;
+    uint32_t y2 = hi0 ^ x3 ^ k1;
+    uint32_t y3 = lo0;
+    x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+  }
+  out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+double orc_u01(uint32_t w) { return ((double)(w >> 9) + 0.5) * (1.0 / 8388608.0); }
+
+/* Words 0..nwords-1 of one stream: word j is word (j mod 4) of the Philox block
+ * with counter (k, m, purpose<<24 | slot<<16 | j/4, epoch). */
+static void stream_words(const orc_problem *P, int k, int64_t m, uint32_t purpose, uint32_t slot,
+                         int nwords, uint32_t *w) {
+  uint32_t key[2] = {(uint32_t)(P->seed & 0xffffffffu), (uint32_t)(P->seed >> 32)};
+  for (int j = 0; j < nwords; j += 4) {
+    uint32_t ctr[4] = {(uint32_t)k, (uint32_t)m, (purpose << 24) | (slot << 16) | (uint32_t)(j / 4),
+                       P->epoch};
+    uint32_t blk[4];
+    orc_philox4x32_10(key, ctr, blk);
+    for (int t = 0; t < 4 && j + t < nwords; ++t) w[j + t] = blk[t];
+  }
+}
+
+/* Box-Muller: one pair of standard normals from two words. */
+static void normal_pair(uint32_t wa, uint32_t wb, double *z0, double *z1) {
+  double ua = orc_u01(wa), ub = orc_u01(wb);
+  double r = sqrt(-2.0 * log(ua));
+  *z0 = r * cos(2.0 * M_PI * ub);
+  *z1 = r * sin(2.0 * M_PI * ub);
+}
+
+/* d standard normals from words w[0..2*ceil(d/2)-1]. */
+static void normals_from_words(int d, const uint32_t *w, double *z) {
+  for (int p = 0; 2 * p < d; ++p) {
+    double a, b;
+    normal_pair(w[2 * p], w[2 * p + 1], &a, &b);
+    z[2 * p] = a;
+    if (2 * p + 1 < d) z[2 * p + 1] = b;
+  }
+}
+
+/* Poisson CDF thresholds, pmf accumulated in order p_0 = e^-mu, p_n = p_{n-1} mu / n. */
+void orc_poisson_thresholds(double mu, uint64_t thr[ORC_NMAX]) {
+  double p = exp(-mu), F = p;
+  for (int n = 0; n < ORC_NMAX; ++n) {
+    if (n > 0) {
+      p = p * mu / (double)n;
+      F = F + p;
+    }
+    double t = floor(F * 4294967296.0);
+    if (t > 4294967296.0) t = 4294967296.0;
+    if (t < 0.0) t = 0.0;
+    thr[n] = (uint64_t)t;
+  }
+}
+
+static int jumps_enabled(const orc_problem *P) {
+  return P->jump_law != ORC_JUMP_NONE && P->lambda > 0.0;
+}
+
+/* The draws of uniform step k of path m: Poisson count from main-stream word 0,
+ * sub-step-0 normals from main-stream words 1.., and for every jump slot i a time
+ * fraction, a jump size and the normals of the sub-step that starts at that jump.
+ * Jump times are sorted (stable) and each slot's size and normals travel with its
+ * time.  This is the per-step form of Algorithm 5.2's jump-time sampling: given the
+ * count, the times of a Poisson process on a step are uniform order statistics. */
+int orc_step_draws(const orc_problem *P, int k, int64_t m, orc_draws *D) {
+  const int d = P->d, npair = (d + 1) / 2;
+  const double dt = P->T / (double)P->Nt;
+  uint32_t w[1 + 2 * ((ORC_DMAX + 1) / 2) + 2 * ((ORC_DMAX + 1) / 2) + 4];
+
+  memset(D, 0, sizeof(*D));
+  stream_words(P, k, m, 0u, 0u, 1 + 2 * npair, w);
+  int n = 0;
+  if (jumps_enabled(P)) {
+    uint64_t thr[ORC_NMAX];
+    orc_poisson_thresholds(P->lambda * dt, thr);
+    for (int i = 0; i < ORC_NMAX; ++i)
+      if ((uint64_t)w[0] >= thr[i]) n++;
+  }
+  D->n = n;
+  normals_from_words(d, w + 1, D->Z[0]);
+
+  /* slots in draw order */
+  double theta[ORC_NMAX], xi[ORC_NMAX][ORC_DMAX], zs[ORC_NMAX][ORC_DMAX];
+  for (int i = 0; i < n; ++i) {
+    stream_words(P, k, m, 1u, (uint32_t)(i + 1), 1 + 4 * npair, w);
+    theta[i] = orc_u01(w[0]);
+    if (P->jump_law == ORC_JUMP_NORMAL) {
+      normals_from_words(d, w + 1, xi[i]);
+    } else {
+      for (int c = 0; c < d; ++c) xi[i][c] = 2.0 * orc_u01(w[1 + c]) - 1.0;
+    }
+    normals_from_words(d, w + 1 + 2 * npair, zs[i]);
+  }
+  /* stable insertion sort of the slots by time */
+  int order[ORC_NMAX];
+  for (int i = 0; i < n; ++i) order[i] = i;
+  for (int i = 1; i < n; ++i) {
+    int cur = order[i], j = i - 1;
+    while (j >= 0 && theta[order[j]] > theta[cur]) {
+      order[j + 1] = order[j];
+      j--;
+    }
+    order[j + 1] = cur;
+  }
+  for (int i = 0; i < n; ++i) {
+    D->theta[i] = theta[order[i]];
+    memcpy(D->xi_hat[i], xi[order[i]], sizeof(double) * d);
+    memcpy(D->Z[i + 1], zs[order[i]], sizeof(double) * d);
+  }
+  /* sub-step lengths between consecutive grid points of the jump-adapted grid */
+  if (n == 0) {
+    D->delta[0] = dt;
+  } else {
+    D->delta[0] = dt * D->theta[0];
+    for (int i = 1; i < n; ++i) D->delta[i] = dt * (D->theta[i] - D->theta[i - 1]);
+    D->delta[n] = dt * (1.0 - D->theta[n - 1]);
+  }
+  return 0;
+}
+
+/* f(y,u) = A y + C y^3 + B u */
+static void drift(const orc_problem *P, const double *y, const double *u, double *f) {
+  const int d = P->d, du = P->du;
+  for (int i = 0; i < d; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < d; ++j) s += P->A[i * d + j] * y[j];
+    if (P->drift == ORC_CUBIC)
+      for (int j = 0; j < d; ++j) s += P->C[i * d + j] * y[j] * y[j] * y[j];
+    for (int l = 0; l < du; ++l) s += P->B[i * du + l] * u[l];
+    f[i] = s;
+  }
+}
+
+/* out = J_f(y)^T v,  J_f = A + 3 C diag(y^2) */
+static void drift_jacobian_T(const orc_problem *P, const double *y, const double *v, double *out) {
+  const int d = P->d;
+  for (int j = 0; j < d; ++j) {
+    double s = 0.0;
+    for (int i = 0; i < d; ++i) {
+      double Jij = P->A[i * d + j];
+      if (P->drift == ORC_CUBIC) Jij += 3.0 * P->C[i * d + j] * y[j] * y[j];
+      s += Jij * v[i];
+    }
+    out[j] = s;
+  }
+}
+
+/* Sub-step start states of step k (Algorithm 5.1): Y[0] = X_k; Euler sub-step of
+ * length delta_i with the drift at its left end; the jump of slot i+1 is added after
+ * sub-step i (additive jump map c(z) = z + xi). Y[n+1] = X_{k+1}. */
+static void integrate_step(const orc_problem *P, const orc_draws *D, const double *xk,
+                           const double *uk, double (*Y)[ORC_DMAX]) {
+  const int d = P->d;
+  double f[ORC_DMAX];
+  memcpy(Y[0], xk, sizeof(double) * d);
+  for (int i = 0; i <= D->n; ++i) {
+    drift(P, Y[i], uk, f);
+    double sq = sqrt(D->delta[i]);
+    for (int c = 0; c < d; ++c) {
+      Y[i + 1][c] = Y[i][c] + D->delta[i] * f[c] + P->sigma[c] * sq * D->Z[i][c];
+      if (i < D->n) Y[i + 1][c] += P->jump_scale * D->xi_hat[i][c];
+    }
+  }
+}
+
+static double running_cost(const orc_problem *P, const double *x, int k) {
+  double s = 0.0;
+  for (int i = 0; i < P->d; ++i) {
+    double e = x[i] - P->xd[k * P->d + i];
+    s += P->q[i] * e * e;
+  }
+  return 0.5 * s;
+}
+
+static int valid(const orc_problem *P) {
+  if (!P || P->d < 1 || P->d > ORC_DMAX || P->du < 1 || P->du > ORC_DUMAX || P->Nt < 1 ||
+      P->M < 1 || !(P->T > 0.0))
+    return 0;
+  if (!P->A || !P->B || !P->sigma || !P->x0 || !P->q || !P->xd) return 0;
+  if (P->drift == ORC_CUBIC && !P->C) return 0;
+  if (P->jump_law < 0 || P->jump_law > 2) return 0;
+  return 1;
+}
+
+int orc_path(const orc_problem *P, const double *u, int64_t m, double *X, double *lam, double *G,
+             double *cost, double *gtheta, int *njumps) {
+  if (!valid(P) || !u || m < 0 || m >= P->M) return 1;
+  const int d = P->d, du = P->du, Nt = P->Nt;
+  const double dt = P->T / (double)Nt;
+  double *Xs = X ? X : (double *)malloc(sizeof(double) * (size_t)(Nt + 1) * d);
+  orc_draws *D = (orc_draws *)malloc(sizeof(orc_draws));
+  double (*Y)[ORC_DMAX] = (double (*)[ORC_DMAX])malloc(sizeof(double) * ORC_DMAX * (ORC_NMAX + 2));
+  if (!Xs || !D || !Y) return 2;
+
+  /* forward sweep */
+  memcpy(Xs, P->x0, sizeof(double) * d);
+  double c_m = 0.0;
+  for (int k = 0; k < Nt; ++k) {
+    orc_step_draws(P, k, m, D);
+    if (njumps) njumps[k] = D->n;
+    integrate_step(P, D, Xs + (size_t)k * d, u + (size_t)k * du, Y);
+    memcpy(Xs + (size_t)(k + 1) * d, Y[D->n + 1], sizeof(double) * d);
+    c_m += dt * running_cost(P, Xs + (size_t)(k + 1) * d, k + 1);
+  }
+  if (cost) *cost = c_m;
+
+  /* adjoint sweep: mu is the derivative of the path cost with respect to the
+   * current state, carried backwards through every sub-step */
+  if (G || lam || gtheta) {
+    double mu[ORC_DMAX], jt[ORC_DMAX];
+    if (gtheta) memset(gtheta, 0, sizeof(double) * (d + 2));
+    for (int i = 0; i < d; ++i)
+      mu[i] = dt * P->q[i] * (Xs[(size_t)Nt * d + i] - P->xd[(size_t)Nt * d + i]);
+    if (lam) memcpy(lam + (size_t)Nt * d, mu, sizeof(double) * d);
+    for (int k = Nt - 1; k >= 0; --k) {
+      orc_step_draws(P, k, m, D);
+      integrate_step(P, D, Xs + (size_t)k * d, u + (size_t)k * du, Y);
+      double g[ORC_DUMAX];
+      memset(g, 0, sizeof(g));
+      for (int i = D->n; i >= 0; --i) {
+        /* mu = derivative w.r.t. Y[i+1]; the additive jump after sub-step i has
+         * identity Jacobian, so it is also the derivative w.r.t. the pre-jump state */
+        if (gtheta && i < D->n)
+          for (int c = 0; c < d; ++c) gtheta[d + 1] += mu[c] * D->xi_hat[i][c];
+        for (int l = 0; l < du; ++l) {
+          double s = 0.0;
+          for (int c = 0; c < d; ++c) s += P->B[c * du + l] * mu[c];
+          g[l] += D->delta[i] * s;
+        }
+        if (gtheta) {
+          double sq = sqrt(D->delta[i]);
+          for (int c = 0; c < d; ++c) gtheta[1 + c] += mu[c] * sq * D->Z[i][c];
+          if (P->dA) {
+            double s = 0.0;
+            for (int r = 0; r < d; ++r)
+              for (int c = 0; c < d; ++c) s += mu[r] * P->dA[r * d + c] * Y[i][c];
+            gtheta[0] += D->delta[i] * s;
+          }
+        }
+        drift_jacobian_T(P, Y[i], mu, jt);
+        for (int c = 0; c < d; ++c) mu[c] = mu[c] + D->delta[i] * jt[c];
+      }
+      if (G) memcpy(G + (size_t)k * du, g, sizeof(double) * du);
+      if (k >= 1)
+        for (int c = 0; c < d; ++c)
+          mu[c] += dt * P->q[c] * (Xs[(size_t)k * d + c] - P->xd[(size_t)k * d + c]);
+      if (lam) memcpy(lam + (size_t)k * d, mu, sizeof(double) * d);
+    }
+  }
+  if (!X) free(Xs);
+  free(D);
+  free(Y);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Sums over paths: fixed chunks of ORC_CHUNK paths, summed in path order;      */
+/* chunk sums are then added in chunk order.  Threads only pick chunks.        */
+/* ------------------------------------------------------------------------- */
+#define ORC_CHUNK 256
+
+typedef struct {
+  const orc_problem *P;
+  const double *u;
+  int want_grad, want_theta;
+  int64_t nchunks;
+  double *chunk_cost;   /* nchunks */
+  double *chunk_grad;   /* nchunks * Nt * du */
+  double *chunk_theta;  /* nchunks * (d+2) */
+  int64_t next;
+  pthread_mutex_t lock;
+  int err;
+} sweep_job;
+
+static void *sweep_worker(void *arg) {
+  sweep_job *J = (sweep_job *)arg;
+  const orc_problem *P = J->P;
+  const int Nt = P->Nt, du = P->du, d = P->d;
+  double *G = (double *)malloc(sizeof(double) * (size_t)Nt * du);
+  double gth[ORC_DMAX + 2];
+  for (;;) {
+    pthread_mutex_lock(&J->lock);
+    int64_t c = J->next++;
+    pthread_mutex_unlock(&J->lock);
+    if (c >= J->nchunks) break;
+    double cs = 0.0;
+    double *cg = J->want_grad ? J->chunk_grad + (size_t)c * Nt * du : NULL;
+    double *ct = J->want_theta ? J->chunk_theta + (size_t)c * (d + 2) : NULL;
+    if (cg) memset(cg, 0, sizeof(double) * (size_t)Nt * du);
+    if (ct) memset(ct, 0, sizeof(double) * (d + 2));
+    int64_t m_end = (c + 1) * ORC_CHUNK < P->M ? (c + 1) * ORC_CHUNK : P->M;
+    for (int64_t m = c * ORC_CHUNK; m < m_end; ++m) {
+      double cm = 0.0;
+      int rc = orc_path(P, J->u, m, NULL, NULL, cg ? G : NULL, &cm, ct ? gth : NULL, NULL);
+      if (rc) J->err = rc;
+      cs += cm;
+      if (cg)
+        for (size_t t = 0; t < (size_t)Nt * du; ++t) cg[t] += G[t];
+      if (ct)
+        for (int t = 0; t < d + 2; ++t) ct[t] += gth[t];
+    }
+    J->chunk_cost[c] = cs;
+  }
+  free(G);
+  return NULL;
+}
+
+static int sweep(const orc_problem *P, const double *u, int nthreads, int want_grad, int want_theta,
+                 double *J, double *grad, double *gtheta) {
+  if (!valid(P) || !u) return 1;
+  const int Nt = P->Nt, du = P->du, d = P->d;
+  const double dt = P->T / (double)Nt;
+  sweep_job job;
+  memset(&job, 0, sizeof(job));
+  job.P = P;
+  job.u = u;
+  job.want_grad = want_grad;
+  job.want_theta = want_theta;
+  job.nchunks = (P->M + ORC_CHUNK - 1) / ORC_CHUNK;
+  job.chunk_cost = (double *)calloc((size_t)job.nchunks, sizeof(double));
+  if (want_grad) job.chunk_grad = (double *)calloc((size_t)job.nchunks * Nt * du, sizeof(double));
+  if (want_theta) job.chunk_theta = (double *)calloc((size_t)job.nchunks * (d + 2), sizeof(double));
+  pthread_mutex_init(&job.lock, NULL);
+  if (nthreads < 1) nthreads = 1;
+  if (nthreads > 256) nthreads = 256;
+  pthread_t th[256];
+  for (int t = 0; t < nthreads; ++t) pthread_create(&th[t], NULL, sweep_worker, &job);
+  for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+  pthread_mutex_destroy(&job.lock);
+
+  /* J = (1/M) sum_m c_m + (nu/2) dt sum_k |u_k|^2 */
+  double csum = 0.0;
+  for (int64_t c = 0; c < job.nchunks; ++c) csum += job.chunk_cost[c];
+  double usq = 0.0;
+  for (size_t t = 0; t < (size_t)Nt * du; ++t) usq += u[t] * u[t];
+  if (J) *J = csum / (double)P->M + 0.5 * P->nu * dt * usq;
+
+  /* dJ/du_k = nu dt u_k + (1/M) sum_m G_k^m */
+  if (want_grad && grad) {
+    for (size_t t = 0; t < (size_t)Nt * du; ++t) {
+      double s = 0.0;
+      for (int64_t c = 0; c < job.nchunks; ++c) s += job.chunk_grad[(size_t)c * Nt * du + t];
+      grad[t] = P->nu * dt * u[t] + s / (double)P->M;
+    }
+  }
+  if (want_theta && gtheta) {
+    for (int t = 0; t < d + 2; ++t) {
+      double s = 0.0;
+      for (int64_t c = 0; c < job.nchunks; ++c) s += job.chunk_theta[(size_t)c * (d + 2) + t];
+      gtheta[t] = s / (double)P->M;
+    }
+  }
+  int err = job.err;
+  free(job.chunk_cost);
+  free(job.chunk_grad);
+  free(job.chunk_theta);
+  return err;
+}
+
+int orc_cost(const orc_problem *P, const double *u, int nthreads, double *J) {
+  return sweep(P, u, nthreads, 0, 0, J, NULL, NULL);
+}
+
+int orc_gradient(const orc_problem *P, const double *u, int nthreads, double *J, double *grad,
+                 double *gtheta) {
+  return sweep(P, u, nthreads, 1, gtheta != NULL, J, grad, gtheta);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Projected gradient descent with the Armijo rule (Algorithm 5.4).            */
+/* g = (dJ/du)/dt is the L2 representative of the gradient; the trial point is  */
+/* u+ = clip(u - zeta g); accept when J(u+) <= J(u) + c <g, u+ - u>_{L2}, which  */
+/* without active bounds is J(u) - c zeta |g|^2_{L2} (eq:Stochastic_Armijo).     */
+/* ------------------------------------------------------------------------- */
+static double clip(double v, double lo, double hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+int orc_optimize(const orc_problem *P, double *u, const orc_opt_params *o, int nthreads,
+                 orc_opt_result *r, double *J_hist) {
+  if (!valid(P) || !u || !o || !r) return 1;
+  const size_t n = (size_t)P->Nt * P->du;
+  const double dt = P->T / (double)P->Nt;
+  double *grad = (double *)malloc(sizeof(double) * n);
+  double *g = (double *)malloc(sizeof(double) * n);
+  double *ut = (double *)malloc(sizeof(double) * n);
+  memset(r, 0, sizeof(*r));
+  double J = 0.0, pg0 = -1.0, zeta = o->zeta0 > 0 ? o->zeta0 : 1.0;
+  double zeta_max = o->zeta_max > 0 ? o->zeta_max : 1e3;
+  int status = 0, it = 0;
+  for (it = 0;; ++it) {
+    int rc = orc_gradient(P, u, nthreads, &J, grad, NULL);
+    r->evals++;
+    if (rc) { status = 1; break; }
+    if (J_hist) J_hist[it] = J;
+    /* projected-gradient norm |P(u - g) - u|_{L2} */
+    double pg = 0.0;
+    for (size_t t = 0; t < n; ++t) {
+      g[t] = grad[t] / dt;
+      double e = clip(u[t] - g[t], P->u_min, P->u_max) - u[t];
+      pg += dt * e * e;
+    }
+    pg = sqrt(pg);
+    if (pg0 < 0.0) pg0 = pg;
+    r->rel_grad_norm = pg0 > 0.0 ? pg / pg0 : 0.0;
+    if (r->rel_grad_norm <= o->tol_rel_grad || it >= o->max_iter) break;
+
+    /* Armijo backtracking on the projected path */
+    if (it > 0) zeta = fmin(2.0 * zeta, zeta_max);
+    int accepted = 0;
+    double Jt = 0.0, step2 = 0.0;
+    for (int b = 0; b <= o->max_backtracks; ++b) {
+      double dot = 0.0;
+      for (size_t t = 0; t < n; ++t) {
+        ut[t] = clip(u[t] - zeta * g[t], P->u_min, P->u_max);
+        dot += dt * g[t] * (ut[t] - u[t]);
+      }
+      rc = orc_cost(P, ut, nthreads, &Jt);
+      r->evals++;
+      if (rc) { status = 1; break; }
+      if (Jt <= J + o->armijo_c * dot) { accepted = 1; break; }
+      zeta *= 0.5;
+    }
+    if (status) break;
+    if (!accepted) { status = 5; break; }
+    step2 = 0.0;
+    for (size_t t = 0; t < n; ++t) {
+      step2 += dt * (ut[t] - u[t]) * (ut[t] - u[t]);
+      u[t] = ut[t];
+    }
+    J = Jt;
+    if (sqrt(step2) < o->tol_step) {
+      it++;
+      if (J_hist) J_hist[it] = J;
+      break;
+    }
+  }
+  r->iters = it;
+  r->J = J;
+  r->zeta = zeta;
+  r->status = status;
+  free(grad);
+  free(g);
+  free(ut);
+  return status;
+}

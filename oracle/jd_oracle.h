@@ -1,0 +1,127 @@
+/*
+ * jd_oracle.h -- plain FP64 CPU oracle for the discretize-then-optimize method of
+ * "Adjoint-based optimal control of jump-diffusion processes" (arXiv 2505.04328).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library.  It shares no code, header,
+ * table or constant generator with the CUDA path; it implements the same
+ * counter-based random streams independently, from the published Philox4x32-10
+ * definition (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as
+ * 1, 2, 3", SC'11).
+ *
+ * What is computed (paper section / equation in brackets):
+ *   - controlled SDE dX = f(X,u) dt + sigma dB + dY with additive compound-Poisson
+ *     jumps [Sec. 1 eq:SDE_general; Sec. 2 eq:compact_forward], drift
+ *     f(x,u) = A x + C (x*x*x) + B u [Sec. 5.4 eq:coefficients, H <-> A, h <-> C x^3];
+ *   - jump-adapted Euler-Maruyama grid: per uniform step the jump times split the
+ *     step into sub-steps [Sec. 3 eq:Deterministic_timestep and the grid union that
+ *     follows it; Algorithm 5.1; Algorithm 5.2];
+ *   - discrete cost  J(u) = (1/M) sum_m sum_{k=1..Nt} dt l(X_k^m, t_k)
+ *                        + (nu/2) dt sum_{k=0..Nt-1} |u_k|^2,
+ *     l(x,t) = 1/2 sum_i q_i (x_i - xd_i(t))^2   [Sec. 3 eq:discrete_functional];
+ *   - the exact discrete adjoint and the reduced gradient [Sec. 4 eq:AdjointModel,
+ *     eq:definition_Gradient; Sec. 5.5 eq:adjoint_eq_approximation];
+ *   - projected gradient descent with the Armijo rule [Sec. 5.6 eq:Stochastic_Armijo,
+ *     Algorithm 5.4].
+ */
+#ifndef JD_ORACLE_H
+#define JD_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_DMAX 64      /* largest state dimension the oracle accepts */
+#define ORC_DUMAX 16     /* largest control dimension */
+#define ORC_NMAX 16      /* jumps per uniform step are capped at this count */
+
+enum { ORC_LINEAR = 0, ORC_CUBIC = 1 };
+enum { ORC_JUMP_NONE = 0, ORC_JUMP_NORMAL = 1, ORC_JUMP_UNIFORM = 2 };
+
+typedef struct {
+  int d, du, Nt;
+  int64_t M;
+  double T;
+  int drift;                 /* ORC_LINEAR or ORC_CUBIC */
+  const double *A;           /* d*d row-major */
+  const double *C;           /* d*d row-major, used when drift == ORC_CUBIC */
+  const double *B;           /* d*du row-major */
+  const double *dA;          /* d*d direction for the drift-coefficient gradient, or NULL */
+  const double *sigma;       /* d, diagonal additive diffusion */
+  double lambda;             /* jump intensity */
+  int jump_law;              /* ORC_JUMP_* */
+  double jump_scale;         /* std (NORMAL) or half-width (UNIFORM) */
+  const double *x0;          /* d */
+  const double *q;           /* d, diagonal tracking weights */
+  const double *xd;          /* (Nt+1)*d target samples xd(t_k) */
+  double nu, u_min, u_max;
+  uint64_t seed;
+  uint32_t epoch;
+} orc_problem;
+
+/* One Philox4x32-10 block: out = Philox(key, ctr). */
+void orc_philox4x32_10(const uint32_t key[2], const uint32_t ctr[4], uint32_t out[4]);
+
+/* Uniform in (0,1) from one word: ((w >> 9) + 1/2) * 2^-23. */
+double orc_u01(uint32_t w);
+
+/* Poisson-count thresholds T_n = floor(2^32 F(n; mu)), n = 0..ORC_NMAX-1 (values in [0, 2^32]). */
+void orc_poisson_thresholds(double mu, uint64_t thr[ORC_NMAX]);
+
+/* The random draws of one uniform step, in the order the integrator uses them. */
+typedef struct {
+  int n;                                   /* jumps in this step */
+  double theta[ORC_NMAX];                  /* sorted jump-time fractions in (0,1) */
+  double delta[ORC_NMAX + 1];              /* sub-step lengths */
+  double Z[ORC_NMAX + 1][ORC_DMAX];        /* standard normals per sub-step */
+  double xi_hat[ORC_NMAX][ORC_DMAX];       /* unit jump sizes, time order */
+} orc_draws;
+
+/* Draws of step k of path m (used by tests to check the jump law and to drive
+ * independent re-derivations). */
+int orc_step_draws(const orc_problem *P, int k, int64_t m, orc_draws *out);
+
+/* One path: forward sweep, optional adjoint sweep.
+ *   X      (Nt+1)*d states on the uniform grid, or NULL
+ *   lam    (Nt+1)*d adjoint states lambda_k, or NULL (lambda_0 = derivative w.r.t. X_0)
+ *   G      Nt*du per-path control sensitivities sum_i delta_i B^T lambda', or NULL
+ *          (NULL also skips the adjoint sweep unless gtheta or lam is given)
+ *   cost   per-path running cost sum_k dt l(X_k, t_k), or NULL
+ *   gtheta d+2 per-path parameter sensitivities [dA-direction, sigma_0..sigma_{d-1},
+ *          jump_scale], or NULL
+ *   njumps Nt jump counts, or NULL
+ * u is Nt*du.  Returns 0 on success, nonzero on invalid input. */
+int orc_path(const orc_problem *P, const double *u, int64_t m, double *X, double *lam,
+             double *G, double *cost, double *gtheta, int *njumps);
+
+/* Reduced cost J(u), paths summed in fixed chunks so the result does not depend on
+ * nthreads. */
+int orc_cost(const orc_problem *P, const double *u, int nthreads, double *J);
+
+/* J(u) and the Euclidean gradient dJ/du_k (Nt*du); gtheta (d+2, nullable) is the
+ * gradient with respect to [drift direction dA, sigma_i, jump_scale]. */
+int orc_gradient(const orc_problem *P, const double *u, int nthreads, double *J,
+                 double *grad, double *gtheta);
+
+typedef struct {
+  int max_iter;
+  double tol_rel_grad, tol_step, armijo_c, zeta0, zeta_max;
+  int max_backtracks;
+} orc_opt_params;
+
+typedef struct {
+  int iters, evals, status;     /* status 0 ok, 5 = line search failed */
+  double J, rel_grad_norm, zeta;
+} orc_opt_result;
+
+/* Projected gradient descent with the Armijo rule.  u is updated in place.
+ * J_hist (max_iter+1, nullable) receives J(u^n) for every iterate that was evaluated. */
+int orc_optimize(const orc_problem *P, double *u, const orc_opt_params *o, int nthreads,
+                 orc_opt_result *r, double *J_hist);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
