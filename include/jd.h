@@ -1,0 +1,184 @@
+/*
+ * jd.h -- C ABI of the GB300 (sm_103a) library for adjoint-based optimal control of
+ * jump-diffusion processes, after "Adjoint-based optimal control of jump-diffusion
+ * processes" (arXiv 2505.04328).
+ *
+ * The library evaluates, for a time-dependent control u = (u_0, ..., u_{Nt-1}),
+ * u_k in R^du constant on [t_k, t_{k+1}) (Sec. 3 eq:piecewise_constant_control),
+ *
+ *   J(u) = (1/M) sum_m sum_{k=1..Nt} dt l(X_k^m, t_k) + (nu/2) dt sum_k |u_k|^2
+ *          (Sec. 3 eq:discrete_functional),  l(x,t) = 1/2 sum_i q_i (x_i - xd_i(t))^2,
+ *
+ * where each path X^m solves the controlled SDE dX = f(X,u) dt + diag(sigma) dB + dY
+ * (Sec. 1 eq:SDE_general, Sec. 2 eq:compact_forward) with drift
+ * f(x,u) = A x + C (x*x*x) + B u (Sec. 5.4 eq:coefficients: H <-> A, h <-> C x^3) and
+ * additive compound-Poisson jumps Y of intensity lambda, discretized by Euler-Maruyama
+ * on the jump-adapted grid (Sec. 3 eq:Deterministic_timestep; Algorithms 5.1, 5.2);
+ * and its exact discrete gradient by the backward adjoint sweep (Sec. 4
+ * eq:AdjointModel, eq:definition_Gradient; Sec. 5.5 eq:adjoint_eq_approximation).
+ *
+ * Random numbers: counter-based Philox4x32-10 (Salmon et al., SC'11).  Key = seed
+ * (low word, high word).  Step k of path m draws its Poisson count and sub-step-0
+ * normals from the blocks with counter (k, m, b, epoch), b = 0, 1, ...; jump slot i
+ * (i = 1..n) draws from counter (k, m, 1<<24 | i<<16 | b, epoch).  A result therefore
+ * depends only on (seed, epoch, path index, step index), never on launch geometry.
+ *
+ * Conventions for every function:
+ *   - returns a jd_status; no exception or abort crosses the ABI; a message for the
+ *     last failure of the calling thread is available from jd_last_error();
+ *   - the caller owns every buffer passed in; jd_problem_create deep-copies the
+ *     descriptor's arrays, so they may be freed after it returns;
+ *   - arrays are row-major float64.  A pointer tagged JD_MEM_DEVICE is a CUDA device
+ *     pointer read or written on the problem's stream; JD_MEM_HOST is host memory;
+ *   - calls that write host memory synchronize the problem's stream before
+ *     returning; calls whose outputs are all device pointers return without
+ *     synchronizing (results are ready in stream order).
+ *   - a problem object is not thread-safe: calls on one problem must not overlap.
+ */
+#ifndef JD_H
+#define JD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  JD_OK = 0,
+  JD_ERR_INVALID_ARG = 1,  /* bad size, NULL where required, non-finite input */
+  JD_ERR_OOM = 2,          /* device allocation failed or the plan exceeds the memory budget */
+  JD_ERR_CUDA = 3,         /* a CUDA runtime call failed (message in jd_last_error) */
+  JD_ERR_NONFINITE = 4,    /* the cost or gradient came out NaN or Inf */
+  JD_ERR_LINESEARCH = 5,   /* Armijo backtracking exhausted max_backtracks */
+  JD_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up */
+  JD_ERR_UNSUPPORTED = 7,  /* valid request this build does not implement (e.g. d > 32) */
+  JD_ERR_BUSY = 8          /* serving: result not ready yet */
+} jd_status;
+
+typedef enum { JD_DRIFT_LINEAR = 0, JD_DRIFT_CUBIC = 1 } jd_drift;
+typedef enum { JD_JUMP_NONE = 0, JD_JUMP_NORMAL = 1, JD_JUMP_UNIFORM = 2 } jd_jump_law;
+typedef enum { JD_FP32 = 0, JD_FP64 = 1 } jd_precision;
+typedef enum { JD_ADJ_AUTO = 0, JD_ADJ_STORED = 1, JD_ADJ_RECOMPUTE = 2 } jd_adjoint_mode;
+typedef enum { JD_MEM_HOST = 0, JD_MEM_DEVICE = 1 } jd_memspace;
+
+/* Problem descriptor (Sec. 3 eq:OCP_fully_discrete with the additive jump map).
+ *   d, du        state and control dimensions, 1 <= d <= 32, 1 <= du <= 4
+ *   T, Nt, M     horizon, uniform steps (dt = T/Nt), Monte Carlo paths (M < 2^32)
+ *   drift        LINEAR (C ignored) or CUBIC
+ *   A, C         d*d; B d*du; dA d*d direction for the drift-coefficient gradient
+ *                (A(theta) = A + theta dA), NULL if not needed
+ *   sigma        d, diagonal additive diffusion
+ *   lambda       jump intensity; jump_law NONE/NORMAL (N(0, jump_scale^2) per
+ *                component) / UNIFORM (U[-jump_scale, jump_scale] per component)
+ *   x0           d, deterministic initial state
+ *   q            d, diagonal tracking weights; xd (Nt+1)*d, target xd(t_k)
+ *   nu           control weight (the paper's alpha); u_min, u_max box bounds
+ *   seed, epoch  Philox key and the counter's fourth word (resampling mode)
+ *   prec         JD_FP32: path arithmetic in FP32, reductions in FP64;
+ *                JD_FP64: everything in FP64
+ *   mode         adjoint variant: STORED keeps X_k in device memory; RECOMPUTE keeps
+ *                checkpoints every S steps and regenerates each segment from the
+ *                counter-based streams (exact, same result); AUTO picks STORED when it
+ *                fits mem_budget_bytes
+ *   use_tensor_cores  d = 32 LINEAR only: A x on tcgen05 tensor cores (BF16 inputs,
+ *                FP32 accumulation); 0 = CUDA cores
+ *   mem_budget_bytes  device bytes this problem may allocate, 0 = library default
+ *                (half of the free device memory at creation)
+ *   cuda_stream  cudaStream_t for all work of this problem; NULL = the library
+ *                creates its own stream
+ */
+typedef struct {
+  int d, du;
+  double T;
+  int Nt;
+  int64_t M;
+  jd_drift drift;
+  const double *A, *C, *B, *dA;
+  const double *sigma;
+  double lambda;
+  jd_jump_law jump_law;
+  double jump_scale;
+  const double *x0;
+  const double *q;
+  const double *xd;
+  double nu, u_min, u_max;
+  uint64_t seed;
+  uint32_t epoch;
+  jd_precision prec;
+  jd_adjoint_mode mode;
+  int use_tensor_cores;
+  size_t mem_budget_bytes;
+  void *cuda_stream;
+} jd_problem_desc;
+
+typedef struct jd_problem jd_problem;
+
+/* Validate and copy a descriptor; upload coefficients; no path memory is allocated
+ * yet.  Errors: INVALID_ARG (sizes, NULL arrays, non-finite values, u_min > u_max),
+ * UNSUPPORTED (d > 32, du > 4, use_tensor_cores with d != 32 or CUBIC), CUDA. */
+jd_status jd_problem_create(const jd_problem_desc *desc, jd_problem **out);
+jd_status jd_problem_destroy(jd_problem *p);
+
+/* J(u) (eq:discrete_functional): forward sweep and cross-path reduction.
+ * u: Nt*du in memory space us.  J: host double.  Errors: INVALID_ARG, NONFINITE, CUDA. */
+jd_status jd_cost(jd_problem *p, const double *u, jd_memspace us, double *J);
+
+/* J(u) and the Euclidean gradient grad_k = dJ/du_k = nu dt u_k + (1/M) sum_m G_k^m,
+ * G_k^m = sum over the sub-steps i of step k of delta_i B^T lambda'_i (exact discrete
+ * adjoint; eq:definition_Gradient).  J: host double, may be NULL.  grad: Nt*du in
+ * memory space gs, may be NULL.  grad_theta: host, d+2 doubles or NULL:
+ * [dJ/dtheta along dA, dJ/dsigma_0 .. dJ/dsigma_{d-1}, dJ/djump_scale].
+ * Errors: INVALID_ARG, OOM (plan does not fit), NONFINITE, CUDA. */
+jd_status jd_gradient(jd_problem *p, const double *u, jd_memspace us, double *J, double *grad,
+                      jd_memspace gs, double *grad_theta);
+
+/* Trajectories of paths m0 .. m0+count-1 (host outputs, any may be NULL):
+ * X (count, Nt+1, d) states on the uniform grid; lam (count, Nt+1, d) adjoint states
+ * lambda_k = d(path cost)/dX_k; cost (count) per-path running cost.  Uses the same
+ * kernels and streams as jd_gradient.  Errors: INVALID_ARG, OOM, CUDA. */
+jd_status jd_sample_paths(jd_problem *p, const double *u, jd_memspace us, int64_t m0,
+                          int64_t count, double *X, double *lam, double *cost);
+
+/* Projected gradient descent with the Armijo rule (Algorithm 5.4, eq:Stochastic_Armijo).
+ * With g = grad/dt (the L2 representative), the trial point is
+ * u+ = clip(u - zeta g, u_min, u_max), accepted when J(u+) <= J(u) + c <g, u+ - u>_{L2};
+ * zeta starts at zeta0, is doubled (capped at zeta_max) at the start of every later
+ * iteration and halved on rejection.  Stops when
+ * |P(u - g) - u|_{L2} <= tol_rel_grad |P(u0 - g0) - u0|_{L2}, when |u+ - u|_{L2} <
+ * tol_step, or after max_iter updates.  The Armijo test and every FP64 reduction run
+ * on the device; the host only reads the accept flag. */
+typedef struct {
+  int max_iter;
+  double tol_rel_grad, tol_step, armijo_c, zeta0, zeta_max;
+  int max_backtracks;
+} jd_opt_params;
+
+typedef struct {
+  int iters, evals;
+  double J, rel_grad_norm, zeta;
+  jd_status status;
+} jd_opt_result;
+
+/* u_inout: Nt*du in memory space us, updated in place.  J_hist: host, max_iter+1
+ * doubles or NULL (J of every iterate).  Errors: INVALID_ARG, LINESEARCH, NONFINITE,
+ * OOM, CUDA. */
+jd_status jd_optimize(jd_problem *p, double *u_inout, jd_memspace us, const jd_opt_params *o,
+                      jd_opt_result *r, double *J_hist);
+
+/* Device bytes the plan of this problem uses (after the first evaluation) and the
+ * adjoint variant in use (JD_ADJ_STORED or JD_ADJ_RECOMPUTE; JD_ADJ_AUTO before the
+ * first evaluation). */
+jd_status jd_problem_info(const jd_problem *p, size_t *device_bytes, jd_adjoint_mode *mode);
+
+/* Number of kernels this library has launched in this process (monotone counter). */
+uint64_t jd_kernel_launch_count(void);
+
+const char *jd_status_string(jd_status s);
+const char *jd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JD_H */

@@ -94,6 +94,8 @@ def lib():
             L.orc_u01.argtypes = [ctypes.c_uint32]
             L.orc_u01.restype = ctypes.c_double
             L.orc_poisson_thresholds.argtypes = [ctypes.c_double, P(ctypes.c_uint64)]
+            L.orc_poisson_count.argtypes = [ctypes.c_uint32, P(ctypes.c_uint64)]
+            L.orc_normal_pair.argtypes = [ctypes.c_uint32, ctypes.c_uint32, P(ctypes.c_double)]
             L.orc_step_draws.argtypes = [P(_Problem), ctypes.c_int, ctypes.c_int64, P(_Draws)]
             L.orc_path.argtypes = [P(_Problem), ctypes.c_void_p, ctypes.c_int64] + [ctypes.c_void_p] * 6
             L.orc_cost.argtypes = [P(_Problem), ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
@@ -152,6 +154,17 @@ def poisson_thresholds(mu: float):
     t = (ctypes.c_uint64 * NMAX)()
     lib().orc_poisson_thresholds(float(mu), t)
     return [int(x) for x in t]
+
+
+def poisson_count(w: int, thr) -> int:
+    t = (ctypes.c_uint64 * NMAX)(*[int(x) for x in thr])
+    return lib().orc_poisson_count(int(w) & 0xffffffff, t)
+
+
+def normal_pair(wa: int, wb: int):
+    z = (ctypes.c_double * 2)()
+    lib().orc_normal_pair(int(wa) & 0xffffffff, int(wb) & 0xffffffff, z)
+    return float(z[0]), float(z[1])
 
 
 def step_draws(p, k: int, m: int):

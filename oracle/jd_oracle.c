@@ -92,6 +92,16 @@ void orc_poisson_thresholds(double mu, uint64_t thr[ORC_NMAX]) {
   }
 }
 
+int orc_poisson_count(uint32_t w, const uint64_t thr[ORC_NMAX]) {
+  /* n = #{n : T_n <= w}, so that P(count <= n) = P(w < T_n) = T_n / 2^32 ~ F(n) */
+  int n = 0;
+  for (int i = 0; i < ORC_NMAX; ++i)
+    if ((uint64_t)w >= thr[i]) n++;
+  return n;
+}
+
+void orc_normal_pair(uint32_t wa, uint32_t wb, double z[2]) { normal_pair(wa, wb, &z[0], &z[1]); }
+
 static int jumps_enabled(const orc_problem *P) {
   return P->jump_law != ORC_JUMP_NONE && P->lambda > 0.0;
 }
@@ -113,8 +123,7 @@ int orc_step_draws(const orc_problem *P, int k, int64_t m, orc_draws *D) {
   if (jumps_enabled(P)) {
     uint64_t thr[ORC_NMAX];
     orc_poisson_thresholds(P->lambda * dt, thr);
-    for (int i = 0; i < ORC_NMAX; ++i)
-      if ((uint64_t)w[0] >= thr[i]) n++;
+    n = orc_poisson_count(w[0], thr);
   }
   D->n = n;
   normals_from_words(d, w + 1, D->Z[0]);

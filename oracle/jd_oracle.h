@@ -70,6 +70,13 @@ double orc_u01(uint32_t w);
 /* Poisson-count thresholds T_n = floor(2^32 F(n; mu)), n = 0..ORC_NMAX-1 (values in [0, 2^32]). */
 void orc_poisson_thresholds(double mu, uint64_t thr[ORC_NMAX]);
 
+/* Poisson count of one word: n = #{n : T_n <= w}. */
+int orc_poisson_count(uint32_t w, const uint64_t thr[ORC_NMAX]);
+
+/* Box-Muller pair from two words: the first word sets the radius
+ * sqrt(-2 ln U(wa)), the second the angle 2 pi U(wb); z = (r cos, r sin). */
+void orc_normal_pair(uint32_t wa, uint32_t wb, double z[2]);
+
 /* The random draws of one uniform step, in the order the integrator uses them. */
 typedef struct {
   int n;                                   /* jumps in this step */

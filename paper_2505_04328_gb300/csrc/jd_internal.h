@@ -1,0 +1,87 @@
+// jd_internal.h -- types shared by the host library and the path kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "jd.h"
+
+namespace jd {
+
+constexpr int NMAX = 16;   // jumps per uniform step are capped at this count
+constexpr int TPB = 128;   // threads (one path each) per block of the path kernels
+constexpr int BATCH = 8;   // steps per transposed warp reduction
+
+enum FwdMode { FWD_COST = 0, FWD_STORE = 1, FWD_CKPT = 2 };
+enum AdjVariant { ADJ_STORED_V = 1, ADJ_RECOMPUTE_V = 2 };
+
+// Kernel parameters: coefficients padded to the compiled dimensions D, DU and passed
+// by value, so the hot loop reads them as constant-bank operands.
+template <typename R, int D, int DU>
+struct KParams {
+  R A[D * D], C[D * D], dA[D * D], B[D * DU];
+  R sigma[D];      // sigma_c
+  R sig_sqdt[D];   // sigma_c * sqrt(dt)
+  R qdt[D];        // q_c * dt            (cost gradient)
+  R hqdt[D];       // q_c * dt / 2        (cost)
+  R x0[D];
+  R dt, sqdt, jump_scale;
+  unsigned long long thr[NMAX];  // Poisson thresholds floor(2^32 F(n; lambda dt))
+  uint32_t key0, key1, epoch;
+  int d, npair, Nt, cubic, jump_law, jumps_on, has_dA, S, nblk;
+  int64_t m_begin;                // global index of path 0 of this launch
+};
+
+// Per-instantiation launch table (one entry per precision x compiled dimension).
+struct PathOps {
+  int D, DU, S, elem;
+  // forward sweep: cost partials per block; optional trajectory / checkpoint stores
+  cudaError_t (*fwd)(const struct ::jd_problem *p, int mode, int64_t m_begin, int64_t mloc,
+                     const void *uk, void *traj, uint32_t *flags, void *ckpt, double *partC,
+                     cudaStream_t s);
+  // adjoint sweep: per-step gradient partials [Nt][DU][nblk]; theta partials [D+2][nblk]
+  cudaError_t (*adj)(const struct ::jd_problem *p, int variant, bool theta, int64_t m_begin,
+                     int64_t mloc, const void *uk, const void *traj, const uint32_t *flags,
+                     const void *ckpt, double *partG, double *partT, void *lam_out,
+                     cudaStream_t s);
+};
+
+const PathOps *path_ops(int prec, int D);
+int compiled_dim(int d);         // smallest compiled D >= d, or 0
+int compiled_du(int D);          // control dimension compiled for D
+
+void count_launch(int n = 1);
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace jd
+
+// Host-side problem object (opaque to the ABI user).
+struct jd_problem {
+  jd_problem_desc desc;              // scalars; array pointers are cleared
+  std::vector<double> A, C, B, dA, sigma, x0, q, xd;
+  int D = 0, DU = 0;
+  const jd::PathOps *ops = nullptr;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  size_t budget = 0;
+  jd_adjoint_mode plan = JD_ADJ_AUTO;
+  // device buffers
+  void *uk = nullptr;        // kernel-precision padded control, Nt*DU
+  void *xdk = nullptr;       // kernel-precision padded target, (Nt+1)*D
+  double *u_in = nullptr;    // FP64 control copy, Nt*du
+  double *grad_d = nullptr;  // FP64 gradient, Nt*du
+  double *scal_d = nullptr;  // FP64 scalars: J, theta grads, optimizer values
+  double *partC = nullptr, *partG = nullptr, *partT = nullptr;
+  void *traj = nullptr;
+  uint32_t *flags = nullptr;
+  void *ckpt = nullptr;
+  double *opt_u = nullptr, *opt_ut = nullptr, *opt_g = nullptr;
+  double *host_pinned = nullptr;  // small pinned staging buffer
+  size_t bytes = 0;
+  int64_t nblk = 0;
+};

@@ -48,6 +48,21 @@ def test_fd_cubic_random_directions(maker):
             assert abs(fd - dd) <= 2e-7 * np.linalg.norm(g) + 1e-12, (h, fd, dd)
 
 
+def test_fd_harmonic_oscillator_nonsymmetric():
+    """The paper's H = [[0, 1], [-eta, 0]] (Sec. 5.4 eq:coefficients) with a cubic term:
+    a non-symmetric Jacobian, so a transposed A or C in the adjoint fails here."""
+    p = workloads.double_well(M=256, Nt=60).replace(
+        A=np.array([[0.0, 1.0], [-1.0, -0.2]]), C=np.array([[0.0, 0.0], [-0.5, 0.0]]))
+    u = workloads.random_control(p, scale=0.5)
+    _, g, _ = oracle.gradient(p, u)
+    rng = np.random.default_rng(11)
+    for _ in range(4):
+        e = rng.standard_normal(u.shape)
+        e /= np.linalg.norm(e)
+        fd = _fd(lambda v: oracle.cost(p, v), u, e, 1e-4)
+        assert abs(fd - (g * e).sum()) <= 2e-7 * np.linalg.norm(g)
+
+
 def test_fd_linear32_multicontrol():
     p = workloads.linear_family(8, M=128, Nt=30, lam=2.0)
     u = workloads.random_control(p, scale=0.5)
@@ -93,7 +108,8 @@ def test_sympy_derivative_tiny_forced_jumps():
 
 
 def test_lambda0_is_derivative_wrt_initial_state():
-    p = workloads.double_well(M=4, Nt=120)
+    # x0 differs from the target at t = 0, so a cost term at k = 0 would show up
+    p = workloads.double_well(M=4, Nt=120).replace(x0=np.array([0.5, 0.3]))
     u = workloads.random_control(p, scale=0.4)
     for m in range(3):
         r = oracle.path(p, u, m)

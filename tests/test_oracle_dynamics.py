@@ -49,6 +49,25 @@ def test_double_well_ode_euler_order_one():
     assert np.all(np.abs(ratios - 2.0) < 0.1), ratios
 
 
+def test_harmonic_oscillator_euler_order_one():
+    """The paper's H = [[0, 1], [-eta, 0]] (Sec. 5.4): x' = v, v' = -eta x; exact
+    x = cos(w t), v = -w sin(w t) for x0 = (1, 0), w = sqrt(eta).  A transposed A
+    gives x' = -eta v, v' = x and misses this solution."""
+    eta = 2.0
+    w = np.sqrt(eta)
+    errs = []
+    for Nt in (200, 400, 800, 1600):
+        p = workloads.double_well(M=1, Nt=Nt).replace(
+            drift=workloads.LINEAR, A=np.array([[0.0, 1.0], [-eta, 0.0]]), sigma=np.zeros(2),
+            lam=0.0, x0=np.array([1.0, 0.0]))
+        X = oracle.path(p, None, 0, adjoint=False)["X"]
+        t = np.arange(Nt + 1) * p.dt
+        exact = np.stack([np.cos(w * t), -w * np.sin(w * t)], axis=1)
+        errs.append(np.abs(X - exact).max())
+    ratios = np.array(errs[:-1]) / np.array(errs[1:])
+    assert np.all(np.abs(ratios - 2.0) < 0.15), ratios
+
+
 def test_scalar_moments_match_closed_form():
     M, Nt = 6000, 200
     p = workloads.lq_scalar(M=M, Nt=Nt).replace(lam=6.0, jump_scale=0.15)

@@ -169,3 +169,27 @@ def test_streams_depend_on_seed_epoch_path_step():
         assert not np.allclose(oracle.step_draws(q, 3, 5)["Z"][0], a)
     assert not np.allclose(oracle.step_draws(p, 4, 5)["Z"][0], a)
     assert not np.allclose(oracle.step_draws(p, 3, 6)["Z"][0], a)
+
+
+def test_poisson_count_boundaries():
+    """The count is #{n : T_n <= w}: a word equal to a threshold counts it."""
+    thr = oracle.poisson_thresholds(0.5)
+    assert oracle.poisson_count(0, thr) == 0
+    assert oracle.poisson_count(thr[0] - 1, thr) == 0
+    assert oracle.poisson_count(thr[0], thr) == 1
+    assert oracle.poisson_count(thr[1] - 1, thr) == 1
+    assert oracle.poisson_count(thr[1], thr) == 2
+    assert oracle.poisson_count(0xFFFFFFFF, thr) == sum(1 for t in thr if t <= 0xFFFFFFFF)
+
+
+def test_normal_pair_radius_and_angle_words():
+    """Convention: the first word sets the radius, the second the angle."""
+    w_small = 0x00000200          # U = 1.5 * 2^-23: large radius
+    w_quarter = 0x40000000        # U = 1/4 + 2^-24: angle pi/2 + tiny
+    z0, z1 = oracle.normal_pair(w_small, w_quarter)
+    r = np.sqrt(-2 * np.log(oracle.u01(w_small)))
+    assert r > 5.5
+    assert abs(z1 - r) < 1e-6 * r and abs(z0) < 1e-5 * r
+    # angle 0 (U -> 2^-24): the pair lies on the positive first axis
+    z0, z1 = oracle.normal_pair(0x80000000, 0)
+    assert z0 > 0 and abs(z1) < 1e-6
