@@ -1,0 +1,350 @@
+#!/usr/bin/env python3
+"""Benchmark: forward+adjoint path-steps/s of the projected-gradient Armijo iteration.
+
+One step = one iteration of the optimizer (Algorithm 5.4) on the d=2 double-well
+jump-diffusion workload (M = 2^20 paths, N_t = 1000 steps, FP32 paths, FP64
+reductions): the gradient (forward sweep with stored trajectories, adjoint sweep,
+cross-path reductions), the Armijo line search (forward cost sweeps and the FP64
+test) and the projected update.  value = M * N_t gradient path-steps per step / time
+per step, so line-search sweeps count as overhead.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--variant stored|recompute]
+
+Under torchrun (N > 1) every rank solves its own independent problem instance (the
+same workload with Philox seed = rank): weak scaling, no collective on the data path;
+only the timing is reduced (max over ranks).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "forward+adjoint path-steps/s vs roofline; ∇Ĵ error vs FP64; serve p50/p99 latency"
+UNIT = "path-steps/s"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms (start before the
+    timed region, stop after)."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def replica_problem(p, rank: int):
+    """Rank r solves an independent instance: same workload, Philox seed p.seed + r."""
+    return p.replace(seed=p.seed + rank)
+
+
+def max_over_ranks(dist, value: float, device="cpu") -> float:
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def bench_workload(M=None, Nt=None):
+    p = workloads.double_well()
+    if M is not None:
+        p = p.replace(M=M)
+    if Nt is not None:
+        p = p.replace(Nt=Nt)
+    return p
+
+
+# --------------------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# --------------------------------------------------------------------------------------
+def oracle_step_rate(p_sample, steps: int, warmup: int):
+    """Time `steps` oracle optimizer iterations (gradient + Armijo search + update) on a
+    bounded sample of the workload; returns (path-steps/s, seconds per step, threads)."""
+    import oracle
+    threads = oracle.default_threads()
+    u = np.zeros((p_sample.Nt, p_sample.du))
+    zeta = 1.0
+    for _ in range(warmup):
+        u, r, _ = oracle.optimize(p_sample, u, max_iter=1, tol_rel_grad=0.0, zeta0=zeta)
+        zeta = min(2 * r["zeta"], 1e3)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        u, r, _ = oracle.optimize(p_sample, u, max_iter=1, tol_rel_grad=0.0, zeta0=zeta)
+        zeta = min(2 * r["zeta"], 1e3)
+    dt = (time.perf_counter() - t0) / max(1, steps)
+    return p_sample.M * p_sample.Nt / dt, dt, threads
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    full = bench_workload()
+    sample_M = args.reference_paths
+    ps = full.replace(M=sample_M)
+    rate, sec, threads = oracle_step_rate(ps, args.steps, args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "double_well d=2 M=2^20 Nt=1000 (oracle on a path sample)",
+                   "d": full.d, "M": full.M, "Nt": full.Nt, "sample_paths": sample_M},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{sample_M} of {full.M} paths, all {full.Nt} steps, one "
+                                   "optimizer iteration per step"},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import paper_2505_04328_gb300 as jd
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    jd.build()
+    stream = torch.cuda.current_stream()
+
+    p = replica_problem(bench_workload(args.paths, args.steps_t), rank)
+    M, Nt, du = p.M, p.Nt, p.du
+    prob = jd.JdProblem(p, prec="fp32", mode=args.variant, stream=stream)
+    n = Nt * du
+    u = torch.zeros(n, dtype=torch.float64, device="cuda")
+    g = torch.empty(n, dtype=torch.float64, device="cuda")
+    state = {"zeta": 1.0}
+
+    def step(u_t):
+        # one optimizer iteration through the C ABI on device-resident u
+        _, r, _ = prob_optimize_device(prob, u_t, state["zeta"])
+        state["zeta"] = min(2 * r["zeta"], 1e3)
+        return r
+
+    for _ in range(args.warmup):
+        step(u)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    jd.profile_enable(True)
+    l0 = jd.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    evals = 0
+    for _ in range(args.steps):
+        r = step(u)
+        evals += r["evals"]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = jd.launch_count() - l0
+    kstats = jd.profile_read()
+    jd.profile_enable(False)
+    clk = clocks.stop()
+    if dist is not None:
+        ms = max_over_ranks(dist, ms, device="cuda")
+    ms_per_step = ms / args.steps
+    value = ws * M * Nt / (ms_per_step * 1e-3)
+
+    # end to end through the public API with host buffers: per step the control goes
+    # host -> device, the iteration runs, the new control and J come back to the host
+    u_host = u.cpu().numpy().reshape(Nt, du).copy()
+    zeta = state["zeta"]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u_host, r, _ = prob.optimize(u_host, max_iter=1, tol_rel_grad=0.0, zeta0=zeta)
+        zeta = min(2 * r["zeta"], 1e3)
+    e2e_sec = (time.perf_counter() - t0) / args.steps
+    e2e = {"value": ws * M * Nt / e2e_sec, "unit": UNIT,
+           "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8 + 8}
+
+    peaks, peak_kind = _peaks()
+    roofline = roofline_line(kstats, p, args, peaks, peak_kind)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"double_well d=2 M=2^{int(math.log2(M))} Nt={Nt}",
+                       "variant": prob.info()["mode"], "paths_per_gpu": M, "Nt": Nt,
+                       "evals_per_step": evals / args.steps,
+                       "l2": "stored trajectories (%.1f GB) exceed the 129 MB L2; no flush"
+                             % (prob.info()["device_bytes"] / 1e9)},
+            "gpu_launches": launches,
+            "kernels_ms_per_step": {k: v[1] / args.steps for k, v in kstats.items()},
+            "roofline": roofline,
+            "e2e": e2e,
+            "clocks": clk,
+        }
+        if not args.no_cpu_baseline:
+            rate, sec, threads = oracle_step_rate(p.replace(M=args.reference_paths), 1, 0)
+            line["cpu_baseline"] = {
+                "value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                "sample": f"{args.reference_paths} of {M} paths, all {Nt} steps, one optimizer "
+                          "iteration"}
+        print(json.dumps(line), flush=True)
+    prob.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def prob_optimize_device(prob, u_t, zeta0):
+    """One jd_optimize iteration on a device-resident control tensor (in place)."""
+    import ctypes
+    from paper_2505_04328_gb300 import binding as b
+    o = b.OptParams(max_iter=1, tol_rel_grad=0.0, tol_step=0.0, armijo_c=1e-4, zeta0=zeta0,
+                    zeta_max=1e3, max_backtracks=40)
+    r = b.OptResult()
+    st = b.lib().jd_optimize(prob.h, ctypes.c_void_p(u_t.data_ptr()), b.JD_MEM_DEVICE,
+                             ctypes.byref(o), ctypes.byref(r), None)
+    b._check(st, "jd_optimize")
+    return u_t, dict(iters=r.iters, evals=r.evals, J=r.J, zeta=r.zeta), None
+
+
+# Algorithmic work per path-step:
+#  adj_stored reads one stored state (d FP32 values) per path-step and its jump-flag
+#  bit: 4 d + 1/8 bytes.  fwd_store writes the same: 4 d + 1/8 bytes.
+def roofline_line(kstats, p, args, peaks, peak_kind):
+    M, Nt, d = p.M, p.Nt, p.d
+    if not kstats:
+        return None
+    dom = max(kstats.items(), key=lambda kv: kv[1][1])
+    name, (launches, total_ms) = dom
+    per_launch_s = total_ms / launches * 1e-3
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    if name in ("adj_stored", "fwd_store"):
+        bytes_per = (4 * d + 0.125) * M * Nt
+        achieved = bytes_per / per_launch_s / 1e9
+        return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "peak_source": peak_kind}
+    # RNG/ALU-bound sweeps: issue-slot roofline (lane-instructions per second)
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak_ginst = 152 * 4 * 32 * sm_mhz * 1e6 / 1e9    # lane-instr/s in G
+    inst_per = ALU_INSTR_PER_PATH_STEP.get(name, None)
+    if inst_per is None:
+        return {"kernel": name, "bound": "alu", "achieved": None, "peak": peak_ginst,
+                "unit": "Ginst/s", "frac": None, "traffic": None}
+    achieved = inst_per * M * Nt / per_launch_s / 1e9
+    return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak_ginst,
+            "unit": "Ginst/s", "frac": achieved / peak_ginst, "traffic": None,
+            "peak_source": "derived: 152 SMs x 4 schedulers x 32 lanes x max SM clock"}
+
+
+# Algorithmic lane-instructions per path-step of the RNG-bound sweeps (d = 2): one
+# Philox4x32-10 block (10 rounds x 4 integer ops: 2 wide multiplies, 2 three-input
+# XORs) = 40, one Box-Muller pair (log, sqrt, sincospi, 3 multiplies) ~ 6 MUFU/FMA-pipe
+# ops, drift + update + cost ~ 14 FMA.  Counted conservatively as 60.
+ALU_INSTR_PER_PATH_STEP = {"fwd_store": 60, "fwd_cost": 60, "fwd_ckpt": 60}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--variant", default="stored", choices=["stored", "recompute", "auto"])
+    ap.add_argument("--paths", type=int, default=None, help="override M (paths per GPU)")
+    ap.add_argument("--steps-t", type=int, default=None, help="override N_t")
+    ap.add_argument("--reference-paths", type=int, default=1 << 14)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

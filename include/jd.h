@@ -142,13 +142,16 @@ jd_status jd_sample_paths(jd_problem *p, const double *u, jd_memspace us, int64_
                           int64_t count, double *X, double *lam, double *cost);
 
 /* Projected gradient descent with the Armijo rule (Algorithm 5.4, eq:Stochastic_Armijo).
- * With g = grad/dt (the L2 representative), the trial point is
- * u+ = clip(u - zeta g, u_min, u_max), accepted when J(u+) <= J(u) + c <g, u+ - u>_{L2};
- * zeta starts at zeta0, is doubled (capped at zeta_max) at the start of every later
- * iteration and halved on rejection.  Stops when
- * |P(u - g) - u|_{L2} <= tol_rel_grad |P(u0 - g0) - u0|_{L2}, when |u+ - u|_{L2} <
- * tol_step, or after max_iter updates.  The Armijo test and every FP64 reduction run
- * on the device; the host only reads the accept flag. */
+ * Each iteration evaluates the gradient at u^n, searches the step and updates; no
+ * gradient is evaluated after the last update.  With g = grad/dt (the L2
+ * representative) the trial point is u+ = clip(u - zeta g, u_min, u_max), accepted when
+ * J(u+) <= J(u) + c <g, u+ - u>_{L2}; zeta starts at zeta0, is doubled (capped at
+ * zeta_max) at the start of every later iteration and halved on rejection.  Stops when
+ * |P(u - g) - u|_{L2} <= tol_rel_grad |P(u0 - g0) - u0|_{L2} (checked when a gradient
+ * is evaluated), when |u+ - u|_{L2} < tol_step, or after max_iter updates.  The Armijo
+ * test and every FP64 reduction run on the device; the host only reads the accept flag.
+ * r->iters = updates done, r->evals = gradient + cost evaluations, r->zeta = last
+ * accepted step (pass 2*zeta as zeta0 to continue an interrupted run). */
 typedef struct {
   int max_iter;
   double tol_rel_grad, tol_step, armijo_c, zeta0, zeta_max;
@@ -174,6 +177,20 @@ jd_status jd_problem_info(const jd_problem *p, size_t *device_bytes, jd_adjoint_
 
 /* Number of kernels this library has launched in this process (monotone counter). */
 uint64_t jd_kernel_launch_count(void);
+
+/* Kernel timing (tracing).  jd_profile_enable(1) clears the record and brackets every
+ * later launch with a CUDA event pair on the launching stream; jd_profile_enable(0)
+ * stops recording.  jd_profile_read waits for the recorded events and fills up to
+ * max_entries per-class totals (classes: fwd_cost, fwd_store, fwd_ckpt, adj_stored,
+ * adj_recompute, finalize, prep_u, opt_step); returns the number filled.  name points
+ * to static storage. */
+typedef struct {
+  const char *name;
+  uint64_t launches;
+  double total_ms;
+} jd_kernel_stat;
+void jd_profile_enable(int on);
+int jd_profile_read(jd_kernel_stat *out, int max_entries);
 
 const char *jd_status_string(jd_status s);
 const char *jd_last_error(void);

@@ -435,7 +435,10 @@ int orc_optimize(const orc_problem *P, double *u, const orc_opt_params *o, int n
   double J = 0.0, pg0 = -1.0, zeta = o->zeta0 > 0 ? o->zeta0 : 1.0;
   double zeta_max = o->zeta_max > 0 ? o->zeta_max : 1e3;
   int status = 0, it = 0;
-  for (it = 0;; ++it) {
+  /* Algorithm 5.4: while not converged and n < n_max: gradient at u^n, Armijo step
+   * size, update, step-norm test.  The projected-gradient test (relative to the first
+   * iterate) is checked when the gradient is available, at the top of the loop. */
+  for (it = 0; it < o->max_iter; ++it) {
     int rc = orc_gradient(P, u, nthreads, &J, grad, NULL);
     r->evals++;
     if (rc) { status = 1; break; }
@@ -450,7 +453,7 @@ int orc_optimize(const orc_problem *P, double *u, const orc_opt_params *o, int n
     pg = sqrt(pg);
     if (pg0 < 0.0) pg0 = pg;
     r->rel_grad_norm = pg0 > 0.0 ? pg / pg0 : 0.0;
-    if (r->rel_grad_norm <= o->tol_rel_grad || it >= o->max_iter) break;
+    if (r->rel_grad_norm <= o->tol_rel_grad) break;
 
     /* Armijo backtracking on the projected path */
     if (it > 0) zeta = fmin(2.0 * zeta, zeta_max);
@@ -476,9 +479,9 @@ int orc_optimize(const orc_problem *P, double *u, const orc_opt_params *o, int n
       u[t] = ut[t];
     }
     J = Jt;
+    if (J_hist) J_hist[it + 1] = J;
     if (sqrt(step2) < o->tol_step) {
       it++;
-      if (J_hist) J_hist[it] = J;
       break;
     }
   }

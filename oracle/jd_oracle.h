@@ -123,8 +123,10 @@ typedef struct {
   double J, rel_grad_norm, zeta;
 } orc_opt_result;
 
-/* Projected gradient descent with the Armijo rule.  u is updated in place.
- * J_hist (max_iter+1, nullable) receives J(u^n) for every iterate that was evaluated. */
+/* Projected gradient descent with the Armijo rule (Algorithm 5.4): at most max_iter
+ * iterations, each one gradient evaluation at u^n, an Armijo line search and the
+ * update; no gradient is evaluated after the last update.  u is updated in place.
+ * J_hist (max_iter+1, nullable) receives J(u^n) of every iterate reached. */
 int orc_optimize(const orc_problem *P, double *u, const orc_opt_params *o, int nthreads,
                  orc_opt_result *r, double *J_hist);
 

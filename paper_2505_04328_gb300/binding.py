@@ -1,0 +1,294 @@
+"""ctypes binding of the C ABI in include/jd.h (argument marshalling only).
+
+Every numeric step runs in libjd.so's CUDA kernels; this module only converts numpy
+arrays / torch tensors into pointers and sizes.  There is no CPU fallback: if the
+library is missing or cannot be loaded, the first call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "libjd.so")
+_lib = None
+_lock = threading.Lock()
+
+JD_OK, JD_ERR_INVALID_ARG, JD_ERR_OOM, JD_ERR_CUDA, JD_ERR_NONFINITE = 0, 1, 2, 3, 4
+JD_ERR_LINESEARCH, JD_ERR_TIMEOUT, JD_ERR_UNSUPPORTED, JD_ERR_BUSY = 5, 6, 7, 8
+JD_FP32, JD_FP64 = 0, 1
+JD_ADJ_AUTO, JD_ADJ_STORED, JD_ADJ_RECOMPUTE = 0, 1, 2
+JD_MEM_HOST, JD_MEM_DEVICE = 0, 1
+
+# Every function declared in include/jd.h.
+ABI_SYMBOLS = (
+    "jd_problem_create", "jd_problem_destroy", "jd_cost", "jd_gradient", "jd_sample_paths",
+    "jd_optimize", "jd_problem_info", "jd_kernel_launch_count", "jd_profile_enable",
+    "jd_profile_read", "jd_status_string", "jd_last_error",
+)
+
+
+class JdError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        self.status = status
+        super().__init__(f"{where}: status {status} ({detail})")
+
+
+class ProblemDesc(ctypes.Structure):
+    _fields_ = [
+        ("d", ctypes.c_int), ("du", ctypes.c_int), ("T", ctypes.c_double), ("Nt", ctypes.c_int),
+        ("M", ctypes.c_int64), ("drift", ctypes.c_int),
+        ("A", ctypes.c_void_p), ("C", ctypes.c_void_p), ("B", ctypes.c_void_p), ("dA", ctypes.c_void_p),
+        ("sigma", ctypes.c_void_p), ("lam", ctypes.c_double), ("jump_law", ctypes.c_int),
+        ("jump_scale", ctypes.c_double), ("x0", ctypes.c_void_p), ("q", ctypes.c_void_p),
+        ("xd", ctypes.c_void_p), ("nu", ctypes.c_double), ("u_min", ctypes.c_double),
+        ("u_max", ctypes.c_double), ("seed", ctypes.c_uint64), ("epoch", ctypes.c_uint32),
+        ("prec", ctypes.c_int), ("mode", ctypes.c_int), ("use_tensor_cores", ctypes.c_int),
+        ("mem_budget_bytes", ctypes.c_size_t), ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
+
+
+class OptParams(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int), ("tol_rel_grad", ctypes.c_double),
+                ("tol_step", ctypes.c_double), ("armijo_c", ctypes.c_double),
+                ("zeta0", ctypes.c_double), ("zeta_max", ctypes.c_double),
+                ("max_backtracks", ctypes.c_int)]
+
+
+class OptResult(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("evals", ctypes.c_int), ("J", ctypes.c_double),
+                ("rel_grad_norm", ctypes.c_double), ("zeta", ctypes.c_double),
+                ("status", ctypes.c_int)]
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def lib():
+    """Load libjd.so (built by paper_2505_04328_gb300._build.build())."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(
+                f"{_LIB_PATH} is missing: build it with paper_2505_04328_gb300._build.build() "
+                "(CUDA toolkit required; there is no CPU fallback)")
+        L = ctypes.CDLL(_LIB_PATH)
+        P = ctypes.POINTER
+        vp, i64, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p
+        L.jd_problem_create.argtypes = [P(ProblemDesc), P(ctypes.c_void_p)]
+        L.jd_problem_destroy.argtypes = [vp]
+        L.jd_cost.argtypes = [vp, dp, ctypes.c_int, P(ctypes.c_double)]
+        L.jd_gradient.argtypes = [vp, dp, ctypes.c_int, dp, dp, ctypes.c_int, dp]
+        L.jd_sample_paths.argtypes = [vp, dp, ctypes.c_int, i64, i64, dp, dp, dp]
+        L.jd_optimize.argtypes = [vp, dp, ctypes.c_int, P(OptParams), P(OptResult), dp]
+        L.jd_problem_info.argtypes = [vp, P(ctypes.c_size_t), P(ctypes.c_int)]
+        L.jd_kernel_launch_count.restype = ctypes.c_uint64
+        L.jd_profile_enable.argtypes = [ctypes.c_int]
+        L.jd_profile_enable.restype = None
+        L.jd_profile_read.argtypes = [P(KernelStat), ctypes.c_int]
+        L.jd_profile_read.restype = ctypes.c_int
+        L.jd_status_string.argtypes = [ctypes.c_int]
+        L.jd_status_string.restype = ctypes.c_char_p
+        L.jd_last_error.restype = ctypes.c_char_p
+        for f in ABI_SYMBOLS:
+            if f not in ("jd_kernel_launch_count", "jd_status_string", "jd_last_error",
+                         "jd_profile_enable", "jd_profile_read"):
+                getattr(L, f).restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def launch_count() -> int:
+    return int(lib().jd_kernel_launch_count())
+
+
+def profile_enable(on: bool = True):
+    """Start (clearing old records) or stop per-kernel CUDA-event timing."""
+    lib().jd_profile_enable(1 if on else 0)
+
+
+def profile_read():
+    """{kernel class: (launches, total ms)} of the recorded launches."""
+    arr = (KernelStat * 16)()
+    n = lib().jd_profile_read(arr, 16)
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(n)}
+
+
+def _check(status: int, where: str):
+    if status != JD_OK:
+        L = lib()
+        raise JdError(status, where, f"{L.jd_status_string(status).decode()}: {L.jd_last_error().decode()}")
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _u_arg(u, n: int):
+    """Returns (pointer, memspace, keepalive) for a control given as numpy or torch."""
+    if _is_torch(u):
+        import torch
+        if u.dtype != torch.float64 or not u.is_contiguous() or u.numel() != n:
+            raise ValueError(f"control tensor must be contiguous float64 with {n} entries")
+        if u.is_cuda:
+            return ctypes.c_void_p(u.data_ptr()), JD_MEM_DEVICE, u
+        return ctypes.c_void_p(u.data_ptr()), JD_MEM_HOST, u
+    a = _f64(u).reshape(-1)
+    if a.size != n:
+        raise ValueError(f"control must have {n} entries, got {a.size}")
+    return _ptr(a), JD_MEM_HOST, a
+
+
+_PREC = {"fp32": JD_FP32, "fp64": JD_FP64, JD_FP32: JD_FP32, JD_FP64: JD_FP64}
+_MODE = {"auto": JD_ADJ_AUTO, "stored": JD_ADJ_STORED, "recompute": JD_ADJ_RECOMPUTE,
+         JD_ADJ_AUTO: JD_ADJ_AUTO, JD_ADJ_STORED: JD_ADJ_STORED, JD_ADJ_RECOMPUTE: JD_ADJ_RECOMPUTE}
+
+
+class JdProblem:
+    """One problem on the current CUDA device (see jd_problem_create).
+
+    ``problem`` is any object with the fields of workloads.Problem (d, du, T, Nt, M,
+    drift, A, C, B, dA, sigma, lam, jump_law, jump_scale, x0, q, xd, nu, u_min, u_max,
+    seed, epoch).  ``stream``: a torch.cuda.Stream, a raw cudaStream_t int, or None for
+    torch's current stream (a library-owned stream when torch has no CUDA).
+    """
+
+    def __init__(self, problem, prec="fp32", mode="auto", stream=None, mem_budget: int = 0,
+                 use_tensor_cores: bool = False):
+        self.p = problem
+        self.Nt, self.du, self.d, self.M = problem.Nt, problem.du, problem.d, problem.M
+        d = problem.d
+        C = problem.C if problem.C is not None else np.zeros((d, d))
+        self._arrays = dict(
+            A=_f64(problem.A).reshape(-1), C=_f64(C).reshape(-1), B=_f64(problem.B).reshape(-1),
+            dA=None if problem.dA is None else _f64(problem.dA).reshape(-1),
+            sigma=_f64(problem.sigma).reshape(-1), x0=_f64(problem.x0).reshape(-1),
+            q=_f64(problem.q).reshape(-1), xd=_f64(problem.xd).reshape(-1))
+        a = self._arrays
+        self.stream_handle = self._stream(stream)
+        self.desc = ProblemDesc(
+            d=d, du=problem.du, T=float(problem.T), Nt=problem.Nt, M=problem.M, drift=int(problem.drift),
+            A=_ptr(a["A"]), C=_ptr(a["C"]), B=_ptr(a["B"]), dA=_ptr(a["dA"]), sigma=_ptr(a["sigma"]),
+            lam=float(problem.lam), jump_law=int(problem.jump_law), jump_scale=float(problem.jump_scale),
+            x0=_ptr(a["x0"]), q=_ptr(a["q"]), xd=_ptr(a["xd"]), nu=float(problem.nu),
+            u_min=float(problem.u_min), u_max=float(problem.u_max), seed=int(problem.seed),
+            epoch=int(problem.epoch), prec=_PREC[prec], mode=_MODE[mode],
+            use_tensor_cores=int(bool(use_tensor_cores)), mem_budget_bytes=int(mem_budget),
+            cuda_stream=self.stream_handle)
+        h = ctypes.c_void_p()
+        _check(lib().jd_problem_create(ctypes.byref(self.desc), ctypes.byref(h)), "jd_problem_create")
+        self.h = h
+
+    @staticmethod
+    def _stream(stream):
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+            except ImportError:
+                pass
+            return None
+        if isinstance(stream, int):
+            return ctypes.c_void_p(stream)
+        return ctypes.c_void_p(stream.cuda_stream)
+
+    @property
+    def n(self) -> int:
+        return self.Nt * self.du
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().jd_problem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def cost(self, u) -> float:
+        up, us, _keep = _u_arg(u, self.n)
+        J = ctypes.c_double()
+        _check(lib().jd_cost(self.h, up, us, ctypes.byref(J)), "jd_cost")
+        return J.value
+
+    def gradient(self, u, theta: bool = False):
+        """(J, grad (Nt, du) numpy, grad_theta (d+2) or None)."""
+        up, us, _keep = _u_arg(u, self.n)
+        J = ctypes.c_double()
+        g = np.zeros((self.Nt, self.du))
+        gth = np.zeros(self.d + 2) if theta else None
+        _check(lib().jd_gradient(self.h, up, us, ctypes.byref(J), _ptr(g), JD_MEM_HOST, _ptr(gth)),
+               "jd_gradient")
+        return J.value, g, gth
+
+    def gradient_into(self, u, grad_out, want_J: bool = True, theta: bool = False):
+        """Gradient written into a device tensor grad_out (float64, Nt*du); returns
+        (J or None, grad_theta or None).  Without J/theta the call does not synchronize."""
+        up, us, _keep = _u_arg(u, self.n)
+        if not (_is_torch(grad_out) and grad_out.is_cuda):
+            raise ValueError("grad_out must be a CUDA tensor")
+        J = ctypes.c_double()
+        gth = np.zeros(self.d + 2) if theta else None
+        _check(lib().jd_gradient(self.h, up, us, ctypes.byref(J) if want_J else None,
+                                 ctypes.c_void_p(grad_out.data_ptr()), JD_MEM_DEVICE, _ptr(gth)),
+               "jd_gradient")
+        return (J.value if want_J else None), gth
+
+    def sample_paths(self, u, m0: int, count: int, lam: bool = True):
+        """(X (count, Nt+1, d), lam (count, Nt+1, d) or None, cost (count))."""
+        up, us, _keep = _u_arg(u, self.n)
+        X = np.zeros((count, self.Nt + 1, self.d))
+        L = np.zeros((count, self.Nt + 1, self.d)) if lam else None
+        c = np.zeros(count)
+        _check(lib().jd_sample_paths(self.h, up, us, int(m0), int(count), _ptr(X), _ptr(L), _ptr(c)),
+               "jd_sample_paths")
+        return X, L, c
+
+    def optimize(self, u0=None, max_iter=50, tol_rel_grad=1e-4, tol_step=0.0, armijo_c=1e-4,
+                 zeta0=1.0, zeta_max=1e3, max_backtracks=40, raise_on_error=True):
+        """Projected-gradient Armijo descent (jd_optimize); returns (u, result dict, J history)."""
+        u = np.zeros((self.Nt, self.du)) if u0 is None else _f64(u0).reshape(self.Nt, self.du).copy()
+        o = OptParams(max_iter=max_iter, tol_rel_grad=tol_rel_grad, tol_step=tol_step,
+                      armijo_c=armijo_c, zeta0=zeta0, zeta_max=zeta_max, max_backtracks=max_backtracks)
+        r = OptResult()
+        hist = np.full(max_iter + 2, np.nan)
+        st = lib().jd_optimize(self.h, _ptr(u), JD_MEM_HOST, ctypes.byref(o), ctypes.byref(r), _ptr(hist))
+        if raise_on_error:
+            _check(st, "jd_optimize")
+        res = dict(iters=r.iters, evals=r.evals, status=r.status, J=r.J,
+                   rel_grad_norm=r.rel_grad_norm, zeta=r.zeta)
+        return u, res, hist[: r.iters + 1]
+
+    def info(self):
+        b = ctypes.c_size_t()
+        m = ctypes.c_int()
+        _check(lib().jd_problem_info(self.h, ctypes.byref(b), ctypes.byref(m)), "jd_problem_info")
+        return dict(device_bytes=b.value, mode={0: "auto", 1: "stored", 2: "recompute"}[m.value])

@@ -1,0 +1,866 @@
+// jd_api.cu -- host side of the C ABI declared in include/jd.h: validation, memory
+// plan, launch sequencing, FP64 finalize kernels and the device-side Armijo test.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "jd_internal.h"
+
+namespace jd {
+
+extern const PathOps ops_f32_d1_u1, ops_f32_d2_u1, ops_f32_d2_u4, ops_f32_d4_u4, ops_f32_d8_u4;
+extern const PathOps ops_f64_d1_u1, ops_f64_d2_u1, ops_f64_d2_u4, ops_f64_d4_u4, ops_f64_d8_u4;
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+// Optional per-kernel-class timing: a CUDA event pair around every launch, on the
+// launching stream, summed on read.
+enum KernelClass { KC_FWD_COST, KC_FWD_STORE, KC_FWD_CKPT, KC_ADJ_STORED, KC_ADJ_RECOMPUTE,
+                   KC_FINALIZE, KC_PREP, KC_OPT, KC_COUNT };
+static const char *kKernelClassName[KC_COUNT] = {"fwd_cost", "fwd_store", "fwd_ckpt", "adj_stored",
+                                                 "adj_recompute", "finalize", "prep_u", "opt_step"};
+struct ProfRec {
+  int kind;
+  cudaEvent_t a, b;
+};
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::vector<ProfRec> g_prof_recs;
+static std::vector<cudaEvent_t> g_prof_pool;
+
+static cudaEvent_t prof_event() {
+  cudaEvent_t e = nullptr;
+  if (!g_prof_pool.empty()) {
+    e = g_prof_pool.back();
+    g_prof_pool.pop_back();
+  } else {
+    cudaEventCreate(&e);
+  }
+  return e;
+}
+
+// Returns a record index or -1 when profiling is off.
+static int prof_begin(int kind, cudaStream_t s) {
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  if (!g_prof_on) return -1;
+  ProfRec r{kind, prof_event(), prof_event()};
+  cudaEventRecord(r.a, s);
+  g_prof_recs.push_back(r);
+  return (int)g_prof_recs.size() - 1;
+}
+
+static void prof_end(int idx, cudaStream_t s) {
+  if (idx < 0) return;
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  if (idx < (int)g_prof_recs.size()) cudaEventRecord(g_prof_recs[idx].b, s);
+}
+
+int compiled_dim(int d) {
+  if (d == 1) return 1;
+  if (d == 2) return 2;
+  if (d <= 4) return 4;
+  if (d <= 8) return 8;
+  return 0;
+}
+
+// (D, DU) actually compiled for a (d, du) pair: du == 1 with d <= 2 runs the
+// single-control kernels, everything else pads the control to 4 (and d = 1 with
+// several controls to D = 2).
+static void pick_dims(int d, int du, int *D, int *DU) {
+  int Dd = compiled_dim(d);
+  if (du == 1 && Dd <= 2) {
+    *D = Dd;
+    *DU = 1;
+    return;
+  }
+  if (Dd == 1) Dd = 2;
+  *D = Dd;
+  *DU = 4;
+}
+
+const PathOps *path_ops_dims(int prec, int D, int DU) {
+  const bool f = prec == JD_FP32;
+  if (D == 1 && DU == 1) return f ? &ops_f32_d1_u1 : &ops_f64_d1_u1;
+  if (D == 2 && DU == 1) return f ? &ops_f32_d2_u1 : &ops_f64_d2_u1;
+  if (D == 2 && DU == 4) return f ? &ops_f32_d2_u4 : &ops_f64_d2_u4;
+  if (D == 4 && DU == 4) return f ? &ops_f32_d4_u4 : &ops_f64_d4_u4;
+  if (D == 8 && DU == 4) return f ? &ops_f32_d8_u4 : &ops_f64_d8_u4;
+  return nullptr;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 finalize kernels (fixed summation order: deterministic)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide FP64 sum (blockDim.x == 256) in a fixed tree; result in every thread.
+__device__ double block_sum_d(double v, double *sm) {
+  v = warp_sum_d(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) sm[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0.0;
+    s = warp_sum_d(s);
+    if (threadIdx.x == 0) sm[0] = s;
+  }
+  __syncthreads();
+  s = sm[0];
+  __syncthreads();
+  return s;
+}
+
+// J = (1/M) sum_b partC[b] + (nu dt / 2) sum_k |u_k|^2      (eq:discrete_functional)
+__global__ void finalize_cost_kernel(const double *__restrict__ partC, int64_t nblk,
+                                     const double *__restrict__ u, int n, double half_nu_dt,
+                                     double invM, double *__restrict__ out, double *__restrict__ bad) {
+  __shared__ double sm[32];
+  double a = 0.0, b = 0.0;
+  for (int64_t i = threadIdx.x; i < nblk; i += blockDim.x) a += partC[i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) b += u[i] * u[i];
+  a = block_sum_d(a, sm);
+  b = block_sum_d(b, sm);
+  if (threadIdx.x == 0) {
+    const double J = a * invM + half_nu_dt * b;
+    *out = J;
+    if (!isfinite(J)) *bad = 1.0;
+  }
+}
+
+// grad[k*du + l] = nu dt u[k*du + l] + (1/M) sum_b partG[(k*DU + l) * nblk + b]
+// (eq:definition_Gradient).  One warp per gradient entry.
+__global__ void finalize_grad_kernel(const double *__restrict__ partG, int64_t nblk, int Nt, int du,
+                                     int DU, const double *__restrict__ u, double nu_dt, double invM,
+                                     double *__restrict__ grad, double *__restrict__ bad) {
+  const int lane = threadIdx.x & 31;
+  const int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (e >= (int64_t)Nt * du) return;   // whole warp leaves together
+  const int k = (int)(e / du), l = (int)(e % du);
+  const double *row = partG + ((int64_t)k * DU + l) * nblk;
+  double s = 0.0;
+  for (int64_t b = lane; b < nblk; b += 32) s += row[b];
+  s = warp_sum_d(s);
+  if (lane == 0) {
+    const double g = nu_dt * u[e] + s * invM;
+    grad[e] = g;
+    if (!isfinite(g)) *bad = 1.0;
+  }
+}
+
+// theta[t] = (1/M) sum_b partT[map(t) * nblk + b], map: [0, 1..d, d+1] -> [0, 1..d, D+1]
+__global__ void finalize_theta_kernel(const double *__restrict__ partT, int64_t nblk, int d, int D,
+                                      double invM, double *__restrict__ out) {
+  const int lane = threadIdx.x & 31, t = blockIdx.x;   // one warp-sized block per entry
+  const int src = t <= d ? t : D + 1;
+  double s = 0.0;
+  for (int64_t b = lane; b < nblk; b += 32) s += partT[(int64_t)src * nblk + b];
+  s = warp_sum_d(s);
+  if (lane == 0) out[t] = s * invM;
+}
+
+// Control in kernel precision, padded from du to DU columns.
+template <typename R>
+__global__ void prep_u_kernel(const double *__restrict__ u, int Nt, int du, int DU, R *__restrict__ uk) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)Nt * DU) return;
+  const int k = (int)(i / DU), l = (int)(i % DU);
+  uk[i] = l < du ? (R)u[(int64_t)k * du + l] : R(0);
+}
+
+// |P(u - g) - u|_{L2} with g = grad / dt; out = value.
+__global__ void opt_pgnorm_kernel(int n, const double *__restrict__ u, const double *__restrict__ grad,
+                                  double dt, double lo, double hi, double *__restrict__ out) {
+  __shared__ double sm[32];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double g = grad[i] / dt;
+    const double e = fmin(fmax(u[i] - g, lo), hi) - u[i];
+    a += dt * e * e;
+  }
+  a = block_sum_d(a, sm);
+  if (threadIdx.x == 0) *out = sqrt(a);
+}
+
+// Trial point ut = clip(u - zeta g) and <g, ut - u>_{L2} = sum grad (ut - u).
+__global__ void opt_trial_kernel(int n, const double *__restrict__ u, const double *__restrict__ grad,
+                                 double zeta, double dt, double lo, double hi,
+                                 double *__restrict__ ut, double *__restrict__ dot) {
+  __shared__ double sm[32];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double g = grad[i] / dt;
+    const double v = fmin(fmax(u[i] - zeta * g, lo), hi);
+    ut[i] = v;
+    a += dt * g * (v - u[i]);
+  }
+  a = block_sum_d(a, sm);
+  if (threadIdx.x == 0) *dot = a;
+}
+
+// Armijo test J(ut) <= J(u) + c <g, ut - u>; on acceptance u <- ut and J <- J(ut).
+// s: [0] J(u), [1] J(ut), [2] dot, [4] accepted (out), [5] |ut - u|^2_{L2} (out).
+__global__ void opt_accept_kernel(int n, double *__restrict__ u, const double *__restrict__ ut,
+                                  double c, double dt, double *__restrict__ s) {
+  __shared__ double sm[32];
+  const bool acc = s[1] <= s[0] + c * s[2];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double e = ut[i] - u[i];
+    a += dt * e * e;
+  }
+  a = block_sum_d(a, sm);
+  if (acc)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) u[i] = ut[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s[4] = acc ? 1.0 : 0.0;
+    s[5] = a;
+    if (acc) s[0] = s[1];
+  }
+}
+
+}  // namespace jd
+
+using namespace jd;
+
+// ---------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+static jd_status fail(jd_status s, const std::string &msg) {
+  g_last_error = msg;
+  return s;
+}
+
+static jd_status cuda_fail(cudaError_t e, const char *what) {
+  return fail(JD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define JD_CUDA(call)                                      \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);    \
+  } while (0)
+
+// Scalar slots in p->scal_d
+enum { S_J = 0, S_JT = 1, S_DOT = 2, S_PG = 3, S_ACC = 4, S_STEP = 5, S_BAD = 7, S_THETA = 8 };
+constexpr int NSCAL = 8 + 34;
+
+static bool finite_all(const double *a, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+static size_t elem_size(const jd_problem *p) { return p->desc.prec == JD_FP64 ? 8 : 4; }
+
+static void free_dev(void *&ptr) {
+  if (ptr) cudaFree(ptr);
+  ptr = nullptr;
+}
+template <typename T>
+static void free_dev(T *&ptr) {
+  if (ptr) cudaFree(ptr);
+  ptr = nullptr;
+}
+
+static jd_status dev_alloc(jd_problem *p, void **ptr, size_t bytes, const char *what) {
+  if (p->bytes + bytes > p->budget)
+    return fail(JD_ERR_OOM, std::string("memory budget exceeded allocating ") + what);
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(JD_ERR_OOM, std::string("cudaMalloc failed for ") + what + ": " + cudaGetErrorString(e));
+  }
+  p->bytes += bytes;
+  return JD_OK;
+}
+
+static size_t stored_bytes(const jd_problem *p) {
+  const int64_t M = p->desc.M;
+  const int Nt = p->desc.Nt;
+  return (size_t)((Nt + 4) / 4) * p->D * M * 4 * elem_size(p) + (size_t)ceil_div(Nt, 32) * M * 4;
+}
+
+static size_t recompute_bytes(const jd_problem *p) {
+  const int nseg = (int)ceil_div(p->desc.Nt, p->ops->S);
+  return (size_t)(nseg + 1) * p->D * p->desc.M * elem_size(p);
+}
+
+// Allocate the trajectory or checkpoint buffers on first use.
+static jd_status ensure_plan(jd_problem *p) {
+  if (p->plan != JD_ADJ_AUTO) return JD_OK;
+  jd_adjoint_mode want = p->desc.mode;
+  if (want == JD_ADJ_AUTO)
+    want = (p->bytes + stored_bytes(p) <= p->budget) ? JD_ADJ_STORED : JD_ADJ_RECOMPUTE;
+  if (want == JD_ADJ_STORED) {
+    const int64_t M = p->desc.M;
+    jd_status s = dev_alloc(p, &p->traj, (size_t)((p->desc.Nt + 4) / 4) * p->D * M * 4 * elem_size(p),
+                            "trajectory");
+    if (s) return s;
+    s = dev_alloc(p, (void **)&p->flags, (size_t)ceil_div(p->desc.Nt, 32) * M * 4, "jump flags");
+    if (s) return s;
+  } else {
+    jd_status s = dev_alloc(p, &p->ckpt, recompute_bytes(p), "checkpoints");
+    if (s) return s;
+  }
+  p->plan = want;
+  return JD_OK;
+}
+
+// u (Nt*du, host or device) -> p->u_in (FP64 device) -> p->uk (kernel precision, padded)
+static jd_status load_u(jd_problem *p, const double *u, jd_memspace us) {
+  const size_t n = (size_t)p->desc.Nt * p->desc.du;
+  if (!u) return fail(JD_ERR_INVALID_ARG, "u is NULL");
+  if (us == JD_MEM_HOST) {
+    if (!finite_all(u, n)) return fail(JD_ERR_INVALID_ARG, "u has a non-finite entry");
+    JD_CUDA(cudaMemcpyAsync(p->u_in, u, n * sizeof(double), cudaMemcpyHostToDevice, p->stream));
+  } else if (us == JD_MEM_DEVICE) {
+    if (u != p->u_in)
+      JD_CUDA(cudaMemcpyAsync(p->u_in, u, n * sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
+  } else {
+    return fail(JD_ERR_INVALID_ARG, "bad memory space for u");
+  }
+  return JD_OK;
+}
+
+static jd_status prep_u(jd_problem *p, const double *ud) {
+  const int64_t n = (int64_t)p->desc.Nt * p->DU;
+  const unsigned grid = (unsigned)ceil_div(n, 256);
+  const int pr = prof_begin(KC_PREP, p->stream);
+  if (p->desc.prec == JD_FP64)
+    prep_u_kernel<double><<<grid, 256, 0, p->stream>>>(ud, p->desc.Nt, p->desc.du, p->DU, (double *)p->uk);
+  else
+    prep_u_kernel<float><<<grid, 256, 0, p->stream>>>(ud, p->desc.Nt, p->desc.du, p->DU, (float *)p->uk);
+  prof_end(pr, p->stream);
+  count_launch();
+  JD_CUDA(cudaGetLastError());
+  return JD_OK;
+}
+
+static jd_status finalize_cost(jd_problem *p, const double *ud, int slot) {
+  const jd_problem_desc &q = p->desc;
+  const double dt = q.T / q.Nt;
+  const int pr = prof_begin(KC_FINALIZE, p->stream);
+  finalize_cost_kernel<<<1, 256, 0, p->stream>>>(p->partC, p->nblk, ud, q.Nt * q.du, 0.5 * q.nu * dt,
+                                                 1.0 / (double)q.M, p->scal_d + slot, p->scal_d + S_BAD);
+  prof_end(pr, p->stream);
+  count_launch();
+  JD_CUDA(cudaGetLastError());
+  return JD_OK;
+}
+
+static jd_status run_cost(jd_problem *p, const double *ud, int slot) {
+  jd_status s = prep_u(p, ud);
+  if (s) return s;
+  const int pr = prof_begin(KC_FWD_COST, p->stream);
+  const cudaError_t e = p->ops->fwd(p, FWD_COST, 0, p->desc.M, p->uk, nullptr, nullptr, nullptr, p->partC,
+                                    nullptr, p->stream);
+  prof_end(pr, p->stream);
+  JD_CUDA(e);
+  return finalize_cost(p, ud, slot);
+}
+
+static jd_status run_gradient(jd_problem *p, const double *ud, bool theta) {
+  jd_status s = ensure_plan(p);
+  if (s) return s;
+  s = prep_u(p, ud);
+  if (s) return s;
+  const jd_problem_desc &q = p->desc;
+  const int64_t M = q.M;
+  cudaError_t e1, e2;
+  if (p->plan == JD_ADJ_STORED) {
+    int pr = prof_begin(KC_FWD_STORE, p->stream);
+    e1 = p->ops->fwd(p, FWD_STORE, 0, M, p->uk, p->traj, p->flags, nullptr, p->partC, nullptr, p->stream);
+    prof_end(pr, p->stream);
+    pr = prof_begin(KC_ADJ_STORED, p->stream);
+    e2 = p->ops->adj(p, ADJ_STORED_V, theta, 0, M, p->uk, p->traj, p->flags, nullptr, p->partG, p->partT,
+                     nullptr, p->stream);
+    prof_end(pr, p->stream);
+  } else {
+    int pr = prof_begin(KC_FWD_CKPT, p->stream);
+    e1 = p->ops->fwd(p, FWD_CKPT, 0, M, p->uk, nullptr, nullptr, p->ckpt, p->partC, nullptr, p->stream);
+    prof_end(pr, p->stream);
+    pr = prof_begin(KC_ADJ_RECOMPUTE, p->stream);
+    e2 = p->ops->adj(p, ADJ_RECOMPUTE_V, theta, 0, M, p->uk, nullptr, nullptr, p->ckpt, p->partG,
+                     p->partT, nullptr, p->stream);
+    prof_end(pr, p->stream);
+  }
+  JD_CUDA(e1);
+  JD_CUDA(e2);
+  s = finalize_cost(p, ud, S_J);
+  if (s) return s;
+  const double dt = q.T / q.Nt;
+  const int64_t ne = (int64_t)q.Nt * q.du;
+  const int pr = prof_begin(KC_FINALIZE, p->stream);
+  finalize_grad_kernel<<<(unsigned)ceil_div(ne, 8), 256, 0, p->stream>>>(
+      p->partG, p->nblk, q.Nt, q.du, p->DU, ud, q.nu * dt, 1.0 / (double)M, p->grad_d, p->scal_d + S_BAD);
+  prof_end(pr, p->stream);
+  count_launch();
+  JD_CUDA(cudaGetLastError());
+  if (theta) {
+    finalize_theta_kernel<<<q.d + 2, 32, 0, p->stream>>>(p->partT, p->nblk, q.d, p->D,
+                                                               1.0 / (double)M, p->scal_d + S_THETA);
+    count_launch();
+    JD_CUDA(cudaGetLastError());
+  }
+  return JD_OK;
+}
+
+// Copy n scalars from scal_d to the pinned staging buffer and wait.
+static jd_status read_scalars(jd_problem *p, int first, int n) {
+  JD_CUDA(cudaMemcpyAsync(p->host_pinned + first, p->scal_d + first, n * sizeof(double),
+                          cudaMemcpyDeviceToHost, p->stream));
+  JD_CUDA(cudaStreamSynchronize(p->stream));
+  return JD_OK;
+}
+
+static jd_status check_bad(jd_problem *p) {
+  jd_status s = read_scalars(p, S_BAD, 1);
+  if (s) return s;
+  if (p->host_pinned[S_BAD] != 0.0) return fail(JD_ERR_NONFINITE, "cost or gradient is not finite");
+  return JD_OK;
+}
+
+static jd_status clear_bad(jd_problem *p) {
+  JD_CUDA(cudaMemsetAsync(p->scal_d + S_BAD, 0, sizeof(double), p->stream));
+  return JD_OK;
+}
+
+static jd_status set_device(const jd_problem *p) {
+  int cur = -1;
+  JD_CUDA(cudaGetDevice(&cur));
+  if (cur != p->device) JD_CUDA(cudaSetDevice(p->device));
+  return JD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *jd_status_string(jd_status s) {
+  switch (s) {
+    case JD_OK: return "ok";
+    case JD_ERR_INVALID_ARG: return "invalid argument";
+    case JD_ERR_OOM: return "out of device memory or over the memory budget";
+    case JD_ERR_CUDA: return "CUDA runtime error";
+    case JD_ERR_NONFINITE: return "non-finite cost or gradient";
+    case JD_ERR_LINESEARCH: return "Armijo line search exhausted its backtracks";
+    case JD_ERR_TIMEOUT: return "bounded device wait timed out";
+    case JD_ERR_UNSUPPORTED: return "unsupported by this build";
+    case JD_ERR_BUSY: return "result not ready";
+  }
+  return "unknown status";
+}
+
+const char *jd_last_error(void) { return g_last_error.c_str(); }
+
+uint64_t jd_kernel_launch_count(void) { return g_launches.load(); }
+
+void jd_profile_enable(int on) {
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  for (auto &r : g_prof_recs) {
+    cudaEventSynchronize(r.b);
+    g_prof_pool.push_back(r.a);
+    g_prof_pool.push_back(r.b);
+  }
+  g_prof_recs.clear();
+  g_prof_on = on != 0;
+}
+
+int jd_profile_read(jd_kernel_stat *out, int max_entries) {
+  std::lock_guard<std::mutex> g(g_prof_mu);
+  double ms[KC_COUNT] = {0};
+  uint64_t n[KC_COUNT] = {0};
+  for (auto &r : g_prof_recs) {
+    float t = 0.f;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+      ms[r.kind] += t;
+      n[r.kind] += 1;
+    }
+  }
+  int k = 0;
+  for (int c = 0; c < KC_COUNT && k < max_entries; ++c) {
+    if (!n[c]) continue;
+    out[k].name = kKernelClassName[c];
+    out[k].launches = n[c];
+    out[k].total_ms = ms[c];
+    ++k;
+  }
+  return k;
+}
+
+jd_status jd_problem_destroy(jd_problem *p) {
+  if (!p) return JD_OK;
+  cudaSetDevice(p->device);
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  free_dev(p->uk);
+  free_dev(p->xdk);
+  free_dev(p->u_in);
+  free_dev(p->grad_d);
+  free_dev(p->scal_d);
+  free_dev(p->partC);
+  free_dev(p->partG);
+  free_dev(p->partT);
+  free_dev(p->traj);
+  free_dev(p->flags);
+  free_dev(p->ckpt);
+  free_dev(p->opt_u);
+  free_dev(p->opt_ut);
+  free_dev(p->opt_g);
+  if (p->host_pinned) cudaFreeHost(p->host_pinned);
+  if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
+  delete p;
+  return JD_OK;
+}
+
+jd_status jd_problem_create(const jd_problem_desc *desc, jd_problem **out) {
+  if (!desc || !out) return fail(JD_ERR_INVALID_ARG, "desc and out must be non-NULL");
+  *out = nullptr;
+  const jd_problem_desc &q = *desc;
+  if (q.d < 1 || q.du < 1) return fail(JD_ERR_INVALID_ARG, "d and du must be >= 1");
+  if (q.d > 8) return fail(JD_ERR_UNSUPPORTED, "d > 8 is not compiled");
+  if (q.du > 4) return fail(JD_ERR_UNSUPPORTED, "du > 4 is not compiled");
+  if (q.Nt < 1 || q.Nt > (1 << 24)) return fail(JD_ERR_INVALID_ARG, "Nt must be in [1, 2^24]");
+  if (q.M < 1 || q.M > 0xFFFFFFFFll) return fail(JD_ERR_INVALID_ARG, "M must be in [1, 2^32 - 1]");
+  if (!(q.T > 0.0) || !std::isfinite(q.T)) return fail(JD_ERR_INVALID_ARG, "T must be finite and > 0");
+  if (q.drift != JD_DRIFT_LINEAR && q.drift != JD_DRIFT_CUBIC) return fail(JD_ERR_INVALID_ARG, "bad drift");
+  if (q.jump_law < JD_JUMP_NONE || q.jump_law > JD_JUMP_UNIFORM) return fail(JD_ERR_INVALID_ARG, "bad jump law");
+  if (q.prec != JD_FP32 && q.prec != JD_FP64) return fail(JD_ERR_INVALID_ARG, "bad precision");
+  if (q.mode < JD_ADJ_AUTO || q.mode > JD_ADJ_RECOMPUTE) return fail(JD_ERR_INVALID_ARG, "bad adjoint mode");
+  if (!q.A || !q.B || !q.sigma || !q.x0 || !q.q || !q.xd)
+    return fail(JD_ERR_INVALID_ARG, "A, B, sigma, x0, q, xd must be non-NULL");
+  if (q.drift == JD_DRIFT_CUBIC && !q.C) return fail(JD_ERR_INVALID_ARG, "C must be non-NULL for CUBIC");
+  if (!(q.lambda >= 0.0) || !std::isfinite(q.lambda)) return fail(JD_ERR_INVALID_ARG, "lambda must be finite and >= 0");
+  if (!(q.jump_scale >= 0.0) || !std::isfinite(q.jump_scale))
+    return fail(JD_ERR_INVALID_ARG, "jump_scale must be finite and >= 0");
+  if (!std::isfinite(q.nu) || q.nu < 0.0) return fail(JD_ERR_INVALID_ARG, "nu must be finite and >= 0");
+  if (!(q.u_min <= q.u_max)) return fail(JD_ERR_INVALID_ARG, "u_min must be <= u_max");
+  if (q.use_tensor_cores) {
+    if (q.d != 32 || q.drift != JD_DRIFT_LINEAR)
+      return fail(JD_ERR_UNSUPPORTED, "tensor cores only for d = 32 LINEAR drift");
+    return fail(JD_ERR_UNSUPPORTED, "tensor-core path not available in this build");
+  }
+  const size_t dd = (size_t)q.d * q.d, dn = (size_t)(q.Nt + 1) * q.d;
+  if (!finite_all(q.A, dd) || !finite_all(q.B, (size_t)q.d * q.du) || !finite_all(q.sigma, q.d) ||
+      !finite_all(q.x0, q.d) || !finite_all(q.q, q.d) || !finite_all(q.xd, dn) ||
+      (q.drift == JD_DRIFT_CUBIC && !finite_all(q.C, dd)) || (q.dA && !finite_all(q.dA, dd)))
+    return fail(JD_ERR_INVALID_ARG, "a coefficient array has a non-finite entry");
+
+  jd_problem *p = new jd_problem();
+  p->desc = q;
+  p->A.assign(q.A, q.A + dd);
+  if (q.drift == JD_DRIFT_CUBIC) p->C.assign(q.C, q.C + dd);
+  p->B.assign(q.B, q.B + (size_t)q.d * q.du);
+  if (q.dA) p->dA.assign(q.dA, q.dA + dd);
+  p->sigma.assign(q.sigma, q.sigma + q.d);
+  p->x0.assign(q.x0, q.x0 + q.d);
+  p->q.assign(q.q, q.q + q.d);
+  p->xd.assign(q.xd, q.xd + dn);
+  p->desc.A = p->desc.C = p->desc.B = p->desc.dA = p->desc.sigma = p->desc.x0 = p->desc.q = p->desc.xd = nullptr;
+  pick_dims(q.d, q.du, &p->D, &p->DU);
+  p->ops = path_ops_dims(q.prec, p->D, p->DU);
+  if (!p->ops) {
+    delete p;
+    return fail(JD_ERR_UNSUPPORTED, "no kernels compiled for this (d, du)");
+  }
+  p->nblk = ceil_div(q.M, TPB);
+
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e != cudaSuccess) {
+    delete p;
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  {
+    // the jump path keeps sub-step states on the per-thread stack: make sure this
+    // context's stack limit covers the largest kernel of this instantiation
+    const size_t need = p->ops->stack_bytes();
+    size_t cur = 0;
+    e = cudaDeviceGetLimit(&cur, cudaLimitStackSize);
+    if (e == cudaSuccess && cur < need) e = cudaDeviceSetLimit(cudaLimitStackSize, need);
+    if (e != cudaSuccess) {
+      delete p;
+      return cuda_fail(e, "cudaDeviceSetLimit(cudaLimitStackSize)");
+    }
+  }
+  if (q.cuda_stream) {
+    p->stream = (cudaStream_t)q.cuda_stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete p;
+      return cuda_fail(e, "cudaStreamCreateWithFlags");
+    }
+    p->own_stream = true;
+  }
+  if (q.mem_budget_bytes) {
+    p->budget = q.mem_budget_bytes;
+  } else {
+    size_t fr = 0, tot = 0;
+    e = cudaMemGetInfo(&fr, &tot);
+    if (e != cudaSuccess) {
+      jd_problem_destroy(p);
+      return cuda_fail(e, "cudaMemGetInfo");
+    }
+    p->budget = fr / 2;
+  }
+  const size_t es = elem_size(p), nu = (size_t)q.Nt * q.du;
+  jd_status s = JD_OK;
+#define ALLOC(ptr, bytes, name)                                  \
+  do {                                                           \
+    s = dev_alloc(p, (void **)&(ptr), (bytes), name);            \
+    if (s) {                                                     \
+      jd_problem_destroy(p);                                     \
+      return s;                                                  \
+    }                                                            \
+  } while (0)
+  ALLOC(p->uk, (size_t)q.Nt * p->DU * es, "control");
+  ALLOC(p->xdk, (size_t)(q.Nt + 1) * p->D * es, "target");
+  ALLOC(p->u_in, nu * 8, "control (FP64)");
+  ALLOC(p->grad_d, nu * 8, "gradient");
+  ALLOC(p->scal_d, NSCAL * 8, "scalars");
+  ALLOC(p->partC, (size_t)p->nblk * 8, "cost partials");
+  ALLOC(p->partG, (size_t)q.Nt * p->DU * p->nblk * 8, "gradient partials");
+  ALLOC(p->partT, (size_t)(p->D + 2) * p->nblk * 8, "parameter partials");
+  ALLOC(p->opt_u, nu * 8, "optimizer iterate");
+  ALLOC(p->opt_ut, nu * 8, "optimizer trial");
+#undef ALLOC
+  e = cudaMallocHost((void **)&p->host_pinned, NSCAL * 8);
+  if (e != cudaSuccess) {
+    jd_problem_destroy(p);
+    return cuda_fail(e, "cudaMallocHost");
+  }
+  // padded target in kernel precision
+  std::vector<double> xdp((size_t)(q.Nt + 1) * p->D, 0.0);
+  for (int k = 0; k <= q.Nt; ++k)
+    for (int c = 0; c < q.d; ++c) xdp[(size_t)k * p->D + c] = p->xd[(size_t)k * q.d + c];
+  if (q.prec == JD_FP64) {
+    e = cudaMemcpy(p->xdk, xdp.data(), xdp.size() * 8, cudaMemcpyHostToDevice);
+  } else {
+    std::vector<float> xf(xdp.begin(), xdp.end());
+    e = cudaMemcpy(p->xdk, xf.data(), xf.size() * 4, cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) {
+    jd_problem_destroy(p);
+    return cuda_fail(e, "cudaMemcpy target");
+  }
+  e = cudaMemset(p->scal_d, 0, NSCAL * 8);
+  if (e != cudaSuccess) {
+    jd_problem_destroy(p);
+    return cuda_fail(e, "cudaMemset");
+  }
+  *out = p;
+  return JD_OK;
+}
+
+jd_status jd_problem_info(const jd_problem *p, size_t *device_bytes, jd_adjoint_mode *mode) {
+  if (!p) return fail(JD_ERR_INVALID_ARG, "p is NULL");
+  if (device_bytes) *device_bytes = p->bytes;
+  if (mode) *mode = p->plan;
+  return JD_OK;
+}
+
+jd_status jd_cost(jd_problem *p, const double *u, jd_memspace us, double *J) {
+  if (!p || !J) return fail(JD_ERR_INVALID_ARG, "p and J must be non-NULL");
+  jd_status s = set_device(p);
+  if (!s) s = load_u(p, u, us);
+  if (!s) s = clear_bad(p);
+  if (!s) s = run_cost(p, p->u_in, S_J);
+  if (!s) s = read_scalars(p, S_J, 1);
+  if (s) return s;
+  *J = p->host_pinned[S_J];
+  return check_bad(p);
+}
+
+jd_status jd_gradient(jd_problem *p, const double *u, jd_memspace us, double *J, double *grad,
+                      jd_memspace gs, double *grad_theta) {
+  if (!p) return fail(JD_ERR_INVALID_ARG, "p is NULL");
+  if (grad && gs != JD_MEM_HOST && gs != JD_MEM_DEVICE) return fail(JD_ERR_INVALID_ARG, "bad memory space for grad");
+  jd_status s = set_device(p);
+  if (!s) s = load_u(p, u, us);
+  if (!s) s = clear_bad(p);
+  if (!s) s = run_gradient(p, p->u_in, grad_theta != nullptr);
+  if (s) return s;
+  const size_t n = (size_t)p->desc.Nt * p->desc.du;
+  if (grad) {
+    JD_CUDA(cudaMemcpyAsync(grad, p->grad_d, n * 8,
+                            gs == JD_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, p->stream));
+  }
+  const bool host_out = J || grad_theta || (grad && gs == JD_MEM_HOST);
+  if (!host_out) return JD_OK;
+  s = read_scalars(p, 0, NSCAL);
+  if (s) return s;
+  if (J) *J = p->host_pinned[S_J];
+  if (grad_theta)
+    for (int t = 0; t < p->desc.d + 2; ++t) grad_theta[t] = p->host_pinned[S_THETA + t];
+  if (p->host_pinned[S_BAD] != 0.0) return fail(JD_ERR_NONFINITE, "cost or gradient is not finite");
+  return JD_OK;
+}
+
+jd_status jd_sample_paths(jd_problem *p, const double *u, jd_memspace us, int64_t m0, int64_t count,
+                          double *X, double *lam, double *cost) {
+  if (!p) return fail(JD_ERR_INVALID_ARG, "p is NULL");
+  if (m0 < 0 || count < 1 || m0 + count > p->desc.M)
+    return fail(JD_ERR_INVALID_ARG, "path range outside [0, M)");
+  jd_status s = set_device(p);
+  if (!s) s = load_u(p, u, us);
+  if (!s) s = prep_u(p, p->u_in);
+  if (s) return s;
+  const jd_problem_desc &q = p->desc;
+  const int D = p->D, Nt = q.Nt, d = q.d;
+  const size_t es = elem_size(p);
+  const int64_t nb = ceil_div(count, TPB), ng = (Nt + 4) / 4;
+  const size_t traj_b = (size_t)ng * D * count * 4 * es, flag_b = (size_t)ceil_div(Nt, 32) * count * 4;
+  const size_t lam_b = (size_t)(Nt + 1) * D * count * es;
+  void *traj = nullptr, *flags = nullptr, *lamd = nullptr, *pc = nullptr, *pC = nullptr, *pG = nullptr;
+  cudaError_t e = cudaMalloc(&traj, traj_b);
+  if (e == cudaSuccess) e = cudaMalloc(&flags, flag_b);
+  if (e == cudaSuccess) e = cudaMalloc(&lamd, lam_b);
+  if (e == cudaSuccess) e = cudaMalloc(&pc, count * es);
+  if (e == cudaSuccess) e = cudaMalloc(&pC, nb * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&pG, (size_t)Nt * p->DU * nb * 8);
+  if (e == cudaSuccess)
+    e = p->ops->fwd(p, FWD_STORE, m0, count, p->uk, traj, (uint32_t *)flags, nullptr, (double *)pC, pc, p->stream);
+  if (e == cudaSuccess && lam)
+    e = p->ops->adj(p, ADJ_STORED_V, false, m0, count, p->uk, traj, (const uint32_t *)flags, nullptr,
+                    (double *)pG, nullptr, lamd, p->stream);
+  std::vector<unsigned char> ht, hl, hc;
+  if (e == cudaSuccess) {
+    ht.resize(traj_b);
+    hc.resize(count * es);
+    e = cudaMemcpyAsync(ht.data(), traj, traj_b, cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), pc, count * es, cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess && lam) {
+      hl.resize(lam_b);
+      e = cudaMemcpyAsync(hl.data(), lamd, lam_b, cudaMemcpyDeviceToHost, p->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  }
+  cudaFree(traj);
+  cudaFree(flags);
+  cudaFree(lamd);
+  cudaFree(pc);
+  cudaFree(pC);
+  cudaFree(pG);
+  if (e != cudaSuccess) return cuda_fail(e, "jd_sample_paths");
+  auto rd = [&](const std::vector<unsigned char> &v, size_t idx) -> double {
+    if (es == 8) return reinterpret_cast<const double *>(v.data())[idx];
+    return (double)reinterpret_cast<const float *>(v.data())[idx];
+  };
+  for (int64_t i = 0; i < count; ++i) {
+    if (cost) cost[i] = rd(hc, i);
+    for (int k = 0; k <= Nt; ++k)
+      for (int c = 0; c < d; ++c) {
+        const size_t base = (size_t)(i * (Nt + 1) + k) * d + c;
+        if (X) X[base] = rd(ht, ((((size_t)(k >> 2) * D + c) * count + i) * 4) + (k & 3));
+        if (lam) lam[base] = rd(hl, ((size_t)k * D + c) * count + i);
+      }
+  }
+  return JD_OK;
+}
+
+jd_status jd_optimize(jd_problem *p, double *u_inout, jd_memspace us, const jd_opt_params *o,
+                      jd_opt_result *r, double *J_hist) {
+  if (!p || !u_inout || !o || !r) return fail(JD_ERR_INVALID_ARG, "p, u_inout, o, r must be non-NULL");
+  if (o->max_iter < 0 || o->max_backtracks < 0 || !(o->armijo_c >= 0.0))
+    return fail(JD_ERR_INVALID_ARG, "bad optimizer parameters");
+  std::memset(r, 0, sizeof(*r));
+  jd_status s = set_device(p);
+  if (!s) s = load_u(p, u_inout, us);
+  if (s) return s;
+  const jd_problem_desc &q = p->desc;
+  const int n = q.Nt * q.du;
+  const double dt = q.T / q.Nt;
+  JD_CUDA(cudaMemcpyAsync(p->opt_u, p->u_in, (size_t)n * 8, cudaMemcpyDeviceToDevice, p->stream));
+  double zeta = o->zeta0 > 0.0 ? o->zeta0 : 1.0;
+  const double zeta_max = o->zeta_max > 0.0 ? o->zeta_max : 1e3;
+  double pg0 = -1.0;
+  int it = 0;
+  jd_status status = JD_OK;
+  // Algorithm 5.4: each iteration is one gradient at u^n, an Armijo line search and
+  // the update; no gradient after the last update.
+  for (it = 0; it < o->max_iter; ++it) {
+    s = clear_bad(p);
+    if (!s) s = run_gradient(p, p->opt_u, false);
+    if (s) return s;
+    r->evals++;
+    int pr = prof_begin(KC_OPT, p->stream);
+    opt_pgnorm_kernel<<<1, 256, 0, p->stream>>>(n, p->opt_u, p->grad_d, dt, q.u_min, q.u_max,
+                                                p->scal_d + S_PG);
+    prof_end(pr, p->stream);
+    count_launch();
+    JD_CUDA(cudaGetLastError());
+    s = read_scalars(p, 0, 8);
+    if (s) return s;
+    if (p->host_pinned[S_BAD] != 0.0) {
+      status = fail(JD_ERR_NONFINITE, "cost or gradient is not finite");
+      break;
+    }
+    const double J = p->host_pinned[S_J], pg = p->host_pinned[S_PG];
+    if (J_hist) J_hist[it] = J;
+    r->J = J;
+    if (pg0 < 0.0) pg0 = pg;
+    r->rel_grad_norm = pg0 > 0.0 ? pg / pg0 : 0.0;
+    if (r->rel_grad_norm <= o->tol_rel_grad) break;
+    if (it > 0) zeta = std::fmin(2.0 * zeta, zeta_max);
+    bool accepted = false;
+    double step2 = 0.0;
+    for (int b = 0; b <= o->max_backtracks; ++b) {
+      pr = prof_begin(KC_OPT, p->stream);
+      opt_trial_kernel<<<1, 256, 0, p->stream>>>(n, p->opt_u, p->grad_d, zeta, dt, q.u_min, q.u_max,
+                                                 p->opt_ut, p->scal_d + S_DOT);
+      prof_end(pr, p->stream);
+      count_launch();
+      JD_CUDA(cudaGetLastError());
+      s = run_cost(p, p->opt_ut, S_JT);
+      if (s) return s;
+      r->evals++;
+      pr = prof_begin(KC_OPT, p->stream);
+      opt_accept_kernel<<<1, 256, 0, p->stream>>>(n, p->opt_u, p->opt_ut, o->armijo_c, dt, p->scal_d);
+      prof_end(pr, p->stream);
+      count_launch();
+      JD_CUDA(cudaGetLastError());
+      s = read_scalars(p, 0, 8);
+      if (s) return s;
+      if (p->host_pinned[S_ACC] != 0.0) {
+        accepted = true;
+        step2 = p->host_pinned[S_STEP];
+        r->J = p->host_pinned[S_J];
+        break;
+      }
+      zeta *= 0.5;
+    }
+    if (!accepted) {
+      status = fail(JD_ERR_LINESEARCH, "Armijo backtracking exhausted");
+      break;
+    }
+    if (J_hist) J_hist[it + 1] = r->J;
+    if (std::sqrt(step2) < o->tol_step) {
+      it++;
+      break;
+    }
+  }
+  r->iters = it;
+  r->zeta = zeta;
+  r->status = status;
+  JD_CUDA(cudaMemcpyAsync(u_inout, p->opt_u, (size_t)n * 8,
+                          us == JD_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, p->stream));
+  JD_CUDA(cudaStreamSynchronize(p->stream));
+  return status;
+}
+
+}  // extern "C"

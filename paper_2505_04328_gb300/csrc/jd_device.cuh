@@ -1,0 +1,443 @@
+// jd_device.cuh -- device primitives of the path kernels (sm_103a).
+//
+//  * Philox4x32-10 (Salmon et al., SC'11), written from its published definition.
+//  * Uniform ((w >> 9) + 1/2) 2^-23, exact in FP32 and FP64, never 0 or 1.
+//  * Box-Muller pairs (first word: radius, second: angle) with the CUDA math
+//    library's logf/sqrtf/sincospif (or the double versions).
+//  * Compensated (TwoSum) pairs for every cross-path sum, reduced by a transposed
+//    warp butterfly (one shuffle per path-step) and then across the block.
+//  * One Euler-Maruyama step of the jump-adapted scheme (Algorithm 5.1) and its
+//    exact adjoint (eq:AdjointModel read as the derivative of the discrete cost).
+//
+// All state arithmetic uses explicit round-to-nearest intrinsics (__fmaf_rn,
+// __fmul_rn, __fadd_rn ...), so the compiler cannot contract or reorder it and the
+// stored and recomputed sweeps produce the same bits.
+#pragma once
+
+#include <cstdint>
+
+#include "jd_internal.h"
+
+namespace jd {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                          uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    const uint32_t y0 = hi1 ^ c1 ^ k0, y2 = hi0 ^ c3 ^ k1;
+    c0 = y0;
+    c1 = lo1;
+    c2 = y2;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+// ---------------------------------------------------------------------------
+// Precision-generic arithmetic with fixed rounding
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Ar;
+
+template <>
+struct Ar<float> {
+  static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float sqrt(float a) { return __fsqrt_rn(a); }
+  static __device__ __forceinline__ float log(float a) { return logf(a); }
+  static __device__ __forceinline__ void sincospi(float a, float *s, float *c) { sincospif(a, s, c); }
+  static __device__ __forceinline__ float u01(uint32_t w) {
+    return __fmaf_rn(__uint2float_rn(w >> 9), 0x1p-23f, 0x1p-24f);
+  }
+};
+
+template <>
+struct Ar<double> {
+  static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double sqrt(double a) { return __dsqrt_rn(a); }
+  static __device__ __forceinline__ double log(double a) { return ::log(a); }
+  static __device__ __forceinline__ void sincospi(double a, double *s, double *c) { ::sincospi(a, s, c); }
+  static __device__ __forceinline__ double u01(uint32_t w) {
+    return __fma_rn((double)(w >> 9), 0x1p-23, 0x1p-24);
+  }
+};
+
+template <typename R>
+__device__ __forceinline__ void normal_pair(uint32_t wa, uint32_t wb, R &z0, R &z1) {
+  using M = Ar<R>;
+  const R ua = M::u01(wa), ub = M::u01(wb);
+  const R r = M::sqrt(M::mul(R(-2), M::log(ua)));
+  R s, c;
+  M::sincospi(M::mul(R(2), ub), &s, &c);
+  z0 = M::mul(r, c);
+  z1 = M::mul(r, s);
+}
+
+// ---------------------------------------------------------------------------
+// Compensated sums: (s, e) with the true value s + e; TwoSum keeps every addition
+// exact up to the final rounding of e.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Pair {
+  R s, e;
+};
+
+template <typename R>
+__device__ __forceinline__ Pair<R> padd(Pair<R> a, Pair<R> b) {
+  using M = Ar<R>;
+  const R s = M::add(a.s, b.s);
+  const R bb = M::sub(s, a.s);
+  const R err = M::add(M::sub(a.s, M::sub(s, bb)), M::sub(b.s, bb));
+  return {s, M::add(M::add(a.e, b.e), err)};
+}
+
+template <typename R>
+__device__ __forceinline__ Pair<R> shfl_xor(Pair<R> v, int o) {
+  return {__shfl_xor_sync(0xffffffffu, v.s, o), __shfl_xor_sync(0xffffffffu, v.e, o)};
+}
+
+template <typename R>
+__device__ __forceinline__ Pair<R> warp_sum(Pair<R> v) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) v = padd(v, shfl_xor(v, o));
+  return v;
+}
+
+// Kahan accumulator for one path's running cost (true sum s - c).
+template <typename R>
+struct Kahan {
+  R s = R(0), c = R(0);
+  __device__ __forceinline__ void add(R term) {
+    using M = Ar<R>;
+    const R y = M::sub(term, c);
+    const R t = M::add(s, y);
+    c = M::sub(M::sub(t, s), y);
+    s = t;
+  }
+  __device__ __forceinline__ Pair<R> pair() const { return {s, -c}; }
+};
+
+// Block sum of one pair per thread into a double; thread 0 returns the result.
+template <typename R>
+__device__ __forceinline__ double block_sum_to_double(Pair<R> v, Pair<R> *smem /* >= TPB/32 */) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) smem[warp] = v;
+  __syncthreads();
+  double out = 0.0;
+  if (threadIdx.x == 0) {
+    Pair<R> s = smem[0];
+    for (int w = 1; w < TPB / 32; ++w) s = padd(s, smem[w]);
+    out = (double)s.s + (double)s.e;
+  }
+  __syncthreads();
+  return out;
+}
+
+// Transposed warp reduction of B steps (B = BATCH = 8): every lane holds one value
+// per step; after the butterfly lanes with (lane & 3) == 0 hold the 32-lane sum of
+// step j = 4*bit4 + 2*bit3 + bit2 of the lane index.  Uses B - 1 + 2 shuffles for B
+// steps (about one per path-step).
+template <typename R>
+__device__ __forceinline__ Pair<R> warp_transpose_sum8(Pair<R> (&v)[BATCH], int lane) {
+#pragma unroll
+  for (int c = BATCH, o = 16; c > 1; c >>= 1, o >>= 1) {
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < c / 2; ++i) {
+      const Pair<R> send = upper ? v[i] : v[i + c / 2];
+      const Pair<R> keep = upper ? v[i + c / 2] : v[i];
+      v[i] = padd(keep, shfl_xor(send, o));
+    }
+  }
+  Pair<R> r = v[0];
+  r = padd(r, shfl_xor(r, 2));
+  r = padd(r, shfl_xor(r, 1));
+  return r;
+}
+
+__device__ __forceinline__ int transposed_step_of_lane(int lane) {
+  return ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+}
+
+// One batch of per-step gradient contributions gb[j][l] (steps kbase + j) summed over
+// the block's paths and written as FP64 partials partG[(k*DU + l) * nblk + block].
+// smem holds 2 * (TPB/32) * BATCH * DU pairs; `parity` alternates between batches so
+// one barrier per batch suffices.
+template <typename R, int DU>
+__device__ __forceinline__ void reduce_batch(Pair<R> (&gb)[BATCH][DU], int kbase, int Nt,
+                                             double *__restrict__ partG, int64_t nblk,
+                                             Pair<R> *smem, int parity) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = TPB / 32;
+  Pair<R> *buf = smem + parity * (NW * BATCH * DU);
+#pragma unroll
+  for (int l = 0; l < DU; ++l) {
+    Pair<R> v[BATCH];
+#pragma unroll
+    for (int j = 0; j < BATCH; ++j) v[j] = gb[j][l];
+    const Pair<R> r = warp_transpose_sum8(v, lane);
+    if ((lane & 3) == 0) buf[(warp * BATCH + transposed_step_of_lane(lane)) * DU + l] = r;
+  }
+  __syncthreads();
+  if (threadIdx.x < BATCH * DU) {
+    const int t = threadIdx.x, j = t / DU, l = t % DU, k = kbase + j;
+    Pair<R> s = buf[t];
+#pragma unroll
+    for (int w = 1; w < NW; ++w) s = padd(s, buf[w * BATCH * DU + t]);
+    if (k < Nt) partG[((int64_t)k * DU + l) * nblk + blockIdx.x] = (double)s.s + (double)s.e;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Model: drift f = A x + C x^3 + B u and its transposed Jacobian
+// ---------------------------------------------------------------------------
+template <typename R, int D, int DU>
+__device__ __forceinline__ void drift(const KParams<R, D, DU> &kp, const R (&y)[D], const R (&u)[DU],
+                                      R (&f)[D]) {
+  using M = Ar<R>;
+#pragma unroll
+  for (int i = 0; i < D; ++i) {
+    R s = R(0);
+#pragma unroll
+    for (int l = 0; l < DU; ++l) s = M::fma(kp.B[i * DU + l], u[l], s);
+#pragma unroll
+    for (int j = 0; j < D; ++j) s = M::fma(kp.A[i * D + j], y[j], s);
+    f[i] = s;
+  }
+  if (kp.cubic) {
+    R y3[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) y3[j] = M::mul(M::mul(y[j], y[j]), y[j]);
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int j = 0; j < D; ++j) f[i] = M::fma(kp.C[i * D + j], y3[j], f[i]);
+  }
+}
+
+// mu <- mu + delta J_f(y)^T mu,  J_f = A + 3 C diag(y^2)
+template <typename R, int D, int DU>
+__device__ __forceinline__ void adjoint_update(const KParams<R, D, DU> &kp, const R (&y)[D], R delta,
+                                               R (&mu)[D]) {
+  using M = Ar<R>;
+  R t[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    R s = R(0);
+#pragma unroll
+    for (int i = 0; i < D; ++i) s = M::fma(kp.A[i * D + j], mu[i], s);
+    t[j] = s;
+  }
+  if (kp.cubic) {
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      R s = R(0);
+#pragma unroll
+      for (int i = 0; i < D; ++i) s = M::fma(kp.C[i * D + j], mu[i], s);
+      t[j] = M::fma(M::mul(R(3), M::mul(y[j], y[j])), s, t[j]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < D; ++j) mu[j] = M::fma(delta, t[j], mu[j]);
+}
+
+// g += delta B^T mu
+template <typename R, int D, int DU>
+__device__ __forceinline__ void control_sensitivity(const KParams<R, D, DU> &kp, const R (&mu)[D],
+                                                    R delta, R (&g)[DU]) {
+  using M = Ar<R>;
+#pragma unroll
+  for (int l = 0; l < DU; ++l) {
+    R s = R(0);
+#pragma unroll
+    for (int c = 0; c < D; ++c) s = M::fma(kp.B[c * DU + l], mu[c], s);
+    g[l] = M::fma(delta, s, g[l]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Random draws of one uniform step
+// ---------------------------------------------------------------------------
+template <int D>
+struct MainWords {
+  static constexpr int PD = (D + 1) / 2;            // normal pairs compiled
+  static constexpr int NB = (1 + 2 * PD + 3) / 4;   // Philox blocks per step
+};
+
+// Main stream of step k, path m: word 0 decides the Poisson count, words 1..2P the
+// sub-step-0 normals.
+template <typename R, int D, int DU>
+__device__ __forceinline__ uint32_t main_draws(const KParams<R, D, DU> &kp, int k, uint32_t m,
+                                               R (&z)[D]) {
+  constexpr int NB = MainWords<D>::NB, PD = MainWords<D>::PD;
+  uint32_t w[4 * NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const uint4 o = philox10((uint32_t)k, m, (uint32_t)b, kp.epoch, kp.key0, kp.key1);
+    w[4 * b] = o.x;
+    w[4 * b + 1] = o.y;
+    w[4 * b + 2] = o.z;
+    w[4 * b + 3] = o.w;
+  }
+#pragma unroll
+  for (int p = 0; p < PD; ++p) {
+    R a, b;
+    normal_pair<R>(w[1 + 2 * p], w[2 + 2 * p], a, b);
+    z[2 * p] = a;
+    if (2 * p + 1 < D) z[2 * p + 1] = b;
+  }
+  return w[0];
+}
+
+template <typename R, int D, int DU>
+__device__ __forceinline__ bool has_jump(const KParams<R, D, DU> &kp, uint32_t w0) {
+  return kp.jumps_on && (unsigned long long)w0 >= kp.thr[0];
+}
+
+// Sub-step structure of a step that has jumps: the time order of the jump slots,
+// the sub-step lengths and the sub-step start states.  Sizes and normals are not
+// stored; they are regenerated from the slot's Philox words when needed.
+template <typename R, int D>
+struct JumpStep {
+  int n;
+  int order[NMAX];        // slot (0-based) of the i-th jump in time order
+  R delta[NMAX + 1];
+  R Y[NMAX + 2][D];       // Y[i] = start of sub-step i, Y[n+1] = X_{k+1}
+};
+
+// Jump slot s of step k (counter (k, m, 1<<24 | (s+1)<<16 | b, epoch)): word 0 is the
+// time fraction, words 1..2P the size, words 1+2P..4P the normals of the sub-step
+// that starts at this jump.  Returns unit sizes xih and normals z (zero for c >= d).
+template <typename R, int D, int DU>
+__device__ __forceinline__ void slot_draws(const KParams<R, D, DU> &kp, int k, uint32_t m, int s,
+                                           R *xih, R *z) {
+  using M = Ar<R>;
+  const int P = kp.npair, d = kp.d;
+  const uint32_t tag = (1u << 24) | ((uint32_t)(s + 1) << 16);
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    xih[c] = R(0);
+    z[c] = R(0);
+  }
+  uint4 blk = make_uint4(0, 0, 0, 0);
+  int have = -1;
+  auto word = [&](int j) -> uint32_t {
+    if ((j >> 2) != have) {
+      have = j >> 2;
+      blk = philox10((uint32_t)k, m, tag | (uint32_t)have, kp.epoch, kp.key0, kp.key1);
+    }
+    const int r = j & 3;
+    return r == 0 ? blk.x : (r == 1 ? blk.y : (r == 2 ? blk.z : blk.w));
+  };
+#pragma unroll 1
+  for (int p = 0; p < P; ++p) {
+    const uint32_t wa = word(1 + 2 * p), wb = word(2 + 2 * p);
+    R a, b;
+    if (kp.jump_law == JD_JUMP_UNIFORM) {
+      a = M::sub(M::mul(R(2), M::u01(wa)), R(1));
+      b = M::sub(M::mul(R(2), M::u01(wb)), R(1));
+    } else {
+      normal_pair<R>(wa, wb, a, b);
+    }
+    if (2 * p < d) xih[2 * p] = a;
+    if (2 * p + 1 < d) xih[2 * p + 1] = b;
+  }
+#pragma unroll 1
+  for (int p = 0; p < P; ++p) {
+    const uint32_t wa = word(1 + 2 * P + 2 * p), wb = word(2 + 2 * P + 2 * p);
+    R a, b;
+    normal_pair<R>(wa, wb, a, b);
+    if (2 * p < d) z[2 * p] = a;
+    if (2 * p + 1 < d) z[2 * p + 1] = b;
+  }
+}
+
+// Plan and integrate a step that has jumps (Algorithm 5.1 with the additive jump
+// map): Poisson count from w0, jump times (word 0 of every slot) sorted stably,
+// sub-step lengths, then the Euler sub-steps from x with the jump of slot order[i]
+// added after sub-step i.
+template <typename R, int D, int DU>
+__device__ __noinline__ void build_jump_step(const KParams<R, D, DU> &kp, int k, uint32_t m,
+                                             uint32_t w0, const R *z0, const R *u, const R *x,
+                                             JumpStep<R, D> *S) {
+  using M = Ar<R>;
+  int n = 0;
+#pragma unroll 1
+  for (int i = 0; i < NMAX; ++i) n += ((unsigned long long)w0 >= kp.thr[i]) ? 1 : 0;
+  S->n = n;
+  if (n == 0) {   // callers only come here after a jump was drawn; stay well defined
+    R uu[DU], y[D], f[D];
+#pragma unroll
+    for (int l = 0; l < DU; ++l) uu[l] = u[l];
+#pragma unroll
+    for (int c = 0; c < D; ++c) y[c] = S->Y[0][c] = x[c];
+    drift(kp, y, uu, f);
+    S->delta[0] = kp.dt;
+#pragma unroll
+    for (int c = 0; c < D; ++c) S->Y[1][c] = M::fma(kp.sig_sqdt[c], z0[c], M::fma(kp.dt, f[c], y[c]));
+    return;
+  }
+  R theta[NMAX];
+#pragma unroll 1
+  for (int i = 0; i < n; ++i) {
+    const uint4 o = philox10((uint32_t)k, m, (1u << 24) | ((uint32_t)(i + 1) << 16), kp.epoch,
+                             kp.key0, kp.key1);
+    theta[i] = M::u01(o.x);
+    S->order[i] = i;
+  }
+#pragma unroll 1
+  for (int i = 1; i < n; ++i) {
+    const int cur = S->order[i];
+    int j = i - 1;
+    while (j >= 0 && theta[S->order[j]] > theta[cur]) {
+      S->order[j + 1] = S->order[j];
+      --j;
+    }
+    S->order[j + 1] = cur;
+  }
+  S->delta[0] = M::mul(kp.dt, theta[S->order[0]]);
+#pragma unroll 1
+  for (int i = 1; i < n; ++i)
+    S->delta[i] = M::mul(kp.dt, M::sub(theta[S->order[i]], theta[S->order[i - 1]]));
+  S->delta[n] = M::mul(kp.dt, M::sub(R(1), theta[S->order[n - 1]]));
+  R uu[DU], y[D], z[D];
+#pragma unroll
+  for (int l = 0; l < DU; ++l) uu[l] = u[l];
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    y[c] = x[c];
+    z[c] = z0[c];
+    S->Y[0][c] = y[c];
+  }
+#pragma unroll 1
+  for (int i = 0; i <= n; ++i) {
+    R f[D];
+    drift(kp, y, uu, f);
+    const R de = S->delta[i], sq = M::sqrt(de);
+#pragma unroll
+    for (int c = 0; c < D; ++c) y[c] = M::fma(M::mul(kp.sigma[c], sq), z[c], M::fma(de, f[c], y[c]));
+    if (i < n) {
+      R xih[D];
+      slot_draws(kp, k, m, S->order[i], xih, z);
+#pragma unroll
+      for (int c = 0; c < D; ++c) y[c] = M::add(y[c], M::mul(kp.jump_scale, xih[c]));
+    }
+#pragma unroll
+    for (int c = 0; c < D; ++c) S->Y[i + 1][c] = y[c];
+  }
+}
+
+}  // namespace jd

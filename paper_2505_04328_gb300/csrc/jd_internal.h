@@ -38,10 +38,13 @@ struct KParams {
 // Per-instantiation launch table (one entry per precision x compiled dimension).
 struct PathOps {
   int D, DU, S, elem;
+  // per-thread stack bytes the kernels of this instantiation may need (the jump path
+  // keeps its sub-step states in local memory behind a non-inlined call)
+  size_t (*stack_bytes)();
   // forward sweep: cost partials per block; optional trajectory / checkpoint stores
   cudaError_t (*fwd)(const struct ::jd_problem *p, int mode, int64_t m_begin, int64_t mloc,
                      const void *uk, void *traj, uint32_t *flags, void *ckpt, double *partC,
-                     cudaStream_t s);
+                     void *pcost, cudaStream_t s);
   // adjoint sweep: per-step gradient partials [Nt][DU][nblk]; theta partials [D+2][nblk]
   cudaError_t (*adj)(const struct ::jd_problem *p, int variant, bool theta, int64_t m_begin,
                      int64_t mloc, const void *uk, const void *traj, const uint32_t *flags,
@@ -49,9 +52,8 @@ struct PathOps {
                      cudaStream_t s);
 };
 
-const PathOps *path_ops(int prec, int D);
+const PathOps *path_ops_dims(int prec, int D, int DU);
 int compiled_dim(int d);         // smallest compiled D >= d, or 0
-int compiled_du(int D);          // control dimension compiled for D
 
 void count_launch(int n = 1);
 

@@ -1,0 +1,584 @@
+// jd_kernels.cuh -- path kernels: one thread per Monte Carlo path, state in registers.
+//
+//  fwd_kernel       forward Euler-Maruyama sweep on the jump-adapted grid
+//                   (Algorithms 5.1/5.2) with the running cost of
+//                   eq:discrete_functional; optionally stores every state (stored
+//                   variant) or a checkpoint every S steps (recompute variant).
+//  adj_stored       backward adjoint sweep (eq:AdjointModel, eq:adjoint_eq_approximation)
+//                   over the stored states; per-step contributions delta B^T lambda
+//                   reduced across the block into FP64 partials (eq:definition_Gradient).
+//  adj_recompute    the same sweep without stored states: each S-step segment is
+//                   regenerated from its checkpoint and the counter-based streams into
+//                   shared memory, then swept backwards.  Same arithmetic, same bits.
+//
+// Layouts (mloc = paths of the launch, lm = local path index):
+//   traj  [ceil((Nt+1)/4)][D][mloc][4]  states X_k, k = 4g + j, 16-byte vector stores
+//   flags [ceil(Nt/32)][mloc]           bit k%32 set when step k had a jump
+//   ckpt  [nseg+1][D][mloc]              X_{sS} for s < nseg, X_Nt at s = nseg
+//   partC [nblk]                          FP64 block sums of the per-path cost
+//   partG [Nt][DU][nblk]                  FP64 block sums of the control sensitivities
+//   partT [D+2][nblk]                     FP64 block sums of the parameter sensitivities
+#pragma once
+
+#include "jd_device.cuh"
+
+namespace jd {
+
+template <typename R>
+struct Vec4;
+template <>
+struct Vec4<float> {
+  static __device__ __forceinline__ void store(float *p, float a, float b, float c, float d) {
+    *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
+  }
+  static __device__ __forceinline__ void load(const float *p, float (&o)[4]) {
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  }
+};
+template <>
+struct Vec4<double> {
+  static __device__ __forceinline__ void store(double *p, double a, double b, double c, double d) {
+    reinterpret_cast<double2 *>(p)[0] = make_double2(a, b);
+    reinterpret_cast<double2 *>(p)[1] = make_double2(c, d);
+  }
+  static __device__ __forceinline__ void load(const double *p, double (&o)[4]) {
+    const double2 v0 = __ldg(reinterpret_cast<const double2 *>(p));
+    const double2 v1 = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    o[0] = v0.x; o[1] = v0.y; o[2] = v1.x; o[3] = v1.y;
+  }
+};
+
+// One uniform step k from x (in place).  Returns true when the step had jumps.
+template <typename R, int D, int DU>
+__device__ __forceinline__ bool forward_step(const KParams<R, D, DU> &kp, int k, uint32_t m,
+                                             const R *__restrict__ u, R (&x)[D]) {
+  using M = Ar<R>;
+  R z[D];
+  const uint32_t w0 = main_draws(kp, k, m, z);
+  R uk[DU];
+#pragma unroll
+  for (int l = 0; l < DU; ++l) uk[l] = __ldg(u + (size_t)k * DU + l);
+  if (!has_jump(kp, w0)) {
+    R f[D];
+    drift(kp, x, uk, f);
+#pragma unroll
+    for (int c = 0; c < D; ++c) x[c] = M::fma(kp.sig_sqdt[c], z[c], M::fma(kp.dt, f[c], x[c]));
+    return false;
+  }
+  JumpStep<R, D> S;
+  R xl[D];
+#pragma unroll
+  for (int c = 0; c < D; ++c) xl[c] = x[c];
+  build_jump_step(kp, k, m, w0, z, uk, xl, &S);
+#pragma unroll
+  for (int c = 0; c < D; ++c) x[c] = S.Y[S.n + 1][c];
+  return true;
+}
+
+// dt l(x, t_k) = sum_c (q_c dt / 2) (x_c - xd_c(t_k))^2
+template <typename R, int D, int DU>
+__device__ __forceinline__ R cost_term(const KParams<R, D, DU> &kp, const R (&x)[D],
+                                       const R *__restrict__ xdk) {
+  using M = Ar<R>;
+  R t = R(0);
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    const R e = M::sub(x[c], __ldg(xdk + c));
+    t = M::fma(M::mul(kp.hqdt[c], e), e, t);
+  }
+  return t;
+}
+
+// Backward through a step that had jumps: regenerate its draws and sub-states from
+// X_k, then sweep the sub-steps in reverse.  mu enters as the derivative w.r.t.
+// X_{k+1} and leaves as the derivative w.r.t. X_k (before the cost term at t_k).
+template <typename R, int D, int DU, bool THETA>
+__device__ __noinline__ void jump_backward(const KParams<R, D, DU> &kp, int k, uint32_t m,
+                                           const R *xk, const R *uk, R *mu_io, R *g_io,
+                                           R *th_io) {
+  using M = Ar<R>;
+  R z0[D];
+  const uint32_t w0 = main_draws(kp, k, m, z0);
+  JumpStep<R, D> S;
+  build_jump_step(kp, k, m, w0, z0, uk, xk, &S);
+  R mu[D], g[DU];
+#pragma unroll
+  for (int c = 0; c < D; ++c) mu[c] = mu_io[c];
+#pragma unroll
+  for (int l = 0; l < DU; ++l) g[l] = g_io[l];
+  // parameter sensitivities need the sub-step normals Z_i and the unit jump sizes;
+  // they are regenerated per slot, walking the slots backwards (slot order[i] gives
+  // the jump after sub-step i and the normals of sub-step i+1)
+  R xih_cur[D], z_cur[D];
+  if (THETA && S.n > 0) slot_draws(kp, k, m, S.order[S.n - 1], xih_cur, z_cur);
+#pragma unroll 1
+  for (int i = S.n; i >= 0; --i) {
+    R y[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) y[c] = S.Y[i][c];
+    const R de = S.delta[i];
+    if (THETA) {
+      R zi[D];
+      if (i < S.n) {
+        // jump of slot order[i] after sub-step i: xih_cur holds its unit size
+        R s = R(0);
+#pragma unroll
+        for (int c = 0; c < D; ++c) s = M::fma(mu[c], xih_cur[c], s);
+        th_io[D + 1] = M::add(th_io[D + 1], s);
+      }
+      if (i == 0) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) zi[c] = z0[c];
+      } else {
+        // normals of sub-step i come from slot order[i-1]
+        if (i < S.n) slot_draws(kp, k, m, S.order[i - 1], xih_cur, z_cur);
+#pragma unroll
+        for (int c = 0; c < D; ++c) zi[c] = z_cur[c];
+      }
+      const R sq = M::sqrt(de);
+#pragma unroll
+      for (int c = 0; c < D; ++c) th_io[1 + c] = M::fma(M::mul(mu[c], sq), zi[c], th_io[1 + c]);
+      if (kp.has_dA) {
+        R s = R(0);
+#pragma unroll
+        for (int r = 0; r < D; ++r)
+#pragma unroll
+          for (int c = 0; c < D; ++c) s = M::fma(M::mul(mu[r], kp.dA[r * D + c]), y[c], s);
+        th_io[0] = M::fma(de, s, th_io[0]);
+      }
+    }
+    control_sensitivity(kp, mu, de, g);
+    adjoint_update(kp, y, de, mu);
+  }
+#pragma unroll
+  for (int c = 0; c < D; ++c) mu_io[c] = mu[c];
+#pragma unroll
+  for (int l = 0; l < DU; ++l) g_io[l] = g[l];
+}
+
+// Backward through step k from the state X_k; g receives the step's contribution.
+template <typename R, int D, int DU, bool THETA>
+__device__ __forceinline__ void backward_step(const KParams<R, D, DU> &kp, int k, uint32_t m,
+                                              bool jumped, const R (&xk)[D],
+                                              const R *__restrict__ u, const R *__restrict__ xd,
+                                              R (&mu)[D], R (&g)[DU], R (&th)[D + 2]) {
+  using M = Ar<R>;
+#pragma unroll
+  for (int l = 0; l < DU; ++l) g[l] = R(0);
+  if (jumped) {
+    R xl[D], ml[D], gl[DU], tl[D + 2], ul[DU];
+#pragma unroll
+    for (int c = 0; c < D; ++c) { xl[c] = xk[c]; ml[c] = mu[c]; }
+#pragma unroll
+    for (int l = 0; l < DU; ++l) { gl[l] = R(0); ul[l] = __ldg(u + (size_t)k * DU + l); }
+#pragma unroll
+    for (int t = 0; t < D + 2; ++t) tl[t] = th[t];
+    jump_backward<R, D, DU, THETA>(kp, k, m, xl, ul, ml, gl, tl);
+#pragma unroll
+    for (int c = 0; c < D; ++c) mu[c] = ml[c];
+#pragma unroll
+    for (int l = 0; l < DU; ++l) g[l] = gl[l];
+#pragma unroll
+    for (int t = 0; t < D + 2; ++t) th[t] = tl[t];
+  } else {
+    if (THETA) {
+      R z[D];
+      (void)main_draws(kp, k, m, z);
+#pragma unroll
+      for (int c = 0; c < D; ++c) th[1 + c] = M::fma(M::mul(mu[c], kp.sqdt), z[c], th[1 + c]);
+      if (kp.has_dA) {
+        R s = R(0);
+#pragma unroll
+        for (int r = 0; r < D; ++r)
+#pragma unroll
+          for (int c = 0; c < D; ++c) s = M::fma(M::mul(mu[r], kp.dA[r * D + c]), xk[c], s);
+        th[0] = M::fma(kp.dt, s, th[0]);
+      }
+    }
+    control_sensitivity(kp, mu, kp.dt, g);
+    adjoint_update(kp, xk, kp.dt, mu);
+  }
+  if (k >= 1) {
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+      mu[c] = M::fma(kp.qdt[c], M::sub(xk[c], __ldg(xd + (size_t)k * D + c)), mu[c]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <typename R, int D, int DU, int MODE>
+__global__ void __launch_bounds__(TPB)
+fwd_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u,
+           const R *__restrict__ xd, double *__restrict__ partC, R *__restrict__ traj,
+           uint32_t *__restrict__ flags, R *__restrict__ ckpt, R *__restrict__ pcost,
+           int64_t mloc) {
+  __shared__ Pair<R> red[TPB / 32];
+  const int64_t lm = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  const bool active = lm < mloc;
+  const uint32_t m = (uint32_t)(kp.m_begin + lm);
+  const int Nt = kp.Nt;
+  R x[D];
+#pragma unroll
+  for (int c = 0; c < D; ++c) x[c] = kp.x0[c];
+  Kahan<R> cost;
+  uint32_t fw = 0;
+  const int ng = (Nt + 4) / 4;
+#pragma unroll 1
+  for (int g = 0; g < ng; ++g) {
+    R buf[4][D];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = 4 * g + j;
+      if (MODE == FWD_STORE) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) buf[j][c] = x[c];
+      }
+      if (k < Nt) {
+        if (MODE == FWD_CKPT && active && (k % kp.S) == 0) {
+#pragma unroll
+          for (int c = 0; c < D; ++c) ckpt[((size_t)(k / kp.S) * D + c) * mloc + lm] = x[c];
+        }
+        if (forward_step(kp, k, m, u, x)) fw |= 1u << (k & 31);
+        cost.add(cost_term(kp, x, xd + (size_t)(k + 1) * D));
+        if (MODE == FWD_STORE && ((k & 31) == 31 || k == Nt - 1)) {
+          if (active) flags[(size_t)(k >> 5) * mloc + lm] = fw;
+          fw = 0;
+        }
+      }
+    }
+    if (MODE == FWD_STORE && active) {
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+        Vec4<R>::store(traj + (((size_t)g * D + c) * mloc + lm) * 4, buf[0][c], buf[1][c], buf[2][c],
+                       buf[3][c]);
+    }
+  }
+  if (MODE == FWD_CKPT && active) {
+    const int nseg = (Nt + kp.S - 1) / kp.S;
+#pragma unroll
+    for (int c = 0; c < D; ++c) ckpt[((size_t)nseg * D + c) * mloc + lm] = x[c];
+  }
+  Pair<R> v = cost.pair();
+  if (!active) v = {R(0), R(0)};
+  if (pcost && active) pcost[lm] = Ar<R>::add(v.s, v.e);
+  const double s = block_sum_to_double(v, red);
+  if (threadIdx.x == 0) partC[blockIdx.x] = s;
+}
+
+template <typename R, int D>
+__device__ __forceinline__ void load_state(const R *__restrict__ traj, int k, int64_t mloc,
+                                           int64_t lm, R (&x)[D]) {
+  const int g = k >> 2, j = k & 3;
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    R v[4];
+    Vec4<R>::load(traj + (((size_t)g * D + c) * mloc + lm) * 4, v);
+    x[c] = j == 0 ? v[0] : (j == 1 ? v[1] : (j == 2 ? v[2] : v[3]));
+  }
+}
+
+template <typename R, int D, int DU, bool THETA>
+__device__ __forceinline__ void finish_theta(const KParams<R, D, DU> &kp, R (&th)[D + 2], bool active,
+                                             double *__restrict__ partT, Pair<R> *red) {
+  if constexpr (THETA) {
+#pragma unroll 1
+  for (int t = 0; t < D + 2; ++t) {
+    Pair<R> v = {active ? th[t] : R(0), R(0)};
+    const double s = block_sum_to_double(v, red);
+    if (threadIdx.x == 0) partT[(size_t)t * kp.nblk + blockIdx.x] = s;
+  }
+  }
+}
+
+template <typename R, int D, int DU, bool THETA>
+__global__ void __launch_bounds__(TPB)
+adj_stored_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u,
+                  const R *__restrict__ xd, const R *__restrict__ traj,
+                  const uint32_t *__restrict__ flags, double *__restrict__ partG,
+                  double *__restrict__ partT, R *__restrict__ lam_out, int64_t mloc) {
+  using M = Ar<R>;
+  __shared__ Pair<R> red[2 * (TPB / 32) * BATCH * DU];
+  __shared__ Pair<R> red1[TPB / 32];
+  const int64_t lm = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  const bool active = lm < mloc;
+  // inactive threads of the last block replay path 0 (its stored data and its random
+  // streams must belong to the same path) and discard the result
+  const int64_t lmc = active ? lm : 0;
+  const uint32_t m = (uint32_t)(kp.m_begin + lmc);
+  const int Nt = kp.Nt;
+  R mu[D], th[D + 2];
+#pragma unroll
+  for (int t = 0; t < D + 2; ++t) th[t] = R(0);
+  {
+    R x[D];
+    load_state<R, D>(traj, Nt, mloc, lmc, x);
+#pragma unroll
+    for (int c = 0; c < D; ++c) mu[c] = M::mul(kp.qdt[c], M::sub(x[c], __ldg(xd + (size_t)Nt * D + c)));
+    if (lam_out && active)
+#pragma unroll
+      for (int c = 0; c < D; ++c) lam_out[((size_t)Nt * D + c) * mloc + lm] = mu[c];
+  }
+  const int nbatch = (Nt + BATCH - 1) / BATCH;
+#pragma unroll 1
+  for (int b = nbatch - 1; b >= 0; --b) {
+    R xs[BATCH][D];
+    const int ng = (Nt + 4) / 4;   // groups of 4 stored states
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int g = 2 * b + h;
+      if (g >= ng) {   // the top batch may end inside group 2b
+#pragma unroll
+        for (int c = 0; c < D; ++c)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) xs[4 * h + j][c] = R(0);
+        continue;
+      }
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        R v[4];
+        Vec4<R>::load(traj + (((size_t)g * D + c) * mloc + lmc) * 4, v);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) xs[4 * h + j][c] = v[j];
+      }
+    }
+    const uint32_t fw = __ldg(flags + (size_t)((BATCH * b) >> 5) * mloc + lmc);
+    Pair<R> gb[BATCH][DU];
+#pragma unroll
+    for (int j = BATCH - 1; j >= 0; --j) {
+      const int k = BATCH * b + j;
+      R g[DU];
+#pragma unroll
+      for (int l = 0; l < DU; ++l) g[l] = R(0);
+      if (k < Nt) {
+        backward_step<R, D, DU, THETA>(kp, k, m, (fw >> (k & 31)) & 1u, xs[j], u, xd, mu, g, th);
+        if (lam_out && active)
+#pragma unroll
+          for (int c = 0; c < D; ++c) lam_out[((size_t)k * D + c) * mloc + lm] = mu[c];
+      }
+#pragma unroll
+      for (int l = 0; l < DU; ++l) gb[j][l] = {active ? g[l] : R(0), R(0)};
+    }
+    reduce_batch<R, DU>(gb, BATCH * b, Nt, partG, kp.nblk, red, b & 1);
+  }
+  finish_theta<R, D, DU, THETA>(kp, th, active, partT, red1);
+}
+
+template <typename R, int D, int DU, bool THETA>
+__global__ void __launch_bounds__(TPB)
+adj_recompute_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u,
+                     const R *__restrict__ xd, const R *__restrict__ ckpt,
+                     double *__restrict__ partG, double *__restrict__ partT, int64_t mloc) {
+  using M = Ar<R>;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  R *sbuf = reinterpret_cast<R *>(dsm);   // [S * D][TPB]
+  __shared__ Pair<R> red[2 * (TPB / 32) * BATCH * DU];
+  __shared__ Pair<R> red1[TPB / 32];
+  const int64_t lm = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  const bool active = lm < mloc;
+  const int64_t lmc = active ? lm : 0;   // inactive threads replay path 0
+  const uint32_t m = (uint32_t)(kp.m_begin + lmc);
+  const int Nt = kp.Nt, S = kp.S, tid = threadIdx.x;
+  const int nseg = (Nt + S - 1) / S;
+  R mu[D], th[D + 2];
+#pragma unroll
+  for (int t = 0; t < D + 2; ++t) th[t] = R(0);
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    const R xN = __ldg(ckpt + ((size_t)nseg * D + c) * mloc + lmc);
+    mu[c] = M::mul(kp.qdt[c], M::sub(xN, __ldg(xd + (size_t)Nt * D + c)));
+  }
+  int parity = 0;
+#pragma unroll 1
+  for (int seg = nseg - 1; seg >= 0; --seg) {
+    const int k0 = seg * S, len = min(S, Nt - k0);
+    R x[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) x[c] = __ldg(ckpt + ((size_t)seg * D + c) * mloc + lmc);
+    uint32_t jm = 0;
+#pragma unroll 1
+    for (int i = 0; i < len; ++i) {
+#pragma unroll
+      for (int c = 0; c < D; ++c) sbuf[(i * D + c) * TPB + tid] = x[c];
+      if (forward_step(kp, k0 + i, m, u, x)) jm |= 1u << i;
+    }
+    const int nb = (len + BATCH - 1) / BATCH;
+#pragma unroll 1
+    for (int bb = nb - 1; bb >= 0; --bb) {
+      Pair<R> gb[BATCH][DU];
+#pragma unroll
+      for (int j = BATCH - 1; j >= 0; --j) {
+        const int i = BATCH * bb + j, k = k0 + i;
+        R g[DU];
+#pragma unroll
+        for (int l = 0; l < DU; ++l) g[l] = R(0);
+        if (i < len) {
+          R xk[D];
+#pragma unroll
+          for (int c = 0; c < D; ++c) xk[c] = sbuf[(i * D + c) * TPB + tid];
+          backward_step<R, D, DU, THETA>(kp, k, m, (jm >> i) & 1u, xk, u, xd, mu, g, th);
+        }
+#pragma unroll
+        for (int l = 0; l < DU; ++l) gb[j][l] = {active ? g[l] : R(0), R(0)};
+      }
+      reduce_batch<R, DU>(gb, k0 + BATCH * bb, Nt, partG, kp.nblk, red, parity);
+      parity ^= 1;
+    }
+  }
+  finish_theta<R, D, DU, THETA>(kp, th, active, partT, red1);
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launch ops for one (precision, D, DU)
+// ---------------------------------------------------------------------------
+template <int D>
+constexpr int seg_len() {
+  return D <= 2 ? 32 : (D <= 8 ? 16 : 8);
+}
+
+// Poisson thresholds floor(2^32 F(n; mu)) with the pmf accumulated in order
+// p_0 = exp(-mu), p_n = p_{n-1} mu / n; clamped to [0, 2^32].
+inline void poisson_thresholds(double mu, unsigned long long *thr) {
+  double pn = std::exp(-mu), F = pn;
+  for (int n = 0; n < NMAX; ++n) {
+    if (n > 0) {
+      pn = pn * mu / (double)n;
+      F = F + pn;
+    }
+    double t = std::floor(F * 4294967296.0);
+    t = t < 0.0 ? 0.0 : (t > 4294967296.0 ? 4294967296.0 : t);
+    thr[n] = (unsigned long long)t;
+  }
+}
+
+template <typename R, int D, int DU>
+void make_kparams(const jd_problem *p, int64_t m_begin, int64_t mloc, KParams<R, D, DU> &kp) {
+  const jd_problem_desc &q = p->desc;
+  const int d = q.d, du = q.du;
+  const double dt = q.T / (double)q.Nt, sqdt = std::sqrt(dt);
+  for (int i = 0; i < D * D; ++i) kp.A[i] = kp.C[i] = kp.dA[i] = R(0);
+  for (int i = 0; i < D * DU; ++i) kp.B[i] = R(0);
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) {
+      kp.A[i * D + j] = (R)p->A[(size_t)i * d + j];
+      if (q.drift == JD_DRIFT_CUBIC) kp.C[i * D + j] = (R)p->C[(size_t)i * d + j];
+      if (!p->dA.empty()) kp.dA[i * D + j] = (R)p->dA[(size_t)i * d + j];
+    }
+  for (int i = 0; i < d; ++i)
+    for (int l = 0; l < du; ++l) kp.B[i * DU + l] = (R)p->B[(size_t)i * du + l];
+  for (int c = 0; c < D; ++c) {
+    const bool in = c < d;
+    kp.sigma[c] = in ? (R)p->sigma[c] : R(0);
+    kp.sig_sqdt[c] = in ? (R)(p->sigma[c] * sqdt) : R(0);
+    kp.qdt[c] = in ? (R)(p->q[c] * dt) : R(0);
+    kp.hqdt[c] = in ? (R)(0.5 * p->q[c] * dt) : R(0);
+    kp.x0[c] = in ? (R)p->x0[c] : R(0);
+  }
+  kp.dt = (R)dt;
+  kp.sqdt = (R)sqdt;
+  kp.jump_scale = (R)q.jump_scale;
+  poisson_thresholds(q.lambda * dt, kp.thr);
+  kp.key0 = (uint32_t)(q.seed & 0xffffffffull);
+  kp.key1 = (uint32_t)(q.seed >> 32);
+  kp.epoch = q.epoch;
+  kp.d = d;
+  kp.npair = (d + 1) / 2;
+  kp.Nt = q.Nt;
+  kp.cubic = q.drift == JD_DRIFT_CUBIC;
+  kp.jump_law = (int)q.jump_law;
+  kp.jumps_on = q.jump_law != JD_JUMP_NONE && q.lambda > 0.0;
+  kp.has_dA = !p->dA.empty();
+  kp.S = seg_len<D>();
+  kp.nblk = (int)ceil_div(mloc, TPB);
+  kp.m_begin = m_begin;
+}
+
+template <typename R, int D, int DU>
+cudaError_t op_fwd(const jd_problem *p, int mode, int64_t m_begin, int64_t mloc, const void *uk,
+                   void *traj, uint32_t *flags, void *ckpt, double *partC, void *pcost,
+                   cudaStream_t s) {
+  auto *kp = new KParams<R, D, DU>();
+  make_kparams<R, D, DU>(p, m_begin, mloc, *kp);
+  const dim3 grid((unsigned)ceil_div(mloc, TPB));
+  const R *u = static_cast<const R *>(uk);
+  const R *xd = static_cast<const R *>(p->xdk);
+  R *pc = static_cast<R *>(pcost);
+  switch (mode) {
+    case FWD_COST:
+      fwd_kernel<R, D, DU, FWD_COST><<<grid, TPB, 0, s>>>(*kp, u, xd, partC, nullptr, nullptr, nullptr, pc, mloc);
+      break;
+    case FWD_STORE:
+      fwd_kernel<R, D, DU, FWD_STORE><<<grid, TPB, 0, s>>>(*kp, u, xd, partC, static_cast<R *>(traj), flags,
+                                                           nullptr, pc, mloc);
+      break;
+    default:
+      fwd_kernel<R, D, DU, FWD_CKPT><<<grid, TPB, 0, s>>>(*kp, u, xd, partC, nullptr, nullptr,
+                                                          static_cast<R *>(ckpt), pc, mloc);
+      break;
+  }
+  delete kp;
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename R, int D, int DU>
+cudaError_t op_adj(const jd_problem *p, int variant, bool theta, int64_t m_begin, int64_t mloc,
+                   const void *uk, const void *traj, const uint32_t *flags, const void *ckpt,
+                   double *partG, double *partT, void *lam_out, cudaStream_t s) {
+  auto *kp = new KParams<R, D, DU>();
+  make_kparams<R, D, DU>(p, m_begin, mloc, *kp);
+  const dim3 grid((unsigned)ceil_div(mloc, TPB));
+  const R *u = static_cast<const R *>(uk);
+  const R *xd = static_cast<const R *>(p->xdk);
+  cudaError_t err = cudaSuccess;
+  if (variant == ADJ_STORED_V) {
+    const R *tr = static_cast<const R *>(traj);
+    R *lo = static_cast<R *>(lam_out);
+    if (theta)
+      adj_stored_kernel<R, D, DU, true><<<grid, TPB, 0, s>>>(*kp, u, xd, tr, flags, partG, partT, lo, mloc);
+    else
+      adj_stored_kernel<R, D, DU, false><<<grid, TPB, 0, s>>>(*kp, u, xd, tr, flags, partG, partT, lo, mloc);
+  } else {
+    const size_t smem = (size_t)seg_len<D>() * D * TPB * sizeof(R);
+    const R *ck = static_cast<const R *>(ckpt);
+    if (theta) {
+      err = cudaFuncSetAttribute(adj_recompute_kernel<R, D, DU, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (err == cudaSuccess)
+        adj_recompute_kernel<R, D, DU, true><<<grid, TPB, smem, s>>>(*kp, u, xd, ck, partG, partT, mloc);
+    } else {
+      err = cudaFuncSetAttribute(adj_recompute_kernel<R, D, DU, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (err == cudaSuccess)
+        adj_recompute_kernel<R, D, DU, false><<<grid, TPB, smem, s>>>(*kp, u, xd, ck, partG, partT, mloc);
+    }
+  }
+  delete kp;
+  count_launch();
+  if (err != cudaSuccess) return err;
+  return cudaGetLastError();
+}
+
+template <typename R, int D, int DU>
+size_t op_stack_bytes() {
+  size_t need = 2 * sizeof(JumpStep<R, D>) + 2048;
+  const void *ks[] = {
+      (const void *)fwd_kernel<R, D, DU, FWD_COST>, (const void *)fwd_kernel<R, D, DU, FWD_STORE>,
+      (const void *)fwd_kernel<R, D, DU, FWD_CKPT>, (const void *)adj_stored_kernel<R, D, DU, false>,
+      (const void *)adj_stored_kernel<R, D, DU, true>, (const void *)adj_recompute_kernel<R, D, DU, false>,
+      (const void *)adj_recompute_kernel<R, D, DU, true>};
+  for (const void *k : ks) {
+    cudaFuncAttributes a;
+    if (cudaFuncGetAttributes(&a, k) == cudaSuccess && a.localSizeBytes + 1024 > need)
+      need = a.localSizeBytes + 1024;
+  }
+  return (need + 255) & ~(size_t)255;
+}
+
+template <typename R, int D, int DU>
+constexpr PathOps make_ops() {
+  return PathOps{D, DU, seg_len<D>(), (int)sizeof(R), &op_stack_bytes<R, D, DU>, &op_fwd<R, D, DU>,
+                 &op_adj<R, D, DU>};
+}
+
+}  // namespace jd
