@@ -289,10 +289,41 @@ static jd_status dev_alloc(jd_problem *p, void **ptr, size_t bytes, const char *
   return JD_OK;
 }
 
+// Jump-log capacity per path: mean jump count lambda T plus a wide Poisson margin
+// (steps that do not fit are regenerated by the adjoint, so this only trades memory
+// for speed).
+static int log_capacity(const jd_problem_desc &q) {
+  if (q.jump_law == JD_JUMP_NONE || q.lambda <= 0.0) return 0;
+  const double mean = q.lambda * q.T;
+  double c = std::ceil(mean + 6.0 * std::sqrt(mean) + 8.0);
+  if (c > 1024.0) c = 1024.0;
+  return (int)c;
+}
+
+static size_t log_bytes(const jd_problem *p, int64_t M, int cap) {
+  return (size_t)cap * M * (2 + p->D) * elem_size(p) + (size_t)M * 4;
+}
+
 static size_t stored_bytes(const jd_problem *p) {
   const int64_t M = p->desc.M;
   const int Nt = p->desc.Nt;
-  return (size_t)((Nt + 4) / 4) * p->D * M * 4 * elem_size(p) + (size_t)ceil_div(Nt, 32) * M * 4;
+  return (size_t)((Nt + 4) / 4) * p->D * M * 4 * elem_size(p) + (size_t)ceil_div(Nt, 32) * M * 4 +
+         log_bytes(p, M, log_capacity(p->desc));
+}
+
+static PathBufs plan_bufs(const jd_problem *p) {
+  PathBufs b;
+  b.traj = p->traj;
+  b.flags = p->flags;
+  b.ckpt = p->ckpt;
+  b.log_kt = p->log_kt;
+  b.log_y = p->log_y;
+  b.jcnt = p->jcnt;
+  b.log_cap = p->log_cap;
+  b.partC = p->partC;
+  b.partG = p->partG;
+  b.partT = p->partT;
+  return b;
 }
 
 static size_t recompute_bytes(const jd_problem *p) {
@@ -312,6 +343,14 @@ static jd_status ensure_plan(jd_problem *p) {
                             "trajectory");
     if (s) return s;
     s = dev_alloc(p, (void **)&p->flags, (size_t)ceil_div(p->desc.Nt, 32) * M * 4, "jump flags");
+    if (s) return s;
+    p->log_cap = log_capacity(p->desc);
+    const size_t cap = (size_t)(p->log_cap > 0 ? p->log_cap : 1);
+    s = dev_alloc(p, &p->log_kt, cap * M * 2 * elem_size(p), "jump log");
+    if (s) return s;
+    s = dev_alloc(p, &p->log_y, cap * M * p->D * elem_size(p), "jump log states");
+    if (s) return s;
+    s = dev_alloc(p, (void **)&p->jcnt, (size_t)M * 4, "jump log counts");
     if (s) return s;
   } else {
     jd_status s = dev_alloc(p, &p->ckpt, recompute_bytes(p), "checkpoints");
@@ -367,8 +406,7 @@ static jd_status run_cost(jd_problem *p, const double *ud, int slot) {
   jd_status s = prep_u(p, ud);
   if (s) return s;
   const int pr = prof_begin(KC_FWD_COST, p->stream);
-  const cudaError_t e = p->ops->fwd(p, FWD_COST, 0, p->desc.M, p->uk, nullptr, nullptr, nullptr, p->partC,
-                                    nullptr, p->stream);
+  const cudaError_t e = p->ops->fwd(p, FWD_COST, 0, p->desc.M, p->uk, plan_bufs(p), p->stream);
   prof_end(pr, p->stream);
   JD_CUDA(e);
   return finalize_cost(p, ud, slot);
@@ -382,21 +420,20 @@ static jd_status run_gradient(jd_problem *p, const double *ud, bool theta) {
   const jd_problem_desc &q = p->desc;
   const int64_t M = q.M;
   cudaError_t e1, e2;
+  const PathBufs b = plan_bufs(p);
   if (p->plan == JD_ADJ_STORED) {
     int pr = prof_begin(KC_FWD_STORE, p->stream);
-    e1 = p->ops->fwd(p, FWD_STORE, 0, M, p->uk, p->traj, p->flags, nullptr, p->partC, nullptr, p->stream);
+    e1 = p->ops->fwd(p, FWD_STORE, 0, M, p->uk, b, p->stream);
     prof_end(pr, p->stream);
     pr = prof_begin(KC_ADJ_STORED, p->stream);
-    e2 = p->ops->adj(p, ADJ_STORED_V, theta, 0, M, p->uk, p->traj, p->flags, nullptr, p->partG, p->partT,
-                     nullptr, p->stream);
+    e2 = p->ops->adj(p, ADJ_STORED_V, theta, 0, M, p->uk, b, p->stream);
     prof_end(pr, p->stream);
   } else {
     int pr = prof_begin(KC_FWD_CKPT, p->stream);
-    e1 = p->ops->fwd(p, FWD_CKPT, 0, M, p->uk, nullptr, nullptr, p->ckpt, p->partC, nullptr, p->stream);
+    e1 = p->ops->fwd(p, FWD_CKPT, 0, M, p->uk, b, p->stream);
     prof_end(pr, p->stream);
     pr = prof_begin(KC_ADJ_RECOMPUTE, p->stream);
-    e2 = p->ops->adj(p, ADJ_RECOMPUTE_V, theta, 0, M, p->uk, nullptr, nullptr, p->ckpt, p->partG,
-                     p->partT, nullptr, p->stream);
+    e2 = p->ops->adj(p, ADJ_RECOMPUTE_V, theta, 0, M, p->uk, b, p->stream);
     prof_end(pr, p->stream);
   }
   JD_CUDA(e1);
@@ -519,6 +556,9 @@ jd_status jd_problem_destroy(jd_problem *p) {
   free_dev(p->traj);
   free_dev(p->flags);
   free_dev(p->ckpt);
+  free_dev(p->log_kt);
+  free_dev(p->log_y);
+  free_dev(p->jcnt);
   free_dev(p->opt_u);
   free_dev(p->opt_ut);
   free_dev(p->opt_g);
@@ -726,18 +766,32 @@ jd_status jd_sample_paths(jd_problem *p, const double *u, jd_memspace us, int64_
   const int64_t nb = ceil_div(count, TPB), ng = (Nt + 4) / 4;
   const size_t traj_b = (size_t)ng * D * count * 4 * es, flag_b = (size_t)ceil_div(Nt, 32) * count * 4;
   const size_t lam_b = (size_t)(Nt + 1) * D * count * es;
+  const int cap = log_capacity(q);
+  const size_t capa = (size_t)(cap > 0 ? cap : 1);
   void *traj = nullptr, *flags = nullptr, *lamd = nullptr, *pc = nullptr, *pC = nullptr, *pG = nullptr;
+  void *lkt = nullptr, *ly = nullptr, *jc = nullptr;
   cudaError_t e = cudaMalloc(&traj, traj_b);
   if (e == cudaSuccess) e = cudaMalloc(&flags, flag_b);
   if (e == cudaSuccess) e = cudaMalloc(&lamd, lam_b);
   if (e == cudaSuccess) e = cudaMalloc(&pc, count * es);
   if (e == cudaSuccess) e = cudaMalloc(&pC, nb * 8);
   if (e == cudaSuccess) e = cudaMalloc(&pG, (size_t)Nt * p->DU * nb * 8);
-  if (e == cudaSuccess)
-    e = p->ops->fwd(p, FWD_STORE, m0, count, p->uk, traj, (uint32_t *)flags, nullptr, (double *)pC, pc, p->stream);
-  if (e == cudaSuccess && lam)
-    e = p->ops->adj(p, ADJ_STORED_V, false, m0, count, p->uk, traj, (const uint32_t *)flags, nullptr,
-                    (double *)pG, nullptr, lamd, p->stream);
+  if (e == cudaSuccess) e = cudaMalloc(&lkt, capa * count * 2 * es);
+  if (e == cudaSuccess) e = cudaMalloc(&ly, capa * count * D * es);
+  if (e == cudaSuccess) e = cudaMalloc(&jc, (size_t)count * 4);
+  PathBufs b;
+  b.traj = traj;
+  b.flags = (uint32_t *)flags;
+  b.pcost = pc;
+  b.log_kt = lkt;
+  b.log_y = ly;
+  b.jcnt = (int *)jc;
+  b.log_cap = cap;
+  b.partC = (double *)pC;
+  b.partG = (double *)pG;
+  b.lam_out = lamd;
+  if (e == cudaSuccess) e = p->ops->fwd(p, FWD_STORE, m0, count, p->uk, b, p->stream);
+  if (e == cudaSuccess && lam) e = p->ops->adj(p, ADJ_STORED_V, false, m0, count, p->uk, b, p->stream);
   std::vector<unsigned char> ht, hl, hc;
   if (e == cudaSuccess) {
     ht.resize(traj_b);
@@ -756,6 +810,9 @@ jd_status jd_sample_paths(jd_problem *p, const double *u, jd_memspace us, int64_
   cudaFree(pc);
   cudaFree(pC);
   cudaFree(pG);
+  cudaFree(lkt);
+  cudaFree(ly);
+  cudaFree(jc);
   if (e != cudaSuccess) return cuda_fail(e, "jd_sample_paths");
   auto rd = [&](const std::vector<unsigned char> &v, size_t idx) -> double {
     if (es == 8) return reinterpret_cast<const double *>(v.data())[idx];

@@ -27,13 +27,13 @@ __device__ __forceinline__ uint4 philox10(uint32_t c0, uint32_t c1, uint32_t c2,
                                           uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
-    const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
-    const uint32_t y0 = hi1 ^ c1 ^ k0, y2 = hi0 ^ c3 ^ k1;
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c0;   // one wide multiply
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c2;
+    const uint32_t y0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0, y2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
     c0 = y0;
-    c1 = lo1;
+    c1 = (uint32_t)p1;
     c2 = y2;
-    c3 = lo0;
+    c3 = (uint32_t)p0;
     k0 += 0x9E3779B9u;
     k1 += 0xBB67AE85u;
   }
@@ -314,6 +314,7 @@ template <typename R, int D>
 struct JumpStep {
   int n;
   int order[NMAX];        // slot (0-based) of the i-th jump in time order
+  R th[NMAX];             // sorted jump-time fractions
   R delta[NMAX + 1];
   R Y[NMAX + 2][D];       // Y[i] = start of sub-step i, Y[n+1] = X_{k+1}
 };
@@ -365,6 +366,55 @@ __device__ __forceinline__ void slot_draws(const KParams<R, D, DU> &kp, int k, u
   }
 }
 
+// Draws of jump slot 0 for a step with exactly one jump, with the word layout known at
+// compile time (valid when kp.npair == ceil(D/2)): time fraction, unit size, and the
+// normals of the sub-step after the jump.  Same values as slot_draws(kp, k, m, 0, ..).
+template <typename R, int D, int DU>
+__device__ __forceinline__ R slot0_draws(const KParams<R, D, DU> &kp, int k, uint32_t m, R (&xih)[D],
+                                         R (&z)[D]) {
+  using M = Ar<R>;
+  constexpr int PD = MainWords<D>::PD;
+  constexpr int NB = (1 + 4 * PD + 3) / 4;
+  uint32_t w[4 * NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const uint4 o = philox10((uint32_t)k, m, (1u << 24) | (1u << 16) | (uint32_t)b, kp.epoch, kp.key0, kp.key1);
+    w[4 * b] = o.x;
+    w[4 * b + 1] = o.y;
+    w[4 * b + 2] = o.z;
+    w[4 * b + 3] = o.w;
+  }
+  const int d = kp.d;
+#pragma unroll
+  for (int p = 0; p < PD; ++p) {
+    R a, b;
+    if (kp.jump_law == JD_JUMP_UNIFORM) {
+      a = M::sub(M::mul(R(2), M::u01(w[1 + 2 * p])), R(1));
+      b = M::sub(M::mul(R(2), M::u01(w[2 + 2 * p])), R(1));
+    } else {
+      normal_pair<R>(w[1 + 2 * p], w[2 + 2 * p], a, b);
+    }
+    xih[2 * p] = 2 * p < d ? a : R(0);
+    if (2 * p + 1 < D) xih[2 * p + 1] = 2 * p + 1 < d ? b : R(0);
+    normal_pair<R>(w[1 + 2 * PD + 2 * p], w[2 + 2 * PD + 2 * p], a, b);
+    z[2 * p] = 2 * p < d ? a : R(0);
+    if (2 * p + 1 < D) z[2 * p + 1] = 2 * p + 1 < d ? b : R(0);
+  }
+  return M::u01(w[0]);
+}
+
+// One Euler sub-step y <- y + de f(y, u) + sigma sqrt(de) z (the form every jump path uses).
+template <typename R, int D, int DU>
+__device__ __forceinline__ void euler_substep(const KParams<R, D, DU> &kp, R de, const R (&z)[D],
+                                              const R (&u)[DU], R (&y)[D]) {
+  using M = Ar<R>;
+  R f[D];
+  drift(kp, y, u, f);
+  const R sq = M::sqrt(de);
+#pragma unroll
+  for (int c = 0; c < D; ++c) y[c] = M::fma(M::mul(kp.sigma[c], sq), z[c], M::fma(de, f[c], y[c]));
+}
+
 // Plan and integrate a step that has jumps (Algorithm 5.1 with the additive jump
 // map): Poisson count from w0, jump times (word 0 of every slot) sorted stably,
 // sub-step lengths, then the Euler sub-steps from x with the jump of slot order[i]
@@ -408,11 +458,12 @@ __device__ __noinline__ void build_jump_step(const KParams<R, D, DU> &kp, int k,
     }
     S->order[j + 1] = cur;
   }
-  S->delta[0] = M::mul(kp.dt, theta[S->order[0]]);
 #pragma unroll 1
-  for (int i = 1; i < n; ++i)
-    S->delta[i] = M::mul(kp.dt, M::sub(theta[S->order[i]], theta[S->order[i - 1]]));
-  S->delta[n] = M::mul(kp.dt, M::sub(R(1), theta[S->order[n - 1]]));
+  for (int i = 0; i < n; ++i) S->th[i] = theta[S->order[i]];
+  S->delta[0] = M::mul(kp.dt, S->th[0]);
+#pragma unroll 1
+  for (int i = 1; i < n; ++i) S->delta[i] = M::mul(kp.dt, M::sub(S->th[i], S->th[i - 1]));
+  S->delta[n] = M::mul(kp.dt, M::sub(R(1), S->th[n - 1]));
   R uu[DU], y[D], z[D];
 #pragma unroll
   for (int l = 0; l < DU; ++l) uu[l] = u[l];

@@ -35,21 +35,32 @@ struct KParams {
   int64_t m_begin;                // global index of path 0 of this launch
 };
 
+// Device buffers of one launch (unused ones are null).
+struct PathBufs {
+  void *traj = nullptr;        // stored states
+  uint32_t *flags = nullptr;   // jump flags, 1 bit per path-step
+  void *ckpt = nullptr;        // checkpoints (recompute variant)
+  void *pcost = nullptr;       // per-path cost (optional)
+  void *log_kt = nullptr;      // jump log: (step, time fraction) per record
+  void *log_y = nullptr;       // jump log: post-jump states
+  int *jcnt = nullptr;         // jump log: records per path
+  int log_cap = 0;             // jump log: records per path capacity
+  double *partC = nullptr, *partG = nullptr, *partT = nullptr;
+  void *lam_out = nullptr;     // adjoint states (optional)
+};
+
 // Per-instantiation launch table (one entry per precision x compiled dimension).
 struct PathOps {
   int D, DU, S, elem;
   // per-thread stack bytes the kernels of this instantiation may need (the jump path
   // keeps its sub-step states in local memory behind a non-inlined call)
   size_t (*stack_bytes)();
-  // forward sweep: cost partials per block; optional trajectory / checkpoint stores
+  // forward sweep in mode FWD_COST / FWD_STORE / FWD_CKPT
   cudaError_t (*fwd)(const struct ::jd_problem *p, int mode, int64_t m_begin, int64_t mloc,
-                     const void *uk, void *traj, uint32_t *flags, void *ckpt, double *partC,
-                     void *pcost, cudaStream_t s);
+                     const void *uk, const PathBufs &b, cudaStream_t s);
   // adjoint sweep: per-step gradient partials [Nt][DU][nblk]; theta partials [D+2][nblk]
   cudaError_t (*adj)(const struct ::jd_problem *p, int variant, bool theta, int64_t m_begin,
-                     int64_t mloc, const void *uk, const void *traj, const uint32_t *flags,
-                     const void *ckpt, double *partG, double *partT, void *lam_out,
-                     cudaStream_t s);
+                     int64_t mloc, const void *uk, const PathBufs &b, cudaStream_t s);
 };
 
 const PathOps *path_ops_dims(int prec, int D, int DU);
@@ -82,6 +93,9 @@ struct jd_problem {
   void *traj = nullptr;
   uint32_t *flags = nullptr;
   void *ckpt = nullptr;
+  void *log_kt = nullptr, *log_y = nullptr;
+  int *jcnt = nullptr;
+  int log_cap = 0;
   double *opt_u = nullptr, *opt_ut = nullptr, *opt_g = nullptr;
   double *host_pinned = nullptr;  // small pinned staging buffer
   size_t bytes = 0;

@@ -20,6 +20,8 @@
 //   partT [D+2][nblk]                     FP64 block sums of the parameter sensitivities
 #pragma once
 
+#include <type_traits>
+
 #include "jd_device.cuh"
 
 namespace jd {
@@ -49,11 +51,79 @@ struct Vec4<double> {
   }
 };
 
-// One uniform step k from x (in place).  Returns true when the step had jumps.
-template <typename R, int D, int DU>
-__device__ __forceinline__ bool forward_step(const KParams<R, D, DU> &kp, int k, uint32_t m,
-                                             const R *__restrict__ u, R (&x)[D]) {
+// ---------------------------------------------------------------------------
+// Jump log: for every step with jumps, the post-jump sub-states of the jump-adapted
+// grid in time order (one record per jump: step index k, time fraction theta, state
+// Y right after the jump).  A step is logged only when all its records fit, so a
+// backward sweep that finds record k == step k has the step's whole sub-grid; any
+// other jump step is regenerated from the counter-based streams.
+//   kt[r * stride + idx] = (k, theta),   y[(r * D + c) * stride + idx] = Y_c
+// ---------------------------------------------------------------------------
+template <typename R>
+struct V2;
+template <>
+struct V2<float> {
+  using T = float2;
+  static __device__ __forceinline__ T make(float a, float b) { return make_float2(a, b); }
+};
+template <>
+struct V2<double> {
+  using T = double2;
+  static __device__ __forceinline__ T make(double a, double b) { return make_double2(a, b); }
+};
+
+template <typename R, int D>
+struct JLog {
+  typename V2<R>::T *kt;
+  R *y;
+  int64_t stride;   // mloc (global log) or TPB (shared log)
+  int cap;          // records per path
+};
+
+template <typename R, int D>
+struct LogWriter {
+  JLog<R, D> L;
+  int64_t idx;
+  int r = 0;
+  __device__ __forceinline__ bool fits(int n) const { return r + n <= L.cap; }
+  __device__ __forceinline__ void put(int k, R theta, const R (&y)[D]) {
+    L.kt[(int64_t)r * L.stride + idx] = V2<R>::make((R)k, theta);
+#pragma unroll
+    for (int c = 0; c < D; ++c) L.y[((int64_t)r * D + c) * L.stride + idx] = y[c];
+    ++r;
+  }
+};
+
+template <typename R, int D>
+struct LogReader {
+  JLog<R, D> L;
+  int64_t idx;
+  int rec;   // latest unconsumed record, -1 when empty
+  R rk;      // its step index (or -1)
+  __device__ __forceinline__ void init(int count) {
+    rec = count - 1;
+    rk = rec >= 0 ? L.kt[(int64_t)rec * L.stride + idx].x : R(-1);
+  }
+  __device__ __forceinline__ bool has(int k) const { return rk == (R)k; }
+  __device__ __forceinline__ void pop(R &theta, R (&y)[D]) {
+    theta = L.kt[(int64_t)rec * L.stride + idx].y;
+#pragma unroll
+    for (int c = 0; c < D; ++c) y[c] = L.y[((int64_t)rec * D + c) * L.stride + idx];
+    --rec;
+    rk = rec >= 0 ? L.kt[(int64_t)rec * L.stride + idx].x : R(-1);
+  }
+};
+
+struct NoLog {};
+
+// One uniform step k from x (in place); returns the number of jumps.  Steps with one
+// jump take an inline path (the common case); two or more go through
+// build_jump_step.  With a LogWriter the post-jump states of the step are recorded.
+template <typename R, int D, int DU, typename LW>
+__device__ __forceinline__ int forward_step(const KParams<R, D, DU> &kp, int k, uint32_t m,
+                                            const R *__restrict__ u, R (&x)[D], LW &lw) {
   using M = Ar<R>;
+  constexpr bool LOG = !std::is_same<LW, NoLog>::value;
   R z[D];
   const uint32_t w0 = main_draws(kp, k, m, z);
   R uk[DU];
@@ -64,7 +134,19 @@ __device__ __forceinline__ bool forward_step(const KParams<R, D, DU> &kp, int k,
     drift(kp, x, uk, f);
 #pragma unroll
     for (int c = 0; c < D; ++c) x[c] = M::fma(kp.sig_sqdt[c], z[c], M::fma(kp.dt, f[c], x[c]));
-    return false;
+    return 0;
+  }
+  if (kp.npair == MainWords<D>::PD && (unsigned long long)w0 < kp.thr[1]) {
+    R xih[D], z1[D];
+    const R th = slot0_draws(kp, k, m, xih, z1);
+    euler_substep(kp, M::mul(kp.dt, th), z, uk, x);
+#pragma unroll
+    for (int c = 0; c < D; ++c) x[c] = M::add(x[c], M::mul(kp.jump_scale, xih[c]));
+    if constexpr (LOG) {
+      if (lw.fits(1)) lw.put(k, th, x);
+    }
+    euler_substep(kp, M::mul(kp.dt, M::sub(R(1), th)), z1, uk, x);
+    return 1;
   }
   JumpStep<R, D> S;
   R xl[D];
@@ -73,7 +155,17 @@ __device__ __forceinline__ bool forward_step(const KParams<R, D, DU> &kp, int k,
   build_jump_step(kp, k, m, w0, z, uk, xl, &S);
 #pragma unroll
   for (int c = 0; c < D; ++c) x[c] = S.Y[S.n + 1][c];
-  return true;
+  if constexpr (LOG) {
+    if (lw.fits(S.n)) {
+      for (int i = 0; i < S.n; ++i) {
+        R y[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) y[c] = S.Y[i + 1][c];
+        lw.put(k, S.th[i], y);
+      }
+    }
+  }
+  return S.n;
 }
 
 // dt l(x, t_k) = sum_c (q_c dt / 2) (x_c - xd_c(t_k))^2
@@ -158,15 +250,34 @@ __device__ __noinline__ void jump_backward(const KParams<R, D, DU> &kp, int k, u
 }
 
 // Backward through step k from the state X_k; g receives the step's contribution.
-template <typename R, int D, int DU, bool THETA>
+// Jump steps use the log when it holds the step (u-gradient only), else regenerate.
+template <typename R, int D, int DU, bool THETA, typename LR>
 __device__ __forceinline__ void backward_step(const KParams<R, D, DU> &kp, int k, uint32_t m,
                                               bool jumped, const R (&xk)[D],
                                               const R *__restrict__ u, const R *__restrict__ xd,
-                                              R (&mu)[D], R (&g)[DU], R (&th)[D + 2]) {
+                                              R (&mu)[D], R (&g)[DU], R (&th)[D + 2], LR &lr) {
   using M = Ar<R>;
 #pragma unroll
   for (int l = 0; l < DU; ++l) g[l] = R(0);
-  if (jumped) {
+  if (jumped && !THETA && lr.has(k)) {
+    // sub-steps n..1 from the logged post-jump states, then sub-step 0 from X_k
+    R thn = R(1);
+    while (lr.has(k)) {
+      R the, y[D];
+      lr.pop(the, y);
+      const R de = M::mul(kp.dt, M::sub(thn, the));
+      control_sensitivity(kp, mu, de, g);
+      adjoint_update(kp, y, de, mu);
+      thn = the;
+    }
+    const R de0 = M::mul(kp.dt, thn);
+    control_sensitivity(kp, mu, de0, g);
+    adjoint_update(kp, xk, de0, mu);
+  } else if (jumped) {
+    while (lr.has(k)) {   // THETA: the log is not used, but stay in step with it
+      R the, y[D];
+      lr.pop(the, y);
+    }
     R xl[D], ml[D], gl[DU], tl[D + 2], ul[DU];
 #pragma unroll
     for (int c = 0; c < D; ++c) { xl[c] = xk[c]; ml[c] = mu[c]; }
@@ -212,7 +323,7 @@ __global__ void __launch_bounds__(TPB)
 fwd_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u,
            const R *__restrict__ xd, double *__restrict__ partC, R *__restrict__ traj,
            uint32_t *__restrict__ flags, R *__restrict__ ckpt, R *__restrict__ pcost,
-           int64_t mloc) {
+           JLog<R, D> jl, int *__restrict__ jcnt, int64_t mloc) {
   __shared__ Pair<R> red[TPB / 32];
   const int64_t lm = (int64_t)blockIdx.x * TPB + threadIdx.x;
   const bool active = lm < mloc;
@@ -223,6 +334,13 @@ fwd_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u
   for (int c = 0; c < D; ++c) x[c] = kp.x0[c];
   Kahan<R> cost;
   uint32_t fw = 0;
+  using LW = typename std::conditional<MODE == FWD_STORE, LogWriter<R, D>, NoLog>::type;
+  LW lw;
+  if constexpr (MODE == FWD_STORE) {
+    lw.L = jl;
+    lw.idx = lm;
+    if (!active) lw.L.cap = 0;   // inactive threads log nothing
+  }
   const int ng = (Nt + 4) / 4;
 #pragma unroll 1
   for (int g = 0; g < ng; ++g) {
@@ -239,7 +357,7 @@ fwd_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u
 #pragma unroll
           for (int c = 0; c < D; ++c) ckpt[((size_t)(k / kp.S) * D + c) * mloc + lm] = x[c];
         }
-        if (forward_step(kp, k, m, u, x)) fw |= 1u << (k & 31);
+        if (forward_step(kp, k, m, u, x, lw)) fw |= 1u << (k & 31);
         cost.add(cost_term(kp, x, xd + (size_t)(k + 1) * D));
         if (MODE == FWD_STORE && ((k & 31) == 31 || k == Nt - 1)) {
           if (active) flags[(size_t)(k >> 5) * mloc + lm] = fw;
@@ -253,6 +371,9 @@ fwd_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u
         Vec4<R>::store(traj + (((size_t)g * D + c) * mloc + lm) * 4, buf[0][c], buf[1][c], buf[2][c],
                        buf[3][c]);
     }
+  }
+  if constexpr (MODE == FWD_STORE) {
+    if (active) jcnt[lm] = lw.r;
   }
   if (MODE == FWD_CKPT && active) {
     const int nseg = (Nt + kp.S - 1) / kp.S;
@@ -295,8 +416,9 @@ template <typename R, int D, int DU, bool THETA>
 __global__ void __launch_bounds__(TPB)
 adj_stored_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u,
                   const R *__restrict__ xd, const R *__restrict__ traj,
-                  const uint32_t *__restrict__ flags, double *__restrict__ partG,
-                  double *__restrict__ partT, R *__restrict__ lam_out, int64_t mloc) {
+                  const uint32_t *__restrict__ flags, JLog<R, D> jl, const int *__restrict__ jcnt,
+                  double *__restrict__ partG, double *__restrict__ partT, R *__restrict__ lam_out,
+                  int64_t mloc) {
   using M = Ar<R>;
   __shared__ Pair<R> red[2 * (TPB / 32) * BATCH * DU];
   __shared__ Pair<R> red1[TPB / 32];
@@ -307,6 +429,10 @@ adj_stored_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restr
   const int64_t lmc = active ? lm : 0;
   const uint32_t m = (uint32_t)(kp.m_begin + lmc);
   const int Nt = kp.Nt;
+  LogReader<R, D> lr;
+  lr.L = jl;
+  lr.idx = lmc;
+  lr.init(min(__ldg(jcnt + lmc), jl.cap));
   R mu[D], th[D + 2];
 #pragma unroll
   for (int t = 0; t < D + 2; ++t) th[t] = R(0);
@@ -320,10 +446,10 @@ adj_stored_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restr
       for (int c = 0; c < D; ++c) lam_out[((size_t)Nt * D + c) * mloc + lm] = mu[c];
   }
   const int nbatch = (Nt + BATCH - 1) / BATCH;
+  const int ng = (Nt + 4) / 4;   // groups of 4 stored states
 #pragma unroll 1
   for (int b = nbatch - 1; b >= 0; --b) {
     R xs[BATCH][D];
-    const int ng = (Nt + 4) / 4;   // groups of 4 stored states
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int g = 2 * b + h;
@@ -351,7 +477,7 @@ adj_stored_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restr
 #pragma unroll
       for (int l = 0; l < DU; ++l) g[l] = R(0);
       if (k < Nt) {
-        backward_step<R, D, DU, THETA>(kp, k, m, (fw >> (k & 31)) & 1u, xs[j], u, xd, mu, g, th);
+        backward_step<R, D, DU, THETA>(kp, k, m, (fw >> (k & 31)) & 1u, xs[j], u, xd, mu, g, th, lr);
         if (lam_out && active)
 #pragma unroll
           for (int c = 0; c < D; ++c) lam_out[((size_t)k * D + c) * mloc + lm] = mu[c];
@@ -364,22 +490,32 @@ adj_stored_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restr
   finish_theta<R, D, DU, THETA>(kp, th, active, partT, red1);
 }
 
+template <int D>
+constexpr int seg_log_cap() {
+  return D <= 2 ? 8 : 4;
+}
+
 template <typename R, int D, int DU, bool THETA>
 __global__ void __launch_bounds__(TPB)
 adj_recompute_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u,
                      const R *__restrict__ xd, const R *__restrict__ ckpt,
                      double *__restrict__ partG, double *__restrict__ partT, int64_t mloc) {
   using M = Ar<R>;
+  constexpr int JS = seg_log_cap<D>();
   extern __shared__ __align__(16) unsigned char dsm[];
-  R *sbuf = reinterpret_cast<R *>(dsm);   // [S * D][TPB]
+  R *sbuf = reinterpret_cast<R *>(dsm);   // [S * D][TPB] segment states
+  const int S = kp.S;
+  auto *skt = reinterpret_cast<typename V2<R>::T *>(sbuf + (size_t)S * D * TPB);   // [JS][TPB]
+  R *sy = reinterpret_cast<R *>(skt + JS * TPB);                                    // [JS * D][TPB]
   __shared__ Pair<R> red[2 * (TPB / 32) * BATCH * DU];
   __shared__ Pair<R> red1[TPB / 32];
   const int64_t lm = (int64_t)blockIdx.x * TPB + threadIdx.x;
   const bool active = lm < mloc;
   const int64_t lmc = active ? lm : 0;   // inactive threads replay path 0
   const uint32_t m = (uint32_t)(kp.m_begin + lmc);
-  const int Nt = kp.Nt, S = kp.S, tid = threadIdx.x;
+  const int Nt = kp.Nt, tid = threadIdx.x;
   const int nseg = (Nt + S - 1) / S;
+  const JLog<R, D> sl{skt, sy, TPB, JS};
   R mu[D], th[D + 2];
 #pragma unroll
   for (int t = 0; t < D + 2; ++t) th[t] = R(0);
@@ -396,12 +532,19 @@ adj_recompute_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__re
 #pragma unroll
     for (int c = 0; c < D; ++c) x[c] = __ldg(ckpt + ((size_t)seg * D + c) * mloc + lmc);
     uint32_t jm = 0;
+    LogWriter<R, D> lw;
+    lw.L = sl;
+    lw.idx = tid;
 #pragma unroll 1
     for (int i = 0; i < len; ++i) {
 #pragma unroll
       for (int c = 0; c < D; ++c) sbuf[(i * D + c) * TPB + tid] = x[c];
-      if (forward_step(kp, k0 + i, m, u, x)) jm |= 1u << i;
+      if (forward_step(kp, k0 + i, m, u, x, lw)) jm |= 1u << i;
     }
+    LogReader<R, D> lr;
+    lr.L = sl;
+    lr.idx = tid;
+    lr.init(lw.r);
     const int nb = (len + BATCH - 1) / BATCH;
 #pragma unroll 1
     for (int bb = nb - 1; bb >= 0; --bb) {
@@ -416,7 +559,7 @@ adj_recompute_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__re
           R xk[D];
 #pragma unroll
           for (int c = 0; c < D; ++c) xk[c] = sbuf[(i * D + c) * TPB + tid];
-          backward_step<R, D, DU, THETA>(kp, k, m, (jm >> i) & 1u, xk, u, xd, mu, g, th);
+          backward_step<R, D, DU, THETA>(kp, k, m, (jm >> i) & 1u, xk, u, xd, mu, g, th, lr);
         }
 #pragma unroll
         for (int l = 0; l < DU; ++l) gb[j][l] = {active ? g[l] : R(0), R(0)};
@@ -495,25 +638,26 @@ void make_kparams(const jd_problem *p, int64_t m_begin, int64_t mloc, KParams<R,
 
 template <typename R, int D, int DU>
 cudaError_t op_fwd(const jd_problem *p, int mode, int64_t m_begin, int64_t mloc, const void *uk,
-                   void *traj, uint32_t *flags, void *ckpt, double *partC, void *pcost,
-                   cudaStream_t s) {
+                   const PathBufs &b, cudaStream_t s) {
   auto *kp = new KParams<R, D, DU>();
   make_kparams<R, D, DU>(p, m_begin, mloc, *kp);
   const dim3 grid((unsigned)ceil_div(mloc, TPB));
   const R *u = static_cast<const R *>(uk);
   const R *xd = static_cast<const R *>(p->xdk);
-  R *pc = static_cast<R *>(pcost);
+  R *pc = static_cast<R *>(b.pcost);
+  const JLog<R, D> jl{static_cast<typename V2<R>::T *>(b.log_kt), static_cast<R *>(b.log_y), mloc, b.log_cap};
   switch (mode) {
     case FWD_COST:
-      fwd_kernel<R, D, DU, FWD_COST><<<grid, TPB, 0, s>>>(*kp, u, xd, partC, nullptr, nullptr, nullptr, pc, mloc);
+      fwd_kernel<R, D, DU, FWD_COST><<<grid, TPB, 0, s>>>(*kp, u, xd, b.partC, nullptr, nullptr, nullptr, pc,
+                                                          jl, nullptr, mloc);
       break;
     case FWD_STORE:
-      fwd_kernel<R, D, DU, FWD_STORE><<<grid, TPB, 0, s>>>(*kp, u, xd, partC, static_cast<R *>(traj), flags,
-                                                           nullptr, pc, mloc);
+      fwd_kernel<R, D, DU, FWD_STORE><<<grid, TPB, 0, s>>>(*kp, u, xd, b.partC, static_cast<R *>(b.traj),
+                                                           b.flags, nullptr, pc, jl, b.jcnt, mloc);
       break;
     default:
-      fwd_kernel<R, D, DU, FWD_CKPT><<<grid, TPB, 0, s>>>(*kp, u, xd, partC, nullptr, nullptr,
-                                                          static_cast<R *>(ckpt), pc, mloc);
+      fwd_kernel<R, D, DU, FWD_CKPT><<<grid, TPB, 0, s>>>(*kp, u, xd, b.partC, nullptr, nullptr,
+                                                          static_cast<R *>(b.ckpt), pc, jl, nullptr, mloc);
       break;
   }
   delete kp;
@@ -521,10 +665,14 @@ cudaError_t op_fwd(const jd_problem *p, int mode, int64_t m_begin, int64_t mloc,
   return cudaGetLastError();
 }
 
+template <typename R, int D>
+constexpr size_t recompute_smem() {
+  return (size_t)seg_len<D>() * D * TPB * sizeof(R) + (size_t)seg_log_cap<D>() * (2 + D) * TPB * sizeof(R);
+}
+
 template <typename R, int D, int DU>
 cudaError_t op_adj(const jd_problem *p, int variant, bool theta, int64_t m_begin, int64_t mloc,
-                   const void *uk, const void *traj, const uint32_t *flags, const void *ckpt,
-                   double *partG, double *partT, void *lam_out, cudaStream_t s) {
+                   const void *uk, const PathBufs &b, cudaStream_t s) {
   auto *kp = new KParams<R, D, DU>();
   make_kparams<R, D, DU>(p, m_begin, mloc, *kp);
   const dim3 grid((unsigned)ceil_div(mloc, TPB));
@@ -532,25 +680,28 @@ cudaError_t op_adj(const jd_problem *p, int variant, bool theta, int64_t m_begin
   const R *xd = static_cast<const R *>(p->xdk);
   cudaError_t err = cudaSuccess;
   if (variant == ADJ_STORED_V) {
-    const R *tr = static_cast<const R *>(traj);
-    R *lo = static_cast<R *>(lam_out);
+    const R *tr = static_cast<const R *>(b.traj);
+    R *lo = static_cast<R *>(b.lam_out);
+    const JLog<R, D> jl{static_cast<typename V2<R>::T *>(b.log_kt), static_cast<R *>(b.log_y), mloc, b.log_cap};
     if (theta)
-      adj_stored_kernel<R, D, DU, true><<<grid, TPB, 0, s>>>(*kp, u, xd, tr, flags, partG, partT, lo, mloc);
+      adj_stored_kernel<R, D, DU, true><<<grid, TPB, 0, s>>>(*kp, u, xd, tr, b.flags, jl, b.jcnt, b.partG,
+                                                             b.partT, lo, mloc);
     else
-      adj_stored_kernel<R, D, DU, false><<<grid, TPB, 0, s>>>(*kp, u, xd, tr, flags, partG, partT, lo, mloc);
+      adj_stored_kernel<R, D, DU, false><<<grid, TPB, 0, s>>>(*kp, u, xd, tr, b.flags, jl, b.jcnt, b.partG,
+                                                              b.partT, lo, mloc);
   } else {
-    const size_t smem = (size_t)seg_len<D>() * D * TPB * sizeof(R);
-    const R *ck = static_cast<const R *>(ckpt);
+    const size_t smem = recompute_smem<R, D>();
+    const R *ck = static_cast<const R *>(b.ckpt);
     if (theta) {
       err = cudaFuncSetAttribute(adj_recompute_kernel<R, D, DU, true>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (err == cudaSuccess)
-        adj_recompute_kernel<R, D, DU, true><<<grid, TPB, smem, s>>>(*kp, u, xd, ck, partG, partT, mloc);
+        adj_recompute_kernel<R, D, DU, true><<<grid, TPB, smem, s>>>(*kp, u, xd, ck, b.partG, b.partT, mloc);
     } else {
       err = cudaFuncSetAttribute(adj_recompute_kernel<R, D, DU, false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (err == cudaSuccess)
-        adj_recompute_kernel<R, D, DU, false><<<grid, TPB, smem, s>>>(*kp, u, xd, ck, partG, partT, mloc);
+        adj_recompute_kernel<R, D, DU, false><<<grid, TPB, smem, s>>>(*kp, u, xd, ck, b.partG, b.partT, mloc);
     }
   }
   delete kp;
