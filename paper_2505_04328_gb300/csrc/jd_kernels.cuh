@@ -491,7 +491,7 @@ adj_stored_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restr
 }
 
 template <int D>
-constexpr int seg_log_cap() {
+__host__ __device__ constexpr int seg_log_cap() {
   return D <= 2 ? 8 : 4;
 }
 
