@@ -192,6 +192,34 @@ typedef struct {
 void jd_profile_enable(int on);
 int jd_profile_read(jd_kernel_stat *out, int max_entries);
 
+/* J(u) for callers that cannot allocate device memory once they are running: a
+ * real-time control loop (cudaMalloc can take milliseconds and synchronizes the
+ * device) or an application whose memory pool owns the whole GPU.  The paper has no
+ * counterpart; this is a deployment variant of jd_cost.
+ *
+ * It runs the same forward cost kernel as jd_cost, but allocates nothing, on the
+ * device or on the host: its scratch is one fixed 4 MiB file-scope device array that
+ * every GPU loading this library holds until the process exits.
+ *   desc   problem descriptor (host arrays, read during the call; xd is copied into
+ *          the scratch); d <= 2, du == 1, FP32 or FP64; mode, mem_budget_bytes and
+ *          use_tensor_cores are ignored (use_tensor_cores must be 0)
+ *   u      device pointer, Nt doubles
+ *   J      device pointer, one double, written in stream order on desc->cuda_stream
+ *          (NULL = the legacy default stream); the call does not synchronize
+ * The scratch holds the FP64 target, the padded target and control in kernel
+ * precision and one FP64 partial per 128 paths; a problem whose total exceeds 4 MiB
+ * is rejected with JD_ERR_OOM (for d = 2, Nt = 1000 in FP32 that allows M up to
+ * about 3.9 million paths).  Every entry read is written earlier in the same call,
+ * so nothing needs clearing between calls.  All calls on a device share the one
+ * array: calls that overlap on the GPU (other streams, other host threads) race and
+ * must be serialized by the caller.  The first call on each device takes the array's
+ * device address with cudaGetSymbolAddress (with that device current); make that
+ * first call before any stream capture.  Errors are reported by status only
+ * (jd_last_error is not updated, since that would allocate): INVALID_ARG,
+ * UNSUPPORTED (d > 2, du != 1, or a per-thread stack limit below 1 KiB), OOM (beyond
+ * the scratch), CUDA. */
+jd_status jd_cost_noalloc(const jd_problem_desc *desc, const double *u, double *J);
+
 const char *jd_status_string(jd_status s);
 const char *jd_last_error(void);
 

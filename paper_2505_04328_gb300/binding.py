@@ -28,7 +28,7 @@ JD_MEM_HOST, JD_MEM_DEVICE = 0, 1
 ABI_SYMBOLS = (
     "jd_problem_create", "jd_problem_destroy", "jd_cost", "jd_gradient", "jd_sample_paths",
     "jd_optimize", "jd_problem_info", "jd_kernel_launch_count", "jd_profile_enable",
-    "jd_profile_read", "jd_status_string", "jd_last_error",
+    "jd_profile_read", "jd_cost_noalloc", "jd_status_string", "jd_last_error",
 )
 
 
@@ -93,6 +93,7 @@ def lib():
         L.jd_sample_paths.argtypes = [vp, dp, ctypes.c_int, i64, i64, dp, dp, dp]
         L.jd_optimize.argtypes = [vp, dp, ctypes.c_int, P(OptParams), P(OptResult), dp]
         L.jd_problem_info.argtypes = [vp, P(ctypes.c_size_t), P(ctypes.c_int)]
+        L.jd_cost_noalloc.argtypes = [P(ProblemDesc), dp, dp]
         L.jd_kernel_launch_count.restype = ctypes.c_uint64
         L.jd_profile_enable.argtypes = [ctypes.c_int]
         L.jd_profile_enable.restype = None
