@@ -197,17 +197,11 @@ def run_ours(args):
     prob = jd.JdProblem(p, prec="fp32", mode=args.variant, stream=stream)
     n = Nt * du
     u = torch.zeros(n, dtype=torch.float64, device="cuda")
-    g = torch.empty(n, dtype=torch.float64, device="cuda")
-    state = {"zeta": 1.0}
 
-    def step(u_t):
-        # one optimizer iteration through the C ABI on device-resident u
-        _, r, _ = prob_optimize_device(prob, u_t, state["zeta"])
-        state["zeta"] = min(2 * r["zeta"], 1e3)
-        return r
-
-    for _ in range(args.warmup):
-        step(u)
+    # warm-up iterations, then K timed iterations of one jd_optimize call on the
+    # device-resident control (the optimizer state zeta carries over)
+    r = optimize_device(prob, u, args.warmup, 1.0)
+    zeta = min(2 * r["zeta"], 1e3)
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
@@ -219,10 +213,7 @@ def run_ours(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     ev0.record(stream)
-    evals = 0
-    for _ in range(args.steps):
-        r = step(u)
-        evals += r["evals"]
+    r = optimize_device(prob, u, args.steps, zeta)
     ev1.record(stream)
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
@@ -230,26 +221,30 @@ def run_ours(args):
     kstats = jd.profile_read()
     jd.profile_enable(False)
     clk = clocks.stop()
+    evals = r["evals"]
     if dist is not None:
         ms = max_over_ranks(dist, ms, device="cuda")
     ms_per_step = ms / args.steps
     value = ws * M * Nt / (ms_per_step * 1e-3)
 
-    # end to end through the public API with host buffers: per step the control goes
-    # host -> device, the iteration runs, the new control and J come back to the host
+    # end to end through the public API with host buffers: the control goes host ->
+    # device, K iterations run (each reads its cost and Armijo decision back to the
+    # host), and the new control comes back
     u_host = u.cpu().numpy().reshape(Nt, du).copy()
-    zeta = state["zeta"]
+    zeta = min(2 * r["zeta"], 1e3)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        u_host, r, _ = prob.optimize(u_host, max_iter=1, tol_rel_grad=0.0, zeta0=zeta)
-        zeta = min(2 * r["zeta"], 1e3)
+    u_host, r2, _ = prob.optimize(u_host, max_iter=args.steps, tol_rel_grad=0.0, zeta0=zeta)
     e2e_sec = (time.perf_counter() - t0) / args.steps
+    trials = (r2["evals"] - args.steps) / args.steps
     e2e = {"value": ws * M * Nt / e2e_sec, "unit": UNIT,
-           "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8 + 8}
+           "h2d_bytes_per_step": n * 8 / args.steps,
+           "d2h_bytes_per_step": n * 8 / args.steps + 64 * (1 + trials)}
 
     peaks, peak_kind = _peaks()
-    roofline = roofline_line(kstats, p, args, peaks, peak_kind)
+    rl = {k: kernel_roofline(k, v, p, peaks, peak_kind) for k, v in kstats.items()
+          if k in ALGO}
+    dom = max(rl, key=lambda k: kstats[k][1]) if rl else None
 
     if rank == 0:
         line = {
@@ -259,11 +254,14 @@ def run_ours(args):
             "config": {"workload": f"double_well d=2 M=2^{int(math.log2(M))} Nt={Nt}",
                        "variant": prob.info()["mode"], "paths_per_gpu": M, "Nt": Nt,
                        "evals_per_step": evals / args.steps,
-                       "l2": "stored trajectories (%.1f GB) exceed the 129 MB L2; no flush"
-                             % (prob.info()["device_bytes"] / 1e9)},
+                       "step": "one projected-gradient Armijo iteration (gradient, line search, "
+                               "update) inside one jd_optimize call",
+                       "l2": "inputs larger than L2: the %s buffers (%.2f GB) exceed the 129 MB "
+                             "L2; no flush" % (prob.info()["mode"], prob.info()["device_bytes"] / 1e9)},
             "gpu_launches": launches,
             "kernels_ms_per_step": {k: v[1] / args.steps for k, v in kstats.items()},
-            "roofline": roofline,
+            "roofline": rl.get(dom),
+            "roofline_all": rl,
             "e2e": e2e,
             "clocks": clk,
         }
@@ -280,59 +278,66 @@ def run_ours(args):
     return 0
 
 
-def prob_optimize_device(prob, u_t, zeta0):
-    """One jd_optimize iteration on a device-resident control tensor (in place)."""
+def optimize_device(prob, u_t, iters, zeta0):
+    """iters optimizer iterations (jd_optimize) on a device-resident control tensor."""
     import ctypes
     from paper_2505_04328_gb300 import binding as b
-    o = b.OptParams(max_iter=1, tol_rel_grad=0.0, tol_step=0.0, armijo_c=1e-4, zeta0=zeta0,
+    o = b.OptParams(max_iter=iters, tol_rel_grad=0.0, tol_step=0.0, armijo_c=1e-4, zeta0=zeta0,
                     zeta_max=1e3, max_backtracks=40)
     r = b.OptResult()
     st = b.lib().jd_optimize(prob.h, ctypes.c_void_p(u_t.data_ptr()), b.JD_MEM_DEVICE,
                              ctypes.byref(o), ctypes.byref(r), None)
     b._check(st, "jd_optimize")
-    return u_t, dict(iters=r.iters, evals=r.evals, J=r.J, zeta=r.zeta), None
+    return dict(iters=r.iters, evals=r.evals, J=r.J, zeta=r.zeta)
 
 
-# Algorithmic work per path-step (see DESIGN.md "Roofline"):
-#  adj_stored reads one stored state (d FP32 values) per path-step and its jump-flag
-#  bit: 4 d + 1/8 bytes.  fwd_store writes the same: 4 d + 1/8 bytes.
-def roofline_line(kstats, p, args, peaks, peak_kind):
-    M, Nt, d = p.M, p.Nt, p.d
-    if not kstats:
-        return None
-    dom = max(kstats.items(), key=lambda kv: kv[1][1])
-    name, (launches, total_ms) = dom
+# Algorithmic work per path-step (d = 2; derivation in DESIGN.md, section 9).
+#  * forward sweeps are bound by issue slots: 86 lane-operations per path-step (Philox
+#    block 40, two uniforms 6, Box-Muller 7, Poisson test 1, cubic drift 14, Euler
+#    update 4, running cost 10, loads 3, jumps lambda*dt x 133 = 1.3);
+#  * the stored adjoint is bound by HBM: it reads the state (4 d bytes), the jump-flag
+#    bit (1/8 byte) and the jump log (lambda*dt x (2 + d) x 4 bytes) per path-step;
+#    the stored forward writes the same bytes.
+ALGO = {
+    "fwd_cost": ("alu", 86.0), "fwd_store": ("alu", 86.0), "fwd_ckpt": ("alu", 86.0),
+    "adj_stored": ("hbm", None), "adj_recompute": ("alu", 86.0 + 40.0),
+}
+
+# DRAM bytes per path-step from the ncu captures summarized in profiles/ (small case,
+# M = 2^16, N_t = 1000, scaled per path-step); None once a kernel changed since.
+TRAFFIC_PER_PATH_STEP = {"fwd_store": None, "adj_stored": None, "fwd_cost": None}
+
+
+def kernel_roofline(name, stat, p, peaks, peak_kind):
+    launches, total_ms = stat
     per_launch_s = total_ms / launches * 1e-3
-    hbm = peaks.get("hbm_gbs", 6800.0)
-    if name in ("adj_stored", "fwd_store"):
-        bytes_per = (4 * d + 0.125) * M * Nt
-        achieved = bytes_per / per_launch_s / 1e9
-        return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None, "peak_source": peak_kind}
-    # RNG/ALU-bound sweeps: issue-slot roofline (lane-instructions per second)
+    units = p.M * p.Nt
+    tr = TRAFFIC_PER_PATH_STEP.get(name)
+    traffic = None if tr is None else tr * units
+    bound, ops = ALGO[name]
+    if bound == "hbm":
+        bytes_per = 4 * p.d + 0.125 + p.lam * p.dt * (2 + p.d) * 4
+        achieved = bytes_per * units / per_launch_s / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s",
+                "algorithmic_bytes_per_path_step": bytes_per}
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    peak_ginst = 152 * 4 * 32 * sm_mhz * 1e6 / 1e9    # lane-instr/s in G
-    inst_per = ALU_INSTR_PER_PATH_STEP.get(name, None)
-    if inst_per is None:
-        return {"kernel": name, "bound": "alu", "achieved": None, "peak": peak_ginst,
-                "unit": "Ginst/s", "frac": None, "traffic": None}
-    achieved = inst_per * M * Nt / per_launch_s / 1e9
-    return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak_ginst,
-            "unit": "Ginst/s", "frac": achieved / peak_ginst, "traffic": None,
-            "peak_source": "derived: 152 SMs x 4 schedulers x 32 lanes x max SM clock"}
-
-
-# Algorithmic lane-instructions per path-step of the RNG-bound sweeps (d = 2): one
-# Philox4x32-10 block (10 rounds x 4 integer ops: 2 wide multiplies, 2 three-input
-# XORs) = 40, one Box-Muller pair (log, sqrt, sincospi, 3 multiplies) ~ 6 MUFU/FMA-pipe
-# ops, drift + update + cost ~ 14 FMA.  Counted conservatively as 60.
-ALU_INSTR_PER_PATH_STEP = {"fwd_store": 60, "fwd_cost": 60, "fwd_ckpt": 60}
+    peak = 152 * 4 * 32 * sm_mhz * 1e6 / 1e9   # lane-operations per ns = G lane-ops/s
+    achieved = ops * units / per_launch_s / 1e9
+    return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Glane-op/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "peak_source": "derived: 152 SMs x 4 schedulers x 32 lanes x 1 instruction/clock x "
+                           f"{sm_mhz:.0f} MHz (max SM clock)",
+            "algorithmic_ops_per_path_step": ops}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--variant", default="stored", choices=["stored", "recompute", "auto"])

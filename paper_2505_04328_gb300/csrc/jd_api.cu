@@ -139,20 +139,20 @@ __global__ void finalize_cost_kernel(const double *__restrict__ partC, int64_t n
   }
 }
 
-// grad[k*du + l] = nu dt u[k*du + l] + (1/M) sum_b partG[(k*DU + l) * nblk + b]
-// (eq:definition_Gradient).  One warp per gradient entry.
-__global__ void finalize_grad_kernel(const double *__restrict__ partG, int64_t nblk, int Nt, int du,
+// grad[k*du + l] = nu dt u[k*du + l] + (1/M) sum_w partG[(k*DU + l) * npart + w]
+// (eq:definition_Gradient).  One 256-thread block per gradient entry: strided
+// per-thread sums, then a fixed tree (deterministic).
+__global__ void finalize_grad_kernel(const double *__restrict__ partG, int64_t npart, int Nt, int du,
                                      int DU, const double *__restrict__ u, double nu_dt, double invM,
                                      double *__restrict__ grad, double *__restrict__ bad) {
-  const int lane = threadIdx.x & 31;
-  const int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (e >= (int64_t)Nt * du) return;   // whole warp leaves together
+  __shared__ double sm[32];
+  const int64_t e = blockIdx.x;
   const int k = (int)(e / du), l = (int)(e % du);
-  const double *row = partG + ((int64_t)k * DU + l) * nblk;
+  const double *row = partG + ((int64_t)k * DU + l) * npart;
   double s = 0.0;
-  for (int64_t b = lane; b < nblk; b += 32) s += row[b];
-  s = warp_sum_d(s);
-  if (lane == 0) {
+  for (int64_t b = threadIdx.x; b < npart; b += blockDim.x) s += row[b];
+  s = block_sum_d(s, sm);
+  if (threadIdx.x == 0) {
     const double g = nu_dt * u[e] + s * invM;
     grad[e] = g;
     if (!isfinite(g)) *bad = 1.0;
@@ -412,27 +412,53 @@ static jd_status run_cost(jd_problem *p, const double *ud, int slot) {
   return finalize_cost(p, ud, slot);
 }
 
-static jd_status run_gradient(jd_problem *p, const double *ud, bool theta) {
+// Forward sweep in the plan's mode (stored states or checkpoints) and J.  Used for the
+// line-search trials of jd_optimize, so that the accepted trial's sweep is the forward
+// half of the next gradient.
+static jd_status run_plan_forward(jd_problem *p, const double *ud, int slot) {
   jd_status s = ensure_plan(p);
   if (s) return s;
   s = prep_u(p, ud);
   if (s) return s;
+  const PathBufs b = plan_bufs(p);
+  const bool stored = p->plan == JD_ADJ_STORED;
+  const int pr = prof_begin(stored ? KC_FWD_STORE : KC_FWD_CKPT, p->stream);
+  const cudaError_t e = p->ops->fwd(p, stored ? FWD_STORE : FWD_CKPT, 0, p->desc.M, p->uk, b, p->stream);
+  prof_end(pr, p->stream);
+  JD_CUDA(e);
+  return finalize_cost(p, ud, slot);
+}
+
+// Gradient at ud.  With forward_done the stored states / checkpoints, the control in
+// kernel precision and the cost partials already belong to ud (the accepted trial of
+// the previous line search), and only the adjoint half runs.
+static jd_status run_gradient(jd_problem *p, const double *ud, bool theta, bool forward_done = false) {
+  jd_status s = ensure_plan(p);
+  if (s) return s;
   const jd_problem_desc &q = p->desc;
   const int64_t M = q.M;
-  cudaError_t e1, e2;
+  cudaError_t e1 = cudaSuccess, e2;
   const PathBufs b = plan_bufs(p);
+  if (!forward_done) {
+    s = prep_u(p, ud);
+    if (s) return s;
+  }
   if (p->plan == JD_ADJ_STORED) {
-    int pr = prof_begin(KC_FWD_STORE, p->stream);
-    e1 = p->ops->fwd(p, FWD_STORE, 0, M, p->uk, b, p->stream);
-    prof_end(pr, p->stream);
-    pr = prof_begin(KC_ADJ_STORED, p->stream);
+    if (!forward_done) {
+      const int pr = prof_begin(KC_FWD_STORE, p->stream);
+      e1 = p->ops->fwd(p, FWD_STORE, 0, M, p->uk, b, p->stream);
+      prof_end(pr, p->stream);
+    }
+    const int pr = prof_begin(KC_ADJ_STORED, p->stream);
     e2 = p->ops->adj(p, ADJ_STORED_V, theta, 0, M, p->uk, b, p->stream);
     prof_end(pr, p->stream);
   } else {
-    int pr = prof_begin(KC_FWD_CKPT, p->stream);
-    e1 = p->ops->fwd(p, FWD_CKPT, 0, M, p->uk, b, p->stream);
-    prof_end(pr, p->stream);
-    pr = prof_begin(KC_ADJ_RECOMPUTE, p->stream);
+    if (!forward_done) {
+      const int pr = prof_begin(KC_FWD_CKPT, p->stream);
+      e1 = p->ops->fwd(p, FWD_CKPT, 0, M, p->uk, b, p->stream);
+      prof_end(pr, p->stream);
+    }
+    const int pr = prof_begin(KC_ADJ_RECOMPUTE, p->stream);
     e2 = p->ops->adj(p, ADJ_RECOMPUTE_V, theta, 0, M, p->uk, b, p->stream);
     prof_end(pr, p->stream);
   }
@@ -443,8 +469,8 @@ static jd_status run_gradient(jd_problem *p, const double *ud, bool theta) {
   const double dt = q.T / q.Nt;
   const int64_t ne = (int64_t)q.Nt * q.du;
   const int pr = prof_begin(KC_FINALIZE, p->stream);
-  finalize_grad_kernel<<<(unsigned)ceil_div(ne, 8), 256, 0, p->stream>>>(
-      p->partG, p->nblk, q.Nt, q.du, p->DU, ud, q.nu * dt, 1.0 / (double)M, p->grad_d, p->scal_d + S_BAD);
+  finalize_grad_kernel<<<(unsigned)ne, 256, 0, p->stream>>>(
+      p->partG, grad_parts(M), q.Nt, q.du, p->DU, ud, q.nu * dt, 1.0 / (double)M, p->grad_d, p->scal_d + S_BAD);
   prof_end(pr, p->stream);
   count_launch();
   JD_CUDA(cudaGetLastError());
@@ -674,7 +700,7 @@ jd_status jd_problem_create(const jd_problem_desc *desc, jd_problem **out) {
   ALLOC(p->grad_d, nu * 8, "gradient");
   ALLOC(p->scal_d, NSCAL * 8, "scalars");
   ALLOC(p->partC, (size_t)p->nblk * 8, "cost partials");
-  ALLOC(p->partG, (size_t)q.Nt * p->DU * p->nblk * 8, "gradient partials");
+  ALLOC(p->partG, (size_t)q.Nt * p->DU * grad_parts(q.M) * 8, "gradient partials");
   ALLOC(p->partT, (size_t)(p->D + 2) * p->nblk * 8, "parameter partials");
   ALLOC(p->opt_u, nu * 8, "optimizer iterate");
   ALLOC(p->opt_ut, nu * 8, "optimizer trial");
@@ -775,7 +801,7 @@ jd_status jd_sample_paths(jd_problem *p, const double *u, jd_memspace us, int64_
   if (e == cudaSuccess) e = cudaMalloc(&lamd, lam_b);
   if (e == cudaSuccess) e = cudaMalloc(&pc, count * es);
   if (e == cudaSuccess) e = cudaMalloc(&pC, nb * 8);
-  if (e == cudaSuccess) e = cudaMalloc(&pG, (size_t)Nt * p->DU * nb * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&pG, (size_t)Nt * p->DU * grad_parts(count) * 8);
   if (e == cudaSuccess) e = cudaMalloc(&lkt, capa * count * 2 * es);
   if (e == cudaSuccess) e = cudaMalloc(&ly, capa * count * D * es);
   if (e == cudaSuccess) e = cudaMalloc(&jc, (size_t)count * 4);
@@ -850,10 +876,12 @@ jd_status jd_optimize(jd_problem *p, double *u_inout, jd_memspace us, const jd_o
   jd_status status = JD_OK;
   // Algorithm 5.4: each iteration is one gradient at u^n, an Armijo line search and
   // the update; no gradient after the last update.
+  bool forward_done = false;   // the accepted trial's sweep is the next gradient's forward
   for (it = 0; it < o->max_iter; ++it) {
     s = clear_bad(p);
-    if (!s) s = run_gradient(p, p->opt_u, false);
+    if (!s) s = run_gradient(p, p->opt_u, false, forward_done);
     if (s) return s;
+    forward_done = false;
     r->evals++;
     int pr = prof_begin(KC_OPT, p->stream);
     opt_pgnorm_kernel<<<1, 256, 0, p->stream>>>(n, p->opt_u, p->grad_d, dt, q.u_min, q.u_max,
@@ -883,7 +911,7 @@ jd_status jd_optimize(jd_problem *p, double *u_inout, jd_memspace us, const jd_o
       prof_end(pr, p->stream);
       count_launch();
       JD_CUDA(cudaGetLastError());
-      s = run_cost(p, p->opt_ut, S_JT);
+      s = run_plan_forward(p, p->opt_ut, S_JT);
       if (s) return s;
       r->evals++;
       pr = prof_begin(KC_OPT, p->stream);
@@ -895,6 +923,7 @@ jd_status jd_optimize(jd_problem *p, double *u_inout, jd_memspace us, const jd_o
       if (s) return s;
       if (p->host_pinned[S_ACC] != 0.0) {
         accepted = true;
+        forward_done = true;
         step2 = p->host_pinned[S_STEP];
         r->J = p->host_pinned[S_J];
         break;

@@ -173,31 +173,21 @@ __device__ __forceinline__ int transposed_step_of_lane(int lane) {
 }
 
 // One batch of per-step gradient contributions gb[j][l] (steps kbase + j) summed over
-// the block's paths and written as FP64 partials partG[(k*DU + l) * nblk + block].
-// smem holds 2 * (TPB/32) * BATCH * DU pairs; `parity` alternates between batches so
-// one barrier per batch suffices.
+// the warp's 32 paths (compensated) and written as one FP64 partial per warp:
+// partG[(k*DU + l) * npart + warp_id], npart = blocks * TPB/32.  No block barrier.
 template <typename R, int DU>
 __device__ __forceinline__ void reduce_batch(Pair<R> (&gb)[BATCH][DU], int kbase, int Nt,
-                                             double *__restrict__ partG, int64_t nblk,
-                                             Pair<R> *smem, int parity) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int NW = TPB / 32;
-  Pair<R> *buf = smem + parity * (NW * BATCH * DU);
+                                             double *__restrict__ partG, int64_t npart) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wid = (int64_t)blockIdx.x * (TPB / 32) + (threadIdx.x >> 5);
 #pragma unroll
   for (int l = 0; l < DU; ++l) {
     Pair<R> v[BATCH];
 #pragma unroll
     for (int j = 0; j < BATCH; ++j) v[j] = gb[j][l];
     const Pair<R> r = warp_transpose_sum8(v, lane);
-    if ((lane & 3) == 0) buf[(warp * BATCH + transposed_step_of_lane(lane)) * DU + l] = r;
-  }
-  __syncthreads();
-  if (threadIdx.x < BATCH * DU) {
-    const int t = threadIdx.x, j = t / DU, l = t % DU, k = kbase + j;
-    Pair<R> s = buf[t];
-#pragma unroll
-    for (int w = 1; w < NW; ++w) s = padd(s, buf[w * BATCH * DU + t]);
-    if (k < Nt) partG[((int64_t)k * DU + l) * nblk + blockIdx.x] = (double)s.s + (double)s.e;
+    const int k = kbase + transposed_step_of_lane(lane);
+    if ((lane & 3) == 0 && k < Nt) partG[((int64_t)k * DU + l) * npart + wid] = (double)r.s + (double)r.e;
   }
 }
 

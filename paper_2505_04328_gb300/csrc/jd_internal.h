@@ -58,7 +58,8 @@ struct PathOps {
   // forward sweep in mode FWD_COST / FWD_STORE / FWD_CKPT
   cudaError_t (*fwd)(const struct ::jd_problem *p, int mode, int64_t m_begin, int64_t mloc,
                      const void *uk, const PathBufs &b, cudaStream_t s);
-  // adjoint sweep: per-step gradient partials [Nt][DU][nblk]; theta partials [D+2][nblk]
+  // adjoint sweep: per-step gradient partials [Nt][DU][nblk * TPB/32] (one per warp);
+  // theta partials [D+2][nblk]
   cudaError_t (*adj)(const struct ::jd_problem *p, int variant, bool theta, int64_t m_begin,
                      int64_t mloc, const void *uk, const PathBufs &b, cudaStream_t s);
 };
@@ -69,6 +70,9 @@ int compiled_dim(int d);         // smallest compiled D >= d, or 0
 void count_launch(int n = 1);
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Gradient partials per launch of mloc paths: one per warp of every block.
+inline int64_t grad_parts(int64_t mloc) { return ceil_div(mloc, TPB) * (TPB / 32); }
 
 }  // namespace jd
 

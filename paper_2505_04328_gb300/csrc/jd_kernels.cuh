@@ -16,7 +16,7 @@
 //   flags [ceil(Nt/32)][mloc]           bit k%32 set when step k had a jump
 //   ckpt  [nseg+1][D][mloc]              X_{sS} for s < nseg, X_Nt at s = nseg
 //   partC [nblk]                          FP64 block sums of the per-path cost
-//   partG [Nt][DU][nblk]                  FP64 block sums of the control sensitivities
+//   partG [Nt][DU][nblk * TPB/32]         FP64 warp sums of the control sensitivities
 //   partT [D+2][nblk]                     FP64 block sums of the parameter sensitivities
 #pragma once
 
@@ -148,11 +148,18 @@ __device__ __forceinline__ int forward_step(const KParams<R, D, DU> &kp, int k, 
     euler_substep(kp, M::mul(kp.dt, M::sub(R(1), th)), z1, uk, x);
     return 1;
   }
+  // two or more jumps: the general routine takes pointers, so pass copies and keep
+  // z, uk and x themselves in registers on the common paths
   JumpStep<R, D> S;
-  R xl[D];
+  R xl[D], zl[D], ul[DU];
 #pragma unroll
-  for (int c = 0; c < D; ++c) xl[c] = x[c];
-  build_jump_step(kp, k, m, w0, z, uk, xl, &S);
+  for (int c = 0; c < D; ++c) {
+    xl[c] = x[c];
+    zl[c] = z[c];
+  }
+#pragma unroll
+  for (int l = 0; l < DU; ++l) ul[l] = uk[l];
+  build_jump_step(kp, k, m, w0, zl, ul, xl, &S);
 #pragma unroll
   for (int c = 0; c < D; ++c) x[c] = S.Y[S.n + 1][c];
   if constexpr (LOG) {
@@ -341,35 +348,42 @@ fwd_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u
     lw.idx = lm;
     if (!active) lw.L.cap = 0;   // inactive threads log nothing
   }
-  const int ng = (Nt + 4) / 4;
+  // States X_0..X_Nt.  In store mode the last three states of the current group of
+  // four ride in registers (b0, b1, b2) and the group leaves as one 16-byte vector per
+  // component; the loop is not unrolled, which keeps the step's code small.
+  R b0[D], b1[D], b2[D];
+#pragma unroll
+  for (int c = 0; c < D; ++c) b0[c] = b1[c] = b2[c] = R(0);
 #pragma unroll 1
-  for (int g = 0; g < ng; ++g) {
-    R buf[4][D];
+  for (int k = 0; k <= Nt; ++k) {
+    if (MODE == FWD_STORE) {
+      const int j = k & 3;
+      if (j == 3 || k == Nt) {
+        if (active) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int k = 4 * g + j;
-      if (MODE == FWD_STORE) {
-#pragma unroll
-        for (int c = 0; c < D; ++c) buf[j][c] = x[c];
-      }
-      if (k < Nt) {
-        if (MODE == FWD_CKPT && active && (k % kp.S) == 0) {
-#pragma unroll
-          for (int c = 0; c < D; ++c) ckpt[((size_t)(k / kp.S) * D + c) * mloc + lm] = x[c];
+          for (int c = 0; c < D; ++c)
+            Vec4<R>::store(traj + (((size_t)(k >> 2) * D + c) * mloc + lm) * 4, j == 0 ? x[c] : b0[c],
+                           j == 1 ? x[c] : b1[c], j == 2 ? x[c] : b2[c], x[c]);
         }
-        if (forward_step(kp, k, m, u, x, lw)) fw |= 1u << (k & 31);
-        cost.add(cost_term(kp, x, xd + (size_t)(k + 1) * D));
-        if (MODE == FWD_STORE && ((k & 31) == 31 || k == Nt - 1)) {
-          if (active) flags[(size_t)(k >> 5) * mloc + lm] = fw;
-          fw = 0;
+      } else {
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          b0[c] = j == 0 ? x[c] : b0[c];
+          b1[c] = j == 1 ? x[c] : b1[c];
+          b2[c] = j == 2 ? x[c] : b2[c];
         }
       }
     }
-    if (MODE == FWD_STORE && active) {
+    if (k == Nt) break;
+    if (MODE == FWD_CKPT && active && (k % kp.S) == 0) {
 #pragma unroll
-      for (int c = 0; c < D; ++c)
-        Vec4<R>::store(traj + (((size_t)g * D + c) * mloc + lm) * 4, buf[0][c], buf[1][c], buf[2][c],
-                       buf[3][c]);
+      for (int c = 0; c < D; ++c) ckpt[((size_t)(k / kp.S) * D + c) * mloc + lm] = x[c];
+    }
+    if (forward_step(kp, k, m, u, x, lw)) fw |= 1u << (k & 31);
+    cost.add(cost_term(kp, x, xd + (size_t)(k + 1) * D));
+    if (MODE == FWD_STORE && ((k & 31) == 31 || k == Nt - 1)) {
+      if (active) flags[(size_t)(k >> 5) * mloc + lm] = fw;
+      fw = 0;
     }
   }
   if constexpr (MODE == FWD_STORE) {
@@ -420,8 +434,8 @@ adj_stored_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restr
                   double *__restrict__ partG, double *__restrict__ partT, R *__restrict__ lam_out,
                   int64_t mloc) {
   using M = Ar<R>;
-  __shared__ Pair<R> red[2 * (TPB / 32) * BATCH * DU];
   __shared__ Pair<R> red1[TPB / 32];
+  const int64_t npart = (int64_t)kp.nblk * (TPB / 32);
   const int64_t lm = (int64_t)blockIdx.x * TPB + threadIdx.x;
   const bool active = lm < mloc;
   // inactive threads of the last block replay path 0 (its stored data and its random
@@ -485,7 +499,7 @@ adj_stored_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restr
 #pragma unroll
       for (int l = 0; l < DU; ++l) gb[j][l] = {active ? g[l] : R(0), R(0)};
     }
-    reduce_batch<R, DU>(gb, BATCH * b, Nt, partG, kp.nblk, red, b & 1);
+    reduce_batch<R, DU>(gb, BATCH * b, Nt, partG, npart);
   }
   finish_theta<R, D, DU, THETA>(kp, th, active, partT, red1);
 }
@@ -507,8 +521,8 @@ adj_recompute_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__re
   const int S = kp.S;
   auto *skt = reinterpret_cast<typename V2<R>::T *>(sbuf + (size_t)S * D * TPB);   // [JS][TPB]
   R *sy = reinterpret_cast<R *>(skt + JS * TPB);                                    // [JS * D][TPB]
-  __shared__ Pair<R> red[2 * (TPB / 32) * BATCH * DU];
   __shared__ Pair<R> red1[TPB / 32];
+  const int64_t npart = (int64_t)kp.nblk * (TPB / 32);
   const int64_t lm = (int64_t)blockIdx.x * TPB + threadIdx.x;
   const bool active = lm < mloc;
   const int64_t lmc = active ? lm : 0;   // inactive threads replay path 0
@@ -524,7 +538,6 @@ adj_recompute_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__re
     const R xN = __ldg(ckpt + ((size_t)nseg * D + c) * mloc + lmc);
     mu[c] = M::mul(kp.qdt[c], M::sub(xN, __ldg(xd + (size_t)Nt * D + c)));
   }
-  int parity = 0;
 #pragma unroll 1
   for (int seg = nseg - 1; seg >= 0; --seg) {
     const int k0 = seg * S, len = min(S, Nt - k0);
@@ -564,8 +577,7 @@ adj_recompute_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__re
 #pragma unroll
         for (int l = 0; l < DU; ++l) gb[j][l] = {active ? g[l] : R(0), R(0)};
       }
-      reduce_batch<R, DU>(gb, k0 + BATCH * bb, Nt, partG, kp.nblk, red, parity);
-      parity ^= 1;
+      reduce_batch<R, DU>(gb, k0 + BATCH * bb, Nt, partG, npart);
     }
   }
   finish_theta<R, D, DU, THETA>(kp, th, active, partT, red1);
