@@ -303,16 +303,17 @@ ALGO = {
     "adj_stored": ("hbm", None), "adj_recompute": ("alu", 86.0 + 40.0),
 }
 
-# DRAM bytes per path-step from the ncu captures summarized in profiles/ (small case,
-# M = 2^16, N_t = 1000, scaled per path-step); None once a kernel changed since.
-TRAFFIC_PER_PATH_STEP = {"fwd_store": None, "adj_stored": None, "fwd_cost": None}
+# DRAM bytes (read + write) per path-step of the d = 2 kernels from one ncu capture
+# (profiles/fwd_store_adj_stored_double_well_d2_M2p16_Nt1000.md: M = 2^16, N_t = 1000,
+# scaled per path-step); set to None whenever a kernel changes after its capture.
+TRAFFIC_PER_PATH_STEP = {"fwd_store": 7.70, "adj_stored": 8.86}
 
 
 def kernel_roofline(name, stat, p, peaks, peak_kind):
     launches, total_ms = stat
     per_launch_s = total_ms / launches * 1e-3
     units = p.M * p.Nt
-    tr = TRAFFIC_PER_PATH_STEP.get(name)
+    tr = TRAFFIC_PER_PATH_STEP.get(name) if p.d == 2 else None
     traffic = None if tr is None else tr * units
     bound, ops = ALGO[name]
     if bound == "hbm":
