@@ -52,7 +52,7 @@ typedef enum {
   JD_ERR_CUDA = 3,         /* a CUDA runtime call failed (message in jd_last_error) */
   JD_ERR_NONFINITE = 4,    /* the cost or gradient came out NaN or Inf */
   JD_ERR_LINESEARCH = 5,   /* Armijo backtracking exhausted max_backtracks */
-  JD_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up */
+  JD_ERR_TIMEOUT = 6,      /* a bounded device-side wait (tensor-core completion) gave up */
   JD_ERR_UNSUPPORTED = 7,  /* valid request this build does not implement (e.g. d > 32) */
   JD_ERR_BUSY = 8          /* serving: result not ready yet */
 } jd_status;
@@ -64,7 +64,9 @@ typedef enum { JD_ADJ_AUTO = 0, JD_ADJ_STORED = 1, JD_ADJ_RECOMPUTE = 2 } jd_adj
 typedef enum { JD_MEM_HOST = 0, JD_MEM_DEVICE = 1 } jd_memspace;
 
 /* Problem descriptor (Sec. 3 eq:OCP_fully_discrete with the additive jump map).
- *   d, du        state and control dimensions, 1 <= d <= 32, 1 <= du <= 4
+ *   d, du        state and control dimensions, 1 <= d <= 32, 1 <= du <= 4; for
+ *                8 < d <= 32 the build has FP32 paths, LINEAR drift and the stored
+ *                adjoint (no parameter gradients)
  *   T, Nt, M     horizon, uniform steps (dt = T/Nt), Monte Carlo paths (M < 2^32)
  *   drift        LINEAR (C ignored) or CUBIC
  *   A, C         d*d; B d*du; dA d*d direction for the drift-coefficient gradient
@@ -82,8 +84,10 @@ typedef enum { JD_MEM_HOST = 0, JD_MEM_DEVICE = 1 } jd_memspace;
  *                checkpoints every S steps and regenerates each segment from the
  *                counter-based streams (exact, same result); AUTO picks STORED when it
  *                fits mem_budget_bytes
- *   use_tensor_cores  d = 32 LINEAR only: A x on tcgen05 tensor cores (BF16 inputs,
- *                FP32 accumulation); 0 = CUDA cores
+ *   use_tensor_cores  8 < d <= 32 only: the drift contraction A x (and A^T lambda in the
+ *                adjoint) of each 128-path tile as one tcgen05 MMA per step: 1 = BF16
+ *                inputs, FP32 accumulation; 2 = BF16 high + low parts, three products
+ *                (about 16 mantissa bits); 0 = FP32 on the CUDA cores
  *   mem_budget_bytes  device bytes this problem may allocate, 0 = library default
  *                (half of the free device memory at creation)
  *   cuda_stream  cudaStream_t for all work of this problem; NULL = the library

@@ -171,10 +171,11 @@ class JdProblem:
     drift, A, C, B, dA, sigma, lam, jump_law, jump_scale, x0, q, xd, nu, u_min, u_max,
     seed, epoch).  ``stream``: a torch.cuda.Stream, a raw cudaStream_t int, or None for
     torch's current stream (a library-owned stream when torch has no CUDA).
+    ``use_tensor_cores`` (8 < d <= 32): 0 CUDA cores, 1 BF16 tensor cores, 2 BF16 x3.
     """
 
     def __init__(self, problem, prec="fp32", mode="auto", stream=None, mem_budget: int = 0,
-                 use_tensor_cores: bool = False):
+                 use_tensor_cores: int = 0):
         self.p = problem
         self.Nt, self.du, self.d, self.M = problem.Nt, problem.du, problem.d, problem.M
         d = problem.d
@@ -193,7 +194,7 @@ class JdProblem:
             x0=_ptr(a["x0"]), q=_ptr(a["q"]), xd=_ptr(a["xd"]), nu=float(problem.nu),
             u_min=float(problem.u_min), u_max=float(problem.u_max), seed=int(problem.seed),
             epoch=int(problem.epoch), prec=_PREC[prec], mode=_MODE[mode],
-            use_tensor_cores=int(bool(use_tensor_cores)), mem_budget_bytes=int(mem_budget),
+            use_tensor_cores=int(use_tensor_cores), mem_budget_bytes=int(mem_budget),
             cuda_stream=self.stream_handle)
         h = ctypes.c_void_p()
         _check(lib().jd_problem_create(ctypes.byref(self.desc), ctypes.byref(h)), "jd_problem_create")

@@ -14,7 +14,7 @@
 
 namespace jd {
 
-extern const PathOps ops_f32_d1_u1, ops_f32_d2_u1, ops_f32_d2_u4, ops_f32_d4_u4, ops_f32_d8_u4;
+extern const PathOps ops_f32_d1_u1, ops_f32_d2_u1, ops_f32_d2_u4, ops_f32_d4_u4, ops_f32_d8_u4, ops_f32_d32_u4;
 extern const PathOps ops_f64_d1_u1, ops_f64_d2_u1, ops_f64_d2_u4, ops_f64_d4_u4, ops_f64_d8_u4;
 
 static std::atomic<uint64_t> g_launches{0};
@@ -67,6 +67,7 @@ int compiled_dim(int d) {
   if (d == 2) return 2;
   if (d <= 4) return 4;
   if (d <= 8) return 8;
+  if (d <= 32) return 32;
   return 0;
 }
 
@@ -92,6 +93,7 @@ const PathOps *path_ops_dims(int prec, int D, int DU) {
   if (D == 2 && DU == 4) return f ? &ops_f32_d2_u4 : &ops_f64_d2_u4;
   if (D == 4 && DU == 4) return f ? &ops_f32_d4_u4 : &ops_f64_d4_u4;
   if (D == 8 && DU == 4) return f ? &ops_f32_d8_u4 : &ops_f64_d8_u4;
+  if (D == 32 && DU == 4) return f ? &ops_f32_d32_u4 : nullptr;
   return nullptr;
 }
 
@@ -256,7 +258,7 @@ static jd_status cuda_fail(cudaError_t e, const char *what) {
   } while (0)
 
 // Scalar slots in p->scal_d
-enum { S_J = 0, S_JT = 1, S_DOT = 2, S_PG = 3, S_ACC = 4, S_STEP = 5, S_BAD = 7, S_THETA = 8 };
+enum { S_J = 0, S_JT = 1, S_DOT = 2, S_PG = 3, S_ACC = 4, S_STEP = 5, S_STATUS = 6, S_BAD = 7, S_THETA = 8 };
 constexpr int NSCAL = 8 + 34;
 
 static bool finite_all(const double *a, size_t n) {
@@ -323,6 +325,7 @@ static PathBufs plan_bufs(const jd_problem *p) {
   b.partC = p->partC;
   b.partG = p->partG;
   b.partT = p->partT;
+  b.status = reinterpret_cast<int *>(p->scal_d + S_STATUS);
   return b;
 }
 
@@ -335,6 +338,11 @@ static size_t recompute_bytes(const jd_problem *p) {
 static jd_status ensure_plan(jd_problem *p) {
   if (p->plan != JD_ADJ_AUTO) return JD_OK;
   jd_adjoint_mode want = p->desc.mode;
+  if (p->D == 32) {   // the d = 32 kernels have the stored variant only
+    if (want == JD_ADJ_RECOMPUTE)
+      return fail(JD_ERR_UNSUPPORTED, "the recompute adjoint is not built for 8 < d <= 32");
+    want = JD_ADJ_STORED;
+  }
   if (want == JD_ADJ_AUTO)
     want = (p->bytes + stored_bytes(p) <= p->budget) ? JD_ADJ_STORED : JD_ADJ_RECOMPUTE;
   if (want == JD_ADJ_STORED) {
@@ -491,15 +499,23 @@ static jd_status read_scalars(jd_problem *p, int first, int n) {
   return JD_OK;
 }
 
-static jd_status check_bad(jd_problem *p) {
-  jd_status s = read_scalars(p, S_BAD, 1);
-  if (s) return s;
+// Status after host scalars were read: a bounded device wait that gave up, then
+// non-finite results.
+static jd_status status_of_scalars(jd_problem *p) {
+  if (*reinterpret_cast<const int *>(p->host_pinned + S_STATUS) == (int)JD_ERR_TIMEOUT)
+    return fail(JD_ERR_TIMEOUT, "a bounded tensor-core wait timed out");
   if (p->host_pinned[S_BAD] != 0.0) return fail(JD_ERR_NONFINITE, "cost or gradient is not finite");
   return JD_OK;
 }
 
+static jd_status check_bad(jd_problem *p) {
+  jd_status s = read_scalars(p, S_STATUS, 2);
+  if (s) return s;
+  return status_of_scalars(p);
+}
+
 static jd_status clear_bad(jd_problem *p) {
-  JD_CUDA(cudaMemsetAsync(p->scal_d + S_BAD, 0, sizeof(double), p->stream));
+  JD_CUDA(cudaMemsetAsync(p->scal_d + S_STATUS, 0, 2 * sizeof(double), p->stream));
   return JD_OK;
 }
 
@@ -599,7 +615,9 @@ jd_status jd_problem_create(const jd_problem_desc *desc, jd_problem **out) {
   *out = nullptr;
   const jd_problem_desc &q = *desc;
   if (q.d < 1 || q.du < 1) return fail(JD_ERR_INVALID_ARG, "d and du must be >= 1");
-  if (q.d > 8) return fail(JD_ERR_UNSUPPORTED, "d > 8 is not compiled");
+  if (q.d > 32) return fail(JD_ERR_UNSUPPORTED, "d > 32 is not compiled");
+  if (q.d > 8 && (q.prec != JD_FP32 || q.drift != JD_DRIFT_LINEAR))
+    return fail(JD_ERR_UNSUPPORTED, "8 < d <= 32 is built for FP32 paths with a linear drift only");
   if (q.du > 4) return fail(JD_ERR_UNSUPPORTED, "du > 4 is not compiled");
   if (q.Nt < 1 || q.Nt > (1 << 24)) return fail(JD_ERR_INVALID_ARG, "Nt must be in [1, 2^24]");
   if (q.M < 1 || q.M > 0xFFFFFFFFll) return fail(JD_ERR_INVALID_ARG, "M must be in [1, 2^32 - 1]");
@@ -616,11 +634,10 @@ jd_status jd_problem_create(const jd_problem_desc *desc, jd_problem **out) {
     return fail(JD_ERR_INVALID_ARG, "jump_scale must be finite and >= 0");
   if (!std::isfinite(q.nu) || q.nu < 0.0) return fail(JD_ERR_INVALID_ARG, "nu must be finite and >= 0");
   if (!(q.u_min <= q.u_max)) return fail(JD_ERR_INVALID_ARG, "u_min must be <= u_max");
-  if (q.use_tensor_cores) {
-    if (q.d != 32 || q.drift != JD_DRIFT_LINEAR)
-      return fail(JD_ERR_UNSUPPORTED, "tensor cores only for d = 32 LINEAR drift");
-    return fail(JD_ERR_UNSUPPORTED, "tensor-core path not available in this build");
-  }
+  if (q.use_tensor_cores < 0 || q.use_tensor_cores > 2)
+    return fail(JD_ERR_INVALID_ARG, "use_tensor_cores must be 0, 1 (BF16) or 2 (BF16 x3)");
+  if (q.use_tensor_cores && q.d <= 8)
+    return fail(JD_ERR_UNSUPPORTED, "tensor cores are used for 8 < d <= 32 (linear drift, FP32)");
   const size_t dd = (size_t)q.d * q.d, dn = (size_t)(q.Nt + 1) * q.d;
   if (!finite_all(q.A, dd) || !finite_all(q.B, (size_t)q.d * q.du) || !finite_all(q.sigma, q.d) ||
       !finite_all(q.x0, q.d) || !finite_all(q.q, q.d) || !finite_all(q.xd, dn) ||
@@ -756,6 +773,8 @@ jd_status jd_gradient(jd_problem *p, const double *u, jd_memspace us, double *J,
                       jd_memspace gs, double *grad_theta) {
   if (!p) return fail(JD_ERR_INVALID_ARG, "p is NULL");
   if (grad && gs != JD_MEM_HOST && gs != JD_MEM_DEVICE) return fail(JD_ERR_INVALID_ARG, "bad memory space for grad");
+  if (grad_theta && p->D == 32)
+    return fail(JD_ERR_UNSUPPORTED, "parameter gradients are not built for 8 < d <= 32");
   jd_status s = set_device(p);
   if (!s) s = load_u(p, u, us);
   if (!s) s = clear_bad(p);
@@ -773,8 +792,7 @@ jd_status jd_gradient(jd_problem *p, const double *u, jd_memspace us, double *J,
   if (J) *J = p->host_pinned[S_J];
   if (grad_theta)
     for (int t = 0; t < p->desc.d + 2; ++t) grad_theta[t] = p->host_pinned[S_THETA + t];
-  if (p->host_pinned[S_BAD] != 0.0) return fail(JD_ERR_NONFINITE, "cost or gradient is not finite");
-  return JD_OK;
+  return status_of_scalars(p);
 }
 
 jd_status jd_sample_paths(jd_problem *p, const double *u, jd_memspace us, int64_t m0, int64_t count,
@@ -816,6 +834,7 @@ jd_status jd_sample_paths(jd_problem *p, const double *u, jd_memspace us, int64_
   b.partC = (double *)pC;
   b.partG = (double *)pG;
   b.lam_out = lamd;
+  b.status = reinterpret_cast<int *>(p->scal_d + S_STATUS);
   if (e == cudaSuccess) e = p->ops->fwd(p, FWD_STORE, m0, count, p->uk, b, p->stream);
   if (e == cudaSuccess && lam) e = p->ops->adj(p, ADJ_STORED_V, false, m0, count, p->uk, b, p->stream);
   std::vector<unsigned char> ht, hl, hc;
@@ -849,7 +868,12 @@ jd_status jd_sample_paths(jd_problem *p, const double *u, jd_memspace us, int64_
     for (int k = 0; k <= Nt; ++k)
       for (int c = 0; c < d; ++c) {
         const size_t base = (size_t)(i * (Nt + 1) + k) * d + c;
-        if (X) X[base] = rd(ht, ((((size_t)(k >> 2) * D + c) * count + i) * 4) + (k & 3));
+        if (X) {
+          const size_t ti = p->ops->traj_layout == 0
+                                ? ((((size_t)(k >> 2) * D + c) * count + i) * 4) + (k & 3)
+                                : ((((size_t)k * (D / 4) + (c >> 2)) * count + i) * 4) + (c & 3);
+          X[base] = rd(ht, ti);
+        }
         if (lam) lam[base] = rd(hl, ((size_t)k * D + c) * count + i);
       }
   }
@@ -891,10 +915,8 @@ jd_status jd_optimize(jd_problem *p, double *u_inout, jd_memspace us, const jd_o
     JD_CUDA(cudaGetLastError());
     s = read_scalars(p, 0, 8);
     if (s) return s;
-    if (p->host_pinned[S_BAD] != 0.0) {
-      status = fail(JD_ERR_NONFINITE, "cost or gradient is not finite");
-      break;
-    }
+    status = status_of_scalars(p);
+    if (status != JD_OK) break;
     const double J = p->host_pinned[S_J], pg = p->host_pinned[S_PG];
     if (J_hist) J_hist[it] = J;
     r->J = J;

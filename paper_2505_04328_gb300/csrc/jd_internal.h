@@ -47,11 +47,13 @@ struct PathBufs {
   int log_cap = 0;             // jump log: records per path capacity
   double *partC = nullptr, *partG = nullptr, *partT = nullptr;
   void *lam_out = nullptr;     // adjoint states (optional)
+  int *status = nullptr;       // device status word (bounded waits record timeouts here)
 };
 
 // Per-instantiation launch table (one entry per precision x compiled dimension).
 struct PathOps {
   int D, DU, S, elem;
+  int traj_layout;   // 0: [ceil((Nt+1)/4)][D][M][4]; 1: [Nt+1][D/4][M][4]
   // per-thread stack bytes the kernels of this instantiation may need (the jump path
   // keeps its sub-step states in local memory behind a non-inlined call)
   size_t (*stack_bytes)();
@@ -101,6 +103,7 @@ struct jd_problem {
   int *jcnt = nullptr;
   int log_cap = 0;
   double *opt_u = nullptr, *opt_ut = nullptr, *opt_g = nullptr;
+  int *status_d = nullptr;   // kernel status word (JD_OK or JD_ERR_TIMEOUT)
   double *host_pinned = nullptr;  // small pinned staging buffer
   size_t bytes = 0;
   int64_t nblk = 0;

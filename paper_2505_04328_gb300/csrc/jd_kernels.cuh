@@ -740,7 +740,7 @@ size_t op_stack_bytes() {
 
 template <typename R, int D, int DU>
 constexpr PathOps make_ops() {
-  return PathOps{D, DU, seg_len<D>(), (int)sizeof(R), &op_stack_bytes<R, D, DU>, &op_fwd<R, D, DU>,
+  return PathOps{D, DU, seg_len<D>(), (int)sizeof(R), 0, &op_stack_bytes<R, D, DU>, &op_fwd<R, D, DU>,
                  &op_adj<R, D, DU>};
 }
 
