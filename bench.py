@@ -122,8 +122,15 @@ def max_over_ranks(dist, value: float, device="cpu") -> float:
     return float(t.item())
 
 
-def bench_workload(M=None, Nt=None):
-    p = workloads.double_well()
+WORKLOADS = {
+    "double_well": workloads.double_well,   # d=2 cubic, M=2^20, Nt=1000 (the headline)
+    "linear32": workloads.linear32,         # d=32 linear, M=2^18, Nt=500
+    "lq_scalar": workloads.lq_scalar,       # d=1 linear-quadratic, M=1000, Nt=100 (FP64)
+}
+
+
+def bench_workload(M=None, Nt=None, name="double_well"):
+    p = WORKLOADS[name]()
     if M is not None:
         p = p.replace(M=M)
     if Nt is not None:
@@ -192,9 +199,10 @@ def run_ours(args):
     jd.build()
     stream = torch.cuda.current_stream()
 
-    p = replica_problem(bench_workload(args.paths, args.steps_t), rank)
+    p = replica_problem(bench_workload(args.paths, args.steps_t, args.workload), rank)
     M, Nt, du = p.M, p.Nt, p.du
-    prob = jd.JdProblem(p, prec="fp32", mode=args.variant, stream=stream)
+    prec = "fp64" if args.workload == "lq_scalar" else "fp32"
+    prob = jd.JdProblem(p, prec=prec, mode=args.variant, stream=stream, use_tensor_cores=args.tc)
     n = Nt * du
     u = torch.zeros(n, dtype=torch.float64, device="cuda")
 
@@ -242,16 +250,18 @@ def run_ours(args):
            "d2h_bytes_per_step": n * 8 / args.steps + 64 * (1 + trials)}
 
     peaks, peak_kind = _peaks()
-    rl = {k: kernel_roofline(k, v, p, peaks, peak_kind) for k, v in kstats.items()
-          if k in ALGO}
+    rl = {k: kernel_roofline(k, v, p, peaks, peak_kind, args.tc) for k, v in kstats.items()
+          if k in KERNEL_BOUND}
     dom = max(rl, key=lambda k: kstats[k][1]) if rl else None
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"double_well d=2 M=2^{int(math.log2(M))} Nt={Nt}",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload} d={p.d} M={M} Nt={Nt}",
+                       "tensor_cores": {0: "off", 1: "bf16", 2: "bf16x3"}[args.tc],
                        "variant": prob.info()["mode"], "paths_per_gpu": M, "Nt": Nt,
                        "evals_per_step": evals / args.steps,
                        "step": "one projected-gradient Armijo iteration (gradient, line search, "
@@ -266,7 +276,7 @@ def run_ours(args):
             "clocks": clk,
         }
         if not args.no_cpu_baseline:
-            rate, sec, threads = oracle_step_rate(p.replace(M=args.reference_paths), 1, 0)
+            rate, sec, threads = oracle_step_rate(p.replace(M=min(M, args.reference_paths)), 1, 0)
             line["cpu_baseline"] = {
                 "value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                 "sample": f"{args.reference_paths} of {M} paths, all {Nt} steps, one optimizer "
@@ -291,17 +301,31 @@ def optimize_device(prob, u_t, iters, zeta0):
     return dict(iters=r.iters, evals=r.evals, J=r.J, zeta=r.zeta)
 
 
-# Algorithmic work per path-step (d = 2; derivation in the design doc, section 9).
-#  * forward sweeps are bound by issue slots: 86 lane-operations per path-step (Philox
-#    block 40, two uniforms 6, Box-Muller 7, Poisson test 1, cubic drift 14, Euler
-#    update 4, running cost 10, loads 3, jumps lambda*dt x 133 = 1.3);
-#  * the stored adjoint is bound by HBM: it reads the state (4 d bytes), the jump-flag
-#    bit (1/8 byte) and the jump log (lambda*dt x (2 + d) x 4 bytes) per path-step;
-#    the stored forward writes the same bytes.
-ALGO = {
-    "fwd_cost": ("alu", 86.0), "fwd_store": ("alu", 86.0), "fwd_ckpt": ("alu", 86.0),
-    "adj_stored": ("hbm", None), "adj_recompute": ("alu", 86.0 + 40.0),
-}
+# Algorithmic work per path-step (derivation in the design doc, section 9).  Forward sweeps
+# are bound by issue slots (lane-operations): Philox blocks x 40 (20 wide multiplies,
+# 20 XORs), 3 per uniform, 7 per Box-Muller pair, the drift's multiply-adds (the A x
+# contraction leaves the CUDA cores when it runs on tensor cores), 2 d for the Euler
+# update, 3 d + 4 for the running cost, and lambda dt times the cost of a jump.  The
+# stored adjoint is bound by HBM: state (4 d bytes), jump-flag bit, jump log.
+KERNEL_BOUND = {"fwd_cost": "alu", "fwd_store": "alu", "fwd_ckpt": "alu", "adj_stored": "hbm",
+                "adj_recompute": "alu"}
+
+
+def forward_ops(p, tc=0):
+    d, du = p.d, p.du
+    P = (d + 1) // 2
+    blocks = (1 + 2 * P + 3) // 4
+    drift = (0 if tc else d * d) + d * du + (d * d + 2 * d if p.drift == workloads.CUBIC else 0)
+    base = 40 * blocks + 3 * 2 * P + 7 * P + 1 + drift + 2 * d + 3 * d + 4
+    slot_blocks = (1 + 4 * P + 3) // 4
+    per_jump = 40 * slot_blocks + 3 * 4 * P + 7 * 2 * P + 2 * (d * d + d * du + 2 * d)
+    return base + p.lam * p.dt * per_jump
+
+
+def adjoint_ops(p):
+    d, du = p.d, p.du
+    return d * d + d * du + 2 * d + (d * d + 2 * d if p.drift == workloads.CUBIC else 0) + 10
+
 
 # DRAM bytes (read + write) per path-step of the d = 2 kernels from one ncu capture
 # (profiles/fwd_store_adj_stored_double_well_d2_M2p16_Nt1000.md: M = 2^16, N_t = 1000,
@@ -309,30 +333,34 @@ ALGO = {
 TRAFFIC_PER_PATH_STEP = {"fwd_store": 7.70, "adj_stored": 8.86}
 
 
-def kernel_roofline(name, stat, p, peaks, peak_kind):
+def kernel_roofline(name, stat, p, peaks, peak_kind, tc=0):
     launches, total_ms = stat
     per_launch_s = total_ms / launches * 1e-3
     units = p.M * p.Nt
-    tr = TRAFFIC_PER_PATH_STEP.get(name) if p.d == 2 else None
+    tr = TRAFFIC_PER_PATH_STEP.get(name) if (p.d == 2 and p.name == "double_well") else None
     traffic = None if tr is None else tr * units
-    bound, ops = ALGO[name]
-    if bound == "hbm":
+    if KERNEL_BOUND[name] == "hbm":
         bytes_per = 4 * p.d + 0.125 + p.lam * p.dt * (2 + p.d) * 4
         achieved = bytes_per * units / per_launch_s / 1e9
         peak = peaks.get("hbm_gbs", 6800.0)
         return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                 else "fallback 6.8 TB/s",
                 "algorithmic_bytes_per_path_step": bytes_per}
+    ops = forward_ops(p, tc) + (adjoint_ops(p) if name == "adj_recompute" else 0.0)
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    peak = 152 * 4 * 32 * sm_mhz * 1e6 / 1e9   # lane-operations per ns = G lane-ops/s
+    peak = 152 * 4 * 32 * sm_mhz * 1e6 / 1e9   # G lane-operations per second
     achieved = ops * units / per_launch_s / 1e9
-    return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Glane-op/s",
-            "frac": achieved / peak, "traffic": traffic,
-            "peak_source": "derived: 152 SMs x 4 schedulers x 32 lanes x 1 instruction/clock x "
-                           f"{sm_mhz:.0f} MHz (max SM clock)",
-            "algorithmic_ops_per_path_step": ops}
+    out = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Glane-op/s",
+           "frac": achieved / peak, "traffic": traffic,
+           "peak_source": "derived: 152 SMs x 4 schedulers x 32 lanes x 1 instruction/clock x "
+                          f"{sm_mhz:.0f} MHz (max SM clock)",
+           "algorithmic_ops_per_path_step": ops}
+    if tc:
+        flops = 2.0 * p.d * p.d * (3 if tc == 2 else 1) * units
+        out["tensor_tflops"] = flops / per_launch_s / 1e12
+    return out
 
 
 def main():
@@ -342,6 +370,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--variant", default="stored", choices=["stored", "recompute", "auto"])
+    ap.add_argument("--workload", default="double_well", choices=sorted(WORKLOADS))
+    ap.add_argument("--tc", type=int, default=0, choices=[0, 1, 2],
+                    help="tensor cores for the d=32 workload: 0 off, 1 BF16, 2 BF16x3")
     ap.add_argument("--paths", type=int, default=None, help="override M (paths per GPU)")
     ap.add_argument("--steps-t", type=int, default=None, help="override N_t")
     ap.add_argument("--reference-paths", type=int, default=1 << 14)

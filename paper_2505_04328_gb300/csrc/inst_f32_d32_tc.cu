@@ -3,11 +3,23 @@
 
 namespace jd {
 
+// Coefficients go to the problem's device buffer (stream ordered) for the kernels to stage.
+static cudaError_t upload_kp(const jd_problem *p, int64_t m_begin, int64_t mloc, cudaStream_t s, KP32 **dev) {
+  if (!p->kp_dev) return cudaErrorInvalidValue;
+  auto *kp = new KP32();
+  make_kparams<float, D32, DU32>(p, m_begin, mloc, *kp);
+  const cudaError_t e = cudaMemcpyAsync(p->kp_dev, kp, sizeof(KP32), cudaMemcpyHostToDevice, s);
+  delete kp;   // pageable source: the copy is staged before cudaMemcpyAsync returns
+  *dev = static_cast<KP32 *>(p->kp_dev);
+  return e;
+}
+
 static cudaError_t op32_fwd(const jd_problem *p, int mode, int64_t m_begin, int64_t mloc, const void *uk,
                             const PathBufs &b, cudaStream_t s) {
   if (mode == FWD_CKPT) return cudaErrorNotSupported;
-  auto *kp = new KP32();
-  make_kparams<float, D32, DU32>(p, m_begin, mloc, *kp);
+  KP32 *kp = nullptr;
+  const cudaError_t ue = upload_kp(p, m_begin, mloc, s, &kp);
+  if (ue != cudaSuccess) return ue;
   const dim3 grid((unsigned)ceil_div(mloc, TPB));
   const float *u = static_cast<const float *>(uk);
   const float *xd = static_cast<const float *>(p->xdk);
@@ -16,16 +28,15 @@ static cudaError_t op32_fwd(const jd_problem *p, int mode, int64_t m_begin, int6
   float *pc = static_cast<float *>(b.pcost);
   switch (p->desc.use_tensor_cores) {
     case 1:
-      fwd32_kernel<1><<<grid, TPB, 0, s>>>(*kp, u, xd, b.partC, traj, b.flags, pc, jl, b.jcnt, b.status, mloc);
+      fwd32_kernel<1><<<grid, TPB, 0, s>>>(kp, u, xd, b.partC, traj, b.flags, pc, jl, b.jcnt, b.status, mloc);
       break;
     case 2:
-      fwd32_kernel<2><<<grid, TPB, 0, s>>>(*kp, u, xd, b.partC, traj, b.flags, pc, jl, b.jcnt, b.status, mloc);
+      fwd32_kernel<2><<<grid, TPB, 0, s>>>(kp, u, xd, b.partC, traj, b.flags, pc, jl, b.jcnt, b.status, mloc);
       break;
     default:
-      fwd32_kernel<0><<<grid, TPB, 0, s>>>(*kp, u, xd, b.partC, traj, b.flags, pc, jl, b.jcnt, b.status, mloc);
+      fwd32_kernel<0><<<grid, TPB, 0, s>>>(kp, u, xd, b.partC, traj, b.flags, pc, jl, b.jcnt, b.status, mloc);
       break;
   }
-  delete kp;
   count_launch();
   return cudaGetLastError();
 }
@@ -33,8 +44,9 @@ static cudaError_t op32_fwd(const jd_problem *p, int mode, int64_t m_begin, int6
 static cudaError_t op32_adj(const jd_problem *p, int variant, bool theta, int64_t m_begin, int64_t mloc,
                             const void *uk, const PathBufs &b, cudaStream_t s) {
   if (variant != ADJ_STORED_V || theta) return cudaErrorNotSupported;
-  auto *kp = new KP32();
-  make_kparams<float, D32, DU32>(p, m_begin, mloc, *kp);
+  KP32 *kp = nullptr;
+  const cudaError_t ue = upload_kp(p, m_begin, mloc, s, &kp);
+  if (ue != cudaSuccess) return ue;
   const dim3 grid((unsigned)ceil_div(mloc, TPB));
   const float *u = static_cast<const float *>(uk);
   const float *xd = static_cast<const float *>(p->xdk);
@@ -43,16 +55,15 @@ static cudaError_t op32_adj(const jd_problem *p, int variant, bool theta, int64_
   float *lo = static_cast<float *>(b.lam_out);
   switch (p->desc.use_tensor_cores) {
     case 1:
-      adj32_kernel<1><<<grid, TPB, 0, s>>>(*kp, u, xd, traj, b.flags, jl, b.jcnt, b.partG, lo, b.status, mloc);
+      adj32_kernel<1><<<grid, TPB, 0, s>>>(kp, u, xd, traj, b.flags, jl, b.jcnt, b.partG, lo, b.status, mloc);
       break;
     case 2:
-      adj32_kernel<2><<<grid, TPB, 0, s>>>(*kp, u, xd, traj, b.flags, jl, b.jcnt, b.partG, lo, b.status, mloc);
+      adj32_kernel<2><<<grid, TPB, 0, s>>>(kp, u, xd, traj, b.flags, jl, b.jcnt, b.partG, lo, b.status, mloc);
       break;
     default:
-      adj32_kernel<0><<<grid, TPB, 0, s>>>(*kp, u, xd, traj, b.flags, jl, b.jcnt, b.partG, lo, b.status, mloc);
+      adj32_kernel<0><<<grid, TPB, 0, s>>>(kp, u, xd, traj, b.flags, jl, b.jcnt, b.partG, lo, b.status, mloc);
       break;
   }
-  delete kp;
   count_launch();
   return cudaGetLastError();
 }

@@ -604,6 +604,7 @@ jd_status jd_problem_destroy(jd_problem *p) {
   free_dev(p->opt_u);
   free_dev(p->opt_ut);
   free_dev(p->opt_g);
+  free_dev(p->kp_dev);
   if (p->host_pinned) cudaFreeHost(p->host_pinned);
   if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
   delete p;
@@ -721,6 +722,7 @@ jd_status jd_problem_create(const jd_problem_desc *desc, jd_problem **out) {
   ALLOC(p->partT, (size_t)(p->D + 2) * p->nblk * 8, "parameter partials");
   ALLOC(p->opt_u, nu * 8, "optimizer iterate");
   ALLOC(p->opt_ut, nu * 8, "optimizer trial");
+  if (p->D == 32) ALLOC(p->kp_dev, 16384, "d = 32 coefficients");
 #undef ALLOC
   e = cudaMallocHost((void **)&p->host_pinned, NSCAL * 8);
   if (e != cudaSuccess) {

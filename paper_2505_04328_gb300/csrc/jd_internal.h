@@ -104,6 +104,7 @@ struct jd_problem {
   int log_cap = 0;
   double *opt_u = nullptr, *opt_ut = nullptr, *opt_g = nullptr;
   int *status_d = nullptr;   // kernel status word (JD_OK or JD_ERR_TIMEOUT)
+  void *kp_dev = nullptr;    // coefficient struct of the d = 32 kernels (device copy)
   double *host_pinned = nullptr;  // small pinned staging buffer
   size_t bytes = 0;
   int64_t nblk = 0;

@@ -17,11 +17,16 @@
 // generate the step's noise meanwhile, then wait on the mbarrier (bounded: on timeout the
 // CTA records JD_ERR_TIMEOUT in *status and stops), and read their lane with tcgen05.ld.
 //
+// The coefficient struct (13 KB) reaches the kernels through a device buffer and is
+// staged into shared memory once per CTA; the kernels take no large parameters.
+//
 // Layouts: traj32 [Nt+1][8][mloc][4] (state X_k, components 4c..4c+3 in one 16-byte
 // vector); flags, jump log and partials as in jd_kernels.cuh.
 #pragma once
 
 #include <cuda_bf16.h>
+
+#include <cstddef>
 
 #include "jd_kernels.cuh"
 
@@ -191,14 +196,42 @@ __device__ __forceinline__ bool tc_collect(TcShared &sh, uint32_t parity, float 
   return done;
 }
 
-// out = A x (transpose = false) or A^T x on the CUDA cores (constant-bank coefficients)
-__device__ __forceinline__ void cc_matvec(const KP32 &kp, const float (&x)[32], float (&out)[32], bool transpose) {
+// Coefficients of a tile in shared memory: the parameter struct (13 KB, beyond what the
+// constant bank serves directly) plus A^T, copied once per CTA.
+struct CcShared {
+  float at[32 * 32];   // at[k * 32 + n] = A[n][k]; first, so its 16-byte rows stay aligned
+  KP32 kp;             // kp.A at byte 4096 + 0: 16-byte aligned too
+};
+static_assert(offsetof(CcShared, kp) % 16 == 0 && offsetof(KP32, A) == 0, "16-byte aligned coefficient rows");
+
+__device__ __forceinline__ void stage_params(CcShared &cs, const KP32 *__restrict__ kpg) {
+  const uint32_t *src = reinterpret_cast<const uint32_t *>(kpg);
+  uint32_t *dst = reinterpret_cast<uint32_t *>(&cs.kp);
+  for (int i = threadIdx.x; i < (int)(sizeof(KP32) / 4); i += blockDim.x) dst[i] = __ldg(src + i);
+  for (int i = threadIdx.x; i < 32 * 32; i += blockDim.x) cs.at[(i & 31) * 32 + (i >> 5)] = __ldg(kpg->A + i);
+  __syncthreads();
+}
+
+// out_n = sum_k M[k][n] v_k on the CUDA cores, M row-major in shared memory (M = A^T
+// gives A v, M = A gives A^T v).  v goes through the thread's own shared-memory column
+// (vcol[k * TPB]) so the loop over k stays rolled; the rows of M are broadcast reads.
+__device__ __forceinline__ void cc_matvec(const float *M, float *vcol, const float (&v)[32], float (&out)[32]) {
 #pragma unroll
-  for (int n = 0; n < 32; ++n) {
-    float s = 0.f;
+  for (int k = 0; k < 32; ++k) vcol[k * TPB] = v[k];
 #pragma unroll
-    for (int k = 0; k < 32; ++k) s = __fmaf_rn(transpose ? kp.A[k * 32 + n] : kp.A[n * 32 + k], x[k], s);
-    out[n] = s;
+  for (int n = 0; n < 32; ++n) out[n] = 0.f;
+#pragma unroll 2
+  for (int k = 0; k < 32; ++k) {
+    const float vk = vcol[k * TPB];
+    const float4 *row = reinterpret_cast<const float4 *>(M + k * 32);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float4 a = row[q];
+      out[4 * q] = __fmaf_rn(a.x, vk, out[4 * q]);
+      out[4 * q + 1] = __fmaf_rn(a.y, vk, out[4 * q + 1]);
+      out[4 * q + 2] = __fmaf_rn(a.z, vk, out[4 * q + 2]);
+      out[4 * q + 3] = __fmaf_rn(a.w, vk, out[4 * q + 3]);
+    }
   }
 }
 
@@ -236,15 +269,147 @@ __device__ __forceinline__ uint32_t main_noise_or_jump(const KP32 &kp, int k, ui
   return o0.x;
 }
 
+// ---------------------------------------------------------------------------
+// Steps with jumps at d = 32 (linear drift)
+// ---------------------------------------------------------------------------
+
+// y_c += scale_c * Z_c for the main-stream normals of step k (words 1..32), where
+// scale_c = sigma_c * s (s = sqrt of the sub-step length).
+__device__ __forceinline__ void add_main_noise_scaled(const KP32 &kp, int k, uint32_t m, float s, float (&y)[32]) {
+  uint32_t carry = 0;
+#pragma unroll
+  for (int b = 0; b < 9; ++b) {
+    const uint4 o = philox10((uint32_t)k, m, (uint32_t)b, kp.epoch, kp.key0, kp.key1);
+    const uint32_t w[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = 4 * b + q;
+      if (j == 0 || j > 32) continue;
+      if (j & 1) {
+        carry = w[q];
+      } else {
+        float z0, z1;
+        normal_pair<float>(carry, w[q], z0, z1);
+        const int c = j - 2;
+        y[c] = __fmaf_rn(__fmul_rn(kp.sigma[c], s), z0, y[c]);
+        y[c + 1] = __fmaf_rn(__fmul_rn(kp.sigma[c + 1], s), z1, y[c + 1]);
+      }
+    }
+  }
+}
+
+// Words [first, first + 32) of jump slot 0 of step k decoded into 32 values added to y:
+// sizes (first = 1): y_c += jump_scale * xi_c; post-jump normals (first = 33):
+// y_c += sigma_c * s * Z_c.  Valid for d >= 31 (16 normal pairs per slot).
+template <bool SIZES>
+__device__ __forceinline__ void add_slot0_words(const KP32 &kp, int k, uint32_t m, float s, float (&y)[32]) {
+  constexpr int first = SIZES ? 1 : 33;
+  const uint32_t tag = (1u << 24) | (1u << 16);
+  uint32_t carry = 0;
+#pragma unroll
+  for (int b = first / 4; b <= (first + 31) / 4; ++b) {
+    const uint4 o = philox10((uint32_t)k, m, tag | (uint32_t)b, kp.epoch, kp.key0, kp.key1);
+    const uint32_t w[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = 4 * b + q;
+      if (j < first || j >= first + 32) continue;
+      const int i = j - first;   // value index 0..31
+      if (SIZES && kp.jump_law == JD_JUMP_UNIFORM) {
+        y[i] = __fadd_rn(y[i], __fmul_rn(kp.jump_scale, __fsub_rn(__fmul_rn(2.f, Ar<float>::u01(w[q])), 1.f)));
+      } else if ((i & 1) == 0) {
+        carry = w[q];
+      } else {
+        float z0, z1;
+        normal_pair<float>(carry, w[q], z0, z1);
+        if (SIZES) {
+          y[i - 1] = __fadd_rn(y[i - 1], __fmul_rn(kp.jump_scale, z0));
+          y[i] = __fadd_rn(y[i], __fmul_rn(kp.jump_scale, z1));
+        } else {
+          y[i - 1] = __fmaf_rn(__fmul_rn(kp.sigma[i - 1], s), z0, y[i - 1]);
+          y[i] = __fmaf_rn(__fmul_rn(kp.sigma[i], s), z1, y[i]);
+        }
+      }
+    }
+  }
+}
+
+// y += de * (f + B u_k)
+__device__ __forceinline__ void add_drift(const KP32 &kp, const float *__restrict__ u, int k, float de,
+                                          const float (&f)[32], float (&y)[32]) {
+  float uk[DU32];
+#pragma unroll
+  for (int l = 0; l < DU32; ++l) uk[l] = __ldg(u + (size_t)k * DU32 + l);
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    float bc = 0.f;
+#pragma unroll
+    for (int l = 0; l < DU32; ++l) bc = __fmaf_rn(kp.B[c * DU32 + l], uk[l], bc);
+    y[c] = __fmaf_rn(de, __fadd_rn(f[c], bc), y[c]);
+  }
+}
+
+// Sorted jump-time fractions of step k (n jumps): regenerated from word 0 of each slot.
+__device__ __forceinline__ void regen_jump_times(const KP32 &kp, int k, uint32_t m, int n, float *th) {
+#pragma unroll 1
+  for (int i = 0; i < n; ++i)
+    th[i] = Ar<float>::u01(philox10((uint32_t)k, m, (1u << 24) | ((uint32_t)(i + 1) << 16), kp.epoch, kp.key0,
+                                    kp.key1).x);
+#pragma unroll 1
+  for (int i = 1; i < n; ++i) {
+    const float cur = th[i];
+    int j = i - 1;
+    while (j >= 0 && th[j] > cur) {
+      th[j + 1] = th[j];
+      --j;
+    }
+    th[j + 1] = cur;
+  }
+}
+
+// One-jump step of the forward, out of line (its streamed draws would crowd the
+// instruction cache of the main loop): sub-step 0 with this step's A x (f), the jump,
+// sub-step 1 with A Y_1 on the CUDA cores.  x holds X_k on entry and X_{k+1} on exit;
+// y1 receives the post-jump state for the jump log.
+__device__ __noinline__ float fwd32_one_jump(const KP32 &kp, const float *at, float *vcol, int k, uint32_t m,
+                                             const float *__restrict__ u, float *xio, const float *fin,
+                                             float *y1) {
+  float x[32], f[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    x[c] = xio[c];
+    f[c] = fin[c];
+  }
+  const float th =
+      Ar<float>::u01(philox10((uint32_t)k, m, (1u << 24) | (1u << 16), kp.epoch, kp.key0, kp.key1).x);
+  const float d0 = __fmul_rn(kp.dt, th), d1 = __fmul_rn(kp.dt, __fsub_rn(1.f, th));
+  add_main_noise_scaled(kp, k, m, __fsqrt_rn(d0), x);
+  add_drift(kp, u, k, d0, f, x);
+  add_slot0_words<true>(kp, k, m, 0.f, x);
+#pragma unroll
+  for (int c = 0; c < 32; ++c) y1[c] = x[c];
+  cc_matvec(at, vcol, x, f);
+  add_slot0_words<false>(kp, k, m, __fsqrt_rn(d1), x);
+  add_drift(kp, u, k, d1, f, x);
+#pragma unroll
+  for (int c = 0; c < 32; ++c) xio[c] = x[c];
+  return th;
+}
+
 template <int TC>
-__global__ void __launch_bounds__(TPB)
-fwd32_kernel(const __grid_constant__ KP32 kp, const float *__restrict__ u, const float *__restrict__ xd,
+__global__ void __launch_bounds__(TPB, 4)
+fwd32_kernel(const KP32 *__restrict__ kpg, const float *__restrict__ u, const float *__restrict__ xd,
              double *__restrict__ partC, float *__restrict__ traj, uint32_t *__restrict__ flags,
              float *__restrict__ pcost, JLog<float, D32> jl, int *__restrict__ jcnt, int *status,
              int64_t mloc) {
   constexpr bool SPLIT = TC == 2;
   __shared__ __align__(1024) TcShared sh;
+  __shared__ __align__(16) CcShared cs;
+  __shared__ __align__(16) float vbuf[32 * TPB];   // product staging (CUDA cores, jump sub-steps)
+  float *const vbuf_j = vbuf;
   __shared__ Pair<float> red[TPB / 32];
+  stage_params(cs, kpg);
+  const KP32 &kp = cs.kp;
   const int64_t lm = (int64_t)blockIdx.x * TPB + threadIdx.x;
   const bool active = lm < mloc;
   const uint32_t m = (uint32_t)(kp.m_begin + lm);
@@ -277,7 +442,7 @@ fwd32_kernel(const __grid_constant__ KP32 kp, const float *__restrict__ u, const
       tc_write_row<SPLIT>(sh.xhi, sh.xlo, threadIdx.x, x);
       if (!tc_issue<SPLIT>(sh)) break;
     } else {
-      cc_matvec(kp, x, f, false);
+      cc_matvec(cs.at, vbuf + threadIdx.x, x, f);
     }
     bool jump;
     const uint32_t w0 = main_noise_or_jump(kp, k, m, x, jump);   // x += noise unless jump
@@ -293,8 +458,25 @@ fwd32_kernel(const __grid_constant__ KP32 kp, const float *__restrict__ u, const
         for (int l = 0; l < DU32; ++l) bc = __fmaf_rn(kp.B[c * DU32 + l], uk[l], bc);
         x[c] = __fmaf_rn(kp.dt, __fadd_rn(f[c], bc), x[c]);
       }
+    } else if (kp.npair == 16 && (unsigned long long)w0 < kp.thr[1]) {
+      fw |= 1u << (k & 31);
+      float xl[32], fl[32], yl[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        xl[c] = x[c];
+        fl[c] = f[c];
+      }
+      const float th = fwd32_one_jump(kp, cs.at, vbuf_j + threadIdx.x, k, m, u, xl, fl, yl);
+      if (lw.fits(1)) {
+        float y[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) y[c] = yl[c];
+        lw.put(k, th, y);
+      }
+#pragma unroll
+      for (int c = 0; c < 32; ++c) x[c] = xl[c];
     } else {
-      // steps with jumps run on the CUDA cores through the generic routine (x is X_k)
+      // two or more jumps (rare): the generic routine on the CUDA cores (x is X_k)
       fw |= 1u << (k & 31);
       JumpStep<float, D32> S;
       float zl[32], ul[DU32], xl[32];
@@ -330,40 +512,64 @@ fwd32_kernel(const __grid_constant__ KP32 kp, const float *__restrict__ u, const
   if (TC) tc_teardown(sh);
 }
 
-// Backward through a step that had jumps (rare), out of line so that its register
-// needs do not weigh on the main loop: X_k is reloaded, the generic backward step runs on
-// the CUDA cores (jump log or regeneration), and the cost gradient at t_k is added.
-__device__ __noinline__ void adj32_jump_step(const KP32 &kp, int k, uint32_t m, const float *__restrict__ traj,
-                                             int64_t mloc, int64_t lmc, const float *__restrict__ u,
-                                             const float *__restrict__ xd, float *mu_io, float *g_out,
-                                             LogReader<float, D32> *lr) {
-  float xk[32], mu[32], g[DU32], th[D32 + 2];
+// Adjoint of a step with jumps (linear drift), out of line: sub-steps n..0 with the
+// Jacobian A; sub-step n uses this step's A^T lambda (t), earlier ones the CUDA cores.
+__device__ __noinline__ void adj32_jump_substeps(const KP32 &kp, float *vcol, int k, uint32_t m,
+                                                 LogReader<float, D32> *lr, float *muio, const float *tin,
+                                                 float *gout) {
+  float mu[32], t[32], g[DU32], th[NMAX];
 #pragma unroll
-  for (int c4 = 0; c4 < 8; ++c4) {
-    float v[4];
-    Vec4<float>::load(traj + (((size_t)k * 8 + c4) * mloc + lmc) * 4, v);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) xk[4 * c4 + q] = v[q];
+  for (int c = 0; c < 32; ++c) {
+    mu[c] = muio[c];
+    t[c] = tin[c];
   }
 #pragma unroll
-  for (int c = 0; c < 32; ++c) mu[c] = mu_io[c];
-  LogReader<float, D32> l = *lr;
-  backward_step<float, D32, DU32, false>(kp, k, m, true, xk, u, xd, mu, g, th, l);
-  *lr = l;
+  for (int l = 0; l < DU32; ++l) g[l] = 0.f;
+  int n = 0;
+  if (lr->has(k)) {
+    float tmp[32];
+    while (lr->has(k) && n < NMAX) {
+      lr->pop(th[n], tmp);
+      ++n;
+    }
+    for (int i = 0; i < n / 2; ++i) {   // popped latest first: reverse into time order
+      const float a = th[i];
+      th[i] = th[n - 1 - i];
+      th[n - 1 - i] = a;
+    }
+  } else {
+    const uint4 o0 = philox10((uint32_t)k, m, 0u, kp.epoch, kp.key0, kp.key1);
+    for (int i = 0; i < NMAX; ++i) n += ((unsigned long long)o0.x >= kp.thr[i]) ? 1 : 0;
+    regen_jump_times(kp, k, m, n, th);
+  }
+  float thn = 1.f;
+  for (int i = n; i >= 0; --i) {
+    const float the = i > 0 ? th[i - 1] : 0.f;
+    const float de = i > 0 ? __fmul_rn(kp.dt, __fsub_rn(thn, the)) : __fmul_rn(kp.dt, thn);
+    control_sensitivity(kp, mu, de, g);
+    if (i < n) cc_matvec(kp.A, vcol, mu, t);
 #pragma unroll
-  for (int c = 0; c < 32; ++c) mu_io[c] = mu[c];
+    for (int c = 0; c < 32; ++c) mu[c] = __fmaf_rn(de, t[c], mu[c]);
+    thn = the;
+  }
 #pragma unroll
-  for (int q = 0; q < DU32; ++q) g_out[q] = g[q];
+  for (int c = 0; c < 32; ++c) muio[c] = mu[c];
+#pragma unroll
+  for (int l = 0; l < DU32; ++l) gout[l] = g[l];
 }
 
 template <int TC>
-__global__ void __launch_bounds__(TPB)
-adj32_kernel(const __grid_constant__ KP32 kp, const float *__restrict__ u, const float *__restrict__ xd,
+__global__ void __launch_bounds__(TPB, 4)
+adj32_kernel(const KP32 *__restrict__ kpg, const float *__restrict__ u, const float *__restrict__ xd,
              const float *__restrict__ traj, const uint32_t *__restrict__ flags, JLog<float, D32> jl,
              const int *__restrict__ jcnt, double *__restrict__ partG, float *__restrict__ lam_out,
              int *status, int64_t mloc) {
   constexpr bool SPLIT = TC == 2;
   __shared__ __align__(1024) TcShared sh;
+  __shared__ __align__(16) CcShared cs;
+  __shared__ __align__(16) float vbuf[32 * TPB];   // product staging (CUDA cores, jump sub-steps)
+  stage_params(cs, kpg);
+  const KP32 &kp = cs.kp;
   const int64_t npart = (int64_t)kp.nblk * (TPB / 32);
   const int64_t wid = (int64_t)blockIdx.x * (TPB / 32) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
@@ -403,40 +609,48 @@ adj32_kernel(const __grid_constant__ KP32 kp, const float *__restrict__ u, const
       if (!tc_issue<SPLIT>(sh)) break;
     }
     const bool jumped = (__ldg(flags + (size_t)(k >> 5) * mloc + lmc) >> (k & 31)) & 1u;
+    if (k >= 2) {   // the next step's stored state, into L2 ahead of its use
+#pragma unroll
+      for (int c4 = 0; c4 < 8; ++c4)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(traj + (((size_t)(k - 1) * 8 + c4) * mloc + lmc) * 4));
+    }
     float t[32];
     if (TC)
       tc_collect(sh, (uint32_t)((Nt - 1 - k) & 1), t, status);
     else
-      cc_matvec(kp, mu, t, true);
+      cc_matvec(cs.kp.A, vbuf + threadIdx.x, mu, t);
     float g[DU32];
-    if (!jumped) {
 #pragma unroll
-      for (int l = 0; l < DU32; ++l) g[l] = 0.f;
+    for (int l = 0; l < DU32; ++l) g[l] = 0.f;
+    if (!jumped) {
       control_sensitivity(kp, mu, kp.dt, g);
 #pragma unroll
       for (int c = 0; c < 32; ++c) mu[c] = __fmaf_rn(kp.dt, t[c], mu[c]);
-      if (k >= 1) {
-        // cost gradient dt q (X_k - xd_k), the stored state streamed 4 components at a time
-#pragma unroll
-        for (int c4 = 0; c4 < 8; ++c4) {
-          float v[4];
-          Vec4<float>::load(traj + (((size_t)k * 8 + c4) * mloc + lmc) * 4, v);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int c = 4 * c4 + q;
-            mu[c] = __fmaf_rn(kp.qdt[c], __fsub_rn(v[q], __ldg(xd + (size_t)k * D32 + c)), mu[c]);
-          }
-        }
-      }
     } else {
-      float ml[32], gl[DU32];
+      float ml[32], tl[32], gl[DU32];
 #pragma unroll
-      for (int c = 0; c < 32; ++c) ml[c] = mu[c];
-      adj32_jump_step(kp, k, m, traj, mloc, lmc, u, xd, ml, gl, &lr);
+      for (int c = 0; c < 32; ++c) {
+        ml[c] = mu[c];
+        tl[c] = t[c];
+      }
+      adj32_jump_substeps(kp, vbuf + threadIdx.x, k, m, &lr, ml, tl, gl);
 #pragma unroll
       for (int c = 0; c < 32; ++c) mu[c] = ml[c];
 #pragma unroll
       for (int l = 0; l < DU32; ++l) g[l] = gl[l];
+    }
+    if (k >= 1) {
+      // cost gradient dt q (X_k - xd_k), the stored state streamed 4 components at a time
+#pragma unroll
+      for (int c4 = 0; c4 < 8; ++c4) {
+        float v[4];
+        Vec4<float>::load(traj + (((size_t)k * 8 + c4) * mloc + lmc) * 4, v);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int c = 4 * c4 + q;
+          mu[c] = __fmaf_rn(kp.qdt[c], __fsub_rn(v[q], __ldg(xd + (size_t)k * D32 + c)), mu[c]);
+        }
+      }
     }
     if (lam_out && active)
 #pragma unroll
