@@ -126,6 +126,8 @@ WORKLOADS = {
     "double_well": workloads.double_well,   # d=2 cubic, M=2^20, Nt=1000 (the headline)
     "linear32": workloads.linear32,         # d=32 linear, M=2^18, Nt=500
     "lq_scalar": workloads.lq_scalar,       # d=1 linear-quadratic, M=1000, Nt=100 (FP64)
+    # autograd form: J(u, theta) forward + backward, M=2^22, Nt=4096, checkpointed states
+    "double_well_autograd": workloads.double_well_autograd,
 }
 
 
@@ -200,9 +202,12 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     p = replica_problem(bench_workload(args.paths, args.steps_t, args.workload), rank)
+    if args.workload == "double_well_autograd":
+        return run_autograd(args, p, stream, dist, ws, rank, local)
     M, Nt, du = p.M, p.Nt, p.du
     prec = "fp64" if args.workload == "lq_scalar" else "fp32"
-    prob = jd.JdProblem(p, prec=prec, mode=args.variant, stream=stream, use_tensor_cores=args.tc)
+    prob = jd.JdProblem(p, prec=prec, mode=args.variant or "stored", stream=stream,
+                        use_tensor_cores=args.tc)
     n = Nt * du
     u = torch.zeros(n, dtype=torch.float64, device="cuda")
 
@@ -288,6 +293,190 @@ def run_ours(args):
     return 0
 
 
+def run_autograd(args, p, stream, dist, ws, rank, local):
+    """One step = J(u, theta) and its backward through the torch.autograd.Function
+    (jd_forward with checkpoints, then the recompute adjoint with parameter gradients)."""
+    import torch
+    import paper_2505_04328_gb300 as jd
+    from paper_2505_04328_gb300.autograd import JumpDiffusionCost
+    mode = args.variant or "recompute"
+    f = JumpDiffusionCost(p, rho0=0.5, mode=mode, stream=stream)
+    M, Nt, du = p.M, p.Nt, p.du
+    u = torch.tensor(workloads.random_control(p, seed=41, scale=0.5), dtype=torch.float64,
+                     device="cuda", requires_grad=True)
+    th = torch.tensor((0.5, 0.3, 0.2), dtype=torch.float64, requires_grad=True)
+
+    def step():
+        u.grad = None
+        th.grad = None
+        J = f(u, th)
+        J.backward()
+        return J
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    jd.profile_enable(True)
+    l0 = jd.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        J = step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = jd.launch_count() - l0
+    kstats = jd.profile_read()
+    jd.profile_enable(False)
+    clk = clocks.stop()
+    if dist is not None:
+        ms = max_over_ranks(dist, ms, device="cuda")
+    ms_per_step = ms / args.steps
+    value = ws * M * Nt / (ms_per_step * 1e-3)
+
+    # end to end: the control comes from pinned host memory each step; J, dJ/du and
+    # dJ/dtheta go back to the host
+    u_pin = torch.empty((Nt, du), dtype=torch.float64).pin_memory()
+    u_pin.copy_(u.detach().cpu())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ud = u_pin.to("cuda", non_blocking=True).requires_grad_(True)
+        th.grad = None
+        J = f(ud, th)
+        J.backward()
+        _ = (float(J), ud.grad.cpu(), th.grad.clone())
+    e2e_sec = (time.perf_counter() - t0) / args.steps
+    e2e = {"value": ws * M * Nt / e2e_sec, "unit": UNIT, "h2d_bytes_per_step": Nt * du * 8,
+           "d2h_bytes_per_step": 8 + Nt * du * 8 + 3 * 8}
+
+    peaks, peak_kind = _peaks()
+    rl = {k: kernel_roofline(k, v, p, peaks, peak_kind) for k, v in kstats.items() if k in KERNEL_BOUND}
+    dom = max(rl, key=lambda k: kstats[k][1]) if rl else None
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"double_well_autograd d=2 M={M} Nt={Nt}", "variant": mode,
+                       "theta": "(damping 0.5, sigma 0.3, jump half-width 0.2)",
+                       "step": "J(u, theta) forward + backward (dJ/du, dJ/dtheta) through the "
+                               "torch.autograd.Function",
+                       "l2": "inputs larger than L2: the %s buffers (%.2f GB) exceed the 129 MB "
+                             "L2; no flush" % (mode, f.problem.info()["device_bytes"] / 1e9)},
+            "gpu_launches": launches,
+            "kernels_ms_per_step": {k: v[1] / args.steps for k, v in kstats.items()},
+            "roofline": rl.get(dom), "roofline_all": rl, "e2e": e2e, "clocks": clk,
+            "J": float(J),
+        }
+        if not args.no_cpu_baseline:
+            import oracle
+            ps = p.replace(M=min(M, 2048))
+            t0 = time.perf_counter()
+            oracle.gradient(ps, u.detach().cpu().numpy(), theta=True)
+            sec = time.perf_counter() - t0
+            line["cpu_baseline"] = {"value": ps.M * ps.Nt / sec, "unit": UNIT,
+                                    "cores": oracle.default_threads(), "kind": "oracle",
+                                    "sample": f"{ps.M} of {M} paths, all {Nt} steps, one gradient "
+                                              "with parameter gradients"}
+        print(json.dumps(line), flush=True)
+    f.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_serving(args):
+    """Serving workload: requests of the serving stream (d in {1,2,8,32}, M log-uniform in
+    [2^12, 2^22], N_t in [50, 2000], lambda in [0.5, 10], Poisson arrivals) submitted at
+    their arrival times to one jd_server; each runs projected-gradient steps to a
+    relative projected-gradient norm of 1e-4 (at most --max-iter updates).  value =
+    gradient path-steps of all requests / makespan; latency = done - submit."""
+    import threading as th
+    import torch
+    import paper_2505_04328_gb300 as jd
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    jd.build()
+    reqs = workloads.serving_requests(n=args.requests, rate=args.rate, seed=5 + rank)
+    opt = dict(max_iter=args.max_iter, tol_rel_grad=1e-4)
+    srv = jd.JdServer(max_slots=args.slots)
+    tickets = [None] * len(reqs)
+
+    def submitter():
+        t0 = time.perf_counter()
+        for i, (ta, p) in enumerate(reqs):
+            dt = ta - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            tickets[i] = srv.submit(p, **opt)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = jd.launch_count()
+    t_start = time.perf_counter()
+    sub = th.Thread(target=submitter)
+    sub.start()
+    sub.join()
+    for t in tickets:
+        srv.wait(t)
+    wall = time.perf_counter() - t_start
+    launches = jd.launch_count() - l0
+    clk = clocks.stop()
+    infos = [srv.info(t) for t in tickets]
+    results = [srv.poll(t)[1] for t in tickets]
+    srv.close()
+    lat = np.array([i["done_s"] - i["submit_s"] for i in infos])
+    first = min(i["submit_s"] for i in infos)
+    makespan = max(i["done_s"] for i in infos) - first
+    steps = sum(i["path_steps"] for i in infos)
+    sweeps = sum(i["sweep_steps"] for i in infos)
+    ok = sum(1 for r in results if r["status"] == 0)
+    conv = sum(1 for r in results if r["status"] == 0 and r["rel_grad_norm"] <= 1e-4)
+
+    # the plain per-problem FP64 GPU form on a sample of the same requests (d <= 8; one
+    # request at a time, 3 optimizer iterations each): gradient path-steps / time
+    sample = [p for _, p in reqs if p.d <= 8][: args.plain_sample]
+    plain_steps, plain_t = 0, 0.0
+    for p in sample:
+        with jd.JdProblem(p, prec="fp64") as jp:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, r, _ = jp.optimize(np.zeros((p.Nt, p.du)), max_iter=3, tol_rel_grad=0.0)
+            plain_t += time.perf_counter() - t0
+            plain_steps += r["iters"] * p.M * p.Nt
+    plain = plain_steps / plain_t if plain_t > 0 else None
+    value = steps / makespan
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": len(reqs),
+        "warmup": 0, "ms_per_step": makespan * 1e3 / len(reqs), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"serving {len(reqs)} requests, Poisson arrivals {args.rate}/s, "
+                               "d in {1,2,8,32}, M log-uniform [2^12,2^22], Nt U[50,2000], lambda U[0.5,10]",
+                   "slots": args.slots, "max_iter": args.max_iter, "tol_rel_grad": 1e-4,
+                   "step": "one request (ms_per_step = makespan / requests)",
+                   "l2": "inputs larger than L2 for most requests; no flush"},
+        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                      "mean": float(lat.mean()), "max": float(lat.max())},
+        "makespan_s": makespan, "wall_s": wall, "requests_ok": ok, "requests_converged": conv,
+        "sweep_path_steps_per_s": sweeps / makespan,
+        "plain_fp64_gpu": {"value": plain, "unit": UNIT, "sample": f"{len(sample)} requests with d <= 8, "
+                                                                  "one at a time, 3 iterations each"},
+        "ratio_vs_plain_fp64": (value / plain) if plain else None,
+        "gpu_launches": launches, "roofline": None, "clocks": clk,
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+                "note": "requests enter and leave through host memory (jd_server_submit/poll)"},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def optimize_device(prob, u_t, iters, zeta0):
     """iters optimizer iterations (jd_optimize) on a device-resident control tensor."""
     import ctypes
@@ -369,8 +558,14 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--variant", default="stored", choices=["stored", "recompute", "auto"])
-    ap.add_argument("--workload", default="double_well", choices=sorted(WORKLOADS))
+    ap.add_argument("--variant", default=None, choices=["stored", "recompute", "auto"],
+                    help="adjoint plan (default: stored; recompute for double_well_autograd)")
+    ap.add_argument("--workload", default="double_well", choices=sorted(WORKLOADS) + ["serving"])
+    ap.add_argument("--requests", type=int, default=64, help="serving: requests from the stream")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: Poisson arrival rate (1/s)")
+    ap.add_argument("--slots", type=int, default=16, help="serving: requests in flight at most")
+    ap.add_argument("--max-iter", type=int, default=50, help="serving: optimizer updates at most")
+    ap.add_argument("--plain-sample", type=int, default=6, help="serving: requests timed in plain FP64")
     ap.add_argument("--tc", type=int, default=0, choices=[0, 1, 2],
                     help="tensor cores for the d=32 workload: 0 off, 1 BF16, 2 BF16x3")
     ap.add_argument("--paths", type=int, default=None, help="override M (paths per GPU)")
@@ -380,6 +575,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_ours(args)
 
 

@@ -138,6 +138,36 @@ jd_status jd_cost(jd_problem *p, const double *u, jd_memspace us, double *J);
 jd_status jd_gradient(jd_problem *p, const double *u, jd_memspace us, double *J, double *grad,
                       jd_memspace gs, double *grad_theta);
 
+/* jd_gradient split in two halves, for reverse-mode differentiation frameworks (the
+ * forward pass keeps what the backward pass needs, like an autograd graph).
+ *
+ * jd_forward: J(u) by the forward sweep in the problem's adjoint plan: STORED keeps X_k
+ *   and the post-jump states in device memory; RECOMPUTE keeps only the states at every
+ *   S-th step (S = 32 for d <= 2, 16 for d <= 8: about sqrt(Nt) checkpointing for
+ *   Nt ~ 10^3).  u: Nt*du in memory space us.  J: one double in memory space js, may be
+ *   NULL; with js = JD_MEM_DEVICE the call does not synchronize.
+ * jd_backward: the adjoint sweep and reductions for the u and coefficients of the last
+ *   jd_forward (or jd_gradient) on this problem: grad (Nt*du) and grad_theta (d+2
+ *   doubles, layout as in jd_gradient, may be NULL), both in memory space gs; bitwise
+ *   equal to jd_gradient's results.  With gs = JD_MEM_DEVICE the call does not
+ *   synchronize and non-finite results are not reported (check the outputs).
+ *   It may be called more than once after one forward.  Any other call on the problem
+ *   in between (jd_cost, jd_optimize, jd_sample_paths, jd_problem_update) discards the
+ *   forward; jd_backward then fails with INVALID_ARG.
+ * Errors: as jd_gradient. */
+jd_status jd_forward(jd_problem *p, const double *u, jd_memspace us, double *J, jd_memspace js);
+jd_status jd_backward(jd_problem *p, double *grad, jd_memspace gs, double *grad_theta);
+
+/* Replace the coefficients of a problem without reallocating its device buffers: A, C,
+ * B, dA, sigma, lambda, jump_law, jump_scale, x0, q, xd, nu, u_min, u_max, seed and
+ * epoch are taken from desc (host arrays, copied; validated as in jd_problem_create).
+ * d, du, T, Nt, M, drift, prec, mode and use_tensor_cores must equal the problem's
+ * (else INVALID_ARG); mem_budget_bytes and cuda_stream are ignored.  Used to move a
+ * parameter (drift coefficient, sigma, jump scale) between autograd evaluations, or
+ * the epoch word between resampled iterations (Sec. 5.6).  Synchronizes the stream
+ * only when the target xd changes.  Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
+jd_status jd_problem_update(jd_problem *p, const jd_problem_desc *desc);
+
 /* Trajectories of paths m0 .. m0+count-1 (host outputs, any may be NULL):
  * X (count, Nt+1, d) states on the uniform grid; lam (count, Nt+1, d) adjoint states
  * lambda_k = d(path cost)/dX_k; cost (count) per-path running cost.  Uses the same
@@ -178,6 +208,57 @@ jd_status jd_optimize(jd_problem *p, double *u_inout, jd_memspace us, const jd_o
  * adjoint variant in use (JD_ADJ_STORED or JD_ADJ_RECOMPUTE; JD_ADJ_AUTO before the
  * first evaluation). */
 jd_status jd_problem_info(const jd_problem *p, size_t *device_bytes, jd_adjoint_mode *mode);
+
+/* Device bytes a problem with this descriptor allocates under the given adjoint plan
+ * (JD_ADJ_STORED or JD_ADJ_RECOMPUTE): the buffers of jd_problem_create plus the plan's
+ * state storage.  Host arithmetic only; no device is touched.  Used for admission by
+ * HBM footprint.  Errors: INVALID_ARG (as jd_problem_create, or another plan),
+ * UNSUPPORTED (RECOMPUTE with d > 8). */
+jd_status jd_problem_footprint(const jd_problem_desc *desc, jd_adjoint_mode plan, size_t *bytes);
+
+/* Serving: a request loop that solves many optimal-control problems concurrently on
+ * the current device (the paper's method, Algorithm 5.4, once per request).
+ *
+ * jd_server_create: hbm_budget = device bytes the server may hold for admitted
+ *   requests (0 = 80% of the free memory); max_slots = requests in flight at most
+ *   (1..256).  One worker thread owns the device work; every slot has its own stream.
+ * jd_server_submit: copies the descriptor (host arrays) and the optimizer parameters
+ *   and queues the request; returns at once with a ticket.  The control starts at
+ *   u = 0 projected into [u_min, u_max]; cuda_stream and mem_budget_bytes are ignored
+ *   (the server assigns them); mode AUTO lets the server pick the plan.  Validation
+ *   errors are returned here (as jd_problem_create).
+ * Admission: in arrival order, a request starts when a slot is free and its footprint
+ *   (jd_problem_footprint) fits the free budget; AUTO picks STORED when that plan fits
+ *   a quarter of the budget, else RECOMPUTE (d <= 8).  A request that cannot fit even
+ *   an empty server finishes with status OOM; later requests may overtake one that is
+ *   waiting for memory.
+ * Execution: each request runs jd_optimize's kernels and host decisions on its own
+ *   buffers and stream, so its result is bitwise the same as a solo jd_optimize with
+ *   u0 = 0, whatever else runs; the kernels of all active requests overlap.
+ * jd_server_poll: JD_ERR_BUSY while the request runs; then JD_OK with r (the request's
+ *   own status in r->status) and, if u_out is not NULL, the final control (Nt*du host
+ *   doubles), which is handed out once (a second poll with u_out fails with INVALID_ARG).
+ * jd_server_wait: blocks until the request is done or timeout_s seconds pass (BUSY).
+ * jd_server_info: times in seconds since the server was created (admit_s, done_s are
+ *   -1 until they happen), bytes and plan of the admitted request, its gradient
+ *   path-steps (M*Nt per gradient evaluation: forward + adjoint sweep) and its sweep
+ *   path-steps (M*Nt per evaluation, line-search cost sweeps included).
+ * jd_server_destroy: cancels requests not yet admitted (status INVALID_ARG), waits for
+ *   the running ones, frees everything. */
+typedef struct jd_server jd_server;
+typedef struct {
+  double submit_s, admit_s, done_s;
+  size_t device_bytes;
+  jd_adjoint_mode plan;
+  int done;
+  int64_t path_steps, sweep_steps;
+} jd_request_info;
+jd_status jd_server_create(size_t hbm_budget, int max_slots, jd_server **s);
+jd_status jd_server_submit(jd_server *s, const jd_problem_desc *d, const jd_opt_params *o, uint64_t *ticket);
+jd_status jd_server_poll(jd_server *s, uint64_t ticket, double *u_out, jd_opt_result *r);
+jd_status jd_server_wait(jd_server *s, uint64_t ticket, double timeout_s);
+jd_status jd_server_info(jd_server *s, uint64_t ticket, jd_request_info *info);
+jd_status jd_server_destroy(jd_server *s);
 
 /* Number of kernels this library has launched in this process (monotone counter). */
 uint64_t jd_kernel_launch_count(void);

@@ -23,12 +23,16 @@ JD_ERR_LINESEARCH, JD_ERR_TIMEOUT, JD_ERR_UNSUPPORTED, JD_ERR_BUSY = 5, 6, 7, 8
 JD_FP32, JD_FP64 = 0, 1
 JD_ADJ_AUTO, JD_ADJ_STORED, JD_ADJ_RECOMPUTE = 0, 1, 2
 JD_MEM_HOST, JD_MEM_DEVICE = 0, 1
+_CUDA_STREAM_LEGACY = 0x1   # cudaStreamLegacy
 
 # Every function declared in include/jd.h.
 ABI_SYMBOLS = (
     "jd_problem_create", "jd_problem_destroy", "jd_cost", "jd_gradient", "jd_sample_paths",
+    "jd_forward", "jd_backward", "jd_problem_update",
     "jd_optimize", "jd_problem_info", "jd_kernel_launch_count", "jd_profile_enable",
-    "jd_profile_read", "jd_cost_noalloc", "jd_status_string", "jd_last_error",
+    "jd_profile_read", "jd_cost_noalloc", "jd_problem_footprint", "jd_server_create",
+    "jd_server_submit", "jd_server_poll", "jd_server_wait", "jd_server_info", "jd_server_destroy",
+    "jd_status_string", "jd_last_error",
 )
 
 
@@ -69,6 +73,12 @@ class OptResult(ctypes.Structure):
                 ("status", ctypes.c_int)]
 
 
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double), ("done_s", ctypes.c_double),
+                ("device_bytes", ctypes.c_size_t), ("plan", ctypes.c_int), ("done", ctypes.c_int),
+                ("path_steps", ctypes.c_int64), ("sweep_steps", ctypes.c_int64)]
+
+
 def library_path() -> str:
     return _LIB_PATH
 
@@ -90,10 +100,20 @@ def lib():
         L.jd_problem_destroy.argtypes = [vp]
         L.jd_cost.argtypes = [vp, dp, ctypes.c_int, P(ctypes.c_double)]
         L.jd_gradient.argtypes = [vp, dp, ctypes.c_int, dp, dp, ctypes.c_int, dp]
+        L.jd_forward.argtypes = [vp, dp, ctypes.c_int, dp, ctypes.c_int]
+        L.jd_backward.argtypes = [vp, dp, ctypes.c_int, dp]
+        L.jd_problem_update.argtypes = [vp, P(ProblemDesc)]
         L.jd_sample_paths.argtypes = [vp, dp, ctypes.c_int, i64, i64, dp, dp, dp]
         L.jd_optimize.argtypes = [vp, dp, ctypes.c_int, P(OptParams), P(OptResult), dp]
         L.jd_problem_info.argtypes = [vp, P(ctypes.c_size_t), P(ctypes.c_int)]
         L.jd_cost_noalloc.argtypes = [P(ProblemDesc), dp, dp]
+        L.jd_problem_footprint.argtypes = [P(ProblemDesc), ctypes.c_int, P(ctypes.c_size_t)]
+        L.jd_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int, P(ctypes.c_void_p)]
+        L.jd_server_submit.argtypes = [vp, P(ProblemDesc), P(OptParams), P(ctypes.c_uint64)]
+        L.jd_server_poll.argtypes = [vp, ctypes.c_uint64, dp, P(OptResult)]
+        L.jd_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_double]
+        L.jd_server_info.argtypes = [vp, ctypes.c_uint64, P(RequestInfo)]
+        L.jd_server_destroy.argtypes = [vp]
         L.jd_kernel_launch_count.restype = ctypes.c_uint64
         L.jd_profile_enable.argtypes = [ctypes.c_int]
         L.jd_profile_enable.restype = None
@@ -164,6 +184,37 @@ _MODE = {"auto": JD_ADJ_AUTO, "stored": JD_ADJ_STORED, "recompute": JD_ADJ_RECOM
          JD_ADJ_AUTO: JD_ADJ_AUTO, JD_ADJ_STORED: JD_ADJ_STORED, JD_ADJ_RECOMPUTE: JD_ADJ_RECOMPUTE}
 
 
+def make_desc(problem, prec=JD_FP32, mode=JD_ADJ_AUTO, use_tensor_cores=0, mem_budget_bytes=0,
+              stream_handle=None):
+    """(ProblemDesc, arrays): the descriptor of a workloads Problem and the float64
+    arrays it points to (keep them alive while the descriptor is in use)."""
+    d = problem.d
+    C = problem.C if problem.C is not None else np.zeros((d, d))
+    a = dict(
+        A=_f64(problem.A).reshape(-1), C=_f64(C).reshape(-1), B=_f64(problem.B).reshape(-1),
+        dA=None if problem.dA is None else _f64(problem.dA).reshape(-1),
+        sigma=_f64(problem.sigma).reshape(-1), x0=_f64(problem.x0).reshape(-1),
+        q=_f64(problem.q).reshape(-1), xd=_f64(problem.xd).reshape(-1))
+    desc = ProblemDesc(
+        d=d, du=problem.du, T=float(problem.T), Nt=problem.Nt, M=problem.M, drift=int(problem.drift),
+        A=_ptr(a["A"]), C=_ptr(a["C"]), B=_ptr(a["B"]), dA=_ptr(a["dA"]), sigma=_ptr(a["sigma"]),
+        lam=float(problem.lam), jump_law=int(problem.jump_law), jump_scale=float(problem.jump_scale),
+        x0=_ptr(a["x0"]), q=_ptr(a["q"]), xd=_ptr(a["xd"]), nu=float(problem.nu),
+        u_min=float(problem.u_min), u_max=float(problem.u_max), seed=int(problem.seed),
+        epoch=int(problem.epoch), prec=_PREC[prec], mode=_MODE[mode],
+        use_tensor_cores=int(use_tensor_cores), mem_budget_bytes=int(mem_budget_bytes),
+        cuda_stream=stream_handle)
+    return desc, a
+
+
+def footprint(problem, plan="stored", prec="fp32") -> int:
+    """Device bytes of ``problem`` under an adjoint plan (jd_problem_footprint; no GPU)."""
+    desc, _keep = make_desc(problem, prec=prec)
+    b = ctypes.c_size_t()
+    _check(lib().jd_problem_footprint(ctypes.byref(desc), _MODE[plan], ctypes.byref(b)), "jd_problem_footprint")
+    return b.value
+
+
 class JdProblem:
     """One problem on the current CUDA device (see jd_problem_create).
 
@@ -178,27 +229,57 @@ class JdProblem:
                  use_tensor_cores: int = 0):
         self.p = problem
         self.Nt, self.du, self.d, self.M = problem.Nt, problem.du, problem.d, problem.M
-        d = problem.d
-        C = problem.C if problem.C is not None else np.zeros((d, d))
-        self._arrays = dict(
-            A=_f64(problem.A).reshape(-1), C=_f64(C).reshape(-1), B=_f64(problem.B).reshape(-1),
-            dA=None if problem.dA is None else _f64(problem.dA).reshape(-1),
-            sigma=_f64(problem.sigma).reshape(-1), x0=_f64(problem.x0).reshape(-1),
-            q=_f64(problem.q).reshape(-1), xd=_f64(problem.xd).reshape(-1))
-        a = self._arrays
         self.stream_handle = self._stream(stream)
-        self.desc = ProblemDesc(
-            d=d, du=problem.du, T=float(problem.T), Nt=problem.Nt, M=problem.M, drift=int(problem.drift),
-            A=_ptr(a["A"]), C=_ptr(a["C"]), B=_ptr(a["B"]), dA=_ptr(a["dA"]), sigma=_ptr(a["sigma"]),
-            lam=float(problem.lam), jump_law=int(problem.jump_law), jump_scale=float(problem.jump_scale),
-            x0=_ptr(a["x0"]), q=_ptr(a["q"]), xd=_ptr(a["xd"]), nu=float(problem.nu),
-            u_min=float(problem.u_min), u_max=float(problem.u_max), seed=int(problem.seed),
-            epoch=int(problem.epoch), prec=_PREC[prec], mode=_MODE[mode],
-            use_tensor_cores=int(use_tensor_cores), mem_budget_bytes=int(mem_budget),
-            cuda_stream=self.stream_handle)
+        self._opts = dict(prec=prec, mode=mode, use_tensor_cores=int(use_tensor_cores),
+                          mem_budget_bytes=int(mem_budget))
+        self.desc = self._make_desc(problem)
         h = ctypes.c_void_p()
         _check(lib().jd_problem_create(ctypes.byref(self.desc), ctypes.byref(h)), "jd_problem_create")
         self.h = h
+
+    def _make_desc(self, problem) -> ProblemDesc:
+        """Descriptor of ``problem``; the arrays it points to are kept in self._arrays."""
+        desc, self._arrays = make_desc(problem, stream_handle=self.stream_handle, **self._opts)
+        return desc
+
+    def update(self, problem):
+        """Move the problem's coefficients to those of ``problem`` (jd_problem_update);
+        sizes, drift family and precision must not change."""
+        desc = self._make_desc(problem)
+        _check(lib().jd_problem_update(self.h, ctypes.byref(desc)), "jd_problem_update")
+        self.p, self.desc = problem, desc
+
+    def forward_into(self, u, J_out=None):
+        """jd_forward: forward sweep keeping the adjoint plan's states.  J_out: a CUDA
+        float64 tensor with one element (written in stream order, no synchronization),
+        or None to return J as a float (synchronizes)."""
+        up, us, _keep = _u_arg(u, self.n)
+        if J_out is None:
+            J = ctypes.c_double()
+            _check(lib().jd_forward(self.h, up, us, ctypes.byref(J), JD_MEM_HOST), "jd_forward")
+            return J.value
+        if not (_is_torch(J_out) and J_out.is_cuda and J_out.numel() == 1):
+            raise ValueError("J_out must be a CUDA tensor with one element")
+        _check(lib().jd_forward(self.h, up, us, ctypes.c_void_p(J_out.data_ptr()), JD_MEM_DEVICE),
+               "jd_forward")
+        return None
+
+    def backward_into(self, grad_out, theta_out=None):
+        """jd_backward into CUDA float64 tensors grad_out (Nt*du) and theta_out (d+2) or
+        None; does not synchronize."""
+        for t, n in ((grad_out, self.n), (theta_out, self.d + 2)):
+            if t is not None and not (_is_torch(t) and t.is_cuda and t.is_contiguous() and t.numel() == n):
+                raise ValueError(f"outputs must be contiguous CUDA float64 tensors of {n} entries")
+        _check(lib().jd_backward(self.h, ctypes.c_void_p(grad_out.data_ptr()), JD_MEM_DEVICE,
+                                 None if theta_out is None else ctypes.c_void_p(theta_out.data_ptr())),
+               "jd_backward")
+
+    def backward(self, theta: bool = False):
+        """jd_backward to host memory: (grad (Nt, du), grad_theta (d+2) or None)."""
+        g = np.zeros((self.Nt, self.du))
+        gth = np.zeros(self.d + 2) if theta else None
+        _check(lib().jd_backward(self.h, _ptr(g), JD_MEM_HOST, _ptr(gth)), "jd_backward")
+        return g, gth
 
     @staticmethod
     def _stream(stream):
@@ -206,13 +287,16 @@ class JdProblem:
             try:
                 import torch
                 if torch.cuda.is_available():
-                    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+                    stream = torch.cuda.current_stream()
             except ImportError:
                 pass
-            return None
-        if isinstance(stream, int):
-            return ctypes.c_void_p(stream)
-        return ctypes.c_void_p(stream.cuda_stream)
+            if stream is None:
+                return None
+        handle = stream if isinstance(stream, int) else stream.cuda_stream
+        # torch's default stream has handle 0, which the C ABI reads as "make a private
+        # stream": pass the legacy default stream (cudaStreamLegacy) instead, so the
+        # library's work stays ordered with torch's on that stream
+        return ctypes.c_void_p(handle if handle else _CUDA_STREAM_LEGACY)
 
     @property
     def n(self) -> int:
@@ -294,3 +378,71 @@ class JdProblem:
         m = ctypes.c_int()
         _check(lib().jd_problem_info(self.h, ctypes.byref(b), ctypes.byref(m)), "jd_problem_info")
         return dict(device_bytes=b.value, mode={0: "auto", 1: "stored", 2: "recompute"}[m.value])
+
+
+class JdServer:
+    """The serving loop (jd_server_*): submit problems, poll results.
+
+    ``budget``: device bytes for admitted requests (0 = 80% of free memory);
+    ``max_slots``: requests in flight at most."""
+
+    def __init__(self, budget: int = 0, max_slots: int = 16):
+        h = ctypes.c_void_p()
+        _check(lib().jd_server_create(int(budget), int(max_slots), ctypes.byref(h)), "jd_server_create")
+        self.h = h
+        self._shapes = {}
+
+    def submit(self, problem, prec="fp32", mode="auto", use_tensor_cores=0, max_iter=200,
+               tol_rel_grad=1e-4, tol_step=0.0, armijo_c=1e-4, zeta0=1.0, zeta_max=1e3,
+               max_backtracks=40) -> int:
+        desc, _keep = make_desc(problem, prec=prec, mode=mode, use_tensor_cores=use_tensor_cores)
+        o = OptParams(max_iter=max_iter, tol_rel_grad=tol_rel_grad, tol_step=tol_step,
+                      armijo_c=armijo_c, zeta0=zeta0, zeta_max=zeta_max, max_backtracks=max_backtracks)
+        t = ctypes.c_uint64()
+        _check(lib().jd_server_submit(self.h, ctypes.byref(desc), ctypes.byref(o), ctypes.byref(t)),
+               "jd_server_submit")
+        self._shapes[t.value] = (problem.Nt, problem.du)
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while running; then (u (Nt, du), result dict)."""
+        Nt, du = self._shapes[ticket]
+        u = np.zeros((Nt, du))
+        r = OptResult()
+        st = lib().jd_server_poll(self.h, ticket, _ptr(u), ctypes.byref(r))
+        if st == JD_ERR_BUSY:
+            return None
+        _check(st, "jd_server_poll")
+        return u, dict(iters=r.iters, evals=r.evals, status=r.status, J=r.J,
+                       rel_grad_norm=r.rel_grad_norm, zeta=r.zeta)
+
+    def wait(self, ticket: int, timeout: float = 0.0) -> bool:
+        st = lib().jd_server_wait(self.h, ticket, float(timeout))
+        if st == JD_ERR_BUSY:
+            return False
+        _check(st, "jd_server_wait")
+        return True
+
+    def info(self, ticket: int):
+        i = RequestInfo()
+        _check(lib().jd_server_info(self.h, ticket, ctypes.byref(i)), "jd_server_info")
+        return dict(submit_s=i.submit_s, admit_s=i.admit_s, done_s=i.done_s, device_bytes=i.device_bytes,
+                    plan={0: "auto", 1: "stored", 2: "recompute"}[i.plan], done=bool(i.done),
+                    path_steps=i.path_steps, sweep_steps=i.sweep_steps)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().jd_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -4,10 +4,12 @@
 namespace jd {
 
 // Coefficients go to the problem's device buffer (stream ordered) for the kernels to stage.
-static cudaError_t upload_kp(const jd_problem *p, int64_t m_begin, int64_t mloc, cudaStream_t s, KP32 **dev) {
+static cudaError_t upload_kp(const jd_problem *p, int64_t m_begin, int64_t mloc, const PathBufs &b,
+                             cudaStream_t s, KP32 **dev) {
   if (!p->kp_dev) return cudaErrorInvalidValue;
   auto *kp = new KP32();
   make_kparams<float, D32, DU32>(p, m_begin, mloc, *kp);
+  if (b.npart) kp->npart = b.npart;
   const cudaError_t e = cudaMemcpyAsync(p->kp_dev, kp, sizeof(KP32), cudaMemcpyHostToDevice, s);
   delete kp;   // pageable source: the copy is staged before cudaMemcpyAsync returns
   *dev = static_cast<KP32 *>(p->kp_dev);
@@ -18,7 +20,7 @@ static cudaError_t op32_fwd(const jd_problem *p, int mode, int64_t m_begin, int6
                             const PathBufs &b, cudaStream_t s) {
   if (mode == FWD_CKPT) return cudaErrorNotSupported;
   KP32 *kp = nullptr;
-  const cudaError_t ue = upload_kp(p, m_begin, mloc, s, &kp);
+  const cudaError_t ue = upload_kp(p, m_begin, mloc, b, s, &kp);
   if (ue != cudaSuccess) return ue;
   const dim3 grid((unsigned)ceil_div(mloc, TPB));
   const float *u = static_cast<const float *>(uk);
@@ -45,7 +47,7 @@ static cudaError_t op32_adj(const jd_problem *p, int variant, bool theta, int64_
                             const void *uk, const PathBufs &b, cudaStream_t s) {
   if (variant != ADJ_STORED_V || theta) return cudaErrorNotSupported;
   KP32 *kp = nullptr;
-  const cudaError_t ue = upload_kp(p, m_begin, mloc, s, &kp);
+  const cudaError_t ue = upload_kp(p, m_begin, mloc, b, s, &kp);
   if (ue != cudaSuccess) return ue;
   const dim3 grid((unsigned)ceil_div(mloc, TPB));
   const float *u = static_cast<const float *>(uk);

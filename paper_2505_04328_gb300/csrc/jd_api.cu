@@ -2,6 +2,7 @@
 // plan, launch sequencing, FP64 finalize kernels and the device-side Armijo test.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -259,7 +260,7 @@ static jd_status cuda_fail(cudaError_t e, const char *what) {
 
 // Scalar slots in p->scal_d
 enum { S_J = 0, S_JT = 1, S_DOT = 2, S_PG = 3, S_ACC = 4, S_STEP = 5, S_STATUS = 6, S_BAD = 7, S_THETA = 8 };
-constexpr int NSCAL = 8 + 34;
+constexpr int NSCAL = kScalars;
 
 static bool finite_all(const double *a, size_t n) {
   for (size_t i = 0; i < n; ++i)
@@ -269,20 +270,21 @@ static bool finite_all(const double *a, size_t n) {
 
 static size_t elem_size(const jd_problem *p) { return p->desc.prec == JD_FP64 ? 8 : 4; }
 
-static void free_dev(void *&ptr) {
-  if (ptr) cudaFree(ptr);
-  ptr = nullptr;
-}
 template <typename T>
-static void free_dev(T *&ptr) {
-  if (ptr) cudaFree(ptr);
+static void free_dev(const jd_problem *p, T *&ptr) {
+  if (ptr) {
+    if (p->async_alloc)
+      cudaFreeAsync((void *)ptr, p->stream);
+    else
+      cudaFree((void *)ptr);
+  }
   ptr = nullptr;
 }
 
 static jd_status dev_alloc(jd_problem *p, void **ptr, size_t bytes, const char *what) {
   if (p->bytes + bytes > p->budget)
     return fail(JD_ERR_OOM, std::string("memory budget exceeded allocating ") + what);
-  cudaError_t e = cudaMalloc(ptr, bytes);
+  cudaError_t e = p->async_alloc ? cudaMallocAsync(ptr, bytes, p->stream) : cudaMalloc(ptr, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(JD_ERR_OOM, std::string("cudaMalloc failed for ") + what + ": " + cudaGetErrorString(e));
@@ -302,15 +304,17 @@ static int log_capacity(const jd_problem_desc &q) {
   return (int)c;
 }
 
-static size_t log_bytes(const jd_problem *p, int64_t M, int cap) {
-  return (size_t)cap * M * (2 + p->D) * elem_size(p) + (size_t)M * 4;
+// Bytes of the stored plan for M paths: states, jump flags, jump log (at least one
+// record per path is allocated) and the per-path log counts.
+static size_t stored_plan_bytes(const jd_problem_desc &q, int D, size_t es, int64_t M) {
+  const int cap = log_capacity(q);
+  const size_t capa = (size_t)(cap > 0 ? cap : 1);
+  return (size_t)((q.Nt + 4) / 4) * D * M * 4 * es + (size_t)ceil_div(q.Nt, 32) * M * 4 +
+         capa * M * 2 * es + capa * M * D * es + (size_t)M * 4;
 }
 
 static size_t stored_bytes(const jd_problem *p) {
-  const int64_t M = p->desc.M;
-  const int Nt = p->desc.Nt;
-  return (size_t)((Nt + 4) / 4) * p->D * M * 4 * elem_size(p) + (size_t)ceil_div(Nt, 32) * M * 4 +
-         log_bytes(p, M, log_capacity(p->desc));
+  return stored_plan_bytes(p->desc, p->D, elem_size(p), p->desc.M);
 }
 
 static PathBufs plan_bufs(const jd_problem *p) {
@@ -334,6 +338,13 @@ static size_t recompute_bytes(const jd_problem *p) {
   return (size_t)(nseg + 1) * p->D * p->desc.M * elem_size(p);
 }
 
+// Buffers jd_problem_create allocates (the ALLOC list there).
+static size_t base_bytes(const jd_problem_desc &q, int D, int DU, size_t es) {
+  const size_t nu = (size_t)q.Nt * q.du, nblk = (size_t)ceil_div(q.M, TPB);
+  return (size_t)q.Nt * DU * es + (size_t)(q.Nt + 1) * D * es + 4 * nu * 8 + NSCAL * 8 + nblk * 8 +
+         (size_t)q.Nt * DU * grad_parts(q.M) * 8 + (size_t)(D + 2) * nblk * 8 + (D == 32 ? 16384 : 0);
+}
+
 // Allocate the trajectory or checkpoint buffers on first use.
 static jd_status ensure_plan(jd_problem *p) {
   if (p->plan != JD_ADJ_AUTO) return JD_OK;
@@ -346,7 +357,18 @@ static jd_status ensure_plan(jd_problem *p) {
   if (want == JD_ADJ_AUTO)
     want = (p->bytes + stored_bytes(p) <= p->budget) ? JD_ADJ_STORED : JD_ADJ_RECOMPUTE;
   if (want == JD_ADJ_STORED) {
-    const int64_t M = p->desc.M;
+    int64_t M = p->desc.M;
+    if (p->D == 32 && p->bytes + stored_bytes(p) > p->budget) {
+      // no recompute adjoint at d = 32: store the paths block by block, the largest
+      // multiple of 128 paths whose states fit what is left of the budget
+      const size_t avail = p->budget > p->bytes ? p->budget - p->bytes : 0;
+      const size_t per128 = stored_plan_bytes(p->desc, p->D, elem_size(p), TPB);
+      int64_t c = (int64_t)(avail / per128) * TPB;
+      while (c >= TPB && stored_plan_bytes(p->desc, p->D, elem_size(p), c) > avail) c -= TPB;
+      if (c < TPB) return fail(JD_ERR_OOM, "the memory budget does not hold the states of 128 paths");
+      p->chunk = c;
+      M = c;
+    }
     jd_status s = dev_alloc(p, &p->traj, (size_t)((p->desc.Nt + 4) / 4) * p->D * M * 4 * elem_size(p),
                             "trajectory");
     if (s) return s;
@@ -426,6 +448,7 @@ static jd_status run_cost(jd_problem *p, const double *ud, int slot) {
 static jd_status run_plan_forward(jd_problem *p, const double *ud, int slot) {
   jd_status s = ensure_plan(p);
   if (s) return s;
+  if (p->chunk) return run_cost(p, ud, slot);   // block-wise stored plan: nothing to keep
   s = prep_u(p, ud);
   if (s) return s;
   const PathBufs b = plan_bufs(p);
@@ -451,7 +474,26 @@ static jd_status run_gradient(jd_problem *p, const double *ud, bool theta, bool 
     s = prep_u(p, ud);
     if (s) return s;
   }
-  if (p->plan == JD_ADJ_STORED) {
+  if (p->plan == JD_ADJ_STORED && p->chunk) {
+    // block-wise stored plan: forward and adjoint per block of paths; the blocks write
+    // their cost and gradient partials at their global positions, so the reductions
+    // see the same partials as one launch over all paths
+    for (int64_t c0 = 0; c0 < M && e1 == cudaSuccess; c0 += p->chunk) {
+      const int64_t cn = std::min(p->chunk, M - c0);
+      PathBufs bc = b;
+      bc.partC = b.partC + c0 / TPB;
+      bc.partG = b.partG + c0 / 32;
+      bc.npart = grad_parts(M);
+      int pr = prof_begin(KC_FWD_STORE, p->stream);
+      e1 = p->ops->fwd(p, FWD_STORE, c0, cn, p->uk, bc, p->stream);
+      prof_end(pr, p->stream);
+      if (e1 != cudaSuccess) break;
+      pr = prof_begin(KC_ADJ_STORED, p->stream);
+      e1 = p->ops->adj(p, ADJ_STORED_V, theta, c0, cn, p->uk, bc, p->stream);
+      prof_end(pr, p->stream);
+    }
+    e2 = cudaSuccess;
+  } else if (p->plan == JD_ADJ_STORED) {
     if (!forward_done) {
       const int pr = prof_begin(KC_FWD_STORE, p->stream);
       e1 = p->ops->fwd(p, FWD_STORE, 0, M, p->uk, b, p->stream);
@@ -526,6 +568,195 @@ static jd_status set_device(const jd_problem *p) {
   return JD_OK;
 }
 
+// Padded target in kernel precision, p->xd -> p->xdk, in stream order; returns after
+// the copy has completed (the staging vector is local).
+static cudaError_t upload_target(jd_problem *p) {
+  const jd_problem_desc &q = p->desc;
+  std::vector<double> xdp((size_t)(q.Nt + 1) * p->D, 0.0);
+  for (int k = 0; k <= q.Nt; ++k)
+    for (int c = 0; c < q.d; ++c) xdp[(size_t)k * p->D + c] = p->xd[(size_t)k * q.d + c];
+  std::vector<float> xf;
+  const void *src = xdp.data();
+  size_t bytes = xdp.size() * 8;
+  if (q.prec == JD_FP32) {
+    xf.assign(xdp.begin(), xdp.end());
+    src = xf.data();
+    bytes = xf.size() * 4;
+  }
+  cudaError_t e = cudaMemcpyAsync(p->xdk, src, bytes, cudaMemcpyHostToDevice, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  return e;
+}
+
+// Checks of jd_problem_create, shared with jd_problem_update.
+static jd_status validate_desc(const jd_problem_desc &q) {
+  if (q.d < 1 || q.du < 1) return fail(JD_ERR_INVALID_ARG, "d and du must be >= 1");
+  if (q.d > 32) return fail(JD_ERR_UNSUPPORTED, "d > 32 is not compiled");
+  if (q.d > 8 && (q.prec != JD_FP32 || q.drift != JD_DRIFT_LINEAR))
+    return fail(JD_ERR_UNSUPPORTED, "8 < d <= 32 is built for FP32 paths with a linear drift only");
+  if (q.du > 4) return fail(JD_ERR_UNSUPPORTED, "du > 4 is not compiled");
+  if (q.Nt < 1 || q.Nt > (1 << 24)) return fail(JD_ERR_INVALID_ARG, "Nt must be in [1, 2^24]");
+  if (q.M < 1 || q.M > 0xFFFFFFFFll) return fail(JD_ERR_INVALID_ARG, "M must be in [1, 2^32 - 1]");
+  if (!(q.T > 0.0) || !std::isfinite(q.T)) return fail(JD_ERR_INVALID_ARG, "T must be finite and > 0");
+  if (q.drift != JD_DRIFT_LINEAR && q.drift != JD_DRIFT_CUBIC) return fail(JD_ERR_INVALID_ARG, "bad drift");
+  if (q.jump_law < JD_JUMP_NONE || q.jump_law > JD_JUMP_UNIFORM) return fail(JD_ERR_INVALID_ARG, "bad jump law");
+  if (q.prec != JD_FP32 && q.prec != JD_FP64) return fail(JD_ERR_INVALID_ARG, "bad precision");
+  if (q.mode < JD_ADJ_AUTO || q.mode > JD_ADJ_RECOMPUTE) return fail(JD_ERR_INVALID_ARG, "bad adjoint mode");
+  if (!q.A || !q.B || !q.sigma || !q.x0 || !q.q || !q.xd)
+    return fail(JD_ERR_INVALID_ARG, "A, B, sigma, x0, q, xd must be non-NULL");
+  if (q.drift == JD_DRIFT_CUBIC && !q.C) return fail(JD_ERR_INVALID_ARG, "C must be non-NULL for CUBIC");
+  if (!(q.lambda >= 0.0) || !std::isfinite(q.lambda)) return fail(JD_ERR_INVALID_ARG, "lambda must be finite and >= 0");
+  if (!(q.jump_scale >= 0.0) || !std::isfinite(q.jump_scale))
+    return fail(JD_ERR_INVALID_ARG, "jump_scale must be finite and >= 0");
+  if (!std::isfinite(q.nu) || q.nu < 0.0) return fail(JD_ERR_INVALID_ARG, "nu must be finite and >= 0");
+  if (!(q.u_min <= q.u_max)) return fail(JD_ERR_INVALID_ARG, "u_min must be <= u_max");
+  if (q.use_tensor_cores < 0 || q.use_tensor_cores > 2)
+    return fail(JD_ERR_INVALID_ARG, "use_tensor_cores must be 0, 1 (BF16) or 2 (BF16 x3)");
+  if (q.use_tensor_cores && q.d <= 8)
+    return fail(JD_ERR_UNSUPPORTED, "tensor cores are used for 8 < d <= 32 (linear drift, FP32)");
+  const size_t dd = (size_t)q.d * q.d, dn = (size_t)(q.Nt + 1) * q.d;
+  if (!finite_all(q.A, dd) || !finite_all(q.B, (size_t)q.d * q.du) || !finite_all(q.sigma, q.d) ||
+      !finite_all(q.x0, q.d) || !finite_all(q.q, q.d) || !finite_all(q.xd, dn) ||
+      (q.drift == JD_DRIFT_CUBIC && !finite_all(q.C, dd)) || (q.dA && !finite_all(q.dA, dd)))
+    return fail(JD_ERR_INVALID_ARG, "a coefficient array has a non-finite entry");
+
+  return JD_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Optimizer state machine (Algorithm 5.4, eq:Stochastic_Armijo)
+// ---------------------------------------------------------------------------
+// Phase ends: the first 8 scalars go to pinned memory, then the event.
+static jd_status end_phase(jd::OptMachine &m, jd::OptMachine::Phase ph) {
+  jd_problem *p = m.p;
+  JD_CUDA(cudaMemcpyAsync(p->host_pinned, p->scal_d, 8 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  JD_CUDA(cudaEventRecord(m.ev, p->stream));
+  m.phase = ph;
+  return JD_OK;
+}
+
+// Gradient at u^n (the accepted trial's forward sweep is reused) and the projected-
+// gradient norm.
+static jd_status launch_grad(jd::OptMachine &m) {
+  jd_problem *p = m.p;
+  const jd_problem_desc &q = p->desc;
+  jd_status s = clear_bad(p);
+  if (!s) s = run_gradient(p, p->opt_u, false, m.forward_done);
+  if (s) return s;
+  m.forward_done = false;
+  m.r.evals++;
+  m.grads++;
+  const int pr = prof_begin(KC_OPT, p->stream);
+  opt_pgnorm_kernel<<<1, 256, 0, p->stream>>>(q.Nt * q.du, p->opt_u, p->grad_d, q.T / q.Nt, q.u_min, q.u_max,
+                                              p->scal_d + S_PG);
+  prof_end(pr, p->stream);
+  count_launch();
+  JD_CUDA(cudaGetLastError());
+  return end_phase(m, jd::OptMachine::GRAD);
+}
+
+// One Armijo trial at the current zeta: trial point, forward sweep in the plan's mode,
+// device-side acceptance test.
+static jd_status launch_trial(jd::OptMachine &m) {
+  jd_problem *p = m.p;
+  const jd_problem_desc &q = p->desc;
+  const int n = q.Nt * q.du;
+  const double dt = q.T / q.Nt;
+  int pr = prof_begin(KC_OPT, p->stream);
+  opt_trial_kernel<<<1, 256, 0, p->stream>>>(n, p->opt_u, p->grad_d, m.zeta, dt, q.u_min, q.u_max, p->opt_ut,
+                                             p->scal_d + S_DOT);
+  prof_end(pr, p->stream);
+  count_launch();
+  JD_CUDA(cudaGetLastError());
+  jd_status s = run_plan_forward(p, p->opt_ut, S_JT);
+  if (s) return s;
+  m.r.evals++;
+  pr = prof_begin(KC_OPT, p->stream);
+  opt_accept_kernel<<<1, 256, 0, p->stream>>>(n, p->opt_u, p->opt_ut, m.o.armijo_c, dt, p->scal_d);
+  prof_end(pr, p->stream);
+  count_launch();
+  JD_CUDA(cudaGetLastError());
+  return end_phase(m, jd::OptMachine::TRIAL);
+}
+
+// Final iterate to the caller's buffer.
+static jd_status launch_output(jd::OptMachine &m, jd_status status) {
+  jd_problem *p = m.p;
+  m.r.iters = m.it;
+  m.r.zeta = m.zeta;
+  m.r.status = status;
+  const size_t n = (size_t)p->desc.Nt * p->desc.du;
+  JD_CUDA(cudaMemcpyAsync(m.u_dst, p->opt_u, n * 8,
+                          m.u_space == JD_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                          p->stream));
+  JD_CUDA(cudaEventRecord(m.ev, p->stream));
+  m.phase = jd::OptMachine::OUTPUT;
+  return JD_OK;
+}
+
+jd_status jd::opt_begin(OptMachine &m, jd_problem *p, const jd_opt_params &o, double *u_dst, jd_memspace us,
+                        double *J_hist) {
+  if (o.max_iter < 0 || o.max_backtracks < 0 || !(o.armijo_c >= 0.0))
+    return fail(JD_ERR_INVALID_ARG, "bad optimizer parameters");
+  if (us != JD_MEM_HOST && us != JD_MEM_DEVICE) return fail(JD_ERR_INVALID_ARG, "bad memory space for u");
+  m.p = p;
+  m.o = o;
+  std::memset(&m.r, 0, sizeof(m.r));
+  m.J_hist = J_hist;
+  m.u_dst = u_dst;
+  m.u_space = us;
+  m.it = m.backtracks = m.grads = 0;
+  m.zeta = o.zeta0 > 0.0 ? o.zeta0 : 1.0;
+  m.zeta_max = o.zeta_max > 0.0 ? o.zeta_max : 1e3;
+  m.pg0 = -1.0;
+  m.forward_done = false;
+  const size_t n = (size_t)p->desc.Nt * p->desc.du;
+  JD_CUDA(cudaMemcpyAsync(p->opt_u, p->u_in, n * 8, cudaMemcpyDeviceToDevice, p->stream));
+  if (o.max_iter == 0) return launch_output(m, JD_OK);
+  return launch_grad(m);
+}
+
+jd_status jd::opt_advance(OptMachine &m) {
+  jd_problem *p = m.p;
+  const double *h = p->host_pinned;
+  switch (m.phase) {
+    case OptMachine::GRAD: {
+      const jd_status st = status_of_scalars(p);
+      if (st != JD_OK) return launch_output(m, st);
+      const double J = h[S_J], pg = h[S_PG];
+      if (m.J_hist) m.J_hist[m.it] = J;
+      m.r.J = J;
+      if (m.pg0 < 0.0) m.pg0 = pg;
+      m.r.rel_grad_norm = m.pg0 > 0.0 ? pg / m.pg0 : 0.0;
+      if (m.r.rel_grad_norm <= m.o.tol_rel_grad) return launch_output(m, JD_OK);
+      if (m.it > 0) m.zeta = std::fmin(2.0 * m.zeta, m.zeta_max);
+      m.backtracks = 0;
+      return launch_trial(m);
+    }
+    case OptMachine::TRIAL: {
+      if (h[S_ACC] != 0.0) {
+        m.forward_done = true;
+        const double step2 = h[S_STEP];
+        m.r.J = h[S_J];
+        if (m.J_hist) m.J_hist[m.it + 1] = m.r.J;
+        m.it++;
+        if (std::sqrt(step2) < m.o.tol_step || m.it >= m.o.max_iter) return launch_output(m, JD_OK);
+        return launch_grad(m);
+      }
+      m.zeta *= 0.5;
+      if (++m.backtracks > m.o.max_backtracks)
+        return launch_output(m, fail(JD_ERR_LINESEARCH, "Armijo backtracking exhausted"));
+      return launch_trial(m);
+    }
+    case OptMachine::OUTPUT:
+      m.phase = OptMachine::DONE;
+      return JD_OK;
+    default:
+      return fail(JD_ERR_INVALID_ARG, "optimizer machine is not running");
+  }
+}
+
 // ---------------------------------------------------------------------------
 // ABI
 // ---------------------------------------------------------------------------
@@ -587,25 +818,25 @@ jd_status jd_problem_destroy(jd_problem *p) {
   if (!p) return JD_OK;
   cudaSetDevice(p->device);
   if (p->stream) cudaStreamSynchronize(p->stream);
-  free_dev(p->uk);
-  free_dev(p->xdk);
-  free_dev(p->u_in);
-  free_dev(p->grad_d);
-  free_dev(p->scal_d);
-  free_dev(p->partC);
-  free_dev(p->partG);
-  free_dev(p->partT);
-  free_dev(p->traj);
-  free_dev(p->flags);
-  free_dev(p->ckpt);
-  free_dev(p->log_kt);
-  free_dev(p->log_y);
-  free_dev(p->jcnt);
-  free_dev(p->opt_u);
-  free_dev(p->opt_ut);
-  free_dev(p->opt_g);
-  free_dev(p->kp_dev);
-  if (p->host_pinned) cudaFreeHost(p->host_pinned);
+  free_dev(p, p->uk);
+  free_dev(p, p->xdk);
+  free_dev(p, p->u_in);
+  free_dev(p, p->grad_d);
+  free_dev(p, p->scal_d);
+  free_dev(p, p->partC);
+  free_dev(p, p->partG);
+  free_dev(p, p->partT);
+  free_dev(p, p->traj);
+  free_dev(p, p->flags);
+  free_dev(p, p->ckpt);
+  free_dev(p, p->log_kt);
+  free_dev(p, p->log_y);
+  free_dev(p, p->jcnt);
+  free_dev(p, p->opt_u);
+  free_dev(p, p->opt_ut);
+  free_dev(p, p->opt_g);
+  free_dev(p, p->kp_dev);
+  if (p->host_pinned && p->own_pinned) cudaFreeHost(p->host_pinned);
   if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
   delete p;
   return JD_OK;
@@ -613,37 +844,28 @@ jd_status jd_problem_destroy(jd_problem *p) {
 
 jd_status jd_problem_create(const jd_problem_desc *desc, jd_problem **out) {
   if (!desc || !out) return fail(JD_ERR_INVALID_ARG, "desc and out must be non-NULL");
+  return jd::create_problem(*desc, jd::ProblemOpts{}, out);
+}
+
+jd_status jd_problem_footprint(const jd_problem_desc *desc, jd_adjoint_mode plan, size_t *bytes) {
+  if (!desc || !bytes) return fail(JD_ERR_INVALID_ARG, "desc and bytes must be non-NULL");
+  jd_status s = validate_desc(*desc);
+  if (s) return s;
+  if (plan != JD_ADJ_STORED && plan != JD_ADJ_RECOMPUTE)
+    return fail(JD_ERR_INVALID_ARG, "plan must be JD_ADJ_STORED or JD_ADJ_RECOMPUTE");
+  if (plan == JD_ADJ_RECOMPUTE && desc->d > 8)
+    return fail(JD_ERR_UNSUPPORTED, "the recompute adjoint is not built for 8 < d <= 32");
+  *bytes = jd::problem_bytes(*desc, plan);
+  return JD_OK;
+}
+
+}  // extern "C"
+
+jd_status jd::create_problem(const jd_problem_desc &q, const jd::ProblemOpts &opts, jd_problem **out) {
   *out = nullptr;
-  const jd_problem_desc &q = *desc;
-  if (q.d < 1 || q.du < 1) return fail(JD_ERR_INVALID_ARG, "d and du must be >= 1");
-  if (q.d > 32) return fail(JD_ERR_UNSUPPORTED, "d > 32 is not compiled");
-  if (q.d > 8 && (q.prec != JD_FP32 || q.drift != JD_DRIFT_LINEAR))
-    return fail(JD_ERR_UNSUPPORTED, "8 < d <= 32 is built for FP32 paths with a linear drift only");
-  if (q.du > 4) return fail(JD_ERR_UNSUPPORTED, "du > 4 is not compiled");
-  if (q.Nt < 1 || q.Nt > (1 << 24)) return fail(JD_ERR_INVALID_ARG, "Nt must be in [1, 2^24]");
-  if (q.M < 1 || q.M > 0xFFFFFFFFll) return fail(JD_ERR_INVALID_ARG, "M must be in [1, 2^32 - 1]");
-  if (!(q.T > 0.0) || !std::isfinite(q.T)) return fail(JD_ERR_INVALID_ARG, "T must be finite and > 0");
-  if (q.drift != JD_DRIFT_LINEAR && q.drift != JD_DRIFT_CUBIC) return fail(JD_ERR_INVALID_ARG, "bad drift");
-  if (q.jump_law < JD_JUMP_NONE || q.jump_law > JD_JUMP_UNIFORM) return fail(JD_ERR_INVALID_ARG, "bad jump law");
-  if (q.prec != JD_FP32 && q.prec != JD_FP64) return fail(JD_ERR_INVALID_ARG, "bad precision");
-  if (q.mode < JD_ADJ_AUTO || q.mode > JD_ADJ_RECOMPUTE) return fail(JD_ERR_INVALID_ARG, "bad adjoint mode");
-  if (!q.A || !q.B || !q.sigma || !q.x0 || !q.q || !q.xd)
-    return fail(JD_ERR_INVALID_ARG, "A, B, sigma, x0, q, xd must be non-NULL");
-  if (q.drift == JD_DRIFT_CUBIC && !q.C) return fail(JD_ERR_INVALID_ARG, "C must be non-NULL for CUBIC");
-  if (!(q.lambda >= 0.0) || !std::isfinite(q.lambda)) return fail(JD_ERR_INVALID_ARG, "lambda must be finite and >= 0");
-  if (!(q.jump_scale >= 0.0) || !std::isfinite(q.jump_scale))
-    return fail(JD_ERR_INVALID_ARG, "jump_scale must be finite and >= 0");
-  if (!std::isfinite(q.nu) || q.nu < 0.0) return fail(JD_ERR_INVALID_ARG, "nu must be finite and >= 0");
-  if (!(q.u_min <= q.u_max)) return fail(JD_ERR_INVALID_ARG, "u_min must be <= u_max");
-  if (q.use_tensor_cores < 0 || q.use_tensor_cores > 2)
-    return fail(JD_ERR_INVALID_ARG, "use_tensor_cores must be 0, 1 (BF16) or 2 (BF16 x3)");
-  if (q.use_tensor_cores && q.d <= 8)
-    return fail(JD_ERR_UNSUPPORTED, "tensor cores are used for 8 < d <= 32 (linear drift, FP32)");
+  jd_status vs = validate_desc(q);
+  if (vs) return vs;
   const size_t dd = (size_t)q.d * q.d, dn = (size_t)(q.Nt + 1) * q.d;
-  if (!finite_all(q.A, dd) || !finite_all(q.B, (size_t)q.d * q.du) || !finite_all(q.sigma, q.d) ||
-      !finite_all(q.x0, q.d) || !finite_all(q.q, q.d) || !finite_all(q.xd, dn) ||
-      (q.drift == JD_DRIFT_CUBIC && !finite_all(q.C, dd)) || (q.dA && !finite_all(q.dA, dd)))
-    return fail(JD_ERR_INVALID_ARG, "a coefficient array has a non-finite entry");
 
   jd_problem *p = new jd_problem();
   p->desc = q;
@@ -681,7 +903,10 @@ jd_status jd_problem_create(const jd_problem_desc *desc, jd_problem **out) {
       return cuda_fail(e, "cudaDeviceSetLimit(cudaLimitStackSize)");
     }
   }
-  if (q.cuda_stream) {
+  p->async_alloc = opts.async_alloc;
+  if (opts.stream) {
+    p->stream = opts.stream;
+  } else if (q.cuda_stream) {
     p->stream = (cudaStream_t)q.cuda_stream;
   } else {
     e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking);
@@ -724,26 +949,23 @@ jd_status jd_problem_create(const jd_problem_desc *desc, jd_problem **out) {
   ALLOC(p->opt_ut, nu * 8, "optimizer trial");
   if (p->D == 32) ALLOC(p->kp_dev, 16384, "d = 32 coefficients");
 #undef ALLOC
-  e = cudaMallocHost((void **)&p->host_pinned, NSCAL * 8);
-  if (e != cudaSuccess) {
-    jd_problem_destroy(p);
-    return cuda_fail(e, "cudaMallocHost");
-  }
-  // padded target in kernel precision
-  std::vector<double> xdp((size_t)(q.Nt + 1) * p->D, 0.0);
-  for (int k = 0; k <= q.Nt; ++k)
-    for (int c = 0; c < q.d; ++c) xdp[(size_t)k * p->D + c] = p->xd[(size_t)k * q.d + c];
-  if (q.prec == JD_FP64) {
-    e = cudaMemcpy(p->xdk, xdp.data(), xdp.size() * 8, cudaMemcpyHostToDevice);
+  if (opts.pinned) {
+    p->host_pinned = opts.pinned;
+    p->own_pinned = false;
   } else {
-    std::vector<float> xf(xdp.begin(), xdp.end());
-    e = cudaMemcpy(p->xdk, xf.data(), xf.size() * 4, cudaMemcpyHostToDevice);
+    e = cudaMallocHost((void **)&p->host_pinned, NSCAL * 8);
+    if (e != cudaSuccess) {
+      jd_problem_destroy(p);
+      return cuda_fail(e, "cudaMallocHost");
+    }
   }
+  e = upload_target(p);
   if (e != cudaSuccess) {
     jd_problem_destroy(p);
     return cuda_fail(e, "cudaMemcpy target");
   }
-  e = cudaMemset(p->scal_d, 0, NSCAL * 8);
+  e = cudaMemsetAsync(p->scal_d, 0, NSCAL * 8, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
   if (e != cudaSuccess) {
     jd_problem_destroy(p);
     return cuda_fail(e, "cudaMemset");
@@ -751,6 +973,31 @@ jd_status jd_problem_create(const jd_problem_desc *desc, jd_problem **out) {
   *out = p;
   return JD_OK;
 }
+
+size_t jd::problem_bytes_min(const jd_problem_desc &q) {
+  int D = 0, DU = 0;
+  pick_dims(q.d, q.du, &D, &DU);
+  const size_t es = q.prec == JD_FP64 ? 8 : 4;
+  if (D != 32) return problem_bytes(q, JD_ADJ_RECOMPUTE);
+  return base_bytes(q, D, DU, es) + stored_plan_bytes(q, D, es, TPB);
+}
+
+size_t jd::problem_bytes(const jd_problem_desc &q, jd_adjoint_mode plan) {
+  int D = 0, DU = 0;
+  pick_dims(q.d, q.du, &D, &DU);
+  const size_t es = q.prec == JD_FP64 ? 8 : 4;
+  size_t b = base_bytes(q, D, DU, es);
+  if (plan == JD_ADJ_STORED) {
+    b += stored_plan_bytes(q, D, es, q.M);
+  } else if (plan == JD_ADJ_RECOMPUTE) {
+    const jd::PathOps *ops = path_ops_dims(q.prec, D, DU);
+    const int S = ops ? ops->S : 16;
+    b += (size_t)(ceil_div(q.Nt, S) + 1) * D * q.M * es;
+  }
+  return b;
+}
+
+extern "C" {
 
 jd_status jd_problem_info(const jd_problem *p, size_t *device_bytes, jd_adjoint_mode *mode) {
   if (!p) return fail(JD_ERR_INVALID_ARG, "p is NULL");
@@ -761,6 +1008,7 @@ jd_status jd_problem_info(const jd_problem *p, size_t *device_bytes, jd_adjoint_
 
 jd_status jd_cost(jd_problem *p, const double *u, jd_memspace us, double *J) {
   if (!p || !J) return fail(JD_ERR_INVALID_ARG, "p and J must be non-NULL");
+  p->fwd_valid = false;
   jd_status s = set_device(p);
   if (!s) s = load_u(p, u, us);
   if (!s) s = clear_bad(p);
@@ -777,11 +1025,13 @@ jd_status jd_gradient(jd_problem *p, const double *u, jd_memspace us, double *J,
   if (grad && gs != JD_MEM_HOST && gs != JD_MEM_DEVICE) return fail(JD_ERR_INVALID_ARG, "bad memory space for grad");
   if (grad_theta && p->D == 32)
     return fail(JD_ERR_UNSUPPORTED, "parameter gradients are not built for 8 < d <= 32");
+  p->fwd_valid = false;
   jd_status s = set_device(p);
   if (!s) s = load_u(p, u, us);
   if (!s) s = clear_bad(p);
   if (!s) s = run_gradient(p, p->u_in, grad_theta != nullptr);
   if (s) return s;
+  p->fwd_valid = true;   // the plan's states belong to u_in: jd_backward may follow
   const size_t n = (size_t)p->desc.Nt * p->desc.du;
   if (grad) {
     JD_CUDA(cudaMemcpyAsync(grad, p->grad_d, n * 8,
@@ -797,11 +1047,100 @@ jd_status jd_gradient(jd_problem *p, const double *u, jd_memspace us, double *J,
   return status_of_scalars(p);
 }
 
+jd_status jd_forward(jd_problem *p, const double *u, jd_memspace us, double *J, jd_memspace js) {
+  if (!p) return fail(JD_ERR_INVALID_ARG, "p is NULL");
+  if (J && js != JD_MEM_HOST && js != JD_MEM_DEVICE) return fail(JD_ERR_INVALID_ARG, "bad memory space for J");
+  p->fwd_valid = false;
+  jd_status s = set_device(p);
+  if (!s) s = load_u(p, u, us);
+  if (!s) s = clear_bad(p);
+  if (!s) s = run_plan_forward(p, p->u_in, S_J);
+  if (s) return s;
+  p->fwd_valid = true;
+  if (!J) return JD_OK;
+  if (js == JD_MEM_DEVICE) {
+    JD_CUDA(cudaMemcpyAsync(J, p->scal_d + S_J, sizeof(double), cudaMemcpyDeviceToDevice, p->stream));
+    return JD_OK;
+  }
+  s = read_scalars(p, 0, NSCAL);
+  if (s) return s;
+  *J = p->host_pinned[S_J];
+  return status_of_scalars(p);
+}
+
+jd_status jd_backward(jd_problem *p, double *grad, jd_memspace gs, double *grad_theta) {
+  if (!p) return fail(JD_ERR_INVALID_ARG, "p is NULL");
+  if (gs != JD_MEM_HOST && gs != JD_MEM_DEVICE) return fail(JD_ERR_INVALID_ARG, "bad memory space for grad");
+  if (!p->fwd_valid)
+    return fail(JD_ERR_INVALID_ARG, "jd_backward needs a jd_forward (or jd_gradient) on this problem first");
+  if (grad_theta && p->D == 32)
+    return fail(JD_ERR_UNSUPPORTED, "parameter gradients are not built for 8 < d <= 32");
+  jd_status s = set_device(p);
+  if (!s) s = run_gradient(p, p->u_in, grad_theta != nullptr, /*forward_done=*/true);
+  if (s) return s;
+  const size_t n = (size_t)p->desc.Nt * p->desc.du;
+  const cudaMemcpyKind kind = gs == JD_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (grad) JD_CUDA(cudaMemcpyAsync(grad, p->grad_d, n * 8, kind, p->stream));
+  if (gs == JD_MEM_DEVICE) {
+    if (grad_theta)
+      JD_CUDA(cudaMemcpyAsync(grad_theta, p->scal_d + S_THETA, (size_t)(p->desc.d + 2) * 8,
+                              cudaMemcpyDeviceToDevice, p->stream));
+    return JD_OK;
+  }
+  s = read_scalars(p, 0, NSCAL);
+  if (s) return s;
+  if (grad_theta)
+    for (int t = 0; t < p->desc.d + 2; ++t) grad_theta[t] = p->host_pinned[S_THETA + t];
+  return status_of_scalars(p);
+}
+
+jd_status jd_problem_update(jd_problem *p, const jd_problem_desc *desc) {
+  if (!p || !desc) return fail(JD_ERR_INVALID_ARG, "p and desc must be non-NULL");
+  const jd_problem_desc &q = *desc, &o = p->desc;
+  jd_status s = validate_desc(q);
+  if (s) return s;
+  if (q.d != o.d || q.du != o.du || q.T != o.T || q.Nt != o.Nt || q.M != o.M || q.drift != o.drift ||
+      q.prec != o.prec || q.mode != o.mode || q.use_tensor_cores != o.use_tensor_cores)
+    return fail(JD_ERR_INVALID_ARG,
+                "jd_problem_update may change coefficients only (d, du, T, Nt, M, drift, prec, mode, "
+                "use_tensor_cores must match)");
+  s = set_device(p);
+  if (s) return s;
+  p->fwd_valid = false;
+  const size_t dd = (size_t)q.d * q.d, dn = (size_t)(q.Nt + 1) * q.d;
+  p->A.assign(q.A, q.A + dd);
+  if (q.drift == JD_DRIFT_CUBIC) p->C.assign(q.C, q.C + dd);
+  p->B.assign(q.B, q.B + (size_t)q.d * q.du);
+  if (q.dA)
+    p->dA.assign(q.dA, q.dA + dd);
+  else
+    p->dA.clear();
+  p->sigma.assign(q.sigma, q.sigma + q.d);
+  p->x0.assign(q.x0, q.x0 + q.d);
+  p->q.assign(q.q, q.q + q.d);
+  const bool new_target = !std::equal(q.xd, q.xd + dn, p->xd.begin());
+  if (new_target) p->xd.assign(q.xd, q.xd + dn);
+  p->desc.lambda = q.lambda;
+  p->desc.jump_law = q.jump_law;
+  p->desc.jump_scale = q.jump_scale;
+  p->desc.nu = q.nu;
+  p->desc.u_min = q.u_min;
+  p->desc.u_max = q.u_max;
+  p->desc.seed = q.seed;
+  p->desc.epoch = q.epoch;
+  if (new_target) {
+    const cudaError_t e = upload_target(p);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy target");
+  }
+  return JD_OK;
+}
+
 jd_status jd_sample_paths(jd_problem *p, const double *u, jd_memspace us, int64_t m0, int64_t count,
                           double *X, double *lam, double *cost) {
   if (!p) return fail(JD_ERR_INVALID_ARG, "p is NULL");
   if (m0 < 0 || count < 1 || m0 + count > p->desc.M)
     return fail(JD_ERR_INVALID_ARG, "path range outside [0, M)");
+  p->fwd_valid = false;
   jd_status s = set_device(p);
   if (!s) s = load_u(p, u, us);
   if (!s) s = prep_u(p, p->u_in);
@@ -885,92 +1224,22 @@ jd_status jd_sample_paths(jd_problem *p, const double *u, jd_memspace us, int64_
 jd_status jd_optimize(jd_problem *p, double *u_inout, jd_memspace us, const jd_opt_params *o,
                       jd_opt_result *r, double *J_hist) {
   if (!p || !u_inout || !o || !r) return fail(JD_ERR_INVALID_ARG, "p, u_inout, o, r must be non-NULL");
-  if (o->max_iter < 0 || o->max_backtracks < 0 || !(o->armijo_c >= 0.0))
-    return fail(JD_ERR_INVALID_ARG, "bad optimizer parameters");
   std::memset(r, 0, sizeof(*r));
+  p->fwd_valid = false;
   jd_status s = set_device(p);
   if (!s) s = load_u(p, u_inout, us);
   if (s) return s;
-  const jd_problem_desc &q = p->desc;
-  const int n = q.Nt * q.du;
-  const double dt = q.T / q.Nt;
-  JD_CUDA(cudaMemcpyAsync(p->opt_u, p->u_in, (size_t)n * 8, cudaMemcpyDeviceToDevice, p->stream));
-  double zeta = o->zeta0 > 0.0 ? o->zeta0 : 1.0;
-  const double zeta_max = o->zeta_max > 0.0 ? o->zeta_max : 1e3;
-  double pg0 = -1.0;
-  int it = 0;
-  jd_status status = JD_OK;
-  // Algorithm 5.4: each iteration is one gradient at u^n, an Armijo line search and
-  // the update; no gradient after the last update.
-  bool forward_done = false;   // the accepted trial's sweep is the next gradient's forward
-  for (it = 0; it < o->max_iter; ++it) {
-    s = clear_bad(p);
-    if (!s) s = run_gradient(p, p->opt_u, false, forward_done);
-    if (s) return s;
-    forward_done = false;
-    r->evals++;
-    int pr = prof_begin(KC_OPT, p->stream);
-    opt_pgnorm_kernel<<<1, 256, 0, p->stream>>>(n, p->opt_u, p->grad_d, dt, q.u_min, q.u_max,
-                                                p->scal_d + S_PG);
-    prof_end(pr, p->stream);
-    count_launch();
-    JD_CUDA(cudaGetLastError());
-    s = read_scalars(p, 0, 8);
-    if (s) return s;
-    status = status_of_scalars(p);
-    if (status != JD_OK) break;
-    const double J = p->host_pinned[S_J], pg = p->host_pinned[S_PG];
-    if (J_hist) J_hist[it] = J;
-    r->J = J;
-    if (pg0 < 0.0) pg0 = pg;
-    r->rel_grad_norm = pg0 > 0.0 ? pg / pg0 : 0.0;
-    if (r->rel_grad_norm <= o->tol_rel_grad) break;
-    if (it > 0) zeta = std::fmin(2.0 * zeta, zeta_max);
-    bool accepted = false;
-    double step2 = 0.0;
-    for (int b = 0; b <= o->max_backtracks; ++b) {
-      pr = prof_begin(KC_OPT, p->stream);
-      opt_trial_kernel<<<1, 256, 0, p->stream>>>(n, p->opt_u, p->grad_d, zeta, dt, q.u_min, q.u_max,
-                                                 p->opt_ut, p->scal_d + S_DOT);
-      prof_end(pr, p->stream);
-      count_launch();
-      JD_CUDA(cudaGetLastError());
-      s = run_plan_forward(p, p->opt_ut, S_JT);
-      if (s) return s;
-      r->evals++;
-      pr = prof_begin(KC_OPT, p->stream);
-      opt_accept_kernel<<<1, 256, 0, p->stream>>>(n, p->opt_u, p->opt_ut, o->armijo_c, dt, p->scal_d);
-      prof_end(pr, p->stream);
-      count_launch();
-      JD_CUDA(cudaGetLastError());
-      s = read_scalars(p, 0, 8);
-      if (s) return s;
-      if (p->host_pinned[S_ACC] != 0.0) {
-        accepted = true;
-        forward_done = true;
-        step2 = p->host_pinned[S_STEP];
-        r->J = p->host_pinned[S_J];
-        break;
-      }
-      zeta *= 0.5;
-    }
-    if (!accepted) {
-      status = fail(JD_ERR_LINESEARCH, "Armijo backtracking exhausted");
-      break;
-    }
-    if (J_hist) J_hist[it + 1] = r->J;
-    if (std::sqrt(step2) < o->tol_step) {
-      it++;
-      break;
-    }
+  jd::OptMachine m;
+  JD_CUDA(cudaEventCreateWithFlags(&m.ev, cudaEventDisableTiming));
+  s = jd::opt_begin(m, p, *o, u_inout, us, J_hist);
+  while (!s && m.phase != jd::OptMachine::DONE) {
+    const cudaError_t e = cudaEventSynchronize(m.ev);
+    s = e == cudaSuccess ? jd::opt_advance(m) : cuda_fail(e, "cudaEventSynchronize");
   }
-  r->iters = it;
-  r->zeta = zeta;
-  r->status = status;
-  JD_CUDA(cudaMemcpyAsync(u_inout, p->opt_u, (size_t)n * 8,
-                          us == JD_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, p->stream));
-  JD_CUDA(cudaStreamSynchronize(p->stream));
-  return status;
+  cudaEventDestroy(m.ev);
+  if (s) return s;
+  *r = m.r;
+  return m.r.status;
 }
 
 }  // extern "C"

@@ -33,6 +33,7 @@ struct KParams {
   uint32_t key0, key1, epoch;
   int d, npair, Nt, cubic, jump_law, jumps_on, has_dA, S, nblk;
   int64_t m_begin;                // global index of path 0 of this launch
+  int64_t npart;                  // stride of the per-warp gradient partials (all launches)
 };
 
 // Device buffers of one launch (unused ones are null).
@@ -48,6 +49,10 @@ struct PathBufs {
   double *partC = nullptr, *partG = nullptr, *partT = nullptr;
   void *lam_out = nullptr;     // adjoint states (optional)
   int *status = nullptr;       // device status word (bounded waits record timeouts here)
+  // partial-stride override: a launch that covers one block of the paths (chunked
+  // stored plan) writes its partials at their global positions (partG, partC offset
+  // by the caller) with the stride of all M paths; 0 = this launch's own count
+  int64_t npart = 0;
 };
 
 // Per-instantiation launch table (one entry per precision x compiled dimension).
@@ -89,6 +94,7 @@ struct jd_problem {
   int device = 0;
   size_t budget = 0;
   jd_adjoint_mode plan = JD_ADJ_AUTO;
+  bool fwd_valid = false;   // stored states / checkpoints belong to u_in (jd_forward)
   // device buffers
   void *uk = nullptr;        // kernel-precision padded control, Nt*DU
   void *xdk = nullptr;       // kernel-precision padded target, (Nt+1)*D
@@ -102,10 +108,60 @@ struct jd_problem {
   void *log_kt = nullptr, *log_y = nullptr;
   int *jcnt = nullptr;
   int log_cap = 0;
+  int64_t chunk = 0;         // stored plan in path blocks of this size (0: all paths at once)
   double *opt_u = nullptr, *opt_ut = nullptr, *opt_g = nullptr;
   int *status_d = nullptr;   // kernel status word (JD_OK or JD_ERR_TIMEOUT)
   void *kp_dev = nullptr;    // coefficient struct of the d = 32 kernels (device copy)
   double *host_pinned = nullptr;  // small pinned staging buffer
+  bool own_pinned = true;
+  bool async_alloc = false;  // stream-ordered allocations (server): no device-wide sync on free
   size_t bytes = 0;
   int64_t nblk = 0;
 };
+
+namespace jd {
+
+// How a problem object gets its resources (jd_problem_create: all owned; the server:
+// a slot's stream and pinned buffer, stream-ordered allocations).
+struct ProblemOpts {
+  cudaStream_t stream = nullptr;     // null: own stream (or desc.cuda_stream)
+  double *pinned = nullptr;          // null: own pinned scalar buffer (kScalars doubles)
+  bool async_alloc = false;
+};
+constexpr int kScalars = 8 + 34;     // FP64 scalar slots per problem (device and pinned)
+
+jd_status create_problem(const jd_problem_desc &q, const ProblemOpts &o, jd_problem **out);
+
+// Device bytes a problem allocates: the buffers of jd_problem_create plus those of the
+// adjoint plan (STORED or RECOMPUTE).  Host arithmetic only.
+size_t problem_bytes(const jd_problem_desc &q, jd_adjoint_mode plan);
+// The least a problem can run in: RECOMPUTE for d <= 8; for d = 32 the stored plan in
+// blocks of 128 paths.
+size_t problem_bytes_min(const jd_problem_desc &q);
+
+// Projected-gradient Armijo iteration (Algorithm 5.4) of one problem as a non-blocking
+// state machine: every phase (gradient; one line-search trial; the final copy of u)
+// is enqueued on the problem's stream and ends with a copy of the FP64 scalars to
+// pinned memory and a record of `ev`; opt_advance, called once `ev` has completed,
+// takes the host decision and enqueues the next phase.  jd_optimize drives one
+// machine to the end; the server interleaves many.
+struct OptMachine {
+  enum Phase { IDLE, GRAD, TRIAL, OUTPUT, DONE };
+  ::jd_problem *p = nullptr;
+  jd_opt_params o{};
+  jd_opt_result r{};
+  double *J_hist = nullptr;
+  double *u_dst = nullptr;
+  jd_memspace u_space = JD_MEM_HOST;
+  cudaEvent_t ev = nullptr;
+  Phase phase = IDLE;
+  int it = 0, backtracks = 0, grads = 0;
+  double zeta = 1.0, zeta_max = 1e3, pg0 = -1.0;
+  bool forward_done = false;
+};
+// p->u_in holds u^0.  u_dst (space us) receives the final iterate.
+jd_status opt_begin(OptMachine &m, ::jd_problem *p, const jd_opt_params &o, double *u_dst,
+                    jd_memspace us, double *J_hist);
+jd_status opt_advance(OptMachine &m);
+
+}  // namespace jd

@@ -435,7 +435,7 @@ adj_stored_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restr
                   int64_t mloc) {
   using M = Ar<R>;
   __shared__ Pair<R> red1[TPB / 32];
-  const int64_t npart = (int64_t)kp.nblk * (TPB / 32);
+  const int64_t npart = kp.npart;
   const int64_t lm = (int64_t)blockIdx.x * TPB + threadIdx.x;
   const bool active = lm < mloc;
   // inactive threads of the last block replay path 0 (its stored data and its random
@@ -522,7 +522,7 @@ adj_recompute_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__re
   auto *skt = reinterpret_cast<typename V2<R>::T *>(sbuf + (size_t)S * D * TPB);   // [JS][TPB]
   R *sy = reinterpret_cast<R *>(skt + JS * TPB);                                    // [JS * D][TPB]
   __shared__ Pair<R> red1[TPB / 32];
-  const int64_t npart = (int64_t)kp.nblk * (TPB / 32);
+  const int64_t npart = kp.npart;
   const int64_t lm = (int64_t)blockIdx.x * TPB + threadIdx.x;
   const bool active = lm < mloc;
   const int64_t lmc = active ? lm : 0;   // inactive threads replay path 0
@@ -646,6 +646,7 @@ void make_kparams(const jd_problem *p, int64_t m_begin, int64_t mloc, KParams<R,
   kp.S = seg_len<D>();
   kp.nblk = (int)ceil_div(mloc, TPB);
   kp.m_begin = m_begin;
+  kp.npart = grad_parts(mloc);
 }
 
 template <typename R, int D, int DU>
@@ -653,6 +654,7 @@ cudaError_t op_fwd(const jd_problem *p, int mode, int64_t m_begin, int64_t mloc,
                    const PathBufs &b, cudaStream_t s) {
   auto *kp = new KParams<R, D, DU>();
   make_kparams<R, D, DU>(p, m_begin, mloc, *kp);
+  if (b.npart) kp->npart = b.npart;
   const dim3 grid((unsigned)ceil_div(mloc, TPB));
   const R *u = static_cast<const R *>(uk);
   const R *xd = static_cast<const R *>(p->xdk);
@@ -687,6 +689,7 @@ cudaError_t op_adj(const jd_problem *p, int variant, bool theta, int64_t m_begin
                    const void *uk, const PathBufs &b, cudaStream_t s) {
   auto *kp = new KParams<R, D, DU>();
   make_kparams<R, D, DU>(p, m_begin, mloc, *kp);
+  if (b.npart) kp->npart = b.npart;
   const dim3 grid((unsigned)ceil_div(mloc, TPB));
   const R *u = static_cast<const R *>(uk);
   const R *xd = static_cast<const R *>(p->xdk);

@@ -110,6 +110,7 @@ static void noalloc_kparams(const jd_problem_desc &q, KParams<R, D, DU> &kp) {
   kp.S = seg_len<D>();
   kp.nblk = (int)ceil_div(q.M, TPB);
   kp.m_begin = 0;
+  kp.npart = kp.nblk * (int64_t)(TPB / 32);
 }
 
 template <typename R, int D>

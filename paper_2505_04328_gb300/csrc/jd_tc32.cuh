@@ -570,7 +570,7 @@ adj32_kernel(const KP32 *__restrict__ kpg, const float *__restrict__ u, const fl
   __shared__ __align__(16) float vbuf[32 * TPB];   // product staging (CUDA cores, jump sub-steps)
   stage_params(cs, kpg);
   const KP32 &kp = cs.kp;
-  const int64_t npart = (int64_t)kp.nblk * (TPB / 32);
+  const int64_t npart = kp.npart;
   const int64_t wid = (int64_t)blockIdx.x * (TPB / 32) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   const int64_t lm = (int64_t)blockIdx.x * TPB + threadIdx.x;

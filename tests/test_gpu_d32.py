@@ -97,3 +97,26 @@ def test_d32_rejects_unbuilt_combinations():
     with JdProblem(p) as jp:
         with pytest.raises(JdError):
             jp.gradient(workloads.random_control(p), theta=True)
+
+
+@pytest.mark.parametrize("tc", [0, 1])
+def test_d32_block_wise_stored_plan_is_bitwise_equal(tc):
+    """A memory budget below the full stored plan makes the d = 32 problem store its
+    paths block by block (multiples of 128 paths, the last block ragged); J, the gradient
+    and an optimizer run are bitwise equal to the single-block plan."""
+    from paper_2505_04328_gb300 import footprint
+    p = workloads.linear_family(32, M=1000, Nt=40, lam=3.0)
+    u = workloads.random_control(p, seed=23, scale=0.5)
+    full = footprint(p, "stored")
+    out = []
+    for budget in (0, int(full * 0.55), int(full * 0.2)):
+        with JdProblem(p, prec="fp32", use_tensor_cores=tc, mem_budget=budget) as jp:
+            J, g, _ = jp.gradient(u)
+            info = jp.info()
+            ub, r, hist = jp.optimize(np.zeros((p.Nt, p.du)), max_iter=3, tol_rel_grad=0.0)
+            if budget:
+                assert info["device_bytes"] <= budget < full
+            out.append((J, g, ub, r["J"], hist))
+    for J, g, ub, Jr, hist in out[1:]:
+        assert J == out[0][0] and np.array_equal(g, out[0][1])
+        assert np.array_equal(ub, out[0][2]) and Jr == out[0][3] and np.array_equal(hist, out[0][4])
