@@ -28,18 +28,21 @@ static cudaError_t op32_fwd(const jd_problem *p, int mode, int64_t m_begin, int6
   float *traj = mode == FWD_STORE ? static_cast<float *>(b.traj) : nullptr;
   const JLog<float, D32> jl{static_cast<float2 *>(b.log_kt), static_cast<float *>(b.log_y), mloc, b.log_cap};
   float *pc = static_cast<float *>(b.pcost);
+  const int Nt = p->desc.Nt;
+  bu32_kernel<<<(unsigned)ceil_div((int64_t)Nt * 32, 256), 256, 0, s>>>(kp, u, p->bu_dev, Nt);
+  const float *bu = p->bu_dev;
   switch (p->desc.use_tensor_cores) {
     case 1:
-      fwd32_kernel<1><<<grid, TPB, 0, s>>>(kp, u, xd, b.partC, traj, b.flags, pc, jl, b.jcnt, b.status, mloc);
+      fwd32_kernel<1><<<grid, TPB, 0, s>>>(kp, u, bu, xd, b.partC, traj, b.flags, pc, jl, b.jcnt, b.status, mloc);
       break;
     case 2:
-      fwd32_kernel<2><<<grid, TPB, 0, s>>>(kp, u, xd, b.partC, traj, b.flags, pc, jl, b.jcnt, b.status, mloc);
+      fwd32_kernel<2><<<grid, TPB, 0, s>>>(kp, u, bu, xd, b.partC, traj, b.flags, pc, jl, b.jcnt, b.status, mloc);
       break;
     default:
-      fwd32_kernel<0><<<grid, TPB, 0, s>>>(kp, u, xd, b.partC, traj, b.flags, pc, jl, b.jcnt, b.status, mloc);
+      fwd32_kernel<0><<<grid, TPB, 0, s>>>(kp, u, bu, xd, b.partC, traj, b.flags, pc, jl, b.jcnt, b.status, mloc);
       break;
   }
-  count_launch();
+  count_launch(2);
   return cudaGetLastError();
 }
 

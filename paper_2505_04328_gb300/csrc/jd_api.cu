@@ -342,7 +342,8 @@ static size_t recompute_bytes(const jd_problem *p) {
 static size_t base_bytes(const jd_problem_desc &q, int D, int DU, size_t es) {
   const size_t nu = (size_t)q.Nt * q.du, nblk = (size_t)ceil_div(q.M, TPB);
   return (size_t)q.Nt * DU * es + (size_t)(q.Nt + 1) * D * es + 4 * nu * 8 + NSCAL * 8 + nblk * 8 +
-         (size_t)q.Nt * DU * grad_parts(q.M) * 8 + (size_t)(D + 2) * nblk * 8 + (D == 32 ? 16384 : 0);
+         (size_t)q.Nt * DU * grad_parts(q.M) * 8 + (size_t)(D + 2) * nblk * 8 +
+         (D == 32 ? 16384 + (size_t)q.Nt * 32 * sizeof(float) : 0);
 }
 
 // Allocate the trajectory or checkpoint buffers on first use.
@@ -836,6 +837,7 @@ jd_status jd_problem_destroy(jd_problem *p) {
   free_dev(p, p->opt_ut);
   free_dev(p, p->opt_g);
   free_dev(p, p->kp_dev);
+  free_dev(p, p->bu_dev);
   if (p->host_pinned && p->own_pinned) cudaFreeHost(p->host_pinned);
   if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
   delete p;
@@ -947,7 +949,10 @@ jd_status jd::create_problem(const jd_problem_desc &q, const jd::ProblemOpts &op
   ALLOC(p->partT, (size_t)(p->D + 2) * p->nblk * 8, "parameter partials");
   ALLOC(p->opt_u, nu * 8, "optimizer iterate");
   ALLOC(p->opt_ut, nu * 8, "optimizer trial");
-  if (p->D == 32) ALLOC(p->kp_dev, 16384, "d = 32 coefficients");
+  if (p->D == 32) {
+    ALLOC(p->kp_dev, 16384, "d = 32 coefficients");
+    ALLOC(p->bu_dev, (size_t)q.Nt * 32 * sizeof(float), "d = 32 control drift");
+  }
 #undef ALLOC
   if (opts.pinned) {
     p->host_pinned = opts.pinned;

@@ -112,6 +112,7 @@ struct jd_problem {
   double *opt_u = nullptr, *opt_ut = nullptr, *opt_g = nullptr;
   int *status_d = nullptr;   // kernel status word (JD_OK or JD_ERR_TIMEOUT)
   void *kp_dev = nullptr;    // coefficient struct of the d = 32 kernels (device copy)
+  float *bu_dev = nullptr;   // d = 32: B u_k per step, [Nt][32] (the same for every path)
   double *host_pinned = nullptr;  // small pinned staging buffer
   bool own_pinned = true;
   bool async_alloc = false;  // stream-ordered allocations (server): no device-wide sync on free

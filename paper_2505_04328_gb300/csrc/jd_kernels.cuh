@@ -116,16 +116,57 @@ struct LogReader {
 
 struct NoLog {};
 
+// Recompute variant: steps per checkpoint segment.
+template <int D>
+__host__ __device__ constexpr int seg_len() {
+  return D <= 8 ? 16 : 8;
+}
+
 // One uniform step k from x (in place); returns the number of jumps.  Steps with one
 // jump take an inline path (the common case); two or more go through
 // build_jump_step.  With a LogWriter the post-jump states of the step are recorded.
-template <typename R, int D, int DU, typename LW>
+// The one-jump step out of line: sub-step to the jump, jump, sub-step to t_{k+1}.  x is
+// updated in place; y1 receives the post-jump state; returns the jump's time fraction.
+template <typename R, int D, int DU>
+__device__ __noinline__ R one_jump_substeps(const KParams<R, D, DU> &kp, int k, uint32_t m, const R *z,
+                                            const R *uk, R *x, R *y1) {
+  using M = Ar<R>;
+  R xih[D], z1[D], zz[D], ul[DU], xl[D];
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    zz[c] = z[c];
+    xl[c] = x[c];
+  }
+#pragma unroll
+  for (int l = 0; l < DU; ++l) ul[l] = uk[l];
+  const R th = slot0_draws(kp, k, m, xih, z1);
+  euler_substep(kp, M::mul(kp.dt, th), zz, ul, xl);
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    xl[c] = M::add(xl[c], M::mul(kp.jump_scale, xih[c]));
+    y1[c] = xl[c];
+  }
+  euler_substep(kp, M::mul(kp.dt, M::sub(R(1), th)), z1, ul, xl);
+#pragma unroll
+  for (int c = 0; c < D; ++c) x[c] = xl[c];
+  return th;
+}
+
+// zo (optional, stride zs): receives the step's main-stream normals Z_{k,0}.
+// INLINE_JUMP: the one-jump case inline, or out of line (the replay of the parameter-
+// gradient recompute adjoint, whose loop must stay small for the instruction cache).
+template <typename R, int D, int DU, typename LW, bool ZOUT = false, bool INLINE_JUMP = true>
 __device__ __forceinline__ int forward_step(const KParams<R, D, DU> &kp, int k, uint32_t m,
-                                            const R *__restrict__ u, R (&x)[D], LW &lw) {
+                                            const R *__restrict__ u, R (&x)[D], LW &lw,
+                                            R *zo = nullptr, int zs = 0) {
   using M = Ar<R>;
   constexpr bool LOG = !std::is_same<LW, NoLog>::value;
   R z[D];
   const uint32_t w0 = main_draws(kp, k, m, z);
+  if constexpr (ZOUT) {
+#pragma unroll
+    for (int c = 0; c < D; ++c) zo[c * zs] = z[c];
+  }
   R uk[DU];
 #pragma unroll
   for (int l = 0; l < DU; ++l) uk[l] = __ldg(u + (size_t)k * DU + l);
@@ -136,7 +177,25 @@ __device__ __forceinline__ int forward_step(const KParams<R, D, DU> &kp, int k, 
     for (int c = 0; c < D; ++c) x[c] = M::fma(kp.sig_sqdt[c], z[c], M::fma(kp.dt, f[c], x[c]));
     return 0;
   }
-  if (kp.npair == MainWords<D>::PD && (unsigned long long)w0 < kp.thr[1]) {
+  if (!INLINE_JUMP && kp.npair == MainWords<D>::PD && (unsigned long long)w0 < kp.thr[1]) {
+    // copies: an address taken of x or uk themselves would move them to local memory
+    R zc[D], xc[D], uc[DU], y1[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      zc[c] = z[c];
+      xc[c] = x[c];
+    }
+#pragma unroll
+    for (int l = 0; l < DU; ++l) uc[l] = uk[l];
+    const R th = one_jump_substeps(kp, k, m, zc, uc, xc, y1);
+#pragma unroll
+    for (int c = 0; c < D; ++c) x[c] = xc[c];
+    if constexpr (LOG) {
+      if (lw.fits(1)) lw.put(k, th, y1);
+    }
+    return 1;
+  }
+  if (INLINE_JUMP && kp.npair == MainWords<D>::PD && (unsigned long long)w0 < kp.thr[1]) {
     R xih[D], z1[D];
     const R th = slot0_draws(kp, k, m, xih, z1);
     euler_substep(kp, M::mul(kp.dt, th), z, uk, x);
@@ -258,11 +317,14 @@ __device__ __noinline__ void jump_backward(const KParams<R, D, DU> &kp, int k, u
 
 // Backward through step k from the state X_k; g receives the step's contribution.
 // Jump steps use the log when it holds the step (u-gradient only), else regenerate.
-template <typename R, int D, int DU, bool THETA, typename LR>
+// zi (optional, stride zs): the step's main-stream normals kept by the forward replay;
+// without it the parameter gradients regenerate them.
+template <typename R, int D, int DU, bool THETA, typename LR, bool ZIN = false>
 __device__ __forceinline__ void backward_step(const KParams<R, D, DU> &kp, int k, uint32_t m,
                                               bool jumped, const R (&xk)[D],
                                               const R *__restrict__ u, const R *__restrict__ xd,
-                                              R (&mu)[D], R (&g)[DU], R (&th)[D + 2], LR &lr) {
+                                              R (&mu)[D], R (&g)[DU], R (&th)[D + 2], LR &lr,
+                                              const R *zi = nullptr, int zs = 0) {
   using M = Ar<R>;
 #pragma unroll
   for (int l = 0; l < DU; ++l) g[l] = R(0);
@@ -302,7 +364,12 @@ __device__ __forceinline__ void backward_step(const KParams<R, D, DU> &kp, int k
   } else {
     if (THETA) {
       R z[D];
-      (void)main_draws(kp, k, m, z);
+      if constexpr (ZIN) {
+#pragma unroll
+        for (int c = 0; c < D; ++c) z[c] = zi[c * zs];
+      } else {
+        (void)main_draws(kp, k, m, z);
+      }
 #pragma unroll
       for (int c = 0; c < D; ++c) th[1 + c] = M::fma(M::mul(mu[c], kp.sqdt), z[c], th[1 + c]);
       if (kp.has_dA) {
@@ -375,9 +442,9 @@ fwd_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u
       }
     }
     if (k == Nt) break;
-    if (MODE == FWD_CKPT && active && (k % kp.S) == 0) {
+    if (MODE == FWD_CKPT && active && (k % seg_len<D>()) == 0) {   // S is a power of two
 #pragma unroll
-      for (int c = 0; c < D; ++c) ckpt[((size_t)(k / kp.S) * D + c) * mloc + lm] = x[c];
+      for (int c = 0; c < D; ++c) ckpt[((size_t)(k / seg_len<D>()) * D + c) * mloc + lm] = x[c];
     }
     if (forward_step(kp, k, m, u, x, lw)) fw |= 1u << (k & 31);
     cost.add(cost_term(kp, x, xd + (size_t)(k + 1) * D));
@@ -390,7 +457,7 @@ fwd_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u
     if (active) jcnt[lm] = lw.r;
   }
   if (MODE == FWD_CKPT && active) {
-    const int nseg = (Nt + kp.S - 1) / kp.S;
+    const int nseg = (Nt + seg_len<D>() - 1) / seg_len<D>();
 #pragma unroll
     for (int c = 0; c < D; ++c) ckpt[((size_t)nseg * D + c) * mloc + lm] = x[c];
   }
@@ -417,7 +484,8 @@ template <typename R, int D, int DU, bool THETA>
 __device__ __forceinline__ void finish_theta(const KParams<R, D, DU> &kp, R (&th)[D + 2], bool active,
                                              double *__restrict__ partT, Pair<R> *red) {
   if constexpr (THETA) {
-#pragma unroll 1
+    // unrolled: a runtime index into th would keep the accumulators in local memory
+#pragma unroll
   for (int t = 0; t < D + 2; ++t) {
     Pair<R> v = {active ? th[t] : R(0), R(0)};
     const double s = block_sum_to_double(v, red);
@@ -509,6 +577,16 @@ __host__ __device__ constexpr int seg_log_cap() {
   return D <= 2 ? 8 : 4;
 }
 
+
+// The parameter-gradient variant of the recompute adjoint keeps each step's normals
+// from the forward replay (instead of drawing them again) when the doubled segment
+// buffer still leaves room for two or more blocks per SM.
+template <typename R, int D, bool THETA>
+__host__ __device__ constexpr bool recompute_zbuf() {
+  return THETA && (size_t)seg_len<D>() * D * TPB * sizeof(R) * 2 +
+                          (size_t)seg_log_cap<D>() * (2 + D) * TPB * sizeof(R) <= 100 * 1024;
+}
+
 template <typename R, int D, int DU, bool THETA>
 __global__ void __launch_bounds__(TPB)
 adj_recompute_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u,
@@ -517,9 +595,11 @@ adj_recompute_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__re
   using M = Ar<R>;
   constexpr int JS = seg_log_cap<D>();
   extern __shared__ __align__(16) unsigned char dsm[];
+  constexpr bool ZBUF = recompute_zbuf<R, D, THETA>();
   R *sbuf = reinterpret_cast<R *>(dsm);   // [S * D][TPB] segment states
   const int S = kp.S;
-  auto *skt = reinterpret_cast<typename V2<R>::T *>(sbuf + (size_t)S * D * TPB);   // [JS][TPB]
+  R *zbuf = sbuf + (size_t)S * D * TPB;   // ZBUF: [S * D][TPB] main-stream normals
+  auto *skt = reinterpret_cast<typename V2<R>::T *>(zbuf + (ZBUF ? (size_t)S * D * TPB : 0));   // [JS][TPB]
   R *sy = reinterpret_cast<R *>(skt + JS * TPB);                                    // [JS * D][TPB]
   __shared__ Pair<R> red1[TPB / 32];
   const int64_t npart = kp.npart;
@@ -552,7 +632,9 @@ adj_recompute_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__re
     for (int i = 0; i < len; ++i) {
 #pragma unroll
       for (int c = 0; c < D; ++c) sbuf[(i * D + c) * TPB + tid] = x[c];
-      if (forward_step(kp, k0 + i, m, u, x, lw)) jm |= 1u << i;
+      if (forward_step<R, D, DU, LogWriter<R, D>, ZBUF, !THETA>(kp, k0 + i, m, u, x, lw,
+                                                                zbuf + (size_t)i * D * TPB + tid, TPB))
+        jm |= 1u << i;
     }
     LogReader<R, D> lr;
     lr.L = sl;
@@ -572,7 +654,8 @@ adj_recompute_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__re
           R xk[D];
 #pragma unroll
           for (int c = 0; c < D; ++c) xk[c] = sbuf[(i * D + c) * TPB + tid];
-          backward_step<R, D, DU, THETA>(kp, k, m, (jm >> i) & 1u, xk, u, xd, mu, g, th, lr);
+          backward_step<R, D, DU, THETA, LogReader<R, D>, ZBUF>(kp, k, m, (jm >> i) & 1u, xk, u, xd, mu, g, th,
+                                                                lr, zbuf + (size_t)i * D * TPB + tid, TPB);
         }
 #pragma unroll
         for (int l = 0; l < DU; ++l) gb[j][l] = {active ? g[l] : R(0), R(0)};
@@ -586,11 +669,6 @@ adj_recompute_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__re
 // ---------------------------------------------------------------------------
 // Host-side launch ops for one (precision, D, DU)
 // ---------------------------------------------------------------------------
-template <int D>
-constexpr int seg_len() {
-  return D <= 2 ? 32 : (D <= 8 ? 16 : 8);
-}
-
 // Poisson thresholds floor(2^32 F(n; mu)) with the pmf accumulated in order
 // p_0 = exp(-mu), p_n = p_{n-1} mu / n; clamped to [0, 2^32].
 inline void poisson_thresholds(double mu, unsigned long long *thr) {
@@ -680,8 +758,9 @@ cudaError_t op_fwd(const jd_problem *p, int mode, int64_t m_begin, int64_t mloc,
 }
 
 template <typename R, int D>
-constexpr size_t recompute_smem() {
-  return (size_t)seg_len<D>() * D * TPB * sizeof(R) + (size_t)seg_log_cap<D>() * (2 + D) * TPB * sizeof(R);
+constexpr size_t recompute_smem(bool zbuf = false) {
+  return (size_t)seg_len<D>() * D * TPB * sizeof(R) * (zbuf ? 2 : 1) +
+         (size_t)seg_log_cap<D>() * (2 + D) * TPB * sizeof(R);
 }
 
 template <typename R, int D, int DU>
@@ -705,7 +784,7 @@ cudaError_t op_adj(const jd_problem *p, int variant, bool theta, int64_t m_begin
       adj_stored_kernel<R, D, DU, false><<<grid, TPB, 0, s>>>(*kp, u, xd, tr, b.flags, jl, b.jcnt, b.partG,
                                                               b.partT, lo, mloc);
   } else {
-    const size_t smem = recompute_smem<R, D>();
+    const size_t smem = recompute_smem<R, D>(theta && recompute_zbuf<R, D, true>());
     const R *ck = static_cast<const R *>(b.ckpt);
     if (theta) {
       err = cudaFuncSetAttribute(adj_recompute_kernel<R, D, DU, true>,

@@ -236,10 +236,12 @@ __device__ __forceinline__ void cc_matvec(const float *M, float *vcol, const flo
 }
 
 // Main-stream noise of step k: block 0 first (its word 0 decides the Poisson count);
-// when the step has no jump, x_c += sigma_c sqrt(dt) Z_c is added in place, block by
-// block, so no copy of the state is kept.  Returns word 0.
+// when the step has no jump, x_c += sigma_c sqrt(dt) Z_c.  Blocks 1..8 run in a rolled
+// loop that parks the 30 normals in the thread's shared-memory column zcol[c * TPB]
+// (the unrolled form is 9 Philox blocks and 16 Box-Muller pairs of straight-line code,
+// which overflowed the instruction cache).  Returns word 0.
 __device__ __forceinline__ uint32_t main_noise_or_jump(const KP32 &kp, int k, uint32_t m, float (&x)[32],
-                                                        bool &jump) {
+                                                        float *zcol, bool &jump) {
   const uint4 o0 = philox10((uint32_t)k, m, 0u, kp.epoch, kp.key0, kp.key1);
   jump = has_jump(kp, o0.x);
   if (jump) return o0.x;
@@ -250,22 +252,24 @@ __device__ __forceinline__ uint32_t main_noise_or_jump(const KP32 &kp, int k, ui
     x[0] = __fmaf_rn(kp.sig_sqdt[0], z0, x[0]);
     x[1] = __fmaf_rn(kp.sig_sqdt[1], z1, x[1]);
   }
-#pragma unroll
+#pragma unroll 1
   for (int b = 1; b < 9; ++b) {
     const uint4 o = philox10((uint32_t)k, m, (uint32_t)b, kp.epoch, kp.key0, kp.key1);
     // words 4b..4b+3: pairs (4b-1, 4b) and (4b+1, 4b+2); word 4b+3 carries over
     const int c = 4 * b - 2;   // components of pair (4b-1, 4b)
     float z0, z1;
     normal_pair<float>(carry, o.x, z0, z1);
-    x[c] = __fmaf_rn(kp.sig_sqdt[c], z0, x[c]);
-    x[c + 1] = __fmaf_rn(kp.sig_sqdt[c + 1], z1, x[c + 1]);
+    zcol[c * TPB] = z0;
+    zcol[(c + 1) * TPB] = z1;
     if (b < 8) {
       normal_pair<float>(o.y, o.z, z0, z1);
-      x[c + 2] = __fmaf_rn(kp.sig_sqdt[c + 2], z0, x[c + 2]);
-      x[c + 3] = __fmaf_rn(kp.sig_sqdt[c + 3], z1, x[c + 3]);
+      zcol[(c + 2) * TPB] = z0;
+      zcol[(c + 3) * TPB] = z1;
       carry = o.w;
     }
   }
+#pragma unroll
+  for (int c = 2; c < 32; ++c) x[c] = __fmaf_rn(kp.sig_sqdt[c], zcol[c * TPB], x[c]);
   return o0.x;
 }
 
@@ -396,9 +400,23 @@ __device__ __noinline__ float fwd32_one_jump(const KP32 &kp, const float *at, fl
   return th;
 }
 
+// bu[k][c] = sum_l B[c][l] u_k[l] (FP32, multiply-adds in the order l = 0..3 from zero):
+// the control's drift term is the same for every path, so it is formed once per step.
+__global__ void bu32_kernel(const KP32 *__restrict__ kpg, const float *__restrict__ u, float *__restrict__ bu,
+                            int Nt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= Nt * 32) return;
+  const int k = i >> 5, c = i & 31;
+  float bc = 0.f;
+#pragma unroll
+  for (int l = 0; l < DU32; ++l) bc = __fmaf_rn(kpg->B[c * DU32 + l], u[(size_t)k * DU32 + l], bc);
+  bu[i] = bc;
+}
+
 template <int TC>
 __global__ void __launch_bounds__(TPB, 4)
-fwd32_kernel(const KP32 *__restrict__ kpg, const float *__restrict__ u, const float *__restrict__ xd,
+fwd32_kernel(const KP32 *__restrict__ kpg, const float *__restrict__ u, const float *__restrict__ bu,
+             const float *__restrict__ xd,
              double *__restrict__ partC, float *__restrict__ traj, uint32_t *__restrict__ flags,
              float *__restrict__ pcost, JLog<float, D32> jl, int *__restrict__ jcnt, int *status,
              int64_t mloc) {
@@ -445,18 +463,17 @@ fwd32_kernel(const KP32 *__restrict__ kpg, const float *__restrict__ u, const fl
       cc_matvec(cs.at, vbuf + threadIdx.x, x, f);
     }
     bool jump;
-    const uint32_t w0 = main_noise_or_jump(kp, k, m, x, jump);   // x += noise unless jump
+    const uint32_t w0 = main_noise_or_jump(kp, k, m, x, vbuf + threadIdx.x, jump);   // x += noise unless jump
     if (TC) tc_collect(sh, (uint32_t)(k & 1), f, status);
     if (!jump) {
-      float uk[DU32];
+      const float4 *b4 = reinterpret_cast<const float4 *>(bu + (size_t)k * 32);
 #pragma unroll
-      for (int l = 0; l < DU32; ++l) uk[l] = __ldg(u + (size_t)k * DU32 + l);
-#pragma unroll
-      for (int c = 0; c < 32; ++c) {
-        float bc = 0.f;
-#pragma unroll
-        for (int l = 0; l < DU32; ++l) bc = __fmaf_rn(kp.B[c * DU32 + l], uk[l], bc);
-        x[c] = __fmaf_rn(kp.dt, __fadd_rn(f[c], bc), x[c]);
+      for (int q = 0; q < 8; ++q) {
+        const float4 bc = __ldg(b4 + q);
+        x[4 * q] = __fmaf_rn(kp.dt, __fadd_rn(f[4 * q], bc.x), x[4 * q]);
+        x[4 * q + 1] = __fmaf_rn(kp.dt, __fadd_rn(f[4 * q + 1], bc.y), x[4 * q + 1]);
+        x[4 * q + 2] = __fmaf_rn(kp.dt, __fadd_rn(f[4 * q + 2], bc.z), x[4 * q + 2]);
+        x[4 * q + 3] = __fmaf_rn(kp.dt, __fadd_rn(f[4 * q + 3], bc.w), x[4 * q + 3]);
       }
     } else if (kp.npair == 16 && (unsigned long long)w0 < kp.thr[1]) {
       fw |= 1u << (k & 31);
