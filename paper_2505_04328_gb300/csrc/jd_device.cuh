@@ -74,6 +74,36 @@ struct Ar<double> {
   }
 };
 
+// ---------------------------------------------------------------------------
+// Paired FP32 arithmetic: two independent lanes of a vector in one FFMA2 / FMUL2 (sm_100
+// and later).  Per component the rounding is that of __fmaf_rn / __fmul_rn, so the
+// paired and scalar forms give the same bits; FP64 stays scalar.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Pr {
+  static constexpr bool on = false;
+};
+template <>
+struct Pr<float> {
+  static constexpr bool on = true;
+  static __device__ __forceinline__ void fma(float a0, float a1, float b0, float b1, float &c0, float &c1) {
+    const float2 r = __ffma2_rn(make_float2(a0, a1), make_float2(b0, b1), make_float2(c0, c1));
+    c0 = r.x;
+    c1 = r.y;
+  }
+  static __device__ __forceinline__ void mul(float a0, float a1, float b0, float b1, float &r0, float &r1) {
+    const float2 r = __fmul2_rn(make_float2(a0, a1), make_float2(b0, b1));
+    r0 = r.x;
+    r1 = r.y;
+  }
+  // a - b as a + (-b): the same IEEE operation, so the same bits as __fsub_rn
+  static __device__ __forceinline__ void sub(float a0, float a1, float b0, float b1, float &r0, float &r1) {
+    const float2 r = __fadd2_rn(make_float2(a0, a1), make_float2(-b0, -b1));
+    r0 = r.x;
+    r1 = r.y;
+  }
+};
+
 template <typename R>
 __device__ __forceinline__ void normal_pair(uint32_t wa, uint32_t wb, R &z0, R &z1) {
   using M = Ar<R>;
@@ -81,8 +111,12 @@ __device__ __forceinline__ void normal_pair(uint32_t wa, uint32_t wb, R &z0, R &
   const R r = M::sqrt(M::mul(R(-2), M::log(ua)));
   R s, c;
   M::sincospi(M::mul(R(2), ub), &s, &c);
-  z0 = M::mul(r, c);
-  z1 = M::mul(r, s);
+  if constexpr (Pr<R>::on) {
+    Pr<R>::mul(r, r, c, s, z0, z1);
+  } else {
+    z0 = M::mul(r, c);
+    z1 = M::mul(r, s);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -198,6 +232,32 @@ template <typename R, int D, int DU>
 __device__ __forceinline__ void drift(const KParams<R, D, DU> &kp, const R (&y)[D], const R (&u)[DU],
                                       R (&f)[D]) {
   using M = Ar<R>;
+  if constexpr (Pr<R>::on && D % 2 == 0) {
+    // components i, i+1 together: the same operations in the same order as below
+#pragma unroll
+    for (int i = 0; i < D; i += 2) {
+      R s0 = R(0), s1 = R(0);
+#pragma unroll
+      for (int l = 0; l < DU; ++l) Pr<R>::fma(kp.B[i * DU + l], kp.B[(i + 1) * DU + l], u[l], u[l], s0, s1);
+#pragma unroll
+      for (int j = 0; j < D; ++j) Pr<R>::fma(kp.A[i * D + j], kp.A[(i + 1) * D + j], y[j], y[j], s0, s1);
+      f[i] = s0;
+      f[i + 1] = s1;
+    }
+    if (kp.cubic) {
+      R y2[D], y3[D];
+#pragma unroll
+      for (int j = 0; j < D; j += 2) {
+        Pr<R>::mul(y[j], y[j + 1], y[j], y[j + 1], y2[j], y2[j + 1]);
+        Pr<R>::mul(y2[j], y2[j + 1], y[j], y[j + 1], y3[j], y3[j + 1]);
+      }
+#pragma unroll
+      for (int i = 0; i < D; i += 2)
+#pragma unroll
+        for (int j = 0; j < D; ++j) Pr<R>::fma(kp.C[i * D + j], kp.C[(i + 1) * D + j], y3[j], y3[j], f[i], f[i + 1]);
+    }
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < D; ++i) {
     R s = R(0);
@@ -224,6 +284,32 @@ __device__ __forceinline__ void adjoint_update(const KParams<R, D, DU> &kp, cons
                                                R (&mu)[D]) {
   using M = Ar<R>;
   R t[D];
+  if constexpr (Pr<R>::on && D % 2 == 0) {
+    // components j, j+1 together: the same operations in the same order as below
+#pragma unroll
+    for (int j = 0; j < D; j += 2) {
+      R s0 = R(0), s1 = R(0);
+#pragma unroll
+      for (int i = 0; i < D; ++i) Pr<R>::fma(kp.A[i * D + j], kp.A[i * D + j + 1], mu[i], mu[i], s0, s1);
+      t[j] = s0;
+      t[j + 1] = s1;
+    }
+    if (kp.cubic) {
+#pragma unroll
+      for (int j = 0; j < D; j += 2) {
+        R s0 = R(0), s1 = R(0);
+#pragma unroll
+        for (int i = 0; i < D; ++i) Pr<R>::fma(kp.C[i * D + j], kp.C[i * D + j + 1], mu[i], mu[i], s0, s1);
+        R q0, q1, w0, w1;
+        Pr<R>::mul(y[j], y[j + 1], y[j], y[j + 1], q0, q1);
+        Pr<R>::mul(R(3), R(3), q0, q1, w0, w1);
+        Pr<R>::fma(w0, w1, s0, s1, t[j], t[j + 1]);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < D; j += 2) Pr<R>::fma(delta, delta, t[j], t[j + 1], mu[j], mu[j + 1]);
+    return;
+  }
 #pragma unroll
   for (int j = 0; j < D; ++j) {
     R s = R(0);
@@ -401,6 +487,16 @@ __device__ __forceinline__ void euler_substep(const KParams<R, D, DU> &kp, R de,
   R f[D];
   drift(kp, y, u, f);
   const R sq = M::sqrt(de);
+  if constexpr (Pr<R>::on && D % 2 == 0) {
+#pragma unroll
+    for (int c = 0; c < D; c += 2) {
+      R a0, a1;
+      Pr<R>::fma(de, de, f[c], f[c + 1], y[c], y[c + 1]);
+      Pr<R>::mul(kp.sigma[c], kp.sigma[c + 1], sq, sq, a0, a1);
+      Pr<R>::fma(a0, a1, z[c], z[c + 1], y[c], y[c + 1]);
+    }
+    return;
+  }
 #pragma unroll
   for (int c = 0; c < D; ++c) y[c] = M::fma(M::mul(kp.sigma[c], sq), z[c], M::fma(de, f[c], y[c]));
 }

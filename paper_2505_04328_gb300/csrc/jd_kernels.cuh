@@ -174,7 +174,16 @@ __device__ __forceinline__ int forward_step(const KParams<R, D, DU> &kp, int k, 
     R f[D];
     drift(kp, x, uk, f);
 #pragma unroll
-    for (int c = 0; c < D; ++c) x[c] = M::fma(kp.sig_sqdt[c], z[c], M::fma(kp.dt, f[c], x[c]));
+    for (int c = 0; c < D; ++c) {
+      if constexpr (Pr<R>::on && D % 2 == 0) {   // components c, c+1 in one paired FMA each
+        if (c % 2 == 0) {
+          Pr<R>::fma(kp.dt, kp.dt, f[c], f[c + 1], x[c], x[c + 1]);
+          Pr<R>::fma(kp.sig_sqdt[c], kp.sig_sqdt[c + 1], z[c], z[c + 1], x[c], x[c + 1]);
+        }
+      } else {
+        x[c] = M::fma(kp.sig_sqdt[c], z[c], M::fma(kp.dt, f[c], x[c]));
+      }
+    }
     return 0;
   }
   if (!INLINE_JUMP && kp.npair == MainWords<D>::PD && (unsigned long long)w0 < kp.thr[1]) {
@@ -240,6 +249,18 @@ __device__ __forceinline__ R cost_term(const KParams<R, D, DU> &kp, const R (&x)
                                        const R *__restrict__ xdk) {
   using M = Ar<R>;
   R t = R(0);
+  if constexpr (Pr<R>::on && D % 2 == 0) {
+    // differences and weights in pairs, the sum in the same order as below
+#pragma unroll
+    for (int c = 0; c < D; c += 2) {
+      R e0, e1, h0, h1;
+      Pr<R>::sub(x[c], x[c + 1], __ldg(xdk + c), __ldg(xdk + c + 1), e0, e1);
+      Pr<R>::mul(kp.hqdt[c], kp.hqdt[c + 1], e0, e1, h0, h1);
+      t = M::fma(h0, e0, t);
+      t = M::fma(h1, e1, t);
+    }
+    return t;
+  }
 #pragma unroll
   for (int c = 0; c < D; ++c) {
     const R e = M::sub(x[c], __ldg(xdk + c));
@@ -385,9 +406,18 @@ __device__ __forceinline__ void backward_step(const KParams<R, D, DU> &kp, int k
     adjoint_update(kp, xk, kp.dt, mu);
   }
   if (k >= 1) {
+    if constexpr (Pr<R>::on && D % 2 == 0) {
 #pragma unroll
-    for (int c = 0; c < D; ++c)
-      mu[c] = M::fma(kp.qdt[c], M::sub(xk[c], __ldg(xd + (size_t)k * D + c)), mu[c]);
+      for (int c = 0; c < D; c += 2) {
+        R e0, e1;
+        Pr<R>::sub(xk[c], xk[c + 1], __ldg(xd + (size_t)k * D + c), __ldg(xd + (size_t)k * D + c + 1), e0, e1);
+        Pr<R>::fma(kp.qdt[c], kp.qdt[c + 1], e0, e1, mu[c], mu[c + 1]);
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+        mu[c] = M::fma(kp.qdt[c], M::sub(xk[c], __ldg(xd + (size_t)k * D + c)), mu[c]);
+    }
   }
 }
 
@@ -601,6 +631,7 @@ adj_recompute_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__re
   R *zbuf = sbuf + (size_t)S * D * TPB;   // ZBUF: [S * D][TPB] main-stream normals
   auto *skt = reinterpret_cast<typename V2<R>::T *>(zbuf + (ZBUF ? (size_t)S * D * TPB : 0));   // [JS][TPB]
   R *sy = reinterpret_cast<R *>(skt + JS * TPB);                                    // [JS * D][TPB]
+  R *gcol = sy + (size_t)JS * D * TPB;   // THETA: [BATCH * DU][TPB] per-step contributions
   __shared__ Pair<R> red1[TPB / 32];
   const int64_t npart = kp.npart;
   const int64_t lm = (int64_t)blockIdx.x * TPB + threadIdx.x;
@@ -644,21 +675,46 @@ adj_recompute_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__re
 #pragma unroll 1
     for (int bb = nb - 1; bb >= 0; --bb) {
       Pair<R> gb[BATCH][DU];
+      if constexpr (THETA) {
+        // rolled over the batch (the parameter-gradient step is large): each step's
+        // contribution waits in the thread's shared column gcol[(j DU + l) TPB]
+#pragma unroll 1
+        for (int j = BATCH - 1; j >= 0; --j) {
+          const int i = BATCH * bb + j, k = k0 + i;
+          R g[DU];
 #pragma unroll
-      for (int j = BATCH - 1; j >= 0; --j) {
-        const int i = BATCH * bb + j, k = k0 + i;
-        R g[DU];
+          for (int l = 0; l < DU; ++l) g[l] = R(0);
+          if (i < len) {
+            R xk[D];
 #pragma unroll
-        for (int l = 0; l < DU; ++l) g[l] = R(0);
-        if (i < len) {
-          R xk[D];
+            for (int c = 0; c < D; ++c) xk[c] = sbuf[(i * D + c) * TPB + tid];
+            backward_step<R, D, DU, THETA, LogReader<R, D>, ZBUF>(kp, k, m, (jm >> i) & 1u, xk, u, xd, mu, g, th,
+                                                                  lr, zbuf + (size_t)i * D * TPB + tid, TPB);
+          }
 #pragma unroll
-          for (int c = 0; c < D; ++c) xk[c] = sbuf[(i * D + c) * TPB + tid];
-          backward_step<R, D, DU, THETA, LogReader<R, D>, ZBUF>(kp, k, m, (jm >> i) & 1u, xk, u, xd, mu, g, th,
-                                                                lr, zbuf + (size_t)i * D * TPB + tid, TPB);
+          for (int l = 0; l < DU; ++l) gcol[(j * DU + l) * TPB + tid] = active ? g[l] : R(0);
         }
 #pragma unroll
-        for (int l = 0; l < DU; ++l) gb[j][l] = {active ? g[l] : R(0), R(0)};
+        for (int j = 0; j < BATCH; ++j)
+#pragma unroll
+          for (int l = 0; l < DU; ++l) gb[j][l] = {gcol[(j * DU + l) * TPB + tid], R(0)};
+      } else {
+#pragma unroll
+        for (int j = BATCH - 1; j >= 0; --j) {
+          const int i = BATCH * bb + j, k = k0 + i;
+          R g[DU];
+#pragma unroll
+          for (int l = 0; l < DU; ++l) g[l] = R(0);
+          if (i < len) {
+            R xk[D];
+#pragma unroll
+            for (int c = 0; c < D; ++c) xk[c] = sbuf[(i * D + c) * TPB + tid];
+            backward_step<R, D, DU, THETA, LogReader<R, D>, ZBUF>(kp, k, m, (jm >> i) & 1u, xk, u, xd, mu, g, th,
+                                                                  lr, zbuf + (size_t)i * D * TPB + tid, TPB);
+          }
+#pragma unroll
+          for (int l = 0; l < DU; ++l) gb[j][l] = {active ? g[l] : R(0), R(0)};
+        }
       }
       reduce_batch<R, DU>(gb, k0 + BATCH * bb, Nt, partG, npart);
     }
@@ -757,10 +813,10 @@ cudaError_t op_fwd(const jd_problem *p, int mode, int64_t m_begin, int64_t mloc,
   return cudaGetLastError();
 }
 
-template <typename R, int D>
-constexpr size_t recompute_smem(bool zbuf = false) {
-  return (size_t)seg_len<D>() * D * TPB * sizeof(R) * (zbuf ? 2 : 1) +
-         (size_t)seg_log_cap<D>() * (2 + D) * TPB * sizeof(R);
+template <typename R, int D, int DU>
+constexpr size_t recompute_smem(bool theta) {
+  return (size_t)seg_len<D>() * D * TPB * sizeof(R) * (theta && recompute_zbuf<R, D, true>() ? 2 : 1) +
+         (size_t)seg_log_cap<D>() * (2 + D) * TPB * sizeof(R) + (theta ? (size_t)BATCH * DU * TPB * sizeof(R) : 0);
 }
 
 template <typename R, int D, int DU>
@@ -784,7 +840,7 @@ cudaError_t op_adj(const jd_problem *p, int variant, bool theta, int64_t m_begin
       adj_stored_kernel<R, D, DU, false><<<grid, TPB, 0, s>>>(*kp, u, xd, tr, b.flags, jl, b.jcnt, b.partG,
                                                               b.partT, lo, mloc);
   } else {
-    const size_t smem = recompute_smem<R, D>(theta && recompute_zbuf<R, D, true>());
+    const size_t smem = recompute_smem<R, D, DU>(theta);
     const R *ck = static_cast<const R *>(b.ckpt);
     if (theta) {
       err = cudaFuncSetAttribute(adj_recompute_kernel<R, D, DU, true>,

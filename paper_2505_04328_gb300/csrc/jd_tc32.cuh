@@ -225,12 +225,10 @@ __device__ __forceinline__ void cc_matvec(const float *M, float *vcol, const flo
     const float vk = vcol[k * TPB];
     const float4 *row = reinterpret_cast<const float4 *>(M + k * 32);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < 8; ++q) {   // paired FMAs: per component the rounding of __fmaf_rn
       const float4 a = row[q];
-      out[4 * q] = __fmaf_rn(a.x, vk, out[4 * q]);
-      out[4 * q + 1] = __fmaf_rn(a.y, vk, out[4 * q + 1]);
-      out[4 * q + 2] = __fmaf_rn(a.z, vk, out[4 * q + 2]);
-      out[4 * q + 3] = __fmaf_rn(a.w, vk, out[4 * q + 3]);
+      Pr<float>::fma(a.x, a.y, vk, vk, out[4 * q], out[4 * q + 1]);
+      Pr<float>::fma(a.z, a.w, vk, vk, out[4 * q + 2], out[4 * q + 3]);
     }
   }
 }
@@ -269,7 +267,8 @@ __device__ __forceinline__ uint32_t main_noise_or_jump(const KP32 &kp, int k, ui
     }
   }
 #pragma unroll
-  for (int c = 2; c < 32; ++c) x[c] = __fmaf_rn(kp.sig_sqdt[c], zcol[c * TPB], x[c]);
+  for (int c = 2; c < 32; c += 2)
+    Pr<float>::fma(kp.sig_sqdt[c], kp.sig_sqdt[c + 1], zcol[c * TPB], zcol[(c + 1) * TPB], x[c], x[c + 1]);
   return o0.x;
 }
 
@@ -470,10 +469,10 @@ fwd32_kernel(const KP32 *__restrict__ kpg, const float *__restrict__ u, const fl
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const float4 bc = __ldg(b4 + q);
-        x[4 * q] = __fmaf_rn(kp.dt, __fadd_rn(f[4 * q], bc.x), x[4 * q]);
-        x[4 * q + 1] = __fmaf_rn(kp.dt, __fadd_rn(f[4 * q + 1], bc.y), x[4 * q + 1]);
-        x[4 * q + 2] = __fmaf_rn(kp.dt, __fadd_rn(f[4 * q + 2], bc.z), x[4 * q + 2]);
-        x[4 * q + 3] = __fmaf_rn(kp.dt, __fadd_rn(f[4 * q + 3], bc.w), x[4 * q + 3]);
+        const float2 s01 = __fadd2_rn(make_float2(f[4 * q], f[4 * q + 1]), make_float2(bc.x, bc.y));
+        const float2 s23 = __fadd2_rn(make_float2(f[4 * q + 2], f[4 * q + 3]), make_float2(bc.z, bc.w));
+        Pr<float>::fma(kp.dt, kp.dt, s01.x, s01.y, x[4 * q], x[4 * q + 1]);
+        Pr<float>::fma(kp.dt, kp.dt, s23.x, s23.y, x[4 * q + 2], x[4 * q + 3]);
       }
     } else if (kp.npair == 16 && (unsigned long long)w0 < kp.thr[1]) {
       fw |= 1u << (k & 31);
@@ -642,7 +641,7 @@ adj32_kernel(const KP32 *__restrict__ kpg, const float *__restrict__ u, const fl
     if (!jumped) {
       control_sensitivity(kp, mu, kp.dt, g);
 #pragma unroll
-      for (int c = 0; c < 32; ++c) mu[c] = __fmaf_rn(kp.dt, t[c], mu[c]);
+      for (int c = 0; c < 32; c += 2) Pr<float>::fma(kp.dt, kp.dt, t[c], t[c + 1], mu[c], mu[c + 1]);
     } else {
       float ml[32], tl[32], gl[DU32];
 #pragma unroll
@@ -663,9 +662,11 @@ adj32_kernel(const KP32 *__restrict__ kpg, const float *__restrict__ u, const fl
         float v[4];
         Vec4<float>::load(traj + (((size_t)k * 8 + c4) * mloc + lmc) * 4, v);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < 4; q += 2) {   // paired: the rounding of __fsub_rn / __fmaf_rn per component
           const int c = 4 * c4 + q;
-          mu[c] = __fmaf_rn(kp.qdt[c], __fsub_rn(v[q], __ldg(xd + (size_t)k * D32 + c)), mu[c]);
+          float e0, e1;
+          Pr<float>::sub(v[q], v[q + 1], __ldg(xd + (size_t)k * D32 + c), __ldg(xd + (size_t)k * D32 + c + 1), e0, e1);
+          Pr<float>::fma(kp.qdt[c], kp.qdt[c + 1], e0, e1, mu[c], mu[c + 1]);
         }
       }
     }
