@@ -198,9 +198,10 @@ __global__ void opt_pgnorm_kernel(int n, const double *__restrict__ u, const dou
 
 // Trial point ut = clip(u - zeta g) and <g, ut - u>_{L2} = sum grad (ut - u).
 __global__ void opt_trial_kernel(int n, const double *__restrict__ u, const double *__restrict__ grad,
-                                 double zeta, double dt, double lo, double hi,
+                                 const double *__restrict__ zeta_p, double dt, double lo, double hi,
                                  double *__restrict__ ut, double *__restrict__ dot) {
   __shared__ double sm[32];
+  const double zeta = *zeta_p;
   double a = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const double g = grad[i] / dt;
@@ -259,7 +260,8 @@ static jd_status cuda_fail(cudaError_t e, const char *what) {
   } while (0)
 
 // Scalar slots in p->scal_d
-enum { S_J = 0, S_JT = 1, S_DOT = 2, S_PG = 3, S_ACC = 4, S_STEP = 5, S_STATUS = 6, S_BAD = 7, S_THETA = 8 };
+enum { S_J = 0, S_JT = 1, S_DOT = 2, S_PG = 3, S_ACC = 4, S_STEP = 5, S_STATUS = 6, S_BAD = 7, S_THETA = 8,
+       S_ZETA = 42 };
 constexpr int NSCAL = kScalars;
 
 static bool finite_all(const double *a, size_t n) {
@@ -628,57 +630,110 @@ static jd_status validate_desc(const jd_problem_desc &q) {
 // ---------------------------------------------------------------------------
 // Optimizer state machine (Algorithm 5.4, eq:Stochastic_Armijo)
 // ---------------------------------------------------------------------------
-// Phase ends: the first 8 scalars go to pinned memory, then the event.
-static jd_status end_phase(jd::OptMachine &m, jd::OptMachine::Phase ph) {
-  jd_problem *p = m.p;
-  JD_CUDA(cudaMemcpyAsync(p->host_pinned, p->scal_d, 8 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
-  JD_CUDA(cudaEventRecord(m.ev, p->stream));
-  m.phase = ph;
-  return JD_OK;
-}
 
-// Gradient at u^n (the accepted trial's forward sweep is reused) and the projected-
-// gradient norm.
-static jd_status launch_grad(jd::OptMachine &m) {
-  jd_problem *p = m.p;
+// Work of a gradient phase: gradient at u^n (the accepted trial's forward sweep is reused
+// when forward_done), projected-gradient norm, first scalars to pinned memory.
+static jd_status enqueue_grad(jd_problem *p, bool forward_done) {
   const jd_problem_desc &q = p->desc;
   jd_status s = clear_bad(p);
-  if (!s) s = run_gradient(p, p->opt_u, false, m.forward_done);
+  if (!s) s = run_gradient(p, p->opt_u, false, forward_done);
   if (s) return s;
-  m.forward_done = false;
-  m.r.evals++;
-  m.grads++;
   const int pr = prof_begin(KC_OPT, p->stream);
   opt_pgnorm_kernel<<<1, 256, 0, p->stream>>>(q.Nt * q.du, p->opt_u, p->grad_d, q.T / q.Nt, q.u_min, q.u_max,
                                               p->scal_d + S_PG);
   prof_end(pr, p->stream);
   count_launch();
   JD_CUDA(cudaGetLastError());
-  return end_phase(m, jd::OptMachine::GRAD);
+  JD_CUDA(cudaMemcpyAsync(p->host_pinned, p->scal_d, 8 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  return JD_OK;
 }
 
-// One Armijo trial at the current zeta: trial point, forward sweep in the plan's mode,
-// device-side acceptance test.
-static jd_status launch_trial(jd::OptMachine &m) {
-  jd_problem *p = m.p;
+// Work of a trial phase: zeta from pinned memory, trial point, forward sweep in the
+// plan's mode, device-side acceptance test, first scalars to pinned memory.
+static jd_status enqueue_trial(jd_problem *p, double armijo_c) {
   const jd_problem_desc &q = p->desc;
   const int n = q.Nt * q.du;
   const double dt = q.T / q.Nt;
+  JD_CUDA(cudaMemcpyAsync(p->scal_d + S_ZETA, p->host_pinned + S_ZETA, sizeof(double), cudaMemcpyHostToDevice,
+                          p->stream));
   int pr = prof_begin(KC_OPT, p->stream);
-  opt_trial_kernel<<<1, 256, 0, p->stream>>>(n, p->opt_u, p->grad_d, m.zeta, dt, q.u_min, q.u_max, p->opt_ut,
-                                             p->scal_d + S_DOT);
+  opt_trial_kernel<<<1, 256, 0, p->stream>>>(n, p->opt_u, p->grad_d, p->scal_d + S_ZETA, dt, q.u_min, q.u_max,
+                                             p->opt_ut, p->scal_d + S_DOT);
   prof_end(pr, p->stream);
   count_launch();
   JD_CUDA(cudaGetLastError());
   jd_status s = run_plan_forward(p, p->opt_ut, S_JT);
   if (s) return s;
-  m.r.evals++;
   pr = prof_begin(KC_OPT, p->stream);
-  opt_accept_kernel<<<1, 256, 0, p->stream>>>(n, p->opt_u, p->opt_ut, m.o.armijo_c, dt, p->scal_d);
+  opt_accept_kernel<<<1, 256, 0, p->stream>>>(n, p->opt_u, p->opt_ut, armijo_c, dt, p->scal_d);
   prof_end(pr, p->stream);
   count_launch();
   JD_CUDA(cudaGetLastError());
-  return end_phase(m, jd::OptMachine::TRIAL);
+  JD_CUDA(cudaMemcpyAsync(p->host_pinned, p->scal_d, 8 * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  return JD_OK;
+}
+
+// Run one phase's work: captured into a graph on first use and replayed afterwards
+// (use_graphs), or enqueued directly.  The phase ends with a record of m.ev.
+template <typename F>
+static jd_status run_phase(jd::OptMachine &m, cudaGraphExec_t *exec, int *nlaunch, F &&enqueue) {
+  jd_problem *p = m.p;
+  if (!m.use_graphs) {
+    jd_status s = enqueue();
+    if (s) return s;
+  } else {
+    if (!*exec) {
+      const uint64_t before = g_launches.load();
+      JD_CUDA(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+      const jd_status s = enqueue();
+      cudaGraph_t graph = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(p->stream, &graph);
+      if (s) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+      }
+      JD_CUDA(e);
+      const cudaError_t ei = cudaGraphInstantiate(exec, graph, 0);
+      cudaGraphDestroy(graph);
+      JD_CUDA(ei);
+      *nlaunch = (int)(g_launches.load() - before);   // captured, not launched: count on replay
+      g_launches.fetch_sub((uint64_t)*nlaunch);
+    }
+    JD_CUDA(cudaGraphLaunch(*exec, p->stream));
+    count_launch(*nlaunch);
+  }
+  JD_CUDA(cudaEventRecord(m.ev, p->stream));
+  return JD_OK;
+}
+
+static jd_status launch_grad(jd::OptMachine &m) {
+  const int v = m.forward_done ? 1 : 0;
+  jd_problem *p = m.p;
+  const jd_status s = run_phase(m, &m.g_grad[v], &m.n_grad[v], [&]() { return enqueue_grad(p, v == 1); });
+  if (s) return s;
+  m.forward_done = false;
+  m.r.evals++;
+  m.grads++;
+  m.phase = jd::OptMachine::GRAD;
+  return JD_OK;
+}
+
+// One Armijo trial at the current zeta.
+static jd_status launch_trial(jd::OptMachine &m) {
+  jd_problem *p = m.p;
+  p->host_pinned[S_ZETA] = m.zeta;   // read by the trial's copy when it executes
+  const double c = m.o.armijo_c;
+  const jd_status s = run_phase(m, &m.g_trial, &m.n_trial, [&]() { return enqueue_trial(p, c); });
+  if (s) return s;
+  m.r.evals++;
+  m.phase = jd::OptMachine::TRIAL;
+  return JD_OK;
+}
+
+void jd::opt_release(OptMachine &m) {
+  for (auto &g : m.g_grad)
+    if (g) cudaGraphExecDestroy(g), g = nullptr;
+  if (m.g_trial) cudaGraphExecDestroy(m.g_trial), m.g_trial = nullptr;
 }
 
 // Final iterate to the caller's buffer.
@@ -713,6 +768,19 @@ jd_status jd::opt_begin(OptMachine &m, jd_problem *p, const jd_opt_params &o, do
   m.pg0 = -1.0;
   m.forward_done = false;
   const size_t n = (size_t)p->desc.Nt * p->desc.du;
+  if (m.use_graphs) {
+    // graphs hold fixed launches: not for the d = 32 kernels (their coefficient upload
+    // is a pageable copy per launch) nor while kernel timing is recorded; the plan's
+    // buffers are allocated before the first capture
+    bool prof;
+    {
+      std::lock_guard<std::mutex> g(g_prof_mu);
+      prof = g_prof_on;
+    }
+    if (p->D == 32 || prof) m.use_graphs = false;
+    jd_status s = ensure_plan(p);
+    if (s) return s;
+  }
   JD_CUDA(cudaMemcpyAsync(p->opt_u, p->u_in, n * 8, cudaMemcpyDeviceToDevice, p->stream));
   if (o.max_iter == 0) return launch_output(m, JD_OK);
   return launch_grad(m);

@@ -129,7 +129,7 @@ struct ProblemOpts {
   double *pinned = nullptr;          // null: own pinned scalar buffer (kScalars doubles)
   bool async_alloc = false;
 };
-constexpr int kScalars = 8 + 34;     // FP64 scalar slots per problem (device and pinned)
+constexpr int kScalars = 8 + 34 + 2;   // FP64 scalar slots per problem (device and pinned)
 
 jd_status create_problem(const jd_problem_desc &q, const ProblemOpts &o, jd_problem **out);
 
@@ -159,10 +159,16 @@ struct OptMachine {
   int it = 0, backtracks = 0, grads = 0;
   double zeta = 1.0, zeta_max = 1e3, pg0 = -1.0;
   bool forward_done = false;
+  // CUDA graphs: each phase's launch sequence is captured on first use and replayed
+  // (gradient with and without the forward sweep, trial); kernels per graph counted
+  bool use_graphs = false;
+  cudaGraphExec_t g_grad[2] = {nullptr, nullptr}, g_trial = nullptr;
+  int n_grad[2] = {0, 0}, n_trial = 0;
 };
 // p->u_in holds u^0.  u_dst (space us) receives the final iterate.
 jd_status opt_begin(OptMachine &m, ::jd_problem *p, const jd_opt_params &o, double *u_dst,
                     jd_memspace us, double *J_hist);
 jd_status opt_advance(OptMachine &m);
+void opt_release(OptMachine &m);   // frees the machine's graphs
 
 }  // namespace jd

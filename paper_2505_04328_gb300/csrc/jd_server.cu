@@ -136,6 +136,7 @@ void finish_request(jd_server *s, Slot &sl, jd_status st) {
     rq->t_done = s->now();
     rq->done = true;
   }
+  jd::opt_release(sl.m);
   if (sl.p) jd_problem_destroy(sl.p);   // stream-ordered frees: no device-wide sync
   sl.p = nullptr;
   sl.req = nullptr;
@@ -183,6 +184,7 @@ bool admit_one(jd_server *s) {
   Slot &sl = *free_slot;
   sl.m = jd::OptMachine();
   sl.m.ev = sl.ev;
+  sl.m.use_graphs = true;   // every phase of a request replays a captured graph
   rq->t_admit = s->now();
   rq->plan = plan;
   rq->bytes = bytes;
