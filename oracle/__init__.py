@@ -56,7 +56,7 @@ class _Problem(ctypes.Structure):
         ("jump_law", ctypes.c_int), ("jump_scale", ctypes.c_double),
         ("x0", ctypes.c_void_p), ("q", ctypes.c_void_p), ("xd", ctypes.c_void_p),
         ("nu", ctypes.c_double), ("u_min", ctypes.c_double), ("u_max", ctypes.c_double),
-        ("seed", ctypes.c_uint64), ("epoch", ctypes.c_uint32),
+        ("seed", ctypes.c_uint64), ("epoch", ctypes.c_uint32), ("jump_gain", ctypes.c_double),
     ]
 
 
@@ -123,7 +123,7 @@ class OracleProblem:
             A=_ptr(a["A"]), C=_ptr(a["C"]), B=_ptr(a["B"]), dA=_ptr(a["dA"]),
             sigma=_ptr(a["sigma"]), lam=p.lam, jump_law=p.jump_law, jump_scale=p.jump_scale,
             x0=_ptr(a["x0"]), q=_ptr(a["q"]), xd=_ptr(a["xd"]), nu=p.nu, u_min=p.u_min,
-            u_max=p.u_max, seed=p.seed, epoch=p.epoch)
+            u_max=p.u_max, seed=p.seed, epoch=p.epoch, jump_gain=getattr(p, "jump_gain", 1.0))
 
     def _u(self, u):
         p = self.p

@@ -133,7 +133,7 @@ int orc_step_draws(const orc_problem *P, int k, int64_t m, orc_draws *D) {
   for (int i = 0; i < n; ++i) {
     stream_words(P, k, m, 1u, (uint32_t)(i + 1), 1 + 4 * npair, w);
     theta[i] = orc_u01(w[0]);
-    if (P->jump_law == ORC_JUMP_NORMAL) {
+    if (P->jump_law == ORC_JUMP_NORMAL || P->jump_law == ORC_JUMP_KS) {
       normals_from_words(d, w + 1, xi[i]);
     } else {
       for (int c = 0; c < d; ++c) xi[i][c] = 2.0 * orc_u01(w[1 + c]) - 1.0;
@@ -194,9 +194,21 @@ static void drift_jacobian_T(const orc_problem *P, const double *y, const double
   }
 }
 
+/* The jump map c acts on component c of the state: additive jumps move every component,
+ * y + s xi (NORMAL, UNIFORM); the Keilson-Storer reset (Sec. 5.3 Eq. jump_law) acts on
+ * the velocity half of the state z = (x, v), components c >= d/2: v <- gamma v + s xi,
+ * positions unchanged.  jump_gain_of is the diagonal of the map's Jacobian. */
+static int jump_acts_on(const orc_problem *P, int c) {
+  return P->jump_law != ORC_JUMP_KS || c >= P->d / 2;
+}
+
+static double jump_gain_of(const orc_problem *P, int c) {
+  return (P->jump_law == ORC_JUMP_KS && c >= P->d / 2) ? P->jump_gain : 1.0;
+}
+
 /* Sub-step start states of step k (Algorithm 5.1): Y[0] = X_k; Euler sub-step of
- * length delta_i with the drift at its left end; the jump of slot i+1 is added after
- * sub-step i (additive jump map c(z) = z + xi). Y[n+1] = X_{k+1}. */
+ * length delta_i with the drift at its left end; the jump of slot i+1 is applied after
+ * sub-step i (c(z) = z + xi, or the velocity reset). Y[n+1] = X_{k+1}. */
 static void integrate_step(const orc_problem *P, const orc_draws *D, const double *xk,
                            const double *uk, double (*Y)[ORC_DMAX]) {
   const int d = P->d;
@@ -207,7 +219,8 @@ static void integrate_step(const orc_problem *P, const orc_draws *D, const doubl
     double sq = sqrt(D->delta[i]);
     for (int c = 0; c < d; ++c) {
       Y[i + 1][c] = Y[i][c] + D->delta[i] * f[c] + P->sigma[c] * sq * D->Z[i][c];
-      if (i < D->n) Y[i + 1][c] += P->jump_scale * D->xi_hat[i][c];
+      if (i < D->n && jump_acts_on(P, c))
+        Y[i + 1][c] = jump_gain_of(P, c) * Y[i + 1][c] + P->jump_scale * D->xi_hat[i][c];
     }
   }
 }
@@ -227,7 +240,7 @@ static int valid(const orc_problem *P) {
     return 0;
   if (!P->A || !P->B || !P->sigma || !P->x0 || !P->q || !P->xd) return 0;
   if (P->drift == ORC_CUBIC && !P->C) return 0;
-  if (P->jump_law < 0 || P->jump_law > 2) return 0;
+  if (P->jump_law < 0 || P->jump_law > 3) return 0;
   return 1;
 }
 
@@ -267,10 +280,15 @@ int orc_path(const orc_problem *P, const double *u, int64_t m, double *X, double
       double g[ORC_DUMAX];
       memset(g, 0, sizeof(g));
       for (int i = D->n; i >= 0; --i) {
-        /* mu = derivative w.r.t. Y[i+1]; the additive jump after sub-step i has
-         * identity Jacobian, so it is also the derivative w.r.t. the pre-jump state */
-        if (gtheta && i < D->n)
-          for (int c = 0; c < d; ++c) gtheta[d + 1] += mu[c] * D->xi_hat[i][c];
+        /* mu = derivative w.r.t. Y[i+1], the state after the jump that follows sub-step
+         * i; the jump's Jacobian (identity for additive jumps, gamma on the velocities
+         * for the reset) turns it into the derivative w.r.t. the pre-jump state */
+        if (i < D->n) {
+          if (gtheta)
+            for (int c = 0; c < d; ++c)
+              if (jump_acts_on(P, c)) gtheta[d + 1] += mu[c] * D->xi_hat[i][c];
+          for (int c = 0; c < d; ++c) mu[c] *= jump_gain_of(P, c);
+        }
         for (int l = 0; l < du; ++l) {
           double s = 0.0;
           for (int c = 0; c < d; ++c) s += P->B[c * du + l] * mu[c];

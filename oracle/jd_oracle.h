@@ -38,7 +38,7 @@ extern "C" {
 #define ORC_NMAX 16      /* jumps per uniform step are capped at this count */
 
 enum { ORC_LINEAR = 0, ORC_CUBIC = 1 };
-enum { ORC_JUMP_NONE = 0, ORC_JUMP_NORMAL = 1, ORC_JUMP_UNIFORM = 2 };
+enum { ORC_JUMP_NONE = 0, ORC_JUMP_NORMAL = 1, ORC_JUMP_UNIFORM = 2, ORC_JUMP_KS = 3 };
 
 typedef struct {
   int d, du, Nt;
@@ -52,13 +52,14 @@ typedef struct {
   const double *sigma;       /* d, diagonal additive diffusion */
   double lambda;             /* jump intensity */
   int jump_law;              /* ORC_JUMP_* */
-  double jump_scale;         /* std (NORMAL) or half-width (UNIFORM) */
+  double jump_scale;         /* std (NORMAL, KS) or half-width (UNIFORM) */
   const double *x0;          /* d */
   const double *q;           /* d, diagonal tracking weights */
   const double *xd;          /* (Nt+1)*d target samples xd(t_k) */
   double nu, u_min, u_max;
   uint64_t seed;
   uint32_t epoch;
+  double jump_gain;          /* KS: velocity gain gamma of the reset v <- gamma v + s xi */
 } orc_problem;
 
 /* One Philox4x32-10 block: out = Philox(key, ctr). */

@@ -151,3 +151,33 @@ def test_gradient_is_mean_of_path_sensitivities():
     assert np.allclose(g, p.nu * p.dt * u + G, rtol=1e-13, atol=1e-16)
     c = np.mean([r["cost"] for r in rs])
     assert abs(J - (c + 0.5 * p.nu * p.dt * (u ** 2).sum())) < 1e-13
+
+
+# --- Keilson-Storer velocity resets (Sec. 5.3 eq:jump_law) -------------------------
+def test_fd_keilson_storer():
+    """Reset v <- gamma v + s xi: the adjoint crosses each jump as lambda_v <- gamma
+    lambda_v.  Central differences in u (random directions), in x0 (lambda_0), and in
+    the jump scale s pin it; a dropped gamma, or a gamma applied to the position,
+    fails here."""
+    p = workloads.ks_oscillator(M=400, Nt=60, gamma=0.7).replace(lam=6.0)
+    u = workloads.random_control(p, scale=0.5)
+    _, g, gth = oracle.gradient(p, u, theta=True)
+    rng = np.random.default_rng(5)
+    for _ in range(4):
+        e = rng.standard_normal(u.shape)
+        e /= np.linalg.norm(e)
+        fd = _fd(lambda v: oracle.cost(p, v), u, e, 1e-4)
+        assert abs(fd - float((g * e).sum())) <= 1e-8 * np.linalg.norm(g) + 1e-13
+    # lambda_0 of one path against differences in the initial state
+    r = oracle.path(p, u, 7)
+    for c in range(2):
+        e = np.zeros(2)
+        e[c] = 1.0
+        fd = (oracle.path(p.replace(x0=p.x0 + 1e-5 * e), u, 7)["cost"]
+              - oracle.path(p.replace(x0=p.x0 - 1e-5 * e), u, 7)["cost"]) / 2e-5
+        assert abs(fd - r["lam"][0, c]) <= 1e-7 * max(1.0, abs(fd)), c
+    # jump-scale derivative (only the velocity is moved by a reset)
+    h = 1e-5
+    fd = (oracle.cost(p.replace(jump_scale=p.jump_scale + h), u)
+          - oracle.cost(p.replace(jump_scale=p.jump_scale - h), u)) / (2 * h)
+    assert abs(fd - gth[3]) <= 1e-6 * max(1.0, abs(fd))

@@ -140,3 +140,25 @@ def test_cost_and_gradient_independent_of_thread_count():
     J1, g1, _ = oracle.gradient(p, u, nthreads=1)
     J4, g4, _ = oracle.gradient(p, u, nthreads=5)
     assert J1 == J4 and np.array_equal(g1, g4)
+
+
+def test_keilson_storer_moments_closed_form():
+    """Pure velocity resets v <- gamma v + s xi at Poisson times of rate lam (no drift,
+    no diffusion): with N(t) ~ Poisson(lam t),
+        E v(t)   = v0 exp(-lam (1 - gamma) t),
+        E v(t)^2 = v0^2 exp(-lam (1 - gamma^2) t) + s^2 (1 - exp(-lam (1 - gamma^2) t)) / (1 - gamma^2),
+    and the position component of z = (x, v) is never moved by a reset."""
+    lam, gamma, s, v0, T = 3.0, 0.6, 0.4, 1.5, 1.0
+    p = workloads.ks_oscillator(M=20000, Nt=8).replace(
+        A=np.zeros((2, 2)), B=np.zeros((2, 1)), sigma=np.zeros(2), x0=np.array([0.25, v0]),
+        lam=lam, jump_scale=s, jump_gain=gamma, T=T)
+    X = np.stack([oracle.path(p, None, m, adjoint=False)["X"][-1] for m in range(p.M)])
+    assert np.all(X[:, 0] == 0.25)
+    v = X[:, 1]
+    m1 = v0 * np.exp(-lam * (1 - gamma) * T)
+    e2 = np.exp(-lam * (1 - gamma ** 2) * T)
+    m2 = v0 ** 2 * e2 + s ** 2 * (1 - e2) / (1 - gamma ** 2)
+    se1 = np.sqrt(np.var(v) / p.M)
+    se2 = np.sqrt(np.var(v ** 2) / p.M)
+    assert abs(v.mean() - m1) < 4 * se1, (v.mean(), m1, se1)
+    assert abs(np.mean(v ** 2) - m2) < 4 * se2, (np.mean(v ** 2), m2, se2)

@@ -34,7 +34,7 @@ from typing import Optional
 import numpy as np
 
 LINEAR, CUBIC = 0, 1
-JUMP_NONE, JUMP_NORMAL, JUMP_UNIFORM = 0, 1, 2
+JUMP_NONE, JUMP_NORMAL, JUMP_UNIFORM, JUMP_KS = 0, 1, 2, 3
 
 
 @dataclasses.dataclass
@@ -56,6 +56,7 @@ class Problem:
     lam: float = 0.0
     jump_law: int = JUMP_NONE
     jump_scale: float = 0.0
+    jump_gain: float = 1.0        # JUMP_KS: velocity gain gamma (v <- gamma v + jump_scale xi)
     nu: float = 1e-3
     u_min: float = -5.0
     u_max: float = 5.0
@@ -97,6 +98,8 @@ def _target(name: str, T: float, Nt: int, d: int) -> np.ndarray:
         return np.sin(2 * np.pi * t).reshape(Nt + 1, 1)
     if name.startswith("double_well"):
         return np.stack([np.ones_like(t), np.sin(2 * np.pi * t)], axis=1)
+    if name.startswith("ks_oscillator"):
+        return np.stack([0.5 * np.cos(np.pi * t), -0.5 * np.pi * np.sin(np.pi * t)], axis=1)
     return np.zeros((Nt + 1, d))
 
 
@@ -134,6 +137,21 @@ def double_well_autograd(M: int = 1 << 22, Nt: int = 4096, seed: int = 0) -> Pro
     p.name = "double_well_autograd"
     p.dA = np.array([[0.0, 0.0], [0.0, -1.0]])
     return p
+
+
+def ks_oscillator(M: int = 1 << 20, Nt: int = 500, seed: int = 0, beta: float = 10.0,
+                  gamma: float = 0.9) -> Problem:
+    """The paper's phase-space particle with Keilson-Storer velocity resets (Sec. 5.3,
+    Sec. 6 parameters beta = 10, gamma = 0.9): z = (x, v), harmonic drift x' = v,
+    v' = -x + u, jumps at rate sqrt(beta/pi) resetting v <- gamma v + N(0, 1/(2 beta)),
+    small diffusion, tracking a half-amplitude circle."""
+    return Problem(
+        name="ks_oscillator", d=2, du=1, T=1.0, Nt=Nt, M=M, drift=LINEAR,
+        A=np.array([[0.0, 1.0], [-1.0, 0.0]]), B=np.array([[0.0], [1.0]]),
+        sigma=np.array([0.05, 0.1]), x0=np.array([1.0, 0.0]), q=np.array([1.0, 1.0]),
+        xd=_target("ks_oscillator", 1.0, Nt, 2), lam=float(np.sqrt(beta / np.pi)), jump_law=JUMP_KS,
+        jump_scale=float(1.0 / np.sqrt(2.0 * beta)), jump_gain=gamma, nu=1e-3, u_min=-5.0, u_max=5.0,
+        seed=seed)
 
 
 def linear_family(d: int, M: int, Nt: int, lam: float = 1.0, seed: int = 0,
