@@ -58,7 +58,7 @@ typedef enum {
 } jd_status;
 
 typedef enum { JD_DRIFT_LINEAR = 0, JD_DRIFT_CUBIC = 1 } jd_drift;
-typedef enum { JD_JUMP_NONE = 0, JD_JUMP_NORMAL = 1, JD_JUMP_UNIFORM = 2 } jd_jump_law;
+typedef enum { JD_JUMP_NONE = 0, JD_JUMP_NORMAL = 1, JD_JUMP_UNIFORM = 2, JD_JUMP_KS = 3 } jd_jump_law;
 typedef enum { JD_FP32 = 0, JD_FP64 = 1 } jd_precision;
 typedef enum { JD_ADJ_AUTO = 0, JD_ADJ_STORED = 1, JD_ADJ_RECOMPUTE = 2 } jd_adjoint_mode;
 typedef enum { JD_MEM_HOST = 0, JD_MEM_DEVICE = 1 } jd_memspace;
@@ -73,7 +73,13 @@ typedef enum { JD_MEM_HOST = 0, JD_MEM_DEVICE = 1 } jd_memspace;
  *                (A(theta) = A + theta dA), NULL if not needed
  *   sigma        d, diagonal additive diffusion
  *   lambda       jump intensity; jump_law NONE/NORMAL (N(0, jump_scale^2) per
- *                component) / UNIFORM (U[-jump_scale, jump_scale] per component)
+ *                component) / UNIFORM (U[-jump_scale, jump_scale] per component) /
+ *                KS, the Keilson-Storer velocity reset of Sec. 5.3 Eq. jump_law: the
+ *                state is z = (x, v) with v the components c >= d/2, and a jump sets
+ *                v_c <- jump_gain v_c + jump_scale xi_c, xi_c ~ N(0, 1), leaving x;
+ *                the paper's kernel has jump_scale = 1/sqrt(2 beta) and intensity
+ *                sqrt(beta/pi).  KS is built for d <= 8 (UNSUPPORTED above) and is
+ *                not taken by jd_cost_noalloc
  *   x0           d, deterministic initial state
  *   q            d, diagonal tracking weights; xd (Nt+1)*d, target xd(t_k)
  *   nu           control weight (the paper's alpha); u_min, u_max box bounds
@@ -92,6 +98,8 @@ typedef enum { JD_MEM_HOST = 0, JD_MEM_DEVICE = 1 } jd_memspace;
  *                (half of the free device memory at creation)
  *   cuda_stream  cudaStream_t for all work of this problem; NULL = the library
  *                creates its own stream
+ *   jump_gain    KS only: the velocity gain gamma (finite; the paper takes 0 <= gamma
+ *                < 1); ignored by the additive laws
  */
 typedef struct {
   int d, du;
@@ -115,6 +123,7 @@ typedef struct {
   int use_tensor_cores;
   size_t mem_budget_bytes;
   void *cuda_stream;
+  double jump_gain;
 } jd_problem_desc;
 
 typedef struct jd_problem jd_problem;

@@ -53,6 +53,7 @@ class ProblemDesc(ctypes.Structure):
         ("u_max", ctypes.c_double), ("seed", ctypes.c_uint64), ("epoch", ctypes.c_uint32),
         ("prec", ctypes.c_int), ("mode", ctypes.c_int), ("use_tensor_cores", ctypes.c_int),
         ("mem_budget_bytes", ctypes.c_size_t), ("cuda_stream", ctypes.c_void_p),
+        ("jump_gain", ctypes.c_double),
     ]
 
 
@@ -203,7 +204,7 @@ def make_desc(problem, prec=JD_FP32, mode=JD_ADJ_AUTO, use_tensor_cores=0, mem_b
         u_min=float(problem.u_min), u_max=float(problem.u_max), seed=int(problem.seed),
         epoch=int(problem.epoch), prec=_PREC[prec], mode=_MODE[mode],
         use_tensor_cores=int(use_tensor_cores), mem_budget_bytes=int(mem_budget_bytes),
-        cuda_stream=stream_handle)
+        cuda_stream=stream_handle, jump_gain=float(getattr(problem, "jump_gain", 1.0)))
     return desc, a
 
 
@@ -219,7 +220,7 @@ class JdProblem:
     """One problem on the current CUDA device (see jd_problem_create).
 
     ``problem`` is any object with the fields of workloads.Problem (d, du, T, Nt, M,
-    drift, A, C, B, dA, sigma, lam, jump_law, jump_scale, x0, q, xd, nu, u_min, u_max,
+    drift, A, C, B, dA, sigma, lam, jump_law, jump_scale, jump_gain, x0, q, xd, nu, u_min, u_max,
     seed, epoch).  ``stream``: a torch.cuda.Stream, a raw cudaStream_t int, or None for
     torch's current stream (a library-owned stream when torch has no CUDA).
     ``use_tensor_cores`` (8 < d <= 32): 0 CUDA cores, 1 BF16 tensor cores, 2 BF16 x3.

@@ -602,7 +602,11 @@ static jd_status validate_desc(const jd_problem_desc &q) {
   if (q.M < 1 || q.M > 0xFFFFFFFFll) return fail(JD_ERR_INVALID_ARG, "M must be in [1, 2^32 - 1]");
   if (!(q.T > 0.0) || !std::isfinite(q.T)) return fail(JD_ERR_INVALID_ARG, "T must be finite and > 0");
   if (q.drift != JD_DRIFT_LINEAR && q.drift != JD_DRIFT_CUBIC) return fail(JD_ERR_INVALID_ARG, "bad drift");
-  if (q.jump_law < JD_JUMP_NONE || q.jump_law > JD_JUMP_UNIFORM) return fail(JD_ERR_INVALID_ARG, "bad jump law");
+  if (q.jump_law < JD_JUMP_NONE || q.jump_law > JD_JUMP_KS) return fail(JD_ERR_INVALID_ARG, "bad jump law");
+  if (q.jump_law == JD_JUMP_KS && q.d > 8)
+    return fail(JD_ERR_UNSUPPORTED, "the Keilson-Storer law is built for d <= 8");
+  if (q.jump_law == JD_JUMP_KS && !std::isfinite(q.jump_gain))
+    return fail(JD_ERR_INVALID_ARG, "jump_gain must be finite");
   if (q.prec != JD_FP32 && q.prec != JD_FP64) return fail(JD_ERR_INVALID_ARG, "bad precision");
   if (q.mode < JD_ADJ_AUTO || q.mode > JD_ADJ_RECOMPUTE) return fail(JD_ERR_INVALID_ARG, "bad adjoint mode");
   if (!q.A || !q.B || !q.sigma || !q.x0 || !q.q || !q.xd)
@@ -1196,6 +1200,7 @@ jd_status jd_problem_update(jd_problem *p, const jd_problem_desc *desc) {
   p->desc.lambda = q.lambda;
   p->desc.jump_law = q.jump_law;
   p->desc.jump_scale = q.jump_scale;
+  p->desc.jump_gain = q.jump_gain;
   p->desc.nu = q.nu;
   p->desc.u_min = q.u_min;
   p->desc.u_max = q.u_max;

@@ -479,6 +479,28 @@ __device__ __forceinline__ R slot0_draws(const KParams<R, D, DU> &kp, int k, uin
   return M::u01(w[0]);
 }
 
+// The jump map applied at an arrival with unit sizes xih (Sec. 5.3 eq:jump_law):
+// y_c <- jgain_c y_c + jscl_c xih_c.  Additive laws: jgain = 1, jscl = s (y + s xih, bit
+// for bit).  Keilson-Storer: the velocity half z_c, c >= d/2, of the phase-space state
+// is reset to gamma z_c + s xih_c; positions have jgain = 1, jscl = 0 and stay.  No
+// branch on the law, so the inline one-jump step keeps its size.
+template <typename R, int D, int DU>
+__device__ __forceinline__ void apply_jump(const KParams<R, D, DU> &kp, R *y, const R *xih) {
+  using M = Ar<R>;
+#pragma unroll
+  for (int c = 0; c < D; ++c) y[c] = M::add(M::mul(kp.jgain[c], y[c]), M::mul(kp.jscl[c], xih[c]));
+}
+
+// Adjoint across a jump: mu (derivative w.r.t. the post-jump state) times the map's
+// Jacobian, the identity for the additive laws and gamma on the reset velocities.
+// (jgain_c = 1 leaves mu_c unchanged bit for bit, so the additive laws need no branch)
+template <typename R, int D, int DU>
+__device__ __forceinline__ void jump_adjoint(const KParams<R, D, DU> &kp, R *mu) {
+  using M = Ar<R>;
+#pragma unroll
+  for (int c = 0; c < D; ++c) mu[c] = M::mul(kp.jgain[c], mu[c]);
+}
+
 // One Euler sub-step y <- y + de f(y, u) + sigma sqrt(de) z (the form every jump path uses).
 template <typename R, int D, int DU>
 __device__ __forceinline__ void euler_substep(const KParams<R, D, DU> &kp, R de, const R (&z)[D],
@@ -504,7 +526,7 @@ __device__ __forceinline__ void euler_substep(const KParams<R, D, DU> &kp, R de,
 // Plan and integrate a step that has jumps (Algorithm 5.1 with the additive jump
 // map): Poisson count from w0, jump times (word 0 of every slot) sorted stably,
 // sub-step lengths, then the Euler sub-steps from x with the jump of slot order[i]
-// added after sub-step i.
+// applied after sub-step i.
 template <typename R, int D, int DU>
 __device__ __noinline__ void build_jump_step(const KParams<R, D, DU> &kp, int k, uint32_t m,
                                              uint32_t w0, const R *z0, const R *u, const R *x,
@@ -569,8 +591,7 @@ __device__ __noinline__ void build_jump_step(const KParams<R, D, DU> &kp, int k,
     if (i < n) {
       R xih[D];
       slot_draws(kp, k, m, S->order[i], xih, z);
-#pragma unroll
-      for (int c = 0; c < D; ++c) y[c] = M::add(y[c], M::mul(kp.jump_scale, xih[c]));
+      apply_jump(kp, y, xih);
     }
 #pragma unroll
     for (int c = 0; c < D; ++c) S->Y[i + 1][c] = y[c];

@@ -28,10 +28,13 @@ struct KParams {
   R qdt[D];        // q_c * dt            (cost gradient)
   R hqdt[D];       // q_c * dt / 2        (cost)
   R x0[D];
+  R jgain[D];      // jump map y_c <- jgain_c y_c + jscl_c xih_c: gamma on reset velocities,
+  R jscl[D];       // else 1; jscl_c = jump_scale on the components a jump moves, else 0
   R dt, sqdt, jump_scale;
   unsigned long long thr[NMAX];  // Poisson thresholds floor(2^32 F(n; lambda dt))
   uint32_t key0, key1, epoch;
   int d, npair, Nt, cubic, jump_law, jumps_on, has_dA, S, nblk;
+  int kvel;                       // first component a jump moves (d/2 for Keilson-Storer, else 0)
   int64_t m_begin;                // global index of path 0 of this launch
   int64_t npart;                  // stride of the per-warp gradient partials (all launches)
 };

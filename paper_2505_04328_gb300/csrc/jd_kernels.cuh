@@ -125,6 +125,9 @@ __host__ __device__ constexpr int seg_len() {
 // One uniform step k from x (in place); returns the number of jumps.  Steps with one
 // jump take an inline path (the common case); two or more go through
 // build_jump_step.  With a LogWriter the post-jump states of the step are recorded.
+// The one-jump paths (inline and out of line) apply the additive map; a step of a
+// Keilson-Storer problem with jumps always takes build_jump_step, whose jump map covers
+// every law.
 // The one-jump step out of line: sub-step to the jump, jump, sub-step to t_{k+1}.  x is
 // updated in place; y1 receives the post-jump state; returns the jump's time fraction.
 template <typename R, int D, int DU>
@@ -186,7 +189,7 @@ __device__ __forceinline__ int forward_step(const KParams<R, D, DU> &kp, int k, 
     }
     return 0;
   }
-  if (!INLINE_JUMP && kp.npair == MainWords<D>::PD && (unsigned long long)w0 < kp.thr[1]) {
+  if (!INLINE_JUMP && kp.jump_law != JD_JUMP_KS && kp.npair == MainWords<D>::PD && (unsigned long long)w0 < kp.thr[1]) {
     // copies: an address taken of x or uk themselves would move them to local memory
     R zc[D], xc[D], uc[DU], y1[D];
 #pragma unroll
@@ -204,7 +207,8 @@ __device__ __forceinline__ int forward_step(const KParams<R, D, DU> &kp, int k, 
     }
     return 1;
   }
-  if (INLINE_JUMP && kp.npair == MainWords<D>::PD && (unsigned long long)w0 < kp.thr[1]) {
+  if (INLINE_JUMP && kp.jump_law != JD_JUMP_KS && kp.npair == MainWords<D>::PD &&
+      (unsigned long long)w0 < kp.thr[1]) {
     R xih[D], z1[D];
     const R th = slot0_draws(kp, k, m, xih, z1);
     euler_substep(kp, M::mul(kp.dt, th), z, uk, x);
@@ -297,15 +301,20 @@ __device__ __noinline__ void jump_backward(const KParams<R, D, DU> &kp, int k, u
 #pragma unroll
     for (int c = 0; c < D; ++c) y[c] = S.Y[i][c];
     const R de = S.delta[i];
-    if (THETA) {
-      R zi[D];
-      if (i < S.n) {
-        // jump of slot order[i] after sub-step i: xih_cur holds its unit size
+    if (i < S.n) {
+      if (THETA) {
+        // jump of slot order[i] after sub-step i: xih_cur holds its unit size; the
+        // derivative in s sums over the components the jump moves
         R s = R(0);
 #pragma unroll
-        for (int c = 0; c < D; ++c) s = M::fma(mu[c], xih_cur[c], s);
+        for (int c = 0; c < D; ++c)
+          if (c >= kp.kvel) s = M::fma(mu[c], xih_cur[c], s);
         th_io[D + 1] = M::add(th_io[D + 1], s);
       }
+      if (kp.jump_law == JD_JUMP_KS) jump_adjoint(kp, mu);   // now w.r.t. the pre-jump state
+    }
+    if (THETA) {
+      R zi[D];
       if (i == 0) {
 #pragma unroll
         for (int c = 0; c < D; ++c) zi[c] = z0[c];
@@ -358,6 +367,7 @@ __device__ __forceinline__ void backward_step(const KParams<R, D, DU> &kp, int k
       const R de = M::mul(kp.dt, M::sub(thn, the));
       control_sensitivity(kp, mu, de, g);
       adjoint_update(kp, y, de, mu);
+      jump_adjoint(kp, mu);   // across the jump that produced y
       thn = the;
     }
     const R de0 = M::mul(kp.dt, thn);
@@ -762,10 +772,14 @@ void make_kparams(const jd_problem *p, int64_t m_begin, int64_t mloc, KParams<R,
     kp.qdt[c] = in ? (R)(p->q[c] * dt) : R(0);
     kp.hqdt[c] = in ? (R)(0.5 * p->q[c] * dt) : R(0);
     kp.x0[c] = in ? (R)p->x0[c] : R(0);
+    const bool reset = q.jump_law == JD_JUMP_KS && c >= d / 2, moved = q.jump_law != JD_JUMP_KS || reset;
+    kp.jgain[c] = reset ? (R)q.jump_gain : R(1);
+    kp.jscl[c] = moved ? (R)q.jump_scale : R(0);
   }
   kp.dt = (R)dt;
   kp.sqdt = (R)sqdt;
   kp.jump_scale = (R)q.jump_scale;
+  kp.kvel = q.jump_law == JD_JUMP_KS ? d / 2 : 0;
   poisson_thresholds(q.lambda * dt, kp.thr);
   kp.key0 = (uint32_t)(q.seed & 0xffffffffull);
   kp.key1 = (uint32_t)(q.seed >> 32);

@@ -92,10 +92,13 @@ static void noalloc_kparams(const jd_problem_desc &q, KParams<R, D, DU> &kp) {
     kp.qdt[c] = in ? (R)(q.q[c] * dt) : R(0);
     kp.hqdt[c] = in ? (R)(0.5 * q.q[c] * dt) : R(0);
     kp.x0[c] = in ? (R)q.x0[c] : R(0);
+    kp.jgain[c] = R(1);   // the additive laws only (a Keilson-Storer problem is rejected)
+    kp.jscl[c] = (R)q.jump_scale;
   }
   kp.dt = (R)dt;
   kp.sqdt = (R)sqdt;
   kp.jump_scale = (R)q.jump_scale;
+  kp.kvel = 0;
   poisson_thresholds(q.lambda * dt, kp.thr);
   kp.key0 = (uint32_t)(q.seed & 0xffffffffull);
   kp.key1 = (uint32_t)(q.seed >> 32);

@@ -105,6 +105,8 @@ def _desc(**over):
     (dict(T=float("nan")), binding.JD_ERR_INVALID_ARG),
     (dict(lam=-1.0), binding.JD_ERR_INVALID_ARG),
     (dict(jump_law=7), binding.JD_ERR_INVALID_ARG),
+    (dict(jump_law=3, jump_gain=float("nan")), binding.JD_ERR_INVALID_ARG),
+    (dict(d=16, drift=0, jump_law=3, jump_gain=0.5), binding.JD_ERR_UNSUPPORTED),
     (dict(drift=3), binding.JD_ERR_INVALID_ARG),
     (dict(u_min=1.0, u_max=0.0), binding.JD_ERR_INVALID_ARG),
     (dict(C=None), binding.JD_ERR_INVALID_ARG),

@@ -56,6 +56,11 @@ CASES = {
     "linear8": lambda: workloads.linear_family(8, M=200, Nt=77, lam=4.0),
     "d1_two_controls": lambda: workloads.lq_scalar(M=150, Nt=50).replace(du=2, B=np.array([[1.0, -0.5]])),
     "many_jumps": lambda: workloads.double_well(M=130, Nt=40).replace(lam=120.0),
+    # Keilson-Storer velocity resets (Sec. 5.3): the paper's beta = 10, gamma = 0.9 at a
+    # larger rate so that most paths see several resets; d = 4 has two velocities
+    "ks_oscillator": lambda: workloads.ks_oscillator(M=300, Nt=150).replace(lam=12.0),
+    "ks_linear4": lambda: workloads.linear_family(4, M=200, Nt=77, lam=6.0).replace(
+        jump_law=workloads.JUMP_KS, jump_gain=0.6, jump_scale=0.3),
 }
 
 
@@ -93,8 +98,12 @@ def test_cost_and_gradient_parity(case, prec, mode):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
-def test_stored_equals_recompute_bitwise(prec):
-    p = workloads.double_well(M=1000, Nt=333).replace(lam=20.0)
+@pytest.mark.parametrize("law", ["normal", "ks"])
+def test_stored_equals_recompute_bitwise(prec, law):
+    if law == "normal":
+        p = workloads.double_well(M=1000, Nt=333).replace(lam=20.0)
+    else:
+        p = workloads.ks_oscillator(M=1000, Nt=333).replace(lam=20.0)
     u = workloads.random_control(p, seed=5)
     with JdProblem(p, prec=prec, mode="stored") as a, JdProblem(p, prec=prec, mode="recompute") as b:
         Ja, ga, ta = a.gradient(u, theta=True)
@@ -114,8 +123,12 @@ def test_repeatable_bitwise():
 
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-4)])
-def test_parameter_gradient_parity(prec, tol):
-    p = workloads.double_well_autograd(M=600, Nt=120)
+@pytest.mark.parametrize("law", ["uniform", "ks"])
+def test_parameter_gradient_parity(prec, tol, law):
+    if law == "uniform":
+        p = workloads.double_well_autograd(M=600, Nt=120)
+    else:   # reset law: the jump-scale derivative sums over the velocity half only
+        p = workloads.ks_oscillator(M=600, Nt=120).replace(lam=10.0, dA=np.array([[0.0, 0.0], [0.0, -1.0]]))
     u = workloads.random_control(p, seed=8, scale=0.5)
     _, _, tho = oracle.gradient(p, u, theta=True)
     with JdProblem(p, prec=prec, mode="recompute") as jp:
