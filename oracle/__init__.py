@@ -60,6 +60,17 @@ class _Problem(ctypes.Structure):
     ]
 
 
+class _Feedback(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("nv", ctypes.c_int), ("x_max", ctypes.c_double),
+                ("v_max", ctypes.c_double), ("eps", ctypes.c_double), ("track", ctypes.c_int),
+                ("sigma_J", ctypes.c_double)]
+
+
+def _fb(f) -> _Feedback:
+    return _Feedback(nx=int(f.nx), nv=int(f.nv), x_max=float(f.x_max), v_max=float(f.v_max),
+                     eps=float(f.eps), track=int(f.track), sigma_J=float(f.sigma_J))
+
+
 class _Draws(ctypes.Structure):
     _fields_ = [
         ("n", ctypes.c_int),
@@ -102,6 +113,15 @@ def lib():
             L.orc_gradient.argtypes = [P(_Problem), ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 3
             L.orc_optimize.argtypes = [P(_Problem), ctypes.c_void_p, P(_OptParams), ctypes.c_int,
                                        P(_OptResult), ctypes.c_void_p]
+            L.orc_bump.argtypes = [ctypes.c_double, ctypes.c_double]
+            L.orc_bump.restype = ctypes.c_double
+            L.orc_bump_dr.argtypes = [ctypes.c_double, ctypes.c_double]
+            L.orc_bump_dr.restype = ctypes.c_double
+            L.orc_fb_control.argtypes = [P(_Feedback)] + [ctypes.c_void_p] * 4
+            L.orc_fb_control.restype = ctypes.c_double
+            L.orc_fb_path.argtypes = [P(_Problem), P(_Feedback), ctypes.c_void_p, ctypes.c_int64] + [ctypes.c_void_p] * 5
+            L.orc_fb_cost.argtypes = [P(_Problem), P(_Feedback), ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+            L.orc_fb_gradient.argtypes = [P(_Problem), P(_Feedback), ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 2
             _lib = L
     return _lib
 
@@ -236,3 +256,75 @@ def optimize(p, u0=None, max_iter=50, tol_rel_grad=1e-4, tol_step=0.0, armijo_c=
     res = dict(iters=r.iters, evals=r.evals, status=r.status, J=r.J,
                rel_grad_norm=r.rel_grad_norm, zeta=r.zeta)
     return u, res, hist[: r.iters + 1]
+
+
+# --- feedback control (Sec. 2 eq:control_structure, Sec. 5.1-5.2, Sec. 6) -------------
+def bump(r, eps):
+    """phi(x, x_c, eps) at r = x - x_c (vectorised over r)."""
+    f = np.vectorize(lambda t: lib().orc_bump(float(t), float(eps)))
+    return f(r)
+
+
+def bump_dr(r, eps):
+    f = np.vectorize(lambda t: lib().orc_bump_dr(float(t), float(eps)))
+    return f(r)
+
+
+def _mu(p, fb, mu):
+    L = fb.nx * fb.nv
+    if mu is None:
+        mu = np.zeros((p.Nt, L))
+    return np.ascontiguousarray(mu, dtype=np.float64).reshape(p.Nt, L)
+
+
+def fb_control(fb, mu_k, z):
+    """(u, (u_x, u_v), phi (L)) at the phase-space point z under the weights mu_k (L)."""
+    mk = np.ascontiguousarray(mu_k, dtype=np.float64).reshape(-1)
+    zz = np.ascontiguousarray(z, dtype=np.float64).reshape(2)
+    du = np.zeros(2)
+    phi = np.zeros(fb.nx * fb.nv)
+    F = _fb(fb)
+    u = lib().orc_fb_control(ctypes.byref(F), _ptr(mk), _ptr(zz), _ptr(du), _ptr(phi))
+    return float(u), du, phi
+
+
+def fb_path(p, fb, mu=None, m: int = 0, adjoint: bool = True):
+    """One path under feedback: dict(X (Nt+1,2), lam, G (Nt,L), cost, njumps)."""
+    op = OracleProblem(p)
+    F = _fb(fb)
+    mu = _mu(p, fb, mu)
+    X = np.zeros((p.Nt + 1, 2))
+    lam = np.zeros((p.Nt + 1, 2)) if adjoint else None
+    G = np.zeros((p.Nt, fb.nx * fb.nv)) if adjoint else None
+    cost = np.zeros(1)
+    nj = np.zeros(p.Nt, dtype=np.int32)
+    rc = lib().orc_fb_path(ctypes.byref(op.s), ctypes.byref(F), _ptr(mu), int(m), _ptr(X),
+                           _ptr(lam), _ptr(G), _ptr(cost), _ptr(nj))
+    if rc:
+        raise ValueError(f"orc_fb_path failed ({rc})")
+    return dict(X=X, lam=lam, G=G, cost=float(cost[0]), njumps=nj)
+
+
+def fb_cost(p, fb, mu=None, nthreads: int | None = None) -> float:
+    op = OracleProblem(p)
+    F = _fb(fb)
+    mu = _mu(p, fb, mu)
+    J = np.zeros(1)
+    rc = lib().orc_fb_cost(ctypes.byref(op.s), ctypes.byref(F), _ptr(mu), nthreads or default_threads(), _ptr(J))
+    if rc:
+        raise ValueError(f"orc_fb_cost failed ({rc})")
+    return float(J[0])
+
+
+def fb_gradient(p, fb, mu=None, nthreads: int | None = None):
+    """(J, dJ/dmu (Nt, L))."""
+    op = OracleProblem(p)
+    F = _fb(fb)
+    mu = _mu(p, fb, mu)
+    J = np.zeros(1)
+    g = np.zeros((p.Nt, fb.nx * fb.nv))
+    rc = lib().orc_fb_gradient(ctypes.byref(op.s), ctypes.byref(F), _ptr(mu), nthreads or default_threads(),
+                               _ptr(J), _ptr(g))
+    if rc:
+        raise ValueError(f"orc_fb_gradient failed ({rc})")
+    return float(J[0]), g

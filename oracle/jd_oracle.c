@@ -512,3 +512,256 @@ int orc_optimize(const orc_problem *P, double *u, const orc_opt_params *o, int n
   free(ut);
   return status;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Feedback control u(z, t) = mu(t)^T phi(z) (Sec. 2 eq:control_structure) on  */
+/* the phase space z = (x, v) of Sec. 5: L = nx nv products of bump functions  */
+/* (Sec. 5.2 eq:Gaussian_RBF) centred on the cell centres of Sec. 5.1.         */
+/* ------------------------------------------------------------------------- */
+
+/* phi(x, x_c, eps) with r = x - x_c: exp(-1 / (1 - (eps r)^2)) for |r| < 1/eps, else 0 */
+double orc_bump(double r, double eps) {
+  double s = (eps * r) * (eps * r);
+  if (!(s < 1.0)) return 0.0;
+  return exp(-1.0 / (1.0 - s));
+}
+
+/* d phi / d x = phi * (-2 eps^2 r) / (1 - (eps r)^2)^2 (zero outside the support) */
+double orc_bump_dr(double r, double eps) {
+  double s = (eps * r) * (eps * r);
+  if (!(s < 1.0)) return 0.0;
+  double e = 1.0 / (1.0 - s);
+  return exp(-e) * (-2.0 * eps * eps * r) * e * e;
+}
+
+/* cell centres x^i = (i - 1/2) dx - x_max, i = 1..n (0-based here: i + 1/2) */
+static double centre(int i, int n, double half_width) {
+  return ((double)i + 0.5) * (2.0 * half_width / (double)n) - half_width;
+}
+
+/* u = sum_{i,l} mu[i nv + l] phi(x - x^i) phi(v - v^l) at z = (x, v); du (nullable)
+ * receives (u_x, u_v), phi (nullable, L) the shape-function values. */
+double orc_fb_control(const orc_feedback *F, const double *mu_k, const double *z, double *du,
+                      double *phi) {
+  double px[ORC_FBMAX], dpx[ORC_FBMAX], pv[ORC_FBMAX], dpv[ORC_FBMAX];
+  for (int i = 0; i < F->nx; ++i) {
+    double r = z[0] - centre(i, F->nx, F->x_max);
+    px[i] = orc_bump(r, F->eps);
+    dpx[i] = orc_bump_dr(r, F->eps);
+  }
+  for (int l = 0; l < F->nv; ++l) {
+    double r = z[1] - centre(l, F->nv, F->v_max);
+    pv[l] = orc_bump(r, F->eps);
+    dpv[l] = orc_bump_dr(r, F->eps);
+  }
+  double u = 0.0, ux = 0.0, uv = 0.0;
+  for (int i = 0; i < F->nx; ++i)
+    for (int l = 0; l < F->nv; ++l) {
+      double m = mu_k[i * F->nv + l];
+      u += m * px[i] * pv[l];
+      ux += m * dpx[i] * pv[l];
+      uv += m * px[i] * dpv[l];
+      if (phi) phi[i * F->nv + l] = px[i] * pv[l];
+    }
+  if (du) {
+    du[0] = ux;
+    du[1] = uv;
+  }
+  return u;
+}
+
+/* Tracking term l(z, t_k) and its gradient (nullable): quadratic 1/2 sum q_c e_c^2, or
+ * the Gaussian of Sec. 6 eq:tracking_cost, -exp(-sum q_c e_c^2 / (2 sigma_J^2)),
+ * e = z - z_d(t_k). */
+static double fb_track(const orc_problem *P, const orc_feedback *F, const double *z, int k,
+                       double *grad) {
+  double Q = 0.0, e[ORC_DMAX];
+  for (int c = 0; c < P->d; ++c) {
+    e[c] = z[c] - P->xd[k * P->d + c];
+    Q += P->q[c] * e[c] * e[c];
+  }
+  if (F->track == ORC_TRACK_GAUSS) {
+    double s2 = F->sigma_J * F->sigma_J, E = exp(-Q / (2.0 * s2));
+    if (grad)
+      for (int c = 0; c < P->d; ++c) grad[c] = E * P->q[c] * e[c] / s2;
+    return -E;
+  }
+  if (grad)
+    for (int c = 0; c < P->d; ++c) grad[c] = P->q[c] * e[c];
+  return 0.5 * Q;
+}
+
+static int fb_valid(const orc_problem *P, const orc_feedback *F) {
+  return valid(P) && F && P->d == 2 && P->du == 1 && F->nx >= 1 && F->nx <= ORC_FBMAX &&
+         F->nv >= 1 && F->nv <= ORC_FBMAX && F->x_max > 0.0 && F->v_max > 0.0 && F->eps > 0.0 &&
+         (F->track == ORC_TRACK_QUAD || (F->track == ORC_TRACK_GAUSS && F->sigma_J > 0.0));
+}
+
+/* Sub-steps of step k under feedback (Algorithm 5.1, the control evaluated at the
+ * left end of every sub-step); returns sum_i (alpha/2) delta_i u(Y_i)^2. */
+static double integrate_step_fb(const orc_problem *P, const orc_feedback *F, const orc_draws *D,
+                                const double *xk, const double *mu_k, double (*Y)[ORC_DMAX]) {
+  double f[ORC_DMAX], ucost = 0.0;
+  memcpy(Y[0], xk, sizeof(double) * 2);
+  for (int i = 0; i <= D->n; ++i) {
+    double u = orc_fb_control(F, mu_k, Y[i], NULL, NULL);
+    ucost += 0.5 * P->nu * D->delta[i] * u * u;
+    drift(P, Y[i], &u, f);
+    double sq = sqrt(D->delta[i]);
+    for (int c = 0; c < 2; ++c) {
+      Y[i + 1][c] = Y[i][c] + D->delta[i] * f[c] + P->sigma[c] * sq * D->Z[i][c];
+      if (i < D->n && jump_acts_on(P, c))
+        Y[i + 1][c] = jump_gain_of(P, c) * Y[i + 1][c] + P->jump_scale * D->xi_hat[i][c];
+    }
+  }
+  return ucost;
+}
+
+int orc_fb_path(const orc_problem *P, const orc_feedback *F, const double *mu, int64_t m,
+                double *X, double *lam, double *G, double *cost, int *njumps) {
+  if (!fb_valid(P, F) || !mu || m < 0 || m >= P->M) return 1;
+  const int Nt = P->Nt, L = F->nx * F->nv;
+  const double dt = P->T / (double)Nt;
+  double *Xs = X ? X : (double *)malloc(sizeof(double) * (size_t)(Nt + 1) * 2);
+  orc_draws *D = (orc_draws *)malloc(sizeof(orc_draws));
+  double (*Y)[ORC_DMAX] = (double (*)[ORC_DMAX])malloc(sizeof(double) * ORC_DMAX * (ORC_NMAX + 2));
+  double *phi = (double *)malloc(sizeof(double) * L);
+  if (!Xs || !D || !Y || !phi) return 2;
+
+  /* forward sweep; the cost is sum_k [dt l(X_{k+1}) + sum_i (alpha/2) delta_i u(Y_i)^2] */
+  memcpy(Xs, P->x0, sizeof(double) * 2);
+  double c_m = 0.0;
+  for (int k = 0; k < Nt; ++k) {
+    orc_step_draws(P, k, m, D);
+    if (njumps) njumps[k] = D->n;
+    c_m += integrate_step_fb(P, F, D, Xs + (size_t)k * 2, mu + (size_t)k * L, Y);
+    memcpy(Xs + (size_t)(k + 1) * 2, Y[D->n + 1], sizeof(double) * 2);
+    c_m += dt * fb_track(P, F, Xs + (size_t)(k + 1) * 2, k + 1, NULL);
+  }
+  if (cost) *cost = c_m;
+
+  /* adjoint sweep: a = derivative of the path cost w.r.t. the current state.  Across
+   * sub-step i (Y_i -> Y_{i+1}) with w = alpha u(Y_i) + B^T a:
+   *   dcost/dmu_k,l += delta_i phi_l(Y_i) w,
+   *   a <- a + delta_i [ (A + 3 C diag(Y_i^2))^T a + w grad u(Y_i) ]
+   * (Sec. 5.5 eq:adjoint_eq_approximation with grad_z j^h = grad l + alpha u grad u). */
+  if (G || lam) {
+    double a[2], jt[ORC_DMAX], gr[ORC_DMAX], du[2];
+    fb_track(P, F, Xs + (size_t)Nt * 2, Nt, gr);
+    for (int c = 0; c < 2; ++c) a[c] = dt * gr[c];
+    if (lam) memcpy(lam + (size_t)Nt * 2, a, sizeof(a));
+    for (int k = Nt - 1; k >= 0; --k) {
+      const double *mu_k = mu + (size_t)k * L;
+      orc_step_draws(P, k, m, D);
+      integrate_step_fb(P, F, D, Xs + (size_t)k * 2, mu_k, Y);
+      if (G) memset(G + (size_t)k * L, 0, sizeof(double) * L);
+      for (int i = D->n; i >= 0; --i) {
+        if (i < D->n)
+          for (int c = 0; c < 2; ++c) a[c] *= jump_gain_of(P, c);
+        double u = orc_fb_control(F, mu_k, Y[i], du, phi);
+        double w = P->nu * u + P->B[0] * a[0] + P->B[1] * a[1];
+        if (G)
+          for (int l = 0; l < L; ++l) G[(size_t)k * L + l] += D->delta[i] * phi[l] * w;
+        drift_jacobian_T(P, Y[i], a, jt);
+        for (int c = 0; c < 2; ++c) a[c] = a[c] + D->delta[i] * (jt[c] + w * du[c]);
+      }
+      if (k >= 1) {
+        fb_track(P, F, Xs + (size_t)k * 2, k, gr);
+        for (int c = 0; c < 2; ++c) a[c] += dt * gr[c];
+      }
+      if (lam) memcpy(lam + (size_t)k * 2, a, sizeof(a));
+    }
+  }
+  if (!X) free(Xs);
+  free(D);
+  free(Y);
+  free(phi);
+  return 0;
+}
+
+/* Sums over paths under feedback, in the same fixed chunk order as sweep():
+ * J = (1/M) sum_m c_m (the control cost is inside c_m), dJ/dmu = (1/M) sum_m G_m. */
+typedef struct {
+  const orc_problem *P;
+  const orc_feedback *F;
+  const double *mu;
+  int want_grad;
+  int64_t nchunks;
+  double *chunk_cost, *chunk_grad;
+  int64_t next;
+  pthread_mutex_t lock;
+  int err;
+} fb_job;
+
+static void *fb_worker(void *arg) {
+  fb_job *J = (fb_job *)arg;
+  const orc_problem *P = J->P;
+  const size_t n = (size_t)P->Nt * J->F->nx * J->F->nv;
+  double *G = J->want_grad ? (double *)malloc(sizeof(double) * n) : NULL;
+  for (;;) {
+    pthread_mutex_lock(&J->lock);
+    int64_t c = J->next++;
+    pthread_mutex_unlock(&J->lock);
+    if (c >= J->nchunks) break;
+    double cs = 0.0;
+    double *cg = J->want_grad ? J->chunk_grad + (size_t)c * n : NULL;
+    if (cg) memset(cg, 0, sizeof(double) * n);
+    int64_t m_end = (c + 1) * ORC_CHUNK < P->M ? (c + 1) * ORC_CHUNK : P->M;
+    for (int64_t m = c * ORC_CHUNK; m < m_end; ++m) {
+      double cm = 0.0;
+      int rc = orc_fb_path(P, J->F, J->mu, m, NULL, NULL, G, &cm, NULL);
+      if (rc) J->err = rc;
+      cs += cm;
+      if (cg)
+        for (size_t t = 0; t < n; ++t) cg[t] += G[t];
+    }
+    J->chunk_cost[c] = cs;
+  }
+  free(G);
+  return NULL;
+}
+
+static int fb_sweep(const orc_problem *P, const orc_feedback *F, const double *mu, int nthreads,
+                    double *J, double *grad) {
+  if (!fb_valid(P, F) || !mu) return 1;
+  const size_t n = (size_t)P->Nt * F->nx * F->nv;
+  fb_job job;
+  memset(&job, 0, sizeof(job));
+  job.P = P;
+  job.F = F;
+  job.mu = mu;
+  job.want_grad = grad != NULL;
+  job.nchunks = (P->M + ORC_CHUNK - 1) / ORC_CHUNK;
+  job.chunk_cost = (double *)calloc((size_t)job.nchunks, sizeof(double));
+  if (grad) job.chunk_grad = (double *)calloc((size_t)job.nchunks * n, sizeof(double));
+  pthread_mutex_init(&job.lock, NULL);
+  if (nthreads < 1) nthreads = 1;
+  if (nthreads > 256) nthreads = 256;
+  pthread_t th[256];
+  for (int t = 0; t < nthreads; ++t) pthread_create(&th[t], NULL, fb_worker, &job);
+  for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+  pthread_mutex_destroy(&job.lock);
+  double csum = 0.0;
+  for (int64_t c = 0; c < job.nchunks; ++c) csum += job.chunk_cost[c];
+  if (J) *J = csum / (double)P->M;
+  if (grad)
+    for (size_t t = 0; t < n; ++t) {
+      double s = 0.0;
+      for (int64_t c = 0; c < job.nchunks; ++c) s += job.chunk_grad[(size_t)c * n + t];
+      grad[t] = s / (double)P->M;
+    }
+  int err = job.err;
+  free(job.chunk_cost);
+  free(job.chunk_grad);
+  return err;
+}
+
+int orc_fb_cost(const orc_problem *P, const orc_feedback *F, const double *mu, int nthreads,
+                double *J) {
+  return fb_sweep(P, F, mu, nthreads, J, NULL);
+}
+
+int orc_fb_gradient(const orc_problem *P, const orc_feedback *F, const double *mu, int nthreads,
+                    double *J, double *grad) {
+  return fb_sweep(P, F, mu, nthreads, J, grad);
+}

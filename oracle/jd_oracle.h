@@ -22,7 +22,11 @@
  *   - the exact discrete adjoint and the reduced gradient [Sec. 4 eq:AdjointModel,
  *     eq:definition_Gradient; Sec. 5.5 eq:adjoint_eq_approximation];
  *   - projected gradient descent with the Armijo rule [Sec. 5.6 eq:Stochastic_Armijo,
- *     Algorithm 5.4].
+ *     Algorithm 5.4];
+ *   - the Keilson-Storer velocity reset as jump map [Sec. 5.3 eq:jump_law];
+ *   - feedback control u = mu(t)^T phi(z) with bump shape functions, the Gaussian
+ *     tracking cost, and the gradient in mu [Sec. 2 eq:control_structure, Sec. 5.1-5.2,
+ *     Sec. 5.5, Sec. 6 eq:tracking_cost] (declarations at the end).
  */
 #ifndef JD_ORACLE_H
 #define JD_ORACLE_H
@@ -130,6 +134,44 @@ typedef struct {
  * J_hist (max_iter+1, nullable) receives J(u^n) of every iterate reached. */
 int orc_optimize(const orc_problem *P, double *u, const orc_opt_params *o, int nthreads,
                  orc_opt_result *r, double *J_hist);
+
+/* ------------------------------------------------------------------------- */
+/* Feedback control (Sec. 2 eq:control_structure; Sec. 5.1-5.2; Sec. 6) for    */
+/* d = 2, du = 1, z = (x, v): u(z, t_k) = sum_{i,l} mu[k][i nv + l]               */
+/*   phi(x - x^i) phi(v - v^l), centres x^i = (i + 1/2) 2 x_max / nx - x_max (same   */
+/* for v), phi the bump exp(-1/(1 - (eps r)^2)) on |r| < 1/eps.  The control acts  */
+/* through B u(z) and is evaluated at the left end of every sub-step; the path    */
+/* cost is sum_k dt l(X_{k+1}, t_{k+1}) + sum over sub-steps (nu/2) delta_i u(Y_i)^2 */
+/* (nu is the paper's alpha), l quadratic or the Gaussian of eq:tracking_cost.    */
+/* mu is Nt * L, L = nx nv, row-major [k][i][l].                                   */
+/* ------------------------------------------------------------------------- */
+#define ORC_FBMAX 16     /* centres per axis */
+enum { ORC_TRACK_QUAD = 0, ORC_TRACK_GAUSS = 1 };
+
+typedef struct {
+  int nx, nv;             /* centres per axis */
+  double x_max, v_max;    /* computational domain (-x_max, x_max) x (-v_max, v_max) */
+  double eps;             /* bump shape parameter eps_phi */
+  int track;              /* ORC_TRACK_QUAD or ORC_TRACK_GAUSS */
+  double sigma_J;         /* Gaussian tracking width */
+} orc_feedback;
+
+/* The bump phi(x, x_c, eps) of r = x - x_c, and its derivative in x. */
+double orc_bump(double r, double eps);
+double orc_bump_dr(double r, double eps);
+/* u(z) under mu_k (L values); du (nullable) gets (u_x, u_v), phi (nullable) the L
+ * shape-function values. */
+double orc_fb_control(const orc_feedback *F, const double *mu_k, const double *z, double *du,
+                      double *phi);
+/* One path under feedback: X (Nt+1)*2, lam (Nt+1)*2, G (Nt*L per-path dcost/dmu), cost,
+ * njumps (each nullable).  Returns 0 on success. */
+int orc_fb_path(const orc_problem *P, const orc_feedback *F, const double *mu, int64_t m,
+                double *X, double *lam, double *G, double *cost, int *njumps);
+/* J(mu) and dJ/dmu (Nt*L, nullable), fixed summation order. */
+int orc_fb_cost(const orc_problem *P, const orc_feedback *F, const double *mu, int nthreads,
+                double *J);
+int orc_fb_gradient(const orc_problem *P, const orc_feedback *F, const double *mu, int nthreads,
+                    double *J, double *grad);
 
 #ifdef __cplusplus
 }

@@ -22,6 +22,15 @@ Workloads (named by what they are):
   * ``linear32``       d=32 linear drift A = Q diag(ev) Q^T, ev ~ U[-2,-0.1], B 32x4
                        N(0,1/32) (numpy default_rng(1)), sigma=0.1, lambda=1, jumps
                        N(0,0.05^2 I), X0=1, target 0, T=1, N_t=500, M=2^18.
+  * ``ks_oscillator``  d=2 phase-space particle x'=v, v'=-x+u with Keilson-Storer
+                       velocity resets (beta=10, gamma=0.9), M=2^20, N_t=500.
+  * ``feedback_centering``  the paper's feedback problem (Sec. 6.1): z=(x,v),
+                       x'=v, v'=-eta x+u(z,t), eta=1, u = mu(t)^T phi(z) with 10x10
+                       bump shape functions on (-2,2)^2, eps=0.5, Keilson-Storer resets
+                       (beta=10, gamma=0.9), Gaussian tracking of z_d=(0,0), sigma_J=1,
+                       alpha=1e-2, b=(0.1,0.1), z0=(0.75,0.75), T=1, N_t=100, M=2^20.
+  * ``feedback_trajectory``  Sec. 6.3: the same model with eta=0, eps=0.1, following
+                       z_d(t) = (-x_max/2 + x_max t/T, v_max/2 - |v_max t/(2T)|).
   * ``serving_requests``  a stream of requests (d in {1,2,8,32}, M log-uniform in
                        [2^12,2^22], N_t uniform in [50,2000], lambda uniform in
                        [0.5,10]) with Poisson arrivals, numpy default_rng(5).
@@ -208,3 +217,54 @@ def serving_requests(n: int = 10000, rate: float = 200.0, seed: int = 5):
         p.name = f"{p.name}#req{i}"
         out.append((float(t[i]), p))
     return out
+
+
+# --- feedback control (Sec. 2 eq:control_structure, Sec. 5.1-5.2, Sec. 6) --------------
+TRACK_QUAD, TRACK_GAUSS = 0, 1
+
+
+@dataclasses.dataclass
+class Feedback:
+    """Shape functions of u(z, t) = mu(t)^T phi(z): nx x nv bump products centred on the
+    cell centres of (-x_max, x_max) x (-v_max, v_max); tracking cost quadratic or Gaussian
+    with width sigma_J."""
+    nx: int = 10
+    nv: int = 10
+    x_max: float = 2.0
+    v_max: float = 2.0
+    eps: float = 0.5
+    track: int = TRACK_GAUSS
+    sigma_J: float = 1.0
+
+    @property
+    def L(self) -> int:
+        return self.nx * self.nv
+
+    def replace(self, **kw) -> "Feedback":
+        return dataclasses.replace(self, **kw)
+
+
+def feedback_centering(M: int = 1 << 20, Nt: int = 100, seed: int = 0, eta: float = 1.0,
+                       beta: float = 10.0, gamma: float = 0.9):
+    """(Problem, Feedback) of Sec. 6.1: center the particles at z_d = (0, 0)."""
+    p = Problem(
+        name="feedback_centering", d=2, du=1, T=1.0, Nt=Nt, M=M, drift=LINEAR,
+        A=np.array([[0.0, 1.0], [-eta, 0.0]]), B=np.array([[0.0], [1.0]]),
+        sigma=np.array([0.1, 0.1]), x0=np.array([0.75, 0.75]), q=np.array([1.0, 1.0]),
+        xd=np.zeros((Nt + 1, 2)), lam=float(np.sqrt(beta / np.pi)), jump_law=JUMP_KS,
+        jump_scale=float(1.0 / np.sqrt(2.0 * beta)), jump_gain=gamma, nu=1e-2,
+        u_min=-np.inf, u_max=np.inf, seed=seed)
+    return p, Feedback()
+
+
+def feedback_trajectory(M: int = 1 << 20, Nt: int = 100, seed: int = 0):
+    """(Problem, Feedback) of Sec. 6.3: eta = 0, eps = 0.1, a piecewise-linear target."""
+    p, fb = feedback_centering(M=M, Nt=Nt, seed=seed, eta=0.0)
+    t = np.linspace(0.0, p.T, Nt + 1)
+    xd = np.stack([-fb.x_max / 2 + fb.x_max * t / p.T, fb.v_max / 2 - np.abs(fb.v_max * t / (2 * p.T))], axis=1)
+    return p.replace(name="feedback_trajectory", xd=xd), fb.replace(eps=0.1)
+
+
+def random_mu(p: Problem, fb: Feedback, seed: int = 7, scale: float = 1.0) -> np.ndarray:
+    """Seeded feedback weights mu (Nt, L) for gradient tests."""
+    return scale * np.random.default_rng(seed).standard_normal((p.Nt, fb.L))
