@@ -314,6 +314,50 @@ int jd_profile_read(jd_kernel_stat *out, int max_entries);
  * the scratch), CUDA. */
 jd_status jd_cost_noalloc(const jd_problem_desc *desc, const double *u, double *J);
 
+/* ---------------------------------------------------------------------------
+ * Feedback control (Sec. 2 eq:control_structure; Sec. 5.1-5.2; Sec. 5.5; Sec. 6).
+ *
+ * On a problem with d = 2, du = 1, read as the phase space z = (x, v), the control is
+ * the state feedback u(z, t) = sum_{i,l} mu_k[i][l] phi(x - x^i) phi(v - v^l) for t in
+ * [t_k, t_{k+1}), with the bump phi(r) = exp(-1/(1 - (eps r)^2)) on |r| < 1/eps
+ * (Sec. 5.2 eq:Gaussian_RBF) centred on the cell centres x^i = (i + 1/2) 2 x_max/nx -
+ * x_max, v^l = (l + 1/2) 2 v_max/nv - v_max (Sec. 5.1; i, l from 0).  B u(z) enters the
+ * drift, evaluated at the left end of every sub-step of the jump-adapted grid.  The
+ * cost is J(mu) = (1/M) sum_m [ sum_{k=1..Nt} dt l(X_k, t_k) + sum over sub-steps
+ * (alpha/2) delta u(Y)^2 ], alpha = the descriptor's nu, with l the quadratic term
+ * (1/2) sum q_c (z_c - xd_c)^2 or the Gaussian -exp(-sum q_c (z_c - xd_c)^2 / (2 sigma_J^2))
+ * of Sec. 6 eq:tracking_cost.  u_min and u_max do not apply.  The gradient is the exact
+ * derivative of J in mu (eq:definition_Gradient with the adjoint of
+ * eq:adjoint_eq_approximation, u_x and u_v included).  Every jump law is accepted.
+ * --------------------------------------------------------------------------- */
+typedef enum { JD_TRACK_QUADRATIC = 0, JD_TRACK_GAUSS = 1 } jd_track;
+
+typedef struct {
+  int nx, nv;            /* centres per axis, 1..16; L = nx nv weights per step */
+  double x_max, v_max;   /* half-widths of the computational domain, > 0 */
+  double eps;            /* bump shape parameter eps_phi, > 0 */
+  jd_track track;        /* tracking term l */
+  double sigma_J;        /* Gaussian width, > 0 for JD_TRACK_GAUSS */
+} jd_feedback_desc;
+
+/* J(mu).  mu: Nt * L doubles, row-major [k][i][l], in mu_space; J: host pointer.  The
+ * problem's device memory gains the weights in kernel precision and M/256 FP64 cost
+ * partials (allocated on first use, kept until destroy, within the memory budget).
+ * Errors: INVALID_ARG (NULL, a descriptor value out of range, a non-finite weight),
+ * UNSUPPORTED (d != 2 or du != 1), OOM, CUDA. */
+jd_status jd_fb_cost(jd_problem *p, const jd_feedback_desc *fb, const double *mu,
+                     jd_memspace mu_space, double *J);
+
+/* J(mu) and grad = dJ/dmu (Nt * L doubles, [k][i][l]), both mu and grad in `space`; J
+ * is a host pointer (nullable).  Runs the forward sweep storing X_k (2 Nt M values in
+ * kernel precision) and the jump flags, then the adjoint sweep; steps with jumps are
+ * regenerated from X_k.  The gradient partials take M/32 * Nt * L' values in kernel
+ * precision (one per warp of 32 paths), L' the padded weight count (16, 100 or 256).
+ * Deterministic: the same call gives the same bits.
+ * Errors as jd_fb_cost. */
+jd_status jd_fb_gradient(jd_problem *p, const jd_feedback_desc *fb, const double *mu,
+                         jd_memspace space, double *J, double *grad);
+
 const char *jd_status_string(jd_status s);
 const char *jd_last_error(void);
 

@@ -32,7 +32,7 @@ ABI_SYMBOLS = (
     "jd_optimize", "jd_problem_info", "jd_kernel_launch_count", "jd_profile_enable",
     "jd_profile_read", "jd_cost_noalloc", "jd_problem_footprint", "jd_server_create",
     "jd_server_submit", "jd_server_poll", "jd_server_wait", "jd_server_info", "jd_server_destroy",
-    "jd_status_string", "jd_last_error",
+    "jd_status_string", "jd_last_error", "jd_fb_cost", "jd_fb_gradient",
 )
 
 
@@ -55,6 +55,18 @@ class ProblemDesc(ctypes.Structure):
         ("mem_budget_bytes", ctypes.c_size_t), ("cuda_stream", ctypes.c_void_p),
         ("jump_gain", ctypes.c_double),
     ]
+
+
+class FeedbackDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("nv", ctypes.c_int), ("x_max", ctypes.c_double),
+                ("v_max", ctypes.c_double), ("eps", ctypes.c_double), ("track", ctypes.c_int),
+                ("sigma_J", ctypes.c_double)]
+
+
+def make_feedback(fb) -> FeedbackDesc:
+    """The jd_feedback_desc of a workloads.Feedback (duck-typed)."""
+    return FeedbackDesc(nx=int(fb.nx), nv=int(fb.nv), x_max=float(fb.x_max), v_max=float(fb.v_max),
+                        eps=float(fb.eps), track=int(fb.track), sigma_J=float(fb.sigma_J))
 
 
 class KernelStat(ctypes.Structure):
@@ -108,6 +120,8 @@ def lib():
         L.jd_optimize.argtypes = [vp, dp, ctypes.c_int, P(OptParams), P(OptResult), dp]
         L.jd_problem_info.argtypes = [vp, P(ctypes.c_size_t), P(ctypes.c_int)]
         L.jd_cost_noalloc.argtypes = [P(ProblemDesc), dp, dp]
+        L.jd_fb_cost.argtypes = [vp, P(FeedbackDesc), dp, ctypes.c_int, dp]
+        L.jd_fb_gradient.argtypes = [vp, P(FeedbackDesc), dp, ctypes.c_int, dp, dp]
         L.jd_problem_footprint.argtypes = [P(ProblemDesc), ctypes.c_int, P(ctypes.c_size_t)]
         L.jd_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int, P(ctypes.c_void_p)]
         L.jd_server_submit.argtypes = [vp, P(ProblemDesc), P(OptParams), P(ctypes.c_uint64)]
@@ -348,6 +362,32 @@ class JdProblem:
                                  ctypes.c_void_p(grad_out.data_ptr()), JD_MEM_DEVICE, _ptr(gth)),
                "jd_gradient")
         return (J.value if want_J else None), gth
+
+    # --- feedback control u(z, t) = mu(t)^T phi(z) (d = 2, du = 1) ---------------------
+    def fb_cost(self, fb, mu) -> float:
+        """J(mu) of the feedback form; mu (Nt, nx*nv) numpy/torch float64."""
+        mp, ms, _keep = _u_arg(mu, self.Nt * fb.nx * fb.nv)
+        J = ctypes.c_double()
+        F = make_feedback(fb)
+        _check(lib().jd_fb_cost(self.h, ctypes.byref(F), mp, ms, ctypes.byref(J)), "jd_fb_cost")
+        return J.value
+
+    def fb_gradient(self, fb, mu):
+        """(J, dJ/dmu (Nt, nx*nv) numpy) for host mu; for a CUDA tensor mu the gradient is a
+        CUDA tensor too."""
+        n = self.Nt * fb.nx * fb.nv
+        mp, ms, _keep = _u_arg(mu, n)
+        J = ctypes.c_double()
+        F = make_feedback(fb)
+        if ms == JD_MEM_DEVICE:
+            import torch
+            g = torch.empty((self.Nt, fb.nx * fb.nv), dtype=torch.float64, device=mu.device)
+            gp = ctypes.c_void_p(g.data_ptr())
+        else:
+            g = np.zeros((self.Nt, fb.nx * fb.nv))
+            gp = _ptr(g)
+        _check(lib().jd_fb_gradient(self.h, ctypes.byref(F), mp, ms, ctypes.byref(J), gp), "jd_fb_gradient")
+        return J.value, g
 
     def sample_paths(self, u, m0: int, count: int, lam: bool = True):
         """(X (count, Nt+1, d), lam (count, Nt+1, d) or None, cost (count))."""

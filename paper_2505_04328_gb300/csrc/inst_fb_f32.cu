@@ -1,0 +1,40 @@
+// Feedback-control kernels, FP32 path arithmetic (FP64 reductions), padded 4x4, 10x10
+// and 16x16 weights per step; the FP64 finalize of both precisions.
+#include "jd_feedback.cuh"
+
+namespace jd {
+
+extern const FbOps fb_ops_f32[3] = {fb_make_ops<float, 4, 4>(), fb_make_ops<float, 10, 10>(),
+                                    fb_make_ops<float, 16, 16>()};
+
+__global__ void fb_finalize_kernel(const double *__restrict__ partC, const double *__restrict__ partG,
+                                   int64_t nblk, int64_t ngroup, int Nt, int nx, int nv, int NX, int NV,
+                                   int64_t M, double *__restrict__ J, double *__restrict__ grad) {
+  const int64_t n = (int64_t)Nt * nx * nv, ncol = (int64_t)Nt * NX * NV;
+  const double inv = 1.0 / (double)M;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = t / (nx * nv);
+    const int r = (int)(t - k * nx * nv), i = r / nv, l = r - i * nv;
+    const int64_t src = k * NX * NV + ((i / 2) * NV + l) * 2 + (i & 1);   // pair layout
+    double s = 0.0;
+    for (int64_t g = 0; g < ngroup; ++g) s += partG[g * ncol + src];
+    grad[t] = s * inv;
+  }
+  if (J && blockIdx.x == 0 && threadIdx.x == 0) {
+    double s = 0.0;
+    for (int64_t b = 0; b < nblk; ++b) s += partC[b];
+    *J = s * inv;
+  }
+}
+
+cudaError_t fb_finalize(const double *partC, const double *partG, int64_t nblk, int64_t ngroup, int Nt, int nx,
+                        int nv, int NX, int NV, int64_t M, double *J, double *grad, cudaStream_t s) {
+  const int64_t n = grad ? (int64_t)Nt * nx * nv : 0;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 128), 4096));
+  fb_finalize_kernel<<<grid, 128, 0, s>>>(partC, grad ? partG : nullptr, nblk, ngroup, grad ? Nt : 0, nx, nv, NX,
+                                         NV, M, J, grad);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace jd

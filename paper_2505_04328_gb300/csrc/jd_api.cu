@@ -24,9 +24,10 @@ void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_r
 // Optional per-kernel-class timing: a CUDA event pair around every launch, on the
 // launching stream, summed on read.
 enum KernelClass { KC_FWD_COST, KC_FWD_STORE, KC_FWD_CKPT, KC_ADJ_STORED, KC_ADJ_RECOMPUTE,
-                   KC_FINALIZE, KC_PREP, KC_OPT, KC_COUNT };
+                   KC_FINALIZE, KC_PREP, KC_OPT, KC_FB_FWD, KC_FB_ADJ, KC_FB_FIN, KC_COUNT };
 static const char *kKernelClassName[KC_COUNT] = {"fwd_cost", "fwd_store", "fwd_ckpt", "adj_stored",
-                                                 "adj_recompute", "finalize", "prep_u", "opt_step"};
+                                                 "adj_recompute", "finalize", "prep_u", "opt_step",
+                                                 "fb_fwd", "fb_adj", "fb_finalize"};
 struct ProfRec {
   int kind;
   cudaEvent_t a, b;
@@ -85,6 +86,15 @@ static void pick_dims(int d, int du, int *D, int *DU) {
   if (Dd == 1) Dd = 2;
   *D = Dd;
   *DU = 4;
+}
+
+extern const FbOps fb_ops_f32[3], fb_ops_f64[3];
+
+const FbOps *fb_ops(int prec, int nx, int nv) {
+  const FbOps *t = prec == JD_FP64 ? fb_ops_f64 : fb_ops_f32;
+  for (int i = 0; i < 3; ++i)
+    if (nx <= t[i].NX && nv <= t[i].NV) return &t[i];
+  return nullptr;
 }
 
 const PathOps *path_ops_dims(int prec, int D, int DU) {
@@ -910,6 +920,14 @@ jd_status jd_problem_destroy(jd_problem *p) {
   free_dev(p, p->opt_g);
   free_dev(p, p->kp_dev);
   free_dev(p, p->bu_dev);
+  free_dev(p, p->fb_mu);
+  free_dev(p, p->fb_traj);
+  free_dev(p, p->fb_flags);
+  free_dev(p, p->fb_mu64);
+  free_dev(p, p->fb_grad);
+  free_dev(p, p->fb_partC);
+  free_dev(p, p->fb_partG);
+  free_dev(p, p->fb_partW);
   if (p->host_pinned && p->own_pinned) cudaFreeHost(p->host_pinned);
   if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
   delete p;
@@ -1297,6 +1315,139 @@ jd_status jd_sample_paths(jd_problem *p, const double *u, jd_memspace us, int64_
       }
   }
   return JD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Feedback control (jd_fb_cost, jd_fb_gradient)
+// ---------------------------------------------------------------------------
+static jd_status fb_validate(const jd_problem *p, const jd_feedback_desc *fb) {
+  if (!p || !fb) return fail(JD_ERR_INVALID_ARG, "p and fb must be non-NULL");
+  if (p->desc.d != 2 || p->desc.du != 1)
+    return fail(JD_ERR_UNSUPPORTED, "feedback control is built for d = 2 (x, v) and du = 1");
+  if (fb->nx < 1 || fb->nx > FB_NB || fb->nv < 1 || fb->nv > FB_NB)
+    return fail(JD_ERR_INVALID_ARG, "nx and nv must be in [1, 16]");
+  if (!(fb->x_max > 0.0) || !std::isfinite(fb->x_max) || !(fb->v_max > 0.0) || !std::isfinite(fb->v_max) ||
+      !(fb->eps > 0.0) || !std::isfinite(fb->eps))
+    return fail(JD_ERR_INVALID_ARG, "x_max, v_max and eps must be finite and > 0");
+  if (fb->track != JD_TRACK_QUADRATIC && fb->track != JD_TRACK_GAUSS)
+    return fail(JD_ERR_INVALID_ARG, "bad tracking term");
+  if (fb->track == JD_TRACK_GAUSS && (!(fb->sigma_J > 0.0) || !std::isfinite(fb->sigma_J)))
+    return fail(JD_ERR_INVALID_ARG, "sigma_J must be finite and > 0");
+  return JD_OK;
+}
+
+// Buffers of the feedback sweeps for padded size LP (the gradient also needs the states,
+// the flags and the gradient partials); raises the stack limit for the jump routines.
+static jd_status fb_ensure(jd_problem *p, const FbOps *ops, bool grad) {
+  const int LP = ops->NX * ops->NV, Nt = p->desc.Nt;
+  const int64_t M = p->desc.M, nblk = ceil_div(M, FB_TPB);
+  const size_t es = elem_size(p);
+  const int64_t nwarp = nblk * (FB_TPB / 32);
+  if (p->fb_LP != LP) {
+    free_dev(p, p->fb_mu);
+    free_dev(p, p->fb_partW);
+    free_dev(p, p->fb_partG);
+    p->fb_LP = LP;
+  }
+  jd_status s = JD_OK;
+  if (!p->fb_mu) s = dev_alloc(p, &p->fb_mu, (size_t)Nt * LP * es, "feedback weights");
+  if (!s && !p->fb_mu64)
+    s = dev_alloc(p, (void **)&p->fb_mu64, (size_t)Nt * FB_NB * FB_NB * 8, "feedback weights (FP64)");
+  if (!s && !p->fb_partC) s = dev_alloc(p, (void **)&p->fb_partC, (size_t)nblk * 8, "feedback cost partials");
+  if (!s && grad && !p->fb_grad)
+    s = dev_alloc(p, (void **)&p->fb_grad, (size_t)Nt * FB_NB * FB_NB * 8, "feedback gradient");
+  if (!s && grad && !p->fb_traj)
+    s = dev_alloc(p, &p->fb_traj, (size_t)(Nt + 1) * 2 * M * es, "feedback states");
+  if (!s && grad && !p->fb_flags)
+    s = dev_alloc(p, (void **)&p->fb_flags, (size_t)ceil_div(Nt, 32) * M * 4, "feedback jump flags");
+  if (!s && grad && !p->fb_partW)
+    s = dev_alloc(p, &p->fb_partW, (size_t)nwarp * Nt * LP * es, "feedback warp partials");
+  if (!s && grad && !p->fb_partG)
+    s = dev_alloc(p, (void **)&p->fb_partG, (size_t)fb_groups(nwarp) * Nt * LP * 8, "feedback group partials");
+  if (s) return s;
+  // once per padded size: raising the limit reallocates local memory (a device-wide sync)
+  const size_t need = ops->stack_bytes();
+  if (need > p->fb_stack) {
+    size_t cur = 0;
+    JD_CUDA(cudaDeviceGetLimit(&cur, cudaLimitStackSize));
+    if (cur < need) JD_CUDA(cudaDeviceSetLimit(cudaLimitStackSize, need));
+    p->fb_stack = need;
+  }
+  return JD_OK;
+}
+
+// Forward (and with grad the adjoint) sweep under feedback, then the FP64 finalize into
+// scal_d[S_J] and grad_out (device, Nt*L; null for the cost only).
+static jd_status fb_run(jd_problem *p, const jd_feedback_desc *fb, const double *mu, jd_memspace ms,
+                        double *grad_out) {
+  jd_status s = fb_validate(p, fb);
+  if (s) return s;
+  if (!mu) return fail(JD_ERR_INVALID_ARG, "mu is NULL");
+  if (ms != JD_MEM_HOST && ms != JD_MEM_DEVICE) return fail(JD_ERR_INVALID_ARG, "bad memory space for mu");
+  const FbOps *ops = fb_ops(p->desc.prec, fb->nx, fb->nv);
+  if (!ops) return fail(JD_ERR_UNSUPPORTED, "no compiled feedback size fits nx x nv");
+  const int Nt = p->desc.Nt;
+  const size_t L = (size_t)fb->nx * fb->nv;
+  s = set_device(p);
+  if (!s) s = fb_ensure(p, ops, grad_out != nullptr);
+  if (s) return s;
+  const double *mud = mu;
+  if (ms == JD_MEM_HOST) {
+    if (!finite_all(mu, (size_t)Nt * L)) return fail(JD_ERR_INVALID_ARG, "mu has a non-finite entry");
+    JD_CUDA(cudaMemcpyAsync(p->fb_mu64, mu, (size_t)Nt * L * 8, cudaMemcpyHostToDevice, p->stream));
+    mud = p->fb_mu64;
+  }
+  JD_CUDA(ops->prep_mu(mud, p->fb_mu, Nt, fb->nx, fb->nv, p->stream));
+  FbBufs b;
+  b.mu = p->fb_mu;
+  b.traj = p->fb_traj;
+  b.flags = p->fb_flags;
+  b.partC = p->fb_partC;
+  b.partW = p->fb_partW;
+  b.partG = p->fb_partG;
+  int pr = prof_begin(KC_FB_FWD, p->stream);
+  JD_CUDA(ops->fwd(p, *fb, grad_out != nullptr, b, p->stream));
+  prof_end(pr, p->stream);
+  if (grad_out) {
+    pr = prof_begin(KC_FB_ADJ, p->stream);
+    JD_CUDA(ops->adj(p, *fb, b, p->stream));
+    prof_end(pr, p->stream);
+  }
+  pr = prof_begin(KC_FB_FIN, p->stream);
+  const int64_t nblk = ceil_div(p->desc.M, FB_TPB);
+  JD_CUDA(fb_finalize(p->fb_partC, p->fb_partG, nblk, fb_groups(nblk * (FB_TPB / 32)), Nt, fb->nx, fb->nv,
+                      ops->NX, ops->NV, p->desc.M, p->scal_d + S_J, grad_out, p->stream));
+  prof_end(pr, p->stream);
+  return JD_OK;
+}
+
+jd_status jd_fb_cost(jd_problem *p, const jd_feedback_desc *fb, const double *mu, jd_memspace mu_space,
+                     double *J) {
+  if (!J) return fail(JD_ERR_INVALID_ARG, "J is NULL");
+  jd_status s = fb_run(p, fb, mu, mu_space, nullptr);
+  if (!s) s = read_scalars(p, S_J, 1);
+  if (s) return s;
+  *J = p->host_pinned[S_J];
+  return std::isfinite(*J) ? JD_OK : fail(JD_ERR_NONFINITE, "J is not finite");
+}
+
+jd_status jd_fb_gradient(jd_problem *p, const jd_feedback_desc *fb, const double *mu, jd_memspace space,
+                         double *J, double *grad) {
+  if (!grad) return fail(JD_ERR_INVALID_ARG, "grad is NULL");
+  if (space != JD_MEM_HOST && space != JD_MEM_DEVICE) return fail(JD_ERR_INVALID_ARG, "bad memory space");
+  jd_status s = fb_validate(p, fb);
+  if (!s && !p->fb_grad)   // the gradient buffer exists before fb_run picks its target
+    s = dev_alloc(p, (void **)&p->fb_grad, (size_t)p->desc.Nt * FB_NB * FB_NB * 8, "feedback gradient");
+  if (s) return s;
+  s = fb_run(p, fb, mu, space, space == JD_MEM_DEVICE ? grad : p->fb_grad);
+  if (s) return s;
+  if (space == JD_MEM_HOST)
+    JD_CUDA(cudaMemcpyAsync(grad, p->fb_grad, (size_t)p->desc.Nt * fb->nx * fb->nv * 8, cudaMemcpyDeviceToHost,
+                            p->stream));
+  s = read_scalars(p, S_J, 1);
+  if (s) return s;
+  if (J) *J = p->host_pinned[S_J];
+  return std::isfinite(p->host_pinned[S_J]) ? JD_OK : fail(JD_ERR_NONFINITE, "J is not finite");
 }
 
 jd_status jd_optimize(jd_problem *p, double *u_inout, jd_memspace us, const jd_opt_params *o,

@@ -96,6 +96,11 @@ struct Pr<float> {
     r0 = r.x;
     r1 = r.y;
   }
+  static __device__ __forceinline__ void add(float a0, float a1, float b0, float b1, float &r0, float &r1) {
+    const float2 r = __fadd2_rn(make_float2(a0, a1), make_float2(b0, b1));
+    r0 = r.x;
+    r1 = r.y;
+  }
   // a - b as a + (-b): the same IEEE operation, so the same bits as __fsub_rn
   static __device__ __forceinline__ void sub(float a0, float a1, float b0, float b1, float &r0, float &r1) {
     const float2 r = __fadd2_rn(make_float2(a0, a1), make_float2(-b0, -b1));

@@ -1,0 +1,707 @@
+// jd_feedback.cuh -- path kernels of the feedback control u(z, t) = mu(t)^T phi(z)
+// (Sec. 2 eq:control_structure) on the phase space z = (x, v) (d = 2, du = 1):
+//
+//  phi_{i,l}(z) = phi(x - x^i) phi(v - v^l), the bump of Sec. 5.2 eq:Gaussian_RBF,
+//  phi(r) = exp(-1 / (1 - (eps r)^2)) on |r| < 1/eps, centred on the cell centres of
+//  Sec. 5.1.  The control enters the drift as B u(z) and is evaluated at the left end
+//  of every sub-step of the jump-adapted grid (Algorithm 5.1); the path cost is
+//  sum_k dt l(X_{k+1}) + sum over sub-steps (alpha/2) delta u(Y)^2 with the quadratic
+//  or the Gaussian tracking term l (Sec. 6 eq:tracking_cost).
+//
+//  fb_fwd_kernel     forward sweep, one thread per path; per-block FP64 cost partials;
+//                    optionally stores X_k and the jump flags for the adjoint.
+//  fb_adj_kernel     backward sweep over the stored states (steps with jumps are
+//                    regenerated from X_k and the counter-based streams) with
+//                    a <- a + delta [J_f^T a + w grad u],  w = alpha u + B^T a
+//                    (Sec. 5.5 eq:adjoint_eq_approximation); the gradient
+//                    dJ/dmu_{k,i,l} = (1/M) sum over paths and sub-steps of
+//                    delta w phi_x,i phi_v,l (eq:definition_Gradient) is, per step, a
+//                    sum of outer products over paths: each warp exchanges its 32 paths'
+//                    factors through shared memory and forms 32-path dot products
+//                    (paired FMAs), one partial per warp, step and weight.
+//  fb_reduce_kernel  FP64 sums of the warp partials over groups of warps (fixed order).
+//
+// No block barrier inside the sweeps: the weights are read through L1 (every thread of
+// a step reads the same 4 NX NV bytes), the exchange is per warp.  FP32 paths use the
+// SFU for the bumps (rcp.approx, ex2.approx with e^y = 2^(y log2 e)) and paired
+// FFMA2/FMUL2 arithmetic; FP64 paths use IEEE division and exp.
+//
+// The kernels work on padded sizes NX x NV (instances 4x4, 10x10, 16x16): the weights
+// beyond nx x nv are 0, so the bumps of the padding centres do not reach u.
+//
+// A step with jumps runs its sub-steps in the same loop as a step without (forward: one
+// sub-step per iteration; adjoint: one backward sub-step and one warp exchange per
+// round), so a warp in which one path jumps pays one more pass of the same code rather
+// than a separate, serialized jump routine.
+//
+// Layouts (mloc paths, nwarp = ceil(mloc / 32)):
+//   mu    [Nt][NX/2][NV][2]        kernel precision, weights of rows i, i+1 interleaved
+//   traj  [Nt+1][2][mloc]          states X_k
+//   flags [ceil(Nt/32)][mloc]      bit k%32 set when step k had a jump
+//   partC [nblk]                   FP64 block sums of the path costs
+//   partW [nwarp][Nt][NX/2][NV][2] kernel-precision warp sums of the gradient (weight
+//                                  (i, l) at 2 (i/2 NV + l) + i%2)
+//   partG [ngroup][Nt][NX/2][NV][2] FP64 sums of partW over groups of FB_GROUP_WARPS warps
+#pragma once
+
+#include "jd_kernels.cuh"
+
+namespace jd {
+
+constexpr int FB_AROW = 68;   // exchange buffer: pitch of a pair row (2 x 32 values + 4)
+constexpr int FB_BROW = 36;   // exchange buffer: pitch of a phi_v row (32 values + 4)
+
+template <typename R>
+struct FbParams {
+  R xc0, dxc, vc0, dvc;     // centres x^i = xc0 + i dxc, v^l = vc0 + l dvc
+  R eps2, m2eps2;           // eps^2, -2 eps^2
+  R alpha, halpha;          // alpha, alpha / 2
+  R q[2];                   // tracking weights
+  R hinv_s2, inv_s2;        // Gaussian: 1 / (2 sigma_J^2), 1 / sigma_J^2
+  int gauss, Nt;
+  int64_t mloc;
+};
+
+// ---------------------------------------------------------------------------
+// Bumps.  phi = exp(-t), t = 1 / (1 - eps^2 r^2) on the support;
+// d phi / dr = phi t^2 (-2 eps^2 r).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float sfu_rcp(float a) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
+}
+__device__ __forceinline__ float sfu_ex2(float a) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
+}
+constexpr float kNegLog2e = -1.4426950408889634f;   // -log2(e): exp(-t) = 2^(-t log2 e)
+
+// FP64: one bump (IEEE division and exp)
+template <bool GRAD>
+__device__ __forceinline__ double bump(double r, const FbParams<double> &fp, double &dphi) {
+  using M = Ar<double>;
+  const double s1 = M::fma(-fp.eps2, M::mul(r, r), 1.0);   // 1 - eps^2 r^2
+  if (!(s1 > 0.0)) {
+    dphi = 0.0;
+    return 0.0;
+  }
+  const double t = 1.0 / s1;
+  const double ph = ::exp(-t);
+  if (GRAD) dphi = M::mul(M::mul(ph, M::mul(t, t)), M::mul(fp.m2eps2, r));
+  return ph;
+}
+
+// FP32: two bumps at once (distances r0, r1 to their centres): paired arithmetic, SFU
+// reciprocal and 2^y
+template <bool GRAD>
+__device__ __forceinline__ void bump2(float r0, float r1, const FbParams<float> &fp, float &p0, float &p1,
+                                      float &d0, float &d1) {
+  float q0, q1, s0 = 1.f, s1 = 1.f;
+  Pr<float>::mul(r0, r1, r0, r1, q0, q1);
+  Pr<float>::fma(-fp.eps2, -fp.eps2, q0, q1, s0, s1);   // 1 - eps^2 r^2
+  const float t0 = sfu_rcp(s0), t1 = sfu_rcp(s1);
+  float y0, y1;
+  Pr<float>::mul(t0, t1, kNegLog2e, kNegLog2e, y0, y1);
+  const float e0 = sfu_ex2(y0), e1 = sfu_ex2(y1);
+  p0 = s0 > 0.f ? e0 : 0.f;
+  p1 = s1 > 0.f ? e1 : 0.f;
+  if (GRAD) {
+    float tt0, tt1, w0, w1, z0, z1;
+    Pr<float>::mul(t0, t1, t0, t1, tt0, tt1);
+    Pr<float>::mul(p0, p1, tt0, tt1, w0, w1);
+    Pr<float>::mul(r0, r1, fp.m2eps2, fp.m2eps2, z0, z1);
+    Pr<float>::mul(w0, w1, z0, z1, d0, d1);
+    // off the support t may be infinite (1 - eps^2 r^2 == 0) and 0 * inf is NaN
+    d0 = s0 > 0.f ? d0 : 0.f;
+    d1 = s1 > 0.f ? d1 : 0.f;
+  }
+}
+
+// The N bumps at x of the centres c0 + i dc (distances r_i = (x - c0) - i dc; FP32 steps
+// them down two at a time).  Centres beyond nx / nv give bumps whose weights are 0.
+template <typename R, int N, bool GRAD>
+__device__ __forceinline__ void bumps(R x, R c0, R dc, const FbParams<R> &fp, R (&p)[N], R (&d)[N]) {
+  using M = Ar<R>;
+  const R r0 = M::sub(x, c0);
+  if constexpr (Pr<R>::on) {
+    R a0 = r0, a1 = M::sub(r0, dc);
+    const R st = M::add(dc, dc);
+#pragma unroll
+    for (int i = 0; i < N; i += 2) {
+      bump2<GRAD>(a0, a1, fp, p[i], p[i + 1], d[i], d[i + 1]);
+      if (i + 2 < N) Pr<R>::sub(a0, a1, st, st, a0, a1);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) p[i] = bump<GRAD>(M::fma(R(-i), dc, r0), fp, d[i]);
+  }
+}
+
+// Two values of mu, rows i and i+1 at column l, and the next column (one 16-byte load
+// in FP32).
+template <typename R>
+struct Mu4 {
+  R a0, a1, b0, b1;   // (i, l), (i+1, l), (i, l+1), (i+1, l+1)
+};
+template <typename R>
+__device__ __forceinline__ Mu4<R> load_mu4(const R *p);
+template <>
+__device__ __forceinline__ Mu4<float> load_mu4<float>(const float *p) {
+  const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+  return {v.x, v.y, v.z, v.w};
+}
+template <>
+__device__ __forceinline__ Mu4<double> load_mu4<double>(const double *p) {
+  const double2 v = __ldg(reinterpret_cast<const double2 *>(p)), w = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+  return {v.x, v.y, w.x, w.y};
+}
+
+// u(z) = sum_i phi_x,i sum_l mu_k[i][l] phi_v,l with the shape-function values, and with
+// GRAD also (u_x, u_v).  mk: the step's interleaved weights (global, read through L1).
+template <typename R, int NX, int NV, bool GRAD>
+__device__ __forceinline__ R fb_eval(const FbParams<R> &fp, const R *__restrict__ mk, R x, R v, R (&px)[NX],
+                                     R (&pv)[NV], R &ux, R &uv) {
+  using M = Ar<R>;
+  R dpx[NX], dpv[NV];
+  bumps<R, NX, GRAD>(x, fp.xc0, fp.dxc, fp, px, dpx);
+  bumps<R, NV, GRAD>(v, fp.vc0, fp.dvc, fp, pv, dpv);
+  // t_i = sum_l mu[i][l] phi_v,l (and tv_i with phi_v'), rows i, i+1 together
+  R t[NX], tv[NX];
+#pragma unroll
+  for (int i = 0; i < NX; i += 2) {
+    R a0 = R(0), a1 = R(0), b0 = R(0), b1 = R(0);
+#pragma unroll
+    for (int l = 0; l < NV; l += 2) {
+      const Mu4<R> m = load_mu4<R>(mk + ((i / 2) * NV + l) * 2);
+      if constexpr (Pr<R>::on) {
+        Pr<R>::fma(m.a0, m.a1, pv[l], pv[l], a0, a1);
+        Pr<R>::fma(m.b0, m.b1, pv[l + 1], pv[l + 1], a0, a1);
+        if (GRAD) {
+          Pr<R>::fma(m.a0, m.a1, dpv[l], dpv[l], b0, b1);
+          Pr<R>::fma(m.b0, m.b1, dpv[l + 1], dpv[l + 1], b0, b1);
+        }
+      } else {
+        a0 = M::fma(m.a0, pv[l], a0);
+        a1 = M::fma(m.a1, pv[l], a1);
+        a0 = M::fma(m.b0, pv[l + 1], a0);
+        a1 = M::fma(m.b1, pv[l + 1], a1);
+        if (GRAD) {
+          b0 = M::fma(m.a0, dpv[l], b0);
+          b1 = M::fma(m.a1, dpv[l], b1);
+          b0 = M::fma(m.b0, dpv[l + 1], b0);
+          b1 = M::fma(m.b1, dpv[l + 1], b1);
+        }
+      }
+    }
+    t[i] = a0;
+    t[i + 1] = a1;
+    tv[i] = b0;
+    tv[i + 1] = b1;
+  }
+  // u = sum_i phi_x,i t_i, u_x = sum_i phi_x,i' t_i, u_v = sum_i phi_x,i tv_i (even and
+  // odd i in two halves)
+  R u0 = R(0), u1 = R(0), x0 = R(0), x1 = R(0), v0 = R(0), v1 = R(0);
+#pragma unroll
+  for (int i = 0; i < NX; i += 2) {
+    if constexpr (Pr<R>::on) {
+      Pr<R>::fma(px[i], px[i + 1], t[i], t[i + 1], u0, u1);
+      if (GRAD) {
+        Pr<R>::fma(dpx[i], dpx[i + 1], t[i], t[i + 1], x0, x1);
+        Pr<R>::fma(px[i], px[i + 1], tv[i], tv[i + 1], v0, v1);
+      }
+    } else {
+      u0 = M::fma(px[i], t[i], u0);
+      u1 = M::fma(px[i + 1], t[i + 1], u1);
+      if (GRAD) {
+        x0 = M::fma(dpx[i], t[i], x0);
+        x1 = M::fma(dpx[i + 1], t[i + 1], x1);
+        v0 = M::fma(px[i], tv[i], v0);
+        v1 = M::fma(px[i + 1], tv[i + 1], v1);
+      }
+    }
+  }
+  ux = M::add(x0, x1);
+  uv = M::add(v0, v1);
+  return M::add(u0, u1);
+}
+
+// dt l(z, t_k) and (with GRAD) its gradient dt grad l: quadratic (1/2) sum q_c e_c^2 or
+// Gaussian -exp(-sum q_c e_c^2 / (2 sigma_J^2)), e = z - z_d(t_k).
+template <typename R, bool GRAD>
+__device__ __forceinline__ R fb_track(const FbParams<R> &fp, R dt, const R (&z)[2],
+                                      const R *__restrict__ xdk, R (&g)[2]) {
+  using M = Ar<R>;
+  const R e0 = M::sub(z[0], __ldg(xdk)), e1 = M::sub(z[1], __ldg(xdk + 1));
+  const R w0 = M::mul(fp.q[0], e0), w1 = M::mul(fp.q[1], e1);
+  const R Q = M::fma(w1, e1, M::mul(w0, e0));
+  if (fp.gauss) {
+    const R E = exp(-M::mul(Q, fp.hinv_s2));
+    if (GRAD) {
+      const R c = M::mul(dt, M::mul(E, fp.inv_s2));
+      g[0] = M::mul(c, w0);
+      g[1] = M::mul(c, w1);
+    }
+    return -M::mul(dt, E);
+  }
+  if (GRAD) {
+    g[0] = M::mul(dt, w0);
+    g[1] = M::mul(dt, w1);
+  }
+  return M::mul(M::mul(R(0.5), dt), Q);
+}
+
+// One Euler sub-step of length de from y under the feedback control; returns the
+// sub-step's control cost (alpha/2) de u(y)^2.
+template <typename R, int NX, int NV>
+__device__ __forceinline__ R fb_substep(const KParams<R, 2, 1> &kp, const FbParams<R> &fp,
+                                        const R *__restrict__ mk, R de, R sqde, const R (&z)[2], R (&y)[2]) {
+  using M = Ar<R>;
+  R px[NX], pv[NV], ux, uv;
+  const R u = fb_eval<R, NX, NV, false>(fp, mk, y[0], y[1], px, pv, ux, uv);
+  const R uu[1] = {u};
+  R f[2];
+  drift(kp, y, uu, f);
+#pragma unroll
+  for (int c = 0; c < 2; ++c) y[c] = M::fma(M::mul(kp.sigma[c], sqde), z[c], M::fma(de, f[c], y[c]));
+  return M::mul(M::mul(fp.halpha, de), M::mul(u, u));
+}
+
+// Jump plan of a step with jumps (the per-step draws of Algorithm 5.2, as in
+// build_jump_step): the Poisson count n from w0, the time fractions of the n slots
+// sorted stably, and the slot of each jump in time order.
+template <typename R>
+struct FbPlan {
+  R th[NMAX];
+  int order[NMAX];
+};
+
+template <typename R>
+__device__ __forceinline__ int fb_plan(const KParams<R, 2, 1> &kp, int k, uint32_t m, uint32_t w0, FbPlan<R> &P) {
+  using M = Ar<R>;
+  int n = 0;
+#pragma unroll 1
+  for (int i = 0; i < NMAX; ++i) n += ((unsigned long long)w0 >= kp.thr[i]) ? 1 : 0;
+  R theta[NMAX];
+#pragma unroll 1
+  for (int i = 0; i < n; ++i) {
+    const uint4 o = philox10((uint32_t)k, m, (1u << 24) | ((uint32_t)(i + 1) << 16), kp.epoch,
+                             kp.key0, kp.key1);
+    theta[i] = M::u01(o.x);
+    P.order[i] = i;
+  }
+#pragma unroll 1
+  for (int i = 1; i < n; ++i) {
+    const int cur = P.order[i];
+    int j = i - 1;
+    while (j >= 0 && theta[P.order[j]] > theta[cur]) {
+      P.order[j + 1] = P.order[j];
+      --j;
+    }
+    P.order[j + 1] = cur;
+  }
+#pragma unroll 1
+  for (int i = 0; i < n; ++i) P.th[i] = theta[P.order[i]];
+  return n;
+}
+
+// Length of sub-step i of a step with n >= 1 jumps.
+template <typename R>
+__device__ __forceinline__ R fb_delta(const KParams<R, 2, 1> &kp, const FbPlan<R> &P, int n, int i) {
+  using M = Ar<R>;
+  if (i == 0) return M::mul(kp.dt, P.th[0]);
+  if (i < n) return M::mul(kp.dt, M::sub(P.th[i], P.th[i - 1]));
+  return M::mul(kp.dt, M::sub(R(1), P.th[n - 1]));
+}
+
+// Block sum of one compensated pair per thread (FB_TPB threads) into a double.
+template <typename R>
+__device__ __forceinline__ double fb_block_sum(Pair<R> v, Pair<R> *red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double out = 0.0;
+  if (threadIdx.x == 0) {
+    Pair<R> s = red[0];
+    for (int w = 1; w < FB_TPB / 32; ++w) s = padd(s, red[w]);
+    out = (double)s.s + (double)s.e;
+  }
+  return out;
+}
+
+template <typename R, int NX, int NV, bool STORE>
+__global__ void __launch_bounds__(FB_TPB)
+fb_fwd_kernel(const __grid_constant__ KParams<R, 2, 1> kp, const __grid_constant__ FbParams<R> fp,
+              const R *__restrict__ mu, const R *__restrict__ xd, R *__restrict__ traj,
+              uint32_t *__restrict__ flags, double *__restrict__ partC) {
+  constexpr int LP = NX * NV;
+  __shared__ Pair<R> red[FB_TPB / 32];
+  const int64_t mloc = fp.mloc, m = (int64_t)blockIdx.x * FB_TPB + threadIdx.x;
+  const bool active = m < mloc;
+  const uint32_t mg = (uint32_t)(kp.m_begin + m);
+  const int Nt = fp.Nt;
+  Kahan<R> cost;
+  if (active) {
+    R z[2] = {kp.x0[0], kp.x0[1]};
+    uint32_t fw = 0;
+    if (STORE) {
+      traj[m] = z[0];
+      traj[mloc + m] = z[1];
+    }
+#pragma unroll 1
+    for (int k = 0; k < Nt; ++k) {
+      const R *mk = mu + (size_t)k * LP;
+      R zs[2];
+      const uint32_t w0 = main_draws(kp, k, mg, zs);
+      int n = 0;
+      FbPlan<R> P;
+      if (has_jump(kp, w0)) {
+        n = fb_plan(kp, k, mg, w0, P);
+        fw |= 1u << (k & 31);
+      }
+      // sub-steps 0..n (one when the step has no jump) in one loop, so that a warp with
+      // a jumping path runs the same code for every sub-step (Algorithm 5.1)
+#pragma unroll 1
+      for (int i = 0;; ++i) {
+        R de = kp.dt, sq = kp.sqdt;
+        if (n > 0) {
+          de = fb_delta(kp, P, n, i);
+          sq = Ar<R>::sqrt(de);
+        }
+        cost.add(fb_substep<R, NX, NV>(kp, fp, mk, de, sq, zs, z));
+        if (i >= n) break;
+        R xih[2];
+        slot_draws(kp, k, mg, P.order[i], xih, zs);   // the jump's size and the next normals
+        apply_jump(kp, z, xih);
+      }
+      R g[2];
+      cost.add(fb_track<R, false>(fp, kp.dt, z, xd + (size_t)(k + 1) * 2, g));
+      if (STORE) {
+        traj[((size_t)(k + 1) * 2) * mloc + m] = z[0];
+        traj[((size_t)(k + 1) * 2 + 1) * mloc + m] = z[1];
+        if ((k & 31) == 31 || k == Nt - 1) {
+          flags[(size_t)(k >> 5) * mloc + m] = fw;
+          fw = 0;
+        }
+      }
+    }
+  }
+  const double bs = fb_block_sum(active ? cost.pair() : Pair<R>{R(0), R(0)}, red);
+  if (threadIdx.x == 0) partC[blockIdx.x] = bs;
+}
+
+// 32-path dot products of one pair row (rows i, i+1 of the delta w phi_x factors,
+// interleaved) with one phi_v row: (s0, s1) += sum_m (A_i,m, A_i+1,m) B_l,m.  FP32:
+// four independent chains (paths m = 4q + c), then added, so that the paired FMAs do
+// not wait on one another.
+template <typename R>
+__device__ __forceinline__ void pair_dot32(const R *pa, const R *pb, R &s0, R &s1);
+template <>
+__device__ __forceinline__ void pair_dot32<float>(const float *pa, const float *pb, float &s0, float &s1) {
+  float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int j = 0; j < 32; j += 4) {
+    const float4 a = *reinterpret_cast<const float4 *>(pa + 2 * j);
+    const float4 c = *reinterpret_cast<const float4 *>(pa + 2 * j + 4);
+    const float4 b = *reinterpret_cast<const float4 *>(pb + j);
+    Pr<float>::fma(a.x, a.y, b.x, b.x, c0[0], c1[0]);
+    Pr<float>::fma(a.z, a.w, b.y, b.y, c0[1], c1[1]);
+    Pr<float>::fma(c.x, c.y, b.z, b.z, c0[2], c1[2]);
+    Pr<float>::fma(c.z, c.w, b.w, b.w, c0[3], c1[3]);
+  }
+  float u0, u1, v0, v1;
+  Pr<float>::add(c0[0], c1[0], c0[1], c1[1], u0, u1);
+  Pr<float>::add(c0[2], c1[2], c0[3], c1[3], v0, v1);
+  Pr<float>::add(u0, u1, v0, v1, u0, u1);
+  Pr<float>::add(s0, s1, u0, u1, s0, s1);
+}
+template <>
+__device__ __forceinline__ void pair_dot32<double>(const double *pa, const double *pb, double &s0, double &s1) {
+#pragma unroll
+  for (int j = 0; j < 32; j += 2) {
+    const double2 a = *reinterpret_cast<const double2 *>(pa + 2 * j);
+    const double2 c = *reinterpret_cast<const double2 *>(pa + 2 * j + 2);
+    const double2 b = *reinterpret_cast<const double2 *>(pb + j);
+    s0 = __fma_rn(a.x, b.x, s0);
+    s1 = __fma_rn(a.y, b.x, s1);
+    s0 = __fma_rn(c.x, b.y, s0);
+    s1 = __fma_rn(c.y, b.y, s1);
+  }
+}
+
+// Shared memory of fb_adj_kernel: per warp NX/2 pair rows and NV phi_v rows.
+template <typename R, int NX, int NV>
+constexpr size_t fb_adj_smem() {
+  return sizeof(R) * (size_t)(FB_TPB / 32) * ((NX / 2) * FB_AROW + NV * FB_BROW);
+}
+
+template <typename R, int NX, int NV>
+__global__ void __launch_bounds__(FB_TPB)
+fb_adj_kernel(const __grid_constant__ KParams<R, 2, 1> kp, const __grid_constant__ FbParams<R> fp,
+              const R *__restrict__ mu, const R *__restrict__ xd, const R *__restrict__ traj,
+              const uint32_t *__restrict__ flags, R *__restrict__ partW) {
+  using M = Ar<R>;
+  constexpr int LP = NX * NV, NP = (NX / 2) * NV, PPL = (NP + 31) / 32;
+  extern __shared__ __align__(16) unsigned char fb_smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  R *wa = reinterpret_cast<R *>(fb_smem) + warp * ((NX / 2) * FB_AROW + NV * FB_BROW);
+  R *wb = wa + (NX / 2) * FB_AROW;
+  const int64_t mloc = fp.mloc, m = (int64_t)blockIdx.x * FB_TPB + threadIdx.x;
+  const int64_t wid = (int64_t)blockIdx.x * (FB_TPB / 32) + warp;
+  const bool active = m < mloc;
+  const uint32_t mg = (uint32_t)(kp.m_begin + m);
+  const int Nt = fp.Nt;
+  R a[2] = {R(0), R(0)};
+  if (active) {
+    const R zT[2] = {traj[((size_t)Nt * 2) * mloc + m], traj[((size_t)Nt * 2 + 1) * mloc + m]};
+    fb_track<R, true>(fp, kp.dt, zT, xd + (size_t)Nt * 2, a);
+  }
+  // X_k and the flag word of step k are loaded one step ahead (the loop waits on nothing
+  // but its own arithmetic)
+  R zn[2] = {R(0), R(0)};
+  uint32_t fword = 0;
+  if (active && Nt > 0) {
+    zn[0] = traj[((size_t)(Nt - 1) * 2) * mloc + m];
+    zn[1] = traj[((size_t)(Nt - 1) * 2 + 1) * mloc + m];
+    fword = flags[(size_t)((Nt - 1) >> 5) * mloc + m];
+  }
+#pragma unroll 1
+  for (int k = Nt - 1; k >= 0; --k) {
+    const R *mk = mu + (size_t)k * LP;
+    R zk[2] = {zn[0], zn[1]};
+    const uint32_t fk = fword;
+    if (active && k >= 1) {
+      zn[0] = traj[((size_t)(k - 1) * 2) * mloc + m];
+      zn[1] = traj[((size_t)(k - 1) * 2 + 1) * mloc + m];
+      if ((k & 31) == 0) fword = flags[(size_t)((k - 1) >> 5) * mloc + m];
+    }
+    int n = 0;
+    FbPlan<R> P;
+    R Ys[NMAX + 1][2];   // sub-step start states of a step with jumps (Ys[0] = X_k)
+    if (active) {
+      if ((fk >> (k & 31)) & 1u) {
+        // regenerate the step's sub-states from X_k with the forward's arithmetic
+        R zs[2], y[2] = {zk[0], zk[1]};
+        const uint32_t w0 = main_draws(kp, k, mg, zs);
+        n = fb_plan(kp, k, mg, w0, P);
+#pragma unroll 1
+        for (int i = 0; i < n; ++i) {
+          const R de = fb_delta(kp, P, n, i);
+          fb_substep<R, NX, NV>(kp, fp, mk, de, Ar<R>::sqrt(de), zs, y);
+          R xih[2];
+          slot_draws(kp, k, mg, P.order[i], xih, zs);
+          apply_jump(kp, y, xih);
+          Ys[i + 1][0] = y[0];
+          Ys[i + 1][1] = y[1];
+        }
+      }
+    }
+    // sub-steps n..0 backwards, round r = sub-step n - r of every path (paths with fewer
+    // sub-steps contribute zeros); each round's records (delta w phi_x, phi_v) are summed
+    // over the warp's 32 paths through the exchange buffer.  Lane p forms the pair of
+    // weights (i, i+1) x l with i/2 = p / NV, l = p % NV: eight consecutive lanes read at
+    // most two pair rows (mostly the same address) and eight phi_v rows.
+    R s0[PPL], s1[PPL];
+#pragma unroll
+    for (int t = 0; t < PPL; ++t) s0[t] = s1[t] = R(0);
+    const int rounds = (int)__reduce_max_sync(0xffffffffu, active ? (unsigned)(n + 1) : 0u);
+#pragma unroll 1
+    for (int r = 0; r < rounds; ++r) {
+      R ra[NX], rb[NV];
+      if (active && r <= n) {
+        const int i = n - r;
+        if (i < n) jump_adjoint(kp, a);   // across the jump that ends sub-step i
+        R y[2] = {zk[0], zk[1]};
+        R de = kp.dt;
+        if (n > 0) {
+          de = fb_delta(kp, P, n, i);
+          if (i > 0) {
+            y[0] = Ys[i][0];
+            y[1] = Ys[i][1];
+          }
+        }
+        R ux, uv;
+        const R u = fb_eval<R, NX, NV, true>(fp, mk, y[0], y[1], ra, rb, ux, uv);
+        const R w = M::fma(kp.B[1], a[1], M::fma(kp.B[0], a[0], M::mul(fp.alpha, u)));
+        const R dw = M::mul(de, w);
+#pragma unroll
+        for (int c = 0; c < NX; ++c) ra[c] = M::mul(dw, ra[c]);
+        adjoint_update(kp, y, de, a);
+        a[0] = M::fma(dw, ux, a[0]);
+        a[1] = M::fma(dw, uv, a[1]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < NX; ++c) ra[c] = R(0);
+#pragma unroll
+        for (int c = 0; c < NV; ++c) rb[c] = R(0);
+      }
+#pragma unroll
+      for (int c = 0; c < NX; ++c) wa[(c / 2) * FB_AROW + 2 * lane + (c & 1)] = ra[c];
+#pragma unroll
+      for (int c = 0; c < NV; ++c) wb[c * FB_BROW + lane] = rb[c];
+      __syncwarp();
+#pragma unroll
+      for (int t = 0; t < PPL; ++t) {
+        const int p = lane + 32 * t;
+        if (p < NP) pair_dot32<R>(wa + (p / NV) * FB_AROW, wb + (p % NV) * FB_BROW, s0[t], s1[t]);
+      }
+      __syncwarp();
+    }
+    if (active && k >= 1) {
+      R g[2];
+      fb_track<R, true>(fp, kp.dt, zk, xd + (size_t)k * 2, g);
+      a[0] = M::add(a[0], g[0]);
+      a[1] = M::add(a[1], g[1]);
+    }
+    R *dst = partW + ((size_t)wid * Nt + k) * LP;
+#pragma unroll
+    for (int t = 0; t < PPL; ++t) {
+      const int p = lane + 32 * t;
+      if (p < NP) {
+        dst[2 * p] = s0[t];
+        dst[2 * p + 1] = s1[t];
+      }
+    }
+  }
+}
+
+// partG[g][c] = sum over warps w of group g (in order) of partW[w][c], FP64; one thread
+// per (group, column), consecutive threads on consecutive columns.
+template <typename R>
+__global__ void fb_reduce_kernel(const R *__restrict__ partW, int64_t nwarp, int64_t ncol,
+                                 double *__restrict__ partG) {
+  const int64_t ngroup = (nwarp + FB_GROUP_WARPS - 1) / FB_GROUP_WARPS;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ngroup * ncol;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t g = t / ncol, c = t - g * ncol;
+    const int64_t w1 = std::min<int64_t>(nwarp, (g + 1) * FB_GROUP_WARPS);
+    double s = 0.0;
+    for (int64_t w = g * FB_GROUP_WARPS; w < w1; ++w) s += (double)partW[w * ncol + c];
+    partG[t] = s;
+  }
+}
+
+// mu (FP64, [Nt][nx][nv]) -> kernel precision [Nt][NX/2][NV][2] (rows i, i+1
+// interleaved), zero beyond nx, nv.
+template <typename R>
+__global__ void fb_prep_mu_kernel(const double *__restrict__ mu, R *__restrict__ out, int Nt, int nx, int nv,
+                                  int NX, int NV) {
+  const int64_t n = (int64_t)Nt * NX * NV;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = t / (NX * NV);
+    const int r = (int)(t - k * NX * NV), e = r & 1, pl = r >> 1, ip = pl / NV, l = pl - ip * NV;
+    const int i = 2 * ip + e;
+    out[t] = (i < nx && l < nv) ? (R)mu[(k * nx + i) * nv + l] : R(0);
+  }
+}
+
+// J = (1/M) sum_b partC[b];  grad[k][i][l] = (1/M) sum_g partG[g][k][2 (i/2 NV + l) + i%2],
+// groups in order.
+__global__ void fb_finalize_kernel(const double *__restrict__ partC, const double *__restrict__ partG,
+                                   int64_t nblk, int64_t ngroup, int Nt, int nx, int nv, int NX, int NV,
+                                   int64_t M, double *__restrict__ J, double *__restrict__ grad);
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+template <typename R>
+void fb_make_params(const ::jd_problem *p, const jd_feedback_desc &fb, FbParams<R> &fp) {
+  const double dx = 2.0 * fb.x_max / fb.nx, dv = 2.0 * fb.v_max / fb.nv;   // cell widths (Sec. 5.1)
+  fp.xc0 = (R)(0.5 * dx - fb.x_max);
+  fp.dxc = (R)dx;
+  fp.vc0 = (R)(0.5 * dv - fb.v_max);
+  fp.dvc = (R)dv;
+  fp.eps2 = (R)(fb.eps * fb.eps);
+  fp.m2eps2 = (R)(-2.0 * fb.eps * fb.eps);
+  fp.alpha = (R)p->desc.nu;
+  fp.halpha = (R)(0.5 * p->desc.nu);
+  fp.q[0] = (R)p->q[0];
+  fp.q[1] = (R)p->q[1];
+  const double s2 = fb.track == JD_TRACK_GAUSS ? fb.sigma_J * fb.sigma_J : 1.0;
+  fp.hinv_s2 = (R)(0.5 / s2);
+  fp.inv_s2 = (R)(1.0 / s2);
+  fp.gauss = fb.track == JD_TRACK_GAUSS;
+  fp.Nt = p->desc.Nt;
+  fp.mloc = p->desc.M;
+}
+
+template <typename R, int NX, int NV>
+cudaError_t fb_fwd_launch(const ::jd_problem *p, const jd_feedback_desc &fb, bool store, const FbBufs &b,
+                          cudaStream_t s) {
+  KParams<R, 2, 1> kp;
+  make_kparams<R, 2, 1>(p, 0, p->desc.M, kp);
+  FbParams<R> fp;
+  fb_make_params<R>(p, fb, fp);
+  const unsigned grid = (unsigned)ceil_div(p->desc.M, FB_TPB);
+  const R *mu = static_cast<const R *>(b.mu), *xd = static_cast<const R *>(p->xdk);
+  if (store)
+    fb_fwd_kernel<R, NX, NV, true><<<grid, FB_TPB, 0, s>>>(kp, fp, mu, xd, static_cast<R *>(b.traj), b.flags,
+                                                            b.partC);
+  else
+    fb_fwd_kernel<R, NX, NV, false><<<grid, FB_TPB, 0, s>>>(kp, fp, mu, xd, nullptr, nullptr, b.partC);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// The adjoint sweep, then the first (group) stage of the gradient reduction.
+template <typename R, int NX, int NV>
+cudaError_t fb_adj_launch(const ::jd_problem *p, const jd_feedback_desc &fb, const FbBufs &b, cudaStream_t s) {
+  KParams<R, 2, 1> kp;
+  make_kparams<R, 2, 1>(p, 0, p->desc.M, kp);
+  FbParams<R> fp;
+  fb_make_params<R>(p, fb, fp);
+  constexpr size_t smem = fb_adj_smem<R, NX, NV>();
+  static_assert(smem <= 232448, "fb_adj_kernel shared memory");
+  cudaError_t e = cudaFuncSetAttribute(fb_adj_kernel<R, NX, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)ceil_div(p->desc.M, FB_TPB);
+  fb_adj_kernel<R, NX, NV><<<grid, FB_TPB, smem, s>>>(kp, fp, static_cast<const R *>(b.mu),
+                                                      static_cast<const R *>(p->xdk),
+                                                      static_cast<const R *>(b.traj), b.flags,
+                                                      static_cast<R *>(b.partW));
+  count_launch();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int64_t nwarp = (int64_t)grid * (FB_TPB / 32), ncol = (int64_t)p->desc.Nt * NX * NV;
+  const int64_t n = fb_groups(nwarp) * ncol;
+  const unsigned g2 = (unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 16);
+  fb_reduce_kernel<R><<<g2, 256, 0, s>>>(static_cast<const R *>(b.partW), nwarp, ncol, b.partG);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename R, int NX, int NV>
+cudaError_t fb_prep_dims(const double *mu64, void *muR, int Nt, int nx, int nv, cudaStream_t s) {
+  const int64_t n = (int64_t)Nt * NX * NV;
+  const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(n, 256), 4096);
+  fb_prep_mu_kernel<R><<<grid, 256, 0, s>>>(mu64, static_cast<R *>(muR), Nt, nx, nv, NX, NV);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename R, int NX, int NV>
+size_t fb_stack_bytes() {
+  static const size_t bytes = [] {   // the kernels' attributes do not change: ask once
+    size_t need = 0;
+    const void *ks[] = {(const void *)fb_fwd_kernel<R, NX, NV, false>,
+                        (const void *)fb_fwd_kernel<R, NX, NV, true>, (const void *)fb_adj_kernel<R, NX, NV>};
+    for (const void *k : ks) {
+      cudaFuncAttributes a;
+      if (cudaFuncGetAttributes(&a, k) == cudaSuccess) need = std::max(need, a.localSizeBytes);
+    }
+    need += 2048;
+    return (need + 255) & ~(size_t)255;
+  }();
+  return bytes;
+}
+
+template <typename R, int NX, int NV>
+constexpr FbOps fb_make_ops() {
+  return FbOps{NX, NV, (int)sizeof(R), &fb_stack_bytes<R, NX, NV>, &fb_fwd_launch<R, NX, NV>,
+               &fb_adj_launch<R, NX, NV>, &fb_prep_dims<R, NX, NV>};
+}
+
+}  // namespace jd

@@ -75,6 +75,35 @@ struct PathOps {
 };
 
 const PathOps *path_ops_dims(int prec, int D, int DU);
+
+// Feedback control kernels (jd_fb_*): d = 2, du = 1, padded NX x NV weights.
+constexpr int FB_TPB = 256;   // threads (one path each) per block
+constexpr int FB_NB = 16;     // largest centre count per axis
+constexpr int FB_GROUP_WARPS = 512;   // warps per group of the first gradient reduction stage
+inline int64_t fb_groups(int64_t nwarp) { return (nwarp + FB_GROUP_WARPS - 1) / FB_GROUP_WARPS; }
+
+struct FbBufs {
+  const void *mu = nullptr;     // [Nt][NX/2][NV][2] padded, interleaved weights, kernel precision
+  void *traj = nullptr;         // [Nt+1][2][M] states (gradient only)
+  uint32_t *flags = nullptr;    // [ceil(Nt/32)][M] jump flags (gradient only)
+  double *partC = nullptr;      // [nblk] cost partials
+  void *partW = nullptr;        // [nwarp][Nt][NX*NV] warp partials, kernel precision
+  double *partG = nullptr;      // [ngroup][Nt][NX*NV] FP64 group partials
+};
+
+struct FbOps {
+  int NX, NV, elem;
+  size_t (*stack_bytes)();   // per-thread stack the kernels may need (jump steps)
+  // forward sweep (store: keep X_k and the flags); adjoint sweep over the stored states
+  cudaError_t (*fwd)(const struct ::jd_problem *p, const jd_feedback_desc &fb, bool store,
+                     const FbBufs &b, cudaStream_t s);
+  cudaError_t (*adj)(const struct ::jd_problem *p, const jd_feedback_desc &fb, const FbBufs &b,
+                     cudaStream_t s);
+  cudaError_t (*prep_mu)(const double *mu64, void *muR, int Nt, int nx, int nv, cudaStream_t s);
+};
+const FbOps *fb_ops(int prec, int nx, int nv);   // the smallest compiled NX x NV that fits
+cudaError_t fb_finalize(const double *partC, const double *partG, int64_t nblk, int64_t ngroup, int Nt, int nx,
+                        int nv, int NX, int NV, int64_t M, double *J, double *grad, cudaStream_t s);
 int compiled_dim(int d);         // smallest compiled D >= d, or 0
 
 void count_launch(int n = 1);
@@ -121,6 +150,13 @@ struct jd_problem {
   bool async_alloc = false;  // stream-ordered allocations (server): no device-wide sync on free
   size_t bytes = 0;
   int64_t nblk = 0;
+  // feedback control (jd_fb_*): buffers of the last padded size, allocated on use
+  void *fb_mu = nullptr, *fb_traj = nullptr;
+  uint32_t *fb_flags = nullptr;
+  double *fb_mu64 = nullptr, *fb_grad = nullptr, *fb_partC = nullptr, *fb_partG = nullptr;
+  void *fb_partW = nullptr;
+  int fb_LP = 0;             // padded weights per step of fb_mu / fb_partW / fb_partG
+  size_t fb_stack = 0;       // stack limit already ensured for the feedback kernels
 };
 
 namespace jd {

@@ -68,6 +68,28 @@ int main(void) {{
         assert int(vals[f][0]) == getattr(binding.ProblemDesc, f).offset, f
 
 
+def test_feedback_desc_layout_matches_c(tmp_path):
+    src = tmp_path / "fb_layout.c"
+    fields = [f[0] for f in binding.FeedbackDesc._fields_]
+    body = "\n".join(f'  printf("{f} %zu\\n", offsetof(jd_feedback_desc, {f}));' for f in fields)
+    src.write_text(f"""#include <stdio.h>
+#include <stddef.h>
+#include "jd.h"
+int main(void) {{
+  printf("size %zu\\n", sizeof(jd_feedback_desc));
+{body}
+  return 0;
+}}
+""")
+    exe = tmp_path / "fb_layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    lines = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    vals = dict((ln.split()[0], ln.split()[1:]) for ln in lines if ln)
+    assert int(vals["size"][0]) == ctypes.sizeof(binding.FeedbackDesc)
+    for f in fields:
+        assert int(vals[f][0]) == getattr(binding.FeedbackDesc, f).offset, f
+
+
 def _create(desc):
     h = ctypes.c_void_p()
     st = binding.lib().jd_problem_create(ctypes.byref(desc), ctypes.byref(h))
