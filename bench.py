@@ -128,6 +128,10 @@ WORKLOADS = {
     "lq_scalar": workloads.lq_scalar,       # d=1 linear-quadratic, M=1000, Nt=100 (FP64)
     # autograd form: J(u, theta) forward + backward, M=2^22, Nt=4096, checkpointed states
     "double_well_autograd": workloads.double_well_autograd,
+    # Keilson-Storer velocity resets (beta=10, gamma=0.9), d=2 oscillator, M=2^20, Nt=500
+    "ks_oscillator": workloads.ks_oscillator,
+    # feedback control mu(t)^T phi(z), 10x10 bumps, Gaussian tracking, resets; M=2^20, Nt=100
+    "feedback_centering": lambda: workloads.feedback_centering()[0],
 }
 
 
@@ -204,6 +208,8 @@ def run_ours(args):
     p = replica_problem(bench_workload(args.paths, args.steps_t, args.workload), rank)
     if args.workload == "double_well_autograd":
         return run_autograd(args, p, stream, dist, ws, rank, local)
+    if args.workload == "feedback_centering":
+        return run_feedback(args, p, stream, dist, ws, rank, local)
     M, Nt, du = p.M, p.Nt, p.du
     prec = "fp64" if args.workload == "lq_scalar" else "fp32"
     prob = jd.JdProblem(p, prec=prec, mode=args.variant or "stored", stream=stream,
@@ -286,6 +292,126 @@ def run_ours(args):
                 "value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                 "sample": f"{args.reference_paths} of {M} paths, all {Nt} steps, one optimizer "
                           "iteration"}
+        print(json.dumps(line), flush=True)
+    prob.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def fb_forward_ops(p, fb):
+    """Lane operations per path-step of the feedback forward sweep: the open-loop step
+    (draws, drift, Euler, cost) plus the feedback: per bump r, r^2, 1 - eps^2 r^2, rcp,
+    scale, 2^y (6), the bilinear form (nx nv + nx FMA), the control cost (3) and the
+    Gaussian tracking term (6)."""
+    return forward_ops(p) + 6 * (fb.nx + fb.nv) + fb.nx * fb.nv + fb.nx + 3 + 6
+
+
+def fb_adjoint_ops(p, fb):
+    """Lane operations per path-step of the feedback adjoint: bumps with derivatives (10
+    each), the bilinear forms for u and u_v (2 nx nv + 3 nx), the outer product
+    delta w phi_x phi_v^T summed over paths (nx nv FMA per path), the costate update
+    (2 d^2 + 4) and the tracking gradient (6)."""
+    return 10 * (fb.nx + fb.nv) + 2 * fb.nx * fb.nv + 3 * fb.nx + fb.nx * fb.nv + 2 * p.d * p.d + 4 + 6
+
+
+def run_feedback(args, p, stream, dist, ws, rank, local):
+    """One step = one feedback gradient dJ/dmu (forward sweep storing X_k, adjoint sweep
+    with the per-step outer-product reduction, FP64 reductions) on device-resident mu."""
+    import torch
+    import paper_2505_04328_gb300 as jd
+    from paper_2505_04328_gb300.binding import JD_MEM_DEVICE, _check, lib, make_feedback
+    import ctypes
+
+    fb = workloads.feedback_centering()[1]
+    M, Nt, L = p.M, p.Nt, fb.L
+    prob = jd.JdProblem(p, prec="fp32", stream=stream)
+    mu = torch.tensor(workloads.random_mu(p, fb, seed=23, scale=0.5), dtype=torch.float64, device="cuda")
+    g = torch.empty_like(mu)
+    F = make_feedback(fb)
+    J = ctypes.c_double()
+
+    def step():
+        _check(lib().jd_fb_gradient(prob.h, ctypes.byref(F), ctypes.c_void_p(mu.data_ptr()), JD_MEM_DEVICE,
+                                    ctypes.byref(J), ctypes.c_void_p(g.data_ptr())), "jd_fb_gradient")
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    jd.profile_enable(True)
+    l0 = jd.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = jd.launch_count() - l0
+    kstats = jd.profile_read()
+    jd.profile_enable(False)
+    clk = clocks.stop()
+    if dist is not None:
+        ms = max_over_ranks(dist, ms, device="cuda")
+    ms_per_step = ms / args.steps
+    value = ws * M * Nt / (ms_per_step * 1e-3)
+
+    # end to end: mu from host memory, the gradient back to host memory, every step
+    mu_h = mu.cpu().numpy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        Jh, gh = prob.fb_gradient(fb, mu_h)
+    e2e_sec = (time.perf_counter() - t0) / args.steps
+    e2e = {"value": ws * M * Nt / e2e_sec, "unit": UNIT, "h2d_bytes_per_step": Nt * L * 8,
+           "d2h_bytes_per_step": Nt * L * 8 + 8}
+
+    peaks, _ = _peaks()
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak = 152 * 4 * 32 * sm_mhz * 1e6 / 1e9
+    rl = {}
+    for name, ops in (("fb_fwd", fb_forward_ops(p, fb)), ("fb_adj", fb_adjoint_ops(p, fb))):
+        if name in kstats:
+            launches_k, total_ms = kstats[name]
+            achieved = ops * M * Nt / (total_ms / launches_k * 1e-3) / 1e9
+            rl[name] = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Glane-op/s",
+                        "frac": achieved / peak, "traffic": None,
+                        "peak_source": "derived: 152 SMs x 4 schedulers x 32 lanes x 1 instruction/clock x "
+                                       f"{sm_mhz:.0f} MHz (max SM clock)",
+                        "algorithmic_ops_per_path_step": ops}
+    dom = max(rl, key=lambda k: kstats[k][1]) if rl else None
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"feedback_centering d=2 M={M} Nt={Nt} L={fb.nx}x{fb.nv}",
+                       "variant": "stored", "paths_per_gpu": M, "Nt": Nt, "eps": fb.eps,
+                       "step": "one feedback gradient dJ/dmu (forward sweep, adjoint sweep, reductions)",
+                       "l2": "inputs larger than L2: the stored states (%.2f GB) and warp partials exceed "
+                             "the 129 MB L2; no flush" % ((Nt + 1) * 2 * M * 4 / 1e9)},
+            "gpu_launches": launches,
+            "kernels_ms_per_step": {k: v[1] / args.steps for k, v in kstats.items()},
+            "roofline": rl.get(dom),
+            "roofline_all": rl,
+            "e2e": e2e,
+            "clocks": clk,
+            "J": J.value,
+        }
+        if not args.no_cpu_baseline:
+            import oracle
+            ps = p.replace(M=min(M, args.reference_paths // 4))
+            t0 = time.perf_counter()
+            oracle.fb_gradient(ps, fb, mu.cpu().numpy())
+            sec = time.perf_counter() - t0
+            line["cpu_baseline"] = {
+                "value": ps.M * Nt / sec, "unit": UNIT, "cores": oracle.default_threads(), "kind": "oracle",
+                "sample": f"{ps.M} of {M} paths, all {Nt} steps, one feedback gradient"}
         print(json.dumps(line), flush=True)
     prob.close()
     if dist is not None:

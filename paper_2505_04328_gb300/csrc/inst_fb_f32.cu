@@ -17,13 +17,22 @@ __global__ void fb_finalize_kernel(const double *__restrict__ partC, const doubl
     const int r = (int)(t - k * nx * nv), i = r / nv, l = r - i * nv;
     const int64_t src = k * NX * NV + ((i / 2) * NV + l) * 2 + (i & 1);   // pair layout
     double s = 0.0;
+#pragma unroll 8
     for (int64_t g = 0; g < ngroup; ++g) s += partG[g * ncol + src];
     grad[t] = s * inv;
   }
-  if (J && blockIdx.x == 0 && threadIdx.x == 0) {
+  if (J && blockIdx.x == 0) {
+    // J: block 0's threads take partC[t], partC[t + 128], ... then a fixed tree
+    __shared__ double red[128];
     double s = 0.0;
-    for (int64_t b = 0; b < nblk; ++b) s += partC[b];
-    *J = s * inv;
+    for (int64_t b = threadIdx.x; b < nblk; b += blockDim.x) s += partC[b];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = 64; h >= 1; h >>= 1) {
+      if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) *J = red[0] * inv;
   }
 }
 

@@ -24,10 +24,10 @@ void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_r
 // Optional per-kernel-class timing: a CUDA event pair around every launch, on the
 // launching stream, summed on read.
 enum KernelClass { KC_FWD_COST, KC_FWD_STORE, KC_FWD_CKPT, KC_ADJ_STORED, KC_ADJ_RECOMPUTE,
-                   KC_FINALIZE, KC_PREP, KC_OPT, KC_FB_FWD, KC_FB_ADJ, KC_FB_FIN, KC_COUNT };
+                   KC_FINALIZE, KC_PREP, KC_OPT, KC_FB_FWD, KC_FB_ADJ, KC_FB_RED, KC_FB_FIN, KC_COUNT };
 static const char *kKernelClassName[KC_COUNT] = {"fwd_cost", "fwd_store", "fwd_ckpt", "adj_stored",
                                                  "adj_recompute", "finalize", "prep_u", "opt_step",
-                                                 "fb_fwd", "fb_adj", "fb_finalize"};
+                                                 "fb_fwd", "fb_adj", "fb_reduce", "fb_finalize"};
 struct ProfRec {
   int kind;
   cudaEvent_t a, b;
@@ -1411,6 +1411,9 @@ static jd_status fb_run(jd_problem *p, const jd_feedback_desc *fb, const double 
   if (grad_out) {
     pr = prof_begin(KC_FB_ADJ, p->stream);
     JD_CUDA(ops->adj(p, *fb, b, p->stream));
+    prof_end(pr, p->stream);
+    pr = prof_begin(KC_FB_RED, p->stream);
+    JD_CUDA(ops->reduce(p, b, p->stream));
     prof_end(pr, p->stream);
   }
   pr = prof_begin(KC_FB_FIN, p->stream);

@@ -49,7 +49,6 @@
 namespace jd {
 
 constexpr int FB_AROW = 68;   // exchange buffer: pitch of a pair row (2 x 32 values + 4)
-constexpr int FB_BROW = 36;   // exchange buffer: pitch of a phi_v row (32 values + 4)
 
 template <typename R>
 struct FbParams {
@@ -94,28 +93,26 @@ __device__ __forceinline__ double bump(double r, const FbParams<double> &fp, dou
 }
 
 // FP32: two bumps at once (distances r0, r1 to their centres): paired arithmetic, SFU
-// reciprocal and 2^y
+// reciprocal and 2^y.  1 - eps^2 r^2 is clamped below at 2^-40 instead of branching on
+// the support: off it (and where 1 - eps^2 r^2 < 2^-40, inside) t = 2^40 makes
+// 2^(-t log2 e) exactly 0, and t^2 = 2^80 stays finite, so phi and phi' are 0.
 template <bool GRAD>
 __device__ __forceinline__ void bump2(float r0, float r1, const FbParams<float> &fp, float &p0, float &p1,
                                       float &d0, float &d1) {
   float q0, q1, s0 = 1.f, s1 = 1.f;
   Pr<float>::mul(r0, r1, r0, r1, q0, q1);
   Pr<float>::fma(-fp.eps2, -fp.eps2, q0, q1, s0, s1);   // 1 - eps^2 r^2
-  const float t0 = sfu_rcp(s0), t1 = sfu_rcp(s1);
+  const float t0 = sfu_rcp(fmaxf(s0, 0x1p-40f)), t1 = sfu_rcp(fmaxf(s1, 0x1p-40f));
   float y0, y1;
   Pr<float>::mul(t0, t1, kNegLog2e, kNegLog2e, y0, y1);
-  const float e0 = sfu_ex2(y0), e1 = sfu_ex2(y1);
-  p0 = s0 > 0.f ? e0 : 0.f;
-  p1 = s1 > 0.f ? e1 : 0.f;
+  p0 = sfu_ex2(y0);
+  p1 = sfu_ex2(y1);
   if (GRAD) {
     float tt0, tt1, w0, w1, z0, z1;
     Pr<float>::mul(t0, t1, t0, t1, tt0, tt1);
     Pr<float>::mul(p0, p1, tt0, tt1, w0, w1);
     Pr<float>::mul(r0, r1, fp.m2eps2, fp.m2eps2, z0, z1);
     Pr<float>::mul(w0, w1, z0, z1, d0, d1);
-    // off the support t may be infinite (1 - eps^2 r^2 == 0) and 0 * inf is NaN
-    d0 = s0 > 0.f ? d0 : 0.f;
-    d1 = s1 > 0.f ? d1 : 0.f;
   }
 }
 
@@ -392,49 +389,47 @@ fb_fwd_kernel(const __grid_constant__ KParams<R, 2, 1> kp, const __grid_constant
   if (threadIdx.x == 0) partC[blockIdx.x] = bs;
 }
 
-// 32-path dot products of one pair row (rows i, i+1 of the delta w phi_x factors,
-// interleaved) with one phi_v row: (s0, s1) += sum_m (A_i,m, A_i+1,m) B_l,m.  FP32:
-// four independent chains (paths m = 4q + c), then added, so that the paired FMAs do
-// not wait on one another.
+// 32-path dot products of a 2 x 2 block of weights: pa is the pair row of rows i, i+1 of
+// the delta w phi_x factors, pb the pair row of phi_v at l, l+1 (both [path][2]):
+// q += sum_m (A_i,m B_l,m, A_i+1,m B_l,m, A_i,m B_l+1,m, A_i+1,m B_l+1,m).  FP32: the
+// even and odd paths in separate chains, added at the end.
 template <typename R>
-__device__ __forceinline__ void pair_dot32(const R *pa, const R *pb, R &s0, R &s1);
+__device__ __forceinline__ void quad_dot32(const R *pa, const R *pb, R (&q)[4]);
 template <>
-__device__ __forceinline__ void pair_dot32<float>(const float *pa, const float *pb, float &s0, float &s1) {
-  float c0[4] = {0.f, 0.f, 0.f, 0.f}, c1[4] = {0.f, 0.f, 0.f, 0.f};
+__device__ __forceinline__ void quad_dot32<float>(const float *pa, const float *pb, float (&q)[4]) {
+  float e[4] = {0.f, 0.f, 0.f, 0.f}, o[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-  for (int j = 0; j < 32; j += 4) {
-    const float4 a = *reinterpret_cast<const float4 *>(pa + 2 * j);
-    const float4 c = *reinterpret_cast<const float4 *>(pa + 2 * j + 4);
+  for (int j = 0; j < 64; j += 4) {   // paths j/2 and j/2 + 1
+    const float4 a = *reinterpret_cast<const float4 *>(pa + j);
     const float4 b = *reinterpret_cast<const float4 *>(pb + j);
-    Pr<float>::fma(a.x, a.y, b.x, b.x, c0[0], c1[0]);
-    Pr<float>::fma(a.z, a.w, b.y, b.y, c0[1], c1[1]);
-    Pr<float>::fma(c.x, c.y, b.z, b.z, c0[2], c1[2]);
-    Pr<float>::fma(c.z, c.w, b.w, b.w, c0[3], c1[3]);
+    Pr<float>::fma(a.x, a.y, b.x, b.x, e[0], e[1]);
+    Pr<float>::fma(a.x, a.y, b.y, b.y, e[2], e[3]);
+    Pr<float>::fma(a.z, a.w, b.z, b.z, o[0], o[1]);
+    Pr<float>::fma(a.z, a.w, b.w, b.w, o[2], o[3]);
   }
-  float u0, u1, v0, v1;
-  Pr<float>::add(c0[0], c1[0], c0[1], c1[1], u0, u1);
-  Pr<float>::add(c0[2], c1[2], c0[3], c1[3], v0, v1);
-  Pr<float>::add(u0, u1, v0, v1, u0, u1);
-  Pr<float>::add(s0, s1, u0, u1, s0, s1);
+  float t0, t1;
+  Pr<float>::add(e[0], e[1], o[0], o[1], t0, t1);
+  Pr<float>::add(q[0], q[1], t0, t1, q[0], q[1]);
+  Pr<float>::add(e[2], e[3], o[2], o[3], t0, t1);
+  Pr<float>::add(q[2], q[3], t0, t1, q[2], q[3]);
 }
 template <>
-__device__ __forceinline__ void pair_dot32<double>(const double *pa, const double *pb, double &s0, double &s1) {
+__device__ __forceinline__ void quad_dot32<double>(const double *pa, const double *pb, double (&q)[4]) {
 #pragma unroll
-  for (int j = 0; j < 32; j += 2) {
-    const double2 a = *reinterpret_cast<const double2 *>(pa + 2 * j);
-    const double2 c = *reinterpret_cast<const double2 *>(pa + 2 * j + 2);
+  for (int j = 0; j < 64; j += 2) {
+    const double2 a = *reinterpret_cast<const double2 *>(pa + j);
     const double2 b = *reinterpret_cast<const double2 *>(pb + j);
-    s0 = __fma_rn(a.x, b.x, s0);
-    s1 = __fma_rn(a.y, b.x, s1);
-    s0 = __fma_rn(c.x, b.y, s0);
-    s1 = __fma_rn(c.y, b.y, s1);
+    q[0] = __fma_rn(a.x, b.x, q[0]);
+    q[1] = __fma_rn(a.y, b.x, q[1]);
+    q[2] = __fma_rn(a.x, b.y, q[2]);
+    q[3] = __fma_rn(a.y, b.y, q[3]);
   }
 }
 
-// Shared memory of fb_adj_kernel: per warp NX/2 pair rows and NV phi_v rows.
+// Shared memory of fb_adj_kernel: per warp NX/2 pair rows of phi_x factors and NV/2 of phi_v.
 template <typename R, int NX, int NV>
 constexpr size_t fb_adj_smem() {
-  return sizeof(R) * (size_t)(FB_TPB / 32) * ((NX / 2) * FB_AROW + NV * FB_BROW);
+  return sizeof(R) * (size_t)(FB_TPB / 32) * ((NX / 2) + (NV / 2)) * FB_AROW;
 }
 
 template <typename R, int NX, int NV>
@@ -443,10 +438,10 @@ fb_adj_kernel(const __grid_constant__ KParams<R, 2, 1> kp, const __grid_constant
               const R *__restrict__ mu, const R *__restrict__ xd, const R *__restrict__ traj,
               const uint32_t *__restrict__ flags, R *__restrict__ partW) {
   using M = Ar<R>;
-  constexpr int LP = NX * NV, NP = (NX / 2) * NV, PPL = (NP + 31) / 32;
+  constexpr int LP = NX * NV, NQ = (NX / 2) * (NV / 2), QPL = (NQ + 31) / 32;   // 2 x 2 blocks
   extern __shared__ __align__(16) unsigned char fb_smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  R *wa = reinterpret_cast<R *>(fb_smem) + warp * ((NX / 2) * FB_AROW + NV * FB_BROW);
+  R *wa = reinterpret_cast<R *>(fb_smem) + warp * ((NX / 2) + (NV / 2)) * FB_AROW;
   R *wb = wa + (NX / 2) * FB_AROW;
   const int64_t mloc = fp.mloc, m = (int64_t)blockIdx.x * FB_TPB + threadIdx.x;
   const int64_t wid = (int64_t)blockIdx.x * (FB_TPB / 32) + warp;
@@ -500,12 +495,13 @@ fb_adj_kernel(const __grid_constant__ KParams<R, 2, 1> kp, const __grid_constant
     }
     // sub-steps n..0 backwards, round r = sub-step n - r of every path (paths with fewer
     // sub-steps contribute zeros); each round's records (delta w phi_x, phi_v) are summed
-    // over the warp's 32 paths through the exchange buffer.  Lane p forms the pair of
-    // weights (i, i+1) x l with i/2 = p / NV, l = p % NV: eight consecutive lanes read at
-    // most two pair rows (mostly the same address) and eight phi_v rows.
-    R s0[PPL], s1[PPL];
+    // over the warp's 32 paths through the exchange buffer (pair rows: values of rows
+    // c, c+1 interleaved per path).  Lane p forms the 2 x 2 block of weights
+    // (i, i+1) x (l, l+1), i/2 = p / (NV/2), l/2 = p % (NV/2): eight consecutive lanes read
+    // at most three phi_x pair rows and distinct phi_v pair rows (4-bank offsets).
+    R sq[QPL][4];
 #pragma unroll
-    for (int t = 0; t < PPL; ++t) s0[t] = s1[t] = R(0);
+    for (int t = 0; t < QPL; ++t) sq[t][0] = sq[t][1] = sq[t][2] = sq[t][3] = R(0);
     const int rounds = (int)__reduce_max_sync(0xffffffffu, active ? (unsigned)(n + 1) : 0u);
 #pragma unroll 1
     for (int r = 0; r < rounds; ++r) {
@@ -540,12 +536,12 @@ fb_adj_kernel(const __grid_constant__ KParams<R, 2, 1> kp, const __grid_constant
 #pragma unroll
       for (int c = 0; c < NX; ++c) wa[(c / 2) * FB_AROW + 2 * lane + (c & 1)] = ra[c];
 #pragma unroll
-      for (int c = 0; c < NV; ++c) wb[c * FB_BROW + lane] = rb[c];
+      for (int c = 0; c < NV; ++c) wb[(c / 2) * FB_AROW + 2 * lane + (c & 1)] = rb[c];
       __syncwarp();
 #pragma unroll
-      for (int t = 0; t < PPL; ++t) {
+      for (int t = 0; t < QPL; ++t) {
         const int p = lane + 32 * t;
-        if (p < NP) pair_dot32<R>(wa + (p / NV) * FB_AROW, wb + (p % NV) * FB_BROW, s0[t], s1[t]);
+        if (p < NQ) quad_dot32<R>(wa + (p / (NV / 2)) * FB_AROW, wb + (p % (NV / 2)) * FB_AROW, sq[t]);
       }
       __syncwarp();
     }
@@ -555,31 +551,71 @@ fb_adj_kernel(const __grid_constant__ KParams<R, 2, 1> kp, const __grid_constant
       a[0] = M::add(a[0], g[0]);
       a[1] = M::add(a[1], g[1]);
     }
+    // block (i/2, l/2) = (p / (NV/2), p % (NV/2)): weights (i, l), (i+1, l), (i, l+1),
+    // (i+1, l+1) are contiguous in the pair layout, one 16-byte store in FP32
     R *dst = partW + ((size_t)wid * Nt + k) * LP;
 #pragma unroll
-    for (int t = 0; t < PPL; ++t) {
+    for (int t = 0; t < QPL; ++t) {
       const int p = lane + 32 * t;
-      if (p < NP) {
-        dst[2 * p] = s0[t];
-        dst[2 * p + 1] = s1[t];
+      if (p < NQ) {
+        R *o = dst + 2 * ((p / (NV / 2)) * NV + 2 * (p % (NV / 2)));
+        if constexpr (sizeof(R) == 4) {
+          *reinterpret_cast<float4 *>(o) = make_float4(sq[t][0], sq[t][1], sq[t][2], sq[t][3]);
+        } else {
+          o[0] = sq[t][0];
+          o[1] = sq[t][1];
+          o[2] = sq[t][2];
+          o[3] = sq[t][3];
+        }
       }
     }
   }
 }
 
-// partG[g][c] = sum over warps w of group g (in order) of partW[w][c], FP64; one thread
-// per (group, column), consecutive threads on consecutive columns.
+// partG[g][c] = sum over warps w of group g (in order) of partW[w][c]; one thread per
+// group and four consecutive columns (16-byte loads in FP32), consecutive threads on
+// consecutive columns.  FP32 partials are added as compensated FP32 pairs (TwoSum: FP64
+// adds are scarce on this part) and the pair is rounded to FP64 once per group; FP64
+// partials are added in FP64.  ncol is a multiple of 4 (NX NV is 16, 100 or 256).
 template <typename R>
 __global__ void fb_reduce_kernel(const R *__restrict__ partW, int64_t nwarp, int64_t ncol,
                                  double *__restrict__ partG) {
-  const int64_t ngroup = (nwarp + FB_GROUP_WARPS - 1) / FB_GROUP_WARPS;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ngroup * ncol;
+  const int64_t ngroup = (nwarp + FB_GROUP_WARPS - 1) / FB_GROUP_WARPS, nc4 = ncol / 4;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ngroup * nc4;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t g = t / ncol, c = t - g * ncol;
+    const int64_t g = t / nc4, c = 4 * (t - g * nc4);
     const int64_t w1 = std::min<int64_t>(nwarp, (g + 1) * FB_GROUP_WARPS);
-    double s = 0.0;
-    for (int64_t w = g * FB_GROUP_WARPS; w < w1; ++w) s += (double)partW[w * ncol + c];
-    partG[t] = s;
+    double *o = partG + g * ncol + c;
+    if constexpr (sizeof(R) == 4) {
+      Pair<float> s0{0.f, 0.f}, s1{0.f, 0.f}, s2{0.f, 0.f}, s3{0.f, 0.f};
+#pragma unroll 8
+      for (int64_t w = g * FB_GROUP_WARPS; w < w1; ++w) {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(partW + w * ncol + c));
+        s0 = padd(s0, Pair<float>{v.x, 0.f});
+        s1 = padd(s1, Pair<float>{v.y, 0.f});
+        s2 = padd(s2, Pair<float>{v.z, 0.f});
+        s3 = padd(s3, Pair<float>{v.w, 0.f});
+      }
+      o[0] = (double)s0.s + (double)s0.e;
+      o[1] = (double)s1.s + (double)s1.e;
+      o[2] = (double)s2.s + (double)s2.e;
+      o[3] = (double)s3.s + (double)s3.e;
+    } else {
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+#pragma unroll 4
+      for (int64_t w = g * FB_GROUP_WARPS; w < w1; ++w) {
+        const R *q = partW + w * ncol + c;
+        const double2 v = __ldg(reinterpret_cast<const double2 *>(q)), u = __ldg(reinterpret_cast<const double2 *>(q) + 1);
+        s0 += v.x;
+        s1 += v.y;
+        s2 += u.x;
+        s3 += u.y;
+      }
+      o[0] = s0;
+      o[1] = s1;
+      o[2] = s2;
+      o[3] = s3;
+    }
   }
 }
 
@@ -645,7 +681,7 @@ cudaError_t fb_fwd_launch(const ::jd_problem *p, const jd_feedback_desc &fb, boo
   return cudaGetLastError();
 }
 
-// The adjoint sweep, then the first (group) stage of the gradient reduction.
+// The adjoint sweep (warp partials of the gradient).
 template <typename R, int NX, int NV>
 cudaError_t fb_adj_launch(const ::jd_problem *p, const jd_feedback_desc &fb, const FbBufs &b, cudaStream_t s) {
   KParams<R, 2, 1> kp;
@@ -663,12 +699,16 @@ cudaError_t fb_adj_launch(const ::jd_problem *p, const jd_feedback_desc &fb, con
                                                       static_cast<const R *>(b.traj), b.flags,
                                                       static_cast<R *>(b.partW));
   count_launch();
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const int64_t nwarp = (int64_t)grid * (FB_TPB / 32), ncol = (int64_t)p->desc.Nt * NX * NV;
-  const int64_t n = fb_groups(nwarp) * ncol;
-  const unsigned g2 = (unsigned)std::min<int64_t>(ceil_div(n, 256), 152 * 16);
-  fb_reduce_kernel<R><<<g2, 256, 0, s>>>(static_cast<const R *>(b.partW), nwarp, ncol, b.partG);
+  return cudaGetLastError();
+}
+
+// First stage of the gradient reduction: warp partials -> FP64 group partials.
+template <typename R, int NX, int NV>
+cudaError_t fb_reduce_launch(const ::jd_problem *p, const FbBufs &b, cudaStream_t s) {
+  const int64_t nwarp = ceil_div(p->desc.M, FB_TPB) * (FB_TPB / 32), ncol = (int64_t)p->desc.Nt * NX * NV;
+  const int64_t n = fb_groups(nwarp) * (ncol / 4);
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 152 * 16));
+  fb_reduce_kernel<R><<<grid, 256, 0, s>>>(static_cast<const R *>(b.partW), nwarp, ncol, b.partG);
   count_launch();
   return cudaGetLastError();
 }
@@ -701,7 +741,7 @@ size_t fb_stack_bytes() {
 template <typename R, int NX, int NV>
 constexpr FbOps fb_make_ops() {
   return FbOps{NX, NV, (int)sizeof(R), &fb_stack_bytes<R, NX, NV>, &fb_fwd_launch<R, NX, NV>,
-               &fb_adj_launch<R, NX, NV>, &fb_prep_dims<R, NX, NV>};
+               &fb_adj_launch<R, NX, NV>, &fb_reduce_launch<R, NX, NV>, &fb_prep_dims<R, NX, NV>};
 }
 
 }  // namespace jd

@@ -79,7 +79,7 @@ const PathOps *path_ops_dims(int prec, int D, int DU);
 // Feedback control kernels (jd_fb_*): d = 2, du = 1, padded NX x NV weights.
 constexpr int FB_TPB = 256;   // threads (one path each) per block
 constexpr int FB_NB = 16;     // largest centre count per axis
-constexpr int FB_GROUP_WARPS = 512;   // warps per group of the first gradient reduction stage
+constexpr int FB_GROUP_WARPS = 128;   // warps per group of the first gradient reduction stage
 inline int64_t fb_groups(int64_t nwarp) { return (nwarp + FB_GROUP_WARPS - 1) / FB_GROUP_WARPS; }
 
 struct FbBufs {
@@ -99,6 +99,7 @@ struct FbOps {
                      const FbBufs &b, cudaStream_t s);
   cudaError_t (*adj)(const struct ::jd_problem *p, const jd_feedback_desc &fb, const FbBufs &b,
                      cudaStream_t s);
+  cudaError_t (*reduce)(const struct ::jd_problem *p, const FbBufs &b, cudaStream_t s);   // partW -> partG
   cudaError_t (*prep_mu)(const double *mu64, void *muR, int Nt, int nx, int nv, cudaStream_t s);
 };
 const FbOps *fb_ops(int prec, int nx, int nv);   // the smallest compiled NX x NV that fits
