@@ -358,6 +358,20 @@ jd_status jd_fb_cost(jd_problem *p, const jd_feedback_desc *fb, const double *mu
 jd_status jd_fb_gradient(jd_problem *p, const jd_feedback_desc *fb, const double *mu,
                          jd_memspace space, double *J, double *grad);
 
+/* Gradient descent with the Armijo rule on the weights (Algorithm 5.4 with
+ * eq:Stochastic_Armijo; mu is unconstrained): per iteration one jd_fb_gradient at mu^n,
+ * then trial points mu^n - zeta g, g = (dJ/dmu)/dt, until J(trial) <= J(mu^n) -
+ * c zeta |g|^2_{L2} (|g|^2_{L2} = dt sum g^2), zeta halved per rejection; zeta doubles
+ * (capped at zeta_max) from the second iteration on.  Stops on |g|_{L2} <= tol_rel_grad
+ * times its first value, on a step |mu^{n+1} - mu^n|_{L2} < tol_step, or after max_iter
+ * updates.  The update kernels and the norms run on the device in FP64; the host reads
+ * J and |g|^2 back for each decision.  mu_inout: Nt * L doubles in `space`, updated in
+ * place; J_hist (host, max_iter + 1, nullable).  r->status is JD_ERR_LINESEARCH (also
+ * returned) when max_backtracks halvings did not satisfy the test.  Other errors as
+ * jd_fb_cost. */
+jd_status jd_fb_optimize(jd_problem *p, const jd_feedback_desc *fb, double *mu_inout, jd_memspace space,
+                         const jd_opt_params *o, jd_opt_result *r, double *J_hist);
+
 const char *jd_status_string(jd_status s);
 const char *jd_last_error(void);
 

@@ -122,6 +122,8 @@ def lib():
             L.orc_fb_path.argtypes = [P(_Problem), P(_Feedback), ctypes.c_void_p, ctypes.c_int64] + [ctypes.c_void_p] * 5
             L.orc_fb_cost.argtypes = [P(_Problem), P(_Feedback), ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
             L.orc_fb_gradient.argtypes = [P(_Problem), P(_Feedback), ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 2
+            L.orc_fb_optimize.argtypes = [P(_Problem), P(_Feedback), ctypes.c_void_p, P(_OptParams), ctypes.c_int,
+                                          P(_OptResult), ctypes.c_void_p]
             _lib = L
     return _lib
 
@@ -328,3 +330,20 @@ def fb_gradient(p, fb, mu=None, nthreads: int | None = None):
     if rc:
         raise ValueError(f"orc_fb_gradient failed ({rc})")
     return float(J[0]), g
+
+
+def fb_optimize(p, fb, mu0=None, max_iter=20, tol_rel_grad=1e-4, tol_step=0.0, armijo_c=1e-4,
+                zeta0=1.0, zeta_max=1e3, max_backtracks=40, nthreads=None):
+    """Armijo gradient descent on the feedback weights; returns (mu, result dict, J history)."""
+    op = OracleProblem(p)
+    F = _fb(fb)
+    mu = _mu(p, fb, mu0).copy()
+    o = _OptParams(max_iter=max_iter, tol_rel_grad=tol_rel_grad, tol_step=tol_step,
+                   armijo_c=armijo_c, zeta0=zeta0, zeta_max=zeta_max, max_backtracks=max_backtracks)
+    r = _OptResult()
+    hist = np.full(max_iter + 2, np.nan)
+    lib().orc_fb_optimize(ctypes.byref(op.s), ctypes.byref(F), _ptr(mu), ctypes.byref(o),
+                          nthreads or default_threads(), ctypes.byref(r), _ptr(hist))
+    res = dict(iters=r.iters, evals=r.evals, status=r.status, J=r.J,
+               rel_grad_norm=r.rel_grad_norm, zeta=r.zeta)
+    return mu, res, hist[: r.iters + 1]

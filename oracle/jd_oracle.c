@@ -765,3 +765,63 @@ int orc_fb_gradient(const orc_problem *P, const orc_feedback *F, const double *m
                     double *J, double *grad) {
   return fb_sweep(P, F, mu, nthreads, J, grad);
 }
+
+/* Gradient descent with the Armijo rule on the feedback weights (Algorithm 5.4 with
+ * eq:Stochastic_Armijo; mu is unconstrained).  g = (dJ/dmu)/dt is the L2 representative;
+ * the trial point is mu+ = mu - zeta g, accepted when J(mu+) <= J(mu) - c zeta |g|_{L2}^2.
+ * Same schedule of zeta and the same stopping tests as orc_optimize. */
+int orc_fb_optimize(const orc_problem *P, const orc_feedback *F, double *mu, const orc_opt_params *o,
+                    int nthreads, orc_opt_result *r, double *J_hist) {
+  if (!fb_valid(P, F) || !mu || !o || !r) return 1;
+  const size_t n = (size_t)P->Nt * F->nx * F->nv;
+  const double dt = P->T / (double)P->Nt;
+  double *grad = (double *)malloc(sizeof(double) * n);
+  double *mt = (double *)malloc(sizeof(double) * n);
+  memset(r, 0, sizeof(*r));
+  double J = 0.0, pg0 = -1.0, zeta = o->zeta0 > 0 ? o->zeta0 : 1.0;
+  double zeta_max = o->zeta_max > 0 ? o->zeta_max : 1e3;
+  int status = 0, it = 0;
+  for (it = 0; it < o->max_iter; ++it) {
+    int rc = orc_fb_gradient(P, F, mu, nthreads, &J, grad);
+    r->evals++;
+    if (rc) { status = 1; break; }
+    if (J_hist) J_hist[it] = J;
+    double g2 = 0.0;   /* |g|_{L2}^2 = dt sum (grad/dt)^2 */
+    for (size_t t = 0; t < n; ++t) g2 += dt * (grad[t] / dt) * (grad[t] / dt);
+    double pg = sqrt(g2);
+    if (pg0 < 0.0) pg0 = pg;
+    r->rel_grad_norm = pg0 > 0.0 ? pg / pg0 : 0.0;
+    if (r->rel_grad_norm <= o->tol_rel_grad) break;
+    if (it > 0) zeta = fmin(2.0 * zeta, zeta_max);
+    int accepted = 0;
+    double Jt = 0.0;
+    for (int b = 0; b <= o->max_backtracks; ++b) {
+      for (size_t t = 0; t < n; ++t) mt[t] = mu[t] - zeta * (grad[t] / dt);
+      rc = orc_fb_cost(P, F, mt, nthreads, &Jt);
+      r->evals++;
+      if (rc) { status = 1; break; }
+      if (Jt <= J - o->armijo_c * zeta * g2) { accepted = 1; break; }
+      zeta *= 0.5;
+    }
+    if (status) break;
+    if (!accepted) { status = 5; break; }
+    double step2 = 0.0;
+    for (size_t t = 0; t < n; ++t) {
+      step2 += dt * (mt[t] - mu[t]) * (mt[t] - mu[t]);
+      mu[t] = mt[t];
+    }
+    J = Jt;
+    if (J_hist) J_hist[it + 1] = J;
+    if (sqrt(step2) < o->tol_step) {
+      it++;
+      break;
+    }
+  }
+  r->iters = it;
+  r->J = J;
+  r->zeta = zeta;
+  r->status = status;
+  free(grad);
+  free(mt);
+  return status;
+}

@@ -172,6 +172,10 @@ int orc_fb_cost(const orc_problem *P, const orc_feedback *F, const double *mu, i
                 double *J);
 int orc_fb_gradient(const orc_problem *P, const orc_feedback *F, const double *mu, int nthreads,
                     double *J, double *grad);
+/* Gradient descent with the Armijo rule on mu (Algorithm 5.4, unconstrained): the same
+ * zeta schedule and stopping tests as orc_optimize; mu (Nt*L) is updated in place. */
+int orc_fb_optimize(const orc_problem *P, const orc_feedback *F, double *mu, const orc_opt_params *o,
+                    int nthreads, orc_opt_result *r, double *J_hist);
 
 #ifdef __cplusplus
 }

@@ -32,7 +32,7 @@ ABI_SYMBOLS = (
     "jd_optimize", "jd_problem_info", "jd_kernel_launch_count", "jd_profile_enable",
     "jd_profile_read", "jd_cost_noalloc", "jd_problem_footprint", "jd_server_create",
     "jd_server_submit", "jd_server_poll", "jd_server_wait", "jd_server_info", "jd_server_destroy",
-    "jd_status_string", "jd_last_error", "jd_fb_cost", "jd_fb_gradient",
+    "jd_status_string", "jd_last_error", "jd_fb_cost", "jd_fb_gradient", "jd_fb_optimize",
 )
 
 
@@ -122,6 +122,7 @@ def lib():
         L.jd_cost_noalloc.argtypes = [P(ProblemDesc), dp, dp]
         L.jd_fb_cost.argtypes = [vp, P(FeedbackDesc), dp, ctypes.c_int, dp]
         L.jd_fb_gradient.argtypes = [vp, P(FeedbackDesc), dp, ctypes.c_int, dp, dp]
+        L.jd_fb_optimize.argtypes = [vp, P(FeedbackDesc), dp, ctypes.c_int, P(OptParams), P(OptResult), dp]
         L.jd_problem_footprint.argtypes = [P(ProblemDesc), ctypes.c_int, P(ctypes.c_size_t)]
         L.jd_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int, P(ctypes.c_void_p)]
         L.jd_server_submit.argtypes = [vp, P(ProblemDesc), P(OptParams), P(ctypes.c_uint64)]
@@ -388,6 +389,23 @@ class JdProblem:
             gp = _ptr(g)
         _check(lib().jd_fb_gradient(self.h, ctypes.byref(F), mp, ms, ctypes.byref(J), gp), "jd_fb_gradient")
         return J.value, g
+
+    def fb_optimize(self, fb, mu0=None, max_iter=20, tol_rel_grad=1e-4, tol_step=0.0, armijo_c=1e-4,
+                    zeta0=1.0, zeta_max=1e3, max_backtracks=40):
+        """Armijo descent on the feedback weights: (mu (Nt, L) numpy, result dict, J history)."""
+        L = fb.nx * fb.nv
+        mu = np.zeros((self.Nt, L)) if mu0 is None else _f64(mu0).reshape(self.Nt, L).copy()
+        o = OptParams(max_iter=max_iter, tol_rel_grad=tol_rel_grad, tol_step=tol_step, armijo_c=armijo_c,
+                      zeta0=zeta0, zeta_max=zeta_max, max_backtracks=max_backtracks)
+        r = OptResult()
+        hist = np.full(max_iter + 1, np.nan)
+        F = make_feedback(fb)
+        st = lib().jd_fb_optimize(self.h, ctypes.byref(F), _ptr(mu), JD_MEM_HOST, ctypes.byref(o), ctypes.byref(r),
+                                  _ptr(hist))
+        if st not in (JD_OK, JD_ERR_LINESEARCH):
+            _check(st, "jd_fb_optimize")
+        res = dict(iters=r.iters, evals=r.evals, status=r.status, J=r.J, rel_grad_norm=r.rel_grad_norm, zeta=r.zeta)
+        return mu, res, hist[: r.iters + 1]
 
     def sample_paths(self, u, m0: int, count: int, lam: bool = True):
         """(X (count, Nt+1, d), lam (count, Nt+1, d) or None, cost (count))."""

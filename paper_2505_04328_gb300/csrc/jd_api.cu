@@ -928,6 +928,7 @@ jd_status jd_problem_destroy(jd_problem *p) {
   free_dev(p, p->fb_partC);
   free_dev(p, p->fb_partG);
   free_dev(p, p->fb_partW);
+  free_dev(p, p->fb_mut);
   if (p->host_pinned && p->own_pinned) cudaFreeHost(p->host_pinned);
   if (p->own_stream && p->stream) cudaStreamDestroy(p->stream);
   delete p;
@@ -1451,6 +1452,83 @@ jd_status jd_fb_gradient(jd_problem *p, const jd_feedback_desc *fb, const double
   if (s) return s;
   if (J) *J = p->host_pinned[S_J];
   return std::isfinite(p->host_pinned[S_J]) ? JD_OK : fail(JD_ERR_NONFINITE, "J is not finite");
+}
+
+jd_status jd_fb_optimize(jd_problem *p, const jd_feedback_desc *fb, double *mu_inout, jd_memspace space,
+                         const jd_opt_params *o, jd_opt_result *r, double *J_hist) {
+  if (!mu_inout || !o || !r) return fail(JD_ERR_INVALID_ARG, "mu_inout, o and r must be non-NULL");
+  if (space != JD_MEM_HOST && space != JD_MEM_DEVICE) return fail(JD_ERR_INVALID_ARG, "bad memory space");
+  std::memset(r, 0, sizeof(*r));
+  jd_status s = fb_validate(p, fb);
+  if (s) return s;
+  const int64_t n = (int64_t)p->desc.Nt * fb->nx * fb->nv;
+  const double dt = p->desc.T / p->desc.Nt;
+  s = set_device(p);
+  if (!s && !p->fb_mu64)
+    s = dev_alloc(p, (void **)&p->fb_mu64, (size_t)p->desc.Nt * FB_NB * FB_NB * 8, "feedback weights (FP64)");
+  if (!s && !p->fb_mut)
+    s = dev_alloc(p, (void **)&p->fb_mut, (size_t)p->desc.Nt * FB_NB * FB_NB * 8, "feedback trial weights");
+  if (!s && !p->fb_grad)
+    s = dev_alloc(p, (void **)&p->fb_grad, (size_t)p->desc.Nt * FB_NB * FB_NB * 8, "feedback gradient");
+  if (s) return s;
+  if (space == JD_MEM_HOST && !finite_all(mu_inout, (size_t)n)) return fail(JD_ERR_INVALID_ARG, "mu has a non-finite entry");
+  JD_CUDA(cudaMemcpyAsync(p->fb_mu64, mu_inout, n * 8,
+                          space == JD_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, p->stream));
+  // Algorithm 5.4 on mu: gradient at mu^n, Armijo backtracking along -g (g = grad / dt),
+  // update; the host takes each decision from the FP64 scalars read back
+  double J = 0.0, pg0 = -1.0, zeta = o->zeta0 > 0 ? o->zeta0 : 1.0;
+  const double zeta_max = o->zeta_max > 0 ? o->zeta_max : 1e3;
+  int status = 0, it = 0;
+  for (it = 0; it < o->max_iter; ++it) {
+    s = fb_run(p, fb, p->fb_mu64, JD_MEM_DEVICE, p->fb_grad);
+    if (!s) JD_CUDA(fb_norm(p->fb_grad, n, dt, p->scal_d + S_PG, p->stream));
+    if (!s) s = read_scalars(p, S_J, S_PG + 1);
+    if (s) return s;
+    r->evals++;
+    J = p->host_pinned[S_J];
+    const double g2 = p->host_pinned[S_PG];
+    if (!std::isfinite(J) || !std::isfinite(g2)) return fail(JD_ERR_NONFINITE, "J or the gradient is not finite");
+    if (J_hist) J_hist[it] = J;
+    const double pg = std::sqrt(g2);
+    if (pg0 < 0.0) pg0 = pg;
+    r->rel_grad_norm = pg0 > 0.0 ? pg / pg0 : 0.0;
+    if (r->rel_grad_norm <= o->tol_rel_grad) break;
+    if (it > 0) zeta = std::fmin(2.0 * zeta, zeta_max);
+    bool accepted = false;
+    double Jt = 0.0;
+    for (int b = 0; b <= o->max_backtracks; ++b) {
+      JD_CUDA(fb_trial(p->fb_mu64, p->fb_grad, n, zeta, dt, p->fb_mut, p->stream));
+      s = fb_run(p, fb, p->fb_mut, JD_MEM_DEVICE, nullptr);
+      if (!s) s = read_scalars(p, S_J, 1);
+      if (s) return s;
+      r->evals++;
+      Jt = p->host_pinned[S_J];
+      if (Jt <= J - o->armijo_c * zeta * g2) {
+        accepted = true;
+        break;
+      }
+      zeta *= 0.5;
+    }
+    if (!accepted) {
+      status = JD_ERR_LINESEARCH;
+      break;
+    }
+    std::swap(p->fb_mu64, p->fb_mut);   // mu^{n+1}
+    J = Jt;
+    if (J_hist) J_hist[it + 1] = J;
+    if (zeta * pg < o->tol_step) {   // |mu^{n+1} - mu^n|_{L2} = zeta |g|_{L2}
+      it++;
+      break;
+    }
+  }
+  r->iters = it;
+  r->J = J;
+  r->zeta = zeta;
+  r->status = (jd_status)status;
+  JD_CUDA(cudaMemcpyAsync(mu_inout, p->fb_mu64, n * 8,
+                          space == JD_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, p->stream));
+  JD_CUDA(cudaStreamSynchronize(p->stream));
+  return status == 0 ? JD_OK : fail((jd_status)status, "line search failed");
 }
 
 jd_status jd_optimize(jd_problem *p, double *u_inout, jd_memspace us, const jd_opt_params *o,

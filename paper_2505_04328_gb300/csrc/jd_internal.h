@@ -105,6 +105,10 @@ struct FbOps {
 const FbOps *fb_ops(int prec, int nx, int nv);   // the smallest compiled NX x NV that fits
 cudaError_t fb_finalize(const double *partC, const double *partG, int64_t nblk, int64_t ngroup, int Nt, int nx,
                         int nv, int NX, int NV, int64_t M, double *J, double *grad, cudaStream_t s);
+// Armijo descent on the weights: |g|^2_{L2} into *out; trial point mu - zeta grad / dt.
+cudaError_t fb_norm(const double *grad, int64_t n, double dt, double *out, cudaStream_t s);
+cudaError_t fb_trial(const double *mu, const double *grad, int64_t n, double zeta, double dt, double *mt,
+                     cudaStream_t s);
 int compiled_dim(int d);         // smallest compiled D >= d, or 0
 
 void count_launch(int n = 1);
@@ -156,6 +160,7 @@ struct jd_problem {
   uint32_t *fb_flags = nullptr;
   double *fb_mu64 = nullptr, *fb_grad = nullptr, *fb_partC = nullptr, *fb_partG = nullptr;
   void *fb_partW = nullptr;
+  double *fb_mut = nullptr;  // optimizer: trial weights (FP64)
   int fb_LP = 0;             // padded weights per step of fb_mu / fb_partW / fb_partG
   size_t fb_stack = 0;       // stack limit already ensured for the feedback kernels
 };

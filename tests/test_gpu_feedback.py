@@ -134,3 +134,21 @@ def test_full_size_directional_derivative():
         J32, g32 = jp.fb_gradient(fb, mu)
     print(f"fp32 vs fp64: J {abs(J32 - J) / abs(J):.2e} grad {rel_l2(g32, g):.2e}")
     assert abs(J32 - J) <= 1e-6 * abs(J) and rel_l2(g32, g) <= 1e-5
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_optimizer_follows_the_oracle(prec):
+    """Algorithm 5.4 on mu: the GPU descent takes the oracle's iterate sequence (the same
+    accept/reject decisions); FP64 J history within 1e-10 relative and the final weights
+    within 1e-9 of their scale, FP32 within the FP32 bars (1e-6 for J, 1e-5 for mu)."""
+    p, fb = workloads.feedback_centering(M=700, Nt=20)
+    p = p.replace(lam=6.0)
+    muo, ro, ho = oracle.fb_optimize(p, fb, max_iter=6)
+    with JdProblem(p, prec=prec) as jp:
+        mu, r, h = jp.fb_optimize(fb, max_iter=6)
+    print(prec, r, ro)
+    assert r["status"] == 0 and r["iters"] == ro["iters"] and r["evals"] == ro["evals"]
+    tJ, tm = (1e-10, 1e-9) if prec == "fp64" else (1e-6, 1e-5)
+    assert np.max(np.abs(h - ho) / np.abs(ho)) <= tJ
+    assert np.max(np.abs(mu - muo)) <= tm * np.max(np.abs(muo))
+    assert np.all(np.diff(h) < 0)

@@ -13,7 +13,9 @@ Sec. 5.5, Sec. 6 eq:tracking_cost), each against something other than the oracle
   control cost (alpha/2) dt sum_k u_k^2 in closed form;
 * the adjoint and the gradient in mu: central differences in random directions of mu,
   in single entries, and in the initial state (lambda_0), with noise and Keilson-Storer
-  resets, for both tracking costs; the per-path sensitivities average to the gradient.
+  resets, for both tracking costs; the per-path sensitivities average to the gradient;
+* the optimizer (Algorithm 5.4 on mu): monotone Armijo decrease, and on a frozen state
+  convergence to the closed-form infimum T l(z0) (the control cost goes to 0).
 """
 import numpy as np
 import pytest
@@ -174,3 +176,26 @@ def test_path_sensitivities_average_to_the_gradient():
     # the thread count does not change the bits
     J1, g1 = oracle.fb_gradient(p, fb, mu, nthreads=1)
     assert J1 == J and np.array_equal(g1, g)
+
+
+def test_optimizer_decreases_and_satisfies_armijo():
+    p, fb = workloads.feedback_centering(M=300, Nt=15)
+    mu, r, hist = oracle.fb_optimize(p, fb, max_iter=8)
+    assert r["status"] == 0 and r["iters"] == 8
+    assert np.all(np.diff(hist) < 0), hist
+    # the final iterate's cost is the oracle's cost at the returned weights
+    assert oracle.fb_cost(p, fb, mu) == pytest.approx(r["J"], rel=0, abs=0)
+
+
+def test_optimizer_reaches_the_closed_form_minimum():
+    """B = 0, A = 0, no noise, no jumps: the state stays at z0 and only the control cost
+    (alpha/2) dt sum_k (mu_k . phi(z0))^2 depends on mu; its infimum is 0, so J converges
+    to the constant tracking part N_t dt l(z0) = T l(z0)."""
+    p, fb = workloads.feedback_centering(M=4, Nt=10)
+    p = p.replace(A=np.zeros((2, 2)), B=np.zeros((2, 1)), sigma=np.zeros(2), lam=0.0, x0=np.array([0.3, -0.2]))
+    fb = fb.replace(eps=0.3)
+    mu0 = workloads.random_mu(p, fb, seed=2, scale=5.0)
+    track = -np.exp(-(0.3 ** 2 + 0.2 ** 2) / (2 * fb.sigma_J ** 2))
+    mu, r, hist = oracle.fb_optimize(p, fb, mu0, max_iter=60, tol_rel_grad=1e-12)
+    assert hist[0] > p.T * track + 1e-3
+    assert r["J"] == pytest.approx(p.T * track, abs=1e-10)
