@@ -63,12 +63,13 @@ class _Problem(ctypes.Structure):
 class _Feedback(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("nv", ctypes.c_int), ("x_max", ctypes.c_double),
                 ("v_max", ctypes.c_double), ("eps", ctypes.c_double), ("track", ctypes.c_int),
-                ("sigma_J", ctypes.c_double)]
+                ("sigma_J", ctypes.c_double), ("adjoint", ctypes.c_int), ("sur_rate", ctypes.c_double)]
 
 
 def _fb(f) -> _Feedback:
     return _Feedback(nx=int(f.nx), nv=int(f.nv), x_max=float(f.x_max), v_max=float(f.v_max),
-                     eps=float(f.eps), track=int(f.track), sigma_J=float(f.sigma_J))
+                     eps=float(f.eps), track=int(f.track), sigma_J=float(f.sigma_J),
+                     adjoint=int(getattr(f, "adjoint", 0)), sur_rate=float(getattr(f, "sur_rate", 0.0)))
 
 
 class _Draws(ctypes.Structure):
@@ -122,6 +123,8 @@ def lib():
             L.orc_fb_path.argtypes = [P(_Problem), P(_Feedback), ctypes.c_void_p, ctypes.c_int64] + [ctypes.c_void_p] * 5
             L.orc_fb_cost.argtypes = [P(_Problem), P(_Feedback), ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
             L.orc_fb_gradient.argtypes = [P(_Problem), P(_Feedback), ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 2
+            L.orc_fb_surrogate_state.argtypes = [P(_Problem), P(_Feedback), ctypes.c_int, ctypes.c_int64,
+                                                 ctypes.c_void_p]
             L.orc_fb_optimize.argtypes = [P(_Problem), P(_Feedback), ctypes.c_void_p, P(_OptParams), ctypes.c_int,
                                           P(_OptResult), ctypes.c_void_p]
             _lib = L
@@ -347,3 +350,12 @@ def fb_optimize(p, fb, mu0=None, max_iter=20, tol_rel_grad=1e-4, tol_step=0.0, a
     res = dict(iters=r.iters, evals=r.evals, status=r.status, J=r.J,
                rel_grad_norm=r.rel_grad_norm, zeta=r.zeta)
     return mu, res, hist[: r.iters + 1]
+
+
+def fb_surrogate_state(p, fb, k: int, m: int):
+    """The surrogate state z_d(t_k) + sqrt(rate t_k) xi of step k, path m (Sec. 6.5)."""
+    op = OracleProblem(p)
+    F = _fb(fb)
+    z = np.zeros(2)
+    lib().orc_fb_surrogate_state(ctypes.byref(op.s), ctypes.byref(F), int(k), int(m), _ptr(z))
+    return z

@@ -594,7 +594,19 @@ static double fb_track(const orc_problem *P, const orc_feedback *F, const double
 static int fb_valid(const orc_problem *P, const orc_feedback *F) {
   return valid(P) && F && P->d == 2 && P->du == 1 && F->nx >= 1 && F->nx <= ORC_FBMAX &&
          F->nv >= 1 && F->nv <= ORC_FBMAX && F->x_max > 0.0 && F->v_max > 0.0 && F->eps > 0.0 &&
-         (F->track == ORC_TRACK_QUAD || (F->track == ORC_TRACK_GAUSS && F->sigma_J > 0.0));
+         (F->track == ORC_TRACK_QUAD || (F->track == ORC_TRACK_GAUSS && F->sigma_J > 0.0)) &&
+         (F->adjoint == ORC_FB_EXACT || (F->adjoint == ORC_FB_SURROGATE && F->sur_rate >= 0.0));
+}
+
+/* Surrogate state of step k (Sec. 6.5): z_d(t_k) plus a normal pair scaled by the
+ * standard deviation sqrt(rate t_k) of a variance that grows linearly in time. */
+void orc_fb_surrogate_state(const orc_problem *P, const orc_feedback *F, int k, int64_t m, double zs[2]) {
+  uint32_t w[2];
+  double xi[2];
+  stream_words(P, k, m, 2u, 0u, 2, w);
+  normal_pair(w[0], w[1], &xi[0], &xi[1]);
+  const double sd = sqrt(F->sur_rate * (P->T / (double)P->Nt) * (double)k);
+  for (int c = 0; c < 2; ++c) zs[c] = P->xd[k * 2 + c] + sd * xi[c];
 }
 
 /* Sub-steps of step k under feedback (Algorithm 5.1, the control evaluated at the
@@ -627,6 +639,60 @@ int orc_fb_path(const orc_problem *P, const orc_feedback *F, const double *mu, i
   double (*Y)[ORC_DMAX] = (double (*)[ORC_DMAX])malloc(sizeof(double) * ORC_DMAX * (ORC_NMAX + 2));
   double *phi = (double *)malloc(sizeof(double) * L);
   if (!Xs || !D || !Y || !phi) return 2;
+
+  if (F->adjoint == ORC_FB_SURROGATE && (G || lam)) {
+    /* Sec. 6.5: the costates run backwards along the surrogate states zs_k, never the
+     * forward's; per step one Euler step of the adjoint at zs_k, the jumps of the path's
+     * own step k entering through the Jacobian of the jump map (gamma^n on the reset
+     * velocities).  bhat_k = B^T r after the jumps of step k then drives the gradient of
+     * the forward sweep: dcost/dmu_k += delta_i phi(Y_i) (alpha u(Y_i) + bhat_k). */
+    double *bhat = (double *)malloc(sizeof(double) * Nt);
+    double r[2], zs[2], jt[ORC_DMAX], gr[ORC_DMAX], du[2];
+    orc_fb_surrogate_state(P, F, Nt, m, zs);
+    fb_track(P, F, zs, Nt, gr);
+    for (int c = 0; c < 2; ++c) r[c] = dt * gr[c];
+    if (lam) memcpy(lam + (size_t)Nt * 2, r, sizeof(r));
+    for (int k = Nt - 1; k >= 0; --k) {
+      orc_step_draws(P, k, m, D);
+      for (int i = 0; i < D->n; ++i)
+        for (int c = 0; c < 2; ++c) r[c] *= jump_gain_of(P, c);
+      bhat[k] = P->B[0] * r[0] + P->B[1] * r[1];
+      orc_fb_surrogate_state(P, F, k, m, zs);
+      double u = orc_fb_control(F, mu + (size_t)k * L, zs, du, NULL);
+      double w = P->nu * u + bhat[k];
+      drift_jacobian_T(P, zs, r, jt);
+      for (int c = 0; c < 2; ++c) r[c] = r[c] + dt * (jt[c] + w * du[c]);
+      if (k >= 1) {
+        fb_track(P, F, zs, k, gr);
+        for (int c = 0; c < 2; ++c) r[c] += dt * gr[c];
+      }
+      if (lam) memcpy(lam + (size_t)k * 2, r, sizeof(r));
+    }
+    memcpy(Xs, P->x0, sizeof(double) * 2);
+    double c_m = 0.0;
+    for (int k = 0; k < Nt; ++k) {
+      orc_step_draws(P, k, m, D);
+      if (njumps) njumps[k] = D->n;
+      c_m += integrate_step_fb(P, F, D, Xs + (size_t)k * 2, mu + (size_t)k * L, Y);
+      if (G) {
+        memset(G + (size_t)k * L, 0, sizeof(double) * L);
+        for (int i = 0; i <= D->n; ++i) {
+          double u = orc_fb_control(F, mu + (size_t)k * L, Y[i], NULL, phi);
+          double w = P->nu * u + bhat[k];
+          for (int l = 0; l < L; ++l) G[(size_t)k * L + l] += D->delta[i] * phi[l] * w;
+        }
+      }
+      memcpy(Xs + (size_t)(k + 1) * 2, Y[D->n + 1], sizeof(double) * 2);
+      c_m += dt * fb_track(P, F, Xs + (size_t)(k + 1) * 2, k + 1, NULL);
+    }
+    if (cost) *cost = c_m;
+    free(bhat);
+    if (!X) free(Xs);
+    free(D);
+    free(Y);
+    free(phi);
+    return 0;
+  }
 
   /* forward sweep; the cost is sum_k [dt l(X_{k+1}) + sum_i (alpha/2) delta_i u(Y_i)^2] */
   memcpy(Xs, P->x0, sizeof(double) * 2);

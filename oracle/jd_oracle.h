@@ -147,6 +147,7 @@ int orc_optimize(const orc_problem *P, double *u, const orc_opt_params *o, int n
 /* ------------------------------------------------------------------------- */
 #define ORC_FBMAX 16     /* centres per axis */
 enum { ORC_TRACK_QUAD = 0, ORC_TRACK_GAUSS = 1 };
+enum { ORC_FB_EXACT = 0, ORC_FB_SURROGATE = 1 };
 
 typedef struct {
   int nx, nv;             /* centres per axis */
@@ -154,6 +155,9 @@ typedef struct {
   double eps;             /* bump shape parameter eps_phi */
   int track;              /* ORC_TRACK_QUAD or ORC_TRACK_GAUSS */
   double sigma_J;         /* Gaussian tracking width */
+  int adjoint;            /* ORC_FB_EXACT, or ORC_FB_SURROGATE (Sec. 6.5): the costates run
+                             along states drawn from N(z_d(t_k), rate t_k I) */
+  double sur_rate;        /* surrogate variance growth per unit time */
 } orc_feedback;
 
 /* The bump phi(x, x_c, eps) of r = x - x_c, and its derivative in x. */
@@ -164,7 +168,11 @@ double orc_bump_dr(double r, double eps);
 double orc_fb_control(const orc_feedback *F, const double *mu_k, const double *z, double *du,
                       double *phi);
 /* One path under feedback: X (Nt+1)*2, lam (Nt+1)*2, G (Nt*L per-path dcost/dmu), cost,
- * njumps (each nullable).  Returns 0 on success. */
+ * njumps (each nullable).  Returns 0 on success.  With F->adjoint == ORC_FB_SURROGATE, G
+ * is the surrogate estimate of Sec. 6.5 and lam holds the surrogate costates; the
+ * surrogate state of step k is zs_k = z_d(t_k) + sqrt(rate t_k) (xi_0, xi_1), xi the
+ * Box-Muller pair of Philox words 0, 1 of counter (k, m, 2 << 24, epoch). */
+void orc_fb_surrogate_state(const orc_problem *P, const orc_feedback *F, int k, int64_t m, double zs[2]);
 int orc_fb_path(const orc_problem *P, const orc_feedback *F, const double *mu, int64_t m,
                 double *X, double *lam, double *G, double *cost, int *njumps);
 /* J(mu) and dJ/dmu (Nt*L, nullable), fixed summation order. */

@@ -199,3 +199,75 @@ def test_optimizer_reaches_the_closed_form_minimum():
     mu, r, hist = oracle.fb_optimize(p, fb, mu0, max_iter=60, tol_rel_grad=1e-12)
     assert hist[0] > p.T * track + 1e-3
     assert r["J"] == pytest.approx(p.T * track, abs=1e-10)
+
+
+# --- Sec. 6.5: costates along surrogate states -------------------------------------------
+def test_surrogate_equals_exact_on_the_forward_trajectory():
+    """No noise, no jumps, zero surrogate variance and a target equal to the forward
+    trajectory itself (the forward does not depend on the target): the surrogate states
+    are the forward states, so the surrogate costates and gradient equal the exact ones
+    (the tracking gradients vanish on the target; the drift Jacobian, the feedback terms
+    w grad u and the pairing with the forward's phi(Y) remain)."""
+    p, fb = workloads.feedback_centering(M=3, Nt=30)
+    p = p.replace(sigma=np.zeros(2), lam=0.0)
+    mu = workloads.random_mu(p, fb, seed=8, scale=0.7)
+    X = oracle.fb_path(p, fb, mu, 0, adjoint=False)["X"]
+    for track in (workloads.TRACK_QUAD, workloads.TRACK_GAUSS):
+        q, f = p.replace(xd=X), fb.replace(track=track)
+        ex = oracle.fb_path(q, f, mu, 0)
+        sur = oracle.fb_path(q, f.replace(adjoint=workloads.FB_SURROGATE, sur_rate=0.0), mu, 0)
+        assert np.abs(ex["G"]).max() > 1e-6
+        assert np.allclose(sur["G"], ex["G"], rtol=1e-13, atol=1e-18)
+        assert np.allclose(sur["lam"], ex["lam"], rtol=1e-13, atol=1e-18)
+
+
+def test_surrogate_state_law():
+    """z_d(t_k) + sqrt(rate t_k) xi: mean z_d(t_k), variance rate t_k per component."""
+    p, fb = workloads.feedback_trajectory(M=4000, Nt=10)
+    fb = fb.replace(adjoint=workloads.FB_SURROGATE, sur_rate=0.3)
+    for k in (0, 4, 10):
+        Z = np.array([oracle.fb_surrogate_state(p, fb, k, m) for m in range(p.M)])
+        var = 0.3 * k * p.T / p.Nt
+        if k == 0:
+            assert np.all(Z == p.xd[0])
+            continue
+        se = np.sqrt(var / p.M)
+        assert np.all(np.abs(Z.mean(axis=0) - p.xd[k]) < 4 * se)
+        assert np.all(np.abs(Z.var(axis=0) - var) < 4 * var * np.sqrt(2.0 / p.M))
+        assert abs(np.corrcoef(Z.T)[0, 1]) < 4 / np.sqrt(p.M)
+
+
+def test_surrogate_costates_do_not_see_the_forward():
+    """The surrogate costates depend on the weights, the target and the path's jumps, not
+    on the forward states: moving x0 changes the forward (and the gradient) but not them."""
+    p, fb = workloads.feedback_centering(M=2, Nt=25)
+    p = p.replace(lam=10.0)
+    fb = fb.replace(adjoint=workloads.FB_SURROGATE, sur_rate=0.2)
+    mu = workloads.random_mu(p, fb, seed=9, scale=0.6)
+    a = oracle.fb_path(p, fb, mu, 1)
+    b = oracle.fb_path(p.replace(x0=p.x0 + 0.3), fb, mu, 1)
+    assert np.array_equal(a["lam"], b["lam"])
+    assert not np.allclose(a["G"], b["G"])
+
+
+def test_surrogate_costates_cross_jumps_with_the_reset_gain():
+    """mu = 0 and A = 0: the surrogate costate recursion reduces to
+    r_k = diag(1, gamma^{n_k}) r_{k+1} + dt q (zs_k - z_d(t_k)) (k >= 1), n_k the path's jump
+    count in step k, r_Nt = dt q (zs_Nt - z_d(t_Nt)); written out here with the oracle's
+    surrogate states and jump counts."""
+    p, fb = workloads.feedback_centering(M=2, Nt=40)
+    p = p.replace(A=np.zeros((2, 2)), lam=9.0, jump_gain=0.6, q=np.array([0.7, 1.3]))
+    fb = fb.replace(track=workloads.TRACK_QUAD, adjoint=workloads.FB_SURROGATE, sur_rate=0.4)
+    dt = p.T / p.Nt
+    lam = oracle.fb_path(p, fb, np.zeros((p.Nt, fb.L)), 1)["lam"]
+    r = dt * p.q * (oracle.fb_surrogate_state(p, fb, p.Nt, 1) - p.xd[p.Nt])
+    assert np.allclose(lam[p.Nt], r, rtol=1e-14)
+    jumps = 0
+    for k in range(p.Nt - 1, -1, -1):
+        n = oracle.step_draws(p, k, 1)["n"]
+        jumps += n
+        r = r * np.array([1.0, p.jump_gain ** n])
+        if k >= 1:
+            r = r + dt * p.q * (oracle.fb_surrogate_state(p, fb, k, 1) - p.xd[k])
+        assert np.allclose(lam[k], r, rtol=1e-12, atol=1e-15), k
+    assert jumps > 3

@@ -221,6 +221,7 @@ def serving_requests(n: int = 10000, rate: float = 200.0, seed: int = 5):
 
 # --- feedback control (Sec. 2 eq:control_structure, Sec. 5.1-5.2, Sec. 6) --------------
 TRACK_QUAD, TRACK_GAUSS = 0, 1
+FB_EXACT, FB_SURROGATE = 0, 1
 
 
 @dataclasses.dataclass
@@ -235,6 +236,8 @@ class Feedback:
     eps: float = 0.5
     track: int = TRACK_GAUSS
     sigma_J: float = 1.0
+    adjoint: int = 0          # FB_EXACT, or FB_SURROGATE (Sec. 6.5)
+    sur_rate: float = 0.0     # surrogate states N(z_d(t), sur_rate t I)
 
     @property
     def L(self) -> int:
