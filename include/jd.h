@@ -331,6 +331,7 @@ jd_status jd_cost_noalloc(const jd_problem_desc *desc, const double *u, double *
  * eq:adjoint_eq_approximation, u_x and u_v included).  Every jump law is accepted.
  * --------------------------------------------------------------------------- */
 typedef enum { JD_TRACK_QUADRATIC = 0, JD_TRACK_GAUSS = 1 } jd_track;
+typedef enum { JD_FB_EXACT = 0, JD_FB_SURROGATE = 1 } jd_fb_adjoint;
 
 typedef struct {
   int nx, nv;            /* centres per axis, 1..16; L = nx nv weights per step */
@@ -338,6 +339,16 @@ typedef struct {
   double eps;            /* bump shape parameter eps_phi, > 0 */
   jd_track track;        /* tracking term l */
   double sigma_J;        /* Gaussian width, > 0 for JD_TRACK_GAUSS */
+  jd_fb_adjoint adjoint; /* EXACT: the discrete adjoint along the forward's states.
+                            SURROGATE (Sec. 6.5): the costates run backwards along states
+                            drawn around the target, zs_k = xd(t_k) + sqrt(sur_rate t_k) xi
+                            (xi: Box-Muller pair of the Philox words 0, 1 of counter
+                            (k, m, 2 << 24, epoch)), one Euler adjoint step per uniform step
+                            with the Jacobian of the path's own jumps; the gradient records
+                            delta phi(Y) (alpha u(Y) + B^T r) are formed on the forward's
+                            sub-steps.  An approximation: no states are stored (one value per
+                            path and step instead of two) */
+  double sur_rate;       /* SURROGATE: variance growth per unit time, >= 0 */
 } jd_feedback_desc;
 
 /* J(mu).  mu: Nt * L doubles, row-major [k][i][l], in mu_space; J: host pointer.  The

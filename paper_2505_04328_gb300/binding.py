@@ -60,13 +60,14 @@ class ProblemDesc(ctypes.Structure):
 class FeedbackDesc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("nv", ctypes.c_int), ("x_max", ctypes.c_double),
                 ("v_max", ctypes.c_double), ("eps", ctypes.c_double), ("track", ctypes.c_int),
-                ("sigma_J", ctypes.c_double)]
+                ("sigma_J", ctypes.c_double), ("adjoint", ctypes.c_int), ("sur_rate", ctypes.c_double)]
 
 
 def make_feedback(fb) -> FeedbackDesc:
     """The jd_feedback_desc of a workloads.Feedback (duck-typed)."""
     return FeedbackDesc(nx=int(fb.nx), nv=int(fb.nv), x_max=float(fb.x_max), v_max=float(fb.v_max),
-                        eps=float(fb.eps), track=int(fb.track), sigma_J=float(fb.sigma_J))
+                        eps=float(fb.eps), track=int(fb.track), sigma_J=float(fb.sigma_J),
+                        adjoint=int(getattr(fb, "adjoint", 0)), sur_rate=float(getattr(fb, "sur_rate", 0.0)))
 
 
 class KernelStat(ctypes.Structure):

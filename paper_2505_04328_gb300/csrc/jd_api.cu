@@ -24,10 +24,11 @@ void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_r
 // Optional per-kernel-class timing: a CUDA event pair around every launch, on the
 // launching stream, summed on read.
 enum KernelClass { KC_FWD_COST, KC_FWD_STORE, KC_FWD_CKPT, KC_ADJ_STORED, KC_ADJ_RECOMPUTE,
-                   KC_FINALIZE, KC_PREP, KC_OPT, KC_FB_FWD, KC_FB_ADJ, KC_FB_RED, KC_FB_FIN, KC_COUNT };
+                   KC_FINALIZE, KC_PREP, KC_OPT, KC_FB_FWD, KC_FB_ADJ, KC_FB_SUR, KC_FB_RED, KC_FB_FIN,
+                   KC_COUNT };
 static const char *kKernelClassName[KC_COUNT] = {"fwd_cost", "fwd_store", "fwd_ckpt", "adj_stored",
                                                  "adj_recompute", "finalize", "prep_u", "opt_step",
-                                                 "fb_fwd", "fb_adj", "fb_reduce", "fb_finalize"};
+                                                 "fb_fwd", "fb_adj", "fb_sur", "fb_reduce", "fb_finalize"};
 struct ProfRec {
   int kind;
   cudaEvent_t a, b;
@@ -1334,6 +1335,10 @@ static jd_status fb_validate(const jd_problem *p, const jd_feedback_desc *fb) {
     return fail(JD_ERR_INVALID_ARG, "bad tracking term");
   if (fb->track == JD_TRACK_GAUSS && (!(fb->sigma_J > 0.0) || !std::isfinite(fb->sigma_J)))
     return fail(JD_ERR_INVALID_ARG, "sigma_J must be finite and > 0");
+  if (fb->adjoint != JD_FB_EXACT && fb->adjoint != JD_FB_SURROGATE)
+    return fail(JD_ERR_INVALID_ARG, "bad feedback adjoint");
+  if (fb->adjoint == JD_FB_SURROGATE && (!(fb->sur_rate >= 0.0) || !std::isfinite(fb->sur_rate)))
+    return fail(JD_ERR_INVALID_ARG, "sur_rate must be finite and >= 0");
   return JD_OK;
 }
 
@@ -1406,13 +1411,24 @@ static jd_status fb_run(jd_problem *p, const jd_feedback_desc *fb, const double 
   b.partC = p->fb_partC;
   b.partW = p->fb_partW;
   b.partG = p->fb_partG;
-  int pr = prof_begin(KC_FB_FWD, p->stream);
-  JD_CUDA(ops->fwd(p, *fb, grad_out != nullptr, b, p->stream));
-  prof_end(pr, p->stream);
-  if (grad_out) {
-    pr = prof_begin(KC_FB_ADJ, p->stream);
-    JD_CUDA(ops->adj(p, *fb, b, p->stream));
+  int pr = -1;
+  if (grad_out && fb->adjoint == JD_FB_SURROGATE) {
+    // Sec. 6.5: the surrogate adjoint (bhat into the state buffer), then the forward sweep
+    // with the gradient records
+    pr = prof_begin(KC_FB_SUR, p->stream);
+    JD_CUDA(ops->sur(p, *fb, b, p->stream));
     prof_end(pr, p->stream);
+  } else {
+    pr = prof_begin(KC_FB_FWD, p->stream);
+    JD_CUDA(ops->fwd(p, *fb, grad_out != nullptr, b, p->stream));
+    prof_end(pr, p->stream);
+  }
+  if (grad_out) {
+    if (fb->adjoint != JD_FB_SURROGATE) {
+      pr = prof_begin(KC_FB_ADJ, p->stream);
+      JD_CUDA(ops->adj(p, *fb, b, p->stream));
+      prof_end(pr, p->stream);
+    }
     pr = prof_begin(KC_FB_RED, p->stream);
     JD_CUDA(ops->reduce(p, b, p->stream));
     prof_end(pr, p->stream);

@@ -57,6 +57,7 @@ struct FbParams {
   R alpha, halpha;          // alpha, alpha / 2
   R q[2];                   // tracking weights
   R hinv_s2, inv_s2;        // Gaussian: 1 / (2 sigma_J^2), 1 / sigma_J^2
+  R srate_dt;               // surrogate adjoint (Sec. 6.5): variance of step k is srate_dt k
   int gauss, Nt;
   int64_t mloc;
 };
@@ -426,6 +427,57 @@ __device__ __forceinline__ void quad_dot32<double>(const double *pa, const doubl
   }
 }
 
+// 2 x 2 weight blocks per lane in the warp exchange.
+template <int NX, int NV>
+constexpr int fb_qpl() {
+  return ((NX / 2) * (NV / 2) + 31) / 32;
+}
+
+// One round of the warp exchange: each lane's record (ra = delta w phi_x, rb = phi_v) goes
+// into the warp's buffer (pair rows: values of rows c, c+1 interleaved per path), then
+// lane p adds the 32-path dot products of its 2 x 2 block of weights (i, i+1) x (l, l+1),
+// i/2 = p / (NV/2), l/2 = p % (NV/2), to sq.  Eight consecutive lanes read at most three
+// phi_x pair rows and distinct phi_v pair rows (4-bank offsets apart).
+template <typename R, int NX, int NV>
+__device__ __forceinline__ void fb_exchange_add(R *wa, R *wb, int lane, const R (&ra)[NX], const R (&rb)[NV],
+                                                R (&sq)[fb_qpl<NX, NV>()][4]) {
+  constexpr int NQ = (NX / 2) * (NV / 2), QPL = fb_qpl<NX, NV>();
+#pragma unroll
+  for (int c = 0; c < NX; ++c) wa[(c / 2) * FB_AROW + 2 * lane + (c & 1)] = ra[c];
+#pragma unroll
+  for (int c = 0; c < NV; ++c) wb[(c / 2) * FB_AROW + 2 * lane + (c & 1)] = rb[c];
+  __syncwarp();
+#pragma unroll
+  for (int t = 0; t < QPL; ++t) {
+    const int p = lane + 32 * t;
+    if (p < NQ) quad_dot32<R>(wa + (p / (NV / 2)) * FB_AROW, wb + (p % (NV / 2)) * FB_AROW, sq[t]);
+  }
+  __syncwarp();
+}
+
+// The warp's partial of one step: block (i/2, l/2) = (p / (NV/2), p % (NV/2)) holds
+// weights (i, l), (i+1, l), (i, l+1), (i+1, l+1), contiguous in the pair layout (one
+// 16-byte store in FP32).
+template <typename R, int NX, int NV>
+__device__ __forceinline__ void fb_store_partial(R *dst, int lane, const R (&sq)[fb_qpl<NX, NV>()][4]) {
+  constexpr int NQ = (NX / 2) * (NV / 2), QPL = fb_qpl<NX, NV>();
+#pragma unroll
+  for (int t = 0; t < QPL; ++t) {
+    const int p = lane + 32 * t;
+    if (p < NQ) {
+      R *o = dst + 2 * ((p / (NV / 2)) * NV + 2 * (p % (NV / 2)));
+      if constexpr (sizeof(R) == 4) {
+        *reinterpret_cast<float4 *>(o) = make_float4(sq[t][0], sq[t][1], sq[t][2], sq[t][3]);
+      } else {
+        o[0] = sq[t][0];
+        o[1] = sq[t][1];
+        o[2] = sq[t][2];
+        o[3] = sq[t][3];
+      }
+    }
+  }
+}
+
 // Shared memory of fb_adj_kernel: per warp NX/2 pair rows of phi_x factors and NV/2 of phi_v.
 template <typename R, int NX, int NV>
 constexpr size_t fb_adj_smem() {
@@ -438,7 +490,7 @@ fb_adj_kernel(const __grid_constant__ KParams<R, 2, 1> kp, const __grid_constant
               const R *__restrict__ mu, const R *__restrict__ xd, const R *__restrict__ traj,
               const uint32_t *__restrict__ flags, R *__restrict__ partW) {
   using M = Ar<R>;
-  constexpr int LP = NX * NV, NQ = (NX / 2) * (NV / 2), QPL = (NQ + 31) / 32;   // 2 x 2 blocks
+  constexpr int LP = NX * NV, QPL = fb_qpl<NX, NV>();   // 2 x 2 blocks per lane
   extern __shared__ __align__(16) unsigned char fb_smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   R *wa = reinterpret_cast<R *>(fb_smem) + warp * ((NX / 2) + (NV / 2)) * FB_AROW;
@@ -495,10 +547,7 @@ fb_adj_kernel(const __grid_constant__ KParams<R, 2, 1> kp, const __grid_constant
     }
     // sub-steps n..0 backwards, round r = sub-step n - r of every path (paths with fewer
     // sub-steps contribute zeros); each round's records (delta w phi_x, phi_v) are summed
-    // over the warp's 32 paths through the exchange buffer (pair rows: values of rows
-    // c, c+1 interleaved per path).  Lane p forms the 2 x 2 block of weights
-    // (i, i+1) x (l, l+1), i/2 = p / (NV/2), l/2 = p % (NV/2): eight consecutive lanes read
-    // at most three phi_x pair rows and distinct phi_v pair rows (4-bank offsets).
+    // over the warp's 32 paths through the exchange buffer
     R sq[QPL][4];
 #pragma unroll
     for (int t = 0; t < QPL; ++t) sq[t][0] = sq[t][1] = sq[t][2] = sq[t][3] = R(0);
@@ -533,17 +582,7 @@ fb_adj_kernel(const __grid_constant__ KParams<R, 2, 1> kp, const __grid_constant
 #pragma unroll
         for (int c = 0; c < NV; ++c) rb[c] = R(0);
       }
-#pragma unroll
-      for (int c = 0; c < NX; ++c) wa[(c / 2) * FB_AROW + 2 * lane + (c & 1)] = ra[c];
-#pragma unroll
-      for (int c = 0; c < NV; ++c) wb[(c / 2) * FB_AROW + 2 * lane + (c & 1)] = rb[c];
-      __syncwarp();
-#pragma unroll
-      for (int t = 0; t < QPL; ++t) {
-        const int p = lane + 32 * t;
-        if (p < NQ) quad_dot32<R>(wa + (p / (NV / 2)) * FB_AROW, wb + (p % (NV / 2)) * FB_AROW, sq[t]);
-      }
-      __syncwarp();
+      fb_exchange_add<R, NX, NV>(wa, wb, lane, ra, rb, sq);
     }
     if (active && k >= 1) {
       R g[2];
@@ -551,25 +590,148 @@ fb_adj_kernel(const __grid_constant__ KParams<R, 2, 1> kp, const __grid_constant
       a[0] = M::add(a[0], g[0]);
       a[1] = M::add(a[1], g[1]);
     }
-    // block (i/2, l/2) = (p / (NV/2), p % (NV/2)): weights (i, l), (i+1, l), (i, l+1),
-    // (i+1, l+1) are contiguous in the pair layout, one 16-byte store in FP32
-    R *dst = partW + ((size_t)wid * Nt + k) * LP;
-#pragma unroll
-    for (int t = 0; t < QPL; ++t) {
-      const int p = lane + 32 * t;
-      if (p < NQ) {
-        R *o = dst + 2 * ((p / (NV / 2)) * NV + 2 * (p % (NV / 2)));
-        if constexpr (sizeof(R) == 4) {
-          *reinterpret_cast<float4 *>(o) = make_float4(sq[t][0], sq[t][1], sq[t][2], sq[t][3]);
-        } else {
-          o[0] = sq[t][0];
-          o[1] = sq[t][1];
-          o[2] = sq[t][2];
-          o[3] = sq[t][3];
-        }
-      }
+    fb_store_partial<R, NX, NV>(partW + ((size_t)wid * Nt + k) * LP, lane, sq);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Surrogate-state adjoint (Sec. 6.5): the costates run backwards along states drawn
+// around the target, zs_k = z_d(t_k) + sqrt(rate t_k) xi (xi: the Box-Muller pair of
+// Philox words 0, 1 of counter (k, m, 2 << 24, epoch)), never along the forward's.  The
+// adjoint runs first and keeps bhat_k = B^T r (after the Jacobian of the path's own jumps
+// of step k) per path and step; the forward sweep then forms the gradient records
+// delta phi(Y) (alpha u(Y) + bhat_k) on its own sub-steps, so no state is stored.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void fb_surrogate_state(const KParams<R, 2, 1> &kp, const FbParams<R> &fp, int k,
+                                                   uint32_t m, const R *__restrict__ xd, R (&zs)[2]) {
+  using M = Ar<R>;
+  const uint4 o = philox10((uint32_t)k, m, 2u << 24, kp.epoch, kp.key0, kp.key1);
+  R x0, x1;
+  normal_pair<R>(o.x, o.y, x0, x1);
+  const R sd = M::sqrt(M::mul(fp.srate_dt, (R)k));
+  zs[0] = M::fma(sd, x0, __ldg(xd + (size_t)k * 2));
+  zs[1] = M::fma(sd, x1, __ldg(xd + (size_t)k * 2 + 1));
+}
+
+template <typename R, int NX, int NV>
+__global__ void __launch_bounds__(FB_TPB)
+fb_sur_adj_kernel(const __grid_constant__ KParams<R, 2, 1> kp, const __grid_constant__ FbParams<R> fp,
+                  const R *__restrict__ mu, const R *__restrict__ xd, R *__restrict__ bhat) {
+  using M = Ar<R>;
+  constexpr int LP = NX * NV;
+  const int64_t mloc = fp.mloc, m = (int64_t)blockIdx.x * FB_TPB + threadIdx.x;
+  if (m >= mloc) return;
+  const uint32_t mg = (uint32_t)(kp.m_begin + m);
+  const int Nt = fp.Nt;
+  R zs[2], a[2];
+  fb_surrogate_state(kp, fp, Nt, mg, xd, zs);
+  fb_track<R, true>(fp, kp.dt, zs, xd + (size_t)Nt * 2, a);
+#pragma unroll 1
+  for (int k = Nt - 1; k >= 0; --k) {
+    if (kp.jumps_on) {   // the Jacobian of the step's jumps (gamma per reset on v)
+      const uint32_t w0 = philox10((uint32_t)k, mg, 0u, kp.epoch, kp.key0, kp.key1).x;
+#pragma unroll 1
+      for (int i = 0; i < NMAX && (unsigned long long)w0 >= kp.thr[i]; ++i) jump_adjoint(kp, a);
+    }
+    const R b = M::fma(kp.B[1], a[1], M::mul(kp.B[0], a[0]));
+    bhat[(size_t)k * mloc + m] = b;
+    fb_surrogate_state(kp, fp, k, mg, xd, zs);
+    R px[NX], pv[NV], ux, uv;
+    const R u = fb_eval<R, NX, NV, true>(fp, mu + (size_t)k * LP, zs[0], zs[1], px, pv, ux, uv);
+    const R dw = M::mul(kp.dt, M::fma(fp.alpha, u, b));
+    adjoint_update(kp, zs, kp.dt, a);
+    a[0] = M::fma(dw, ux, a[0]);
+    a[1] = M::fma(dw, uv, a[1]);
+    if (k >= 1) {
+      R g[2];
+      fb_track<R, true>(fp, kp.dt, zs, xd + (size_t)k * 2, g);
+      a[0] = M::add(a[0], g[0]);
+      a[1] = M::add(a[1], g[1]);
     }
   }
+}
+
+// Forward sweep of the surrogate gradient: the path cost as fb_fwd_kernel, and per step
+// the records delta_i phi(Y_i) (alpha u(Y_i) + bhat_k) of every sub-step, summed over the
+// warp by the exchange into partW.  Sub-steps run in rounds across the warp (a path with
+// n jumps takes n + 1 rounds).
+template <typename R, int NX, int NV>
+__global__ void __launch_bounds__(FB_TPB)
+fb_fwd_sur_kernel(const __grid_constant__ KParams<R, 2, 1> kp, const __grid_constant__ FbParams<R> fp,
+                  const R *__restrict__ mu, const R *__restrict__ xd, const R *__restrict__ bhat,
+                  double *__restrict__ partC, R *__restrict__ partW) {
+  using M = Ar<R>;
+  constexpr int LP = NX * NV, QPL = fb_qpl<NX, NV>();
+  extern __shared__ __align__(16) unsigned char fb_smem[];
+  __shared__ Pair<R> red[FB_TPB / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  R *wa = reinterpret_cast<R *>(fb_smem) + warp * ((NX / 2) + (NV / 2)) * FB_AROW;
+  R *wb = wa + (NX / 2) * FB_AROW;
+  const int64_t mloc = fp.mloc, m = (int64_t)blockIdx.x * FB_TPB + threadIdx.x;
+  const int64_t wid = (int64_t)blockIdx.x * (FB_TPB / 32) + warp;
+  const bool active = m < mloc;
+  const uint32_t mg = (uint32_t)(kp.m_begin + m);
+  const int Nt = fp.Nt;
+  Kahan<R> cost;
+  R z[2] = {kp.x0[0], kp.x0[1]};
+#pragma unroll 1
+  for (int k = 0; k < Nt; ++k) {
+    const R *mk = mu + (size_t)k * LP;
+    R zs[2] = {R(0), R(0)};
+    int n = 0;
+    FbPlan<R> P;
+    R bk = R(0);
+    if (active) {
+      const uint32_t w0 = main_draws(kp, k, mg, zs);
+      if (has_jump(kp, w0)) n = fb_plan(kp, k, mg, w0, P);
+      bk = bhat[(size_t)k * mloc + m];
+    }
+    R sq[QPL][4];
+#pragma unroll
+    for (int t = 0; t < QPL; ++t) sq[t][0] = sq[t][1] = sq[t][2] = sq[t][3] = R(0);
+    const int rounds = (int)__reduce_max_sync(0xffffffffu, active ? (unsigned)(n + 1) : 0u);
+#pragma unroll 1
+    for (int r = 0; r < rounds; ++r) {
+      R ra[NX], rb[NV];
+      if (active && r <= n) {
+        R de = kp.dt, sqd = kp.sqdt;
+        if (n > 0) {
+          de = fb_delta(kp, P, n, r);
+          sqd = M::sqrt(de);
+        }
+        R ux, uv;
+        const R u = fb_eval<R, NX, NV, false>(fp, mk, z[0], z[1], ra, rb, ux, uv);
+        const R dw = M::mul(de, M::fma(fp.alpha, u, bk));
+#pragma unroll
+        for (int c = 0; c < NX; ++c) ra[c] = M::mul(dw, ra[c]);
+        cost.add(M::mul(M::mul(fp.halpha, de), M::mul(u, u)));
+        const R uu[1] = {u};
+        R f[2];
+        drift(kp, z, uu, f);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) z[c] = M::fma(M::mul(kp.sigma[c], sqd), zs[c], M::fma(de, f[c], z[c]));
+        if (r < n) {
+          R xih[2];
+          slot_draws(kp, k, mg, P.order[r], xih, zs);
+          apply_jump(kp, z, xih);
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < NX; ++c) ra[c] = R(0);
+#pragma unroll
+        for (int c = 0; c < NV; ++c) rb[c] = R(0);
+      }
+      fb_exchange_add<R, NX, NV>(wa, wb, lane, ra, rb, sq);
+    }
+    if (active) {
+      R g[2];
+      cost.add(fb_track<R, false>(fp, kp.dt, z, xd + (size_t)(k + 1) * 2, g));
+    }
+    fb_store_partial<R, NX, NV>(partW + ((size_t)wid * Nt + k) * LP, lane, sq);
+  }
+  const double bs = fb_block_sum(active ? cost.pair() : Pair<R>{R(0), R(0)}, red);
+  if (threadIdx.x == 0) partC[blockIdx.x] = bs;
 }
 
 // partG[g][c] = sum over warps w of group g (in order) of partW[w][c]; one thread per
@@ -659,6 +821,7 @@ void fb_make_params(const ::jd_problem *p, const jd_feedback_desc &fb, FbParams<
   fp.hinv_s2 = (R)(0.5 / s2);
   fp.inv_s2 = (R)(1.0 / s2);
   fp.gauss = fb.track == JD_TRACK_GAUSS;
+  fp.srate_dt = (R)(fb.adjoint == JD_FB_SURROGATE ? fb.sur_rate * (p->desc.T / p->desc.Nt) : 0.0);
   fp.Nt = p->desc.Nt;
   fp.mloc = p->desc.M;
 }
@@ -702,6 +865,29 @@ cudaError_t fb_adj_launch(const ::jd_problem *p, const jd_feedback_desc &fb, con
   return cudaGetLastError();
 }
 
+// Surrogate gradient (Sec. 6.5): the surrogate adjoint writes bhat, then the forward
+// sweep forms the cost and the warp partials of the gradient.
+template <typename R, int NX, int NV>
+cudaError_t fb_sur_launch(const ::jd_problem *p, const jd_feedback_desc &fb, const FbBufs &b, cudaStream_t s) {
+  KParams<R, 2, 1> kp;
+  make_kparams<R, 2, 1>(p, 0, p->desc.M, kp);
+  FbParams<R> fp;
+  fb_make_params<R>(p, fb, fp);
+  const unsigned grid = (unsigned)ceil_div(p->desc.M, FB_TPB);
+  const R *mu = static_cast<const R *>(b.mu), *xd = static_cast<const R *>(p->xdk);
+  fb_sur_adj_kernel<R, NX, NV><<<grid, FB_TPB, 0, s>>>(kp, fp, mu, xd, static_cast<R *>(b.traj));
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  constexpr size_t smem = fb_adj_smem<R, NX, NV>();
+  e = cudaFuncSetAttribute(fb_fwd_sur_kernel<R, NX, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  fb_fwd_sur_kernel<R, NX, NV><<<grid, FB_TPB, smem, s>>>(kp, fp, mu, xd, static_cast<const R *>(b.traj), b.partC,
+                                                          static_cast<R *>(b.partW));
+  count_launch();
+  return cudaGetLastError();
+}
+
 // First stage of the gradient reduction: warp partials -> FP64 group partials.
 template <typename R, int NX, int NV>
 cudaError_t fb_reduce_launch(const ::jd_problem *p, const FbBufs &b, cudaStream_t s) {
@@ -727,7 +913,8 @@ size_t fb_stack_bytes() {
   static const size_t bytes = [] {   // the kernels' attributes do not change: ask once
     size_t need = 0;
     const void *ks[] = {(const void *)fb_fwd_kernel<R, NX, NV, false>,
-                        (const void *)fb_fwd_kernel<R, NX, NV, true>, (const void *)fb_adj_kernel<R, NX, NV>};
+                        (const void *)fb_fwd_kernel<R, NX, NV, true>, (const void *)fb_adj_kernel<R, NX, NV>,
+                        (const void *)fb_sur_adj_kernel<R, NX, NV>, (const void *)fb_fwd_sur_kernel<R, NX, NV>};
     for (const void *k : ks) {
       cudaFuncAttributes a;
       if (cudaFuncGetAttributes(&a, k) == cudaSuccess) need = std::max(need, a.localSizeBytes);
@@ -741,7 +928,8 @@ size_t fb_stack_bytes() {
 template <typename R, int NX, int NV>
 constexpr FbOps fb_make_ops() {
   return FbOps{NX, NV, (int)sizeof(R), &fb_stack_bytes<R, NX, NV>, &fb_fwd_launch<R, NX, NV>,
-               &fb_adj_launch<R, NX, NV>, &fb_reduce_launch<R, NX, NV>, &fb_prep_dims<R, NX, NV>};
+               &fb_adj_launch<R, NX, NV>, &fb_sur_launch<R, NX, NV>, &fb_reduce_launch<R, NX, NV>,
+               &fb_prep_dims<R, NX, NV>};
 }
 
 }  // namespace jd

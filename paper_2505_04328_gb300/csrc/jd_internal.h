@@ -99,6 +99,10 @@ struct FbOps {
                      const FbBufs &b, cudaStream_t s);
   cudaError_t (*adj)(const struct ::jd_problem *p, const jd_feedback_desc &fb, const FbBufs &b,
                      cudaStream_t s);
+  // surrogate gradient (Sec. 6.5): surrogate adjoint into b.traj (bhat, [Nt][M]), then the
+  // forward sweep with the gradient records into partC / partW
+  cudaError_t (*sur)(const struct ::jd_problem *p, const jd_feedback_desc &fb, const FbBufs &b,
+                     cudaStream_t s);
   cudaError_t (*reduce)(const struct ::jd_problem *p, const FbBufs &b, cudaStream_t s);   // partW -> partG
   cudaError_t (*prep_mu)(const double *mu64, void *muR, int Nt, int nx, int nv, cudaStream_t s);
 };

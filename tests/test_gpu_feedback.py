@@ -152,3 +152,25 @@ def test_optimizer_follows_the_oracle(prec):
     assert np.max(np.abs(h - ho) / np.abs(ho)) <= tJ
     assert np.max(np.abs(mu - muo)) <= tm * np.max(np.abs(muo))
     assert np.all(np.diff(h) < 0)
+
+
+@pytest.mark.parametrize("case", ["centering", "trajectory", "small_quad"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_surrogate_gradient_parity(case, prec):
+    """Sec. 6.5 surrogate adjoint (costates along states drawn around the target) against
+    the oracle's: the same surrogate states (same Philox counter), the same jump counts,
+    the same pairing with the forward's sub-steps."""
+    p, fb = CASES[case]()
+    fb = fb.replace(adjoint=workloads.FB_SURROGATE, sur_rate=0.3)
+    mu = workloads.random_mu(p, fb, seed=26, scale=0.6)
+    Jo, go = oracle.fb_gradient(p, fb, mu)
+    with JdProblem(p, prec=prec) as jp:
+        J, g = jp.fb_gradient(fb, mu)
+        J2, g2 = jp.fb_gradient(fb, mu)
+    eJ, eg = abs(J - Jo) / abs(Jo), rel_l2(g, go)
+    print(f"surrogate {case} {prec}: J {eJ:.2e}  grad {eg:.2e}")
+    assert J == J2 and np.array_equal(g, g2)
+    if prec == "fp64":
+        assert eJ <= 1e-13 and eg <= 1e-12
+    else:
+        assert eJ <= 1e-6 and eg <= 1e-5
