@@ -132,7 +132,11 @@ WORKLOADS = {
     "ks_oscillator": workloads.ks_oscillator,
     # feedback control mu(t)^T phi(z), 10x10 bumps, Gaussian tracking, resets; M=2^20, Nt=100
     "feedback_centering": lambda: workloads.feedback_centering()[0],
+    # the same with eta = 0, eps = 0.1 and the piecewise-linear target of Sec. 6.3
+    "feedback_trajectory": lambda: workloads.feedback_trajectory()[0],
 }
+FB_WORKLOADS = {"feedback_centering": workloads.feedback_centering,
+                "feedback_trajectory": workloads.feedback_trajectory}
 
 
 def bench_workload(M=None, Nt=None, name="double_well"):
@@ -208,7 +212,7 @@ def run_ours(args):
     p = replica_problem(bench_workload(args.paths, args.steps_t, args.workload), rank)
     if args.workload == "double_well_autograd":
         return run_autograd(args, p, stream, dist, ws, rank, local)
-    if args.workload == "feedback_centering":
+    if args.workload in FB_WORKLOADS:
         return run_feedback(args, p, stream, dist, ws, rank, local)
     M, Nt, du = p.M, p.Nt, p.du
     prec = "fp64" if args.workload == "lq_scalar" else "fp32"
@@ -323,7 +327,9 @@ def run_feedback(args, p, stream, dist, ws, rank, local):
     from paper_2505_04328_gb300.binding import JD_MEM_DEVICE, _check, lib, make_feedback
     import ctypes
 
-    fb = workloads.feedback_centering()[1]
+    fb = FB_WORKLOADS[args.workload]()[1]
+    if args.fb_adjoint == "surrogate":
+        fb = fb.replace(adjoint=workloads.FB_SURROGATE, sur_rate=args.sur_rate)
     M, Nt, L = p.M, p.Nt, fb.L
     prob = jd.JdProblem(p, prec="fp32", stream=stream)
     mu = torch.tensor(workloads.random_mu(p, fb, seed=23, scale=0.5), dtype=torch.float64, device="cuda")
@@ -375,7 +381,8 @@ def run_feedback(args, p, stream, dist, ws, rank, local):
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     peak = 152 * 4 * 32 * sm_mhz * 1e6 / 1e9
     rl = {}
-    for name, ops in (("fb_fwd", fb_forward_ops(p, fb)), ("fb_adj", fb_adjoint_ops(p, fb))):
+    for name, ops in (("fb_fwd", fb_forward_ops(p, fb)), ("fb_adj", fb_adjoint_ops(p, fb)),
+                      ("fb_sur", fb_forward_ops(p, fb) + fb_adjoint_ops(p, fb))):
         if name in kstats:
             launches_k, total_ms = kstats[name]
             achieved = ops * M * Nt / (total_ms / launches_k * 1e-3) / 1e9
@@ -390,8 +397,10 @@ def run_feedback(args, p, stream, dist, ws, rank, local):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"feedback_centering d=2 M={M} Nt={Nt} L={fb.nx}x{fb.nv}",
-                       "variant": "stored", "paths_per_gpu": M, "Nt": Nt, "eps": fb.eps,
+            "config": {"workload": f"{args.workload} d=2 M={M} Nt={Nt} L={fb.nx}x{fb.nv}",
+                       "variant": "stored" if fb.adjoint == workloads.FB_EXACT else
+                                  f"surrogate adjoint (Sec. 6.5), rate {fb.sur_rate}",
+                       "paths_per_gpu": M, "Nt": Nt, "eps": fb.eps,
                        "step": "one feedback gradient dJ/dmu (forward sweep, adjoint sweep, reductions)",
                        "l2": "inputs larger than L2: the stored states (%.2f GB) and warp partials exceed "
                              "the 129 MB L2; no flush" % ((Nt + 1) * 2 * M * 4 / 1e9)},
@@ -715,6 +724,9 @@ def main():
     ap.add_argument("--steps-t", type=int, default=None, help="override N_t")
     ap.add_argument("--reference-paths", type=int, default=1 << 14)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fb-adjoint", default="exact", choices=["exact", "surrogate"],
+                    help="feedback workloads: exact adjoint or the surrogate-state adjoint of Sec. 6.5")
+    ap.add_argument("--sur-rate", type=float, default=0.05, help="surrogate variance growth per unit time")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
