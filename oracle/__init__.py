@@ -63,13 +63,17 @@ class _Problem(ctypes.Structure):
 class _Feedback(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("nv", ctypes.c_int), ("x_max", ctypes.c_double),
                 ("v_max", ctypes.c_double), ("eps", ctypes.c_double), ("track", ctypes.c_int),
-                ("sigma_J", ctypes.c_double), ("adjoint", ctypes.c_int), ("sur_rate", ctypes.c_double)]
+                ("sigma_J", ctypes.c_double), ("adjoint", ctypes.c_int), ("sur_rate", ctypes.c_double),
+                ("particles", ctypes.c_int), ("omega", ctypes.c_double), ("ax", ctypes.c_double),
+                ("av", ctypes.c_double)]
 
 
 def _fb(f) -> _Feedback:
     return _Feedback(nx=int(f.nx), nv=int(f.nv), x_max=float(f.x_max), v_max=float(f.v_max),
                      eps=float(f.eps), track=int(f.track), sigma_J=float(f.sigma_J),
-                     adjoint=int(getattr(f, "adjoint", 0)), sur_rate=float(getattr(f, "sur_rate", 0.0)))
+                     adjoint=int(getattr(f, "adjoint", 0)), sur_rate=float(getattr(f, "sur_rate", 0.0)),
+                     particles=int(getattr(f, "particles", 0)), omega=float(getattr(f, "omega", 0.0)),
+                     ax=float(getattr(f, "ax", 1.0)), av=float(getattr(f, "av", 1.0)))
 
 
 class _Draws(ctypes.Structure):
@@ -125,6 +129,9 @@ def lib():
             L.orc_fb_gradient.argtypes = [P(_Problem), P(_Feedback), ctypes.c_void_p, ctypes.c_int] + [ctypes.c_void_p] * 2
             L.orc_fb_surrogate_state.argtypes = [P(_Problem), P(_Feedback), ctypes.c_int, ctypes.c_int64,
                                                  ctypes.c_void_p]
+            L.orc_fb_coupled.argtypes = [P(_Problem), P(_Feedback), ctypes.c_void_p, ctypes.c_int64] + [ctypes.c_void_p] * 4
+            L.orc_fb_coupled_gradient.argtypes = [P(_Problem), P(_Feedback), ctypes.c_void_p, ctypes.c_int,
+                                                  ctypes.c_void_p, ctypes.c_void_p]
             L.orc_fb_optimize.argtypes = [P(_Problem), P(_Feedback), ctypes.c_void_p, P(_OptParams), ctypes.c_int,
                                           P(_OptResult), ctypes.c_void_p]
             _lib = L
@@ -359,3 +366,34 @@ def fb_surrogate_state(p, fb, k: int, m: int):
     z = np.zeros(2)
     lib().orc_fb_surrogate_state(ctypes.byref(op.s), ctypes.byref(F), int(k), int(m), _ptr(z))
     return z
+
+
+def fb_coupled(p, fb, mu=None, r: int = 0, adjoint: bool = True):
+    """Realization r of the coupled particles: dict(X (Nt+1,N,2), lam, G (Nt,L) summed over
+    the particles, cost summed over the particles)."""
+    op = OracleProblem(p)
+    F = _fb(fb)
+    mu = _mu(p, fb, mu)
+    N = fb.particles
+    X = np.zeros((p.Nt + 1, N, 2))
+    lam = np.zeros((p.Nt + 1, N, 2)) if adjoint else None
+    G = np.zeros((p.Nt, fb.nx * fb.nv)) if adjoint else None
+    cost = np.zeros(1)
+    rc = lib().orc_fb_coupled(ctypes.byref(op.s), ctypes.byref(F), _ptr(mu), int(r), _ptr(X), _ptr(lam),
+                              _ptr(G), _ptr(cost))
+    if rc:
+        raise ValueError(f"orc_fb_coupled failed ({rc})")
+    return dict(X=X, lam=lam, G=G, cost=float(cost[0]))
+
+
+def fb_coupled_gradient(p, fb, mu=None):
+    """(J, dJ/dmu (Nt, L)) over the M/32 realizations of the coupled particles."""
+    op = OracleProblem(p)
+    F = _fb(fb)
+    mu = _mu(p, fb, mu)
+    J = np.zeros(1)
+    g = np.zeros((p.Nt, fb.nx * fb.nv))
+    rc = lib().orc_fb_coupled_gradient(ctypes.byref(op.s), ctypes.byref(F), _ptr(mu), 1, _ptr(J), _ptr(g))
+    if rc:
+        raise ValueError(f"orc_fb_coupled_gradient failed ({rc})")
+    return float(J[0]), g

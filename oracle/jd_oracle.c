@@ -586,6 +586,17 @@ static double fb_track(const orc_problem *P, const orc_feedback *F, const double
       for (int c = 0; c < P->d; ++c) grad[c] = E * P->q[c] * e[c] / s2;
     return -E;
   }
+  if (F->track == ORC_TRACK_ELLIPSE) {
+    /* -exp(-(x^2/ax^2 + v^2/av^2 - 1)^2 / (2 sigma_J^2)) (Sec. 6.4 Eq. phonon_functional_tracking) */
+    double s2 = F->sigma_J * F->sigma_J;
+    double Ee = z[0] * z[0] / (F->ax * F->ax) + z[1] * z[1] / (F->av * F->av) - 1.0;
+    double E = exp(-Ee * Ee / (2.0 * s2));
+    if (grad) {
+      grad[0] = E * (Ee / s2) * (2.0 * z[0] / (F->ax * F->ax));
+      grad[1] = E * (Ee / s2) * (2.0 * z[1] / (F->av * F->av));
+    }
+    return -E;
+  }
   if (grad)
     for (int c = 0; c < P->d; ++c) grad[c] = P->q[c] * e[c];
   return 0.5 * Q;
@@ -594,7 +605,9 @@ static double fb_track(const orc_problem *P, const orc_feedback *F, const double
 static int fb_valid(const orc_problem *P, const orc_feedback *F) {
   return valid(P) && F && P->d == 2 && P->du == 1 && F->nx >= 1 && F->nx <= ORC_FBMAX &&
          F->nv >= 1 && F->nv <= ORC_FBMAX && F->x_max > 0.0 && F->v_max > 0.0 && F->eps > 0.0 &&
-         (F->track == ORC_TRACK_QUAD || (F->track == ORC_TRACK_GAUSS && F->sigma_J > 0.0)) &&
+         (F->track == ORC_TRACK_QUAD || ((F->track == ORC_TRACK_GAUSS || F->track == ORC_TRACK_ELLIPSE) &&
+                                          F->sigma_J > 0.0)) &&
+         (F->track != ORC_TRACK_ELLIPSE || (F->ax > 0.0 && F->av > 0.0)) &&
          (F->adjoint == ORC_FB_EXACT || (F->adjoint == ORC_FB_SURROGATE && F->sur_rate >= 0.0));
 }
 
@@ -612,13 +625,14 @@ void orc_fb_surrogate_state(const orc_problem *P, const orc_feedback *F, int k, 
 /* Sub-steps of step k under feedback (Algorithm 5.1, the control evaluated at the
  * left end of every sub-step); returns sum_i (alpha/2) delta_i u(Y_i)^2. */
 static double integrate_step_fb(const orc_problem *P, const orc_feedback *F, const orc_draws *D,
-                                const double *xk, const double *mu_k, double (*Y)[ORC_DMAX]) {
+                                const double *xk, const double *mu_k, double cin, double (*Y)[ORC_DMAX]) {
   double f[ORC_DMAX], ucost = 0.0;
   memcpy(Y[0], xk, sizeof(double) * 2);
   for (int i = 0; i <= D->n; ++i) {
     double u = orc_fb_control(F, mu_k, Y[i], NULL, NULL);
     ucost += 0.5 * P->nu * D->delta[i] * u * u;
     drift(P, Y[i], &u, f);
+    f[1] += cin;   /* coupled particles: the neighbours' force, fixed over the step */
     double sq = sqrt(D->delta[i]);
     for (int c = 0; c < 2; ++c) {
       Y[i + 1][c] = Y[i][c] + D->delta[i] * f[c] + P->sigma[c] * sq * D->Z[i][c];
@@ -673,7 +687,7 @@ int orc_fb_path(const orc_problem *P, const orc_feedback *F, const double *mu, i
     for (int k = 0; k < Nt; ++k) {
       orc_step_draws(P, k, m, D);
       if (njumps) njumps[k] = D->n;
-      c_m += integrate_step_fb(P, F, D, Xs + (size_t)k * 2, mu + (size_t)k * L, Y);
+      c_m += integrate_step_fb(P, F, D, Xs + (size_t)k * 2, mu + (size_t)k * L, 0.0, Y);
       if (G) {
         memset(G + (size_t)k * L, 0, sizeof(double) * L);
         for (int i = 0; i <= D->n; ++i) {
@@ -700,7 +714,7 @@ int orc_fb_path(const orc_problem *P, const orc_feedback *F, const double *mu, i
   for (int k = 0; k < Nt; ++k) {
     orc_step_draws(P, k, m, D);
     if (njumps) njumps[k] = D->n;
-    c_m += integrate_step_fb(P, F, D, Xs + (size_t)k * 2, mu + (size_t)k * L, Y);
+    c_m += integrate_step_fb(P, F, D, Xs + (size_t)k * 2, mu + (size_t)k * L, 0.0, Y);
     memcpy(Xs + (size_t)(k + 1) * 2, Y[D->n + 1], sizeof(double) * 2);
     c_m += dt * fb_track(P, F, Xs + (size_t)(k + 1) * 2, k + 1, NULL);
   }
@@ -719,7 +733,7 @@ int orc_fb_path(const orc_problem *P, const orc_feedback *F, const double *mu, i
     for (int k = Nt - 1; k >= 0; --k) {
       const double *mu_k = mu + (size_t)k * L;
       orc_step_draws(P, k, m, D);
-      integrate_step_fb(P, F, D, Xs + (size_t)k * 2, mu_k, Y);
+      integrate_step_fb(P, F, D, Xs + (size_t)k * 2, mu_k, 0.0, Y);
       if (G) memset(G + (size_t)k * L, 0, sizeof(double) * L);
       for (int i = D->n; i >= 0; --i) {
         if (i < D->n)
@@ -890,4 +904,120 @@ int orc_fb_optimize(const orc_problem *P, const orc_feedback *F, double *mu, con
   free(grad);
   free(mt);
   return status;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Interacting particles (Sec. 6.4)                                           */
+/* ------------------------------------------------------------------------- */
+static int coupled_valid(const orc_problem *P, const orc_feedback *F) {
+  return fb_valid(P, F) && F->particles >= 3 && F->particles <= 32 && F->ax > 0.0 && F->av > 0.0 &&
+         F->adjoint == ORC_FB_EXACT;
+}
+
+int orc_fb_coupled(const orc_problem *P0, const orc_feedback *F, const double *mu, int64_t r, double *X,
+                   double *lam, double *G, double *cost) {
+  if (!coupled_valid(P0, F) || !mu || r < 0 || 32 * r >= P0->M) return 1;
+  const int N = F->particles, Nt = P0->Nt, L = F->nx * F->nv;
+  const double dt = P0->T / (double)Nt, om = F->omega;
+  /* the particle's own share of the coupling, -2 omega x_i, joins its drift matrix */
+  orc_problem P = *P0;
+  double A2[4] = {P0->A[0], P0->A[1], P0->A[2] - 2.0 * om, P0->A[3]};
+  P.A = A2;
+  double *Xs = X ? X : (double *)malloc(sizeof(double) * (size_t)(Nt + 1) * N * 2);
+  orc_draws *D = (orc_draws *)malloc(sizeof(orc_draws));
+  double (*Y)[ORC_DMAX] = (double (*)[ORC_DMAX])malloc(sizeof(double) * ORC_DMAX * (ORC_NMAX + 2));
+  double *phi = (double *)malloc(sizeof(double) * L);
+  double cin[32], s[32];
+  if (!Xs || !D || !Y || !phi) return 2;
+  for (int i = 0; i < N; ++i) {
+    Xs[2 * i] = F->ax * cos(2.0 * M_PI * i / N);
+    Xs[2 * i + 1] = F->av * sin(2.0 * M_PI * i / N);
+  }
+  double c_r = 0.0;
+  for (int k = 0; k < Nt; ++k) {
+    const double *Xk = Xs + (size_t)k * N * 2;
+    for (int i = 0; i < N; ++i) cin[i] = om * (Xk[2 * ((i + N - 1) % N)] + Xk[2 * ((i + 1) % N)]);
+    for (int i = 0; i < N; ++i) {
+      orc_step_draws(&P, k, 32 * r + i, D);
+      c_r += integrate_step_fb(&P, F, D, Xk + 2 * i, mu + (size_t)k * L, cin[i], Y);
+      memcpy(Xs + ((size_t)(k + 1) * N + i) * 2, Y[D->n + 1], sizeof(double) * 2);
+      c_r += dt * fb_track(&P, F, Xs + ((size_t)(k + 1) * N + i) * 2, k + 1, NULL);
+    }
+  }
+  if (cost) *cost = c_r;
+  if (G || lam) {
+    /* per particle the adjoint of its sub-steps and s_i = sum_j delta_j a_v (the derivative
+     * in its neighbour force, fixed over the step); then d/dx_j at t_k gains
+     * omega (s_{j-1} + s_{j+1}) */
+    double *a = (double *)malloc(sizeof(double) * N * 2);
+    double jt[ORC_DMAX], gr[ORC_DMAX], du[2];
+    for (int i = 0; i < N; ++i) {
+      fb_track(&P, F, Xs + ((size_t)Nt * N + i) * 2, Nt, gr);
+      a[2 * i] = dt * gr[0];
+      a[2 * i + 1] = dt * gr[1];
+    }
+    if (lam) memcpy(lam + (size_t)Nt * N * 2, a, sizeof(double) * N * 2);
+    for (int k = Nt - 1; k >= 0; --k) {
+      const double *Xk = Xs + (size_t)k * N * 2, *mu_k = mu + (size_t)k * L;
+      if (G) memset(G + (size_t)k * L, 0, sizeof(double) * L);
+      for (int i = 0; i < N; ++i) cin[i] = om * (Xk[2 * ((i + N - 1) % N)] + Xk[2 * ((i + 1) % N)]);
+      for (int i = 0; i < N; ++i) {
+        double *ai = a + 2 * i;
+        orc_step_draws(&P, k, 32 * r + i, D);
+        integrate_step_fb(&P, F, D, Xk + 2 * i, mu_k, cin[i], Y);
+        s[i] = 0.0;
+        for (int j = D->n; j >= 0; --j) {
+          if (j < D->n)
+            for (int c = 0; c < 2; ++c) ai[c] *= jump_gain_of(&P, c);
+          double u = orc_fb_control(F, mu_k, Y[j], du, phi);
+          double w = P.nu * u + P.B[0] * ai[0] + P.B[1] * ai[1];
+          if (G)
+            for (int l = 0; l < L; ++l) G[(size_t)k * L + l] += D->delta[j] * phi[l] * w;
+          s[i] += D->delta[j] * ai[1];
+          drift_jacobian_T(&P, Y[j], ai, jt);
+          for (int c = 0; c < 2; ++c) ai[c] = ai[c] + D->delta[j] * (jt[c] + w * du[c]);
+        }
+      }
+      for (int i = 0; i < N; ++i) a[2 * i] += om * (s[(i + N - 1) % N] + s[(i + 1) % N]);
+      if (k >= 1)
+        for (int i = 0; i < N; ++i) {
+          fb_track(&P, F, Xk + 2 * i, k, gr);
+          a[2 * i] += dt * gr[0];
+          a[2 * i + 1] += dt * gr[1];
+        }
+      if (lam) memcpy(lam + (size_t)k * N * 2, a, sizeof(double) * N * 2);
+    }
+    free(a);
+  }
+  if (!X) free(Xs);
+  free(D);
+  free(Y);
+  free(phi);
+  return 0;
+}
+
+int orc_fb_coupled_gradient(const orc_problem *P, const orc_feedback *F, const double *mu, int nthreads,
+                            double *J, double *grad) {
+  (void)nthreads;
+  if (!coupled_valid(P, F) || !mu || P->M % 32 != 0) return 1;
+  const int64_t R = P->M / 32;
+  const size_t n = (size_t)P->Nt * F->nx * F->nv;
+  double *G = grad ? (double *)malloc(sizeof(double) * n) : NULL;
+  if (grad) memset(grad, 0, sizeof(double) * n);
+  double csum = 0.0;
+  int err = 0;
+  for (int64_t r = 0; r < R; ++r) {
+    double c = 0.0;
+    int rc = orc_fb_coupled(P, F, mu, r, NULL, NULL, G, &c);
+    if (rc) err = rc;
+    csum += c;
+    if (grad)
+      for (size_t t = 0; t < n; ++t) grad[t] += G[t];
+  }
+  const double inv = 1.0 / ((double)R * F->particles);
+  if (J) *J = csum * inv;
+  if (grad)
+    for (size_t t = 0; t < n; ++t) grad[t] *= inv;
+  free(G);
+  return err;
 }

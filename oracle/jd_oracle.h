@@ -146,7 +146,7 @@ int orc_optimize(const orc_problem *P, double *u, const orc_opt_params *o, int n
 /* mu is Nt * L, L = nx nv, row-major [k][i][l].                                   */
 /* ------------------------------------------------------------------------- */
 #define ORC_FBMAX 16     /* centres per axis */
-enum { ORC_TRACK_QUAD = 0, ORC_TRACK_GAUSS = 1 };
+enum { ORC_TRACK_QUAD = 0, ORC_TRACK_GAUSS = 1, ORC_TRACK_ELLIPSE = 2 };
 enum { ORC_FB_EXACT = 0, ORC_FB_SURROGATE = 1 };
 
 typedef struct {
@@ -158,6 +158,10 @@ typedef struct {
   int adjoint;            /* ORC_FB_EXACT, or ORC_FB_SURROGATE (Sec. 6.5): the costates run
                              along states drawn from N(z_d(t_k), rate t_k I) */
   double sur_rate;        /* surrogate variance growth per unit time */
+  int particles;          /* coupled particles per realization (Sec. 6.4), 0 = independent paths */
+  double omega;           /* nearest-neighbour coupling of the ring */
+  double ax, av;          /* ellipse half-axes: tracking term ORC_TRACK_ELLIPSE (Eq.
+                             phonon_functional_tracking) and the coupled initial states */
 } orc_feedback;
 
 /* The bump phi(x, x_c, eps) of r = x - x_c, and its derivative in x. */
@@ -180,6 +184,19 @@ int orc_fb_cost(const orc_problem *P, const orc_feedback *F, const double *mu, i
                 double *J);
 int orc_fb_gradient(const orc_problem *P, const orc_feedback *F, const double *mu, int nthreads,
                     double *J, double *grad);
+/* Interacting particles (Sec. 6.4 eq:interacting_model): N = F->particles particles on a
+ * ring, particle i of realization r with the random streams of path index 32 r + i,
+ *   dx_i = v_i dt,  dv_i = (u(x_i, v_i, t) - eta x_i - omega (2 x_i - x_{i-1} - x_{i+1})) dt + ...
+ * (eta = -A[1][0]; the own term 2 omega x_i with the particle's drift; the neighbours'
+ * positions at t_k drive every sub-step of step k).  Particles start equidistant on the
+ * ellipse (ax cos(2 pi i/N), av sin(2 pi i/N)).  X (Nt+1)*N*2, lam (Nt+1)*N*2, G (Nt*L,
+ * summed over the realization's particles), cost (sum of the particles' path costs); each
+ * nullable. */
+int orc_fb_coupled(const orc_problem *P, const orc_feedback *F, const double *mu, int64_t r, double *X,
+                   double *lam, double *G, double *cost);
+/* J = (1/(R N)) sum over R = M/32 realizations and N particles; grad likewise (Nt*L). */
+int orc_fb_coupled_gradient(const orc_problem *P, const orc_feedback *F, const double *mu, int nthreads,
+                            double *J, double *grad);
 /* Gradient descent with the Armijo rule on mu (Algorithm 5.4, unconstrained): the same
  * zeta schedule and stopping tests as orc_optimize; mu (Nt*L) is updated in place. */
 int orc_fb_optimize(const orc_problem *P, const orc_feedback *F, double *mu, const orc_opt_params *o,

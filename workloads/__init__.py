@@ -31,6 +31,9 @@ Workloads (named by what they are):
                        alpha=1e-2, b=(0.1,0.1), z0=(0.75,0.75), T=1, N_t=100, M=2^20.
   * ``feedback_trajectory``  Sec. 6.3: the same model with eta=0, eps=0.1, following
                        z_d(t) = (-x_max/2 + x_max t/T, v_max/2 - |v_max t/(2T)|).
+  * ``feedback_coupled``  Sec. 6.4: rings of 32 coupled oscillators (eta=1, omega=0.5)
+                       on the ellipse A_x=1.5, A_v=1.7071, ellipse tracking cost, M=2^20
+                       (2^15 realizations), N_t=100.
   * ``serving_requests``  a stream of requests (d in {1,2,8,32}, M log-uniform in
                        [2^12,2^22], N_t uniform in [50,2000], lambda uniform in
                        [0.5,10]) with Poisson arrivals, numpy default_rng(5).
@@ -220,7 +223,7 @@ def serving_requests(n: int = 10000, rate: float = 200.0, seed: int = 5):
 
 
 # --- feedback control (Sec. 2 eq:control_structure, Sec. 5.1-5.2, Sec. 6) --------------
-TRACK_QUAD, TRACK_GAUSS = 0, 1
+TRACK_QUAD, TRACK_GAUSS, TRACK_ELLIPSE = 0, 1, 2
 FB_EXACT, FB_SURROGATE = 0, 1
 
 
@@ -238,6 +241,10 @@ class Feedback:
     sigma_J: float = 1.0
     adjoint: int = 0          # FB_EXACT, or FB_SURROGATE (Sec. 6.5)
     sur_rate: float = 0.0     # surrogate states N(z_d(t), sur_rate t I)
+    particles: int = 0        # coupled particles per realization on a ring (Sec. 6.4), 0 = none
+    omega: float = 0.0        # nearest-neighbour coupling
+    ax: float = 1.0           # ellipse half-axes (TRACK_ELLIPSE, coupled initial states)
+    av: float = 1.0
 
     @property
     def L(self) -> int:
@@ -271,3 +278,13 @@ def feedback_trajectory(M: int = 1 << 20, Nt: int = 100, seed: int = 0):
 def random_mu(p: Problem, fb: Feedback, seed: int = 7, scale: float = 1.0) -> np.ndarray:
     """Seeded feedback weights mu (Nt, L) for gradient tests."""
     return scale * np.random.default_rng(seed).standard_normal((p.Nt, fb.L))
+
+
+def feedback_coupled(M: int = 1 << 20, Nt: int = 100, seed: int = 0, particles: int = 32):
+    """(Problem, Feedback) of Sec. 6.4: rings of `particles` coupled oscillators (eta = 1,
+    omega = 0.5) started equidistant on the ellipse A_x = 1.5, A_v = 1.7071067811865475,
+    ellipse tracking cost (sigma_J = 1), 10x10 bumps (eps = 0.5), Keilson-Storer resets;
+    M = 32 x realizations (lanes beyond `particles` idle)."""
+    p, fb = feedback_centering(M=M, Nt=Nt, seed=seed)
+    fb = fb.replace(track=TRACK_ELLIPSE, particles=particles, omega=0.5, ax=1.5, av=1.7071067811865475)
+    return p.replace(name="feedback_coupled"), fb
