@@ -134,9 +134,12 @@ WORKLOADS = {
     "feedback_centering": lambda: workloads.feedback_centering()[0],
     # the same with eta = 0, eps = 0.1 and the piecewise-linear target of Sec. 6.3
     "feedback_trajectory": lambda: workloads.feedback_trajectory()[0],
+    # Sec. 6.4: rings of 32 coupled oscillators, ellipse cost; M=2^20 (2^15 rings), Nt=100
+    "feedback_coupled": lambda: workloads.feedback_coupled()[0],
 }
 FB_WORKLOADS = {"feedback_centering": workloads.feedback_centering,
-                "feedback_trajectory": workloads.feedback_trajectory}
+                "feedback_trajectory": workloads.feedback_trajectory,
+                "feedback_coupled": workloads.feedback_coupled}
 
 
 def bench_workload(M=None, Nt=None, name="double_well"):

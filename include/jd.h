@@ -325,12 +325,12 @@ jd_status jd_cost_noalloc(const jd_problem_desc *desc, const double *u, double *
  * drift, evaluated at the left end of every sub-step of the jump-adapted grid.  The
  * cost is J(mu) = (1/M) sum_m [ sum_{k=1..Nt} dt l(X_k, t_k) + sum over sub-steps
  * (alpha/2) delta u(Y)^2 ], alpha = the descriptor's nu, with l the quadratic term
- * (1/2) sum q_c (z_c - xd_c)^2 or the Gaussian -exp(-sum q_c (z_c - xd_c)^2 / (2 sigma_J^2))
- * of Sec. 6 eq:tracking_cost.  u_min and u_max do not apply.  The gradient is the exact
+ * (1/2) sum q_c (z_c - xd_c)^2, the Gaussian -exp(-sum q_c (z_c - xd_c)^2 / (2 sigma_J^2))
+ * of Sec. 6 eq:tracking_cost, or the ellipse term of Sec. 6.4.  u_min and u_max do not apply.  The gradient is the exact
  * derivative of J in mu (eq:definition_Gradient with the adjoint of
  * eq:adjoint_eq_approximation, u_x and u_v included).  Every jump law is accepted.
  * --------------------------------------------------------------------------- */
-typedef enum { JD_TRACK_QUADRATIC = 0, JD_TRACK_GAUSS = 1 } jd_track;
+typedef enum { JD_TRACK_QUADRATIC = 0, JD_TRACK_GAUSS = 1, JD_TRACK_ELLIPSE = 2 } jd_track;
 typedef enum { JD_FB_EXACT = 0, JD_FB_SURROGATE = 1 } jd_fb_adjoint;
 
 typedef struct {
@@ -349,6 +349,18 @@ typedef struct {
                             sub-steps.  An approximation: no states are stored (one value per
                             path and step instead of two) */
   double sur_rate;       /* SURROGATE: variance growth per unit time, >= 0 */
+  int particles;         /* interacting particles (Sec. 6.4 eq:interacting_model): 0 for
+                            independent paths, else 3..32 particles per ring: path m is
+                            particle m % 32 of realization m / 32 (lanes >= particles idle; M
+                            must be a multiple of 32), dv_i gains -omega (2 x_i - x_{i-1} -
+                            x_{i+1}) with the neighbours' positions at t_k driving the whole
+                            step k, and the particles start equidistant on the ellipse
+                            (ax cos(2 pi i/N), av sin(2 pi i/N)); J and the gradient average over
+                            the M/32 * particles particles.  EXACT adjoint only */
+  double omega;          /* ring coupling */
+  double ax, av;         /* ellipse half-axes (> 0 for JD_TRACK_ELLIPSE or particles > 0):
+                            JD_TRACK_ELLIPSE is -exp(-(x^2/ax^2 + v^2/av^2 - 1)^2 / (2 sigma_J^2))
+                            of Sec. 6.4 Eq. phonon_functional_tracking */
 } jd_feedback_desc;
 
 /* J(mu).  mu: Nt * L doubles, row-major [k][i][l], in mu_space; J: host pointer.  The

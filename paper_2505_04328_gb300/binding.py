@@ -60,14 +60,18 @@ class ProblemDesc(ctypes.Structure):
 class FeedbackDesc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("nv", ctypes.c_int), ("x_max", ctypes.c_double),
                 ("v_max", ctypes.c_double), ("eps", ctypes.c_double), ("track", ctypes.c_int),
-                ("sigma_J", ctypes.c_double), ("adjoint", ctypes.c_int), ("sur_rate", ctypes.c_double)]
+                ("sigma_J", ctypes.c_double), ("adjoint", ctypes.c_int), ("sur_rate", ctypes.c_double),
+                ("particles", ctypes.c_int), ("omega", ctypes.c_double), ("ax", ctypes.c_double),
+                ("av", ctypes.c_double)]
 
 
 def make_feedback(fb) -> FeedbackDesc:
     """The jd_feedback_desc of a workloads.Feedback (duck-typed)."""
     return FeedbackDesc(nx=int(fb.nx), nv=int(fb.nv), x_max=float(fb.x_max), v_max=float(fb.v_max),
                         eps=float(fb.eps), track=int(fb.track), sigma_J=float(fb.sigma_J),
-                        adjoint=int(getattr(fb, "adjoint", 0)), sur_rate=float(getattr(fb, "sur_rate", 0.0)))
+                        adjoint=int(getattr(fb, "adjoint", 0)), sur_rate=float(getattr(fb, "sur_rate", 0.0)),
+                        particles=int(getattr(fb, "particles", 0)), omega=float(getattr(fb, "omega", 0.0)),
+                        ax=float(getattr(fb, "ax", 1.0)), av=float(getattr(fb, "av", 1.0)))
 
 
 class KernelStat(ctypes.Structure):

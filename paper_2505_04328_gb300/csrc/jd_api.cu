@@ -1331,10 +1331,19 @@ static jd_status fb_validate(const jd_problem *p, const jd_feedback_desc *fb) {
   if (!(fb->x_max > 0.0) || !std::isfinite(fb->x_max) || !(fb->v_max > 0.0) || !std::isfinite(fb->v_max) ||
       !(fb->eps > 0.0) || !std::isfinite(fb->eps))
     return fail(JD_ERR_INVALID_ARG, "x_max, v_max and eps must be finite and > 0");
-  if (fb->track != JD_TRACK_QUADRATIC && fb->track != JD_TRACK_GAUSS)
+  if (fb->track != JD_TRACK_QUADRATIC && fb->track != JD_TRACK_GAUSS && fb->track != JD_TRACK_ELLIPSE)
     return fail(JD_ERR_INVALID_ARG, "bad tracking term");
-  if (fb->track == JD_TRACK_GAUSS && (!(fb->sigma_J > 0.0) || !std::isfinite(fb->sigma_J)))
+  if (fb->track != JD_TRACK_QUADRATIC && (!(fb->sigma_J > 0.0) || !std::isfinite(fb->sigma_J)))
     return fail(JD_ERR_INVALID_ARG, "sigma_J must be finite and > 0");
+  if ((fb->track == JD_TRACK_ELLIPSE || fb->particles) &&
+      (!(fb->ax > 0.0) || !std::isfinite(fb->ax) || !(fb->av > 0.0) || !std::isfinite(fb->av)))
+    return fail(JD_ERR_INVALID_ARG, "ax and av must be finite and > 0");
+  if (fb->particles != 0 && (fb->particles < 3 || fb->particles > 32))
+    return fail(JD_ERR_INVALID_ARG, "particles must be 0 or in [3, 32]");
+  if (fb->particles && (p->desc.M % 32 != 0 || !std::isfinite(fb->omega)))
+    return fail(JD_ERR_INVALID_ARG, "interacting particles need M a multiple of 32 and a finite omega");
+  if (fb->particles && fb->adjoint != JD_FB_EXACT)
+    return fail(JD_ERR_UNSUPPORTED, "interacting particles take the exact adjoint only");
   if (fb->adjoint != JD_FB_EXACT && fb->adjoint != JD_FB_SURROGATE)
     return fail(JD_ERR_INVALID_ARG, "bad feedback adjoint");
   if (fb->adjoint == JD_FB_SURROGATE && (!(fb->sur_rate >= 0.0) || !std::isfinite(fb->sur_rate)))
@@ -1435,8 +1444,10 @@ static jd_status fb_run(jd_problem *p, const jd_feedback_desc *fb, const double 
   }
   pr = prof_begin(KC_FB_FIN, p->stream);
   const int64_t nblk = ceil_div(p->desc.M, FB_TPB);
+  // the average runs over the particles that exist: M paths, or M/32 rings of N particles
+  const int64_t count = fb->particles ? p->desc.M / 32 * fb->particles : p->desc.M;
   JD_CUDA(fb_finalize(p->fb_partC, p->fb_partG, nblk, fb_groups(nblk * (FB_TPB / 32)), Nt, fb->nx, fb->nv,
-                      ops->NX, ops->NV, p->desc.M, p->scal_d + S_J, grad_out, p->stream));
+                      ops->NX, ops->NV, count, p->scal_d + S_J, grad_out, p->stream));
   prof_end(pr, p->stream);
   return JD_OK;
 }

@@ -58,7 +58,10 @@ struct FbParams {
   R q[2];                   // tracking weights
   R hinv_s2, inv_s2;        // Gaussian: 1 / (2 sigma_J^2), 1 / sigma_J^2
   R srate_dt;               // surrogate adjoint (Sec. 6.5): variance of step k is srate_dt k
-  int gauss, Nt;
+  R omega;                  // interacting particles (Sec. 6.4): ring coupling
+  R iax2, iav2;             // ellipse cost: 1 / A_x^2, 1 / A_v^2
+  R x0c[32], v0c[32];       // interacting particles: initial state of lane i (on the ellipse)
+  int gauss, ellipse, N, Nt;   // N: particles per warp (ring), 0 = independent paths
   int64_t mloc;
 };
 
@@ -231,6 +234,16 @@ template <typename R, bool GRAD>
 __device__ __forceinline__ R fb_track(const FbParams<R> &fp, R dt, const R (&z)[2],
                                       const R *__restrict__ xdk, R (&g)[2]) {
   using M = Ar<R>;
+  if (fp.ellipse) {   // -exp(-E^2 / (2 sigma_J^2)), E = x^2/A_x^2 + v^2/A_v^2 - 1 (Sec. 6.4)
+    const R E = M::sub(M::fma(M::mul(z[1], z[1]), fp.iav2, M::mul(M::mul(z[0], z[0]), fp.iax2)), R(1));
+    const R X = exp(-M::mul(M::mul(E, E), fp.hinv_s2));
+    if (GRAD) {
+      const R c = M::mul(dt, M::mul(M::mul(X, M::mul(E, fp.inv_s2)), R(2)));
+      g[0] = M::mul(c, M::mul(z[0], fp.iax2));
+      g[1] = M::mul(c, M::mul(z[1], fp.iav2));
+    }
+    return -M::mul(dt, X);
+  }
   const R e0 = M::sub(z[0], __ldg(xdk)), e1 = M::sub(z[1], __ldg(xdk + 1));
   const R w0 = M::mul(fp.q[0], e0), w1 = M::mul(fp.q[1], e1);
   const R Q = M::fma(w1, e1, M::mul(w0, e0));
@@ -250,17 +263,20 @@ __device__ __forceinline__ R fb_track(const FbParams<R> &fp, R dt, const R (&z)[
   return M::mul(M::mul(R(0.5), dt), Q);
 }
 
-// One Euler sub-step of length de from y under the feedback control; returns the
+// One Euler sub-step of length de from y under the feedback control (plus, for
+// interacting particles, the neighbours' force cin on the velocity); returns the
 // sub-step's control cost (alpha/2) de u(y)^2.
-template <typename R, int NX, int NV>
+template <typename R, int NX, int NV, bool CPL>
 __device__ __forceinline__ R fb_substep(const KParams<R, 2, 1> &kp, const FbParams<R> &fp,
-                                        const R *__restrict__ mk, R de, R sqde, const R (&z)[2], R (&y)[2]) {
+                                        const R *__restrict__ mk, R de, R sqde, const R (&z)[2], R (&y)[2],
+                                        R cin) {
   using M = Ar<R>;
   R px[NX], pv[NV], ux, uv;
   const R u = fb_eval<R, NX, NV, false>(fp, mk, y[0], y[1], px, pv, ux, uv);
   const R uu[1] = {u};
   R f[2];
   drift(kp, y, uu, f);
+  if (CPL) f[1] = M::add(f[1], cin);   // interacting particles: the neighbours' force
 #pragma unroll
   for (int c = 0; c < 2; ++c) y[c] = M::fma(M::mul(kp.sigma[c], sqde), z[c], M::fma(de, f[c], y[c]));
   return M::mul(M::mul(fp.halpha, de), M::mul(u, u));
@@ -329,27 +345,42 @@ __device__ __forceinline__ double fb_block_sum(Pair<R> v, Pair<R> *red) {
   return out;
 }
 
-template <typename R, int NX, int NV, bool STORE>
+template <typename R, int NX, int NV, bool STORE, bool CPL>
 __global__ void __launch_bounds__(FB_TPB)
 fb_fwd_kernel(const __grid_constant__ KParams<R, 2, 1> kp, const __grid_constant__ FbParams<R> fp,
               const R *__restrict__ mu, const R *__restrict__ xd, R *__restrict__ traj,
               uint32_t *__restrict__ flags, double *__restrict__ partC) {
+  using M = Ar<R>;
   constexpr int LP = NX * NV;
   __shared__ Pair<R> red[FB_TPB / 32];
+  const int lane = threadIdx.x & 31;
   const int64_t mloc = fp.mloc, m = (int64_t)blockIdx.x * FB_TPB + threadIdx.x;
-  const bool active = m < mloc;
+  // interacting particles: lane i < N of a warp is particle i of one ring (M is a multiple
+  // of 32, so warps are whole); every lane of the warp runs the step loop for the shuffles
+  const bool in_range = m < mloc, active = in_range && (!CPL || lane < fp.N);
+  const int left = CPL ? (lane + fp.N - 1) % fp.N : 0, right = CPL ? (lane + 1) % fp.N : 0;
   const uint32_t mg = (uint32_t)(kp.m_begin + m);
   const int Nt = fp.Nt;
   Kahan<R> cost;
-  if (active) {
+  if (in_range) {
     R z[2] = {kp.x0[0], kp.x0[1]};
+    if (CPL && active) {
+      z[0] = fp.x0c[lane];
+      z[1] = fp.v0c[lane];
+    }
     uint32_t fw = 0;
-    if (STORE) {
+    if (STORE && active) {
       traj[m] = z[0];
       traj[mloc + m] = z[1];
     }
 #pragma unroll 1
     for (int k = 0; k < Nt; ++k) {
+      R cin = R(0);
+      if constexpr (CPL) {   // omega (x_{i-1} + x_{i+1}) at t_k, fixed over the step
+        const R xl = __shfl_sync(0xffffffffu, z[0], left), xr = __shfl_sync(0xffffffffu, z[0], right);
+        cin = M::mul(fp.omega, M::add(xl, xr));
+        if (!active) continue;
+      }
       const R *mk = mu + (size_t)k * LP;
       R zs[2];
       const uint32_t w0 = main_draws(kp, k, mg, zs);
@@ -368,7 +399,7 @@ fb_fwd_kernel(const __grid_constant__ KParams<R, 2, 1> kp, const __grid_constant
           de = fb_delta(kp, P, n, i);
           sq = Ar<R>::sqrt(de);
         }
-        cost.add(fb_substep<R, NX, NV>(kp, fp, mk, de, sq, zs, z));
+        cost.add(fb_substep<R, NX, NV, CPL>(kp, fp, mk, de, sq, zs, z, cin));
         if (i >= n) break;
         R xih[2];
         slot_draws(kp, k, mg, P.order[i], xih, zs);   // the jump's size and the next normals
@@ -484,7 +515,7 @@ constexpr size_t fb_adj_smem() {
   return sizeof(R) * (size_t)(FB_TPB / 32) * ((NX / 2) + (NV / 2)) * FB_AROW;
 }
 
-template <typename R, int NX, int NV>
+template <typename R, int NX, int NV, bool CPL>
 __global__ void __launch_bounds__(FB_TPB)
 fb_adj_kernel(const __grid_constant__ KParams<R, 2, 1> kp, const __grid_constant__ FbParams<R> fp,
               const R *__restrict__ mu, const R *__restrict__ xd, const R *__restrict__ traj,
@@ -497,7 +528,8 @@ fb_adj_kernel(const __grid_constant__ KParams<R, 2, 1> kp, const __grid_constant
   R *wb = wa + (NX / 2) * FB_AROW;
   const int64_t mloc = fp.mloc, m = (int64_t)blockIdx.x * FB_TPB + threadIdx.x;
   const int64_t wid = (int64_t)blockIdx.x * (FB_TPB / 32) + warp;
-  const bool active = m < mloc;
+  const bool active = m < mloc && (!CPL || lane < fp.N);
+  const int left = CPL ? (lane + fp.N - 1) % fp.N : 0, right = CPL ? (lane + 1) % fp.N : 0;
   const uint32_t mg = (uint32_t)(kp.m_begin + m);
   const int Nt = fp.Nt;
   R a[2] = {R(0), R(0)};
@@ -527,6 +559,11 @@ fb_adj_kernel(const __grid_constant__ KParams<R, 2, 1> kp, const __grid_constant
     int n = 0;
     FbPlan<R> P;
     R Ys[NMAX + 1][2];   // sub-step start states of a step with jumps (Ys[0] = X_k)
+    R cin = R(0);
+    if constexpr (CPL) {   // interacting particles: the neighbours' force of step k
+      const R xl = __shfl_sync(0xffffffffu, zk[0], left), xr = __shfl_sync(0xffffffffu, zk[0], right);
+      cin = M::mul(fp.omega, M::add(xl, xr));
+    }
     if (active) {
       if ((fk >> (k & 31)) & 1u) {
         // regenerate the step's sub-states from X_k with the forward's arithmetic
@@ -536,7 +573,7 @@ fb_adj_kernel(const __grid_constant__ KParams<R, 2, 1> kp, const __grid_constant
 #pragma unroll 1
         for (int i = 0; i < n; ++i) {
           const R de = fb_delta(kp, P, n, i);
-          fb_substep<R, NX, NV>(kp, fp, mk, de, Ar<R>::sqrt(de), zs, y);
+          fb_substep<R, NX, NV, CPL>(kp, fp, mk, de, Ar<R>::sqrt(de), zs, y, cin);
           R xih[2];
           slot_draws(kp, k, mg, P.order[i], xih, zs);
           apply_jump(kp, y, xih);
@@ -552,6 +589,7 @@ fb_adj_kernel(const __grid_constant__ KParams<R, 2, 1> kp, const __grid_constant
 #pragma unroll
     for (int t = 0; t < QPL; ++t) sq[t][0] = sq[t][1] = sq[t][2] = sq[t][3] = R(0);
     const int rounds = (int)__reduce_max_sync(0xffffffffu, active ? (unsigned)(n + 1) : 0u);
+    R sn = R(0);   // interacting particles: sum over sub-steps of delta a_v (d/d neighbour force)
 #pragma unroll 1
     for (int r = 0; r < rounds; ++r) {
       R ra[NX], rb[NV];
@@ -573,6 +611,7 @@ fb_adj_kernel(const __grid_constant__ KParams<R, 2, 1> kp, const __grid_constant
         const R dw = M::mul(de, w);
 #pragma unroll
         for (int c = 0; c < NX; ++c) ra[c] = M::mul(dw, ra[c]);
+        if (CPL) sn = M::fma(de, a[1], sn);
         adjoint_update(kp, y, de, a);
         a[0] = M::fma(dw, ux, a[0]);
         a[1] = M::fma(dw, uv, a[1]);
@@ -583,6 +622,10 @@ fb_adj_kernel(const __grid_constant__ KParams<R, 2, 1> kp, const __grid_constant
         for (int c = 0; c < NV; ++c) rb[c] = R(0);
       }
       fb_exchange_add<R, NX, NV>(wa, wb, lane, ra, rb, sq);
+    }
+    if constexpr (CPL) {   // the neighbour force of particle j drove particles j-1 and j+1
+      const R sl = __shfl_sync(0xffffffffu, sn, left), sr = __shfl_sync(0xffffffffu, sn, right);
+      if (active) a[0] = M::fma(fp.omega, M::add(sl, sr), a[0]);
     }
     if (active && k >= 1) {
       R g[2];
@@ -822,24 +865,49 @@ void fb_make_params(const ::jd_problem *p, const jd_feedback_desc &fb, FbParams<
   fp.inv_s2 = (R)(1.0 / s2);
   fp.gauss = fb.track == JD_TRACK_GAUSS;
   fp.srate_dt = (R)(fb.adjoint == JD_FB_SURROGATE ? fb.sur_rate * (p->desc.T / p->desc.Nt) : 0.0);
+  fp.ellipse = fb.track == JD_TRACK_ELLIPSE;
+  fp.iax2 = (R)(fb.track == JD_TRACK_ELLIPSE || fb.particles ? 1.0 / (fb.ax * fb.ax) : 0.0);
+  fp.iav2 = (R)(fb.track == JD_TRACK_ELLIPSE || fb.particles ? 1.0 / (fb.av * fb.av) : 0.0);
+  fp.N = fb.particles;
+  fp.omega = (R)fb.omega;
+  for (int i = 0; i < 32; ++i) {   // particles start equidistant on the ellipse (Sec. 6.4)
+    const double th = 2.0 * 3.14159265358979323846 * i / (fb.particles > 0 ? fb.particles : 1);
+    fp.x0c[i] = (R)(fb.particles ? fb.ax * std::cos(th) : 0.0);
+    fp.v0c[i] = (R)(fb.particles ? fb.av * std::sin(th) : 0.0);
+  }
   fp.Nt = p->desc.Nt;
   fp.mloc = p->desc.M;
+}
+
+// Kernel coefficients of a feedback problem: for interacting particles the particle's own
+// share of the ring coupling, -2 omega x_i, joins its drift matrix (A[1][0]).
+template <typename R>
+void fb_make_kparams(const ::jd_problem *p, const jd_feedback_desc &fb, KParams<R, 2, 1> &kp) {
+  make_kparams<R, 2, 1>(p, 0, p->desc.M, kp);
+  if (fb.particles) kp.A[2] = (R)(p->A[2] - 2.0 * fb.omega);
 }
 
 template <typename R, int NX, int NV>
 cudaError_t fb_fwd_launch(const ::jd_problem *p, const jd_feedback_desc &fb, bool store, const FbBufs &b,
                           cudaStream_t s) {
   KParams<R, 2, 1> kp;
-  make_kparams<R, 2, 1>(p, 0, p->desc.M, kp);
+  fb_make_kparams<R>(p, fb, kp);
   FbParams<R> fp;
   fb_make_params<R>(p, fb, fp);
   const unsigned grid = (unsigned)ceil_div(p->desc.M, FB_TPB);
   const R *mu = static_cast<const R *>(b.mu), *xd = static_cast<const R *>(p->xdk);
-  if (store)
-    fb_fwd_kernel<R, NX, NV, true><<<grid, FB_TPB, 0, s>>>(kp, fp, mu, xd, static_cast<R *>(b.traj), b.flags,
-                                                            b.partC);
-  else
-    fb_fwd_kernel<R, NX, NV, false><<<grid, FB_TPB, 0, s>>>(kp, fp, mu, xd, nullptr, nullptr, b.partC);
+  R *traj = static_cast<R *>(b.traj);
+  if (fb.particles) {
+    if (store)
+      fb_fwd_kernel<R, NX, NV, true, true><<<grid, FB_TPB, 0, s>>>(kp, fp, mu, xd, traj, b.flags, b.partC);
+    else
+      fb_fwd_kernel<R, NX, NV, false, true><<<grid, FB_TPB, 0, s>>>(kp, fp, mu, xd, nullptr, nullptr, b.partC);
+  } else {
+    if (store)
+      fb_fwd_kernel<R, NX, NV, true, false><<<grid, FB_TPB, 0, s>>>(kp, fp, mu, xd, traj, b.flags, b.partC);
+    else
+      fb_fwd_kernel<R, NX, NV, false, false><<<grid, FB_TPB, 0, s>>>(kp, fp, mu, xd, nullptr, nullptr, b.partC);
+  }
   count_launch();
   return cudaGetLastError();
 }
@@ -848,19 +916,17 @@ cudaError_t fb_fwd_launch(const ::jd_problem *p, const jd_feedback_desc &fb, boo
 template <typename R, int NX, int NV>
 cudaError_t fb_adj_launch(const ::jd_problem *p, const jd_feedback_desc &fb, const FbBufs &b, cudaStream_t s) {
   KParams<R, 2, 1> kp;
-  make_kparams<R, 2, 1>(p, 0, p->desc.M, kp);
+  fb_make_kparams<R>(p, fb, kp);
   FbParams<R> fp;
   fb_make_params<R>(p, fb, fp);
   constexpr size_t smem = fb_adj_smem<R, NX, NV>();
   static_assert(smem <= 232448, "fb_adj_kernel shared memory");
-  cudaError_t e = cudaFuncSetAttribute(fb_adj_kernel<R, NX, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  auto kern = fb.particles ? fb_adj_kernel<R, NX, NV, true> : fb_adj_kernel<R, NX, NV, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const unsigned grid = (unsigned)ceil_div(p->desc.M, FB_TPB);
-  fb_adj_kernel<R, NX, NV><<<grid, FB_TPB, smem, s>>>(kp, fp, static_cast<const R *>(b.mu),
-                                                      static_cast<const R *>(p->xdk),
-                                                      static_cast<const R *>(b.traj), b.flags,
-                                                      static_cast<R *>(b.partW));
+  kern<<<grid, FB_TPB, smem, s>>>(kp, fp, static_cast<const R *>(b.mu), static_cast<const R *>(p->xdk),
+                                  static_cast<const R *>(b.traj), b.flags, static_cast<R *>(b.partW));
   count_launch();
   return cudaGetLastError();
 }
@@ -912,8 +978,11 @@ template <typename R, int NX, int NV>
 size_t fb_stack_bytes() {
   static const size_t bytes = [] {   // the kernels' attributes do not change: ask once
     size_t need = 0;
-    const void *ks[] = {(const void *)fb_fwd_kernel<R, NX, NV, false>,
-                        (const void *)fb_fwd_kernel<R, NX, NV, true>, (const void *)fb_adj_kernel<R, NX, NV>,
+    const void *ks[] = {(const void *)fb_fwd_kernel<R, NX, NV, false, false>,
+                        (const void *)fb_fwd_kernel<R, NX, NV, true, false>,
+                        (const void *)fb_fwd_kernel<R, NX, NV, false, true>,
+                        (const void *)fb_fwd_kernel<R, NX, NV, true, true>,
+                        (const void *)fb_adj_kernel<R, NX, NV, false>, (const void *)fb_adj_kernel<R, NX, NV, true>,
                         (const void *)fb_sur_adj_kernel<R, NX, NV>, (const void *)fb_fwd_sur_kernel<R, NX, NV>};
     for (const void *k : ks) {
       cudaFuncAttributes a;

@@ -174,3 +174,24 @@ def test_surrogate_gradient_parity(case, prec):
         assert eJ <= 1e-13 and eg <= 1e-12
     else:
         assert eJ <= 1e-6 and eg <= 1e-5
+
+
+@pytest.mark.parametrize("N", [5, 32])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_coupled_particles_parity(N, prec):
+    """Sec. 6.4: rings of N coupled particles (one warp per ring, neighbours by shuffles),
+    ellipse tracking cost, shared weights; against the oracle's ring."""
+    p, fb = workloads.feedback_coupled(M=32 * 37, Nt=30, particles=N)
+    p = p.replace(lam=5.0)
+    mu = workloads.random_mu(p, fb, seed=27, scale=0.6)
+    Jo, go = oracle.fb_coupled_gradient(p, fb, mu)
+    with JdProblem(p, prec=prec) as jp:
+        Jc = jp.fb_cost(fb, mu)
+        J, g = jp.fb_gradient(fb, mu)
+    eJ, eg = abs(J - Jo) / abs(Jo), rel_l2(g, go)
+    print(f"coupled N={N} {prec}: J {eJ:.2e}  grad {eg:.2e}")
+    assert Jc == J
+    if prec == "fp64":
+        assert eJ <= 1e-13 and eg <= 1e-12
+    else:
+        assert eJ <= 1e-6 and eg <= 1e-5
