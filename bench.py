@@ -422,8 +422,9 @@ def run_feedback(args, p, stream, dist, ws, rank, local):
             oracle.fb_gradient(ps, fb, mu.cpu().numpy())
             sec = time.perf_counter() - t0
             line["cpu_baseline"] = {
-                "value": ps.M * Nt / sec, "unit": UNIT, "cores": oracle.default_threads(), "kind": "oracle",
-                "sample": f"{ps.M} of {M} paths, all {Nt} steps, one feedback gradient"}
+                "value": ps.M * Nt / sec, "unit": UNIT,
+                "cores": 1 if fb.particles else oracle.default_threads(),   # the ring sweep is one thread
+                "kind": "oracle", "sample": f"{ps.M} of {M} paths, all {Nt} steps, one feedback gradient"}
         print(json.dumps(line), flush=True)
     prob.close()
     if dist is not None:

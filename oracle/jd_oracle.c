@@ -803,6 +803,7 @@ static void *fb_worker(void *arg) {
 
 static int fb_sweep(const orc_problem *P, const orc_feedback *F, const double *mu, int nthreads,
                     double *J, double *grad) {
+  if (F && F->particles > 0) return orc_fb_coupled_gradient(P, F, mu, nthreads, J, grad);   /* Sec. 6.4 */
   if (!fb_valid(P, F) || !mu) return 1;
   const size_t n = (size_t)P->Nt * F->nx * F->nv;
   fb_job job;

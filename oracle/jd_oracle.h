@@ -179,7 +179,8 @@ double orc_fb_control(const orc_feedback *F, const double *mu_k, const double *z
 void orc_fb_surrogate_state(const orc_problem *P, const orc_feedback *F, int k, int64_t m, double zs[2]);
 int orc_fb_path(const orc_problem *P, const orc_feedback *F, const double *mu, int64_t m,
                 double *X, double *lam, double *G, double *cost, int *njumps);
-/* J(mu) and dJ/dmu (Nt*L, nullable), fixed summation order. */
+/* J(mu) and dJ/dmu (Nt*L, nullable), fixed summation order; with F->particles > 0 the
+ * interacting-particle rings (orc_fb_coupled_gradient). */
 int orc_fb_cost(const orc_problem *P, const orc_feedback *F, const double *mu, int nthreads,
                 double *J);
 int orc_fb_gradient(const orc_problem *P, const orc_feedback *F, const double *mu, int nthreads,

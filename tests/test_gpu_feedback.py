@@ -195,3 +195,18 @@ def test_coupled_particles_parity(N, prec):
         assert eJ <= 1e-13 and eg <= 1e-12
     else:
         assert eJ <= 1e-6 and eg <= 1e-5
+
+
+def test_coupled_optimizer_follows_the_oracle():
+    """Algorithm 5.4 on the shared weights of the coupled rings (FP64): the oracle's iterate
+    sequence, J history within 1e-10."""
+    p, fb = workloads.feedback_coupled(M=32 * 12, Nt=20, particles=8)
+    p = p.replace(lam=4.0)
+    muo, ro, ho = oracle.fb_optimize(p, fb, max_iter=5)
+    with JdProblem(p, prec="fp64") as jp:
+        mu, r, h = jp.fb_optimize(fb, max_iter=5)
+    print("coupled optimizer", r, ro)
+    assert r["iters"] == ro["iters"] and r["evals"] == ro["evals"]
+    assert np.max(np.abs(h - ho) / np.abs(ho)) <= 1e-10
+    assert np.max(np.abs(mu - muo)) <= 1e-9 * np.max(np.abs(muo))
+    assert h[-1] < h[0]
