@@ -199,6 +199,12 @@ typedef struct {
   int max_iter;
   double tol_rel_grad, tol_step, armijo_c, zeta0, zeta_max;
   int max_backtracks;
+  int resample;   /* 0: one fixed sample (sample average approximation).  1: the stochastic
+                     descent of Sec. 5.6 / Algorithm 5.4 with fresh random data every
+                     iteration: iteration n evaluates its gradient and its Armijo trials on
+                     epoch desc.epoch + n; J_hist[n] is J(u^n) on sample n, the last entry
+                     the accepted trial's cost on the last iteration's sample; the problem's
+                     epoch is restored when the call returns */
 } jd_opt_params;
 
 typedef struct {

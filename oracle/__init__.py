@@ -90,7 +90,7 @@ class _OptParams(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int), ("tol_rel_grad", ctypes.c_double),
                 ("tol_step", ctypes.c_double), ("armijo_c", ctypes.c_double),
                 ("zeta0", ctypes.c_double), ("zeta_max", ctypes.c_double),
-                ("max_backtracks", ctypes.c_int)]
+                ("max_backtracks", ctypes.c_int), ("resample", ctypes.c_int)]
 
 
 class _OptResult(ctypes.Structure):
@@ -254,13 +254,13 @@ def gradient(p, u=None, nthreads: int | None = None, theta: bool = False):
 
 
 def optimize(p, u0=None, max_iter=50, tol_rel_grad=1e-4, tol_step=0.0, armijo_c=1e-4,
-             zeta0=1.0, zeta_max=1e3, max_backtracks=40, nthreads=None):
+             zeta0=1.0, zeta_max=1e3, max_backtracks=40, nthreads=None, resample=False):
     """Projected-gradient Armijo descent; returns (u, result dict, J history)."""
     op = OracleProblem(p)
     u = op._u(u0).copy()
     o = _OptParams(max_iter=max_iter, tol_rel_grad=tol_rel_grad, tol_step=tol_step,
                    armijo_c=armijo_c, zeta0=zeta0, zeta_max=zeta_max,
-                   max_backtracks=max_backtracks)
+                   max_backtracks=max_backtracks, resample=int(resample))
     r = _OptResult()
     hist = np.full(max_iter + 2, np.nan)
     lib().orc_optimize(ctypes.byref(op.s), _ptr(u), ctypes.byref(o), nthreads or default_threads(),
@@ -343,13 +343,14 @@ def fb_gradient(p, fb, mu=None, nthreads: int | None = None):
 
 
 def fb_optimize(p, fb, mu0=None, max_iter=20, tol_rel_grad=1e-4, tol_step=0.0, armijo_c=1e-4,
-                zeta0=1.0, zeta_max=1e3, max_backtracks=40, nthreads=None):
+                zeta0=1.0, zeta_max=1e3, max_backtracks=40, nthreads=None, resample=False):
     """Armijo gradient descent on the feedback weights; returns (mu, result dict, J history)."""
     op = OracleProblem(p)
     F = _fb(fb)
     mu = _mu(p, fb, mu0).copy()
     o = _OptParams(max_iter=max_iter, tol_rel_grad=tol_rel_grad, tol_step=tol_step,
-                   armijo_c=armijo_c, zeta0=zeta0, zeta_max=zeta_max, max_backtracks=max_backtracks)
+                   armijo_c=armijo_c, zeta0=zeta0, zeta_max=zeta_max, max_backtracks=max_backtracks,
+                   resample=int(resample))
     r = _OptResult()
     hist = np.full(max_iter + 2, np.nan)
     lib().orc_fb_optimize(ctypes.byref(op.s), ctypes.byref(F), _ptr(mu), ctypes.byref(o),

@@ -456,8 +456,10 @@ int orc_optimize(const orc_problem *P, double *u, const orc_opt_params *o, int n
   /* Algorithm 5.4: while not converged and n < n_max: gradient at u^n, Armijo step
    * size, update, step-norm test.  The projected-gradient test (relative to the first
    * iterate) is checked when the gradient is available, at the top of the loop. */
+  orc_problem Pn = *P;   /* the sample of iteration it: epoch P->epoch + it when resampling */
   for (it = 0; it < o->max_iter; ++it) {
-    int rc = orc_gradient(P, u, nthreads, &J, grad, NULL);
+    if (o->resample) Pn.epoch = P->epoch + (uint32_t)it;
+    int rc = orc_gradient(&Pn, u, nthreads, &J, grad, NULL);
     r->evals++;
     if (rc) { status = 1; break; }
     if (J_hist) J_hist[it] = J;
@@ -483,7 +485,7 @@ int orc_optimize(const orc_problem *P, double *u, const orc_opt_params *o, int n
         ut[t] = clip(u[t] - zeta * g[t], P->u_min, P->u_max);
         dot += dt * g[t] * (ut[t] - u[t]);
       }
-      rc = orc_cost(P, ut, nthreads, &Jt);
+      rc = orc_cost(&Pn, ut, nthreads, &Jt);
       r->evals++;
       if (rc) { status = 1; break; }
       if (Jt <= J + o->armijo_c * dot) { accepted = 1; break; }
@@ -862,8 +864,10 @@ int orc_fb_optimize(const orc_problem *P, const orc_feedback *F, double *mu, con
   double J = 0.0, pg0 = -1.0, zeta = o->zeta0 > 0 ? o->zeta0 : 1.0;
   double zeta_max = o->zeta_max > 0 ? o->zeta_max : 1e3;
   int status = 0, it = 0;
+  orc_problem Pn = *P;   /* the sample of iteration it: epoch P->epoch + it when resampling */
   for (it = 0; it < o->max_iter; ++it) {
-    int rc = orc_fb_gradient(P, F, mu, nthreads, &J, grad);
+    if (o->resample) Pn.epoch = P->epoch + (uint32_t)it;
+    int rc = orc_fb_gradient(&Pn, F, mu, nthreads, &J, grad);
     r->evals++;
     if (rc) { status = 1; break; }
     if (J_hist) J_hist[it] = J;
@@ -878,7 +882,7 @@ int orc_fb_optimize(const orc_problem *P, const orc_feedback *F, double *mu, con
     double Jt = 0.0;
     for (int b = 0; b <= o->max_backtracks; ++b) {
       for (size_t t = 0; t < n; ++t) mt[t] = mu[t] - zeta * (grad[t] / dt);
-      rc = orc_fb_cost(P, F, mt, nthreads, &Jt);
+      rc = orc_fb_cost(&Pn, F, mt, nthreads, &Jt);
       r->evals++;
       if (rc) { status = 1; break; }
       if (Jt <= J - o->armijo_c * zeta * g2) { accepted = 1; break; }

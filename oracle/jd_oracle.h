@@ -121,6 +121,7 @@ typedef struct {
   int max_iter;
   double tol_rel_grad, tol_step, armijo_c, zeta0, zeta_max;
   int max_backtracks;
+  int resample;   /* 1: iteration n draws a fresh sample, epoch = P->epoch + n (Sec. 5.6 SGD) */
 } orc_opt_params;
 
 typedef struct {

@@ -82,7 +82,7 @@ class OptParams(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int), ("tol_rel_grad", ctypes.c_double),
                 ("tol_step", ctypes.c_double), ("armijo_c", ctypes.c_double),
                 ("zeta0", ctypes.c_double), ("zeta_max", ctypes.c_double),
-                ("max_backtracks", ctypes.c_int)]
+                ("max_backtracks", ctypes.c_int), ("resample", ctypes.c_int)]
 
 
 class OptResult(ctypes.Structure):
@@ -396,12 +396,12 @@ class JdProblem:
         return J.value, g
 
     def fb_optimize(self, fb, mu0=None, max_iter=20, tol_rel_grad=1e-4, tol_step=0.0, armijo_c=1e-4,
-                    zeta0=1.0, zeta_max=1e3, max_backtracks=40):
+                    zeta0=1.0, zeta_max=1e3, max_backtracks=40, resample=False):
         """Armijo descent on the feedback weights: (mu (Nt, L) numpy, result dict, J history)."""
         L = fb.nx * fb.nv
         mu = np.zeros((self.Nt, L)) if mu0 is None else _f64(mu0).reshape(self.Nt, L).copy()
         o = OptParams(max_iter=max_iter, tol_rel_grad=tol_rel_grad, tol_step=tol_step, armijo_c=armijo_c,
-                      zeta0=zeta0, zeta_max=zeta_max, max_backtracks=max_backtracks)
+                      zeta0=zeta0, zeta_max=zeta_max, max_backtracks=max_backtracks, resample=int(resample))
         r = OptResult()
         hist = np.full(max_iter + 1, np.nan)
         F = make_feedback(fb)
@@ -423,11 +423,12 @@ class JdProblem:
         return X, L, c
 
     def optimize(self, u0=None, max_iter=50, tol_rel_grad=1e-4, tol_step=0.0, armijo_c=1e-4,
-                 zeta0=1.0, zeta_max=1e3, max_backtracks=40, raise_on_error=True):
+                 zeta0=1.0, zeta_max=1e3, max_backtracks=40, raise_on_error=True, resample=False):
         """Projected-gradient Armijo descent (jd_optimize); returns (u, result dict, J history)."""
         u = np.zeros((self.Nt, self.du)) if u0 is None else _f64(u0).reshape(self.Nt, self.du).copy()
         o = OptParams(max_iter=max_iter, tol_rel_grad=tol_rel_grad, tol_step=tol_step,
-                      armijo_c=armijo_c, zeta0=zeta0, zeta_max=zeta_max, max_backtracks=max_backtracks)
+                      armijo_c=armijo_c, zeta0=zeta0, zeta_max=zeta_max, max_backtracks=max_backtracks,
+                      resample=int(resample))
         r = OptResult()
         hist = np.full(max_iter + 2, np.nan)
         st = lib().jd_optimize(self.h, _ptr(u), JD_MEM_HOST, ctypes.byref(o), ctypes.byref(r), _ptr(hist))

@@ -724,6 +724,7 @@ static jd_status run_phase(jd::OptMachine &m, cudaGraphExec_t *exec, int *nlaunc
 static jd_status launch_grad(jd::OptMachine &m) {
   const int v = m.forward_done ? 1 : 0;
   jd_problem *p = m.p;
+  if (m.o.resample) p->desc.epoch = m.epoch0 + (uint32_t)m.it;   // fresh sample per iteration
   const jd_status s = run_phase(m, &m.g_grad[v], &m.n_grad[v], [&]() { return enqueue_grad(p, v == 1); });
   if (s) return s;
   m.forward_done = false;
@@ -754,6 +755,7 @@ void jd::opt_release(OptMachine &m) {
 // Final iterate to the caller's buffer.
 static jd_status launch_output(jd::OptMachine &m, jd_status status) {
   jd_problem *p = m.p;
+  p->desc.epoch = m.epoch0;
   m.r.iters = m.it;
   m.r.zeta = m.zeta;
   m.r.status = status;
@@ -782,6 +784,8 @@ jd_status jd::opt_begin(OptMachine &m, jd_problem *p, const jd_opt_params &o, do
   m.zeta_max = o.zeta_max > 0.0 ? o.zeta_max : 1e3;
   m.pg0 = -1.0;
   m.forward_done = false;
+  m.epoch0 = p->desc.epoch;
+  if (o.resample) m.use_graphs = false;   // every iteration's launches carry a new epoch
   const size_t n = (size_t)p->desc.Nt * p->desc.du;
   if (m.use_graphs) {
     // graphs hold fixed launches: not for the d = 32 kernels (their coefficient upload
@@ -820,7 +824,7 @@ jd_status jd::opt_advance(OptMachine &m) {
     }
     case OptMachine::TRIAL: {
       if (h[S_ACC] != 0.0) {
-        m.forward_done = true;
+        m.forward_done = !m.o.resample;   // the trial's sweep is the next gradient's forward
         const double step2 = h[S_STEP];
         m.r.J = h[S_J];
         if (m.J_hist) m.J_hist[m.it + 1] = m.r.J;
@@ -1506,7 +1510,14 @@ jd_status jd_fb_optimize(jd_problem *p, const jd_feedback_desc *fb, double *mu_i
   double J = 0.0, pg0 = -1.0, zeta = o->zeta0 > 0 ? o->zeta0 : 1.0;
   const double zeta_max = o->zeta_max > 0 ? o->zeta_max : 1e3;
   int status = 0, it = 0;
+  const uint32_t epoch0 = p->desc.epoch;
+  struct EpochBack {   // the problem's sample is restored on every way out
+    jd_problem *p;
+    uint32_t e;
+    ~EpochBack() { p->desc.epoch = e; }
+  } epoch_back{p, epoch0};
   for (it = 0; it < o->max_iter; ++it) {
+    if (o->resample) p->desc.epoch = epoch0 + (uint32_t)it;   // fresh sample per iteration
     s = fb_run(p, fb, p->fb_mu64, JD_MEM_DEVICE, p->fb_grad);
     if (!s) JD_CUDA(fb_norm(p->fb_grad, n, dt, p->scal_d + S_PG, p->stream));
     if (!s) s = read_scalars(p, S_J, S_PG + 1);

@@ -208,6 +208,7 @@ struct OptMachine {
   int it = 0, backtracks = 0, grads = 0;
   double zeta = 1.0, zeta_max = 1e3, pg0 = -1.0;
   bool forward_done = false;
+  uint32_t epoch0 = 0;   // the problem's epoch; resampling uses epoch0 + it
   // CUDA graphs: each phase's launch sequence is captured on first use and replayed
   // (gradient with and without the forward sweep, trial); kernels per graph counted
   bool use_graphs = false;

@@ -210,3 +210,14 @@ def test_coupled_optimizer_follows_the_oracle():
     assert np.max(np.abs(h - ho) / np.abs(ho)) <= 1e-10
     assert np.max(np.abs(mu - muo)) <= 1e-9 * np.max(np.abs(muo))
     assert h[-1] < h[0]
+
+
+def test_feedback_resampling_descent_follows_the_oracle():
+    p, fb = workloads.feedback_centering(M=500, Nt=15)
+    p = p.replace(lam=6.0, epoch=2)
+    muo, ro, ho = oracle.fb_optimize(p, fb, max_iter=5, resample=True)
+    with JdProblem(p, prec="fp64") as jp:
+        mu, r, h = jp.fb_optimize(fb, max_iter=5, resample=True)
+    assert r["iters"] == ro["iters"] and r["evals"] == ro["evals"]
+    assert np.max(np.abs(h - ho) / np.abs(ho)) <= 1e-10
+    assert np.max(np.abs(mu - muo)) <= 1e-9 * np.max(np.abs(muo))

@@ -48,3 +48,19 @@ def test_optimizer_reports_linesearch_failure():
         u, r, h = jp.optimize(max_iter=3, tol_rel_grad=0.0, armijo_c=5.0, max_backtracks=3,
                               raise_on_error=False)
     assert r["status"] == 5
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+def test_resampling_descent_follows_the_oracle(prec, tol):
+    """Per-iteration resampling (Sec. 5.6): iteration n on epoch e0 + n, for the gradient
+    and its Armijo trials; the GPU takes the oracle's iterates, and the problem's epoch is
+    unchanged afterwards (the same cost before and after the run)."""
+    p = workloads.lq_scalar(M=1000, Nt=50).replace(epoch=3)
+    uo, ro, ho = oracle.optimize(p, max_iter=8, resample=True)
+    with JdProblem(p, prec=prec) as jp:
+        J0 = jp.cost(np.zeros((p.Nt, p.du)))
+        u, r, h = jp.optimize(max_iter=8, resample=True)
+        assert jp.cost(np.zeros((p.Nt, p.du))) == J0
+    assert r["iters"] == ro["iters"] and r["evals"] == ro["evals"]
+    assert np.max(np.abs(h - ho) / np.abs(ho)) <= tol
+    assert np.max(np.abs(u - uo)) <= 10 * tol * max(1.0, np.max(np.abs(uo)))

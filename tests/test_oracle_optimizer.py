@@ -51,3 +51,28 @@ def test_discrete_optimum_approaches_continuous_lq_optimum():
         errs.append(np.sqrt(np.mean((u.ravel() - cells) ** 2)) / np.sqrt(np.mean(cells ** 2)))
     assert errs[1] < errs[0]
     assert errs[1] < 0.1
+
+
+# --- per-iteration resampling (Sec. 5.6 SGD, Algorithm 5.4 with fresh samples) -----------
+def test_resampling_without_randomness_is_the_fixed_sample_descent():
+    """No noise and no jumps: every sample is the same, so the resampled descent takes the
+    fixed-sample iterates exactly."""
+    p = workloads.lq_scalar(M=64, Nt=30).replace(sigma=np.array([0.0]), lam=0.0)
+    u1, r1, h1 = oracle.optimize(p, max_iter=6)
+    u2, r2, h2 = oracle.optimize(p, max_iter=6, resample=True)
+    assert np.array_equal(h1, h2) and np.array_equal(u1, u2)
+
+
+def test_resampling_uses_the_sample_of_each_iteration():
+    """Iteration n evaluates its gradient and its Armijo trials on epoch e0 + n: J_hist[n] is
+    the cost of u^n on sample e0 + n, and the last entry the accepted trial's cost of u^{N}
+    on the sample of the last iteration, e0 + N - 1."""
+    p = workloads.lq_scalar(M=300, Nt=30).replace(epoch=5)
+    us = [oracle.optimize(p, max_iter=n, resample=True)[0] for n in range(4)]
+    _, r, h = oracle.optimize(p, max_iter=3, resample=True)
+    assert r["iters"] == 3
+    for n in range(3):
+        assert h[n] == oracle.cost(p.replace(epoch=5 + n), us[n])
+    assert h[3] == oracle.cost(p.replace(epoch=7), us[3]) == r["J"]
+    # and the samples differ: the fixed-sample descent takes other iterates
+    assert not np.array_equal(oracle.optimize(p, max_iter=3)[2], h)
