@@ -675,7 +675,7 @@ def adjoint_ops(p):
 # DRAM bytes (read + write) per path-step of the d = 2 kernels from one ncu capture
 # (profiles/fwd_store_adj_stored_double_well_d2_M2p16_Nt1000.md: M = 2^16, N_t = 1000,
 # scaled per path-step); set to None whenever a kernel changes after its capture.
-TRAFFIC_PER_PATH_STEP = {"fwd_store": 7.68, "adj_stored": 8.86}
+TRAFFIC_PER_PATH_STEP = {"fwd_store": 7.68, "adj_stored": 8.89}
 
 
 def kernel_roofline(name, stat, p, peaks, peak_kind, tc=0):

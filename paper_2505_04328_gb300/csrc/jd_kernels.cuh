@@ -534,7 +534,9 @@ __device__ __forceinline__ void finish_theta(const KParams<R, D, DU> &kp, R (&th
   }
 }
 
-template <typename R, int D, int DU, bool THETA>
+// LAM: write the adjoint states to lam_out (jd_sample_paths); a compile-time switch, since
+// a run-time test leaves its stores and their address arithmetic in every step.
+template <typename R, int D, int DU, bool THETA, bool LAM = false>
 __global__ void __launch_bounds__(TPB)
 adj_stored_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u,
                   const R *__restrict__ xd, const R *__restrict__ traj,
@@ -563,7 +565,7 @@ adj_stored_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restr
     load_state<R, D>(traj, Nt, mloc, lmc, x);
 #pragma unroll
     for (int c = 0; c < D; ++c) mu[c] = M::mul(kp.qdt[c], M::sub(x[c], __ldg(xd + (size_t)Nt * D + c)));
-    if (lam_out && active)
+    if (LAM && active)
 #pragma unroll
       for (int c = 0; c < D; ++c) lam_out[((size_t)Nt * D + c) * mloc + lm] = mu[c];
   }
@@ -600,7 +602,7 @@ adj_stored_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restr
       for (int l = 0; l < DU; ++l) g[l] = R(0);
       if (k < Nt) {
         backward_step<R, D, DU, THETA>(kp, k, m, (fw >> (k & 31)) & 1u, xs[j], u, xd, mu, g, th, lr);
-        if (lam_out && active)
+        if (LAM && active)
 #pragma unroll
           for (int c = 0; c < D; ++c) lam_out[((size_t)k * D + c) * mloc + lm] = mu[c];
       }
@@ -850,9 +852,12 @@ cudaError_t op_adj(const jd_problem *p, int variant, bool theta, int64_t m_begin
     if (theta)
       adj_stored_kernel<R, D, DU, true><<<grid, TPB, 0, s>>>(*kp, u, xd, tr, b.flags, jl, b.jcnt, b.partG,
                                                              b.partT, lo, mloc);
+    else if (lo)
+      adj_stored_kernel<R, D, DU, false, true><<<grid, TPB, 0, s>>>(*kp, u, xd, tr, b.flags, jl, b.jcnt, b.partG,
+                                                                    b.partT, lo, mloc);
     else
       adj_stored_kernel<R, D, DU, false><<<grid, TPB, 0, s>>>(*kp, u, xd, tr, b.flags, jl, b.jcnt, b.partG,
-                                                              b.partT, lo, mloc);
+                                                              b.partT, nullptr, mloc);
   } else {
     const size_t smem = recompute_smem<R, D, DU>(theta);
     const R *ck = static_cast<const R *>(b.ckpt);
@@ -880,6 +885,7 @@ size_t op_stack_bytes() {
   const void *ks[] = {
       (const void *)fwd_kernel<R, D, DU, FWD_COST>, (const void *)fwd_kernel<R, D, DU, FWD_STORE>,
       (const void *)fwd_kernel<R, D, DU, FWD_CKPT>, (const void *)adj_stored_kernel<R, D, DU, false>,
+      (const void *)adj_stored_kernel<R, D, DU, false, true>,
       (const void *)adj_stored_kernel<R, D, DU, true>, (const void *)adj_recompute_kernel<R, D, DU, false>,
       (const void *)adj_recompute_kernel<R, D, DU, true>};
   for (const void *k : ks) {
