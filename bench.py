@@ -394,6 +394,9 @@ def run_feedback(args, p, stream, dist, ws, rank, local):
                         "peak_source": "derived: 152 SMs x 4 schedulers x 32 lanes x 1 instruction/clock x "
                                        f"{sm_mhz:.0f} MHz (max SM clock)",
                         "algorithmic_ops_per_path_step": ops}
+            iss = issue_fraction(args.workload, name, M * Nt, total_ms / launches_k * 1e-3, peaks)
+            if iss and fb.adjoint == workloads.FB_EXACT:
+                rl[name]["issue"] = iss
     dom = max(rl, key=lambda k: kstats[k][1]) if rl else None
     if rank == 0:
         line = {
@@ -677,6 +680,25 @@ def adjoint_ops(p):
 # scaled per path-step); set to None whenever a kernel changes after its capture.
 TRAFFIC_PER_PATH_STEP = {"fwd_store": 7.68, "adj_stored": 8.89}
 
+# Warp-instructions issued per warp-step (32 path-steps) from the same kind of ncu capture
+# (smsp__inst_executed.sum / warp-steps; profiles/*.md): with the measured time they give
+# the fraction of the SM's issue rate (4 schedulers x 1 instruction per clock) the kernel
+# uses, next to the algorithmic fraction; None when the kernel changed since the capture.
+INST_PER_WARP_STEP = {("double_well", "fwd_store"): 286, ("double_well", "adj_stored"): 111,
+                      ("double_well", "adj_recompute"): 352, ("feedback_centering", "fb_fwd"): 830,
+                      ("feedback_centering", "fb_adj"): 1224}
+
+
+def issue_fraction(workload, name, units, per_launch_s, peaks):
+    n = INST_PER_WARP_STEP.get((workload, name))
+    if n is None:
+        return None
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak = 152 * 4 * sm_mhz * 1e6
+    achieved = n * units / 32 / per_launch_s
+    return {"inst_per_warp_step": n, "achieved_warp_inst_per_s": achieved, "peak_warp_inst_per_s": peak,
+            "frac": achieved / peak, "source": "ncu smsp__inst_executed.sum of a small case of the same kernel"}
+
 
 def kernel_roofline(name, stat, p, peaks, peak_kind, tc=0):
     launches, total_ms = stat
@@ -688,11 +710,15 @@ def kernel_roofline(name, stat, p, peaks, peak_kind, tc=0):
         bytes_per = 4 * p.d + 0.125 + p.lam * p.dt * (2 + p.d) * 4
         achieved = bytes_per * units / per_launch_s / 1e9
         peak = peaks.get("hbm_gbs", 6800.0)
-        return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
-                else "fallback 6.8 TB/s",
-                "algorithmic_bytes_per_path_step": bytes_per}
+        out = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+               "frac": achieved / peak, "traffic": traffic,
+               "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+               else "fallback 6.8 TB/s",
+               "algorithmic_bytes_per_path_step": bytes_per}
+        iss = issue_fraction(p.name, name, units, per_launch_s, peaks)
+        if iss:
+            out["issue"] = iss
+        return out
     ops = forward_ops(p, tc) + (adjoint_ops(p) if name == "adj_recompute" else 0.0)
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     peak = 152 * 4 * 32 * sm_mhz * 1e6 / 1e9   # G lane-operations per second
@@ -705,6 +731,9 @@ def kernel_roofline(name, stat, p, peaks, peak_kind, tc=0):
     if tc:
         flops = 2.0 * p.d * p.d * (3 if tc == 2 else 1) * units
         out["tensor_tflops"] = flops / per_launch_s / 1e12
+    iss = issue_fraction(p.name, name, units, per_launch_s, peaks)
+    if iss:
+        out["issue"] = iss
     return out
 
 
