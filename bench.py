@@ -649,7 +649,7 @@ def optimize_device(prob, u_t, iters, zeta0):
     return dict(iters=r.iters, evals=r.evals, J=r.J, zeta=r.zeta)
 
 
-# Algorithmic work per path-step (derivation in the design doc, section 9).  Forward sweeps
+# Algorithmic work per path-step.  Forward sweeps
 # are bound by issue slots (lane-operations): Philox blocks x 40 (20 wide multiplies,
 # 20 XORs), 3 per uniform, 7 per Box-Muller pair, the drift's multiply-adds (the A x
 # contraction leaves the CUDA cores when it runs on tensor cores), 2 d for the Euler
