@@ -262,7 +262,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     u_host, r2, _ = prob.optimize(u_host, max_iter=args.steps, tol_rel_grad=0.0, zeta0=zeta)
     e2e_sec = (time.perf_counter() - t0) / args.steps
-    trials = (r2["evals"] - args.steps) / args.steps
+    trials = (r2["sweeps"] - 1) / args.steps   # trial phases (a pair is one); the first gradient's sweep
     e2e = {"value": ws * M * Nt / e2e_sec, "unit": UNIT,
            "h2d_bytes_per_step": n * 8 / args.steps,
            "d2h_bytes_per_step": n * 8 / args.steps + 64 * (1 + trials)}
@@ -282,6 +282,7 @@ def run_ours(args):
                        "tensor_cores": {0: "off", 1: "bf16", 2: "bf16x3"}[args.tc],
                        "variant": prob.info()["mode"], "paths_per_gpu": M, "Nt": Nt,
                        "evals_per_step": evals / args.steps,
+                       "sweeps_per_step": r["sweeps"] / args.steps,
                        "step": "one projected-gradient Armijo iteration (gradient, line search, "
                                "update) inside one jd_optimize call",
                        "l2": "inputs larger than L2: the %s buffers (%.2f GB) exceed the 129 MB "
@@ -646,7 +647,7 @@ def optimize_device(prob, u_t, iters, zeta0):
     st = b.lib().jd_optimize(prob.h, ctypes.c_void_p(u_t.data_ptr()), b.JD_MEM_DEVICE,
                              ctypes.byref(o), ctypes.byref(r), None)
     b._check(st, "jd_optimize")
-    return dict(iters=r.iters, evals=r.evals, J=r.J, zeta=r.zeta)
+    return dict(iters=r.iters, evals=r.evals, J=r.J, zeta=r.zeta, sweeps=r.sweeps)
 
 
 # Algorithmic work per path-step.  Forward sweeps
@@ -655,18 +656,21 @@ def optimize_device(prob, u_t, iters, zeta0):
 # contraction leaves the CUDA cores when it runs on tensor cores), 2 d for the Euler
 # update, 3 d + 4 for the running cost, and lambda dt times the cost of a jump.  The
 # stored adjoint is bound by HBM: state (4 d bytes), jump-flag bit, jump log.
-KERNEL_BOUND = {"fwd_cost": "alu", "fwd_store": "alu", "fwd_ckpt": "alu", "adj_stored": "hbm",
-                "adj_recompute": "alu"}
+KERNEL_BOUND = {"fwd_cost": "alu", "fwd_store": "alu", "fwd_ckpt": "alu", "fwd_pair": "alu",
+                "adj_stored": "hbm", "adj_recompute": "alu"}
 
 
-def forward_ops(p, tc=0):
+def forward_ops(p, tc=0, controls=1):
+    """controls = 2: the paired sweep of two Armijo trials, which draws once and runs the
+    drift, Euler update, cost and jump sub-steps once per control."""
     d, du = p.d, p.du
     P = (d + 1) // 2
     blocks = (1 + 2 * P + 3) // 4
     drift = (0 if tc else d * d) + d * du + (d * d + 2 * d if p.drift == workloads.CUBIC else 0)
-    base = 40 * blocks + 3 * 2 * P + 7 * P + 1 + drift + 2 * d + 3 * d + 4
+    draws = 40 * blocks + 3 * 2 * P + 7 * P + 1
+    base = draws + controls * (drift + 2 * d + 3 * d + 4)
     slot_blocks = (1 + 4 * P + 3) // 4
-    per_jump = 40 * slot_blocks + 3 * 4 * P + 7 * 2 * P + 2 * (d * d + d * du + 2 * d)
+    per_jump = 40 * slot_blocks + 3 * 4 * P + 7 * 2 * P + controls * 2 * (d * d + d * du + 2 * d)
     return base + p.lam * p.dt * per_jump
 
 
@@ -719,7 +723,7 @@ def kernel_roofline(name, stat, p, peaks, peak_kind, tc=0):
         if iss:
             out["issue"] = iss
         return out
-    ops = forward_ops(p, tc) + (adjoint_ops(p) if name == "adj_recompute" else 0.0)
+    ops = forward_ops(p, tc, 2 if name == "fwd_pair" else 1) + (adjoint_ops(p) if name == "adj_recompute" else 0.0)
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     peak = 152 * 4 * 32 * sm_mhz * 1e6 / 1e9   # G lane-operations per second
     achieved = ops * units / per_launch_s / 1e9

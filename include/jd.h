@@ -194,7 +194,16 @@ jd_status jd_sample_paths(jd_problem *p, const double *u, jd_memspace us, int64_
  * is evaluated), when |u+ - u|_{L2} < tol_step, or after max_iter updates.  The Armijo
  * test and every FP64 reduction run on the device; the host only reads the accept flag.
  * r->iters = updates done, r->evals = gradient + cost evaluations, r->zeta = last
- * accepted step (pass 2*zeta as zeta0 to continue an interrupted run). */
+ * accepted step (pass 2*zeta as zeta0 to continue an interrupted run).
+ * Paired trials: for an iteration's first trial (unless the last two iterations took
+ * their first point) the trial point zeta and its backtrack zeta/2 are evaluated in
+ * one forward sweep on the same
+ * random data (both controls share the draws; each state's arithmetic is that of a
+ * sweep of its control alone) and tested in backtracking order, so iterates, J values,
+ * zeta and r->evals are those of one trial per sweep; r->sweeps counts the forward
+ * sweeps run (a pair counts one).  Needs a second set of the plan's path buffers within
+ * the memory budget (else one trial per sweep); not with the block-wise stored plan,
+ * d > 8 or the server's requests. */
 typedef struct {
   int max_iter;
   double tol_rel_grad, tol_step, armijo_c, zeta0, zeta_max;
@@ -205,12 +214,14 @@ typedef struct {
                      epoch desc.epoch + n; J_hist[n] is J(u^n) on sample n, the last entry
                      the accepted trial's cost on the last iteration's sample; the problem's
                      epoch is restored when the call returns */
+  int one_trial_per_sweep;   /* 0: paired trials where available (above); 1: never */
 } jd_opt_params;
 
 typedef struct {
   int iters, evals;
   double J, rel_grad_norm, zeta;
   jd_status status;
+  int sweeps;   /* forward sweeps run (gradients with their own forward, trials, pairs) */
 } jd_opt_result;
 
 /* u_inout: Nt*du in memory space us, updated in place.  J_hist: host, max_iter+1

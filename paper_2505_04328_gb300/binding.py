@@ -82,13 +82,14 @@ class OptParams(ctypes.Structure):
     _fields_ = [("max_iter", ctypes.c_int), ("tol_rel_grad", ctypes.c_double),
                 ("tol_step", ctypes.c_double), ("armijo_c", ctypes.c_double),
                 ("zeta0", ctypes.c_double), ("zeta_max", ctypes.c_double),
-                ("max_backtracks", ctypes.c_int), ("resample", ctypes.c_int)]
+                ("max_backtracks", ctypes.c_int), ("resample", ctypes.c_int),
+                ("one_trial_per_sweep", ctypes.c_int)]
 
 
 class OptResult(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("evals", ctypes.c_int), ("J", ctypes.c_double),
                 ("rel_grad_norm", ctypes.c_double), ("zeta", ctypes.c_double),
-                ("status", ctypes.c_int)]
+                ("status", ctypes.c_int), ("sweeps", ctypes.c_int)]
 
 
 class RequestInfo(ctypes.Structure):
@@ -423,19 +424,21 @@ class JdProblem:
         return X, L, c
 
     def optimize(self, u0=None, max_iter=50, tol_rel_grad=1e-4, tol_step=0.0, armijo_c=1e-4,
-                 zeta0=1.0, zeta_max=1e3, max_backtracks=40, raise_on_error=True, resample=False):
-        """Projected-gradient Armijo descent (jd_optimize); returns (u, result dict, J history)."""
+                 zeta0=1.0, zeta_max=1e3, max_backtracks=40, raise_on_error=True, resample=False,
+                 pairs=True):
+        """Projected-gradient Armijo descent (jd_optimize); returns (u, result dict, J history).
+        ``pairs``: paired Armijo trials in one sweep where memory allows (same iterates)."""
         u = np.zeros((self.Nt, self.du)) if u0 is None else _f64(u0).reshape(self.Nt, self.du).copy()
         o = OptParams(max_iter=max_iter, tol_rel_grad=tol_rel_grad, tol_step=tol_step,
                       armijo_c=armijo_c, zeta0=zeta0, zeta_max=zeta_max, max_backtracks=max_backtracks,
-                      resample=int(resample))
+                      resample=int(resample), one_trial_per_sweep=int(not pairs))
         r = OptResult()
         hist = np.full(max_iter + 2, np.nan)
         st = lib().jd_optimize(self.h, _ptr(u), JD_MEM_HOST, ctypes.byref(o), ctypes.byref(r), _ptr(hist))
         if raise_on_error:
             _check(st, "jd_optimize")
         res = dict(iters=r.iters, evals=r.evals, status=r.status, J=r.J,
-                   rel_grad_norm=r.rel_grad_norm, zeta=r.zeta)
+                   rel_grad_norm=r.rel_grad_norm, zeta=r.zeta, sweeps=r.sweeps)
         return u, res, hist[: r.iters + 1]
 
     def info(self):

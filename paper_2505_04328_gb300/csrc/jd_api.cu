@@ -25,10 +25,11 @@ void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_r
 // launching stream, summed on read.
 enum KernelClass { KC_FWD_COST, KC_FWD_STORE, KC_FWD_CKPT, KC_ADJ_STORED, KC_ADJ_RECOMPUTE,
                    KC_FINALIZE, KC_PREP, KC_OPT, KC_FB_FWD, KC_FB_ADJ, KC_FB_SUR, KC_FB_RED, KC_FB_FIN,
-                   KC_COUNT };
+                   KC_FWD_PAIR, KC_COUNT };
 static const char *kKernelClassName[KC_COUNT] = {"fwd_cost", "fwd_store", "fwd_ckpt", "adj_stored",
                                                  "adj_recompute", "finalize", "prep_u", "opt_step",
-                                                 "fb_fwd", "fb_adj", "fb_sur", "fb_reduce", "fb_finalize"};
+                                                 "fb_fwd", "fb_adj", "fb_sur", "fb_reduce", "fb_finalize",
+                                                 "fwd_pair"};
 struct ProfRec {
   int kind;
   cudaEvent_t a, b;
@@ -117,6 +118,11 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+
+// Scalar slots in p->scal_d
+enum { S_J = 0, S_JT = 1, S_DOT = 2, S_PG = 3, S_ACC = 4, S_STEP = 5, S_STATUS = 6, S_BAD = 7, S_THETA = 8,
+       S_ZETA = 42, S_JT2 = 44, S_DOT2 = 45 };
+constexpr int NSCAL = kScalars;
 
 // Block-wide FP64 sum (blockDim.x == 256) in a fixed tree; result in every thread.
 __device__ double block_sum_d(double v, double *sm) {
@@ -207,42 +213,55 @@ __global__ void opt_pgnorm_kernel(int n, const double *__restrict__ u, const dou
   if (threadIdx.x == 0) *out = sqrt(a);
 }
 
-// Trial point ut = clip(u - zeta g) and <g, ut - u>_{L2} = sum grad (ut - u).
+// Trial point ut = clip(u - zeta g) and <g, ut - u>_{L2} = sum grad (ut - u); with ut2
+// also the point at zeta / 2 (the second trial of a pair) and its product in dot2.
 __global__ void opt_trial_kernel(int n, const double *__restrict__ u, const double *__restrict__ grad,
                                  const double *__restrict__ zeta_p, double dt, double lo, double hi,
-                                 double *__restrict__ ut, double *__restrict__ dot) {
+                                 double *__restrict__ ut, double *__restrict__ dot, double *__restrict__ ut2,
+                                 double *__restrict__ dot2) {
   __shared__ double sm[32];
   const double zeta = *zeta_p;
-  double a = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double g = grad[i] / dt;
-    const double v = fmin(fmax(u[i] - zeta * g, lo), hi);
-    ut[i] = v;
-    a += dt * g * (v - u[i]);
+  for (int h = 0; h < (ut2 ? 2 : 1); ++h) {
+    const double z = h ? 0.5 * zeta : zeta;
+    double *w = h ? ut2 : ut;
+    double a = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double g = grad[i] / dt;
+      const double v = fmin(fmax(u[i] - z * g, lo), hi);
+      w[i] = v;
+      a += dt * g * (v - u[i]);
+    }
+    a = block_sum_d(a, sm);
+    if (threadIdx.x == 0) *(h ? dot2 : dot) = a;
   }
-  a = block_sum_d(a, sm);
-  if (threadIdx.x == 0) *dot = a;
 }
 
 // Armijo test J(ut) <= J(u) + c <g, ut - u>; on acceptance u <- ut and J <- J(ut).
 // s: [0] J(u), [1] J(ut), [2] dot, [4] accepted (out), [5] |ut - u|^2_{L2} (out).
+// With ut2 (a pair of trials, ut2 at half the step, J(ut2) and its product in
+// s[S_JT2], s[S_DOT2]) the points are tested in the order of backtracking and the first
+// that passes is taken: s[4] = 1 (ut), 2 (ut2) or 0, s[5] the squared step of the taken
+// point (of ut2 when neither passes).
 __global__ void opt_accept_kernel(int n, double *__restrict__ u, const double *__restrict__ ut,
-                                  double c, double dt, double *__restrict__ s) {
+                                  const double *__restrict__ ut2, double c, double dt, double *__restrict__ s) {
   __shared__ double sm[32];
-  const bool acc = s[1] <= s[0] + c * s[2];
+  const bool acc1 = s[1] <= s[0] + c * s[2];
+  const bool acc2 = ut2 && !acc1 && s[S_JT2] <= s[0] + c * s[S_DOT2];
+  const double *w = (ut2 && !acc1) ? ut2 : ut;
   double a = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const double e = ut[i] - u[i];
+    const double e = w[i] - u[i];
     a += dt * e * e;
   }
   a = block_sum_d(a, sm);
-  if (acc)
-    for (int i = threadIdx.x; i < n; i += blockDim.x) u[i] = ut[i];
+  if (acc1 || acc2)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) u[i] = w[i];
   __syncthreads();
   if (threadIdx.x == 0) {
-    s[4] = acc ? 1.0 : 0.0;
+    s[4] = acc1 ? 1.0 : (acc2 ? 2.0 : 0.0);
     s[5] = a;
-    if (acc) s[0] = s[1];
+    if (acc1) s[0] = s[1];
+    if (acc2) s[0] = s[1] = s[S_JT2];
   }
 }
 
@@ -270,10 +289,6 @@ static jd_status cuda_fail(cudaError_t e, const char *what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, #call);    \
   } while (0)
 
-// Scalar slots in p->scal_d
-enum { S_J = 0, S_JT = 1, S_DOT = 2, S_PG = 3, S_ACC = 4, S_STEP = 5, S_STATUS = 6, S_BAD = 7, S_THETA = 8,
-       S_ZETA = 42 };
-constexpr int NSCAL = kScalars;
 
 static bool finite_all(const double *a, size_t n) {
   for (size_t i = 0; i < n; ++i)
@@ -420,25 +435,26 @@ static jd_status load_u(jd_problem *p, const double *u, jd_memspace us) {
   return JD_OK;
 }
 
-static jd_status prep_u(jd_problem *p, const double *ud) {
+static jd_status prep_u(jd_problem *p, const double *ud, void *dst = nullptr) {
   const int64_t n = (int64_t)p->desc.Nt * p->DU;
   const unsigned grid = (unsigned)ceil_div(n, 256);
+  if (!dst) dst = p->uk;
   const int pr = prof_begin(KC_PREP, p->stream);
   if (p->desc.prec == JD_FP64)
-    prep_u_kernel<double><<<grid, 256, 0, p->stream>>>(ud, p->desc.Nt, p->desc.du, p->DU, (double *)p->uk);
+    prep_u_kernel<double><<<grid, 256, 0, p->stream>>>(ud, p->desc.Nt, p->desc.du, p->DU, (double *)dst);
   else
-    prep_u_kernel<float><<<grid, 256, 0, p->stream>>>(ud, p->desc.Nt, p->desc.du, p->DU, (float *)p->uk);
+    prep_u_kernel<float><<<grid, 256, 0, p->stream>>>(ud, p->desc.Nt, p->desc.du, p->DU, (float *)dst);
   prof_end(pr, p->stream);
   count_launch();
   JD_CUDA(cudaGetLastError());
   return JD_OK;
 }
 
-static jd_status finalize_cost(jd_problem *p, const double *ud, int slot) {
+static jd_status finalize_cost(jd_problem *p, const double *ud, int slot, const double *partC = nullptr) {
   const jd_problem_desc &q = p->desc;
   const double dt = q.T / q.Nt;
   const int pr = prof_begin(KC_FINALIZE, p->stream);
-  finalize_cost_kernel<<<1, 256, 0, p->stream>>>(p->partC, p->nblk, ud, q.Nt * q.du, 0.5 * q.nu * dt,
+  finalize_cost_kernel<<<1, 256, 0, p->stream>>>(partC ? partC : p->partC, p->nblk, ud, q.Nt * q.du, 0.5 * q.nu * dt,
                                                  1.0 / (double)q.M, p->scal_d + slot, p->scal_d + S_BAD);
   prof_end(pr, p->stream);
   count_launch();
@@ -472,6 +488,67 @@ static jd_status run_plan_forward(jd_problem *p, const double *ud, int slot) {
   prof_end(pr, p->stream);
   JD_CUDA(e);
   return finalize_cost(p, ud, slot);
+}
+
+// Second set of the plan's buffers for paired trials: allocated once, when the memory
+// budget holds it beside everything else; not for the block-wise stored plan nor d = 32.
+static bool ensure_pair(jd_problem *p) {
+  if (p->pair_state) return p->pair_state > 0;
+  p->pair_state = -1;
+  if (ensure_plan(p) || p->chunk || p->D == 32) return false;
+  const jd_problem_desc &q = p->desc;
+  const size_t es = elem_size(p), n = (size_t)q.Nt * q.du, M = (size_t)q.M;
+  const bool stored = p->plan == JD_ADJ_STORED;
+  const size_t cap = (size_t)(p->log_cap > 0 ? p->log_cap : 1);
+  const size_t b_traj = (size_t)((q.Nt + 4) / 4) * p->D * M * 4 * es;
+  const size_t need = (size_t)q.Nt * p->DU * es + (size_t)p->nblk * 8 + n * 8 +
+                      (stored ? b_traj + cap * M * 2 * es + cap * M * p->D * es : recompute_bytes(p));
+  if (p->bytes + need > p->budget) return false;
+  jd_status s = dev_alloc(p, &p->uk2, (size_t)q.Nt * p->DU * es, "paired control");
+  if (!s) s = dev_alloc(p, (void **)&p->partC2, (size_t)p->nblk * 8, "paired cost partials");
+  if (!s) s = dev_alloc(p, (void **)&p->opt_ut2, n * 8, "paired trial");
+  if (!s && stored) s = dev_alloc(p, &p->traj2, b_traj, "paired trajectory");
+  if (!s && stored) s = dev_alloc(p, &p->log_kt2, cap * M * 2 * es, "paired jump log");
+  if (!s && stored) s = dev_alloc(p, &p->log_y2, cap * M * p->D * es, "paired jump log states");
+  if (!s && !stored) s = dev_alloc(p, &p->ckpt2, recompute_bytes(p), "paired checkpoints");
+  if (s) return false;   // what was allocated is freed with the problem
+  p->pair_state = 1;
+  return true;
+}
+
+// The second set becomes the plan's (after the second trial of a pair was taken).
+static void swap_pair(jd_problem *p) {
+  std::swap(p->uk, p->uk2);
+  std::swap(p->partC, p->partC2);
+  std::swap(p->traj, p->traj2);
+  std::swap(p->log_kt, p->log_kt2);
+  std::swap(p->log_y, p->log_y2);
+  std::swap(p->ckpt, p->ckpt2);
+}
+
+// Paired forward sweep (FWD_PAIR) of ud and ud2 on the same random data, in the plan's
+// mode: ud's outputs in the plan's buffers, ud2's in the second set; J(ud) to slot,
+// J(ud2) to slot2.
+static jd_status run_pair_forward(jd_problem *p, const double *ud, int slot, const double *ud2, int slot2) {
+  jd_status s = prep_u(p, ud);
+  if (!s) s = prep_u(p, ud2, p->uk2);
+  if (s) return s;
+  PathBufs b = plan_bufs(p);
+  b.uk2 = p->uk2;
+  b.traj2 = p->traj2;
+  b.ckpt2 = p->ckpt2;
+  b.log_kt2 = p->log_kt2;
+  b.log_y2 = p->log_y2;
+  b.partC2 = p->partC2;
+  const bool stored = p->plan == JD_ADJ_STORED;
+  const int pr = prof_begin(KC_FWD_PAIR, p->stream);
+  const cudaError_t e =
+      p->ops->fwd(p, (stored ? FWD_STORE : FWD_CKPT) | FWD_PAIR, 0, p->desc.M, p->uk, b, p->stream);
+  prof_end(pr, p->stream);
+  JD_CUDA(e);
+  s = finalize_cost(p, ud, slot);
+  if (!s) s = finalize_cost(p, ud2, slot2, p->partC2);
+  return s;
 }
 
 // Gradient at ud.  With forward_done the stored states / checkpoints, the control in
@@ -664,8 +741,9 @@ static jd_status enqueue_grad(jd_problem *p, bool forward_done) {
 }
 
 // Work of a trial phase: zeta from pinned memory, trial point, forward sweep in the
-// plan's mode, device-side acceptance test, first scalars to pinned memory.
-static jd_status enqueue_trial(jd_problem *p, double armijo_c) {
+// plan's mode, device-side acceptance test, first scalars to pinned memory.  pair: the
+// trial points at zeta and zeta / 2 in one paired sweep, tested in that order.
+static jd_status enqueue_trial(jd_problem *p, double armijo_c, bool pair) {
   const jd_problem_desc &q = p->desc;
   const int n = q.Nt * q.du;
   const double dt = q.T / q.Nt;
@@ -673,14 +751,16 @@ static jd_status enqueue_trial(jd_problem *p, double armijo_c) {
                           p->stream));
   int pr = prof_begin(KC_OPT, p->stream);
   opt_trial_kernel<<<1, 256, 0, p->stream>>>(n, p->opt_u, p->grad_d, p->scal_d + S_ZETA, dt, q.u_min, q.u_max,
-                                             p->opt_ut, p->scal_d + S_DOT);
+                                             p->opt_ut, p->scal_d + S_DOT, pair ? p->opt_ut2 : nullptr,
+                                             p->scal_d + S_DOT2);
   prof_end(pr, p->stream);
   count_launch();
   JD_CUDA(cudaGetLastError());
-  jd_status s = run_plan_forward(p, p->opt_ut, S_JT);
+  jd_status s = pair ? run_pair_forward(p, p->opt_ut, S_JT, p->opt_ut2, S_JT2) : run_plan_forward(p, p->opt_ut, S_JT);
   if (s) return s;
   pr = prof_begin(KC_OPT, p->stream);
-  opt_accept_kernel<<<1, 256, 0, p->stream>>>(n, p->opt_u, p->opt_ut, armijo_c, dt, p->scal_d);
+  opt_accept_kernel<<<1, 256, 0, p->stream>>>(n, p->opt_u, p->opt_ut, pair ? p->opt_ut2 : nullptr, armijo_c, dt,
+                                              p->scal_d);
   prof_end(pr, p->stream);
   count_launch();
   JD_CUDA(cudaGetLastError());
@@ -729,19 +809,29 @@ static jd_status launch_grad(jd::OptMachine &m) {
   if (s) return s;
   m.forward_done = false;
   m.r.evals++;
+  if (v == 0) m.r.sweeps++;
   m.grads++;
   m.phase = jd::OptMachine::GRAD;
   return JD_OK;
 }
 
-// One Armijo trial at the current zeta.
+// One Armijo trial at the current zeta, or the pair (zeta, zeta / 2) in one sweep.  A
+// pair costs about a third more than one trial and saves a whole sweep when the first
+// point is rejected: it is taken for an iteration's first trial (zeta was doubled, so
+// a backtrack is the common case) unless the last two iterations accepted their first
+// point (a run of growing steps); later trials of the iteration are single (after two
+// rejections the next point is the likely one).  Never beyond the backtrack budget.
 static jd_status launch_trial(jd::OptMachine &m) {
   jd_problem *p = m.p;
   p->host_pinned[S_ZETA] = m.zeta;   // read by the trial's copy when it executes
   const double c = m.o.armijo_c;
-  const jd_status s = run_phase(m, &m.g_trial, &m.n_trial, [&]() { return enqueue_trial(p, c); });
+  const bool want = m.backtracks == 0 && m.first_accepts < 2;
+  m.pair = m.pairs && want && m.backtracks + 1 <= m.o.max_backtracks && ensure_pair(p);
+  const bool pair = m.pair;
+  const jd_status s = run_phase(m, &m.g_trial, &m.n_trial, [&]() { return enqueue_trial(p, c, pair); });
   if (s) return s;
   m.r.evals++;
+  m.r.sweeps++;
   m.phase = jd::OptMachine::TRIAL;
   return JD_OK;
 }
@@ -780,6 +870,9 @@ jd_status jd::opt_begin(OptMachine &m, jd_problem *p, const jd_opt_params &o, do
   m.u_dst = u_dst;
   m.u_space = us;
   m.it = m.backtracks = m.grads = 0;
+  m.pairs = o.one_trial_per_sweep == 0 && !m.use_graphs;
+  m.first_accepts = 0;
+  m.pair = false;
   m.zeta = o.zeta0 > 0.0 ? o.zeta0 : 1.0;
   m.zeta_max = o.zeta_max > 0.0 ? o.zeta_max : 1e3;
   m.pg0 = -1.0;
@@ -823,6 +916,14 @@ jd_status jd::opt_advance(OptMachine &m) {
       return launch_trial(m);
     }
     case OptMachine::TRIAL: {
+      if (m.backtracks == 0) m.first_accepts = h[S_ACC] == 1.0 ? m.first_accepts + 1 : 0;
+      if (m.pair && h[S_ACC] != 1.0) {
+        // the pair's second trial counts as the evaluation sequential backtracking makes next
+        m.r.evals++;
+        m.zeta *= 0.5;
+        ++m.backtracks;
+        if (h[S_ACC] == 2.0) swap_pair(p);   // its states become the plan's
+      }
       if (h[S_ACC] != 0.0) {
         m.forward_done = !m.o.resample;   // the trial's sweep is the next gradient's forward
         const double step2 = h[S_STEP];
@@ -923,6 +1024,13 @@ jd_status jd_problem_destroy(jd_problem *p) {
   free_dev(p, p->opt_u);
   free_dev(p, p->opt_ut);
   free_dev(p, p->opt_g);
+  free_dev(p, p->uk2);
+  free_dev(p, p->partC2);
+  free_dev(p, p->opt_ut2);
+  free_dev(p, p->traj2);
+  free_dev(p, p->log_kt2);
+  free_dev(p, p->log_y2);
+  free_dev(p, p->ckpt2);
   free_dev(p, p->kp_dev);
   free_dev(p, p->bu_dev);
   free_dev(p, p->fb_mu);

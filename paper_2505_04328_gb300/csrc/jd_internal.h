@@ -15,7 +15,9 @@ constexpr int NMAX = 16;   // jumps per uniform step are capped at this count
 constexpr int TPB = 128;   // threads (one path each) per block of the path kernels
 constexpr int BATCH = 8;   // steps per transposed warp reduction
 
-enum FwdMode { FWD_COST = 0, FWD_STORE = 1, FWD_CKPT = 2 };
+// FWD_PAIR (with FWD_STORE or FWD_CKPT): a second control on the same random data in the
+// same sweep (PathBufs' second set).
+enum FwdMode { FWD_COST = 0, FWD_STORE = 1, FWD_CKPT = 2, FWD_PAIR = 4 };
 enum AdjVariant { ADJ_STORED_V = 1, ADJ_RECOMPUTE_V = 2 };
 
 // Kernel parameters: coefficients padded to the compiled dimensions D, DU and passed
@@ -52,6 +54,10 @@ struct PathBufs {
   double *partC = nullptr, *partG = nullptr, *partT = nullptr;
   void *lam_out = nullptr;     // adjoint states (optional)
   int *status = nullptr;       // device status word (bounded waits record timeouts here)
+  // second control of a paired sweep (FWD_PAIR) and its outputs
+  const void *uk2 = nullptr;
+  void *traj2 = nullptr, *ckpt2 = nullptr, *log_kt2 = nullptr, *log_y2 = nullptr;
+  double *partC2 = nullptr;
   // partial-stride override: a launch that covers one block of the paths (chunked
   // stored plan) writes its partials at their global positions (partG, partC offset
   // by the caller) with the stride of all M paths; 0 = this launch's own count
@@ -149,6 +155,12 @@ struct jd_problem {
   void *log_kt = nullptr, *log_y = nullptr;
   int *jcnt = nullptr;
   int log_cap = 0;
+  // second set of the plan's buffers for the paired Armijo trials of jd_optimize
+  // (allocated on first use when the memory budget holds it; pair_state 1 ready,
+  // -1 unavailable, 0 not tried)
+  void *uk2 = nullptr, *traj2 = nullptr, *ckpt2 = nullptr, *log_kt2 = nullptr, *log_y2 = nullptr;
+  double *partC2 = nullptr, *opt_ut2 = nullptr;
+  int pair_state = 0;
   int64_t chunk = 0;         // stored plan in path blocks of this size (0: all paths at once)
   double *opt_u = nullptr, *opt_ut = nullptr, *opt_g = nullptr;
   int *status_d = nullptr;   // kernel status word (JD_OK or JD_ERR_TIMEOUT)
@@ -178,7 +190,7 @@ struct ProblemOpts {
   double *pinned = nullptr;          // null: own pinned scalar buffer (kScalars doubles)
   bool async_alloc = false;
 };
-constexpr int kScalars = 8 + 34 + 2;   // FP64 scalar slots per problem (device and pinned)
+constexpr int kScalars = 8 + 34 + 4;   // FP64 scalar slots per problem (device and pinned)
 
 jd_status create_problem(const jd_problem_desc &q, const ProblemOpts &o, jd_problem **out);
 
@@ -209,6 +221,10 @@ struct OptMachine {
   double zeta = 1.0, zeta_max = 1e3, pg0 = -1.0;
   bool forward_done = false;
   uint32_t epoch0 = 0;   // the problem's epoch; resampling uses epoch0 + it
+  // paired trials: allowed (pairs), whether the running trial is a pair, and the
+  // number of consecutive iterations that accepted their first trial point
+  bool pairs = false, pair = false;
+  int first_accepts = 0;
   // CUDA graphs: each phase's launch sequence is captured on first use and replayed
   // (gradient with and without the forward sweep, trial); kernels per graph counted
   bool use_graphs = false;

@@ -122,12 +122,10 @@ __host__ __device__ constexpr int seg_len() {
   return D <= 8 ? 16 : 8;
 }
 
-// One uniform step k from x (in place); returns the number of jumps.  Steps with one
-// jump take an inline path (the common case); two or more go through
-// build_jump_step.  With a LogWriter the post-jump states of the step are recorded.
-// The one-jump paths (inline and out of line) apply the additive map; a step of a
-// Keilson-Storer problem with jumps always takes build_jump_step, whose jump map covers
-// every law.
+// Steps with one jump take a short path (the common case); two or more go through
+// build_jump_step.  The one-jump paths (inline and out of line) apply the additive map;
+// a step of a Keilson-Storer problem with jumps always takes build_jump_step, whose jump
+// map covers every law.
 // The one-jump step out of line: sub-step to the jump, jump, sub-step to t_{k+1}.  x is
 // updated in place; y1 receives the post-jump state; returns the jump's time fraction.
 template <typename R, int D, int DU>
@@ -155,41 +153,63 @@ __device__ __noinline__ R one_jump_substeps(const KParams<R, D, DU> &kp, int k, 
   return th;
 }
 
-// zo (optional, stride zs): receives the step's main-stream normals Z_{k,0}.
+// The step has exactly one jump and the additive jump map (the one-jump paths).
+template <typename R, int D, int DU>
+__device__ __forceinline__ bool one_jump(const KParams<R, D, DU> &kp, uint32_t w0) {
+  return kp.jump_law != JD_JUMP_KS && kp.npair == MainWords<D>::PD && (unsigned long long)w0 < kp.thr[1];
+}
+
+// The one-jump step inline, its slot draws (time fraction th, jump size xih, second
+// sub-step normals z1) given: sub-step to the jump, jump, sub-step to t_{k+1}.
+template <typename R, int D, int DU, typename LW>
+__device__ __forceinline__ void one_jump_inline(const KParams<R, D, DU> &kp, int k, R th, const R (&xih)[D],
+                                                const R (&z)[D], const R (&z1)[D], const R (&uk)[DU], R (&x)[D],
+                                                LW &lw) {
+  using M = Ar<R>;
+  euler_substep(kp, M::mul(kp.dt, th), z, uk, x);
+#pragma unroll
+  for (int c = 0; c < D; ++c) x[c] = M::add(x[c], M::mul(kp.jump_scale, xih[c]));
+  if constexpr (!std::is_same<LW, NoLog>::value) {
+    if (lw.fits(1)) lw.put(k, th, x);
+  }
+  euler_substep(kp, M::mul(kp.dt, M::sub(R(1), th)), z1, uk, x);
+}
+
+// x <- x + dt f + sigma sqrt(dt) z: the step without jumps.
+template <typename R, int D, int DU>
+__device__ __forceinline__ void plain_update(const KParams<R, D, DU> &kp, const R (&f)[D], const R (&z)[D],
+                                             R (&x)[D]) {
+  using M = Ar<R>;
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    if constexpr (Pr<R>::on && D % 2 == 0) {   // components c, c+1 in one paired FMA each
+      if (c % 2 == 0) {
+        Pr<R>::fma(kp.dt, kp.dt, f[c], f[c + 1], x[c], x[c + 1]);
+        Pr<R>::fma(kp.sig_sqdt[c], kp.sig_sqdt[c + 1], z[c], z[c + 1], x[c], x[c + 1]);
+      }
+    } else {
+      x[c] = M::fma(kp.sig_sqdt[c], z[c], M::fma(kp.dt, f[c], x[c]));
+    }
+  }
+}
+
+// Step k from x (in place) once the main-stream draws z and the Poisson word w0 are
+// taken; returns the number of jumps.
 // INLINE_JUMP: the one-jump case inline, or out of line (the replay of the parameter-
-// gradient recompute adjoint, whose loop must stay small for the instruction cache).
-template <typename R, int D, int DU, typename LW, bool ZOUT = false, bool INLINE_JUMP = true>
-__device__ __forceinline__ int forward_step(const KParams<R, D, DU> &kp, int k, uint32_t m,
-                                            const R *__restrict__ u, R (&x)[D], LW &lw,
-                                            R *zo = nullptr, int zs = 0) {
+// gradient recompute adjoint, whose loop must stay small for the instruction cache, and
+// the paired sweep of two controls).
+template <typename R, int D, int DU, typename LW, bool INLINE_JUMP = true>
+__device__ __forceinline__ int step_from_draws(const KParams<R, D, DU> &kp, int k, uint32_t m, uint32_t w0,
+                                               const R (&z)[D], const R (&uk)[DU], R (&x)[D], LW &lw) {
   using M = Ar<R>;
   constexpr bool LOG = !std::is_same<LW, NoLog>::value;
-  R z[D];
-  const uint32_t w0 = main_draws(kp, k, m, z);
-  if constexpr (ZOUT) {
-#pragma unroll
-    for (int c = 0; c < D; ++c) zo[c * zs] = z[c];
-  }
-  R uk[DU];
-#pragma unroll
-  for (int l = 0; l < DU; ++l) uk[l] = __ldg(u + (size_t)k * DU + l);
   if (!has_jump(kp, w0)) {
     R f[D];
     drift(kp, x, uk, f);
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-      if constexpr (Pr<R>::on && D % 2 == 0) {   // components c, c+1 in one paired FMA each
-        if (c % 2 == 0) {
-          Pr<R>::fma(kp.dt, kp.dt, f[c], f[c + 1], x[c], x[c + 1]);
-          Pr<R>::fma(kp.sig_sqdt[c], kp.sig_sqdt[c + 1], z[c], z[c + 1], x[c], x[c + 1]);
-        }
-      } else {
-        x[c] = M::fma(kp.sig_sqdt[c], z[c], M::fma(kp.dt, f[c], x[c]));
-      }
-    }
+    plain_update(kp, f, z, x);
     return 0;
   }
-  if (!INLINE_JUMP && kp.jump_law != JD_JUMP_KS && kp.npair == MainWords<D>::PD && (unsigned long long)w0 < kp.thr[1]) {
+  if (!INLINE_JUMP && one_jump(kp, w0)) {
     // copies: an address taken of x or uk themselves would move them to local memory
     R zc[D], xc[D], uc[DU], y1[D];
 #pragma unroll
@@ -207,17 +227,10 @@ __device__ __forceinline__ int forward_step(const KParams<R, D, DU> &kp, int k, 
     }
     return 1;
   }
-  if (INLINE_JUMP && kp.jump_law != JD_JUMP_KS && kp.npair == MainWords<D>::PD &&
-      (unsigned long long)w0 < kp.thr[1]) {
+  if (INLINE_JUMP && one_jump(kp, w0)) {
     R xih[D], z1[D];
     const R th = slot0_draws(kp, k, m, xih, z1);
-    euler_substep(kp, M::mul(kp.dt, th), z, uk, x);
-#pragma unroll
-    for (int c = 0; c < D; ++c) x[c] = M::add(x[c], M::mul(kp.jump_scale, xih[c]));
-    if constexpr (LOG) {
-      if (lw.fits(1)) lw.put(k, th, x);
-    }
-    euler_substep(kp, M::mul(kp.dt, M::sub(R(1), th)), z1, uk, x);
+    one_jump_inline(kp, k, th, xih, z, z1, uk, x, lw);
     return 1;
   }
   // two or more jumps: the general routine takes pointers, so pass copies and keep
@@ -245,6 +258,61 @@ __device__ __forceinline__ int forward_step(const KParams<R, D, DU> &kp, int k, 
     }
   }
   return S.n;
+}
+
+// One uniform step k from x (in place); returns the number of jumps.  With a LogWriter
+// the post-jump states of the step are recorded.  zo (optional, stride zs) receives the
+// step's main-stream normals Z_{k,0}.
+template <typename R, int D, int DU, typename LW, bool ZOUT = false, bool INLINE_JUMP = true>
+__device__ __forceinline__ int forward_step(const KParams<R, D, DU> &kp, int k, uint32_t m,
+                                            const R *__restrict__ u, R (&x)[D], LW &lw,
+                                            R *zo = nullptr, int zs = 0) {
+  R z[D];
+  const uint32_t w0 = main_draws(kp, k, m, z);
+  if constexpr (ZOUT) {
+#pragma unroll
+    for (int c = 0; c < D; ++c) zo[c * zs] = z[c];
+  }
+  R uk[DU];
+#pragma unroll
+  for (int l = 0; l < DU; ++l) uk[l] = __ldg(u + (size_t)k * DU + l);
+  return step_from_draws<R, D, DU, LW, INLINE_JUMP>(kp, k, m, w0, z, uk, x, lw);
+}
+
+// Step k of two controls u, u2 on the same random data (the pair of Armijo trials of one
+// sweep): one draw of the main stream, and on a jump step the same jump times and sizes
+// for both states.  Each state's arithmetic is forward_step's, so each result is bitwise
+// the one of a sweep of its control alone.  Returns the number of jumps.
+template <typename R, int D, int DU, typename LW>
+__device__ __forceinline__ int forward_step2(const KParams<R, D, DU> &kp, int k, uint32_t m,
+                                             const R *__restrict__ u, R (&x)[D], LW &lw,
+                                             const R *__restrict__ u2, R (&x2)[D], LW &lw2) {
+  R z[D];
+  const uint32_t w0 = main_draws(kp, k, m, z);
+  R uk[DU], uk2[DU];
+#pragma unroll
+  for (int l = 0; l < DU; ++l) {
+    uk[l] = __ldg(u + (size_t)k * DU + l);
+    uk2[l] = __ldg(u2 + (size_t)k * DU + l);
+  }
+  if (!has_jump(kp, w0)) {
+    R f[D], f2[D];
+    drift(kp, x, uk, f);
+    drift(kp, x2, uk2, f2);
+    plain_update(kp, f, z, x);
+    plain_update(kp, f2, z, x2);
+    return 0;
+  }
+  if (one_jump(kp, w0)) {   // one slot draw for both states
+    R xih[D], z1[D];
+    const R th = slot0_draws(kp, k, m, xih, z1);
+    one_jump_inline(kp, k, th, xih, z, z1, uk, x, lw);
+    one_jump_inline(kp, k, th, xih, z, z1, uk2, x2, lw2);
+    return 1;
+  }
+  const int n = step_from_draws<R, D, DU, LW, false>(kp, k, m, w0, z, uk, x, lw);
+  step_from_draws<R, D, DU, LW, false>(kp, k, m, w0, z, uk2, x2, lw2);
+  return n;
 }
 
 // dt l(x, t_k) = sum_c (q_c dt / 2) (x_c - xd_c(t_k))^2
@@ -432,80 +500,122 @@ __device__ __forceinline__ void backward_step(const KParams<R, D, DU> &kp, int k
 }
 
 // ---------------------------------------------------------------------------
-template <typename R, int D, int DU, int MODE>
+// Outputs of the second control of a paired sweep (PAIR): its control, cost partials,
+// stored states or checkpoints and jump-log states.  The jump flags and log counts are
+// the same for both controls and are written once.
+template <typename R, int D>
+struct PairOut {
+  const R *u;
+  double *partC;
+  R *traj;
+  R *ckpt;
+  JLog<R, D> jl;
+};
+
+// Store mode: the last three states of the current group of four ride in registers
+// (b0, b1, b2) and the group leaves as one 16-byte vector per component.
+template <typename R, int D>
+__device__ __forceinline__ void stage_state(R *__restrict__ traj, int k, int Nt, int64_t mloc, int64_t lm,
+                                            bool active, const R (&x)[D], R (&b0)[D], R (&b1)[D], R (&b2)[D]) {
+  const int j = k & 3;
+  if (j == 3 || k == Nt) {
+    if (active) {
+#pragma unroll
+      for (int c = 0; c < D; ++c)
+        Vec4<R>::store(traj + (((size_t)(k >> 2) * D + c) * mloc + lm) * 4, j == 0 ? x[c] : b0[c],
+                       j == 1 ? x[c] : b1[c], j == 2 ? x[c] : b2[c], x[c]);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      b0[c] = j == 0 ? x[c] : b0[c];
+      b1[c] = j == 1 ? x[c] : b1[c];
+      b2[c] = j == 2 ? x[c] : b2[c];
+    }
+  }
+}
+
+template <typename R, int D, int DU, int MODE, bool PAIR = false>
 __global__ void __launch_bounds__(TPB)
 fwd_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u,
            const R *__restrict__ xd, double *__restrict__ partC, R *__restrict__ traj,
            uint32_t *__restrict__ flags, R *__restrict__ ckpt, R *__restrict__ pcost,
-           JLog<R, D> jl, int *__restrict__ jcnt, int64_t mloc) {
+           JLog<R, D> jl, int *__restrict__ jcnt, int64_t mloc, PairOut<R, D> p2) {
   __shared__ Pair<R> red[TPB / 32];
   const int64_t lm = (int64_t)blockIdx.x * TPB + threadIdx.x;
   const bool active = lm < mloc;
   const uint32_t m = (uint32_t)(kp.m_begin + lm);
   const int Nt = kp.Nt;
-  R x[D];
+  R x[D], x2[D];
 #pragma unroll
-  for (int c = 0; c < D; ++c) x[c] = kp.x0[c];
-  Kahan<R> cost;
+  for (int c = 0; c < D; ++c) x[c] = x2[c] = kp.x0[c];
+  Kahan<R> cost, cost2;
   uint32_t fw = 0;
   using LW = typename std::conditional<MODE == FWD_STORE, LogWriter<R, D>, NoLog>::type;
-  LW lw;
+  LW lw, lw2;
   if constexpr (MODE == FWD_STORE) {
     lw.L = jl;
     lw.idx = lm;
     if (!active) lw.L.cap = 0;   // inactive threads log nothing
+    if constexpr (PAIR) {
+      lw2.L = p2.jl;
+      lw2.idx = lm;
+      if (!active) lw2.L.cap = 0;
+    }
   }
-  // States X_0..X_Nt.  In store mode the last three states of the current group of
-  // four ride in registers (b0, b1, b2) and the group leaves as one 16-byte vector per
-  // component; the loop is not unrolled, which keeps the step's code small.
-  R b0[D], b1[D], b2[D];
+  // the loop is not unrolled, which keeps the step's code small
+  R b0[D], b1[D], b2[D], c0[D], c1[D], c2[D];
 #pragma unroll
-  for (int c = 0; c < D; ++c) b0[c] = b1[c] = b2[c] = R(0);
+  for (int c = 0; c < D; ++c) b0[c] = b1[c] = b2[c] = c0[c] = c1[c] = c2[c] = R(0);
 #pragma unroll 1
   for (int k = 0; k <= Nt; ++k) {
     if (MODE == FWD_STORE) {
-      const int j = k & 3;
-      if (j == 3 || k == Nt) {
-        if (active) {
-#pragma unroll
-          for (int c = 0; c < D; ++c)
-            Vec4<R>::store(traj + (((size_t)(k >> 2) * D + c) * mloc + lm) * 4, j == 0 ? x[c] : b0[c],
-                           j == 1 ? x[c] : b1[c], j == 2 ? x[c] : b2[c], x[c]);
-        }
-      } else {
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-          b0[c] = j == 0 ? x[c] : b0[c];
-          b1[c] = j == 1 ? x[c] : b1[c];
-          b2[c] = j == 2 ? x[c] : b2[c];
-        }
-      }
+      stage_state<R, D>(traj, k, Nt, mloc, lm, active, x, b0, b1, b2);
+      if constexpr (PAIR) stage_state<R, D>(p2.traj, k, Nt, mloc, lm, active, x2, c0, c1, c2);
     }
     if (k == Nt) break;
     if (MODE == FWD_CKPT && active && (k % seg_len<D>()) == 0) {   // S is a power of two
 #pragma unroll
-      for (int c = 0; c < D; ++c) ckpt[((size_t)(k / seg_len<D>()) * D + c) * mloc + lm] = x[c];
+      for (int c = 0; c < D; ++c) {
+        ckpt[((size_t)(k / seg_len<D>()) * D + c) * mloc + lm] = x[c];
+        if constexpr (PAIR) p2.ckpt[((size_t)(k / seg_len<D>()) * D + c) * mloc + lm] = x2[c];
+      }
     }
-    if (forward_step(kp, k, m, u, x, lw)) fw |= 1u << (k & 31);
+    int nj;
+    if constexpr (PAIR)
+      nj = forward_step2(kp, k, m, u, x, lw, p2.u, x2, lw2);
+    else
+      nj = forward_step(kp, k, m, u, x, lw);
+    if (nj) fw |= 1u << (k & 31);
     cost.add(cost_term(kp, x, xd + (size_t)(k + 1) * D));
+    if constexpr (PAIR) cost2.add(cost_term(kp, x2, xd + (size_t)(k + 1) * D));
     if (MODE == FWD_STORE && ((k & 31) == 31 || k == Nt - 1)) {
       if (active) flags[(size_t)(k >> 5) * mloc + lm] = fw;
       fw = 0;
     }
   }
   if constexpr (MODE == FWD_STORE) {
-    if (active) jcnt[lm] = lw.r;
+    if (active) jcnt[lm] = lw.r;   // the same count for the second control
   }
   if (MODE == FWD_CKPT && active) {
     const int nseg = (Nt + seg_len<D>() - 1) / seg_len<D>();
 #pragma unroll
-    for (int c = 0; c < D; ++c) ckpt[((size_t)nseg * D + c) * mloc + lm] = x[c];
+    for (int c = 0; c < D; ++c) {
+      ckpt[((size_t)nseg * D + c) * mloc + lm] = x[c];
+      if constexpr (PAIR) p2.ckpt[((size_t)nseg * D + c) * mloc + lm] = x2[c];
+    }
   }
   Pair<R> v = cost.pair();
   if (!active) v = {R(0), R(0)};
   if (pcost && active) pcost[lm] = Ar<R>::add(v.s, v.e);
   const double s = block_sum_to_double(v, red);
   if (threadIdx.x == 0) partC[blockIdx.x] = s;
+  if constexpr (PAIR) {
+    Pair<R> v2 = cost2.pair();
+    if (!active) v2 = {R(0), R(0)};
+    const double s2 = block_sum_to_double(v2, red);
+    if (threadIdx.x == 0) p2.partC[blockIdx.x] = s2;
+  }
 }
 
 template <typename R, int D>
@@ -810,18 +920,32 @@ cudaError_t op_fwd(const jd_problem *p, int mode, int64_t m_begin, int64_t mloc,
   const R *xd = static_cast<const R *>(p->xdk);
   R *pc = static_cast<R *>(b.pcost);
   const JLog<R, D> jl{static_cast<typename V2<R>::T *>(b.log_kt), static_cast<R *>(b.log_y), mloc, b.log_cap};
+  PairOut<R, D> p2{};
+  if (mode & FWD_PAIR)
+    p2 = PairOut<R, D>{static_cast<const R *>(b.uk2), b.partC2, static_cast<R *>(b.traj2), static_cast<R *>(b.ckpt2),
+                       JLog<R, D>{static_cast<typename V2<R>::T *>(b.log_kt2), static_cast<R *>(b.log_y2), mloc,
+                                  b.log_cap}};
   switch (mode) {
     case FWD_COST:
       fwd_kernel<R, D, DU, FWD_COST><<<grid, TPB, 0, s>>>(*kp, u, xd, b.partC, nullptr, nullptr, nullptr, pc,
-                                                          jl, nullptr, mloc);
+                                                          jl, nullptr, mloc, p2);
       break;
     case FWD_STORE:
       fwd_kernel<R, D, DU, FWD_STORE><<<grid, TPB, 0, s>>>(*kp, u, xd, b.partC, static_cast<R *>(b.traj),
-                                                           b.flags, nullptr, pc, jl, b.jcnt, mloc);
+                                                           b.flags, nullptr, pc, jl, b.jcnt, mloc, p2);
+      break;
+    case FWD_STORE | FWD_PAIR:
+      fwd_kernel<R, D, DU, FWD_STORE, true><<<grid, TPB, 0, s>>>(*kp, u, xd, b.partC, static_cast<R *>(b.traj),
+                                                                 b.flags, nullptr, nullptr, jl, b.jcnt, mloc, p2);
+      break;
+    case FWD_CKPT | FWD_PAIR:
+      fwd_kernel<R, D, DU, FWD_CKPT, true><<<grid, TPB, 0, s>>>(*kp, u, xd, b.partC, nullptr, nullptr,
+                                                                static_cast<R *>(b.ckpt), nullptr, jl, nullptr,
+                                                                mloc, p2);
       break;
     default:
       fwd_kernel<R, D, DU, FWD_CKPT><<<grid, TPB, 0, s>>>(*kp, u, xd, b.partC, nullptr, nullptr,
-                                                          static_cast<R *>(b.ckpt), pc, jl, nullptr, mloc);
+                                                          static_cast<R *>(b.ckpt), pc, jl, nullptr, mloc, p2);
       break;
   }
   delete kp;
@@ -884,7 +1008,8 @@ size_t op_stack_bytes() {
   size_t need = 2 * sizeof(JumpStep<R, D>) + 2048;
   const void *ks[] = {
       (const void *)fwd_kernel<R, D, DU, FWD_COST>, (const void *)fwd_kernel<R, D, DU, FWD_STORE>,
-      (const void *)fwd_kernel<R, D, DU, FWD_CKPT>, (const void *)adj_stored_kernel<R, D, DU, false>,
+      (const void *)fwd_kernel<R, D, DU, FWD_CKPT>, (const void *)fwd_kernel<R, D, DU, FWD_STORE, true>,
+      (const void *)fwd_kernel<R, D, DU, FWD_CKPT, true>, (const void *)adj_stored_kernel<R, D, DU, false>,
       (const void *)adj_stored_kernel<R, D, DU, false, true>,
       (const void *)adj_stored_kernel<R, D, DU, true>, (const void *)adj_recompute_kernel<R, D, DU, false>,
       (const void *)adj_recompute_kernel<R, D, DU, true>};

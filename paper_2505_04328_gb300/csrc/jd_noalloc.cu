@@ -141,7 +141,7 @@ static jd_status noalloc_run(const jd_problem_desc &q, unsigned char *scratch, c
   noalloc_kparams<R, D, 1>(q, kp);
   const JLog<R, D> nolog{nullptr, nullptr, M, 0};
   fwd_kernel<R, D, 1, FWD_COST><<<(unsigned)nblk, TPB, 0, s>>>(kp, uk, xdk, partC, nullptr, nullptr, nullptr,
-                                                               nullptr, nolog, nullptr, M);
+                                                               nullptr, nolog, nullptr, M, PairOut<R, D>{});
   noalloc_finalize_kernel<<<1, 256, 0, s>>>(partC, nblk, u, Nt, 0.5 * q.nu * (q.T / Nt), 1.0 / (double)M, J);
   count_launch(3);
   return cudaGetLastError() == cudaSuccess ? JD_OK : JD_ERR_CUDA;

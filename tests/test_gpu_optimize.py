@@ -64,3 +64,64 @@ def test_resampling_descent_follows_the_oracle(prec, tol):
     assert r["iters"] == ro["iters"] and r["evals"] == ro["evals"]
     assert np.max(np.abs(h - ho) / np.abs(ho)) <= tol
     assert np.max(np.abs(u - uo)) <= 10 * tol * max(1.0, np.max(np.abs(uo)))
+
+
+def _pair_vs_single(jp, **kw):
+    u1, r1, h1 = jp.optimize(tol_rel_grad=0.0, raise_on_error=False, pairs=False, **kw)
+    u2, r2, h2 = jp.optimize(tol_rel_grad=0.0, raise_on_error=False, pairs=True, **kw)
+    assert r1["status"] == r2["status"]
+    assert r1["iters"] == r2["iters"] and r1["evals"] == r2["evals"] and r1["zeta"] == r2["zeta"]
+    assert np.array_equal(u1, u2)
+    assert np.array_equal(h1, h2, equal_nan=True)
+    assert r1["sweeps"] <= r1["evals"]
+    return r1, r2
+
+
+@pytest.mark.parametrize("prec,mode", [("fp32", "stored"), ("fp32", "recompute"), ("fp64", "stored")])
+@pytest.mark.parametrize("zeta0", [1.0, 512.0])
+def test_paired_trials_take_the_sequential_iterates(prec, mode, zeta0):
+    """Armijo trials in pairs (zeta and zeta / 2 in one forward sweep on the same draws,
+    tested in backtracking order) against one trial per sweep: bitwise the same iterates,
+    J history, evaluation count and final step, in fewer sweeps.  zeta0 = 512 makes the
+    first iteration reject both points of its pair and backtrack further with single
+    trials."""
+    p = workloads.double_well(M=4096 + 77, Nt=150)
+    with JdProblem(p, prec=prec, mode=mode) as jp:
+        r1, r2 = _pair_vs_single(jp, max_iter=10, zeta0=zeta0)
+    assert r1["status"] == 0 and r1["iters"] == 10
+    assert r1["evals"] > r1["iters"] + 1   # some iteration backtracked
+    assert r2["sweeps"] < r1["sweeps"]
+
+
+def test_paired_trials_with_resets_and_the_lq_workload():
+    """Keilson-Storer resets (jumps through the general jump step) and the FP64 scalar
+    workload: the same iterates with and without pairs."""
+    p = workloads.ks_oscillator(M=2048, Nt=120)
+    with JdProblem(p, prec="fp32") as jp:
+        _pair_vs_single(jp, max_iter=8)
+    with JdProblem(workloads.lq_scalar(), prec="fp64") as jp:
+        _, r2 = _pair_vs_single(jp, max_iter=50)
+    assert r2["sweeps"] < r2["evals"]
+
+
+@pytest.mark.parametrize("max_backtracks", [0, 1, 2, 3, 4])
+def test_paired_trials_exhaust_backtracks_like_single_trials(max_backtracks):
+    """armijo_c > 1 rejects every trial: both forms stop with LINESEARCH after the same
+    evaluations, the pairs never trying a point single trials would not."""
+    p = workloads.lq_scalar(M=300, Nt=20)
+    with JdProblem(p, prec="fp64") as jp:
+        r1, r2 = _pair_vs_single(jp, max_iter=3, armijo_c=5.0, max_backtracks=max_backtracks)
+    assert r1["status"] == 5 and r1["evals"] == 1 + max_backtracks + 1
+
+
+def test_paired_trials_fall_back_when_the_budget_holds_one_set():
+    """A memory budget that holds the plan's buffers once: one trial per sweep, the same
+    result."""
+    p = workloads.double_well(M=4096, Nt=100)
+    with JdProblem(p, prec="fp32", mode="stored") as jp:
+        jp.gradient(np.zeros((p.Nt, p.du)))
+        need = jp.info()["device_bytes"]
+    with JdProblem(p, prec="fp32", mode="stored", mem_budget=need + 4096) as jp:
+        r1, r2 = _pair_vs_single(jp, max_iter=6)
+        assert jp.info()["device_bytes"] == need
+    assert r2["sweeps"] == r1["sweeps"]
