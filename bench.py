@@ -688,7 +688,8 @@ TRAFFIC_PER_PATH_STEP = {"fwd_store": 7.68, "adj_stored": 8.89}
 # (smsp__inst_executed.sum / warp-steps; profiles/*.md): with the measured time they give
 # the fraction of the SM's issue rate (4 schedulers x 1 instruction per clock) the kernel
 # uses, next to the algorithmic fraction; None when the kernel changed since the capture.
-INST_PER_WARP_STEP = {("double_well", "fwd_store"): 286, ("double_well", "adj_stored"): 111,
+INST_PER_WARP_STEP = {("double_well", "fwd_store"): 286, ("double_well", "fwd_pair"): 386,
+                      ("double_well", "adj_stored"): 111,
                       ("double_well", "adj_recompute"): 352, ("feedback_centering", "fb_fwd"): 830,
                       ("feedback_centering", "fb_adj"): 1224}
 
