@@ -233,8 +233,8 @@ __device__ __forceinline__ void reduce_batch(Pair<R> (&gb)[BATCH][DU], int kbase
 // ---------------------------------------------------------------------------
 // Model: drift f = A x + C x^3 + B u and its transposed Jacobian
 // ---------------------------------------------------------------------------
-template <typename R, int D, int DU>
-__device__ __forceinline__ void drift(const KParams<R, D, DU> &kp, const R (&y)[D], const R (&u)[DU],
+template <typename KP, typename R, int D, int DU>
+__device__ __forceinline__ void drift(const KP &kp, const R (&y)[D], const R (&u)[DU],
                                       R (&f)[D]) {
   using M = Ar<R>;
   if constexpr (Pr<R>::on && D % 2 == 0) {
@@ -284,8 +284,8 @@ __device__ __forceinline__ void drift(const KParams<R, D, DU> &kp, const R (&y)[
 }
 
 // mu <- mu + delta J_f(y)^T mu,  J_f = A + 3 C diag(y^2)
-template <typename R, int D, int DU>
-__device__ __forceinline__ void adjoint_update(const KParams<R, D, DU> &kp, const R (&y)[D], R delta,
+template <typename KP, typename R, int D>
+__device__ __forceinline__ void adjoint_update(const KP &kp, const R (&y)[D], R delta,
                                                R (&mu)[D]) {
   using M = Ar<R>;
   R t[D];
@@ -336,8 +336,8 @@ __device__ __forceinline__ void adjoint_update(const KParams<R, D, DU> &kp, cons
 }
 
 // g += delta B^T mu
-template <typename R, int D, int DU>
-__device__ __forceinline__ void control_sensitivity(const KParams<R, D, DU> &kp, const R (&mu)[D],
+template <typename KP, typename R, int D, int DU>
+__device__ __forceinline__ void control_sensitivity(const KP &kp, const R (&mu)[D],
                                                     R delta, R (&g)[DU]) {
   using M = Ar<R>;
 #pragma unroll

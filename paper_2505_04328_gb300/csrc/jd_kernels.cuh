@@ -176,9 +176,8 @@ __device__ __forceinline__ void one_jump_inline(const KParams<R, D, DU> &kp, int
 }
 
 // x <- x + dt f + sigma sqrt(dt) z: the step without jumps.
-template <typename R, int D, int DU>
-__device__ __forceinline__ void plain_update(const KParams<R, D, DU> &kp, const R (&f)[D], const R (&z)[D],
-                                             R (&x)[D]) {
+template <typename KP, typename R, int D>
+__device__ __forceinline__ void plain_update(const KP &kp, const R (&f)[D], const R (&z)[D], R (&x)[D]) {
   using M = Ar<R>;
 #pragma unroll
   for (int c = 0; c < D; ++c) {
@@ -198,15 +197,18 @@ __device__ __forceinline__ void plain_update(const KParams<R, D, DU> &kp, const 
 // INLINE_JUMP: the one-jump case inline, or out of line (the replay of the parameter-
 // gradient recompute adjoint, whose loop must stay small for the instruction cache, and
 // the paired sweep of two controls).
-template <typename R, int D, int DU, typename LW, bool INLINE_JUMP = true>
-__device__ __forceinline__ int step_from_draws(const KParams<R, D, DU> &kp, int k, uint32_t m, uint32_t w0,
-                                               const R (&z)[D], const R (&uk)[DU], R (&x)[D], LW &lw) {
+// kh: the source of the drift, noise and step coefficients of the step without jumps
+// (kp itself or a HotFwd); the jump paths read kp.
+template <typename R, int D, int DU, typename LW, bool INLINE_JUMP = true, typename KH = KParams<R, D, DU>>
+__device__ __forceinline__ int step_from_draws(const KParams<R, D, DU> &kp, const KH &kh, int k, uint32_t m,
+                                               uint32_t w0, const R (&z)[D], const R (&uk)[DU], R (&x)[D],
+                                               LW &lw) {
   using M = Ar<R>;
   constexpr bool LOG = !std::is_same<LW, NoLog>::value;
   if (!has_jump(kp, w0)) {
     R f[D];
-    drift(kp, x, uk, f);
-    plain_update(kp, f, z, x);
+    drift(kh, x, uk, f);
+    plain_update(kh, f, z, x);
     return 0;
   }
   if (!INLINE_JUMP && one_jump(kp, w0)) {
@@ -263,10 +265,11 @@ __device__ __forceinline__ int step_from_draws(const KParams<R, D, DU> &kp, int 
 // One uniform step k from x (in place); returns the number of jumps.  With a LogWriter
 // the post-jump states of the step are recorded.  zo (optional, stride zs) receives the
 // step's main-stream normals Z_{k,0}.
-template <typename R, int D, int DU, typename LW, bool ZOUT = false, bool INLINE_JUMP = true>
-__device__ __forceinline__ int forward_step(const KParams<R, D, DU> &kp, int k, uint32_t m,
-                                            const R *__restrict__ u, R (&x)[D], LW &lw,
-                                            R *zo = nullptr, int zs = 0) {
+template <typename R, int D, int DU, typename LW, bool ZOUT = false, bool INLINE_JUMP = true,
+          typename KH = KParams<R, D, DU>>
+__device__ __forceinline__ int forward_step_h(const KParams<R, D, DU> &kp, const KH &kh, int k, uint32_t m,
+                                              const R *__restrict__ u, R (&x)[D], LW &lw,
+                                              R *zo = nullptr, int zs = 0) {
   R z[D];
   const uint32_t w0 = main_draws(kp, k, m, z);
   if constexpr (ZOUT) {
@@ -276,15 +279,22 @@ __device__ __forceinline__ int forward_step(const KParams<R, D, DU> &kp, int k, 
   R uk[DU];
 #pragma unroll
   for (int l = 0; l < DU; ++l) uk[l] = __ldg(u + (size_t)k * DU + l);
-  return step_from_draws<R, D, DU, LW, INLINE_JUMP>(kp, k, m, w0, z, uk, x, lw);
+  return step_from_draws<R, D, DU, LW, INLINE_JUMP, KH>(kp, kh, k, m, w0, z, uk, x, lw);
+}
+
+template <typename R, int D, int DU, typename LW, bool ZOUT = false, bool INLINE_JUMP = true>
+__device__ __forceinline__ int forward_step(const KParams<R, D, DU> &kp, int k, uint32_t m,
+                                            const R *__restrict__ u, R (&x)[D], LW &lw,
+                                            R *zo = nullptr, int zs = 0) {
+  return forward_step_h<R, D, DU, LW, ZOUT, INLINE_JUMP>(kp, kp, k, m, u, x, lw, zo, zs);
 }
 
 // Step k of two controls u, u2 on the same random data (the pair of Armijo trials of one
 // sweep): one draw of the main stream, and on a jump step the same jump times and sizes
 // for both states.  Each state's arithmetic is forward_step's, so each result is bitwise
 // the one of a sweep of its control alone.  Returns the number of jumps.
-template <typename R, int D, int DU, typename LW>
-__device__ __forceinline__ int forward_step2(const KParams<R, D, DU> &kp, int k, uint32_t m,
+template <typename R, int D, int DU, typename LW, typename KH>
+__device__ __forceinline__ int forward_step2(const KParams<R, D, DU> &kp, const KH &kh, int k, uint32_t m,
                                              const R *__restrict__ u, R (&x)[D], LW &lw,
                                              const R *__restrict__ u2, R (&x2)[D], LW &lw2) {
   R z[D];
@@ -297,10 +307,10 @@ __device__ __forceinline__ int forward_step2(const KParams<R, D, DU> &kp, int k,
   }
   if (!has_jump(kp, w0)) {
     R f[D], f2[D];
-    drift(kp, x, uk, f);
-    drift(kp, x2, uk2, f2);
-    plain_update(kp, f, z, x);
-    plain_update(kp, f2, z, x2);
+    drift(kh, x, uk, f);
+    drift(kh, x2, uk2, f2);
+    plain_update(kh, f, z, x);
+    plain_update(kh, f2, z, x2);
     return 0;
   }
   if (one_jump(kp, w0)) {   // one slot draw for both states
@@ -310,15 +320,14 @@ __device__ __forceinline__ int forward_step2(const KParams<R, D, DU> &kp, int k,
     one_jump_inline(kp, k, th, xih, z, z1, uk2, x2, lw2);
     return 1;
   }
-  const int n = step_from_draws<R, D, DU, LW, false>(kp, k, m, w0, z, uk, x, lw);
-  step_from_draws<R, D, DU, LW, false>(kp, k, m, w0, z, uk2, x2, lw2);
+  const int n = step_from_draws<R, D, DU, LW, false>(kp, kp, k, m, w0, z, uk, x, lw);
+  step_from_draws<R, D, DU, LW, false>(kp, kp, k, m, w0, z, uk2, x2, lw2);
   return n;
 }
 
 // dt l(x, t_k) = sum_c (q_c dt / 2) (x_c - xd_c(t_k))^2
-template <typename R, int D, int DU>
-__device__ __forceinline__ R cost_term(const KParams<R, D, DU> &kp, const R (&x)[D],
-                                       const R *__restrict__ xdk) {
+template <typename KP, typename R, int D>
+__device__ __forceinline__ R cost_term(const KP &kp, const R (&x)[D], const R *__restrict__ xdk) {
   using M = Ar<R>;
   R t = R(0);
   if constexpr (Pr<R>::on && D % 2 == 0) {
@@ -413,12 +422,93 @@ __device__ __noinline__ void jump_backward(const KParams<R, D, DU> &kp, int k, u
   for (int l = 0; l < DU; ++l) g_io[l] = g[l];
 }
 
+// Coefficients of the forward step without jumps (drift, noise scale, step, cost
+// weights), held in registers for the forward kernel's step loop like HotCoef below.
+template <typename R, int D, int DU>
+struct HotFwd {
+  R A[D * D], C[D * D], B[D * DU], sig_sqdt[D], hqdt[D];
+  R dt;
+  int cubic;
+};
+
+// Coefficients of the adjoint step (A, C, B, dt, q dt) held in registers for a kernel's
+// step loop.  Each value passes through an empty asm statement, so the compiler cannot
+// rematerialise it from the parameter bank at every use inside the loop.
+template <typename R, int D, int DU>
+struct HotCoef {
+  R A[D * D], C[D * D], B[D * DU], qdt[D];
+  R dt;
+  int cubic;
+};
+
+__device__ __forceinline__ float reg_pin(float v) {
+  asm volatile("" : "+f"(v));
+  return v;
+}
+__device__ __forceinline__ double reg_pin(double v) {
+  asm volatile("" : "+d"(v));
+  return v;
+}
+
+template <typename R, int D, int DU>
+__device__ __forceinline__ HotCoef<R, D, DU> hot_coef(const KParams<R, D, DU> &kp) {
+  HotCoef<R, D, DU> h;
+#pragma unroll
+  for (int i = 0; i < D * D; ++i) {
+    h.A[i] = reg_pin(kp.A[i]);
+    h.C[i] = kp.cubic ? reg_pin(kp.C[i]) : R(0);
+  }
+#pragma unroll
+  for (int i = 0; i < D * DU; ++i) h.B[i] = reg_pin(kp.B[i]);
+#pragma unroll
+  for (int c = 0; c < D; ++c) h.qdt[c] = reg_pin(kp.qdt[c]);
+  h.dt = reg_pin(kp.dt);
+  h.cubic = kp.cubic;
+  return h;
+}
+
+template <typename R, int D, int DU>
+__device__ __forceinline__ HotFwd<R, D, DU> hot_fwd(const KParams<R, D, DU> &kp) {
+  HotFwd<R, D, DU> h;
+#pragma unroll
+  for (int i = 0; i < D * D; ++i) {
+    h.A[i] = reg_pin(kp.A[i]);
+    h.C[i] = kp.cubic ? reg_pin(kp.C[i]) : R(0);
+  }
+#pragma unroll
+  for (int i = 0; i < D * DU; ++i) h.B[i] = reg_pin(kp.B[i]);
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    h.sig_sqdt[c] = reg_pin(kp.sig_sqdt[c]);
+    h.hqdt[c] = reg_pin(kp.hqdt[c]);
+  }
+  h.dt = reg_pin(kp.dt);
+  h.cubic = kp.cubic;
+  return h;
+}
+
+// Pinned copies pay for d <= 2 (a handful of registers); for larger d the A and C blocks
+// alone would take 2 d^2 registers, and the kernels read kp.
+template <int D>
+constexpr bool pin_coef() {
+  return D <= 2;
+}
+template <bool PIN, typename H, typename R, int D, int DU>
+__device__ __forceinline__ const typename std::conditional<PIN, H, KParams<R, D, DU>>::type &coef_src(
+    const KParams<R, D, DU> &kp, const H &h) {
+  if constexpr (PIN)
+    return h;
+  else
+    return kp;
+}
+
 // Backward through step k from the state X_k; g receives the step's contribution.
 // Jump steps use the log when it holds the step (u-gradient only), else regenerate.
 // zi (optional, stride zs): the step's main-stream normals kept by the forward replay;
 // without it the parameter gradients regenerate them.
-template <typename R, int D, int DU, bool THETA, typename LR, bool ZIN = false>
-__device__ __forceinline__ void backward_step(const KParams<R, D, DU> &kp, int k, uint32_t m,
+// kh: the source of A, C, B, dt and q dt for the arithmetic (kp itself or a HotCoef).
+template <typename R, int D, int DU, bool THETA, typename LR, bool ZIN = false, typename KH = KParams<R, D, DU>>
+__device__ __forceinline__ void backward_step(const KParams<R, D, DU> &kp, const KH &kh, int k, uint32_t m,
                                               bool jumped, const R (&xk)[D],
                                               const R *__restrict__ u, const R *__restrict__ xd,
                                               R (&mu)[D], R (&g)[DU], R (&th)[D + 2], LR &lr,
@@ -432,15 +522,15 @@ __device__ __forceinline__ void backward_step(const KParams<R, D, DU> &kp, int k
     while (lr.has(k)) {
       R the, y[D];
       lr.pop(the, y);
-      const R de = M::mul(kp.dt, M::sub(thn, the));
-      control_sensitivity(kp, mu, de, g);
-      adjoint_update(kp, y, de, mu);
+      const R de = M::mul(kh.dt, M::sub(thn, the));
+      control_sensitivity(kh, mu, de, g);
+      adjoint_update(kh, y, de, mu);
       jump_adjoint(kp, mu);   // across the jump that produced y
       thn = the;
     }
-    const R de0 = M::mul(kp.dt, thn);
-    control_sensitivity(kp, mu, de0, g);
-    adjoint_update(kp, xk, de0, mu);
+    const R de0 = M::mul(kh.dt, thn);
+    control_sensitivity(kh, mu, de0, g);
+    adjoint_update(kh, xk, de0, mu);
   } else if (jumped) {
     while (lr.has(k)) {   // THETA: the log is not used, but stay in step with it
       R the, y[D];
@@ -480,8 +570,8 @@ __device__ __forceinline__ void backward_step(const KParams<R, D, DU> &kp, int k
         th[0] = M::fma(kp.dt, s, th[0]);
       }
     }
-    control_sensitivity(kp, mu, kp.dt, g);
-    adjoint_update(kp, xk, kp.dt, mu);
+    control_sensitivity(kh, mu, kh.dt, g);
+    adjoint_update(kh, xk, kh.dt, mu);
   }
   if (k >= 1) {
     if constexpr (Pr<R>::on && D % 2 == 0) {
@@ -489,12 +579,12 @@ __device__ __forceinline__ void backward_step(const KParams<R, D, DU> &kp, int k
       for (int c = 0; c < D; c += 2) {
         R e0, e1;
         Pr<R>::sub(xk[c], xk[c + 1], __ldg(xd + (size_t)k * D + c), __ldg(xd + (size_t)k * D + c + 1), e0, e1);
-        Pr<R>::fma(kp.qdt[c], kp.qdt[c + 1], e0, e1, mu[c], mu[c + 1]);
+        Pr<R>::fma(kh.qdt[c], kh.qdt[c + 1], e0, e1, mu[c], mu[c + 1]);
       }
     } else {
 #pragma unroll
       for (int c = 0; c < D; ++c)
-        mu[c] = M::fma(kp.qdt[c], M::sub(xk[c], __ldg(xd + (size_t)k * D + c)), mu[c]);
+        mu[c] = M::fma(kh.qdt[c], M::sub(xk[c], __ldg(xd + (size_t)k * D + c)), mu[c]);
     }
   }
 }
@@ -563,6 +653,11 @@ fwd_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u
       if (!active) lw2.L.cap = 0;
     }
   }
+  constexpr bool PIN = pin_coef<D>();
+  using KH = typename std::conditional<PIN, HotFwd<R, D, DU>, KParams<R, D, DU>>::type;
+  HotFwd<R, D, DU> khv;
+  if constexpr (PIN) khv = hot_fwd(kp);
+  const KH &kh = coef_src<PIN>(kp, khv);
   // the loop is not unrolled, which keeps the step's code small
   R b0[D], b1[D], b2[D], c0[D], c1[D], c2[D];
 #pragma unroll
@@ -583,12 +678,12 @@ fwd_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u
     }
     int nj;
     if constexpr (PAIR)
-      nj = forward_step2(kp, k, m, u, x, lw, p2.u, x2, lw2);
+      nj = forward_step2(kp, kh, k, m, u, x, lw, p2.u, x2, lw2);
     else
-      nj = forward_step(kp, k, m, u, x, lw);
+      nj = forward_step_h<R, D, DU, LW, false, true, KH>(kp, kh, k, m, u, x, lw);
     if (nj) fw |= 1u << (k & 31);
-    cost.add(cost_term(kp, x, xd + (size_t)(k + 1) * D));
-    if constexpr (PAIR) cost2.add(cost_term(kp, x2, xd + (size_t)(k + 1) * D));
+    cost.add(cost_term(kh, x, xd + (size_t)(k + 1) * D));
+    if constexpr (PAIR) cost2.add(cost_term(kh, x2, xd + (size_t)(k + 1) * D));
     if (MODE == FWD_STORE && ((k & 31) == 31 || k == Nt - 1)) {
       if (active) flags[(size_t)(k >> 5) * mloc + lm] = fw;
       fw = 0;
@@ -679,6 +774,11 @@ adj_stored_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restr
 #pragma unroll
       for (int c = 0; c < D; ++c) lam_out[((size_t)Nt * D + c) * mloc + lm] = mu[c];
   }
+  constexpr bool PIN = pin_coef<D>();
+  using KH = typename std::conditional<PIN, HotCoef<R, D, DU>, KParams<R, D, DU>>::type;
+  HotCoef<R, D, DU> khv;
+  if constexpr (PIN) khv = hot_coef(kp);
+  const KH &kh = coef_src<PIN>(kp, khv);
   const int nbatch = (Nt + BATCH - 1) / BATCH;
   const int ng = (Nt + 4) / 4;   // groups of 4 stored states
 #pragma unroll 1
@@ -711,7 +811,8 @@ adj_stored_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restr
 #pragma unroll
       for (int l = 0; l < DU; ++l) g[l] = R(0);
       if (k < Nt) {
-        backward_step<R, D, DU, THETA>(kp, k, m, (fw >> (k & 31)) & 1u, xs[j], u, xd, mu, g, th, lr);
+        backward_step<R, D, DU, THETA, LogReader<R, D>, false, KH>(
+            kp, kh, k, m, (fw >> (k & 31)) & 1u, xs[j], u, xd, mu, g, th, lr);
         if (LAM && active)
 #pragma unroll
           for (int c = 0; c < D; ++c) lam_out[((size_t)k * D + c) * mloc + lm] = mu[c];
@@ -810,7 +911,7 @@ adj_recompute_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__re
             R xk[D];
 #pragma unroll
             for (int c = 0; c < D; ++c) xk[c] = sbuf[(i * D + c) * TPB + tid];
-            backward_step<R, D, DU, THETA, LogReader<R, D>, ZBUF>(kp, k, m, (jm >> i) & 1u, xk, u, xd, mu, g, th,
+            backward_step<R, D, DU, THETA, LogReader<R, D>, ZBUF>(kp, kp, k, m, (jm >> i) & 1u, xk, u, xd, mu, g, th,
                                                                   lr, zbuf + (size_t)i * D * TPB + tid, TPB);
           }
 #pragma unroll
@@ -831,7 +932,7 @@ adj_recompute_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__re
             R xk[D];
 #pragma unroll
             for (int c = 0; c < D; ++c) xk[c] = sbuf[(i * D + c) * TPB + tid];
-            backward_step<R, D, DU, THETA, LogReader<R, D>, ZBUF>(kp, k, m, (jm >> i) & 1u, xk, u, xd, mu, g, th,
+            backward_step<R, D, DU, THETA, LogReader<R, D>, ZBUF>(kp, kp, k, m, (jm >> i) & 1u, xk, u, xd, mu, g, th,
                                                                   lr, zbuf + (size_t)i * D * TPB + tid, TPB);
           }
 #pragma unroll
