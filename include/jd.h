@@ -202,8 +202,8 @@ jd_status jd_sample_paths(jd_problem *p, const double *u, jd_memspace us, int64_
  * sweep of its control alone) and tested in backtracking order, so iterates, J values,
  * zeta and r->evals are those of one trial per sweep; r->sweeps counts the forward
  * sweeps run (a pair counts one).  Needs a second set of the plan's path buffers within
- * the memory budget (else one trial per sweep); not with the block-wise stored plan,
- * d > 8 or the server's requests. */
+ * the memory budget (else one trial per sweep); not with the block-wise stored plan
+ * or d > 8. */
 typedef struct {
   int max_iter;
   double tol_rel_grad, tol_step, armijo_c, zeta0, zeta_max;
@@ -268,7 +268,9 @@ jd_status jd_problem_footprint(const jd_problem_desc *desc, jd_adjoint_mode plan
  * jd_server_info: times in seconds since the server was created (admit_s, done_s are
  *   -1 until they happen), bytes and plan of the admitted request, its gradient
  *   path-steps (M*Nt per gradient evaluation: forward + adjoint sweep) and its sweep
- *   path-steps (M*Nt per evaluation, line-search cost sweeps included).
+ *   path-steps (M*Nt per sweep over the paths actually run: forward sweeps of gradients
+ *   and line-search trials, a paired trial counting one, plus the adjoint sweeps).  A request's footprint includes the second buffer set of paired
+ *   trials when that keeps it within a quarter of the budget and what is free.
  * jd_server_destroy: cancels requests not yet admitted (status INVALID_ARG), waits for
  *   the running ones, frees everything. */
 typedef struct jd_server jd_server;

@@ -482,7 +482,7 @@ class JdServer:
             return None
         _check(st, "jd_server_poll")
         return u, dict(iters=r.iters, evals=r.evals, status=r.status, J=r.J,
-                       rel_grad_norm=r.rel_grad_norm, zeta=r.zeta)
+                       rel_grad_norm=r.rel_grad_norm, zeta=r.zeta, sweeps=r.sweeps)
 
     def wait(self, ticket: int, timeout: float = 0.0) -> bool:
         st = lib().jd_server_wait(self.h, ticket, float(timeout))

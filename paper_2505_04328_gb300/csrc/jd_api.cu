@@ -501,9 +501,7 @@ static bool ensure_pair(jd_problem *p) {
   const bool stored = p->plan == JD_ADJ_STORED;
   const size_t cap = (size_t)(p->log_cap > 0 ? p->log_cap : 1);
   const size_t b_traj = (size_t)((q.Nt + 4) / 4) * p->D * M * 4 * es;
-  const size_t need = (size_t)q.Nt * p->DU * es + (size_t)p->nblk * 8 + n * 8 +
-                      (stored ? b_traj + cap * M * 2 * es + cap * M * p->D * es : recompute_bytes(p));
-  if (p->bytes + need > p->budget) return false;
+  if (p->bytes + jd::pair_bytes(q, p->plan) > p->budget) return false;
   jd_status s = dev_alloc(p, &p->uk2, (size_t)q.Nt * p->DU * es, "paired control");
   if (!s) s = dev_alloc(p, (void **)&p->partC2, (size_t)p->nblk * 8, "paired cost partials");
   if (!s) s = dev_alloc(p, (void **)&p->opt_ut2, n * 8, "paired trial");
@@ -805,7 +803,8 @@ static jd_status launch_grad(jd::OptMachine &m) {
   const int v = m.forward_done ? 1 : 0;
   jd_problem *p = m.p;
   if (m.o.resample) p->desc.epoch = m.epoch0 + (uint32_t)m.it;   // fresh sample per iteration
-  const jd_status s = run_phase(m, &m.g_grad[v], &m.n_grad[v], [&]() { return enqueue_grad(p, v == 1); });
+  const jd_status s =
+      run_phase(m, &m.g_grad[m.bank][v], &m.n_grad[m.bank][v], [&]() { return enqueue_grad(p, v == 1); });
   if (s) return s;
   m.forward_done = false;
   m.r.evals++;
@@ -828,7 +827,9 @@ static jd_status launch_trial(jd::OptMachine &m) {
   const bool want = m.backtracks == 0 && m.first_accepts < 2;
   m.pair = m.pairs && want && m.backtracks + 1 <= m.o.max_backtracks && ensure_pair(p);
   const bool pair = m.pair;
-  const jd_status s = run_phase(m, &m.g_trial, &m.n_trial, [&]() { return enqueue_trial(p, c, pair); });
+  const int v = pair ? 1 : 0;
+  const jd_status s =
+      run_phase(m, &m.g_trial[m.bank][v], &m.n_trial[m.bank][v], [&]() { return enqueue_trial(p, c, pair); });
   if (s) return s;
   m.r.evals++;
   m.r.sweeps++;
@@ -837,9 +838,12 @@ static jd_status launch_trial(jd::OptMachine &m) {
 }
 
 void jd::opt_release(OptMachine &m) {
-  for (auto &g : m.g_grad)
-    if (g) cudaGraphExecDestroy(g), g = nullptr;
-  if (m.g_trial) cudaGraphExecDestroy(m.g_trial), m.g_trial = nullptr;
+  for (auto &gb : m.g_grad)
+    for (auto &g : gb)
+      if (g) cudaGraphExecDestroy(g), g = nullptr;
+  for (auto &gb : m.g_trial)
+    for (auto &g : gb)
+      if (g) cudaGraphExecDestroy(g), g = nullptr;
 }
 
 // Final iterate to the caller's buffer.
@@ -870,9 +874,10 @@ jd_status jd::opt_begin(OptMachine &m, jd_problem *p, const jd_opt_params &o, do
   m.u_dst = u_dst;
   m.u_space = us;
   m.it = m.backtracks = m.grads = 0;
-  m.pairs = o.one_trial_per_sweep == 0 && !m.use_graphs;
+  m.pairs = o.one_trial_per_sweep == 0;
   m.first_accepts = 0;
   m.pair = false;
+  m.bank = 0;
   m.zeta = o.zeta0 > 0.0 ? o.zeta0 : 1.0;
   m.zeta_max = o.zeta_max > 0.0 ? o.zeta_max : 1e3;
   m.pg0 = -1.0;
@@ -922,7 +927,10 @@ jd_status jd::opt_advance(OptMachine &m) {
         m.r.evals++;
         m.zeta *= 0.5;
         ++m.backtracks;
-        if (h[S_ACC] == 2.0) swap_pair(p);   // its states become the plan's
+        if (h[S_ACC] == 2.0) {   // its states become the plan's
+          swap_pair(p);
+          m.bank ^= 1;   // graphs captured with the other assignment of the two sets
+        }
       }
       if (h[S_ACC] != 0.0) {
         m.forward_done = !m.o.resample;   // the trial's sweep is the next gradient's forward
@@ -1189,6 +1197,24 @@ size_t jd::problem_bytes_min(const jd_problem_desc &q) {
   const size_t es = q.prec == JD_FP64 ? 8 : 4;
   if (D != 32) return problem_bytes(q, JD_ADJ_RECOMPUTE);
   return base_bytes(q, D, DU, es) + stored_plan_bytes(q, D, es, TPB);
+}
+
+size_t jd::pair_bytes(const jd_problem_desc &q, jd_adjoint_mode plan) {
+  int D = 0, DU = 0;
+  pick_dims(q.d, q.du, &D, &DU);
+  if (D == 32) return 0;
+  const size_t es = q.prec == JD_FP64 ? 8 : 4, M = (size_t)q.M;
+  const int cap = log_capacity(q);
+  const size_t capa = (size_t)(cap > 0 ? cap : 1);
+  size_t b = (size_t)q.Nt * DU * es + (size_t)ceil_div(q.M, TPB) * 8 + (size_t)q.Nt * q.du * 8;
+  if (plan == JD_ADJ_STORED) {
+    b += (size_t)((q.Nt + 4) / 4) * D * M * 4 * es + capa * M * 2 * es + capa * M * D * es;
+  } else {
+    const jd::PathOps *ops = path_ops_dims(q.prec, D, DU);
+    const int S = ops ? ops->S : 16;
+    b += (size_t)(ceil_div(q.Nt, S) + 1) * D * M * es;
+  }
+  return b;
 }
 
 size_t jd::problem_bytes(const jd_problem_desc &q, jd_adjoint_mode plan) {

@@ -200,6 +200,9 @@ size_t problem_bytes(const jd_problem_desc &q, jd_adjoint_mode plan);
 // The least a problem can run in: RECOMPUTE for d <= 8; for d = 32 the stored plan in
 // blocks of 128 paths.
 size_t problem_bytes_min(const jd_problem_desc &q);
+// Device bytes of the second set of a plan's buffers that jd_optimize's paired Armijo
+// trials use (0 where pairs are not built: d = 32).  Host arithmetic only.
+size_t pair_bytes(const jd_problem_desc &q, jd_adjoint_mode plan);
 
 // Projected-gradient Armijo iteration (Algorithm 5.4) of one problem as a non-blocking
 // state machine: every phase (gradient; one line-search trial; the final copy of u)
@@ -226,10 +229,14 @@ struct OptMachine {
   bool pairs = false, pair = false;
   int first_accepts = 0;
   // CUDA graphs: each phase's launch sequence is captured on first use and replayed
-  // (gradient with and without the forward sweep, trial); kernels per graph counted
+  // (gradient with and without the forward sweep, single or paired trial), once per
+  // assignment of the problem's two buffer sets (bank: swapped when a pair's second
+  // point is taken); kernels per graph counted
   bool use_graphs = false;
-  cudaGraphExec_t g_grad[2] = {nullptr, nullptr}, g_trial = nullptr;
-  int n_grad[2] = {0, 0}, n_trial = 0;
+  int bank = 0;
+  cudaGraphExec_t g_grad[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  cudaGraphExec_t g_trial[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  int n_grad[2][2] = {{0, 0}, {0, 0}}, n_trial[2][2] = {{0, 0}, {0, 0}};
 };
 // p->u_in holds u^0.  u_dst (space us) receives the final iterate.
 jd_status opt_begin(OptMachine &m, ::jd_problem *p, const jd_opt_params &o, double *u_dst,

@@ -117,6 +117,10 @@ bool choose_plan(const jd_problem_desc &q, size_t budget, size_t free_b, jd_adjo
   if (need2 > free_b) return false;
   *plan = want;
   *bytes = need2;
+  // room for the second buffer set of jd_optimize's paired trials when it keeps the
+  // request within a quarter of the budget and what is free (else single trials)
+  const size_t pb = jd::pair_bytes(q, want);
+  if (pb && need2 + pb <= budget / 4 && need2 + pb <= free_b) *bytes = need2 + pb;
   return true;
 }
 
@@ -407,7 +411,7 @@ jd_status jd_server_info(jd_server *s, uint64_t ticket, jd_request_info *info) {
   info->plan = rq->plan;
   info->done = rq->done ? 1 : 0;
   info->path_steps = rq->done ? (int64_t)rq->grads * rq->desc.M * rq->desc.Nt : 0;
-  info->sweep_steps = rq->done ? (int64_t)rq->r.evals * rq->desc.M * rq->desc.Nt : 0;
+  info->sweep_steps = rq->done ? (int64_t)(rq->r.sweeps + rq->grads) * rq->desc.M * rq->desc.Nt : 0;
   return JD_OK;
 }
 

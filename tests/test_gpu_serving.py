@@ -61,10 +61,13 @@ def test_mixed_equals_solo():
     for p, (us, rs), (um, rm), inf in zip(reqs, solo, res, infos):
         assert rm["status"] == 0 and rs["status"] == 0
         assert rm["J"] == rs["J"] and rm["iters"] == rs["iters"] and rm["evals"] == rs["evals"]
+        # the same paired trials as alone (d <= 8 requests reserve their second buffer set)
+        assert rm["sweeps"] == rs["sweeps"], p.name
         assert np.array_equal(um, us), p.name
         assert 0 <= inf["submit_s"] <= inf["admit_s"] <= inf["done_s"]
-        assert inf["sweep_steps"] == rm["evals"] * p.M * p.Nt and inf["device_bytes"] > 0
-        assert 0 < inf["path_steps"] < inf["sweep_steps"] and inf["path_steps"] % (p.M * p.Nt) == 0
+        grads = inf["path_steps"] // (p.M * p.Nt)
+        assert inf["path_steps"] % (p.M * p.Nt) == 0 and grads > 0 and inf["device_bytes"] > 0
+        assert inf["sweep_steps"] == (rm["sweeps"] + grads) * p.M * p.Nt
     # the requests overlapped: some request was admitted before another one finished
     assert any(b["admit_s"] < a["done_s"] for a in infos for b in infos if a is not b)
 
