@@ -409,8 +409,10 @@ jd_status jd_fb_gradient(jd_problem *p, const jd_feedback_desc *fb, const double
  * updates.  The update kernels and the norms run on the device in FP64; the host reads
  * J and |g|^2 back for each decision.  mu_inout: Nt * L doubles in `space`, updated in
  * place; J_hist (host, max_iter + 1, nullable).  r->status is JD_ERR_LINESEARCH (also
- * returned) when max_backtracks halvings did not satisfy the test.  Other errors as
- * jd_fb_cost. */
+ * returned) when max_backtracks halvings did not satisfy the test.  With the exact
+ * adjoint and a fixed sample the trials keep their states and the accepted trial's sweep
+ * is the next gradient's forward half; r->sweeps counts the forward sweeps run.  Paired
+ * trials (one_trial_per_sweep) are not built here.  Other errors as jd_fb_cost. */
 jd_status jd_fb_optimize(jd_problem *p, const jd_feedback_desc *fb, double *mu_inout, jd_memspace space,
                          const jd_opt_params *o, jd_opt_result *r, double *J_hist);
 

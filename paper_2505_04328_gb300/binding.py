@@ -410,7 +410,8 @@ class JdProblem:
                                   _ptr(hist))
         if st not in (JD_OK, JD_ERR_LINESEARCH):
             _check(st, "jd_fb_optimize")
-        res = dict(iters=r.iters, evals=r.evals, status=r.status, J=r.J, rel_grad_norm=r.rel_grad_norm, zeta=r.zeta)
+        res = dict(iters=r.iters, evals=r.evals, status=r.status, J=r.J, rel_grad_norm=r.rel_grad_norm, zeta=r.zeta,
+                   sweeps=r.sweeps)
         return mu, res, hist[: r.iters + 1]
 
     def sample_paths(self, u, m0: int, count: int, lam: bool = True):

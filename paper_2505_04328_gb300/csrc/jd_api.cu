@@ -1531,8 +1531,12 @@ static jd_status fb_ensure(jd_problem *p, const FbOps *ops, bool grad) {
 
 // Forward (and with grad the adjoint) sweep under feedback, then the FP64 finalize into
 // scal_d[S_J] and grad_out (device, Nt*L; null for the cost only).
+// store: a cost evaluation that also keeps the states (the exact adjoint's forward half;
+// used for line-search trials).  forward_done: the states, the weights in kernel
+// precision and the cost partials already belong to mu (the accepted trial): only the
+// adjoint half runs.
 static jd_status fb_run(jd_problem *p, const jd_feedback_desc *fb, const double *mu, jd_memspace ms,
-                        double *grad_out) {
+                        double *grad_out, bool store = false, bool forward_done = false) {
   jd_status s = fb_validate(p, fb);
   if (s) return s;
   if (!mu) return fail(JD_ERR_INVALID_ARG, "mu is NULL");
@@ -1542,7 +1546,7 @@ static jd_status fb_run(jd_problem *p, const jd_feedback_desc *fb, const double 
   const int Nt = p->desc.Nt;
   const size_t L = (size_t)fb->nx * fb->nv;
   s = set_device(p);
-  if (!s) s = fb_ensure(p, ops, grad_out != nullptr);
+  if (!s) s = fb_ensure(p, ops, grad_out != nullptr || store);
   if (s) return s;
   const double *mud = mu;
   if (ms == JD_MEM_HOST) {
@@ -1550,7 +1554,7 @@ static jd_status fb_run(jd_problem *p, const jd_feedback_desc *fb, const double 
     JD_CUDA(cudaMemcpyAsync(p->fb_mu64, mu, (size_t)Nt * L * 8, cudaMemcpyHostToDevice, p->stream));
     mud = p->fb_mu64;
   }
-  JD_CUDA(ops->prep_mu(mud, p->fb_mu, Nt, fb->nx, fb->nv, p->stream));
+  if (!forward_done) JD_CUDA(ops->prep_mu(mud, p->fb_mu, Nt, fb->nx, fb->nv, p->stream));
   FbBufs b;
   b.mu = p->fb_mu;
   b.traj = p->fb_traj;
@@ -1565,9 +1569,9 @@ static jd_status fb_run(jd_problem *p, const jd_feedback_desc *fb, const double 
     pr = prof_begin(KC_FB_SUR, p->stream);
     JD_CUDA(ops->sur(p, *fb, b, p->stream));
     prof_end(pr, p->stream);
-  } else {
+  } else if (!forward_done) {
     pr = prof_begin(KC_FB_FWD, p->stream);
-    JD_CUDA(ops->fwd(p, *fb, grad_out != nullptr, b, p->stream));
+    JD_CUDA(ops->fwd(p, *fb, grad_out != nullptr || store, b, p->stream));
     prof_end(pr, p->stream);
   }
   if (grad_out) {
@@ -1650,9 +1654,15 @@ jd_status jd_fb_optimize(jd_problem *p, const jd_feedback_desc *fb, double *mu_i
     uint32_t e;
     ~EpochBack() { p->desc.epoch = e; }
   } epoch_back{p, epoch0};
+  // the accepted trial's forward sweep (states kept) is the next gradient's forward half
+  // (exact adjoint, one fixed sample)
+  const bool reuse = fb->adjoint == JD_FB_EXACT && !o->resample;
+  bool forward_done = false;
   for (it = 0; it < o->max_iter; ++it) {
     if (o->resample) p->desc.epoch = epoch0 + (uint32_t)it;   // fresh sample per iteration
-    s = fb_run(p, fb, p->fb_mu64, JD_MEM_DEVICE, p->fb_grad);
+    s = fb_run(p, fb, p->fb_mu64, JD_MEM_DEVICE, p->fb_grad, false, forward_done);
+    if (!forward_done) r->sweeps++;
+    forward_done = false;
     if (!s) JD_CUDA(fb_norm(p->fb_grad, n, dt, p->scal_d + S_PG, p->stream));
     if (!s) s = read_scalars(p, S_J, S_PG + 1);
     if (s) return s;
@@ -1670,10 +1680,11 @@ jd_status jd_fb_optimize(jd_problem *p, const jd_feedback_desc *fb, double *mu_i
     double Jt = 0.0;
     for (int b = 0; b <= o->max_backtracks; ++b) {
       JD_CUDA(fb_trial(p->fb_mu64, p->fb_grad, n, zeta, dt, p->fb_mut, p->stream));
-      s = fb_run(p, fb, p->fb_mut, JD_MEM_DEVICE, nullptr);
+      s = fb_run(p, fb, p->fb_mut, JD_MEM_DEVICE, nullptr, reuse);
       if (!s) s = read_scalars(p, S_J, 1);
       if (s) return s;
       r->evals++;
+      r->sweeps++;
       Jt = p->host_pinned[S_J];
       if (Jt <= J - o->armijo_c * zeta * g2) {
         accepted = true;
@@ -1686,6 +1697,7 @@ jd_status jd_fb_optimize(jd_problem *p, const jd_feedback_desc *fb, double *mu_i
       break;
     }
     std::swap(p->fb_mu64, p->fb_mut);   // mu^{n+1}
+    forward_done = reuse;
     J = Jt;
     if (J_hist) J_hist[it + 1] = J;
     if (zeta * pg < o->tol_step) {   // |mu^{n+1} - mu^n|_{L2} = zeta |g|_{L2}
