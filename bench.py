@@ -268,7 +268,7 @@ def run_ours(args):
            "d2h_bytes_per_step": n * 8 / args.steps + 64 * (1 + trials)}
 
     peaks, peak_kind = _peaks()
-    rl = {k: kernel_roofline(k, v, p, peaks, peak_kind, args.tc) for k, v in kstats.items()
+    rl = {k: kernel_roofline(k, v, p, peaks, peak_kind, args.tc, prob.info()["mode"]) for k, v in kstats.items()
           if k in KERNEL_BOUND}
     dom = max(rl, key=lambda k: kstats[k][1]) if rl else None
 
@@ -705,11 +705,14 @@ def issue_fraction(workload, name, units, per_launch_s, peaks):
             "frac": achieved / peak, "source": "ncu smsp__inst_executed.sum of a small case of the same kernel"}
 
 
-def kernel_roofline(name, stat, p, peaks, peak_kind, tc=0):
+def kernel_roofline(name, stat, p, peaks, peak_kind, tc=0, plan="stored"):
+    """plan: the adjoint plan, which decides the mode of the paired-trial sweep (states
+    stored or checkpoints); the captured counters belong to the stored plan's kernels."""
     launches, total_ms = stat
     per_launch_s = total_ms / launches * 1e-3
     units = p.M * p.Nt
-    tr = TRAFFIC_PER_PATH_STEP.get(name) if (p.d == 2 and p.name == "double_well") else None
+    captured = p.d == 2 and p.name == "double_well" and (name != "fwd_pair" or plan == "stored")
+    tr = TRAFFIC_PER_PATH_STEP.get(name) if captured else None
     traffic = None if tr is None else tr * units
     if KERNEL_BOUND[name] == "hbm":
         bytes_per = 4 * p.d + 0.125 + p.lam * p.dt * (2 + p.d) * 4
@@ -736,7 +739,7 @@ def kernel_roofline(name, stat, p, peaks, peak_kind, tc=0):
     if tc:
         flops = 2.0 * p.d * p.d * (3 if tc == 2 else 1) * units
         out["tensor_tflops"] = flops / per_launch_s / 1e12
-    iss = issue_fraction(p.name, name, units, per_launch_s, peaks)
+    iss = issue_fraction(p.name, name, units, per_launch_s, peaks) if captured or name != "fwd_pair" else None
     if iss:
         out["issue"] = iss
     return out
