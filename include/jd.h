@@ -203,7 +203,7 @@ jd_status jd_sample_paths(jd_problem *p, const double *u, jd_memspace us, int64_
  * zeta and r->evals are those of one trial per sweep; r->sweeps counts the forward
  * sweeps run (a pair counts one).  Needs a second set of the plan's path buffers within
  * the memory budget (else one trial per sweep); not with the block-wise stored plan
- * or d > 8. */
+ * nor for d > 4 (where a pair costs more than two single sweeps or saves nothing). */
 typedef struct {
   int max_iter;
   double tol_rel_grad, tol_step, armijo_c, zeta0, zeta_max;

@@ -490,12 +490,17 @@ static jd_status run_plan_forward(jd_problem *p, const double *ud, int slot) {
   return finalize_cost(p, ud, slot);
 }
 
+// Paired sweeps pay where the second control adds little to the draws' cost: d <= 4
+// (measured: a pair costs 1.2-1.36 single sweeps there; at d = 8 the second state and its
+// drift double the register footprint, 2.5 single sweeps in FP32).
+static bool pairs_built(int D) { return D <= 4; }
+
 // Second set of the plan's buffers for paired trials: allocated once, when the memory
-// budget holds it beside everything else; not for the block-wise stored plan nor d = 32.
+// budget holds it beside everything else; not for the block-wise stored plan nor d > 4.
 static bool ensure_pair(jd_problem *p) {
   if (p->pair_state) return p->pair_state > 0;
   p->pair_state = -1;
-  if (ensure_plan(p) || p->chunk || p->D == 32) return false;
+  if (!pairs_built(p->D) || ensure_plan(p) || p->chunk) return false;
   const jd_problem_desc &q = p->desc;
   const size_t es = elem_size(p), n = (size_t)q.Nt * q.du, M = (size_t)q.M;
   const bool stored = p->plan == JD_ADJ_STORED;
@@ -1202,7 +1207,7 @@ size_t jd::problem_bytes_min(const jd_problem_desc &q) {
 size_t jd::pair_bytes(const jd_problem_desc &q, jd_adjoint_mode plan) {
   int D = 0, DU = 0;
   pick_dims(q.d, q.du, &D, &DU);
-  if (D == 32) return 0;
+  if (!pairs_built(D)) return 0;
   const size_t es = q.prec == JD_FP64 ? 8 : 4, M = (size_t)q.M;
   const int cap = log_capacity(q);
   const size_t capa = (size_t)(cap > 0 ? cap : 1);

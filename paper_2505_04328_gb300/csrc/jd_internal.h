@@ -201,7 +201,7 @@ size_t problem_bytes(const jd_problem_desc &q, jd_adjoint_mode plan);
 // blocks of 128 paths.
 size_t problem_bytes_min(const jd_problem_desc &q);
 // Device bytes of the second set of a plan's buffers that jd_optimize's paired Armijo
-// trials use (0 where pairs are not built: d = 32).  Host arithmetic only.
+// trials use (0 where pairs are not used: d > 4).  Host arithmetic only.
 size_t pair_bytes(const jd_problem_desc &q, jd_adjoint_mode plan);
 
 // Projected-gradient Armijo iteration (Algorithm 5.4) of one problem as a non-blocking

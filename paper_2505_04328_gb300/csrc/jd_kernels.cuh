@@ -590,6 +590,10 @@ __device__ __forceinline__ void backward_step(const KParams<R, D, DU> &kp, const
 }
 
 // ---------------------------------------------------------------------------
+// Paired sweeps are compiled for d <= 4 (the host's pairs_built rule).
+template <int D>
+constexpr bool PAIR_SWEEPS = D <= 4;
+
 // Outputs of the second control of a paired sweep (PAIR): its control, cost partials,
 // stored states or checkpoints and jump-log states.  The jump flags and log counts are
 // the same for both controls and are written once.
@@ -1036,13 +1040,19 @@ cudaError_t op_fwd(const jd_problem *p, int mode, int64_t m_begin, int64_t mloc,
                                                            b.flags, nullptr, pc, jl, b.jcnt, mloc, p2);
       break;
     case FWD_STORE | FWD_PAIR:
-      fwd_kernel<R, D, DU, FWD_STORE, true><<<grid, TPB, 0, s>>>(*kp, u, xd, b.partC, static_cast<R *>(b.traj),
-                                                                 b.flags, nullptr, nullptr, jl, b.jcnt, mloc, p2);
-      break;
     case FWD_CKPT | FWD_PAIR:
-      fwd_kernel<R, D, DU, FWD_CKPT, true><<<grid, TPB, 0, s>>>(*kp, u, xd, b.partC, nullptr, nullptr,
-                                                                static_cast<R *>(b.ckpt), nullptr, jl, nullptr,
-                                                                mloc, p2);
+      if constexpr (PAIR_SWEEPS<D>) {   // the host asks for pairs only where they are built
+        if (mode & FWD_STORE)
+          fwd_kernel<R, D, DU, FWD_STORE, true><<<grid, TPB, 0, s>>>(*kp, u, xd, b.partC, static_cast<R *>(b.traj),
+                                                                     b.flags, nullptr, nullptr, jl, b.jcnt, mloc, p2);
+        else
+          fwd_kernel<R, D, DU, FWD_CKPT, true><<<grid, TPB, 0, s>>>(*kp, u, xd, b.partC, nullptr, nullptr,
+                                                                    static_cast<R *>(b.ckpt), nullptr, jl, nullptr,
+                                                                    mloc, p2);
+      } else {
+        delete kp;
+        return cudaErrorNotSupported;
+      }
       break;
     default:
       fwd_kernel<R, D, DU, FWD_CKPT><<<grid, TPB, 0, s>>>(*kp, u, xd, b.partC, nullptr, nullptr,
@@ -1109,8 +1119,7 @@ size_t op_stack_bytes() {
   size_t need = 2 * sizeof(JumpStep<R, D>) + 2048;
   const void *ks[] = {
       (const void *)fwd_kernel<R, D, DU, FWD_COST>, (const void *)fwd_kernel<R, D, DU, FWD_STORE>,
-      (const void *)fwd_kernel<R, D, DU, FWD_CKPT>, (const void *)fwd_kernel<R, D, DU, FWD_STORE, true>,
-      (const void *)fwd_kernel<R, D, DU, FWD_CKPT, true>, (const void *)adj_stored_kernel<R, D, DU, false>,
+      (const void *)fwd_kernel<R, D, DU, FWD_CKPT>, (const void *)adj_stored_kernel<R, D, DU, false>,
       (const void *)adj_stored_kernel<R, D, DU, false, true>,
       (const void *)adj_stored_kernel<R, D, DU, true>, (const void *)adj_recompute_kernel<R, D, DU, false>,
       (const void *)adj_recompute_kernel<R, D, DU, true>};
@@ -1118,6 +1127,14 @@ size_t op_stack_bytes() {
     cudaFuncAttributes a;
     if (cudaFuncGetAttributes(&a, k) == cudaSuccess && a.localSizeBytes + 1024 > need)
       need = a.localSizeBytes + 1024;
+  }
+  if constexpr (PAIR_SWEEPS<D>) {
+    for (const void *k : {(const void *)fwd_kernel<R, D, DU, FWD_STORE, true>,
+                          (const void *)fwd_kernel<R, D, DU, FWD_CKPT, true>}) {
+      cudaFuncAttributes a;
+      if (cudaFuncGetAttributes(&a, k) == cudaSuccess && a.localSizeBytes + 1024 > need)
+        need = a.localSizeBytes + 1024;
+    }
   }
   return (need + 255) & ~(size_t)255;
 }
