@@ -598,6 +598,18 @@ def run_serving(args):
     infos, results, wall, launches = serve(jd, reqs, opt, args.slots)
     clk = clocks.stop()
     mix = serve_stats(infos, results)
+    if args.mix_only:   # e.g. a rate below capacity: latency of the mix alone
+        line = {"metric": METRIC, "value": mix["path_steps_per_s"], "unit": UNIT, "n_gpus": ws,
+                "steps": len(reqs), "warmup": 0, "ms_per_step": mix["makespan_s"] * 1e3 / len(reqs),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": f"serving {len(reqs)} requests, Poisson arrivals {args.rate}/s",
+                           "slots": args.slots, "max_iter": args.max_iter, "tol_rel_grad": 1e-4},
+                "mix": mix, "latency_s": mix["latency_s"], "gpu_launches": launches, "roofline": None,
+                "clocks": clk}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return 0
 
     small = [(t, p) for t, p in reqs if p.d <= 8]
     i8, r8, _, _ = serve(jd, small, opt, args.slots)
@@ -759,6 +771,8 @@ def main():
     ap.add_argument("--slots", type=int, default=16, help="serving: requests in flight at most")
     ap.add_argument("--max-iter", type=int, default=50, help="serving: optimizer updates at most")
     ap.add_argument("--plain-sample", type=int, default=6, help="serving: requests timed in plain FP64")
+    ap.add_argument("--mix-only", action="store_true",
+                    help="serving: the whole stream only (no d <= 8 pass, no plain FP64 sample)")
     ap.add_argument("--tc", type=int, default=0, choices=[0, 1, 2],
                     help="tensor cores for the d=32 workload: 0 off, 1 BF16, 2 BF16x3")
     ap.add_argument("--paths", type=int, default=None, help="override M (paths per GPU)")
