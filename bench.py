@@ -267,6 +267,20 @@ def run_ours(args):
            "h2d_bytes_per_step": n * 8 / args.steps,
            "d2h_bytes_per_step": n * 8 / args.steps + 64 * (1 + trials)}
 
+    # gradient error of the FP32 path against FP64 at the final control: the FP64 GPU path
+    # on all paths (it equals the oracle within 1e-12 pathwise in the parity tests); the
+    # oracle itself on a path sample is compared in the cpu_baseline leg below
+    u_fin = u.cpu().numpy().reshape(Nt, du).copy()
+    grad_err = None
+    if prec == "fp32":
+        J32, g32, _ = prob.gradient(u_fin)
+        with jd.JdProblem(p, prec="fp64", mode=args.variant or "stored", stream=stream,
+                          use_tensor_cores=0) as p64:
+            J64, g64, _ = p64.gradient(u_fin)
+        grad_err = {"vs": "FP64 GPU path, all paths, at the final control",
+                    "J_rel": abs(J32 - J64) / abs(J64),
+                    "grad_rel_l2": float(np.linalg.norm(g32 - g64) / np.linalg.norm(g64))}
+
     peaks, peak_kind = _peaks()
     rl = {k: kernel_roofline(k, v, p, peaks, peak_kind, args.tc, prob.info()["mode"]) for k, v in kstats.items()
           if k in KERNEL_BOUND}
@@ -293,13 +307,23 @@ def run_ours(args):
             "roofline_all": rl,
             "e2e": e2e,
             "clocks": clk,
+            "grad_error_vs_fp64": grad_err,
         }
         if not args.no_cpu_baseline:
-            rate, sec, threads = oracle_step_rate(p.replace(M=min(M, args.reference_paths)), 1, 0)
+            ps = p.replace(M=min(M, args.reference_paths))
+            rate, sec, threads = oracle_step_rate(ps, 1, 0)
             line["cpu_baseline"] = {
                 "value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                 "sample": f"{args.reference_paths} of {M} paths, all {Nt} steps, one optimizer "
                           "iteration"}
+            # the same path sample in this path's precision against the oracle (FP64)
+            import oracle
+            with jd.JdProblem(ps, prec=prec, stream=stream, use_tensor_cores=args.tc) as q:
+                Js, gs, _ = q.gradient(u_fin)
+            Jo, go, _ = oracle.gradient(ps, u_fin)
+            line["grad_error_vs_oracle"] = {
+                "paths": ps.M, "J_rel": abs(Js - Jo) / abs(Jo),
+                "grad_rel_l2": float(np.linalg.norm(gs - go) / np.linalg.norm(go))}
         print(json.dumps(line), flush=True)
     prob.close()
     if dist is not None:
