@@ -404,6 +404,12 @@ def run_feedback(args, p, stream, dist, ws, rank, local):
     e2e_sec = (time.perf_counter() - t0) / args.steps
     e2e = {"value": ws * M * Nt / e2e_sec, "unit": UNIT, "h2d_bytes_per_step": Nt * L * 8,
            "d2h_bytes_per_step": Nt * L * 8 + 8}
+    # dJ/dmu of the FP32 path against the FP64 GPU path on all paths (the FP64 kernels
+    # equal the oracle within 1e-12 in the parity tests)
+    with jd.JdProblem(p, prec="fp64", stream=stream) as p64:
+        J64, g64 = p64.fb_gradient(fb, mu_h)
+    grad_err = {"vs": "FP64 GPU path, all paths", "J_rel": abs(Jh - J64) / abs(J64),
+                "grad_rel_l2": float(np.linalg.norm(gh - g64) / np.linalg.norm(g64))}
 
     peaks, _ = _peaks()
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
@@ -442,13 +448,19 @@ def run_feedback(args, p, stream, dist, ws, rank, local):
             "e2e": e2e,
             "clocks": clk,
             "J": J.value,
+            "grad_error_vs_fp64": grad_err,
         }
         if not args.no_cpu_baseline:
             import oracle
             ps = p.replace(M=min(M, args.reference_paths // 4))
             t0 = time.perf_counter()
-            oracle.fb_gradient(ps, fb, mu.cpu().numpy())
+            Jo, go = oracle.fb_gradient(ps, fb, mu_h)
             sec = time.perf_counter() - t0
+            with jd.JdProblem(ps, prec="fp32", stream=stream) as q:
+                Js, gs = q.fb_gradient(fb, mu_h)
+            line["grad_error_vs_oracle"] = {
+                "paths": ps.M, "J_rel": abs(Js - Jo) / abs(Jo),
+                "grad_rel_l2": float(np.linalg.norm(np.asarray(gs) - np.asarray(go)) / np.linalg.norm(go))}
             line["cpu_baseline"] = {
                 "value": ps.M * Nt / sec, "unit": UNIT,
                 "cores": 1 if fb.particles else oracle.default_threads(),   # the ring sweep is one thread
