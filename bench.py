@@ -272,7 +272,7 @@ def run_ours(args):
     # oracle itself on a path sample is compared in the cpu_baseline leg below
     u_fin = u.cpu().numpy().reshape(Nt, du).copy()
     grad_err = None
-    if prec == "fp32":
+    if prec == "fp32" and p.d <= 8:   # FP64 paths are built for d <= 8
         J32, g32, _ = prob.gradient(u_fin)
         with jd.JdProblem(p, prec="fp64", mode=args.variant or "stored", stream=stream,
                           use_tensor_cores=0) as p64:
@@ -534,6 +534,18 @@ def run_autograd(args, p, stream, dist, ws, rank, local):
     e2e = {"value": ws * M * Nt / e2e_sec, "unit": UNIT, "h2d_bytes_per_step": Nt * du * 8,
            "d2h_bytes_per_step": 8 + Nt * du * 8 + 3 * 8}
 
+    # dJ/du and the parameter gradients of the FP32 path against the FP64 GPU path on all
+    # paths (the problem's own coefficients, through the C ABI)
+    u_np = u.detach().cpu().numpy()
+    with jd.JdProblem(p, prec="fp32", mode=mode, stream=stream) as q32, \
+            jd.JdProblem(p, prec="fp64", mode=mode, stream=stream) as q64:
+        J32, g32, t32 = q32.gradient(u_np, theta=True)
+        J64, g64, t64 = q64.gradient(u_np, theta=True)
+    grad_err = {"vs": "FP64 GPU path, all paths, the problem's coefficients",
+                "J_rel": abs(J32 - J64) / abs(J64),
+                "grad_rel_l2": float(np.linalg.norm(g32 - g64) / np.linalg.norm(g64)),
+                "theta_rel": [float(abs(a - b) / abs(b)) for a, b in zip(t32, t64)]}
+
     peaks, peak_kind = _peaks()
     rl = {k: kernel_roofline(k, v, p, peaks, peak_kind) for k, v in kstats.items() if k in KERNEL_BOUND}
     dom = max(rl, key=lambda k: kstats[k][1]) if rl else None
@@ -542,6 +554,7 @@ def run_autograd(args, p, stream, dist, ws, rank, local):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "grad_error_vs_fp64": grad_err,
             "config": {"workload": f"double_well_autograd d=2 M={M} Nt={Nt}", "variant": mode,
                        "theta": "(damping 0.5, sigma 0.3, jump half-width 0.2)",
                        "step": "J(u, theta) forward + backward (dJ/du, dJ/dtheta) through the "
@@ -557,8 +570,14 @@ def run_autograd(args, p, stream, dist, ws, rank, local):
             import oracle
             ps = p.replace(M=min(M, 2048))
             t0 = time.perf_counter()
-            oracle.gradient(ps, u.detach().cpu().numpy(), theta=True)
+            Jo, go, to = oracle.gradient(ps, u_np, theta=True)
             sec = time.perf_counter() - t0
+            with jd.JdProblem(ps, prec="fp32", mode=mode, stream=stream) as q:
+                Js, gs, ts = q.gradient(u_np, theta=True)
+            line["grad_error_vs_oracle"] = {
+                "paths": ps.M, "J_rel": abs(Js - Jo) / abs(Jo),
+                "grad_rel_l2": float(np.linalg.norm(gs - go) / np.linalg.norm(go)),
+                "theta_rel": [float(abs(a - b) / abs(b)) for a, b in zip(ts, to)]}
             line["cpu_baseline"] = {"value": ps.M * ps.Nt / sec, "unit": UNIT,
                                     "cores": oracle.default_threads(), "kind": "oracle",
                                     "sample": f"{ps.M} of {M} paths, all {Nt} steps, one gradient "
