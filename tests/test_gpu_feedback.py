@@ -221,3 +221,22 @@ def test_feedback_resampling_descent_follows_the_oracle():
     assert r["iters"] == ro["iters"] and r["evals"] == ro["evals"]
     assert np.max(np.abs(h - ho) / np.abs(ho)) <= 1e-10
     assert np.max(np.abs(mu - muo)) <= 1e-9 * np.max(np.abs(muo))
+
+
+def test_optimizer_reuses_the_accepted_trial_sweep():
+    """With the exact adjoint and a fixed sample each gradient after the first takes the
+    accepted trial's sweep as its forward half: forward sweeps = 1 + trials, i.e. evals
+    minus the iterations plus one; the resampled descent (new sample per gradient) and the
+    surrogate adjoint (its own forward) run one sweep per evaluation.  The J history
+    equals the costs of the iterates evaluated afresh."""
+    p, fb = workloads.feedback_centering(M=700, Nt=20)
+    p = p.replace(lam=6.0)
+    with JdProblem(p, prec="fp64") as jp:
+        mu, r, h = jp.fb_optimize(fb, max_iter=4, tol_rel_grad=0.0)
+        assert r["status"] == 0 and r["iters"] == 4 and r["sweeps"] == r["evals"] - r["iters"] + 1
+        assert jp.fb_cost(fb, mu) == pytest.approx(h[-1], rel=1e-13)
+        _, rr, _ = jp.fb_optimize(fb, max_iter=3, tol_rel_grad=0.0, resample=True)
+        assert rr["sweeps"] == rr["evals"]
+        _, rs, _ = jp.fb_optimize(fb.replace(adjoint=workloads.FB_SURROGATE, sur_rate=0.05), max_iter=3,
+                                  tol_rel_grad=0.0)
+        assert rs["sweeps"] == rs["evals"]
