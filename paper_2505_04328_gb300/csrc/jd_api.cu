@@ -507,6 +507,7 @@ static bool ensure_pair(jd_problem *p) {
   const size_t cap = (size_t)(p->log_cap > 0 ? p->log_cap : 1);
   const size_t b_traj = (size_t)((q.Nt + 4) / 4) * p->D * M * 4 * es;
   if (p->bytes + jd::pair_bytes(q, p->plan) > p->budget) return false;
+  const std::string saved_error = g_last_error;   // a failed allocation here is not the caller's error
   jd_status s = dev_alloc(p, &p->uk2, (size_t)q.Nt * p->DU * es, "paired control");
   if (!s) s = dev_alloc(p, (void **)&p->partC2, (size_t)p->nblk * 8, "paired cost partials");
   if (!s) s = dev_alloc(p, (void **)&p->opt_ut2, n * 8, "paired trial");
@@ -514,7 +515,10 @@ static bool ensure_pair(jd_problem *p) {
   if (!s && stored) s = dev_alloc(p, &p->log_kt2, cap * M * 2 * es, "paired jump log");
   if (!s && stored) s = dev_alloc(p, &p->log_y2, cap * M * p->D * es, "paired jump log states");
   if (!s && !stored) s = dev_alloc(p, &p->ckpt2, recompute_bytes(p), "paired checkpoints");
-  if (s) return false;   // what was allocated is freed with the problem
+  if (s) {   // single trials; what was allocated is freed with the problem
+    g_last_error = saved_error;
+    return false;
+  }
   p->pair_state = 1;
   return true;
 }
