@@ -850,7 +850,10 @@ adj_recompute_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__re
                      const R *__restrict__ xd, const R *__restrict__ ckpt,
                      double *__restrict__ partG, double *__restrict__ partT, int64_t mloc) {
   using M = Ar<R>;
-  constexpr int JS = seg_log_cap<D>();
+  // the parameter-gradient backward regenerates every jump step (it needs the sub-steps'
+  // normals), so its replay keeps no jump log: no shared log, more blocks per SM
+  constexpr int JS = THETA ? 0 : seg_log_cap<D>();
+  using LWR = typename std::conditional<THETA, NoLog, LogWriter<R, D>>::type;
   extern __shared__ __align__(16) unsigned char dsm[];
   constexpr bool ZBUF = recompute_zbuf<R, D, THETA>();
   R *sbuf = reinterpret_cast<R *>(dsm);   // [S * D][TPB] segment states
@@ -883,21 +886,26 @@ adj_recompute_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__re
 #pragma unroll
     for (int c = 0; c < D; ++c) x[c] = __ldg(ckpt + ((size_t)seg * D + c) * mloc + lmc);
     uint32_t jm = 0;
-    LogWriter<R, D> lw;
-    lw.L = sl;
-    lw.idx = tid;
+    LWR lw;
+    if constexpr (!THETA) {
+      lw.L = sl;
+      lw.idx = tid;
+    }
 #pragma unroll 1
     for (int i = 0; i < len; ++i) {
 #pragma unroll
       for (int c = 0; c < D; ++c) sbuf[(i * D + c) * TPB + tid] = x[c];
-      if (forward_step<R, D, DU, LogWriter<R, D>, ZBUF, !THETA>(kp, k0 + i, m, u, x, lw,
-                                                                zbuf + (size_t)i * D * TPB + tid, TPB))
+      if (forward_step<R, D, DU, LWR, ZBUF, !THETA>(kp, k0 + i, m, u, x, lw, zbuf + (size_t)i * D * TPB + tid,
+                                                    TPB))
         jm |= 1u << i;
     }
     LogReader<R, D> lr;
     lr.L = sl;
     lr.idx = tid;
-    lr.init(lw.r);
+    if constexpr (THETA)
+      lr.init(0);   // empty: every jump step is regenerated
+    else
+      lr.init(lw.r);
     const int nb = (len + BATCH - 1) / BATCH;
 #pragma unroll 1
     for (int bb = nb - 1; bb >= 0; --bb) {
@@ -1067,7 +1075,7 @@ cudaError_t op_fwd(const jd_problem *p, int mode, int64_t m_begin, int64_t mloc,
 template <typename R, int D, int DU>
 constexpr size_t recompute_smem(bool theta) {
   return (size_t)seg_len<D>() * D * TPB * sizeof(R) * (theta && recompute_zbuf<R, D, true>() ? 2 : 1) +
-         (size_t)seg_log_cap<D>() * (2 + D) * TPB * sizeof(R) + (theta ? (size_t)BATCH * DU * TPB * sizeof(R) : 0);
+         (theta ? (size_t)BATCH * DU * TPB * sizeof(R) : (size_t)seg_log_cap<D>() * (2 + D) * TPB * sizeof(R));
 }
 
 template <typename R, int D, int DU>
