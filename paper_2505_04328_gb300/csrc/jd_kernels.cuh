@@ -829,9 +829,13 @@ adj_stored_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restr
   finish_theta<R, D, DU, THETA>(kp, th, active, partT, red1);
 }
 
+// Jump-log records per path and checkpoint segment in the recompute adjoint's shared
+// memory (a segment whose jumps do not fit regenerates them).  Four records hold a
+// 16-step segment's jumps except with probability below 1e-5 at lambda dt = 0.01, and
+// keep the d = 2 block at 24 KB (8 blocks per SM, the register limit).
 template <int D>
 __host__ __device__ constexpr int seg_log_cap() {
-  return D <= 2 ? 8 : 4;
+  return 4;
 }
 
 
