@@ -125,3 +125,14 @@ def test_paired_trials_fall_back_when_the_budget_holds_one_set():
         r1, r2 = _pair_vs_single(jp, max_iter=6)
         assert jp.info()["device_bytes"] == need
     assert r2["sweeps"] == r1["sweeps"]
+
+
+def test_paired_trials_at_the_benchmark_size():
+    """The benchmark workload at full size (d = 2, M = 2^20, N_t = 1000, stored plan): three
+    iterations with paired trials and with one trial per sweep give bitwise the same
+    iterates and J history; the paired run takes fewer sweeps."""
+    p = workloads.double_well()
+    with JdProblem(p, prec="fp32", mode="stored") as jp:
+        r1, r2 = _pair_vs_single(jp, max_iter=3, zeta0=2.0)
+    assert r1["status"] == 0 and r1["iters"] == 3
+    assert r2["sweeps"] <= r1["sweeps"]
