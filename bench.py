@@ -293,7 +293,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32",
             "data": "synthetic",
             "config": {"workload": f"{args.workload} d={p.d} M={M} Nt={Nt}",
-                       "tensor_cores": {0: "off", 1: "bf16", 2: "bf16x3"}[args.tc],
+                       "tensor_cores": {0: "off", 1: "bf16", 2: "bf16x3", 3: "bf16x3 adjoint only"}[args.tc],
                        "variant": prob.info()["mode"], "paths_per_gpu": M, "Nt": Nt,
                        "evals_per_step": evals / args.steps,
                        "sweeps_per_step": r["sweeps"] / args.steps,
@@ -794,6 +794,7 @@ def kernel_roofline(name, stat, p, peaks, peak_kind, tc=0, plan="stored"):
         if iss:
             out["issue"] = iss
         return out
+    tc = 0 if tc == 3 else tc   # mode 3: the forward runs on the CUDA cores
     ops = forward_ops(p, tc, 2 if name == "fwd_pair" else 1) + (adjoint_ops(p) if name == "adj_recompute" else 0.0)
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     peak = 152 * 4 * 32 * sm_mhz * 1e6 / 1e9   # G lane-operations per second
@@ -828,8 +829,9 @@ def main():
     ap.add_argument("--plain-sample", type=int, default=6, help="serving: requests timed in plain FP64")
     ap.add_argument("--mix-only", action="store_true",
                     help="serving: the whole stream only (no d <= 8 pass, no plain FP64 sample)")
-    ap.add_argument("--tc", type=int, default=0, choices=[0, 1, 2],
-                    help="tensor cores for the d=32 workload: 0 off, 1 BF16, 2 BF16x3")
+    ap.add_argument("--tc", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="tensor cores for the d=32 workload: 0 off, 1 BF16, 2 BF16x3, "
+                         "3 BF16x3 in the adjoint only")
     ap.add_argument("--paths", type=int, default=None, help="override M (paths per GPU)")
     ap.add_argument("--steps-t", type=int, default=None, help="override N_t")
     ap.add_argument("--reference-paths", type=int, default=1 << 14)

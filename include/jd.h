@@ -93,7 +93,9 @@ typedef enum { JD_MEM_HOST = 0, JD_MEM_DEVICE = 1 } jd_memspace;
  *   use_tensor_cores  8 < d <= 32 only: the drift contraction A x (and A^T lambda in the
  *                adjoint) of each 128-path tile as one tcgen05 MMA per step: 1 = BF16
  *                inputs, FP32 accumulation; 2 = BF16 high + low parts, three products
- *                (about 16 mantissa bits); 0 = FP32 on the CUDA cores
+ *                (about 16 mantissa bits); 3 = the forward on the CUDA cores in FP32 and
+ *                the adjoint's A^T lambda as in 2 (the forward is bound by its draws,
+ *                the adjoint by the contraction); 0 = FP32 on the CUDA cores
  *   mem_budget_bytes  device bytes this problem may allocate, 0 = library default
  *                (half of the free device memory at creation)
  *   cuda_stream  cudaStream_t for all work of this problem; NULL = the library

@@ -244,7 +244,8 @@ class JdProblem:
     drift, A, C, B, dA, sigma, lam, jump_law, jump_scale, jump_gain, x0, q, xd, nu, u_min, u_max,
     seed, epoch).  ``stream``: a torch.cuda.Stream, a raw cudaStream_t int, or None for
     torch's current stream (a library-owned stream when torch has no CUDA).
-    ``use_tensor_cores`` (8 < d <= 32): 0 CUDA cores, 1 BF16 tensor cores, 2 BF16 x3.
+    ``use_tensor_cores`` (8 < d <= 32): 0 CUDA cores, 1 BF16 tensor cores, 2 BF16 x3,
+    3 CUDA-core forward with the BF16 x3 tensor-core adjoint.
     """
 
     def __init__(self, problem, prec="fp32", mode="auto", stream=None, mem_budget: int = 0,

@@ -38,7 +38,7 @@ static cudaError_t op32_fwd(const jd_problem *p, int mode, int64_t m_begin, int6
     case 2:
       fwd32_kernel<2><<<grid, TPB, 0, s>>>(kp, u, bu, xd, b.partC, traj, b.flags, pc, jl, b.jcnt, b.status, mloc);
       break;
-    default:
+    default:   // 0, and 3 (tensor cores in the adjoint only)
       fwd32_kernel<0><<<grid, TPB, 0, s>>>(kp, u, bu, xd, b.partC, traj, b.flags, pc, jl, b.jcnt, b.status, mloc);
       break;
   }
@@ -63,6 +63,7 @@ static cudaError_t op32_adj(const jd_problem *p, int variant, bool theta, int64_
       adj32_kernel<1><<<grid, TPB, 0, s>>>(kp, u, xd, traj, b.flags, jl, b.jcnt, b.partG, lo, b.status, mloc);
       break;
     case 2:
+    case 3:   // BF16 x3 in the adjoint after an FP32 CUDA-core forward
       adj32_kernel<2><<<grid, TPB, 0, s>>>(kp, u, xd, traj, b.flags, jl, b.jcnt, b.partG, lo, b.status, mloc);
       break;
     default:

@@ -712,8 +712,9 @@ static jd_status validate_desc(const jd_problem_desc &q) {
     return fail(JD_ERR_INVALID_ARG, "jump_scale must be finite and >= 0");
   if (!std::isfinite(q.nu) || q.nu < 0.0) return fail(JD_ERR_INVALID_ARG, "nu must be finite and >= 0");
   if (!(q.u_min <= q.u_max)) return fail(JD_ERR_INVALID_ARG, "u_min must be <= u_max");
-  if (q.use_tensor_cores < 0 || q.use_tensor_cores > 2)
-    return fail(JD_ERR_INVALID_ARG, "use_tensor_cores must be 0, 1 (BF16) or 2 (BF16 x3)");
+  if (q.use_tensor_cores < 0 || q.use_tensor_cores > 3)
+    return fail(JD_ERR_INVALID_ARG,
+                "use_tensor_cores must be 0, 1 (BF16), 2 (BF16 x3) or 3 (BF16 x3 in the adjoint only)");
   if (q.use_tensor_cores && q.d <= 8)
     return fail(JD_ERR_UNSUPPORTED, "tensor cores are used for 8 < d <= 32 (linear drift, FP32)");
   const size_t dd = (size_t)q.d * q.d, dn = (size_t)(q.Nt + 1) * q.d;

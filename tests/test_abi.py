@@ -135,6 +135,7 @@ def _desc(**over):
     (dict(sigma=None), binding.JD_ERR_INVALID_ARG),
     (dict(prec=4), binding.JD_ERR_INVALID_ARG),
     (dict(use_tensor_cores=1), binding.JD_ERR_UNSUPPORTED),
+    (dict(use_tensor_cores=4), binding.JD_ERR_INVALID_ARG),
 ])
 def test_invalid_descriptors_rejected_before_cuda(jdlib, over, status):
     st, h = _create(_desc(**over))

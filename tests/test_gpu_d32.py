@@ -8,6 +8,8 @@
   pathwise <= 1e-2, J and gradient relative L2 <= 1e-2 (measured values are printed).
 * use_tensor_cores = 2 (BF16 high + low parts, three products, ~16 mantissa bits):
   pathwise <= 2e-5, gradient relative L2 <= 5e-5.
+* use_tensor_cores = 3 (the forward of 0, the adjoint of 2): the states of 0 bit for bit,
+  the adjoint and gradient within the bounds of 2.
 Steps with jumps run on the CUDA cores in every mode.
 """
 import numpy as np
@@ -19,7 +21,7 @@ from paper_2505_04328_gb300 import JdProblem, build
 
 pytestmark = pytest.mark.gpu
 
-BOUNDS = {0: (1e-5, 1e-5), 1: (1e-2, 1e-2), 2: (2e-5, 5e-5)}
+BOUNDS = {0: (1e-5, 1e-5), 1: (1e-2, 1e-2), 2: (2e-5, 5e-5), 3: (2e-5, 5e-5)}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -44,7 +46,7 @@ CASES = {
 }
 
 
-@pytest.mark.parametrize("tc", [0, 1, 2])
+@pytest.mark.parametrize("tc", [0, 1, 2, 3])
 @pytest.mark.parametrize("case", sorted(CASES))
 def test_d32_paths_and_gradient(case, tc):
     p = CASES[case]()
@@ -120,3 +122,18 @@ def test_d32_block_wise_stored_plan_is_bitwise_equal(tc):
     for J, g, ub, Jr, hist in out[1:]:
         assert J == out[0][0] and np.array_equal(g, out[0][1])
         assert np.array_equal(ub, out[0][2]) and Jr == out[0][3] and np.array_equal(hist, out[0][4])
+
+
+def test_d32_adjoint_only_mode_keeps_the_cuda_core_forward():
+    """Mode 3 runs the CUDA-core forward of mode 0: states, per-path costs and J bit for
+    bit (its BF16 x3 adjoint is checked against the oracle above)."""
+    p = CASES["linear32"]()
+    u = workloads.random_control(p, seed=22, scale=0.5)
+    out = {}
+    for tc in (0, 3):
+        with JdProblem(p, prec="fp32", use_tensor_cores=tc) as jp:
+            X, _, c = jp.sample_paths(u, 0, p.M, lam=False)
+            J, g, _ = jp.gradient(u)
+        out[tc] = (X, c, J, g)
+    assert np.array_equal(out[3][0], out[0][0]) and np.array_equal(out[3][1], out[0][1])
+    assert out[3][2] == out[0][2]
