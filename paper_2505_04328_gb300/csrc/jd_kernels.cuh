@@ -662,11 +662,13 @@ fwd_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u
   HotFwd<R, D, DU> khv;
   if constexpr (PIN) khv = hot_fwd(kp);
   const KH &kh = coef_src<PIN>(kp, khv);
-  // the loop is not unrolled, which keeps the step's code small
+  // the single sweep's loop is not unrolled, which keeps the step's code small; the pair
+  // sweep's is unrolled twice
   R b0[D], b1[D], b2[D], c0[D], c1[D], c2[D];
 #pragma unroll
   for (int c = 0; c < D; ++c) b0[c] = b1[c] = b2[c] = c0[c] = c1[c] = c2[c] = R(0);
-#pragma unroll 1
+  constexpr int UNR = PAIR ? 2 : 1;
+#pragma unroll UNR
   for (int k = 0; k <= Nt; ++k) {
     if (MODE == FWD_STORE) {
       stage_state<R, D>(traj, k, Nt, mloc, lm, active, x, b0, b1, b2);
