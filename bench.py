@@ -749,13 +749,13 @@ def adjoint_ops(p):
 # DRAM bytes (read + write) per path-step of the d = 2 kernels from one ncu capture
 # (profiles/fwd_store_adj_stored_double_well_d2_M2p16_Nt1000.md: M = 2^16, N_t = 1000,
 # scaled per path-step); set to None whenever a kernel changes after its capture.
-TRAFFIC_PER_PATH_STEP = {"fwd_store": 7.71, "fwd_pair": 16.67, "adj_stored": 8.81}
+TRAFFIC_PER_PATH_STEP = {"fwd_store": 7.71, "fwd_pair": 16.68, "adj_stored": 8.81}
 
 # Warp-instructions issued per warp-step (32 path-steps) from the same kind of ncu capture
 # (smsp__inst_executed.sum / warp-steps; profiles/*.md): with the measured time they give
 # the fraction of the SM's issue rate (4 schedulers x 1 instruction per clock) the kernel
 # uses, next to the algorithmic fraction; None when the kernel changed since the capture.
-INST_PER_WARP_STEP = {("double_well", "fwd_store"): 287, ("double_well", "fwd_pair"): 379,
+INST_PER_WARP_STEP = {("double_well", "fwd_store"): 287, ("double_well", "fwd_pair"): 343,
                       ("double_well", "adj_stored"): 108,
                       ("double_well", "adj_recompute"): 352, ("feedback_centering", "fb_fwd"): 830,
                       ("feedback_centering", "fb_adj"): 1224}
