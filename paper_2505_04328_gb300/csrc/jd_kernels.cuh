@@ -20,6 +20,7 @@
 //   partT [D+2][nblk]                     FP64 block sums of the parameter sensitivities
 #pragma once
 
+#include <atomic>
 #include <type_traits>
 
 #include "jd_device.cuh"
@@ -662,12 +663,13 @@ fwd_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u
   HotFwd<R, D, DU> khv;
   if constexpr (PIN) khv = hot_fwd(kp);
   const KH &kh = coef_src<PIN>(kp, khv);
-  // the single sweep's loop is not unrolled, which keeps the step's code small; the pair
-  // sweep's is unrolled twice
+  // the loop of the single store and cost sweeps is not unrolled, which keeps the step's
+  // code small (unrolled twice they ran slower); the pair and checkpoint sweeps' loops are
+  // unrolled twice (faster, measured)
   R b0[D], b1[D], b2[D], c0[D], c1[D], c2[D];
 #pragma unroll
   for (int c = 0; c < D; ++c) b0[c] = b1[c] = b2[c] = c0[c] = c1[c] = c2[c] = R(0);
-  constexpr int UNR = PAIR ? 2 : 1;
+  constexpr int UNR = (PAIR || MODE == FWD_CKPT) ? 2 : 1;
 #pragma unroll UNR
   for (int k = 0; k <= Nt; ++k) {
     if (MODE == FWD_STORE) {
@@ -1110,15 +1112,22 @@ cudaError_t op_adj(const jd_problem *p, int variant, bool theta, int64_t m_begin
   } else {
     const size_t smem = recompute_smem<R, D, DU>(theta);
     const R *ck = static_cast<const R *>(b.ckpt);
-    if (theta) {
-      err = cudaFuncSetAttribute(adj_recompute_kernel<R, D, DU, true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (err == cudaSuccess)
+    // the dynamic shared-memory limit is a property of the function: set once per process
+    // (one device per process)
+    // (it is not a stream operation, and a call per launch sat between the phases)
+    static std::atomic<bool> set_theta{false}, set_plain{false};
+    std::atomic<bool> &done = theta ? set_theta : set_plain;
+    if (!done.load(std::memory_order_acquire)) {
+      err = theta ? cudaFuncSetAttribute(adj_recompute_kernel<R, D, DU, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                  : cudaFuncSetAttribute(adj_recompute_kernel<R, D, DU, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (err == cudaSuccess) done.store(true, std::memory_order_release);
+    }
+    if (err == cudaSuccess) {
+      if (theta)
         adj_recompute_kernel<R, D, DU, true><<<grid, TPB, smem, s>>>(*kp, u, xd, ck, b.partG, b.partT, mloc);
-    } else {
-      err = cudaFuncSetAttribute(adj_recompute_kernel<R, D, DU, false>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (err == cudaSuccess)
+      else
         adj_recompute_kernel<R, D, DU, false><<<grid, TPB, smem, s>>>(*kp, u, xd, ck, b.partG, b.partT, mloc);
     }
   }
