@@ -664,12 +664,13 @@ fwd_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u
   if constexpr (PIN) khv = hot_fwd(kp);
   const KH &kh = coef_src<PIN>(kp, khv);
   // the loop of the single store and cost sweeps is not unrolled, which keeps the step's
-  // code small (unrolled twice they ran slower); the pair and checkpoint sweeps' loops are
-  // unrolled twice (faster, measured)
+  // code small (unrolled twice they ran slower); for d <= 2 the pair and checkpoint
+  // sweeps' loops are unrolled twice (faster, measured; at d = 4 the unrolled pair sweep
+  // took twice as long)
   R b0[D], b1[D], b2[D], c0[D], c1[D], c2[D];
 #pragma unroll
   for (int c = 0; c < D; ++c) b0[c] = b1[c] = b2[c] = c0[c] = c1[c] = c2[c] = R(0);
-  constexpr int UNR = (PAIR || MODE == FWD_CKPT) ? 2 : 1;
+  constexpr int UNR = ((PAIR || MODE == FWD_CKPT) && D <= 2) ? 2 : 1;
 #pragma unroll UNR
   for (int k = 0; k <= Nt; ++k) {
     if (MODE == FWD_STORE) {
