@@ -333,12 +333,12 @@ static int log_capacity(const jd_problem_desc &q) {
 }
 
 // Bytes of the stored plan for M paths: states, jump flags, jump log (at least one
-// record per path is allocated) and the per-path log counts.
+// record per path is allocated) and the per-path log counts and closing steps.
 static size_t stored_plan_bytes(const jd_problem_desc &q, int D, size_t es, int64_t M) {
   const int cap = log_capacity(q);
   const size_t capa = (size_t)(cap > 0 ? cap : 1);
-  return (size_t)((q.Nt + 4) / 4) * D * M * 4 * es + (size_t)ceil_div(q.Nt, 32) * M * 4 +
-         capa * M * 2 * es + capa * M * D * es + (size_t)M * 4;
+  return traj_values(q.Nt, D, (int)es, M) * es + (size_t)ceil_div(q.Nt, 32) * M * 4 + capa * M * 2 * es +
+         capa * M * D * es + (size_t)M * 8;
 }
 
 static size_t stored_bytes(const jd_problem *p) {
@@ -398,7 +398,7 @@ static jd_status ensure_plan(jd_problem *p) {
       p->chunk = c;
       M = c;
     }
-    jd_status s = dev_alloc(p, &p->traj, (size_t)((p->desc.Nt + 4) / 4) * p->D * M * 4 * elem_size(p),
+    jd_status s = dev_alloc(p, &p->traj, traj_values(p->desc.Nt, p->D, (int)elem_size(p), M) * elem_size(p),
                             "trajectory");
     if (s) return s;
     s = dev_alloc(p, (void **)&p->flags, (size_t)ceil_div(p->desc.Nt, 32) * M * 4, "jump flags");
@@ -409,7 +409,7 @@ static jd_status ensure_plan(jd_problem *p) {
     if (s) return s;
     s = dev_alloc(p, &p->log_y, cap * M * p->D * elem_size(p), "jump log states");
     if (s) return s;
-    s = dev_alloc(p, (void **)&p->jcnt, (size_t)M * 4, "jump log counts");
+    s = dev_alloc(p, (void **)&p->jcnt, (size_t)M * 8, "jump log counts");
     if (s) return s;
   } else {
     jd_status s = dev_alloc(p, &p->ckpt, recompute_bytes(p), "checkpoints");
@@ -505,7 +505,7 @@ static bool ensure_pair(jd_problem *p) {
   const size_t es = elem_size(p), n = (size_t)q.Nt * q.du, M = (size_t)q.M;
   const bool stored = p->plan == JD_ADJ_STORED;
   const size_t cap = (size_t)(p->log_cap > 0 ? p->log_cap : 1);
-  const size_t b_traj = (size_t)((q.Nt + 4) / 4) * p->D * M * 4 * es;
+  const size_t b_traj = traj_values(q.Nt, p->D, (int)es, (int64_t)M) * es;
   if (p->bytes + jd::pair_bytes(q, p->plan) > p->budget) return false;
   const std::string saved_error = g_last_error;   // a failed allocation here is not the caller's error
   jd_status s = dev_alloc(p, &p->uk2, (size_t)q.Nt * p->DU * es, "paired control");
@@ -1218,7 +1218,7 @@ size_t jd::pair_bytes(const jd_problem_desc &q, jd_adjoint_mode plan) {
   const size_t capa = (size_t)(cap > 0 ? cap : 1);
   size_t b = (size_t)q.Nt * DU * es + (size_t)ceil_div(q.M, TPB) * 8 + (size_t)q.Nt * q.du * 8;
   if (plan == JD_ADJ_STORED) {
-    b += (size_t)((q.Nt + 4) / 4) * D * M * 4 * es + capa * M * 2 * es + capa * M * D * es;
+    b += traj_values(q.Nt, D, (int)es, (int64_t)M) * es + capa * M * 2 * es + capa * M * D * es;
   } else {
     const jd::PathOps *ops = path_ops_dims(q.prec, D, DU);
     const int S = ops ? ops->S : 16;
@@ -1394,8 +1394,8 @@ jd_status jd_sample_paths(jd_problem *p, const double *u, jd_memspace us, int64_
   const jd_problem_desc &q = p->desc;
   const int D = p->D, Nt = q.Nt, d = q.d;
   const size_t es = elem_size(p);
-  const int64_t nb = ceil_div(count, TPB), ng = (Nt + 4) / 4;
-  const size_t traj_b = (size_t)ng * D * count * 4 * es, flag_b = (size_t)ceil_div(Nt, 32) * count * 4;
+  const int64_t nb = ceil_div(count, TPB);
+  const size_t traj_b = traj_values(Nt, D, (int)es, count) * es, flag_b = (size_t)ceil_div(Nt, 32) * count * 4;
   const size_t lam_b = (size_t)(Nt + 1) * D * count * es;
   const int cap = log_capacity(q);
   const size_t capa = (size_t)(cap > 0 ? cap : 1);
@@ -1409,7 +1409,7 @@ jd_status jd_sample_paths(jd_problem *p, const double *u, jd_memspace us, int64_
   if (e == cudaSuccess) e = cudaMalloc(&pG, (size_t)Nt * p->DU * grad_parts(count) * 8);
   if (e == cudaSuccess) e = cudaMalloc(&lkt, capa * count * 2 * es);
   if (e == cudaSuccess) e = cudaMalloc(&ly, capa * count * D * es);
-  if (e == cudaSuccess) e = cudaMalloc(&jc, (size_t)count * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&jc, (size_t)count * 8);
   PathBufs b;
   b.traj = traj;
   b.flags = (uint32_t *)flags;
@@ -1456,10 +1456,7 @@ jd_status jd_sample_paths(jd_problem *p, const double *u, jd_memspace us, int64_
       for (int c = 0; c < d; ++c) {
         const size_t base = (size_t)(i * (Nt + 1) + k) * d + c;
         if (X) {
-          const size_t ti = p->ops->traj_layout == 0
-                                ? ((((size_t)(k >> 2) * D + c) * count + i) * 4) + (k & 3)
-                                : ((((size_t)k * (D / 4) + (c >> 2)) * count + i) * 4) + (c & 3);
-          X[base] = rd(ht, ti);
+          X[base] = rd(ht, traj_index(k, c, i, count, D, (int)es));
         }
         if (lam) lam[base] = rd(hl, ((size_t)k * D + c) * count + i);
       }

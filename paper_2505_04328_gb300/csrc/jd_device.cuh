@@ -231,6 +231,144 @@ __device__ __forceinline__ void reduce_batch(Pair<R> (&gb)[BATCH][DU], int kbase
 }
 
 // ---------------------------------------------------------------------------
+// Per-warp rows of per-step gradient contributions (the adjoint kernels of d <= 8).
+// Every lane writes its path's contribution of step k to row k mod NR (one shared store
+// per step).  Every NR steps the rows become one FP64 partial per (step, control, warp),
+// partG[(k DU + l) npart + warp_id], with no block barrier:
+//   NR = 16: lane l sums row l/2 over lanes 16 (l % 2) .. +15, one shuffle joins the
+//            halves (fewer instructions per step);
+//   NR = 8:  lane l sums row l/4 over lanes 8 (l % 4) .. +7, two shuffles join the
+//            quarters (half the shared memory).
+// Both evaluate the same tree of compensated (TwoSum) pairs over the warp's lanes
+// (L_i = lane i), so a kernel may take either and the gradient keeps its bits:
+//     a_q = L4q + L4q+2, b_q = L4q+1 + L4q+3                      (q = 0..7)
+//     c_h = a_4h + a_4h+1, d_h = b_4h + b_4h+1                   (quarters, h = 0..3)
+//     e_H = c_2H + c_2H+1, f_H = d_2H + d_2H+1;  s_H = e_H + f_H   (halves, H = 0, 1)
+//     sum = s_0 + s_1
+// Row stride 36 values, the second half of a double row moved by 2 values: the row
+// stores and the 16-byte row reads are free of bank conflicts.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct RowGeom {
+  static constexpr int LD = 36;                          // values per row
+  static constexpr int HALF = sizeof(R) == 8 ? 18 : 16;   // column of lane 16
+};
+
+template <typename R, int DU, int NR>
+__host__ __device__ constexpr size_t grad_rows_bytes() {   // per block
+  return (size_t)(TPB / 32) * DU * NR * RowGeom<R>::LD * sizeof(R);
+}
+
+// TwoSum of two pairs (a, b) with zero error terms, two lanes at once (FP32: one FADD2
+// per operation; FP64: scalar).  Per component the operations of padd.
+template <typename R>
+__device__ __forceinline__ void two_sum2(R a0, R a1, R b0, R b1, Pair<R> &r0, Pair<R> &r1) {
+  if constexpr (Pr<R>::on) {
+    R s0, s1, bb0, bb1, t0, t1, u0, u1, v0, v1, e0, e1;
+    Pr<R>::add(a0, a1, b0, b1, s0, s1);
+    Pr<R>::sub(s0, s1, a0, a1, bb0, bb1);
+    Pr<R>::sub(s0, s1, bb0, bb1, t0, t1);
+    Pr<R>::sub(a0, a1, t0, t1, u0, u1);
+    Pr<R>::sub(b0, b1, bb0, bb1, v0, v1);
+    Pr<R>::add(u0, u1, v0, v1, e0, e1);
+    r0 = {s0, e0};
+    r1 = {s1, e1};
+  } else {
+    r0 = padd(Pair<R>{a0, R(0)}, Pair<R>{b0, R(0)});
+    r1 = padd(Pair<R>{a1, R(0)}, Pair<R>{b1, R(0)});
+  }
+}
+
+// padd of two independent pairs of pairs: r0 = a0 + b0, r1 = a1 + b1.
+template <typename R>
+__device__ __forceinline__ void padd2(Pair<R> a0, Pair<R> a1, Pair<R> b0, Pair<R> b1, Pair<R> &r0, Pair<R> &r1) {
+  if constexpr (Pr<R>::on) {
+    R s0, s1, bb0, bb1, t0, t1, u0, u1, v0, v1, e0, e1, w0, w1, x0, x1;
+    Pr<R>::add(a0.s, a1.s, b0.s, b1.s, s0, s1);
+    Pr<R>::sub(s0, s1, a0.s, a1.s, bb0, bb1);
+    Pr<R>::sub(s0, s1, bb0, bb1, t0, t1);
+    Pr<R>::sub(a0.s, a1.s, t0, t1, u0, u1);
+    Pr<R>::sub(b0.s, b1.s, bb0, bb1, v0, v1);
+    Pr<R>::add(u0, u1, v0, v1, e0, e1);
+    Pr<R>::add(a0.e, a1.e, b0.e, b1.e, w0, w1);
+    Pr<R>::add(w0, w1, e0, e1, x0, x1);
+    r0 = {s0, x0};
+    r1 = {s1, x1};
+  } else {
+    r0 = padd(a0, b0);
+    r1 = padd(a1, b1);
+  }
+}
+
+// Row values at cols c0 .. c0 + N - 1 (16-byte reads).
+template <typename R, int N>
+__device__ __forceinline__ void row_read(const R *src, R (&v)[N]) {
+  if constexpr (sizeof(R) == 4) {
+#pragma unroll
+    for (int q = 0; q < N / 4; ++q) {
+      const float4 t = reinterpret_cast<const float4 *>(src)[q];
+      v[4 * q] = t.x;
+      v[4 * q + 1] = t.y;
+      v[4 * q + 2] = t.z;
+      v[4 * q + 3] = t.w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < N / 2; ++q) {
+      const double2 t = reinterpret_cast<const double2 *>(src)[q];
+      v[2 * q] = t.x;
+      v[2 * q + 1] = t.y;
+    }
+  }
+}
+
+template <typename R, int DU, int NR = 16>
+struct GradRows {
+  static_assert(NR == 8 || NR == 16, "8 or 16 rows");
+  R *w;   // this warp's rows [DU][NR][LD]
+  __device__ __forceinline__ void init(R *block_rows) {
+    w = block_rows + (size_t)(threadIdx.x >> 5) * DU * NR * RowGeom<R>::LD;
+  }
+  static __device__ __forceinline__ int col(int lane) { return lane + (lane >> 4) * (RowGeom<R>::HALF - 16); }
+  // contribution g of the step in row j (= k mod NR); inactive lanes add 0
+  __device__ __forceinline__ void put(int j, const R (&g)[DU], bool active) {
+    const int c = col(threadIdx.x & 31);
+#pragma unroll
+    for (int l = 0; l < DU; ++l) w[(l * NR + j) * RowGeom<R>::LD + c] = active ? g[l] : R(0);
+  }
+  // rows of steps kbase .. kbase + NR - 1 (those < Nt) -> FP64 warp partials
+  __device__ __forceinline__ void flush(int kbase, int Nt, double *__restrict__ partG, int64_t npart) {
+    __syncwarp();
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (int64_t)blockIdx.x * (TPB / 32) + (threadIdx.x >> 5);
+    constexpr int SPAN = 32 / (32 / NR);   // lanes summed by one reader: 16 or 8
+    const int r = lane / (32 / NR), part = lane % (32 / NR);
+#pragma unroll
+    for (int l = 0; l < DU; ++l) {
+      R v[SPAN];
+      row_read<R, SPAN>(w + (l * NR + r) * RowGeom<R>::LD + col(part * SPAN), v);
+      Pair<R> a[SPAN / 4], b[SPAN / 4];
+#pragma unroll
+      for (int q = 0; q < SPAN / 4; ++q) two_sum2(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3], a[q], b[q]);
+      Pair<R> c0, d0, e, f;
+      padd2(a[0], b[0], a[1], b[1], c0, d0);
+      if constexpr (NR == 16) {
+        Pair<R> c1, d1;
+        padd2(a[2], b[2], a[3], b[3], c1, d1);
+        padd2(c0, d0, c1, d1, e, f);
+      } else {
+        padd2(c0, d0, shfl_xor(c0, 1), shfl_xor(d0, 1), e, f);
+      }
+      Pair<R> s = padd(e, f);
+      s = padd(s, shfl_xor(s, 32 / NR / 2));
+      const int k = kbase + r;
+      if (part == 0 && k < Nt) partG[((int64_t)k * DU + l) * npart + wid] = (double)s.s + (double)s.e;
+    }
+    __syncwarp();
+  }
+};
+
+// ---------------------------------------------------------------------------
 // Model: drift f = A x + C x^3 + B u and its transposed Jacobian
 // ---------------------------------------------------------------------------
 template <typename KP, typename R, int D, int DU>
@@ -499,11 +637,17 @@ __device__ __forceinline__ void apply_jump(const KParams<R, D, DU> &kp, R *y, co
 // Adjoint across a jump: mu (derivative w.r.t. the post-jump state) times the map's
 // Jacobian, the identity for the additive laws and gamma on the reset velocities.
 // (jgain_c = 1 leaves mu_c unchanged bit for bit, so the additive laws need no branch)
-template <typename R, int D, int DU>
-__device__ __forceinline__ void jump_adjoint(const KParams<R, D, DU> &kp, R *mu) {
+template <typename KP, typename R>
+__device__ __forceinline__ void jump_adjoint(const KP &kp, R *mu) {
   using M = Ar<R>;
+  constexpr int D = sizeof(kp.jgain) / sizeof(kp.jgain[0]);
+  if constexpr (Pr<R>::on && D % 2 == 0) {
 #pragma unroll
-  for (int c = 0; c < D; ++c) mu[c] = M::mul(kp.jgain[c], mu[c]);
+    for (int c = 0; c < D; c += 2) Pr<R>::mul(kp.jgain[c], kp.jgain[c + 1], mu[c], mu[c + 1], mu[c], mu[c + 1]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < D; ++c) mu[c] = M::mul(kp.jgain[c], mu[c]);
+  }
 }
 
 // One Euler sub-step y <- y + de f(y, u) + sigma sqrt(de) z (the form every jump path uses).

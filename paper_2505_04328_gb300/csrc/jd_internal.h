@@ -67,7 +67,7 @@ struct PathBufs {
 // Per-instantiation launch table (one entry per precision x compiled dimension).
 struct PathOps {
   int D, DU, S, elem;
-  int traj_layout;   // 0: [ceil((Nt+1)/4)][D][M][4]; 1: [Nt+1][D/4][M][4]
+  int traj_layout;   // unused: every instantiation stores states as traj_shape(D, elem) says
   // per-thread stack bytes the kernels of this instantiation may need (the jump path
   // keeps its sub-step states in local memory behind a non-inlined call)
   size_t (*stack_bytes)();
@@ -124,6 +124,31 @@ int compiled_dim(int d);         // smallest compiled D >= d, or 0
 void count_launch(int n = 1);
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Stored trajectories are 16-byte vectors of VW = 16 / elem values.  A group of SV
+// consecutive steps of one path fills VD vectors, and the value of (step g SV + j,
+// component c) sits at position j D + c of its group:  traj[g][v][mloc][VW].  So the
+// components of one step are adjacent (the paired FP32 arithmetic takes them as one
+// 64-bit operand) and a warp's vector loads cover 512 contiguous bytes.
+//   FP32: D = 1 -> 4 steps per vector, D = 2 -> 2, D = 4 -> 1, D = 8 -> 2 vectors per
+//   step, D = 32 -> 8 (the tensor-core tiles).  FP64: D = 1 -> 2 steps, D >= 2 -> D/2.
+struct TrajShape {
+  int VW, SV, VD;
+};
+constexpr TrajShape traj_shape(int D, int elem) {
+  return TrajShape{16 / elem, D >= 16 / elem ? 1 : (16 / elem) / D, D >= 16 / elem ? D / (16 / elem) : 1};
+}
+// Values (of elem bytes) of the stored states X_0..X_Nt of M paths.
+inline size_t traj_values(int Nt, int D, int elem, int64_t M) {
+  const TrajShape t = traj_shape(D, elem);
+  return (size_t)((Nt + t.SV) / t.SV) * t.VD * (size_t)M * t.VW;
+}
+// Index of the value (step k, component c) of local path i among `count` paths.
+inline size_t traj_index(int k, int c, int64_t i, int64_t count, int D, int elem) {
+  const TrajShape t = traj_shape(D, elem);
+  const int pos = (k % t.SV) * D + c;
+  return (((size_t)(k / t.SV) * t.VD + pos / t.VW) * (size_t)count + (size_t)i) * t.VW + pos % t.VW;
+}
 
 // Gradient partials per launch of mloc paths: one per warp of every block.
 inline int64_t grad_parts(int64_t mloc) { return ceil_div(mloc, TPB) * (TPB / 32); }

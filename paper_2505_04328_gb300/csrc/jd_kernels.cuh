@@ -12,20 +12,67 @@
 //                   shared memory, then swept backwards.  Same arithmetic, same bits.
 //
 // Layouts (mloc = paths of the launch, lm = local path index):
-//   traj  [ceil((Nt+1)/4)][D][mloc][4]  states X_k, k = 4g + j, 16-byte vector stores
+//   traj  [ceil((Nt+1)/SV)][VD][mloc][VW] states X_k in 16-byte vectors (traj_shape: the
+//                                        components of a step adjacent, SV steps a group)
 //   flags [ceil(Nt/32)][mloc]           bit k%32 set when step k had a jump
+//   jcnt  [2][mloc]                      jump-log records per path; first step not logged
 //   ckpt  [nseg+1][D][mloc]              X_{sS} for s < nseg, X_Nt at s = nseg
 //   partC [nblk]                          FP64 block sums of the per-path cost
 //   partG [Nt][DU][nblk * TPB/32]         FP64 warp sums of the control sensitivities
 //   partT [D+2][nblk]                     FP64 block sums of the parameter sensitivities
 #pragma once
 
-#include <atomic>
+#include <map>
+#include <mutex>
 #include <type_traits>
+#include <utility>
 
 #include "jd_device.cuh"
 
 namespace jd {
+
+// One 16-byte vector of VW = 16 / sizeof(R) values (the unit of the stored trajectory).
+template <typename R>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  static __device__ __forceinline__ void store(float *p, const float (&v)[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+  static __device__ __forceinline__ void load(const float *p, float (&o)[4]) {
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+  }
+};
+template <>
+struct Vec16<double> {
+  static __device__ __forceinline__ void store(double *p, const double (&v)[2]) {
+    *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+  }
+  static __device__ __forceinline__ void load(const double *p, double (&o)[2]) {
+    const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+    o[0] = v.x; o[1] = v.y;
+  }
+};
+
+template <typename R, int D>
+struct TS {
+  static constexpr TrajShape s = traj_shape(D, (int)sizeof(R));
+  static constexpr int VW = s.VW, SV = s.SV, VD = s.VD;
+};
+
+// Asynchronous 16-byte copies global -> shared (cp.async, L2 only): each thread stages
+// the vectors it will read itself, so a thread waits for its own copies only
+// (cp.async.wait_group) and no barrier is needed.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 template <typename R>
 struct Vec4;
@@ -54,11 +101,13 @@ struct Vec4<double> {
 
 // ---------------------------------------------------------------------------
 // Jump log: for every step with jumps, the post-jump sub-states of the jump-adapted
-// grid in time order (one record per jump: step index k, time fraction theta, state
-// Y right after the jump).  A step is logged only when all its records fit, so a
-// backward sweep that finds record k == step k has the step's whole sub-grid; any
-// other jump step is regenerated from the counter-based streams.
-//   kt[r * stride + idx] = (k, theta),   y[(r * D + c) * stride + idx] = Y_c
+// grid in time order (one record per jump: step index k with the jump's position i
+// within its step, time fraction theta, state Y right after the jump).  A step is logged
+// only when all its records fit, and the first step that does not fit closes the log, so
+// the logged steps are exactly the jump steps before that one; any other jump step is
+// regenerated from the counter-based streams.
+//   kt[r * stride + idx] = (16 k + i, theta),   y[(r * D + c) * stride + idx] = Y_c
+// (16 k + i < 2^24 is exact in FP32 for N_t < 2^20; i < NMAX = 16)
 // ---------------------------------------------------------------------------
 template <typename R>
 struct V2;
@@ -86,9 +135,20 @@ struct LogWriter {
   JLog<R, D> L;
   int64_t idx;
   int r = 0;
+  int kovf = 0x7fffffff;   // first step whose records did not fit
   __device__ __forceinline__ bool fits(int n) const { return r + n <= L.cap; }
-  __device__ __forceinline__ void put(int k, R theta, const R (&y)[D]) {
-    L.kt[(int64_t)r * L.stride + idx] = V2<R>::make((R)k, theta);
+  // Whether the n records of step k fit.  A step that does not fit closes the log, so
+  // the logged steps are exactly the jump steps before kovf: a backward sweep that has
+  // not reached kovf regenerates nothing.
+  __device__ __forceinline__ bool take(int n, int k) {
+    if (r + n <= L.cap) return true;
+    kovf = min(kovf, k);
+    L.cap = r;
+    return false;
+  }
+  // record of the i-th jump (time order) of step k
+  __device__ __forceinline__ void put(int k, int i, R theta, const R (&y)[D]) {
+    L.kt[(int64_t)r * L.stride + idx] = V2<R>::make((R)(16 * k + i), theta);
 #pragma unroll
     for (int c = 0; c < D; ++c) L.y[((int64_t)r * D + c) * L.stride + idx] = y[c];
     ++r;
@@ -101,9 +161,12 @@ struct LogReader {
   int64_t idx;
   int rec;   // latest unconsumed record, -1 when empty
   R rk;      // its step index (or -1)
+  __device__ __forceinline__ R step_of(int r) const {
+    return r >= 0 ? (R)(((int)L.kt[(int64_t)r * L.stride + idx].x) >> 4) : R(-1);
+  }
   __device__ __forceinline__ void init(int count) {
     rec = count - 1;
-    rk = rec >= 0 ? L.kt[(int64_t)rec * L.stride + idx].x : R(-1);
+    rk = step_of(rec);
   }
   __device__ __forceinline__ bool has(int k) const { return rk == (R)k; }
   __device__ __forceinline__ void pop(R &theta, R (&y)[D]) {
@@ -111,7 +174,67 @@ struct LogReader {
 #pragma unroll
     for (int c = 0; c < D; ++c) y[c] = L.y[((int64_t)rec * D + c) * L.stride + idx];
     --rec;
-    rk = rec >= 0 ? L.kt[(int64_t)rec * L.stride + idx].x : R(-1);
+    rk = step_of(rec);
+  }
+};
+
+// Reads the log backwards for sweeps that know from the jump flags which steps had jumps
+// (every jump step before the log's closing step is logged).  The current record (its
+// time fraction, post-jump state and position within its step) waits in registers; a
+// pop hands it over and loads the next one, which is needed only at the path's next jump
+// step.  The popped record's position tells whether another record of the same step
+// follows, so no pop waits for a load except within a step of two or more jumps.
+template <typename R, int D>
+struct LogReader2 {
+  const typename V2<R>::T *kt;   // row of the current record in this path's column
+  const R *y;
+  int64_t stride;
+  int rec;                        // index of the current record (-1: none left)
+  int ci;                         // current record: position within its step,
+  R cth, cy[D];                   // time fraction, post-jump state
+  __device__ __forceinline__ void load() {
+    const typename V2<R>::T t = kt[0];
+    ci = ((int)t.x) & 15;
+    cth = t.y;
+#pragma unroll
+    for (int c = 0; c < D; ++c) cy[c] = y[(int64_t)c * stride];
+  }
+  __device__ __forceinline__ void init(const JLog<R, D> &L, int64_t idx, int count) {
+    stride = L.stride;
+    rec = count - 1;
+    const int64_t r0 = max(rec, 0);
+    kt = L.kt + r0 * stride + idx;
+    y = L.y + r0 * D * stride + idx;
+    if (count > 0) load();
+  }
+  // take: hand over the current record (position i within its step, time fraction theta,
+  // state yo) and load the next one; otherwise theta = 1, yo = x, i = 0 and the reader
+  // keeps its record (it loads the same row again).  No branch.
+  __device__ __forceinline__ int pop_if(bool take, const R (&x)[D], R &theta, R (&yo)[D]) {
+    theta = take ? cth : R(1);
+#pragma unroll
+    for (int c = 0; c < D; ++c) yo[c] = take ? cy[c] : x[c];
+    const int i = take ? ci : 0;
+    const int64_t back = (take && rec > 0) ? stride : 0;
+    kt -= back;
+    y -= back * D;
+    rec -= take ? 1 : 0;
+    load();
+    return i;
+  }
+  // hands over the current record; returns its position within its step (another record
+  // of the same step follows when it is > 0)
+  __device__ __forceinline__ int pop(R &theta, R (&yo)[D]) {
+    theta = cth;
+#pragma unroll
+    for (int c = 0; c < D; ++c) yo[c] = cy[c];
+    const int i = ci;
+    const int64_t back = rec > 0 ? stride : 0;   // the last record is reloaded, not passed
+    kt -= back;
+    y -= back * D;
+    --rec;
+    load();
+    return i;
   }
 };
 
@@ -171,7 +294,7 @@ __device__ __forceinline__ void one_jump_inline(const KParams<R, D, DU> &kp, int
 #pragma unroll
   for (int c = 0; c < D; ++c) x[c] = M::add(x[c], M::mul(kp.jump_scale, xih[c]));
   if constexpr (!std::is_same<LW, NoLog>::value) {
-    if (lw.fits(1)) lw.put(k, th, x);
+    if (lw.take(1, k)) lw.put(k, 0, th, x);
   }
   euler_substep(kp, M::mul(kp.dt, M::sub(R(1), th)), z1, uk, x);
 }
@@ -226,7 +349,7 @@ __device__ __forceinline__ int step_from_draws(const KParams<R, D, DU> &kp, cons
 #pragma unroll
     for (int c = 0; c < D; ++c) x[c] = xc[c];
     if constexpr (LOG) {
-      if (lw.fits(1)) lw.put(k, th, y1);
+      if (lw.take(1, k)) lw.put(k, 0, th, y1);
     }
     return 1;
   }
@@ -251,12 +374,12 @@ __device__ __forceinline__ int step_from_draws(const KParams<R, D, DU> &kp, cons
 #pragma unroll
   for (int c = 0; c < D; ++c) x[c] = S.Y[S.n + 1][c];
   if constexpr (LOG) {
-    if (lw.fits(S.n)) {
+    if (lw.take(S.n, k)) {
       for (int i = 0; i < S.n; ++i) {
         R y[D];
 #pragma unroll
         for (int c = 0; c < D; ++c) y[c] = S.Y[i + 1][c];
-        lw.put(k, S.th[i], y);
+        lw.put(k, i, S.th[i], y);
       }
     }
   }
@@ -434,12 +557,22 @@ struct HotFwd {
 
 // Coefficients of the adjoint step (A, C, B, dt, q dt) held in registers for a kernel's
 // step loop.  Each value passes through an empty asm statement, so the compiler cannot
-// rematerialise it from the parameter bank at every use inside the loop.
-template <typename R, int D, int DU>
-struct HotCoef {
-  R A[D * D], C[D * D], B[D * DU], qdt[D];
-  R dt;
+// rematerialise it from the parameter bank at every use inside the loop.  CUB = 0 or 1
+// makes the drift family a compile-time constant (no branch on it in the loop); -1 reads
+// it at run time.
+template <int CUB>
+struct CubicFlag {
+  static constexpr int cubic = CUB;
+};
+template <>
+struct CubicFlag<-1> {
   int cubic;
+};
+template <typename R, int D, int DU, int CUB = -1>
+struct HotCoef : CubicFlag<CUB> {
+  R A[D * D], C[D * D], B[D * DU], qdt[D], jgain[D];
+  R dt;
+  int jump_law;
 };
 
 __device__ __forceinline__ float reg_pin(float v) {
@@ -451,20 +584,27 @@ __device__ __forceinline__ double reg_pin(double v) {
   return v;
 }
 
-template <typename R, int D, int DU>
-__device__ __forceinline__ HotCoef<R, D, DU> hot_coef(const KParams<R, D, DU> &kp) {
-  HotCoef<R, D, DU> h;
+// withB = false zeroes B: the control sensitivities of that thread are then exactly 0
+// (an inactive thread of the last block, which replays path 0, adds nothing without a
+// select per step).
+template <int CUB = -1, typename R, int D, int DU>
+__device__ __forceinline__ HotCoef<R, D, DU, CUB> hot_coef(const KParams<R, D, DU> &kp, bool withB = true) {
+  HotCoef<R, D, DU, CUB> h;
 #pragma unroll
   for (int i = 0; i < D * D; ++i) {
     h.A[i] = reg_pin(kp.A[i]);
-    h.C[i] = kp.cubic ? reg_pin(kp.C[i]) : R(0);
+    h.C[i] = (CUB == 1 || (CUB == -1 && kp.cubic)) ? reg_pin(kp.C[i]) : R(0);
   }
 #pragma unroll
-  for (int i = 0; i < D * DU; ++i) h.B[i] = reg_pin(kp.B[i]);
+  for (int i = 0; i < D * DU; ++i) h.B[i] = reg_pin(withB ? kp.B[i] : R(0));
 #pragma unroll
-  for (int c = 0; c < D; ++c) h.qdt[c] = reg_pin(kp.qdt[c]);
+  for (int c = 0; c < D; ++c) {
+    h.qdt[c] = reg_pin(kp.qdt[c]);
+    h.jgain[c] = reg_pin(kp.jgain[c]);
+  }
   h.dt = reg_pin(kp.dt);
-  h.cubic = kp.cubic;
+  h.jump_law = kp.jump_law;
+  if constexpr (CUB == -1) h.cubic = kp.cubic;
   return h;
 }
 
@@ -590,6 +730,164 @@ __device__ __forceinline__ void backward_step(const KParams<R, D, DU> &kp, const
   }
 }
 
+// Target row x_d(t_k): D values, as vector loads where the row's size and alignment allow.
+template <typename R, int D>
+__device__ __forceinline__ void load_row(const R *__restrict__ p, R (&o)[D]) {
+  if constexpr (sizeof(R) == 4 && D % 4 == 0) {
+#pragma unroll
+    for (int c = 0; c < D; c += 4) {
+      const float4 v = __ldg(reinterpret_cast<const float4 *>(p + c));
+      o[c] = v.x; o[c + 1] = v.y; o[c + 2] = v.z; o[c + 3] = v.w;
+    }
+  } else if constexpr (sizeof(R) == 4 && D % 2 == 0) {
+#pragma unroll
+    for (int c = 0; c < D; c += 2) {
+      const float2 v = __ldg(reinterpret_cast<const float2 *>(p + c));
+      o[c] = v.x; o[c + 1] = v.y;
+    }
+  } else if constexpr (sizeof(R) == 8 && D % 2 == 0) {
+#pragma unroll
+    for (int c = 0; c < D; c += 2) {
+      const double2 v = __ldg(reinterpret_cast<const double2 *>(p + c));
+      o[c] = v.x; o[c + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < D; ++c) o[c] = __ldg(p + c);
+  }
+}
+
+// mu += q dt (X_k - x_d(t_k)): the running cost's gradient at a grid point k >= 1 (the
+// operations of backward_step's last part).
+template <typename KH, typename R, int D>
+__device__ __forceinline__ void cost_gradient(const KH &kh, const R (&xk)[D], const R (&xdk)[D], R (&mu)[D]) {
+  using M = Ar<R>;
+  if constexpr (Pr<R>::on && D % 2 == 0) {
+#pragma unroll
+    for (int c = 0; c < D; c += 2) {
+      R e0, e1;
+      Pr<R>::sub(xk[c], xk[c + 1], xdk[c], xdk[c + 1], e0, e1);
+      Pr<R>::fma(kh.qdt[c], kh.qdt[c + 1], e0, e1, mu[c], mu[c + 1]);
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < D; ++c) mu[c] = M::fma(kh.qdt[c], M::sub(xk[c], xdk[c]), mu[c]);
+  }
+}
+
+// Backward through step k (no parameter gradients) when the log holds the step's jump
+// sub-grid (jumped: the step had jumps), or the step had no jump: the logged sub-steps in
+// reverse (sub-step i from its post-jump state Y_i over delta_i = dt (theta_{i+1} -
+// theta_i), then back across the jump that produced Y_i), then sub-step 0 from X_k over
+// dt theta_1, which is dt for a step without jumps.  The operations of backward_step's log
+// branch, and of jump_backward sub-step by sub-step, so the result is the same bits
+// whichever form a sweep takes.  maybe = false: no lane of the warp jumped at step k (a
+// warp-uniform hint).  The cost term at t_k is the caller's.
+// One logged sub-step backwards: the record's sub-step, then back across its jump.
+template <typename R, int D, int DU, typename KH>
+__device__ __forceinline__ int logged_substep(const KH &kh, R (&mu)[D], R (&g)[DU], R &thn, LogReader2<R, D> &lr) {
+  using M = Ar<R>;
+  R the, y[D];
+  const int i = lr.pop(the, y);
+  const R de = M::mul(kh.dt, M::sub(thn, the));
+  control_sensitivity(kh, mu, de, g);
+  adjoint_update(kh, y, de, mu);
+  jump_adjoint(kh, mu);   // the identity for the additive laws (times 1, bit for bit)
+  thn = the;
+  return i;
+}
+
+// The records of a step's second and later jumps (rare: out of line, on copies).
+template <typename R, int D, int DU, typename KH>
+__device__ __noinline__ void logged_more(const KH kh, R *mu_io, R *g_io, R *thn_io, LogReader2<R, D> *lr) {
+  R mu[D], g[DU], thn = *thn_io;
+#pragma unroll
+  for (int c = 0; c < D; ++c) mu[c] = mu_io[c];
+#pragma unroll
+  for (int l = 0; l < DU; ++l) g[l] = g_io[l];
+  int i;
+  do {
+    i = logged_substep(kh, mu, g, thn, *lr);
+  } while (i > 0);
+#pragma unroll
+  for (int c = 0; c < D; ++c) mu_io[c] = mu[c];
+#pragma unroll
+  for (int l = 0; l < DU; ++l) g_io[l] = g[l];
+  *thn_io = thn;
+}
+
+template <typename R, int D, int DU, typename KH>
+__device__ __forceinline__ void backward_logged(const KH &kh, const R (&xk)[D], R (&mu)[D], R (&g)[DU],
+                                                LogReader2<R, D> &lr, bool maybe, bool jumped) {
+  using M = Ar<R>;
+#pragma unroll
+  for (int l = 0; l < DU; ++l) g[l] = R(0);
+  R thn = R(1);
+  if (maybe) {
+    // every lane of the warp runs one sub-step: the lanes that jumped at step k take
+    // their step's last logged jump (its sub-step, then back across the jump); the others
+    // a sub-step of length 0, which leaves g and mu as they are (g + 0 s, mu + 0 t)
+    R the, y[D];
+    const int i = lr.pop_if(jumped, xk, the, y);
+    const R de = M::mul(kh.dt, M::sub(thn, the));
+    control_sensitivity(kh, mu, de, g);
+    adjoint_update(kh, y, de, mu);
+    if (kh.jump_law == JD_JUMP_KS) {   // the additive laws' jump map has Jacobian I
+      R mj[D];
+#pragma unroll
+      for (int c = 0; c < D; ++c) mj[c] = mu[c];
+      jump_adjoint(kh, mj);
+#pragma unroll
+      for (int c = 0; c < D; ++c) mu[c] = jumped ? mj[c] : mu[c];
+    }
+    thn = the;
+    if (i > 0) {   // a step with two or more jumps (rare)
+      R ml[D], gl[DU], tl = thn;
+      LogReader2<R, D> ll = lr;
+#pragma unroll
+      for (int c = 0; c < D; ++c) ml[c] = mu[c];
+#pragma unroll
+      for (int l = 0; l < DU; ++l) gl[l] = g[l];
+      logged_more<R, D, DU, KH>(kh, ml, gl, &tl, &ll);
+#pragma unroll
+      for (int c = 0; c < D; ++c) mu[c] = ml[c];
+#pragma unroll
+      for (int l = 0; l < DU; ++l) g[l] = gl[l];
+      thn = tl;
+      lr = ll;
+    }
+  }
+  const R de0 = M::mul(kh.dt, thn);
+  control_sensitivity(kh, mu, de0, g);
+  adjoint_update(kh, xk, de0, mu);
+}
+
+// As backward_logged, and a jump step the log does not hold (logged = false: the step
+// lies at or after the log's closing step) is regenerated from X_k and the counter-based
+// streams (jump_backward).  The cost term at t_k is the caller's.
+template <typename R, int D, int DU, typename KH>
+__device__ __forceinline__ void backward_checked(const KParams<R, D, DU> &kp, const KH &kh, int k, uint32_t m,
+                                                 bool maybe, bool jumped, bool logged, const R (&xk)[D],
+                                                 const R *__restrict__ u, R (&mu)[D], R (&g)[DU],
+                                                 LogReader2<R, D> &lr) {
+  if (jumped && !logged) {
+    R xl[D], ml[D], gl[DU], tl[D + 2], ul[DU];
+#pragma unroll
+    for (int c = 0; c < D; ++c) { xl[c] = xk[c]; ml[c] = mu[c]; }
+#pragma unroll
+    for (int l = 0; l < DU; ++l) { gl[l] = R(0); ul[l] = __ldg(u + (size_t)k * DU + l); }
+#pragma unroll
+    for (int t = 0; t < D + 2; ++t) tl[t] = R(0);
+    jump_backward<R, D, DU, false>(kp, k, m, xl, ul, ml, gl, tl);
+#pragma unroll
+    for (int c = 0; c < D; ++c) mu[c] = ml[c];
+#pragma unroll
+    for (int l = 0; l < DU; ++l) g[l] = gl[l];
+  } else {
+    backward_logged(kh, xk, mu, g, lr, maybe, jumped);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Paired sweeps are compiled for d <= 4 (the host's pairs_built rule).
 template <int D>
@@ -607,26 +905,41 @@ struct PairOut {
   JLog<R, D> jl;
 };
 
-// Store mode: the last three states of the current group of four ride in registers
-// (b0, b1, b2) and the group leaves as one 16-byte vector per component.
+// Store mode: the first SV - 1 states of the current group ride in registers (buf) and
+// the group leaves as VD 16-byte vectors (traj_shape).  The last group may be partial
+// (k == Nt); its unused positions are written as 0.
+template <typename R, int D>
+struct StageBuf {
+  static constexpr int N = TS<R, D>::SV > 1 ? TS<R, D>::SV - 1 : 1;
+  R v[N][D];
+};
+
 template <typename R, int D>
 __device__ __forceinline__ void stage_state(R *__restrict__ traj, int k, int Nt, int64_t mloc, int64_t lm,
-                                            bool active, const R (&x)[D], R (&b0)[D], R (&b1)[D], R (&b2)[D]) {
-  const int j = k & 3;
-  if (j == 3 || k == Nt) {
+                                            bool active, const R (&x)[D], StageBuf<R, D> &b) {
+  constexpr int SV = TS<R, D>::SV, VD = TS<R, D>::VD, VW = TS<R, D>::VW;
+  const int j = k % SV;
+  if (j == SV - 1 || k == Nt) {
     if (active) {
 #pragma unroll
-      for (int c = 0; c < D; ++c)
-        Vec4<R>::store(traj + (((size_t)(k >> 2) * D + c) * mloc + lm) * 4, j == 0 ? x[c] : b0[c],
-                       j == 1 ? x[c] : b1[c], j == 2 ? x[c] : b2[c], x[c]);
-    }
-  } else {
+      for (int v = 0; v < VD; ++v) {
+        R o[VW];
 #pragma unroll
-    for (int c = 0; c < D; ++c) {
-      b0[c] = j == 0 ? x[c] : b0[c];
-      b1[c] = j == 1 ? x[c] : b1[c];
-      b2[c] = j == 2 ? x[c] : b2[c];
+        for (int w = 0; w < VW; ++w) {
+          const int pos = v * VW + w, jj = pos / D, c = pos % D;
+          if (jj == SV - 1)
+            o[w] = j == jj ? x[c] : R(0);
+          else
+            o[w] = j == jj ? x[c] : (jj < j ? b.v[jj][c] : R(0));
+        }
+        Vec16<R>::store(traj + (((size_t)(k / SV) * VD + v) * mloc + lm) * VW, o);
+      }
     }
+  } else if constexpr (SV > 1) {
+#pragma unroll
+    for (int jj = 0; jj < SV - 1; ++jj)
+#pragma unroll
+      for (int c = 0; c < D; ++c) b.v[jj][c] = j == jj ? x[c] : b.v[jj][c];
   }
 }
 
@@ -667,15 +980,17 @@ fwd_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u
   // code small (unrolled twice they ran slower); for d <= 2 the pair and checkpoint
   // sweeps' loops are unrolled twice (faster, measured; at d = 4 the unrolled pair sweep
   // took twice as long)
-  R b0[D], b1[D], b2[D], c0[D], c1[D], c2[D];
+  StageBuf<R, D> sb, sb2;
 #pragma unroll
-  for (int c = 0; c < D; ++c) b0[c] = b1[c] = b2[c] = c0[c] = c1[c] = c2[c] = R(0);
+  for (int i = 0; i < StageBuf<R, D>::N; ++i)
+#pragma unroll
+    for (int c = 0; c < D; ++c) sb.v[i][c] = sb2.v[i][c] = R(0);
   constexpr int UNR = ((PAIR || MODE == FWD_CKPT) && D <= 2) ? 2 : 1;
 #pragma unroll UNR
   for (int k = 0; k <= Nt; ++k) {
     if (MODE == FWD_STORE) {
-      stage_state<R, D>(traj, k, Nt, mloc, lm, active, x, b0, b1, b2);
-      if constexpr (PAIR) stage_state<R, D>(p2.traj, k, Nt, mloc, lm, active, x2, c0, c1, c2);
+      stage_state<R, D>(traj, k, Nt, mloc, lm, active, x, sb);
+      if constexpr (PAIR) stage_state<R, D>(p2.traj, k, Nt, mloc, lm, active, x2, sb2);
     }
     if (k == Nt) break;
     if (MODE == FWD_CKPT && active && (k % seg_len<D>()) == 0) {   // S is a power of two
@@ -699,7 +1014,10 @@ fwd_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u
     }
   }
   if constexpr (MODE == FWD_STORE) {
-    if (active) jcnt[lm] = lw.r;   // the same count for the second control
+    if (active) {   // the same count and closing step for the second control
+      jcnt[lm] = lw.r;
+      jcnt[mloc + lm] = min(lw.kovf, Nt);
+    }
   }
   if (MODE == FWD_CKPT && active) {
     const int nseg = (Nt + seg_len<D>() - 1) / seg_len<D>();
@@ -722,15 +1040,127 @@ fwd_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u
   }
 }
 
+// X_k of one path from the stored trajectory.
 template <typename R, int D>
 __device__ __forceinline__ void load_state(const R *__restrict__ traj, int k, int64_t mloc,
                                            int64_t lm, R (&x)[D]) {
-  const int g = k >> 2, j = k & 3;
+  constexpr int SV = TS<R, D>::SV, VD = TS<R, D>::VD, VW = TS<R, D>::VW;
+  const int g = k / SV, j = k % SV;
 #pragma unroll
-  for (int c = 0; c < D; ++c) {
-    R v[4];
-    Vec4<R>::load(traj + (((size_t)g * D + c) * mloc + lm) * 4, v);
-    x[c] = j == 0 ? v[0] : (j == 1 ? v[1] : (j == 2 ? v[2] : v[3]));
+  for (int v = 0; v < VD; ++v) {
+    R o[VW];
+    Vec16<R>::load(traj + (((size_t)g * VD + v) * mloc + lm) * VW, o);
+#pragma unroll
+    for (int w = 0; w < VW; ++w) {
+      const int pos = v * VW + w;
+      if (pos / D == j) x[pos % D] = o[w];
+    }
+  }
+}
+
+// Steps per chunk of the stored adjoint (CH), and the 16-byte vectors per thread and
+// chunk (NV): a chunk's states are staged in shared memory by cp.async one chunk ahead
+// of their use (two stages), so the loads in flight cost no registers.
+template <typename R, int D>
+struct AdjChunk {
+  static constexpr int CH = D <= 2 ? 8 : 4;
+  static constexpr int NV = CH / TS<R, D>::SV * TS<R, D>::VD;
+};
+
+// Stage bytes per block: the states (NV vectors per thread) and, per warp, the chunk's
+// target rows x_d(t_k) (XB bytes, copied by the first XB / 16 lanes), both twice.
+template <typename R, int D>
+struct AdjStage {
+  static constexpr int XB = AdjChunk<R, D>::CH * D * (int)sizeof(R);
+  static constexpr size_t STATES = (size_t)2 * AdjChunk<R, D>::NV * TPB * 16;
+  static constexpr size_t BYTES = STATES + (size_t)2 * (TPB / 32) * XB;
+  static_assert(XB % 16 == 0, "target rows of a chunk in 16-byte copies");
+};
+template <typename R, int D>
+__host__ __device__ constexpr size_t adj_stage_bytes() {   // per block
+  return AdjStage<R, D>::BYTES;
+}
+
+// Issue the copies of the states of steps c CH .. c CH + CH - 1 into stage st (groups
+// past the last one are read as the last group: those steps lie beyond N_t and are never
+// used) and, when the rows exist (steps below N_t), the warp's copy of the chunk's target
+// rows; then commit them as one group.
+template <typename R, int D>
+__device__ __forceinline__ void issue_chunk(const R *__restrict__ traj, const R *__restrict__ xd, int c, int ng,
+                                            int Nt, int64_t mloc, int64_t lm, unsigned char *stage, int st) {
+  constexpr int CH = AdjChunk<R, D>::CH, NV = AdjChunk<R, D>::NV, XB = AdjStage<R, D>::XB;
+  constexpr int SV = TS<R, D>::SV, VD = TS<R, D>::VD, VW = TS<R, D>::VW;
+  static_assert(CH % SV == 0 && 16 % CH == 0, "chunk geometry");
+#pragma unroll
+  for (int gi = 0; gi < CH / SV; ++gi) {
+    const int g = min(c * (CH / SV) + gi, ng - 1);
+#pragma unroll
+    for (int v = 0; v < VD; ++v)
+      cp_async16(stage + (((size_t)st * NV + gi * VD + v) * TPB + threadIdx.x) * 16,
+                 traj + (((size_t)g * VD + v) * mloc + lm) * VW);
+  }
+  const int lane = threadIdx.x & 31;
+  if (lane < XB / 16 && c * CH + CH <= Nt)
+    cp_async16(stage + AdjStage<R, D>::STATES + ((size_t)st * (TPB / 32) + (threadIdx.x >> 5)) * XB + lane * 16,
+               reinterpret_cast<const unsigned char *>(xd + (size_t)c * CH * D) + lane * 16);
+  cp_async_commit();
+}
+
+// The state X_k of step j of the chunk in stage st (the components of a step are adjacent
+// within their vectors).
+template <typename R, int D>
+__device__ __forceinline__ void stage_step(const unsigned char *stage, int st, int j, R (&x)[D]) {
+  constexpr int NV = AdjChunk<R, D>::NV, SV = TS<R, D>::SV, VD = TS<R, D>::VD;
+  const unsigned char *base = stage + (((size_t)st * NV + (j / SV) * VD) * TPB + threadIdx.x) * 16;
+  if constexpr (D * sizeof(R) == 4) {
+    x[0] = reinterpret_cast<const R *>(base)[j % SV];
+  } else if constexpr (D * sizeof(R) == 8 && sizeof(R) == 4) {
+    const float2 t = reinterpret_cast<const float2 *>(base)[j % SV];
+    x[0] = t.x;
+    x[1] = t.y;
+  } else if constexpr (D * sizeof(R) == 8) {
+    x[0] = reinterpret_cast<const R *>(base)[j % SV];
+  } else {
+#pragma unroll
+    for (int v = 0; v < VD; ++v) {
+      if constexpr (sizeof(R) == 4) {
+        const float4 t = *reinterpret_cast<const float4 *>(base + (size_t)v * TPB * 16);
+        x[4 * v] = t.x; x[4 * v + 1] = t.y; x[4 * v + 2] = t.z; x[4 * v + 3] = t.w;
+      } else {
+        const double2 t = *reinterpret_cast<const double2 *>(base + (size_t)v * TPB * 16);
+        x[2 * v] = t.x; x[2 * v + 1] = t.y;
+      }
+    }
+  }
+}
+
+// The warp's staged target rows of the chunk in stage st.
+template <typename R, int D>
+__device__ __forceinline__ const R *staged_rows(const unsigned char *stage, int st) {
+  return reinterpret_cast<const R *>(stage + AdjStage<R, D>::STATES +
+                                     ((size_t)st * (TPB / 32) + (threadIdx.x >> 5)) * AdjStage<R, D>::XB);
+}
+
+template <typename R, int D>
+__device__ __forceinline__ void read_chunk(const unsigned char *stage, int st, R (&xs)[AdjChunk<R, D>::CH][D]) {
+  constexpr int NV = AdjChunk<R, D>::NV, SV = TS<R, D>::SV, VD = TS<R, D>::VD, VW = TS<R, D>::VW;
+#pragma unroll
+  for (int n = 0; n < NV; ++n) {
+    R o[VW];
+    const unsigned char *src = stage + (((size_t)st * NV + n) * TPB + threadIdx.x) * 16;
+    if constexpr (sizeof(R) == 4) {
+      const float4 t = *reinterpret_cast<const float4 *>(src);
+      o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+    } else {
+      const double2 t = *reinterpret_cast<const double2 *>(src);
+      o[0] = t.x; o[1] = t.y;
+    }
+    const int gi = n / VD, v = n % VD;
+#pragma unroll
+    for (int w = 0; w < VW; ++w) {
+      const int pos = v * VW + w;
+      xs[gi * SV + pos / D][pos % D] = o[w];
+    }
   }
 }
 
@@ -748,17 +1178,33 @@ __device__ __forceinline__ void finish_theta(const KParams<R, D, DU> &kp, R (&th
   }
 }
 
+// Stored adjoint.  The states arrive in chunks of CH steps, staged in shared memory one
+// chunk ahead; every step's contribution B^T lambda' delta goes to the warp's gradient
+// rows, reduced every 16 steps (GradRows).  A chunk runs the fast form when no lane of the
+// warp meets a step the jump log does not cover (the log is a prefix of the path's jump
+// steps, jcnt[mloc + m]): steps without jumps and logged jump steps in one code path, with
+// a warp-uniform test per step (the OR of the chunk's jump flags over the warp) before the
+// log is consulted.  Other chunks (the first and the last, a closed log, the parameter
+// gradients, the adjoint-state output) check every step's flag and regenerate what the
+// log does not hold.
 // LAM: write the adjoint states to lam_out (jd_sample_paths); a compile-time switch, since
 // a run-time test leaves its stores and their address arithmetic in every step.
-template <typename R, int D, int DU, bool THETA, bool LAM = false>
-__global__ void __launch_bounds__(TPB)
-adj_stored_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u,
-                  const R *__restrict__ xd, const R *__restrict__ traj,
-                  const uint32_t *__restrict__ flags, JLog<R, D> jl, const int *__restrict__ jcnt,
-                  double *__restrict__ partG, double *__restrict__ partT, R *__restrict__ lam_out,
-                  int64_t mloc) {
+// CUB: the drift family as a compile-time constant (0, 1) for the pinned coefficients of
+// d <= 2, or read at run time (-1).
+// Dynamic shared memory: grad_rows_bytes<R, DU, 16>() + adj_stage_bytes<R, D>().
+template <typename R, int D, int DU, bool THETA, bool LAM, int CUB>
+__device__ __forceinline__ void stored_sweep(const KParams<R, D, DU> &kp, const R *__restrict__ u,
+                                             const R *__restrict__ xd, const R *__restrict__ traj,
+                                             const uint32_t *__restrict__ flags, const JLog<R, D> &jl,
+                                             const int *__restrict__ jcnt, double *__restrict__ partG,
+                                             double *__restrict__ partT, R *__restrict__ lam_out, int64_t mloc,
+                                             unsigned char *dsm, Pair<R> *red1) {
   using M = Ar<R>;
-  __shared__ Pair<R> red1[TPB / 32];
+  constexpr int CH = AdjChunk<R, D>::CH, SV = TS<R, D>::SV, NR = 16, LD = RowGeom<R>::LD;
+  constexpr bool FAST = !THETA && !LAM, PIN = pin_coef<D>();
+  GradRows<R, DU, NR> rows;
+  rows.init(reinterpret_cast<R *>(dsm));
+  unsigned char *stage = dsm + grad_rows_bytes<R, DU, NR>();
   const int64_t npart = kp.npart;
   const int64_t lm = (int64_t)blockIdx.x * TPB + threadIdx.x;
   const bool active = lm < mloc;
@@ -767,77 +1213,125 @@ adj_stored_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restr
   const int64_t lmc = active ? lm : 0;
   const uint32_t m = (uint32_t)(kp.m_begin + lmc);
   const int Nt = kp.Nt;
-  LogReader<R, D> lr;
-  lr.L = jl;
-  lr.idx = lmc;
-  lr.init(min(__ldg(jcnt + lmc), jl.cap));
+  const int ng = (Nt + SV) / SV;
+  const int nch = (Nt + CH - 1) / CH;
+  issue_chunk<R, D>(traj, xd, nch - 1, ng, Nt, mloc, lmc, stage, (nch - 1) & 1);
+  // the parameter-gradient sweep regenerates every jump step (it needs the sub-steps'
+  // normals), so it reads no log
+  LogReader2<R, D> lr;
+  lr.init(jl, lmc, THETA ? 0 : min(__ldg(jcnt + lmc), jl.cap));
+  const int kovf = THETA ? 0 : __ldg(jcnt + mloc + lmc);
+  LogReader<R, D> lr0;   // an empty log for backward_step (parameter gradients)
+  lr0.L = jl;
+  lr0.idx = lmc;
+  lr0.init(0);
   R mu[D], th[D + 2];
 #pragma unroll
   for (int t = 0; t < D + 2; ++t) th[t] = R(0);
   {
-    R x[D];
+    R x[D], xN[D];
     load_state<R, D>(traj, Nt, mloc, lmc, x);
+    load_row<R, D>(xd + (size_t)Nt * D, xN);
 #pragma unroll
-    for (int c = 0; c < D; ++c) mu[c] = M::mul(kp.qdt[c], M::sub(x[c], __ldg(xd + (size_t)Nt * D + c)));
+    for (int c = 0; c < D; ++c) mu[c] = M::mul(kp.qdt[c], M::sub(x[c], xN[c]));
     if (LAM && active)
 #pragma unroll
       for (int c = 0; c < D; ++c) lam_out[((size_t)Nt * D + c) * mloc + lm] = mu[c];
   }
-  constexpr bool PIN = pin_coef<D>();
-  using KH = typename std::conditional<PIN, HotCoef<R, D, DU>, KParams<R, D, DU>>::type;
-  HotCoef<R, D, DU> khv;
-  if constexpr (PIN) khv = hot_coef(kp);
+  // pinned coefficients (d <= 2); the fast form zeroes B on inactive threads
+  using KH = typename std::conditional<PIN, HotCoef<R, D, DU, CUB>, KParams<R, D, DU>>::type;
+  HotCoef<R, D, DU, CUB> khv;
+  if constexpr (PIN) khv = hot_coef<CUB>(kp, !FAST || active);
   const KH &kh = coef_src<PIN>(kp, khv);
-  const int nbatch = (Nt + BATCH - 1) / BATCH;
-  const int ng = (Nt + 4) / 4;   // groups of 4 stored states
+  const int colw = GradRows<R, DU, NR>::col(threadIdx.x & 31);
+  uint32_t fwn = __ldg(flags + (size_t)(((nch - 1) * CH) >> 5) * mloc + lmc);
 #pragma unroll 1
-  for (int b = nbatch - 1; b >= 0; --b) {
-    R xs[BATCH][D];
+  for (int c = nch - 1; c >= 0; --c) {
+    const int k0 = c * CH;
+    const uint32_t fw = fwn;
+    if (c > 0) {
+      issue_chunk<R, D>(traj, xd, c - 1, ng, Nt, mloc, lmc, stage, (c - 1) & 1);
+      fwn = __ldg(flags + (size_t)((k0 - CH) >> 5) * mloc + lmc);
+    } else {
+      cp_async_commit();   // an empty group keeps the wait count uniform
+    }
+    cp_async_wait<1>();   // this chunk's copies (all groups but the newest) have landed
+    __syncwarp();         // ... and the target rows that other lanes of the warp copied
+    bool slow = true;
+    if constexpr (FAST) slow = __any_sync(0xffffffffu, c == 0 || k0 + CH > Nt || k0 + CH > kovf);
+    if (FAST && !slow) {
+      // warp-uniform: bit j set when some lane of the warp has a jump at step k0 + j
+      const uint32_t jw = __reduce_or_sync(0xffffffffu, (fw >> (k0 & 31)) & ((1u << CH) - 1u));
+      const R *xdc = staged_rows<R, D>(stage, c & 1);
+      R *rp = rows.w + (k0 & (NR - 1)) * LD + colw;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int g = 2 * b + h;
-      if (g >= ng) {   // the top batch may end inside group 2b
+      for (int j = CH - 1; j >= 0; --j) {
+        R g[DU], xk[D], xdk[D];
+        stage_step<R, D>(stage, c & 1, j, xk);
 #pragma unroll
-        for (int c = 0; c < D; ++c)
+        for (int cc = 0; cc < D; ++cc) xdk[cc] = xdc[j * D + cc];
+        backward_logged(kh, xk, mu, g, lr, (jw >> j) & 1u, (fw >> ((k0 + j) & 31)) & 1u);
+        cost_gradient(kh, xk, xdk, mu);
 #pragma unroll
-          for (int j = 0; j < 4; ++j) xs[4 * h + j][c] = R(0);
-        continue;
+        for (int l = 0; l < DU; ++l) rp[(l * NR + j) * LD] = (PIN || active) ? g[l] : R(0);
       }
+    } else {
+      const uint32_t jw = __reduce_or_sync(0xffffffffu, (fw >> (k0 & 31)) & ((1u << CH) - 1u));
+#pragma unroll 1
+      for (int j = CH - 1; j >= 0; --j) {
+        const int k = k0 + j;
+        R g[DU];
 #pragma unroll
-      for (int c = 0; c < D; ++c) {
-        R v[4];
-        Vec4<R>::load(traj + (((size_t)g * D + c) * mloc + lmc) * 4, v);
+        for (int l = 0; l < DU; ++l) g[l] = R(0);
+        if (k < Nt) {
+          R xk[D];
+          stage_step<R, D>(stage, c & 1, j, xk);
+          const bool jumped = (fw >> (k & 31)) & 1u;
+          if constexpr (THETA) {
+            backward_step<R, D, DU, true, LogReader<R, D>, false, KH>(kp, kh, k, m, jumped, xk, u, xd, mu, g, th,
+                                                                      lr0);
+          } else {
+            backward_checked(kp, kh, k, m, (jw >> j) & 1u, jumped, k < kovf, xk, u, mu, g, lr);
+            if (k >= 1) {
+              R xdk[D];
+              load_row<R, D>(xd + (size_t)k * D, xdk);
+              cost_gradient(kh, xk, xdk, mu);
+            }
+          }
+          if (LAM && active)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) xs[4 * h + j][c] = v[j];
+            for (int cc = 0; cc < D; ++cc) lam_out[((size_t)k * D + cc) * mloc + lm] = mu[cc];
+        }
+        rows.put(k & (NR - 1), g, active);
       }
     }
-    const uint32_t fw = __ldg(flags + (size_t)((BATCH * b) >> 5) * mloc + lmc);
-    Pair<R> gb[BATCH][DU];
-#pragma unroll
-    for (int j = BATCH - 1; j >= 0; --j) {
-      const int k = BATCH * b + j;
-      R g[DU];
-#pragma unroll
-      for (int l = 0; l < DU; ++l) g[l] = R(0);
-      if (k < Nt) {
-        backward_step<R, D, DU, THETA, LogReader<R, D>, false, KH>(
-            kp, kh, k, m, (fw >> (k & 31)) & 1u, xs[j], u, xd, mu, g, th, lr);
-        if (LAM && active)
-#pragma unroll
-          for (int c = 0; c < D; ++c) lam_out[((size_t)k * D + c) * mloc + lm] = mu[c];
-      }
-#pragma unroll
-      for (int l = 0; l < DU; ++l) gb[j][l] = {active ? g[l] : R(0), R(0)};
-    }
-    reduce_batch<R, DU>(gb, BATCH * b, Nt, partG, npart);
+    if ((k0 & (NR - 1)) == 0) rows.flush(k0, Nt, partG, npart);
   }
   finish_theta<R, D, DU, THETA>(kp, th, active, partT, red1);
 }
 
+template <typename R, int D, int DU, bool THETA, bool LAM = false>
+__global__ void __launch_bounds__(TPB)
+adj_stored_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u,
+                  const R *__restrict__ xd, const R *__restrict__ traj,
+                  const uint32_t *__restrict__ flags, JLog<R, D> jl, const int *__restrict__ jcnt,
+                  double *__restrict__ partG, double *__restrict__ partT, R *__restrict__ lam_out,
+                  int64_t mloc) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ Pair<R> red1[TPB / 32];
+  if constexpr (pin_coef<D>() && !THETA && !LAM) {   // the drift family decided once
+    if (kp.cubic)
+      stored_sweep<R, D, DU, THETA, LAM, 1>(kp, u, xd, traj, flags, jl, jcnt, partG, partT, lam_out, mloc, dsm, red1);
+    else
+      stored_sweep<R, D, DU, THETA, LAM, 0>(kp, u, xd, traj, flags, jl, jcnt, partG, partT, lam_out, mloc, dsm, red1);
+  } else {
+    stored_sweep<R, D, DU, THETA, LAM, -1>(kp, u, xd, traj, flags, jl, jcnt, partG, partT, lam_out, mloc, dsm, red1);
+  }
+}
+
 // Jump-log records per path and checkpoint segment in the recompute adjoint's shared
 // memory (a segment whose jumps do not fit regenerates them).  Four records hold a
-// 16-step segment's jumps except with probability below 1e-5 at lambda dt = 0.01, and
-// keep the d = 2 block at 24 KB (8 blocks per SM, the register limit).
+// 16-step segment's jumps except with probability below 1e-5 at lambda dt = 0.01.
 template <int D>
 __host__ __device__ constexpr int seg_log_cap() {
   return 4;
@@ -853,12 +1347,19 @@ __host__ __device__ constexpr bool recompute_zbuf() {
                           (size_t)seg_log_cap<D>() * (2 + D) * TPB * sizeof(R) <= 100 * 1024;
 }
 
+// Recompute adjoint.  Per segment of S steps (a multiple of 8): replay the forward from
+// the checkpoint into shared memory (states, a short jump log, and for the parameter
+// gradients the main-stream normals), then sweep the segment backwards in chunks of 8
+// steps, each in the fast form of the stored adjoint when no lane of the warp meets a
+// jump step the segment's log does not hold.  Same step arithmetic and the same gradient
+// tree as the stored adjoint (with 8-step rows, half the shared memory): the same bits.
 template <typename R, int D, int DU, bool THETA>
 __global__ void __launch_bounds__(TPB)
 adj_recompute_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u,
                      const R *__restrict__ xd, const R *__restrict__ ckpt,
                      double *__restrict__ partG, double *__restrict__ partT, int64_t mloc) {
   using M = Ar<R>;
+  constexpr int CH = 8;
   // the parameter-gradient backward regenerates every jump step (it needs the sub-steps'
   // normals), so its replay keeps no jump log: no shared log, more blocks per SM
   constexpr int JS = THETA ? 0 : seg_log_cap<D>();
@@ -870,7 +1371,9 @@ adj_recompute_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__re
   R *zbuf = sbuf + (size_t)S * D * TPB;   // ZBUF: [S * D][TPB] main-stream normals
   auto *skt = reinterpret_cast<typename V2<R>::T *>(zbuf + (ZBUF ? (size_t)S * D * TPB : 0));   // [JS][TPB]
   R *sy = reinterpret_cast<R *>(skt + JS * TPB);                                    // [JS * D][TPB]
-  R *gcol = sy + (size_t)JS * D * TPB;   // THETA: [BATCH * DU][TPB] per-step contributions
+  constexpr int NR = 8;
+  GradRows<R, DU, NR> rows;
+  rows.init(sy + (size_t)JS * D * TPB);
   __shared__ Pair<R> red1[TPB / 32];
   const int64_t npart = kp.npart;
   const int64_t lm = (int64_t)blockIdx.x * TPB + threadIdx.x;
@@ -883,10 +1386,12 @@ adj_recompute_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__re
   R mu[D], th[D + 2];
 #pragma unroll
   for (int t = 0; t < D + 2; ++t) th[t] = R(0);
+  {
+    R xN[D];
+    load_row<R, D>(xd + (size_t)Nt * D, xN);
 #pragma unroll
-  for (int c = 0; c < D; ++c) {
-    const R xN = __ldg(ckpt + ((size_t)nseg * D + c) * mloc + lmc);
-    mu[c] = M::mul(kp.qdt[c], M::sub(xN, __ldg(xd + (size_t)Nt * D + c)));
+    for (int c = 0; c < D; ++c)
+      mu[c] = M::mul(kp.qdt[c], M::sub(__ldg(ckpt + ((size_t)nseg * D + c) * mloc + lmc), xN[c]));
   }
 #pragma unroll 1
   for (int seg = nseg - 1; seg >= 0; --seg) {
@@ -908,44 +1413,44 @@ adj_recompute_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__re
                                                     TPB))
         jm |= 1u << i;
     }
-    LogReader<R, D> lr;
-    lr.L = sl;
-    lr.idx = tid;
-    if constexpr (THETA)
-      lr.init(0);   // empty: every jump step is regenerated
-    else
-      lr.init(lw.r);
-    const int nb = (len + BATCH - 1) / BATCH;
+    LogReader2<R, D> lr;
+    int kovf = 0;
+    if constexpr (THETA) {
+      lr.init(sl, tid, 0);
+    } else {
+      lr.init(sl, tid, lw.r);
+      kovf = lw.kovf;
+    }
+    LogReader<R, D> lr0;   // an empty log for backward_step (parameter gradients)
+    lr0.L = sl;
+    lr0.idx = tid;
+    lr0.init(0);
+    const int nch = (len + CH - 1) / CH;
 #pragma unroll 1
-    for (int bb = nb - 1; bb >= 0; --bb) {
-      Pair<R> gb[BATCH][DU];
-      if constexpr (THETA) {
-        // rolled over the batch (the parameter-gradient step is large): each step's
-        // contribution waits in the thread's shared column gcol[(j DU + l) TPB]
-#pragma unroll 1
-        for (int j = BATCH - 1; j >= 0; --j) {
-          const int i = BATCH * bb + j, k = k0 + i;
-          R g[DU];
+    for (int cc = nch - 1; cc >= 0; --cc) {
+      const int i0 = cc * CH;
+      bool slow = true;
+      if constexpr (!THETA) slow = __any_sync(0xffffffffu, k0 + i0 == 0 || i0 + CH > len || k0 + i0 + CH > kovf);
+      // warp-uniform: bit j set when some lane of the warp has a jump at step k0 + i0 + j
+      const uint32_t jwm = __reduce_or_sync(0xffffffffu, (jm >> i0) & ((1u << CH) - 1u));
+      if (!THETA && !slow) {
+        const R *xdc = xd + (size_t)(k0 + i0) * D;
 #pragma unroll
-          for (int l = 0; l < DU; ++l) g[l] = R(0);
-          if (i < len) {
-            R xk[D];
+        for (int j = CH - 1; j >= 0; --j) {
+          const int i = i0 + j;
+          R g[DU], xk[D], xdk[D];
 #pragma unroll
-            for (int c = 0; c < D; ++c) xk[c] = sbuf[(i * D + c) * TPB + tid];
-            backward_step<R, D, DU, THETA, LogReader<R, D>, ZBUF>(kp, kp, k, m, (jm >> i) & 1u, xk, u, xd, mu, g, th,
-                                                                  lr, zbuf + (size_t)i * D * TPB + tid, TPB);
-          }
-#pragma unroll
-          for (int l = 0; l < DU; ++l) gcol[(j * DU + l) * TPB + tid] = active ? g[l] : R(0);
+          for (int c = 0; c < D; ++c) xk[c] = sbuf[(i * D + c) * TPB + tid];
+          load_row<R, D>(xdc + j * D, xdk);
+          backward_logged(kp, xk, mu, g, lr, (jwm >> j) & 1u, (jm >> i) & 1u);
+          cost_gradient(kp, xk, xdk, mu);
+          rows.put((k0 + i) & (NR - 1), g, active);
         }
-#pragma unroll
-        for (int j = 0; j < BATCH; ++j)
-#pragma unroll
-          for (int l = 0; l < DU; ++l) gb[j][l] = {gcol[(j * DU + l) * TPB + tid], R(0)};
       } else {
-#pragma unroll
-        for (int j = BATCH - 1; j >= 0; --j) {
-          const int i = BATCH * bb + j, k = k0 + i;
+        // rolled (the parameter-gradient step is large and these chunks are rare)
+#pragma unroll 1
+        for (int j = CH - 1; j >= 0; --j) {
+          const int i = i0 + j, k = k0 + i;
           R g[DU];
 #pragma unroll
           for (int l = 0; l < DU; ++l) g[l] = R(0);
@@ -953,14 +1458,23 @@ adj_recompute_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__re
             R xk[D];
 #pragma unroll
             for (int c = 0; c < D; ++c) xk[c] = sbuf[(i * D + c) * TPB + tid];
-            backward_step<R, D, DU, THETA, LogReader<R, D>, ZBUF>(kp, kp, k, m, (jm >> i) & 1u, xk, u, xd, mu, g, th,
-                                                                  lr, zbuf + (size_t)i * D * TPB + tid, TPB);
+            const bool jumped = (jm >> i) & 1u;
+            if constexpr (THETA) {
+              backward_step<R, D, DU, true, LogReader<R, D>, ZBUF>(kp, kp, k, m, jumped, xk, u, xd, mu, g, th, lr0,
+                                                                   zbuf + (size_t)i * D * TPB + tid, TPB);
+            } else {
+              backward_checked(kp, kp, k, m, (jwm >> j) & 1u, jumped, k < kovf, xk, u, mu, g, lr);
+              if (k >= 1) {
+                R xdk[D];
+                load_row<R, D>(xd + (size_t)k * D, xdk);
+                cost_gradient(kp, xk, xdk, mu);
+              }
+            }
           }
-#pragma unroll
-          for (int l = 0; l < DU; ++l) gb[j][l] = {active ? g[l] : R(0), R(0)};
+          rows.put(k & (NR - 1), g, active);
         }
       }
-      reduce_batch<R, DU>(gb, k0 + BATCH * bb, Nt, partG, npart);
+      if (((k0 + i0) & (NR - 1)) == 0) rows.flush(k0 + i0, Nt, partG, npart);
     }
   }
   finish_theta<R, D, DU, THETA>(kp, th, active, partT, red1);
@@ -1034,9 +1548,9 @@ void make_kparams(const jd_problem *p, int64_t m_begin, int64_t mloc, KParams<R,
 template <typename R, int D, int DU>
 cudaError_t op_fwd(const jd_problem *p, int mode, int64_t m_begin, int64_t mloc, const void *uk,
                    const PathBufs &b, cudaStream_t s) {
-  auto *kp = new KParams<R, D, DU>();
-  make_kparams<R, D, DU>(p, m_begin, mloc, *kp);
-  if (b.npart) kp->npart = b.npart;
+  KParams<R, D, DU> kp;   // passed by value to the kernel (copied at the launch)
+  make_kparams<R, D, DU>(p, m_begin, mloc, kp);
+  if (b.npart) kp.npart = b.npart;
   const dim3 grid((unsigned)ceil_div(mloc, TPB));
   const R *u = static_cast<const R *>(uk);
   const R *xd = static_cast<const R *>(p->xdk);
@@ -1049,34 +1563,32 @@ cudaError_t op_fwd(const jd_problem *p, int mode, int64_t m_begin, int64_t mloc,
                                   b.log_cap}};
   switch (mode) {
     case FWD_COST:
-      fwd_kernel<R, D, DU, FWD_COST><<<grid, TPB, 0, s>>>(*kp, u, xd, b.partC, nullptr, nullptr, nullptr, pc,
+      fwd_kernel<R, D, DU, FWD_COST><<<grid, TPB, 0, s>>>(kp, u, xd, b.partC, nullptr, nullptr, nullptr, pc,
                                                           jl, nullptr, mloc, p2);
       break;
     case FWD_STORE:
-      fwd_kernel<R, D, DU, FWD_STORE><<<grid, TPB, 0, s>>>(*kp, u, xd, b.partC, static_cast<R *>(b.traj),
+      fwd_kernel<R, D, DU, FWD_STORE><<<grid, TPB, 0, s>>>(kp, u, xd, b.partC, static_cast<R *>(b.traj),
                                                            b.flags, nullptr, pc, jl, b.jcnt, mloc, p2);
       break;
     case FWD_STORE | FWD_PAIR:
     case FWD_CKPT | FWD_PAIR:
       if constexpr (PAIR_SWEEPS<D>) {   // the host asks for pairs only where they are built
         if (mode & FWD_STORE)
-          fwd_kernel<R, D, DU, FWD_STORE, true><<<grid, TPB, 0, s>>>(*kp, u, xd, b.partC, static_cast<R *>(b.traj),
+          fwd_kernel<R, D, DU, FWD_STORE, true><<<grid, TPB, 0, s>>>(kp, u, xd, b.partC, static_cast<R *>(b.traj),
                                                                      b.flags, nullptr, nullptr, jl, b.jcnt, mloc, p2);
         else
-          fwd_kernel<R, D, DU, FWD_CKPT, true><<<grid, TPB, 0, s>>>(*kp, u, xd, b.partC, nullptr, nullptr,
+          fwd_kernel<R, D, DU, FWD_CKPT, true><<<grid, TPB, 0, s>>>(kp, u, xd, b.partC, nullptr, nullptr,
                                                                     static_cast<R *>(b.ckpt), nullptr, jl, nullptr,
                                                                     mloc, p2);
       } else {
-        delete kp;
         return cudaErrorNotSupported;
       }
       break;
     default:
-      fwd_kernel<R, D, DU, FWD_CKPT><<<grid, TPB, 0, s>>>(*kp, u, xd, b.partC, nullptr, nullptr,
+      fwd_kernel<R, D, DU, FWD_CKPT><<<grid, TPB, 0, s>>>(kp, u, xd, b.partC, nullptr, nullptr,
                                                           static_cast<R *>(b.ckpt), pc, jl, nullptr, mloc, p2);
       break;
   }
-  delete kp;
   count_launch();
   return cudaGetLastError();
 }
@@ -1084,15 +1596,34 @@ cudaError_t op_fwd(const jd_problem *p, int mode, int64_t m_begin, int64_t mloc,
 template <typename R, int D, int DU>
 constexpr size_t recompute_smem(bool theta) {
   return (size_t)seg_len<D>() * D * TPB * sizeof(R) * (theta && recompute_zbuf<R, D, true>() ? 2 : 1) +
-         (theta ? (size_t)BATCH * DU * TPB * sizeof(R) : (size_t)seg_log_cap<D>() * (2 + D) * TPB * sizeof(R));
+         (theta ? 0 : (size_t)seg_log_cap<D>() * (2 + D) * TPB * sizeof(R)) + grad_rows_bytes<R, DU, 8>();
+}
+
+// The dynamic shared-memory limit of a kernel is an attribute of the function on the
+// current device: raised once per (kernel, device) where a launch needs more than the
+// default 48 KB (not before every launch: it is not a stream operation).
+inline cudaError_t ensure_dyn_smem(const void *fn, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  static std::mutex mu;
+  static std::map<std::pair<const void *, int>, size_t> done;
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_pair(fn, dev);
+  const auto it = done.find(key);
+  if (it != done.end() && it->second >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done[key] = bytes;
+  return e;
 }
 
 template <typename R, int D, int DU>
 cudaError_t op_adj(const jd_problem *p, int variant, bool theta, int64_t m_begin, int64_t mloc,
                    const void *uk, const PathBufs &b, cudaStream_t s) {
-  auto *kp = new KParams<R, D, DU>();
-  make_kparams<R, D, DU>(p, m_begin, mloc, *kp);
-  if (b.npart) kp->npart = b.npart;
+  KParams<R, D, DU> kp;   // passed by value to the kernel (copied at the launch)
+  make_kparams<R, D, DU>(p, m_begin, mloc, kp);
+  if (b.npart) kp.npart = b.npart;
   const dim3 grid((unsigned)ceil_div(mloc, TPB));
   const R *u = static_cast<const R *>(uk);
   const R *xd = static_cast<const R *>(p->xdk);
@@ -1101,38 +1632,36 @@ cudaError_t op_adj(const jd_problem *p, int variant, bool theta, int64_t m_begin
     const R *tr = static_cast<const R *>(b.traj);
     R *lo = static_cast<R *>(b.lam_out);
     const JLog<R, D> jl{static_cast<typename V2<R>::T *>(b.log_kt), static_cast<R *>(b.log_y), mloc, b.log_cap};
-    if (theta)
-      adj_stored_kernel<R, D, DU, true><<<grid, TPB, 0, s>>>(*kp, u, xd, tr, b.flags, jl, b.jcnt, b.partG,
-                                                             b.partT, lo, mloc);
-    else if (lo)
-      adj_stored_kernel<R, D, DU, false, true><<<grid, TPB, 0, s>>>(*kp, u, xd, tr, b.flags, jl, b.jcnt, b.partG,
-                                                                    b.partT, lo, mloc);
-    else
-      adj_stored_kernel<R, D, DU, false><<<grid, TPB, 0, s>>>(*kp, u, xd, tr, b.flags, jl, b.jcnt, b.partG,
-                                                              b.partT, nullptr, mloc);
+    const size_t smem = grad_rows_bytes<R, DU, 16>() + adj_stage_bytes<R, D>();
+    if (theta) {
+      err = ensure_dyn_smem((const void *)adj_stored_kernel<R, D, DU, true>, smem);
+      if (err == cudaSuccess)
+        adj_stored_kernel<R, D, DU, true><<<grid, TPB, smem, s>>>(kp, u, xd, tr, b.flags, jl, b.jcnt, b.partG,
+                                                                  b.partT, lo, mloc);
+    } else if (lo) {
+      err = ensure_dyn_smem((const void *)adj_stored_kernel<R, D, DU, false, true>, smem);
+      if (err == cudaSuccess)
+        adj_stored_kernel<R, D, DU, false, true><<<grid, TPB, smem, s>>>(kp, u, xd, tr, b.flags, jl, b.jcnt,
+                                                                         b.partG, b.partT, lo, mloc);
+    } else {
+      err = ensure_dyn_smem((const void *)adj_stored_kernel<R, D, DU, false>, smem);
+      if (err == cudaSuccess)
+        adj_stored_kernel<R, D, DU, false><<<grid, TPB, smem, s>>>(kp, u, xd, tr, b.flags, jl, b.jcnt, b.partG,
+                                                                   b.partT, nullptr, mloc);
+    }
   } else {
     const size_t smem = recompute_smem<R, D, DU>(theta);
     const R *ck = static_cast<const R *>(b.ckpt);
-    // the dynamic shared-memory limit is a property of the function: set once per process
-    // (one device per process)
-    // (it is not a stream operation, and a call per launch sat between the phases)
-    static std::atomic<bool> set_theta{false}, set_plain{false};
-    std::atomic<bool> &done = theta ? set_theta : set_plain;
-    if (!done.load(std::memory_order_acquire)) {
-      err = theta ? cudaFuncSetAttribute(adj_recompute_kernel<R, D, DU, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                  : cudaFuncSetAttribute(adj_recompute_kernel<R, D, DU, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (err == cudaSuccess) done.store(true, std::memory_order_release);
-    }
-    if (err == cudaSuccess) {
-      if (theta)
-        adj_recompute_kernel<R, D, DU, true><<<grid, TPB, smem, s>>>(*kp, u, xd, ck, b.partG, b.partT, mloc);
-      else
-        adj_recompute_kernel<R, D, DU, false><<<grid, TPB, smem, s>>>(*kp, u, xd, ck, b.partG, b.partT, mloc);
+    if (theta) {
+      err = ensure_dyn_smem((const void *)adj_recompute_kernel<R, D, DU, true>, smem);
+      if (err == cudaSuccess)
+        adj_recompute_kernel<R, D, DU, true><<<grid, TPB, smem, s>>>(kp, u, xd, ck, b.partG, b.partT, mloc);
+    } else {
+      err = ensure_dyn_smem((const void *)adj_recompute_kernel<R, D, DU, false>, smem);
+      if (err == cudaSuccess)
+        adj_recompute_kernel<R, D, DU, false><<<grid, TPB, smem, s>>>(kp, u, xd, ck, b.partG, b.partT, mloc);
     }
   }
-  delete kp;
   count_launch();
   if (err != cudaSuccess) return err;
   return cudaGetLastError();

@@ -487,7 +487,7 @@ fwd32_kernel(const KP32 *__restrict__ kpg, const float *__restrict__ u, const fl
         float y[32];
 #pragma unroll
         for (int c = 0; c < 32; ++c) y[c] = yl[c];
-        lw.put(k, th, y);
+        lw.put(k, 0, th, y);
       }
 #pragma unroll
       for (int c = 0; c < 32; ++c) x[c] = xl[c];
@@ -509,7 +509,7 @@ fwd32_kernel(const KP32 *__restrict__ kpg, const float *__restrict__ u, const fl
           float y[32];
 #pragma unroll
           for (int c = 0; c < 32; ++c) y[c] = S.Y[i + 1][c];
-          lw.put(k, S.th[i], y);
+          lw.put(k, i, S.th[i], y);
         }
       }
     }
