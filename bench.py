@@ -39,6 +39,17 @@ UNIT = "path-steps/s"
 L2_BYTES = 129 * 1024 * 1024
 
 
+def _sm_count() -> int:
+    """SMs of the current device (the issue-rate peaks scale with it)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+    except Exception:   # no torch / no device: the GB300's count
+        pass
+    return 152
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -197,6 +208,82 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------------------
+# path sharding: one problem's paths over the ranks (--shard)
+# --------------------------------------------------------------------------------------
+UNIT_PATHS = 16384   # JD_UNIT_PATHS
+
+
+def shard_range(M, rank, world, unit=UNIT_PATHS):
+    """Paths [m0, m0 + n) of one rank: whole units of the path reduction in rank order,
+    split as evenly as possible (a rank may get none)."""
+    nun = -(-M // unit)
+    per, extra = divmod(nun, world)
+    u0 = rank * per + min(rank, extra)
+    u1 = u0 + per + (1 if rank < extra else 0)
+    m0 = min(u0 * unit, M)
+    return m0, min(u1 * unit, M) - m0
+
+
+def gather_units(dist, units, ne):
+    """Every rank's unit sums, concatenated in rank (that is, path) order."""
+    if dist is None:
+        return units
+    parts = [None] * dist.get_world_size()
+    dist.all_gather_object(parts, units)
+    return np.concatenate([np.asarray(q).reshape(-1, ne) for q in parts])
+
+
+def run_shard(args, p, stream, dist, ws, rank, local):
+    """One gradient of the whole problem per step, its paths split over the ranks: each
+    rank runs the units of its shard (jd_gradient_units), the units are all-gathered
+    (about 64 KB per rank), every rank combines them (jd_combine_units) into the whole
+    problem's J and gradient, bit for bit the single-GPU jd_gradient.  Strong scaling."""
+    import torch
+    import paper_2505_04328_gb300 as jd
+    m0, n = shard_range(p.M, rank, ws)
+    prec = "fp64" if args.workload == "lq_scalar" else "fp32"
+    shard = jd.JdProblem(p.replace(M=n, m_offset=m0), prec=prec, mode=args.variant or "stored",
+                         stream=stream) if n else None
+    Nt, du = p.Nt, p.du
+    ne = 1 + Nt * du
+    u = np.zeros((Nt, du))
+
+    def step():
+        units = shard.gradient_units(u) if shard else np.zeros((0, ne))
+        return jd.combine_units(p, u, gather_units(dist, units, ne))
+
+    for _ in range(args.warmup):
+        step()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        J, g = step()
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3
+    if dist is not None:
+        ms = max_over_ranks(dist, ms, device="cuda")
+    ms_per_step = ms / args.steps
+    value = p.M * Nt / (ms_per_step * 1e-3)
+    if shard:
+        shard.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+                "scaling": "strong", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32",
+                "data": "synthetic",
+                "config": {"workload": f"{p.name} d={p.d} M={p.M} Nt={Nt}, paths sharded over {ws} ranks",
+                           "step": "one whole-problem gradient: shard units, all-gather, combine",
+                           "l2": "inputs larger than L2 (stored states); no flush"},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": Nt * du * 8,
+                        "d2h_bytes_per_step": -(-p.M // UNIT_PATHS) * ne * 8 / ws},
+                "J": J}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------------------
 # our arm
 # --------------------------------------------------------------------------------------
 def run_ours(args):
@@ -212,6 +299,9 @@ def run_ours(args):
     jd.build()
     stream = torch.cuda.current_stream()
 
+    if args.shard:   # every rank works on the same sample
+        return run_shard(args, bench_workload(args.paths, args.steps_t, args.workload), stream, dist, ws, rank,
+                         local)
     p = replica_problem(bench_workload(args.paths, args.steps_t, args.workload), rank)
     if args.workload == "double_well_autograd":
         return run_autograd(args, p, stream, dist, ws, rank, local)
@@ -413,7 +503,8 @@ def run_feedback(args, p, stream, dist, ws, rank, local):
 
     peaks, _ = _peaks()
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    peak = 152 * 4 * 32 * sm_mhz * 1e6 / 1e9
+    nsm = _sm_count()
+    peak = nsm * 4 * 32 * sm_mhz * 1e6 / 1e9
     rl = {}
     for name, ops in (("fb_fwd", fb_forward_ops(p, fb)), ("fb_adj", fb_adjoint_ops(p, fb)),
                       ("fb_sur", fb_forward_ops(p, fb) + fb_adjoint_ops(p, fb))):
@@ -422,7 +513,7 @@ def run_feedback(args, p, stream, dist, ws, rank, local):
             achieved = ops * M * Nt / (total_ms / launches_k * 1e-3) / 1e9
             rl[name] = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Glane-op/s",
                         "frac": achieved / peak, "traffic": None,
-                        "peak_source": "derived: 152 SMs x 4 schedulers x 32 lanes x 1 instruction/clock x "
+                        "peak_source": f"derived: {nsm} SMs x 4 schedulers x 32 lanes x 1 instruction/clock x "
                                        f"{sm_mhz:.0f} MHz (max SM clock)",
                         "algorithmic_ops_per_path_step": ops}
             iss = issue_fraction(args.workload, name, M * Nt, total_ms / launches_k * 1e-3, peaks)
@@ -746,30 +837,42 @@ def adjoint_ops(p):
     return d * d + d * du + 2 * d + (d * d + 2 * d if p.drift == workloads.CUBIC else 0) + 10
 
 
-# DRAM bytes (read + write) per path-step of the d = 2 kernels from one ncu capture
-# (profiles/fwd_store_adj_stored_double_well_d2_M2p16_Nt1000.md: M = 2^16, N_t = 1000,
-# scaled per path-step); set to None whenever a kernel changes after its capture.
-TRAFFIC_PER_PATH_STEP = {"fwd_store": 7.71, "fwd_pair": 16.68, "adj_stored": 8.81}
+# Counters of ncu captures (profiles/*.md), per path-step for DRAM bytes and per
+# warp-step (32 path-steps) for issued warp-instructions.  Each entry records the
+# fingerprint of the kernel sources it was counted on; when the sources have changed
+# since, the entry is stale and the figures derived from it are reported as null.
+COUNTERS = {
+    # (workload, kernel): (fingerprint, DRAM bytes per path-step or None, warp-inst per warp-step)
+}
 
-# Warp-instructions issued per warp-step (32 path-steps) from the same kind of ncu capture
-# (smsp__inst_executed.sum / warp-steps; profiles/*.md): with the measured time they give
-# the fraction of the SM's issue rate (4 schedulers x 1 instruction per clock) the kernel
-# uses, next to the algorithmic fraction; None when the kernel changed since the capture.
-INST_PER_WARP_STEP = {("double_well", "fwd_store"): 287, ("double_well", "fwd_pair"): 343,
-                      ("double_well", "adj_stored"): 108,
-                      ("double_well", "adj_recompute"): 352, ("feedback_centering", "fb_fwd"): 830,
-                      ("feedback_centering", "fb_adj"): 1224}
+
+def _kernel_fingerprint() -> str:
+    import hashlib
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_2505_04328_gb300", "csrc")
+    for f in ("jd_kernels.cuh", "jd_device.cuh", "jd_feedback.cuh", "jd_internal.h"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def _counter(workload, name, which):
+    e = COUNTERS.get((workload, name))
+    if e is None or e[0] != _kernel_fingerprint():
+        return None
+    return e[1] if which == "traffic" else e[2]
 
 
 def issue_fraction(workload, name, units, per_launch_s, peaks):
-    n = INST_PER_WARP_STEP.get((workload, name))
+    n = _counter(workload, name, "inst")
     if n is None:
         return None
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    peak = 152 * 4 * sm_mhz * 1e6
+    peak = _sm_count() * 4 * sm_mhz * 1e6
     achieved = n * units / 32 / per_launch_s
     return {"inst_per_warp_step": n, "achieved_warp_inst_per_s": achieved, "peak_warp_inst_per_s": peak,
-            "frac": achieved / peak, "source": "ncu smsp__inst_executed.sum of a small case of the same kernel"}
+            "frac": achieved / peak,
+            "source": "ncu smsp__inst_executed.sum of the same kernel sources (profiles/), per warp-step"}
 
 
 def kernel_roofline(name, stat, p, peaks, peak_kind, tc=0, plan="stored"):
@@ -779,7 +882,7 @@ def kernel_roofline(name, stat, p, peaks, peak_kind, tc=0, plan="stored"):
     per_launch_s = total_ms / launches * 1e-3
     units = p.M * p.Nt
     captured = p.d == 2 and p.name == "double_well" and (name != "fwd_pair" or plan == "stored")
-    tr = TRAFFIC_PER_PATH_STEP.get(name) if captured else None
+    tr = _counter(p.name, name, "traffic") if captured else None
     traffic = None if tr is None else tr * units
     if KERNEL_BOUND[name] == "hbm":
         bytes_per = 4 * p.d + 0.125 + p.lam * p.dt * (2 + p.d) * 4
@@ -797,11 +900,12 @@ def kernel_roofline(name, stat, p, peaks, peak_kind, tc=0, plan="stored"):
     tc = 0 if tc == 3 else tc   # mode 3: the forward runs on the CUDA cores
     ops = forward_ops(p, tc, 2 if name == "fwd_pair" else 1) + (adjoint_ops(p) if name == "adj_recompute" else 0.0)
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    peak = 152 * 4 * 32 * sm_mhz * 1e6 / 1e9   # G lane-operations per second
+    nsm = _sm_count()
+    peak = nsm * 4 * 32 * sm_mhz * 1e6 / 1e9   # G lane-operations per second
     achieved = ops * units / per_launch_s / 1e9
     out = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Glane-op/s",
            "frac": achieved / peak, "traffic": traffic,
-           "peak_source": "derived: 152 SMs x 4 schedulers x 32 lanes x 1 instruction/clock x "
+           "peak_source": f"derived: {nsm} SMs x 4 schedulers x 32 lanes x 1 instruction/clock x "
                           f"{sm_mhz:.0f} MHz (max SM clock)",
            "algorithmic_ops_per_path_step": ops}
     if tc:
@@ -836,6 +940,8 @@ def main():
     ap.add_argument("--steps-t", type=int, default=None, help="override N_t")
     ap.add_argument("--reference-paths", type=int, default=1 << 14)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shard", action="store_true",
+                    help="one problem's paths split over the ranks (one gradient per step, strong scaling)")
     ap.add_argument("--fb-adjoint", default="exact", choices=["exact", "surrogate"],
                     help="feedback workloads: exact adjoint or the surrogate-state adjoint of Sec. 6.5")
     ap.add_argument("--sur-rate", type=float, default=0.05, help="surrogate variance growth per unit time")

@@ -102,6 +102,13 @@ typedef enum { JD_MEM_HOST = 0, JD_MEM_DEVICE = 1 } jd_memspace;
  *                creates its own stream
  *   jump_gain    KS only: the velocity gain gamma (finite; the paper takes 0 <= gamma
  *                < 1); ignored by the additive laws
+ *   m_offset     global index of the problem's first path: the problem is paths
+ *                [m_offset, m_offset + M) of a larger Monte Carlo sample (one shard of
+ *                a problem whose paths are split over several GPUs; every draw is
+ *                keyed by the global path index).  0 for a whole problem;
+ *                m_offset + M <= 2^32.  J and the gradient of such a problem are the
+ *                means over its own M paths; jd_gradient_units gives the sums that
+ *                combine into the whole problem's result.
  */
 typedef struct {
   int d, du;
@@ -126,6 +133,7 @@ typedef struct {
   size_t mem_budget_bytes;
   void *cuda_stream;
   double jump_gain;
+  int64_t m_offset;
 } jd_problem_desc;
 
 typedef struct jd_problem jd_problem;
@@ -307,6 +315,37 @@ typedef struct {
 void jd_profile_enable(int on);
 int jd_profile_read(jd_kernel_stat *out, int max_entries);
 
+/* ---------------------------------------------------------------------------
+ * Path sharding: one problem's M paths split over several GPUs (or processes).
+ *
+ * The Monte Carlo mean of Sec. 3 is a sum over paths, and every draw is keyed by the
+ * global path index, so a problem splits into shards of consecutive paths (m_offset,
+ * M of each shard's descriptor) that run independently.  The reduction over paths is
+ * defined on units of JD_UNIT_PATHS consecutive paths: within a unit a fixed tree over
+ * its per-warp partials, across units a plain sum in unit order.  A shard that starts at
+ * a unit boundary therefore produces exactly the unit sums the whole problem would, and
+ * jd_combine_units over all shards' units (in path order) gives J and the gradient of
+ * jd_gradient on the whole problem bit for bit, for every split.  jd_gradient and
+ * jd_cost use the same unit reduction.
+ *
+ * jd_gradient_units / jd_cost_units: run the problem's paths at u and write its units,
+ *   units[nu][ne], nu = ceil(M / JD_UNIT_PATHS), ne = 1 + Nt du (gradient) or 1 (cost):
+ *   units[i][0] = sum of the unit's path costs sum_k dt l(X_k, t_k) (eq:discrete_functional
+ *   without the control term), units[i][1 + k du + l] = sum over the unit's paths of the
+ *   step's sensitivity delta B^T lambda' (eq:definition_Gradient without the nu term and
+ *   the 1/M).  u as in jd_gradient; units in memory space os (host: synchronizes; device:
+ *   stream ordered).  INVALID_ARG unless m_offset is a multiple of JD_UNIT_PATHS.
+ * jd_combine_units: host arithmetic, no GPU.  M_total: paths of the whole problem; u:
+ *   host, Nt du doubles (the control term nu dt/2 sum |u_k|^2 and nu dt u_k); units: all
+ *   shards' units in path order, nunits = ceil(M_total / JD_UNIT_PATHS) rows of ne;
+ *   grad: Nt du doubles or NULL when ne = 1.  Returns J and grad as jd_gradient would.
+ */
+#define JD_UNIT_PATHS 16384
+jd_status jd_gradient_units(jd_problem *p, const double *u, jd_memspace us, double *units, jd_memspace os);
+jd_status jd_cost_units(jd_problem *p, const double *u, jd_memspace us, double *units, jd_memspace os);
+jd_status jd_combine_units(int64_t M_total, int Nt, int du, double T, double nu, const double *u,
+                           const double *units, int64_t nunits, int ne, double *J, double *grad);
+
 /* J(u) for callers that cannot allocate device memory once they are running: a
  * real-time control loop (cudaMalloc can take milliseconds and synchronizes the
  * device) or an application whose memory pool owns the whole GPU.  The paper has no
@@ -315,24 +354,33 @@ int jd_profile_read(jd_kernel_stat *out, int max_entries);
  * It runs the same forward cost kernel as jd_cost, but allocates nothing, on the
  * device or on the host: its scratch is one fixed 4 MiB file-scope device array that
  * every GPU loading this library holds until the process exits.
- *   desc   problem descriptor (host arrays, read during the call; xd is copied into
- *          the scratch); d <= 2, du == 1, FP32 or FP64; mode, mem_budget_bytes and
- *          use_tensor_cores are ignored (use_tensor_cores must be 0)
+ *   desc   problem descriptor: host arrays; A, B, C, sigma, x0, q are read during the
+ *          call, xd is copied into the scratch by cudaMemcpyAsync on desc->cuda_stream,
+ *          so xd (pageable or page-locked host memory, not device memory) must stay
+ *          unchanged until the stream has reached the call; d <= 2, du == 1, FP32 or
+ *          FP64, the additive jump laws; mode, mem_budget_bytes and use_tensor_cores
+ *          are ignored (use_tensor_cores must be 0)
  *   u      device pointer, Nt doubles
  *   J      device pointer, one double, written in stream order on desc->cuda_stream
  *          (NULL = the legacy default stream); the call does not synchronize
- * The scratch holds the FP64 target, the padded target and control in kernel
- * precision and one FP64 partial per 128 paths; a problem whose total exceeds 4 MiB
- * is rejected with JD_ERR_OOM (for d = 2, Nt = 1000 in FP32 that allows M up to
- * about 3.9 million paths).  Every entry read is written earlier in the same call,
- * so nothing needs clearing between calls.  All calls on a device share the one
- * array: calls that overlap on the GPU (other streams, other host threads) race and
- * must be serialized by the caller.  The first call on each device takes the array's
- * device address with cudaGetSymbolAddress (with that device current); make that
- * first call before any stream capture.  Errors are reported by status only
- * (jd_last_error is not updated, since that would allocate): INVALID_ARG,
- * UNSUPPORTED (d > 2, du != 1, or a per-thread stack limit below 1 KiB), OOM (beyond
- * the scratch), CUDA. */
+ * The scratch holds, each rounded up to 256 bytes, the FP64 target ((Nt+1) d doubles),
+ * the padded target ((Nt+1) d values) and the control (Nt values) in kernel precision,
+ * and one FP64 partial per 128 paths; a problem whose total exceeds 4 MiB is rejected
+ * with JD_ERR_OOM (for d = 2, Nt = 1000 in FP32 the fixed part takes 28,416 bytes,
+ * which leaves room for 520,736 partials: M up to about 66.6 million paths; M is also
+ * limited to 2^32 - 1).  Every entry read is written earlier in the same call, so
+ * nothing needs clearing between calls.  All calls on a device share the one array:
+ * calls that overlap on the GPU (other streams, other host threads) race and must be
+ * serialized by the caller.
+ * The first call on each device is a warm-up: it takes the array's device address
+ * with cudaGetSymbolAddress (with that device current) and the cost kernels'
+ * per-thread stack needs, and its launches may load the kernels' code (the CUDA
+ * runtime loads modules lazily, which allocates).  Make that first call before any
+ * stream capture and before the point from which nothing may allocate; later calls
+ * allocate nothing.  Errors are reported by status only (jd_last_error is not updated,
+ * since that would allocate): INVALID_ARG, UNSUPPORTED (d > 2, du != 1, or a
+ * per-thread stack limit below what the cost kernel needs: the call does not raise
+ * it), OOM (beyond the scratch), CUDA. */
 jd_status jd_cost_noalloc(const jd_problem_desc *desc, const double *u, double *J);
 
 /* ---------------------------------------------------------------------------

@@ -6,11 +6,11 @@ jumps and its exact discrete-adjoint gradient (discretize-then-optimize, after
 minimizes it by projected gradient descent with the Armijo rule.  All numerics run in
 the CUDA library libjd.so (C ABI: include/jd.h); this package only marshals arguments.
 """
-from .binding import (ABI_SYMBOLS, JdError, JdProblem, JdServer, footprint, launch_count, lib,  # noqa: F401
-                      library_path, profile_enable, profile_read)
+from .binding import (ABI_SYMBOLS, UNIT_PATHS, JdError, JdProblem, JdServer, combine_units,  # noqa: F401
+                      footprint, launch_count, lib, library_path, profile_enable, profile_read)
 
-__all__ = ["JdProblem", "JdServer", "JdError", "footprint", "lib", "library_path", "launch_count",
-           "ABI_SYMBOLS", "build"]
+__all__ = ["JdProblem", "JdServer", "JdError", "footprint", "combine_units", "UNIT_PATHS", "lib", "library_path",
+           "launch_count", "ABI_SYMBOLS", "build"]
 
 
 def build(verbose: bool = False) -> str:

@@ -20,7 +20,9 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libjd.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
+# host code: no floating-point contraction, so host arithmetic (thresholds, the unit
+# combine) rounds the same on every host architecture
+NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2,-ffp-contract=off",
                      "-I", INCLUDE, "-I", CSRC, "--expt-relaxed-constexpr"]
 
 

@@ -33,7 +33,10 @@ ABI_SYMBOLS = (
     "jd_profile_read", "jd_cost_noalloc", "jd_problem_footprint", "jd_server_create",
     "jd_server_submit", "jd_server_poll", "jd_server_wait", "jd_server_info", "jd_server_destroy",
     "jd_status_string", "jd_last_error", "jd_fb_cost", "jd_fb_gradient", "jd_fb_optimize",
+    "jd_gradient_units", "jd_cost_units", "jd_combine_units",
 )
+
+UNIT_PATHS = 16384   # JD_UNIT_PATHS: paths per unit of the path reduction (path sharding)
 
 
 class JdError(RuntimeError):
@@ -53,7 +56,7 @@ class ProblemDesc(ctypes.Structure):
         ("u_max", ctypes.c_double), ("seed", ctypes.c_uint64), ("epoch", ctypes.c_uint32),
         ("prec", ctypes.c_int), ("mode", ctypes.c_int), ("use_tensor_cores", ctypes.c_int),
         ("mem_budget_bytes", ctypes.c_size_t), ("cuda_stream", ctypes.c_void_p),
-        ("jump_gain", ctypes.c_double),
+        ("jump_gain", ctypes.c_double), ("m_offset", ctypes.c_int64),
     ]
 
 
@@ -126,6 +129,10 @@ def lib():
         L.jd_optimize.argtypes = [vp, dp, ctypes.c_int, P(OptParams), P(OptResult), dp]
         L.jd_problem_info.argtypes = [vp, P(ctypes.c_size_t), P(ctypes.c_int)]
         L.jd_cost_noalloc.argtypes = [P(ProblemDesc), dp, dp]
+        L.jd_gradient_units.argtypes = [vp, dp, ctypes.c_int, dp, ctypes.c_int]
+        L.jd_cost_units.argtypes = [vp, dp, ctypes.c_int, dp, ctypes.c_int]
+        L.jd_combine_units.argtypes = [i64, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, dp,
+                                       i64, ctypes.c_int, dp, dp]
         L.jd_fb_cost.argtypes = [vp, P(FeedbackDesc), dp, ctypes.c_int, dp]
         L.jd_fb_gradient.argtypes = [vp, P(FeedbackDesc), dp, ctypes.c_int, dp, dp]
         L.jd_fb_optimize.argtypes = [vp, P(FeedbackDesc), dp, ctypes.c_int, P(OptParams), P(OptResult), dp]
@@ -225,8 +232,24 @@ def make_desc(problem, prec=JD_FP32, mode=JD_ADJ_AUTO, use_tensor_cores=0, mem_b
         u_min=float(problem.u_min), u_max=float(problem.u_max), seed=int(problem.seed),
         epoch=int(problem.epoch), prec=_PREC[prec], mode=_MODE[mode],
         use_tensor_cores=int(use_tensor_cores), mem_budget_bytes=int(mem_budget_bytes),
-        cuda_stream=stream_handle, jump_gain=float(getattr(problem, "jump_gain", 1.0)))
+        cuda_stream=stream_handle, jump_gain=float(getattr(problem, "jump_gain", 1.0)),
+        m_offset=int(getattr(problem, "m_offset", 0)))
     return desc, a
+
+
+def combine_units(problem, u, units, M_total=None):
+    """(J, grad (Nt, du) or None) from the unit sums of all shards in path order
+    (jd_combine_units: host arithmetic, the same bits as jd_gradient on the whole
+    problem).  units: [ceil(M_total / UNIT_PATHS), ne] with ne = 1 (cost) or 1 + Nt du."""
+    M_total = int(problem.M if M_total is None else M_total)
+    units = np.ascontiguousarray(units, dtype=np.float64)
+    ne = units.shape[1]
+    u = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(-1))
+    J = ctypes.c_double()
+    g = np.zeros((problem.Nt, problem.du)) if ne > 1 else None
+    _check(lib().jd_combine_units(M_total, problem.Nt, problem.du, float(problem.T), float(problem.nu), _ptr(u),
+                                  _ptr(units), units.shape[0], ne, ctypes.byref(J), _ptr(g)), "jd_combine_units")
+    return J.value, g
 
 
 def footprint(problem, plan="stored", prec="fp32") -> int:
@@ -370,6 +393,21 @@ class JdProblem:
                                  ctypes.c_void_p(grad_out.data_ptr()), JD_MEM_DEVICE, _ptr(gth)),
                "jd_gradient")
         return (J.value if want_J else None), gth
+
+    # --- path sharding: unit sums of this problem's paths ------------------------------
+    def gradient_units(self, u):
+        """Unit sums [ceil(M / UNIT_PATHS), 1 + Nt du] (jd_gradient_units, host)."""
+        up, us, _keep = _u_arg(u, self.n)
+        out = np.zeros((-(-self.M // UNIT_PATHS), 1 + self.n))
+        _check(lib().jd_gradient_units(self.h, up, us, _ptr(out), JD_MEM_HOST), "jd_gradient_units")
+        return out
+
+    def cost_units(self, u):
+        """Cost unit sums [ceil(M / UNIT_PATHS), 1] (jd_cost_units, host)."""
+        up, us, _keep = _u_arg(u, self.n)
+        out = np.zeros((-(-self.M // UNIT_PATHS), 1))
+        _check(lib().jd_cost_units(self.h, up, us, _ptr(out), JD_MEM_HOST), "jd_cost_units")
+        return out
 
     # --- feedback control u(z, t) = mu(t)^T phi(z) (d = 2, du = 1) ---------------------
     def fb_cost(self, fb, mu) -> float:

@@ -7,11 +7,11 @@ namespace jd {
 static cudaError_t upload_kp(const jd_problem *p, int64_t m_begin, int64_t mloc, const PathBufs &b,
                              cudaStream_t s, KP32 **dev) {
   if (!p->kp_dev) return cudaErrorInvalidValue;
-  auto *kp = new KP32();
-  make_kparams<float, D32, DU32>(p, m_begin, mloc, *kp);
-  if (b.npart) kp->npart = b.npart;
-  const cudaError_t e = cudaMemcpyAsync(p->kp_dev, kp, sizeof(KP32), cudaMemcpyHostToDevice, s);
-  delete kp;   // pageable source: the copy is staged before cudaMemcpyAsync returns
+  thread_local KP32 kp;   // 13 KB: not on the stack, and not allocated per launch
+  make_kparams<float, D32, DU32>(p, m_begin, mloc, kp);
+  if (b.npart) kp.npart = b.npart;
+  // pageable source: the copy is staged before cudaMemcpyAsync returns
+  const cudaError_t e = cudaMemcpyAsync(p->kp_dev, &kp, sizeof(KP32), cudaMemcpyHostToDevice, s);
   *dev = static_cast<KP32 *>(p->kp_dev);
   return e;
 }

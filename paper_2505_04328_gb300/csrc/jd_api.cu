@@ -142,41 +142,66 @@ __device__ double block_sum_d(double v, double *sm) {
   return s;
 }
 
-// J = (1/M) sum_b partC[b] + (nu dt / 2) sum_k |u_k|^2      (eq:discrete_functional)
-__global__ void finalize_cost_kernel(const double *__restrict__ partC, int64_t nblk,
-                                     const double *__restrict__ u, int n, double half_nu_dt,
-                                     double invM, double *__restrict__ out, double *__restrict__ bad) {
-  __shared__ double sm[32];
-  double a = 0.0, b = 0.0;
-  for (int64_t i = threadIdx.x; i < nblk; i += blockDim.x) a += partC[i];
-  for (int i = threadIdx.x; i < n; i += blockDim.x) b += u[i] * u[i];
-  a = block_sum_d(a, sm);
-  b = block_sum_d(b, sm);
-  if (threadIdx.x == 0) {
-    const double J = a * invM + half_nu_dt * b;
-    *out = J;
-    if (!isfinite(J)) *bad = 1.0;
+// ---------------------------------------------------------------------------
+// The reduction over paths, defined on units of JD_UNIT_PATHS consecutive paths (128
+// blocks, 512 warps): within a unit a fixed tree over its partials, across units a plain
+// sum in unit order.  A shard of the paths that starts at a unit boundary yields exactly
+// the whole problem's unit sums, so splitting a problem over devices changes no bit.
+// ---------------------------------------------------------------------------
+constexpr int64_t UNIT_PATHS = JD_UNIT_PATHS;
+constexpr int64_t UNIT_BLOCKS = UNIT_PATHS / TPB;
+constexpr int64_t UNIT_WARPS = UNIT_PATHS / 32;
+static_assert(UNIT_PATHS % TPB == 0, "units hold whole blocks");
+
+inline int64_t n_units(int64_t M) { return ceil_div(M, UNIT_PATHS); }
+
+// units[i][e], e < ne: e = 0 the sum of unit i's cost partials (its blocks), e = 1 + k du + l
+// the sum of its gradient partials of entry (k, l) (its warps).  One warp per (unit,
+// entry): lane j adds partials j, j + 32, ... in order, then the warp's fixed tree.
+__global__ void unit_sums_kernel(const double *__restrict__ partC, int64_t nblk, const double *__restrict__ partG,
+                                 int64_t npart, int du, int DU, int64_t nunits, int ne, double *__restrict__ units) {
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (gw >= nunits * ne) return;   // whole warps (blockDim is a multiple of 32)
+  const int64_t i = gw / ne;
+  const int e = (int)(gw % ne);
+  double s = 0.0;
+  if (e == 0) {
+    const int64_t b1 = min((i + 1) * UNIT_BLOCKS, nblk);
+    for (int64_t b = i * UNIT_BLOCKS + lane; b < b1; b += 32) s += partC[b];
+  } else {
+    const int k = (e - 1) / du, l = (e - 1) % du;
+    const double *row = partG + ((int64_t)k * DU + l) * npart;
+    const int64_t w1 = min((i + 1) * UNIT_WARPS, npart);
+    for (int64_t w = i * UNIT_WARPS + lane; w < w1; w += 32) s += row[w];
   }
+  s = warp_sum_d(s);
+  if (lane == 0) units[gw] = s;
 }
 
-// grad[k*du + l] = nu dt u[k*du + l] + (1/M) sum_w partG[(k*DU + l) * npart + w]
-// (eq:definition_Gradient).  One 256-thread block per gradient entry: strided
-// per-thread sums, then a fixed tree (deterministic).
-__global__ void finalize_grad_kernel(const double *__restrict__ partG, int64_t npart, int Nt, int du,
-                                     int DU, const double *__restrict__ u, double nu_dt, double invM,
-                                     double *__restrict__ grad, double *__restrict__ bad) {
-  __shared__ double sm[32];
-  const int64_t e = blockIdx.x;
-  const int k = (int)(e / du), l = (int)(e % du);
-  const double *row = partG + ((int64_t)k * DU + l) * npart;
+// J = (1/M) sum_i units[i][0] + (nu dt / 2) sum_k |u_k|^2          (eq:discrete_functional)
+// grad[e-1] = nu dt u[e-1] + (1/M) sum_i units[i][e], e >= 1       (eq:definition_Gradient)
+// Sums in unit order with the operations of jd_combine_units (host) one for one, so the
+// device and the host combine give the same bits.
+__global__ void combine_units_kernel(const double *__restrict__ units, int64_t nunits, int ne,
+                                     const double *__restrict__ u, int n, double nu_dt, double half_nu_dt,
+                                     double invM, double *__restrict__ J, double *__restrict__ grad,
+                                     double *__restrict__ bad) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
   double s = 0.0;
-  for (int64_t b = threadIdx.x; b < npart; b += blockDim.x) s += row[b];
-  s = block_sum_d(s, sm);
-  if (threadIdx.x == 0) {
-    const double g = nu_dt * u[e] + s * invM;
-    grad[e] = g;
-    if (!isfinite(g)) *bad = 1.0;
+  for (int64_t i = 0; i < nunits; ++i) s = __dadd_rn(s, units[i * ne + e]);
+  double v;
+  if (e == 0) {
+    double b = 0.0;
+    for (int k = 0; k < n; ++k) b = __dadd_rn(b, __dmul_rn(u[k], u[k]));
+    v = __fma_rn(half_nu_dt, b, __dmul_rn(s, invM));
+    *J = v;
+  } else {
+    v = __fma_rn(nu_dt, u[e - 1], __dmul_rn(s, invM));
+    grad[e - 1] = v;
   }
+  if (!isfinite(v)) *bad = 1.0;
 }
 
 // theta[t] = (1/M) sum_b partT[map(t) * nblk + b], map: [0, 1..d, d+1] -> [0, 1..d, D+1]
@@ -371,6 +396,7 @@ static size_t base_bytes(const jd_problem_desc &q, int D, int DU, size_t es) {
   const size_t nu = (size_t)q.Nt * q.du, nblk = (size_t)ceil_div(q.M, TPB);
   return (size_t)q.Nt * DU * es + (size_t)(q.Nt + 1) * D * es + 4 * nu * 8 + NSCAL * 8 + nblk * 8 +
          (size_t)q.Nt * DU * grad_parts(q.M) * 8 + (size_t)(D + 2) * nblk * 8 +
+         (size_t)ceil_div(q.M, JD_UNIT_PATHS) * (1 + nu) * 8 +
          (D == 32 ? 16384 + (size_t)q.Nt * 32 * sizeof(float) : 0);
 }
 
@@ -450,25 +476,47 @@ static jd_status prep_u(jd_problem *p, const double *ud, void *dst = nullptr) {
   return JD_OK;
 }
 
-static jd_status finalize_cost(jd_problem *p, const double *ud, int slot, const double *partC = nullptr) {
+// Unit sums of the launch's partials (ne = 1: cost only; 1 + Nt du: cost and gradient)
+// into p->units.
+static jd_status unit_sums(jd_problem *p, int ne, const double *partC = nullptr) {
   const jd_problem_desc &q = p->desc;
-  const double dt = q.T / q.Nt;
-  const int pr = prof_begin(KC_FINALIZE, p->stream);
-  finalize_cost_kernel<<<1, 256, 0, p->stream>>>(partC ? partC : p->partC, p->nblk, ud, q.Nt * q.du, 0.5 * q.nu * dt,
-                                                 1.0 / (double)q.M, p->scal_d + slot, p->scal_d + S_BAD);
-  prof_end(pr, p->stream);
+  const int64_t nun = n_units(q.M), warps = nun * ne;
+  unit_sums_kernel<<<(unsigned)ceil_div(warps * 32, 256), 256, 0, p->stream>>>(
+      partC ? partC : p->partC, p->nblk, p->partG, grad_parts(q.M), q.du, p->DU, nun, ne, p->units);
   count_launch();
   JD_CUDA(cudaGetLastError());
   return JD_OK;
 }
 
-static jd_status run_cost(jd_problem *p, const double *ud, int slot) {
+// J (scalar slot) and, for ne > 1, the gradient (grad_d) from p->units.
+static jd_status combine_units(jd_problem *p, const double *ud, int ne, int slot) {
+  const jd_problem_desc &q = p->desc;
+  const double dt = q.T / q.Nt;
+  combine_units_kernel<<<(unsigned)ceil_div(ne, 128), 128, 0, p->stream>>>(
+      p->units, n_units(q.M), ne, ud, q.Nt * q.du, q.nu * dt, 0.5 * q.nu * dt, 1.0 / (double)q.M,
+      p->scal_d + slot, p->grad_d, p->scal_d + S_BAD);
+  count_launch();
+  JD_CUDA(cudaGetLastError());
+  return JD_OK;
+}
+
+static jd_status finalize_cost(jd_problem *p, const double *ud, int slot, const double *partC = nullptr) {
+  const int pr = prof_begin(KC_FINALIZE, p->stream);
+  jd_status s = unit_sums(p, 1, partC);
+  if (!s) s = combine_units(p, ud, 1, slot);
+  prof_end(pr, p->stream);
+  return s;
+}
+
+// finalize = false: stop at the unit sums (p->units), for jd_cost_units.
+static jd_status run_cost(jd_problem *p, const double *ud, int slot, bool finalize = true) {
   jd_status s = prep_u(p, ud);
   if (s) return s;
   const int pr = prof_begin(KC_FWD_COST, p->stream);
   const cudaError_t e = p->ops->fwd(p, FWD_COST, 0, p->desc.M, p->uk, plan_bufs(p), p->stream);
   prof_end(pr, p->stream);
   JD_CUDA(e);
+  if (!finalize) return unit_sums(p, 1);
   return finalize_cost(p, ud, slot);
 }
 
@@ -561,7 +609,9 @@ static jd_status run_pair_forward(jd_problem *p, const double *ud, int slot, con
 // Gradient at ud.  With forward_done the stored states / checkpoints, the control in
 // kernel precision and the cost partials already belong to ud (the accepted trial of
 // the previous line search), and only the adjoint half runs.
-static jd_status run_gradient(jd_problem *p, const double *ud, bool theta, bool forward_done = false) {
+// finalize = false: stop at the unit sums (p->units), for jd_gradient_units.
+static jd_status run_gradient(jd_problem *p, const double *ud, bool theta, bool forward_done = false,
+                              bool finalize = true) {
   jd_status s = ensure_plan(p);
   if (s) return s;
   const jd_problem_desc &q = p->desc;
@@ -612,16 +662,12 @@ static jd_status run_gradient(jd_problem *p, const double *ud, bool theta, bool 
   }
   JD_CUDA(e1);
   JD_CUDA(e2);
-  s = finalize_cost(p, ud, S_J);
-  if (s) return s;
-  const double dt = q.T / q.Nt;
-  const int64_t ne = (int64_t)q.Nt * q.du;
+  const int ne = 1 + q.Nt * q.du;
   const int pr = prof_begin(KC_FINALIZE, p->stream);
-  finalize_grad_kernel<<<(unsigned)ne, 256, 0, p->stream>>>(
-      p->partG, grad_parts(M), q.Nt, q.du, p->DU, ud, q.nu * dt, 1.0 / (double)M, p->grad_d, p->scal_d + S_BAD);
+  s = unit_sums(p, ne);
+  if (!s && finalize) s = combine_units(p, ud, ne, S_J);
   prof_end(pr, p->stream);
-  count_launch();
-  JD_CUDA(cudaGetLastError());
+  if (s) return s;
   if (theta) {
     finalize_theta_kernel<<<q.d + 2, 32, 0, p->stream>>>(p->partT, p->nblk, q.d, p->D,
                                                                1.0 / (double)M, p->scal_d + S_THETA);
@@ -695,6 +741,8 @@ static jd_status validate_desc(const jd_problem_desc &q) {
   if (q.du > 4) return fail(JD_ERR_UNSUPPORTED, "du > 4 is not compiled");
   if (q.Nt < 1 || q.Nt > (1 << 24)) return fail(JD_ERR_INVALID_ARG, "Nt must be in [1, 2^24]");
   if (q.M < 1 || q.M > 0xFFFFFFFFll) return fail(JD_ERR_INVALID_ARG, "M must be in [1, 2^32 - 1]");
+  if (q.m_offset < 0 || q.m_offset + q.M > 0x100000000ll)
+    return fail(JD_ERR_INVALID_ARG, "m_offset must be >= 0 with m_offset + M <= 2^32");
   if (!(q.T > 0.0) || !std::isfinite(q.T)) return fail(JD_ERR_INVALID_ARG, "T must be finite and > 0");
   if (q.drift != JD_DRIFT_LINEAR && q.drift != JD_DRIFT_CUBIC) return fail(JD_ERR_INVALID_ARG, "bad drift");
   if (q.jump_law < JD_JUMP_NONE || q.jump_law > JD_JUMP_KS) return fail(JD_ERR_INVALID_ARG, "bad jump law");
@@ -1032,6 +1080,7 @@ jd_status jd_problem_destroy(jd_problem *p) {
   free_dev(p, p->scal_d);
   free_dev(p, p->partC);
   free_dev(p, p->partG);
+  free_dev(p, p->units);
   free_dev(p, p->partT);
   free_dev(p, p->traj);
   free_dev(p, p->flags);
@@ -1169,6 +1218,7 @@ jd_status jd::create_problem(const jd_problem_desc &q, const jd::ProblemOpts &op
   ALLOC(p->partC, (size_t)p->nblk * 8, "cost partials");
   ALLOC(p->partG, (size_t)q.Nt * p->DU * grad_parts(q.M) * 8, "gradient partials");
   ALLOC(p->partT, (size_t)(p->D + 2) * p->nblk * 8, "parameter partials");
+  ALLOC(p->units, (size_t)n_units(q.M) * (1 + nu) * 8, "unit sums");
   ALLOC(p->opt_u, nu * 8, "optimizer iterate");
   ALLOC(p->opt_ut, nu * 8, "optimizer trial");
   if (p->D == 32) {
@@ -1290,6 +1340,71 @@ jd_status jd_gradient(jd_problem *p, const double *u, jd_memspace us, double *J,
   if (grad_theta)
     for (int t = 0; t < p->desc.d + 2; ++t) grad_theta[t] = p->host_pinned[S_THETA + t];
   return status_of_scalars(p);
+}
+
+// The unit sums of a problem (or of one shard of a problem) at u: the sweeps of
+// jd_gradient (grad = true) or jd_cost, then the copy of p->units to `units`.
+static jd_status units_out(jd_problem *p, const double *u, jd_memspace us, double *units, jd_memspace os,
+                           bool grad) {
+  if (!p || !units) return fail(JD_ERR_INVALID_ARG, "p and units must be non-NULL");
+  if (os != JD_MEM_HOST && os != JD_MEM_DEVICE) return fail(JD_ERR_INVALID_ARG, "bad memory space for units");
+  if (p->desc.m_offset % JD_UNIT_PATHS)
+    return fail(JD_ERR_INVALID_ARG, "a shard's m_offset must be a multiple of JD_UNIT_PATHS");
+  p->fwd_valid = false;
+  jd_status s = set_device(p);
+  if (!s) s = load_u(p, u, us);
+  if (!s) s = clear_bad(p);
+  if (!s) s = grad ? run_gradient(p, p->u_in, false, false, /*finalize=*/false) : run_cost(p, p->u_in, S_J, false);
+  if (s) return s;
+  if (grad) p->fwd_valid = true;
+  const int ne = grad ? 1 + p->desc.Nt * p->desc.du : 1;
+  const size_t n = (size_t)n_units(p->desc.M) * ne;
+  JD_CUDA(cudaMemcpyAsync(units, p->units, n * 8, os == JD_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                          p->stream));
+  if (os == JD_MEM_DEVICE) return JD_OK;
+  JD_CUDA(cudaStreamSynchronize(p->stream));
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(units[i])) return fail(JD_ERR_NONFINITE, "non-finite unit sum");
+  return JD_OK;
+}
+
+jd_status jd_gradient_units(jd_problem *p, const double *u, jd_memspace us, double *units, jd_memspace os) {
+  return units_out(p, u, us, units, os, true);
+}
+
+jd_status jd_cost_units(jd_problem *p, const double *u, jd_memspace us, double *units, jd_memspace os) {
+  return units_out(p, u, us, units, os, false);
+}
+
+// The device combine (combine_units_kernel) operation for operation, on the host.
+jd_status jd_combine_units(int64_t M_total, int Nt, int du, double T, double nu, const double *u,
+                           const double *units, int64_t nunits, int ne, double *J, double *grad) {
+  if (M_total < 1 || Nt < 1 || du < 1 || !(T > 0.0) || !std::isfinite(T) || !std::isfinite(nu) || !u || !units ||
+      !J || nunits != ceil_div(M_total, JD_UNIT_PATHS) || (ne != 1 && ne != 1 + Nt * du) || (ne > 1 && !grad))
+    return fail(JD_ERR_INVALID_ARG, "jd_combine_units: bad sizes or NULL arrays");
+  const double dt = T / Nt, nu_dt = nu * dt, half_nu_dt = 0.5 * nu * dt, invM = 1.0 / (double)M_total;
+  bool finite = true;
+  for (int e = 0; e < ne; ++e) {
+    double s = 0.0;
+    for (int64_t i = 0; i < nunits; ++i) s = s + units[i * ne + e];
+    double v;
+    if (e == 0) {
+      double b = 0.0;
+      for (int k = 0; k < Nt * du; ++k) {
+        const double sq = u[k] * u[k];
+        b = b + sq;
+      }
+      const double sm = s * invM;
+      v = std::fma(half_nu_dt, b, sm);
+      *J = v;
+    } else {
+      const double sm = s * invM;
+      v = std::fma(nu_dt, u[e - 1], sm);
+      grad[e - 1] = v;
+    }
+    finite = finite && std::isfinite(v);
+  }
+  return finite ? JD_OK : fail(JD_ERR_NONFINITE, "non-finite J or gradient");
 }
 
 jd_status jd_forward(jd_problem *p, const double *u, jd_memspace us, double *J, jd_memspace js) {

@@ -174,6 +174,7 @@ struct jd_problem {
   double *grad_d = nullptr;  // FP64 gradient, Nt*du
   double *scal_d = nullptr;  // FP64 scalars: J, theta grads, optimizer values
   double *partC = nullptr, *partG = nullptr, *partT = nullptr;
+  double *units = nullptr;   // unit sums [ceil(M / JD_UNIT_PATHS)][1 + Nt du] of the path reduction
   void *traj = nullptr;
   uint32_t *flags = nullptr;
   void *ckpt = nullptr;

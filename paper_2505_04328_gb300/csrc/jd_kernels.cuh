@@ -107,7 +107,7 @@ struct Vec4<double> {
 // the logged steps are exactly the jump steps before that one; any other jump step is
 // regenerated from the counter-based streams.
 //   kt[r * stride + idx] = (16 k + i, theta),   y[(r * D + c) * stride + idx] = Y_c
-// (16 k + i < 2^24 is exact in FP32 for N_t < 2^20; i < NMAX = 16)
+// (i < NMAX = 16; in FP32 the code is stored as the bits of an int, exact for every N_t)
 // ---------------------------------------------------------------------------
 template <typename R>
 struct V2;
@@ -115,11 +115,16 @@ template <>
 struct V2<float> {
   using T = float2;
   static __device__ __forceinline__ T make(float a, float b) { return make_float2(a, b); }
+  // a log record (code 16 k + i, theta); the code travels as the bits of an int
+  static __device__ __forceinline__ T rec(int code, float theta) { return make_float2(__int_as_float(code), theta); }
+  static __device__ __forceinline__ int code(T t) { return __float_as_int(t.x); }
 };
 template <>
 struct V2<double> {
   using T = double2;
   static __device__ __forceinline__ T make(double a, double b) { return make_double2(a, b); }
+  static __device__ __forceinline__ T rec(int code, double theta) { return make_double2((double)code, theta); }
+  static __device__ __forceinline__ int code(T t) { return (int)t.x; }
 };
 
 template <typename R, int D>
@@ -148,7 +153,7 @@ struct LogWriter {
   }
   // record of the i-th jump (time order) of step k
   __device__ __forceinline__ void put(int k, int i, R theta, const R (&y)[D]) {
-    L.kt[(int64_t)r * L.stride + idx] = V2<R>::make((R)(16 * k + i), theta);
+    L.kt[(int64_t)r * L.stride + idx] = V2<R>::rec(16 * k + i, theta);
 #pragma unroll
     for (int c = 0; c < D; ++c) L.y[((int64_t)r * D + c) * L.stride + idx] = y[c];
     ++r;
@@ -162,7 +167,7 @@ struct LogReader {
   int rec;   // latest unconsumed record, -1 when empty
   R rk;      // its step index (or -1)
   __device__ __forceinline__ R step_of(int r) const {
-    return r >= 0 ? (R)(((int)L.kt[(int64_t)r * L.stride + idx].x) >> 4) : R(-1);
+    return r >= 0 ? (R)(V2<R>::code(L.kt[(int64_t)r * L.stride + idx]) >> 4) : R(-1);
   }
   __device__ __forceinline__ void init(int count) {
     rec = count - 1;
@@ -194,7 +199,7 @@ struct LogReader2 {
   R cth, cy[D];                   // time fraction, post-jump state
   __device__ __forceinline__ void load() {
     const typename V2<R>::T t = kt[0];
-    ci = ((int)t.x) & 15;
+    ci = V2<R>::code(t) & 15;
     cth = t.y;
 #pragma unroll
     for (int c = 0; c < D; ++c) cy[c] = y[(int64_t)c * stride];
@@ -1141,29 +1146,6 @@ __device__ __forceinline__ const R *staged_rows(const unsigned char *stage, int 
                                      ((size_t)st * (TPB / 32) + (threadIdx.x >> 5)) * AdjStage<R, D>::XB);
 }
 
-template <typename R, int D>
-__device__ __forceinline__ void read_chunk(const unsigned char *stage, int st, R (&xs)[AdjChunk<R, D>::CH][D]) {
-  constexpr int NV = AdjChunk<R, D>::NV, SV = TS<R, D>::SV, VD = TS<R, D>::VD, VW = TS<R, D>::VW;
-#pragma unroll
-  for (int n = 0; n < NV; ++n) {
-    R o[VW];
-    const unsigned char *src = stage + (((size_t)st * NV + n) * TPB + threadIdx.x) * 16;
-    if constexpr (sizeof(R) == 4) {
-      const float4 t = *reinterpret_cast<const float4 *>(src);
-      o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
-    } else {
-      const double2 t = *reinterpret_cast<const double2 *>(src);
-      o[0] = t.x; o[1] = t.y;
-    }
-    const int gi = n / VD, v = n % VD;
-#pragma unroll
-    for (int w = 0; w < VW; ++w) {
-      const int pos = v * VW + w;
-      xs[gi * SV + pos / D][pos % D] = o[w];
-    }
-  }
-}
-
 template <typename R, int D, int DU, bool THETA>
 __device__ __forceinline__ void finish_theta(const KParams<R, D, DU> &kp, R (&th)[D + 2], bool active,
                                              double *__restrict__ partT, Pair<R> *red) {
@@ -1435,7 +1417,8 @@ adj_recompute_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__re
       const uint32_t jwm = __reduce_or_sync(0xffffffffu, (jm >> i0) & ((1u << CH) - 1u));
       if (!THETA && !slow) {
         const R *xdc = xd + (size_t)(k0 + i0) * D;
-#pragma unroll
+        // rolled (the states come from shared memory anyway; measured faster than unrolled)
+#pragma unroll 1
         for (int j = CH - 1; j >= 0; --j) {
           const int i = i0 + j;
           R g[DU], xk[D], xdk[D];
@@ -1541,7 +1524,7 @@ void make_kparams(const jd_problem *p, int64_t m_begin, int64_t mloc, KParams<R,
   kp.has_dA = !p->dA.empty();
   kp.S = seg_len<D>();
   kp.nblk = (int)ceil_div(mloc, TPB);
-  kp.m_begin = m_begin;
+  kp.m_begin = q.m_offset + m_begin;   // global path index (a shard starts at m_offset)
   kp.npart = grad_parts(mloc);
 }
 

@@ -25,6 +25,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 constexpr int kNoAllocMaxDevices = 64;
 static std::mutex g_noalloc_mu;
 static unsigned char *g_noalloc_ptr[kNoAllocMaxDevices];
+static size_t g_noalloc_stack[kNoAllocMaxDevices][4];   // local bytes per thread of each cost kernel
 
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
@@ -112,7 +113,7 @@ static void noalloc_kparams(const jd_problem_desc &q, KParams<R, D, DU> &kp) {
   kp.has_dA = 0;
   kp.S = seg_len<D>();
   kp.nblk = (int)ceil_div(q.M, TPB);
-  kp.m_begin = 0;
+  kp.m_begin = q.m_offset;   // global index of the first path
   kp.npart = kp.nblk * (int64_t)(TPB / 32);
 }
 
@@ -159,7 +160,8 @@ extern "C" jd_status jd_cost_noalloc(const jd_problem_desc *desc, const double *
       (q.drift == JD_DRIFT_CUBIC && !q.C) || q.drift < JD_DRIFT_LINEAR || q.drift > JD_DRIFT_CUBIC ||
       q.jump_law < JD_JUMP_NONE || q.jump_law > JD_JUMP_UNIFORM || !(q.lambda >= 0.0) ||
       !std::isfinite(q.lambda) || !(q.jump_scale >= 0.0) || !std::isfinite(q.jump_scale) ||
-      !std::isfinite(q.nu) || (q.prec != JD_FP32 && q.prec != JD_FP64))
+      !std::isfinite(q.nu) || (q.prec != JD_FP32 && q.prec != JD_FP64) || q.m_offset < 0 ||
+      q.m_offset + q.M > 0x100000000ll)
     return JD_ERR_INVALID_ARG;
   if (q.d > 2 || q.du != 1 || q.use_tensor_cores) return JD_ERR_UNSUPPORTED;
   const int D = q.d;
@@ -168,27 +170,39 @@ extern "C" jd_status jd_cost_noalloc(const jd_problem_desc *desc, const double *
                       align256((size_t)q.Nt * es) + align256((size_t)ceil_div(q.M, TPB) * 8);
   if (need > kNoAllocScratchBytes) return JD_ERR_OOM;   // beyond the fixed scratch
 
-  // The cost kernels used here need less than the default 1 KiB per-thread stack;
-  // refuse rather than raise the limit (raising it makes the driver allocate).
-  size_t stack = 0;
-  if (cudaDeviceGetLimit(&stack, cudaLimitStackSize) != cudaSuccess || stack < 1024)
-    return JD_ERR_UNSUPPORTED;
-
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return JD_ERR_CUDA;
   if (dev < 0 || dev >= kNoAllocMaxDevices) return JD_ERR_UNSUPPORTED;
+  const int kid = (q.prec == JD_FP64 ? 2 : 0) + (D - 1);   // which cost kernel runs
   unsigned char *scratch = nullptr;
+  size_t need_stack = 0;
   {
     // first call on a device: take the device address of the scratch array with this
-    // device current (the host-side symbol is not a device address)
+    // device current (the host-side symbol is not a device address), and the per-thread
+    // stack each of the four cost kernels needs
     std::lock_guard<std::mutex> g(g_noalloc_mu);
     if (!g_noalloc_ptr[dev]) {
       void *ptr = nullptr;
       if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return JD_ERR_CUDA;
+      const void *ks[4] = {(const void *)fwd_kernel<float, 1, 1, FWD_COST>,
+                           (const void *)fwd_kernel<float, 2, 1, FWD_COST>,
+                           (const void *)fwd_kernel<double, 1, 1, FWD_COST>,
+                           (const void *)fwd_kernel<double, 2, 1, FWD_COST>};
+      for (int i = 0; i < 4; ++i) {
+        cudaFuncAttributes a;
+        if (cudaFuncGetAttributes(&a, ks[i]) != cudaSuccess) return JD_ERR_CUDA;
+        g_noalloc_stack[dev][i] = a.localSizeBytes;
+      }
       g_noalloc_ptr[dev] = static_cast<unsigned char *>(ptr);
     }
     scratch = g_noalloc_ptr[dev];
+    need_stack = g_noalloc_stack[dev][kid];
   }
+  // The context's per-thread stack must hold the kernel's local frame; refuse rather
+  // than raise the limit (raising it makes the driver allocate).
+  size_t stack = 0;
+  if (cudaDeviceGetLimit(&stack, cudaLimitStackSize) != cudaSuccess || stack < need_stack)
+    return JD_ERR_UNSUPPORTED;
   if (q.prec == JD_FP64) return D == 1 ? noalloc_run<double, 1>(q, scratch, u, J) : noalloc_run<double, 2>(q, scratch, u, J);
   return D == 1 ? noalloc_run<float, 1>(q, scratch, u, J) : noalloc_run<float, 2>(q, scratch, u, J);
 }

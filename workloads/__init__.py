@@ -75,6 +75,7 @@ class Problem:
     seed: int = 0
     epoch: int = 0
     name: str = ""
+    m_offset: int = 0             # global index of the first path (one shard of a larger sample)
 
     def replace(self, **kw) -> "Problem":
         """A copy with some fields changed; the target is resampled if Nt changes."""
