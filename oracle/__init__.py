@@ -130,6 +130,7 @@ def lib():
             L.orc_fb_surrogate_state.argtypes = [P(_Problem), P(_Feedback), ctypes.c_int, ctypes.c_int64,
                                                  ctypes.c_void_p]
             L.orc_fb_coupled.argtypes = [P(_Problem), P(_Feedback), ctypes.c_void_p, ctypes.c_int64] + [ctypes.c_void_p] * 4
+            L.orc_ring_lanes.argtypes = [ctypes.c_int]
             L.orc_fb_coupled_gradient.argtypes = [P(_Problem), P(_Feedback), ctypes.c_void_p, ctypes.c_int,
                                                   ctypes.c_void_p, ctypes.c_void_p]
             L.orc_fb_optimize.argtypes = [P(_Problem), P(_Feedback), ctypes.c_void_p, P(_OptParams), ctypes.c_int,
@@ -369,6 +370,11 @@ def fb_surrogate_state(p, fb, k: int, m: int):
     return z
 
 
+def ring_lanes(N: int) -> int:
+    """Path-index stride of a ring of N particles (orc_ring_lanes)."""
+    return int(lib().orc_ring_lanes(int(N)))
+
+
 def fb_coupled(p, fb, mu=None, r: int = 0, adjoint: bool = True):
     """Realization r of the coupled particles: dict(X (Nt+1,N,2), lam, G (Nt,L) summed over
     the particles, cost summed over the particles)."""
@@ -388,7 +394,8 @@ def fb_coupled(p, fb, mu=None, r: int = 0, adjoint: bool = True):
 
 
 def fb_coupled_gradient(p, fb, mu=None):
-    """(J, dJ/dmu (Nt, L)) over the M/32 realizations of the coupled particles."""
+    """(J, dJ/dmu (Nt, L)) over the M/S realizations of the coupled particles
+    (S = ring_lanes(particles))."""
     op = OracleProblem(p)
     F = _fb(fb)
     mu = _mu(p, fb, mu)

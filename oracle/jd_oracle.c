@@ -914,15 +914,28 @@ int orc_fb_optimize(const orc_problem *P, const orc_feedback *F, double *mu, con
 /* ------------------------------------------------------------------------- */
 /* Interacting particles (Sec. 6.4)                                           */
 /* ------------------------------------------------------------------------- */
+/* Path indices of a ring: particle i of realization r has path index S r + i, S the
+ * ring's lane count: 32 for N <= 32, the next power of two for N <= 256, then the next
+ * multiple of 256 (S >= N; indices S r + N .. S r + S - 1 are not used). */
+int orc_ring_lanes(int N) {
+  if (N <= 32) return 32;
+  if (N <= 256) {
+    int s = 64;
+    while (s < N) s *= 2;
+    return s;
+  }
+  return 256 * ((N + 255) / 256);
+}
+
 static int coupled_valid(const orc_problem *P, const orc_feedback *F) {
-  return fb_valid(P, F) && F->particles >= 3 && F->particles <= 32 && F->ax > 0.0 && F->av > 0.0 &&
+  return fb_valid(P, F) && F->particles >= 3 && F->particles <= ORC_RING_MAX && F->ax > 0.0 && F->av > 0.0 &&
          F->adjoint == ORC_FB_EXACT;
 }
 
 int orc_fb_coupled(const orc_problem *P0, const orc_feedback *F, const double *mu, int64_t r, double *X,
                    double *lam, double *G, double *cost) {
-  if (!coupled_valid(P0, F) || !mu || r < 0 || 32 * r >= P0->M) return 1;
-  const int N = F->particles, Nt = P0->Nt, L = F->nx * F->nv;
+  const int N = F->particles, S = orc_ring_lanes(N), Nt = P0->Nt, L = F->nx * F->nv;
+  if (!coupled_valid(P0, F) || !mu || r < 0 || (int64_t)S * r >= P0->M) return 1;
   const double dt = P0->T / (double)Nt, om = F->omega;
   /* the particle's own share of the coupling, -2 omega x_i, joins its drift matrix */
   orc_problem P = *P0;
@@ -932,8 +945,8 @@ int orc_fb_coupled(const orc_problem *P0, const orc_feedback *F, const double *m
   orc_draws *D = (orc_draws *)malloc(sizeof(orc_draws));
   double (*Y)[ORC_DMAX] = (double (*)[ORC_DMAX])malloc(sizeof(double) * ORC_DMAX * (ORC_NMAX + 2));
   double *phi = (double *)malloc(sizeof(double) * L);
-  double cin[32], s[32];
-  if (!Xs || !D || !Y || !phi) return 2;
+  double *cin = (double *)malloc(sizeof(double) * N), *s = (double *)malloc(sizeof(double) * N);
+  if (!Xs || !D || !Y || !phi || !cin || !s) return 2;
   for (int i = 0; i < N; ++i) {
     Xs[2 * i] = F->ax * cos(2.0 * M_PI * i / N);
     Xs[2 * i + 1] = F->av * sin(2.0 * M_PI * i / N);
@@ -943,7 +956,7 @@ int orc_fb_coupled(const orc_problem *P0, const orc_feedback *F, const double *m
     const double *Xk = Xs + (size_t)k * N * 2;
     for (int i = 0; i < N; ++i) cin[i] = om * (Xk[2 * ((i + N - 1) % N)] + Xk[2 * ((i + 1) % N)]);
     for (int i = 0; i < N; ++i) {
-      orc_step_draws(&P, k, 32 * r + i, D);
+      orc_step_draws(&P, k, S * r + i, D);
       c_r += integrate_step_fb(&P, F, D, Xk + 2 * i, mu + (size_t)k * L, cin[i], Y);
       memcpy(Xs + ((size_t)(k + 1) * N + i) * 2, Y[D->n + 1], sizeof(double) * 2);
       c_r += dt * fb_track(&P, F, Xs + ((size_t)(k + 1) * N + i) * 2, k + 1, NULL);
@@ -968,7 +981,7 @@ int orc_fb_coupled(const orc_problem *P0, const orc_feedback *F, const double *m
       for (int i = 0; i < N; ++i) cin[i] = om * (Xk[2 * ((i + N - 1) % N)] + Xk[2 * ((i + 1) % N)]);
       for (int i = 0; i < N; ++i) {
         double *ai = a + 2 * i;
-        orc_step_draws(&P, k, 32 * r + i, D);
+        orc_step_draws(&P, k, S * r + i, D);
         integrate_step_fb(&P, F, D, Xk + 2 * i, mu_k, cin[i], Y);
         s[i] = 0.0;
         for (int j = D->n; j >= 0; --j) {
@@ -998,14 +1011,17 @@ int orc_fb_coupled(const orc_problem *P0, const orc_feedback *F, const double *m
   free(D);
   free(Y);
   free(phi);
+  free(cin);
+  free(s);
   return 0;
 }
 
 int orc_fb_coupled_gradient(const orc_problem *P, const orc_feedback *F, const double *mu, int nthreads,
                             double *J, double *grad) {
   (void)nthreads;
-  if (!coupled_valid(P, F) || !mu || P->M % 32 != 0) return 1;
-  const int64_t R = P->M / 32;
+  const int S = coupled_valid(P, F) ? orc_ring_lanes(F->particles) : 32;
+  if (!coupled_valid(P, F) || !mu || P->M % S != 0) return 1;
+  const int64_t R = P->M / S;
   const size_t n = (size_t)P->Nt * F->nx * F->nv;
   double *G = grad ? (double *)malloc(sizeof(double) * n) : NULL;
   if (grad) memset(grad, 0, sizeof(double) * n);

@@ -186,17 +186,21 @@ int orc_fb_cost(const orc_problem *P, const orc_feedback *F, const double *mu, i
                 double *J);
 int orc_fb_gradient(const orc_problem *P, const orc_feedback *F, const double *mu, int nthreads,
                     double *J, double *grad);
-/* Interacting particles (Sec. 6.4 eq:interacting_model): N = F->particles particles on a
- * ring, particle i of realization r with the random streams of path index 32 r + i,
+/* Interacting particles (Sec. 6.4 eq:interacting_model): N = F->particles particles
+ * (3 <= N <= ORC_RING_MAX) on a ring, particle i of realization r with the random streams
+ * of path index S r + i, S = orc_ring_lanes(N) (32 for N <= 32, the next power of two up
+ * to 256, then the next multiple of 256),
  *   dx_i = v_i dt,  dv_i = (u(x_i, v_i, t) - eta x_i - omega (2 x_i - x_{i-1} - x_{i+1})) dt + ...
  * (eta = -A[1][0]; the own term 2 omega x_i with the particle's drift; the neighbours'
  * positions at t_k drive every sub-step of step k).  Particles start equidistant on the
  * ellipse (ax cos(2 pi i/N), av sin(2 pi i/N)).  X (Nt+1)*N*2, lam (Nt+1)*N*2, G (Nt*L,
  * summed over the realization's particles), cost (sum of the particles' path costs); each
  * nullable. */
+#define ORC_RING_MAX 2048
+int orc_ring_lanes(int N);
 int orc_fb_coupled(const orc_problem *P, const orc_feedback *F, const double *mu, int64_t r, double *X,
                    double *lam, double *G, double *cost);
-/* J = (1/(R N)) sum over R = M/32 realizations and N particles; grad likewise (Nt*L). */
+/* J = (1/(R N)) sum over R = M/S realizations and N particles; grad likewise (Nt*L). */
 int orc_fb_coupled_gradient(const orc_problem *P, const orc_feedback *F, const double *mu, int nthreads,
                             double *J, double *grad);
 /* Gradient descent with the Armijo rule on mu (Algorithm 5.4, unconstrained): the same

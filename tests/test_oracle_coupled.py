@@ -1,6 +1,9 @@
 """Pins of the oracle's interacting-particle form (Sec. 6.4 eq:interacting_model, Eq.
-phonon_functional_tracking): rings of N particles, particle i of realization r on the
-random streams of path index 32 r + i, the neighbours' positions at t_k driving the step.
+phonon_functional_tracking): rings of N particles (3 <= N <= 2048), particle i of
+realization r on the random streams of path index S r + i (S = ring_lanes(N): 32 for
+N <= 32, the next power of two up to 256, then the next multiple of 256), the
+neighbours' positions at t_k driving the step.  Each pin runs a ring of at most 32
+particles and one of more.
 
 * omega = 0 decouples the ring: each particle is the single-particle feedback path from
   its ellipse point (cost and gradient add up);
@@ -26,17 +29,24 @@ def _ellipse(fb, N):
     return np.stack([fb.ax * np.cos(th), fb.av * np.sin(th)], axis=1)
 
 
-def test_zero_coupling_is_independent_particles():
-    p, fb = workloads.feedback_coupled(M=64, Nt=25, particles=5)
+def test_ring_lanes():
+    assert [oracle.ring_lanes(n) for n in (3, 32, 33, 64, 65, 200, 256, 257, 2000, 2048)] == \
+        [32, 32, 64, 64, 128, 256, 256, 512, 2048, 2048]
+
+
+@pytest.mark.parametrize("N", [5, 40])
+def test_zero_coupling_is_independent_particles(N):
+    S = oracle.ring_lanes(N)
+    p, fb = workloads.feedback_coupled(M=2 * S, Nt=25, particles=N)
     p = p.replace(lam=6.0)
     fb = fb.replace(omega=0.0)
     mu = workloads.random_mu(p, fb, seed=4, scale=0.6)
-    Z0 = _ellipse(fb, 5)
+    Z0 = _ellipse(fb, N)
     for r in (0, 1):
         c = oracle.fb_coupled(p, fb, mu, r)
         cost, G = 0.0, np.zeros_like(c["G"])
-        for i in range(5):
-            s = oracle.fb_path(p.replace(x0=Z0[i]), fb.replace(particles=0), mu, 32 * r + i)
+        for i in range(N):
+            s = oracle.fb_path(p.replace(x0=Z0[i]), fb.replace(particles=0), mu, S * r + i)
             cost += s["cost"]
             G += s["G"]
             assert np.allclose(c["X"][:, i], s["X"], rtol=1e-14, atol=1e-14)
@@ -44,11 +54,11 @@ def test_zero_coupling_is_independent_particles():
         assert np.allclose(c["G"], G, rtol=1e-12, atol=1e-16)
 
 
-def test_coupled_euler_converges_to_the_ring_ode():
+@pytest.mark.parametrize("N", [6, 40])
+def test_coupled_euler_converges_to_the_ring_ode(N):
     """No noise, no jumps, constant weights: z' = (x', v') with x_i' = v_i,
     v_i' = u(x_i, v_i) - eta x_i - omega (2 x_i - x_{i-1} - x_{i+1})."""
-    N = 6
-    p0, fb = workloads.feedback_coupled(M=32, Nt=10, particles=N)
+    p0, fb = workloads.feedback_coupled(M=oracle.ring_lanes(N), Nt=10, particles=N)
     fb = fb.replace(nx=4, nv=4, omega=0.7)
     mu1 = np.random.default_rng(12).standard_normal(fb.L) * 0.5
     eta = -p0.A[1, 0]
@@ -90,8 +100,9 @@ def _fd(fun, x, e, h):
     return (fun(x + h * e) - fun(x - h * e)) / (2 * h)
 
 
-def test_coupled_gradient_central_differences():
-    p, fb = workloads.feedback_coupled(M=64, Nt=20, particles=6)
+@pytest.mark.parametrize("N", [6, 40])
+def test_coupled_gradient_central_differences(N):
+    p, fb = workloads.feedback_coupled(M=2 * oracle.ring_lanes(N), Nt=20, particles=N)
     p = p.replace(lam=8.0)
     mu = workloads.random_mu(p, fb, seed=5, scale=0.6)
     J, g = oracle.fb_coupled_gradient(p, fb, mu)
@@ -103,13 +114,13 @@ def test_coupled_gradient_central_differences():
         assert abs(fd - float((g * e).sum())) <= 1e-7 * np.linalg.norm(g), (fd, (g * e).sum())
 
 
-def test_initial_costates_against_differences_in_the_ellipse_axes():
+@pytest.mark.parametrize("N", [5, 300])
+def test_initial_costates_against_differences_in_the_ellipse_axes(N):
     """With the Gaussian tracking term the cost depends on the half-axes only through the
     initial states (A_x cos th_i, A_v sin th_i): dJ/dA_x = sum_i lambda_x,i(0) cos th_i and
     dJ/dA_v = sum_i lambda_v,i(0) sin th_i, with the coupling (omega = 0.5), noise and
     resets in the adjoint."""
-    N = 5
-    p, fb = workloads.feedback_coupled(M=32, Nt=30, particles=N)
+    p, fb = workloads.feedback_coupled(M=oracle.ring_lanes(N), Nt=30, particles=N)
     p = p.replace(lam=5.0)
     fb = fb.replace(track=workloads.TRACK_GAUSS)
     mu = workloads.random_mu(p, fb, seed=6, scale=0.5)

@@ -285,7 +285,8 @@ def feedback_coupled(M: int = 1 << 20, Nt: int = 100, seed: int = 0, particles: 
     """(Problem, Feedback) of Sec. 6.4: rings of `particles` coupled oscillators (eta = 1,
     omega = 0.5) started equidistant on the ellipse A_x = 1.5, A_v = 1.7071067811865475,
     ellipse tracking cost (sigma_J = 1), 10x10 bumps (eps = 0.5), Keilson-Storer resets;
-    M = 32 x realizations (lanes beyond `particles` idle)."""
+    M = S x realizations, S the ring's lane count (32 for up to 32 particles, the next
+    power of two up to 256, then the next multiple of 256; lanes beyond `particles` idle)."""
     p, fb = feedback_centering(M=M, Nt=Nt, seed=seed)
     fb = fb.replace(track=TRACK_ELLIPSE, particles=particles, omega=0.5, ax=1.5, av=1.7071067811865475)
     return p.replace(name="feedback_coupled"), fb
