@@ -213,6 +213,16 @@ def run_reference(args):
 UNIT_PATHS = 16384   # JD_UNIT_PATHS
 
 
+def ring_lanes(N: int) -> int:
+    """Lanes of a ring of N interacting particles (32 up to 32 particles, the next power of
+    two up to 256, then the next multiple of 256): the path-index stride of its rings."""
+    if N <= 32:
+        return 32
+    if N <= 256:
+        return 1 << (N - 1).bit_length()
+    return 256 * -(-N // 256)
+
+
 def shard_range(M, rank, world, unit=UNIT_PATHS):
     """Paths [m0, m0 + n) of one rank: whole units of the path reduction in rank order,
     split as evenly as possible (a rank may get none)."""
@@ -446,6 +456,11 @@ def run_feedback(args, p, stream, dist, ws, rank, local):
     import ctypes
 
     fb = FB_WORKLOADS[args.workload]()[1]
+    if args.particles is not None and fb.particles:
+        # rings of another size: the same number of lanes, rounded to whole rings
+        S = ring_lanes(args.particles)
+        fb = fb.replace(particles=args.particles)
+        p = p.replace(M=max(S, p.M // S * S))
     if args.fb_adjoint == "surrogate":
         fb = fb.replace(adjoint=workloads.FB_SURROGATE, sur_rate=args.sur_rate)
     M, Nt, L = p.M, p.Nt, fb.L
@@ -529,6 +544,7 @@ def run_feedback(args, p, stream, dist, ws, rank, local):
                        "variant": "stored" if fb.adjoint == workloads.FB_EXACT else
                                   f"surrogate adjoint (Sec. 6.5), rate {fb.sur_rate}",
                        "paths_per_gpu": M, "Nt": Nt, "eps": fb.eps,
+                       "particles_per_ring": fb.particles or None,
                        "step": "one feedback gradient dJ/dmu (forward sweep, adjoint sweep, reductions)",
                        "l2": "inputs larger than L2: the stored states (%.2f GB) and warp partials exceed "
                              "the 129 MB L2; no flush" % ((Nt + 1) * 2 * M * 4 / 1e9)},
@@ -940,6 +956,8 @@ def main():
     ap.add_argument("--steps-t", type=int, default=None, help="override N_t")
     ap.add_argument("--reference-paths", type=int, default=1 << 14)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--particles", type=int, default=None,
+                    help="feedback_coupled: particles per ring (3..2048; the paper's Sec. 6 uses 2000)")
     ap.add_argument("--shard", action="store_true",
                     help="one problem's paths split over the ranks (one gradient per step, strong scaling)")
     ap.add_argument("--fb-adjoint", default="exact", choices=["exact", "surrogate"],

@@ -1102,6 +1102,7 @@ jd_status jd_problem_destroy(jd_problem *p) {
   free_dev(p, p->bu_dev);
   free_dev(p, p->fb_mu);
   free_dev(p, p->fb_traj);
+  free_dev(p, p->fb_z0);
   free_dev(p, p->fb_flags);
   free_dev(p, p->fb_mu64);
   free_dev(p, p->fb_grad);
@@ -1598,16 +1599,44 @@ static jd_status fb_validate(const jd_problem *p, const jd_feedback_desc *fb) {
   if ((fb->track == JD_TRACK_ELLIPSE || fb->particles) &&
       (!(fb->ax > 0.0) || !std::isfinite(fb->ax) || !(fb->av > 0.0) || !std::isfinite(fb->av)))
     return fail(JD_ERR_INVALID_ARG, "ax and av must be finite and > 0");
-  if (fb->particles != 0 && (fb->particles < 3 || fb->particles > 32))
-    return fail(JD_ERR_INVALID_ARG, "particles must be 0 or in [3, 32]");
-  if (fb->particles && (p->desc.M % 32 != 0 || !std::isfinite(fb->omega)))
-    return fail(JD_ERR_INVALID_ARG, "interacting particles need M a multiple of 32 and a finite omega");
+  if (fb->particles != 0 && (fb->particles < 3 || fb->particles > RING_MAX))
+    return fail(JD_ERR_INVALID_ARG, "particles must be 0 or in [3, 2048]");
+  if (fb->particles) {
+    // rings are whole: M a multiple of the ring's lanes S, and of the block for rings
+    // beyond one warp (their exchange has block or cluster barriers)
+    const int64_t S = ring_lanes(fb->particles), unit = fb->particles <= 32 ? S : std::max<int64_t>(S, FB_TPB);
+    if (p->desc.M % unit != 0 || !std::isfinite(fb->omega))
+      return fail(JD_ERR_INVALID_ARG,
+                  "interacting particles need a finite omega and M a multiple of the ring's lanes (32 for up to 32 "
+                  "particles, else the next power of two and at least 256 up to 256 particles, then the next "
+                  "multiple of 256)");
+  }
   if (fb->particles && fb->adjoint != JD_FB_EXACT)
     return fail(JD_ERR_UNSUPPORTED, "interacting particles take the exact adjoint only");
   if (fb->adjoint != JD_FB_EXACT && fb->adjoint != JD_FB_SURROGATE)
     return fail(JD_ERR_INVALID_ARG, "bad feedback adjoint");
   if (fb->adjoint == JD_FB_SURROGATE && (!(fb->sur_rate >= 0.0) || !std::isfinite(fb->sur_rate)))
     return fail(JD_ERR_INVALID_ARG, "sur_rate must be finite and >= 0");
+  return JD_OK;
+}
+
+// Initial states of a ring's particles, equidistant on the ellipse (Sec. 6.4): particle
+// i at (ax cos(2 pi i / N), av sin(2 pi i / N)), in kernel precision, [2][S] (idle lanes 0).
+static jd_status fb_upload_ring(jd_problem *p, const jd_feedback_desc &fb) {
+  const int N = fb.particles, S = ring_lanes(N);
+  std::vector<double> z(2 * (size_t)S, 0.0);
+  for (int i = 0; i < N; ++i) {
+    const double th = 2.0 * 3.14159265358979323846 * i / N;
+    z[i] = fb.ax * std::cos(th);
+    z[S + i] = fb.av * std::sin(th);
+  }
+  if (elem_size(p) == 8) {
+    JD_CUDA(cudaMemcpy(p->fb_z0, z.data(), z.size() * 8, cudaMemcpyHostToDevice));
+  } else {
+    std::vector<float> zf(z.size());
+    for (size_t i = 0; i < z.size(); ++i) zf[i] = (float)z[i];
+    JD_CUDA(cudaMemcpy(p->fb_z0, zf.data(), zf.size() * 4, cudaMemcpyHostToDevice));
+  }
   return JD_OK;
 }
 
@@ -1639,6 +1668,7 @@ static jd_status fb_ensure(jd_problem *p, const FbOps *ops, bool grad) {
     s = dev_alloc(p, &p->fb_partW, (size_t)nwarp * Nt * LP * es, "feedback warp partials");
   if (!s && grad && !p->fb_partG)
     s = dev_alloc(p, (void **)&p->fb_partG, (size_t)fb_groups(nwarp) * Nt * LP * 8, "feedback group partials");
+  if (!s && !p->fb_z0) s = dev_alloc(p, &p->fb_z0, (size_t)2 * RING_MAX * es, "ring initial states");
   if (s) return s;
   // once per padded size: raising the limit reallocates local memory (a device-wide sync)
   const size_t need = ops->stack_bytes();
@@ -1677,6 +1707,10 @@ static jd_status fb_run(jd_problem *p, const jd_feedback_desc *fb, const double 
     mud = p->fb_mu64;
   }
   if (!forward_done) JD_CUDA(ops->prep_mu(mud, p->fb_mu, Nt, fb->nx, fb->nv, p->stream));
+  if (fb->particles && !forward_done) {
+    s = fb_upload_ring(p, *fb);
+    if (s) return s;
+  }
   FbBufs b;
   b.mu = p->fb_mu;
   b.traj = p->fb_traj;
@@ -1708,8 +1742,8 @@ static jd_status fb_run(jd_problem *p, const jd_feedback_desc *fb, const double 
   }
   pr = prof_begin(KC_FB_FIN, p->stream);
   const int64_t nblk = ceil_div(p->desc.M, FB_TPB);
-  // the average runs over the particles that exist: M paths, or M/32 rings of N particles
-  const int64_t count = fb->particles ? p->desc.M / 32 * fb->particles : p->desc.M;
+  // the average runs over the particles that exist: M paths, or M/S rings of N particles
+  const int64_t count = fb->particles ? p->desc.M / ring_lanes(fb->particles) * fb->particles : p->desc.M;
   JD_CUDA(fb_finalize(p->fb_partC, p->fb_partG, nblk, fb_groups(nblk * (FB_TPB / 32)), Nt, fb->nx, fb->nv,
                       ops->NX, ops->NV, count, p->scal_d + S_J, grad_out, p->stream));
   prof_end(pr, p->stream);

@@ -44,6 +44,8 @@
 //   partG [ngroup][Nt][NX/2][NV][2] FP64 sums of partW over groups of FB_GROUP_WARPS warps
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "jd_kernels.cuh"
 
 namespace jd {
@@ -60,10 +62,63 @@ struct FbParams {
   R srate_dt;               // surrogate adjoint (Sec. 6.5): variance of step k is srate_dt k
   R omega;                  // interacting particles (Sec. 6.4): ring coupling
   R iax2, iav2;             // ellipse cost: 1 / A_x^2, 1 / A_v^2
-  R x0c[32], v0c[32];       // interacting particles: initial state of lane i (on the ellipse)
-  int gauss, ellipse, N, Nt;   // N: particles per warp (ring), 0 = independent paths
+  const R *z0;              // interacting particles: initial states [2][S] (on the ellipse)
+  int gauss, ellipse, N, Nt;   // N: particles per ring, 0 = independent paths
+  int S;                    // lanes (path indices) per ring: particle i of ring r is lane S r + i
   int64_t mloc;
 };
+
+// ---------------------------------------------------------------------------
+// Rings of interacting particles (Sec. 6.4): particle i of a ring needs a value of its
+// neighbours i - 1 and i + 1 (cyclic over the ring's N particles) once per step.  The ring
+// occupies S consecutive lanes (S = 32 for N <= 32, the next power of two up to 256, then
+// 256 per block of a thread-block cluster), by its size:
+//   RING 1: one warp per ring, two shuffles;
+//   RING 2: rings of 64, 128 or 256 lanes within a block: shared memory, one block barrier;
+//   RING 3: a ring of C = S / 256 blocks forming one thread-block cluster (N <= 2048): each
+//           block's shared memory, read across the cluster (distributed shared memory),
+//           one cluster barrier.
+// Every lane of a ring (idle ones too) calls get() once per step; the buffers alternate,
+// so one barrier per exchange suffices.
+// ---------------------------------------------------------------------------
+template <typename R, int RING>
+struct RingX {
+  R *sv;        // RING >= 2: [2][FB_TPB] shared buffer of this block
+  int i, N;     // particle index in the ring, particles per ring
+  int par = 0;  // buffer in use
+  __device__ __forceinline__ int left() const { return i == 0 ? N - 1 : i - 1; }
+  __device__ __forceinline__ int right() const { return i == N - 1 ? 0 : i + 1; }
+  __device__ __forceinline__ void get(R v, R &vl, R &vr) {
+    if constexpr (RING == 1) {
+      const int l = i < N ? left() : 0, r = i < N ? right() : 0;
+      vl = __shfl_sync(0xffffffffu, v, l);
+      vr = __shfl_sync(0xffffffffu, v, r);
+    } else if constexpr (RING == 2) {
+      R *b = sv + par * FB_TPB;
+      b[threadIdx.x] = v;
+      __syncthreads();
+      const int base = threadIdx.x - i;
+      vl = i < N ? b[base + left()] : R(0);
+      vr = i < N ? b[base + right()] : R(0);
+      par ^= 1;
+    } else if constexpr (RING == 3) {
+      namespace cg = cooperative_groups;
+      cg::cluster_group cl = cg::this_cluster();
+      R *b = sv + par * FB_TPB;
+      b[threadIdx.x] = v;
+      cl.sync();
+      vl = vr = R(0);
+      if (i < N) {
+        const int l = left(), r = right();
+        vl = *cl.map_shared_rank(b + l % FB_TPB, (unsigned)(l / FB_TPB));
+        vr = *cl.map_shared_rank(b + r % FB_TPB, (unsigned)(r / FB_TPB));
+      }
+      par ^= 1;
+    }
+  }
+};
+
+
 
 // ---------------------------------------------------------------------------
 // Bumps.  phi = exp(-t), t = 1 / (1 - eps^2 r^2) on the support;
@@ -345,28 +400,33 @@ __device__ __forceinline__ double fb_block_sum(Pair<R> v, Pair<R> *red) {
   return out;
 }
 
-template <typename R, int NX, int NV, bool STORE, bool CPL>
+template <typename R, int NX, int NV, bool STORE, int RING>
 __global__ void __launch_bounds__(FB_TPB)
 fb_fwd_kernel(const __grid_constant__ KParams<R, 2, 1> kp, const __grid_constant__ FbParams<R> fp,
               const R *__restrict__ mu, const R *__restrict__ xd, R *__restrict__ traj,
               uint32_t *__restrict__ flags, double *__restrict__ partC) {
   using M = Ar<R>;
   constexpr int LP = NX * NV;
+  constexpr bool CPL = RING > 0;
   __shared__ Pair<R> red[FB_TPB / 32];
-  const int lane = threadIdx.x & 31;
+  __shared__ R ringbuf[RING >= 2 ? 2 * FB_TPB : 1];
   const int64_t mloc = fp.mloc, m = (int64_t)blockIdx.x * FB_TPB + threadIdx.x;
-  // interacting particles: lane i < N of a warp is particle i of one ring (M is a multiple
-  // of 32, so warps are whole); every lane of the warp runs the step loop for the shuffles
-  const bool in_range = m < mloc, active = in_range && (!CPL || lane < fp.N);
-  const int left = CPL ? (lane + fp.N - 1) % fp.N : 0, right = CPL ? (lane + 1) % fp.N : 0;
+  // interacting particles: lane i < N of each S-lane ring is particle i (M is a multiple of
+  // S, and of 256 for rings beyond a warp, so rings and blocks are whole); every lane of
+  // the ring runs the step loop for the exchange
+  RingX<R, RING> rx;
+  rx.sv = ringbuf;
+  rx.i = CPL ? (int)(m % fp.S) : 0;
+  rx.N = fp.N;
+  const bool in_range = m < mloc, active = in_range && (!CPL || rx.i < fp.N);
   const uint32_t mg = (uint32_t)(kp.m_begin + m);
   const int Nt = fp.Nt;
   Kahan<R> cost;
   if (in_range) {
     R z[2] = {kp.x0[0], kp.x0[1]};
     if (CPL && active) {
-      z[0] = fp.x0c[lane];
-      z[1] = fp.v0c[lane];
+      z[0] = fp.z0[rx.i];
+      z[1] = fp.z0[fp.S + rx.i];
     }
     uint32_t fw = 0;
     if (STORE && active) {
@@ -377,7 +437,8 @@ fb_fwd_kernel(const __grid_constant__ KParams<R, 2, 1> kp, const __grid_constant
     for (int k = 0; k < Nt; ++k) {
       R cin = R(0);
       if constexpr (CPL) {   // omega (x_{i-1} + x_{i+1}) at t_k, fixed over the step
-        const R xl = __shfl_sync(0xffffffffu, z[0], left), xr = __shfl_sync(0xffffffffu, z[0], right);
+        R xl, xr;
+        rx.get(z[0], xl, xr);
         cin = M::mul(fp.omega, M::add(xl, xr));
         if (!active) continue;
       }
@@ -515,21 +576,28 @@ constexpr size_t fb_adj_smem() {
   return sizeof(R) * (size_t)(FB_TPB / 32) * ((NX / 2) + (NV / 2)) * FB_AROW;
 }
 
-template <typename R, int NX, int NV, bool CPL>
+template <typename R, int NX, int NV, int RING>
 __global__ void __launch_bounds__(FB_TPB)
 fb_adj_kernel(const __grid_constant__ KParams<R, 2, 1> kp, const __grid_constant__ FbParams<R> fp,
               const R *__restrict__ mu, const R *__restrict__ xd, const R *__restrict__ traj,
               const uint32_t *__restrict__ flags, R *__restrict__ partW) {
   using M = Ar<R>;
   constexpr int LP = NX * NV, QPL = fb_qpl<NX, NV>();   // 2 x 2 blocks per lane
+  constexpr bool CPL = RING > 0;
   extern __shared__ __align__(16) unsigned char fb_smem[];
+  __shared__ R ringbuf[RING >= 2 ? 2 * FB_TPB : 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   R *wa = reinterpret_cast<R *>(fb_smem) + warp * ((NX / 2) + (NV / 2)) * FB_AROW;
   R *wb = wa + (NX / 2) * FB_AROW;
   const int64_t mloc = fp.mloc, m = (int64_t)blockIdx.x * FB_TPB + threadIdx.x;
   const int64_t wid = (int64_t)blockIdx.x * (FB_TPB / 32) + warp;
-  const bool active = m < mloc && (!CPL || lane < fp.N);
-  const int left = CPL ? (lane + fp.N - 1) % fp.N : 0, right = CPL ? (lane + 1) % fp.N : 0;
+  RingX<R, RING> rx;
+  rx.sv = ringbuf;
+  rx.i = CPL ? (int)(m % fp.S) : 0;
+  rx.N = fp.N;
+  const bool active = m < mloc && (!CPL || rx.i < fp.N);
+  // lanes of the neighbours (their stored states give the coupling force of each step)
+  const int64_t mleft = CPL ? m - rx.i + rx.left() : m, mright = CPL ? m - rx.i + rx.right() : m;
   const uint32_t mg = (uint32_t)(kp.m_begin + m);
   const int Nt = fp.Nt;
   R a[2] = {R(0), R(0)};
@@ -560,9 +628,13 @@ fb_adj_kernel(const __grid_constant__ KParams<R, 2, 1> kp, const __grid_constant
     FbPlan<R> P;
     R Ys[NMAX + 1][2];   // sub-step start states of a step with jumps (Ys[0] = X_k)
     R cin = R(0);
-    if constexpr (CPL) {   // interacting particles: the neighbours' force of step k
-      const R xl = __shfl_sync(0xffffffffu, zk[0], left), xr = __shfl_sync(0xffffffffu, zk[0], right);
+    if constexpr (RING == 1) {   // interacting particles: the neighbours' force of step k
+      R xl, xr;
+      rx.get(zk[0], xl, xr);
       cin = M::mul(fp.omega, M::add(xl, xr));
+    } else if constexpr (CPL) {   // the same from the neighbours' stored states
+      if (active)
+        cin = M::mul(fp.omega, M::add(traj[((size_t)k * 2) * mloc + mleft], traj[((size_t)k * 2) * mloc + mright]));
     }
     if (active) {
       if ((fk >> (k & 31)) & 1u) {
@@ -624,7 +696,8 @@ fb_adj_kernel(const __grid_constant__ KParams<R, 2, 1> kp, const __grid_constant
       fb_exchange_add<R, NX, NV>(wa, wb, lane, ra, rb, sq);
     }
     if constexpr (CPL) {   // the neighbour force of particle j drove particles j-1 and j+1
-      const R sl = __shfl_sync(0xffffffffu, sn, left), sr = __shfl_sync(0xffffffffu, sn, right);
+      R sl, sr;
+      rx.get(sn, sl, sr);
       if (active) a[0] = M::fma(fp.omega, M::add(sl, sr), a[0]);
     }
     if (active && k >= 1) {
@@ -869,12 +942,9 @@ void fb_make_params(const ::jd_problem *p, const jd_feedback_desc &fb, FbParams<
   fp.iax2 = (R)(fb.track == JD_TRACK_ELLIPSE || fb.particles ? 1.0 / (fb.ax * fb.ax) : 0.0);
   fp.iav2 = (R)(fb.track == JD_TRACK_ELLIPSE || fb.particles ? 1.0 / (fb.av * fb.av) : 0.0);
   fp.N = fb.particles;
+  fp.S = fb.particles ? ring_lanes(fb.particles) : 0;
   fp.omega = (R)fb.omega;
-  for (int i = 0; i < 32; ++i) {   // particles start equidistant on the ellipse (Sec. 6.4)
-    const double th = 2.0 * 3.14159265358979323846 * i / (fb.particles > 0 ? fb.particles : 1);
-    fp.x0c[i] = (R)(fb.particles ? fb.ax * std::cos(th) : 0.0);
-    fp.v0c[i] = (R)(fb.particles ? fb.av * std::sin(th) : 0.0);
-  }
+  fp.z0 = static_cast<const R *>(p->fb_z0);   // the ring's initial states (fb_upload_ring)
   fp.Nt = p->desc.Nt;
   fp.mloc = p->desc.M;
 }
@@ -887,6 +957,37 @@ void fb_make_kparams(const ::jd_problem *p, const jd_feedback_desc &fb, KParams<
   if (fb.particles) kp.A[2] = (R)(p->A[2] - 2.0 * fb.omega);
 }
 
+// Launch of a feedback kernel; a ring of more than 256 lanes (RING 3) runs as one
+// thread-block cluster of S / 256 blocks.
+template <typename... KArgs, typename... Args>
+cudaError_t fb_launch(void (*kern)(KArgs...), int ring, int S, unsigned grid, size_t smem, cudaStream_t s,
+                      Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(FB_TPB);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  if (ring == 3) {
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)(S / FB_TPB);
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+  }
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, args...);
+  count_launch();
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+template <typename R, int NX, int NV, bool STORE, int RING>
+cudaError_t fb_fwd_ring(const KParams<R, 2, 1> &kp, const FbParams<R> &fp, const R *mu, const R *xd, R *traj,
+                        uint32_t *flags, double *partC, unsigned grid, cudaStream_t s) {
+  return fb_launch(fb_fwd_kernel<R, NX, NV, STORE, RING>, RING, fp.S, grid, 0, s, kp, fp, mu, xd, traj, flags,
+                   partC);
+}
+
 template <typename R, int NX, int NV>
 cudaError_t fb_fwd_launch(const ::jd_problem *p, const jd_feedback_desc &fb, bool store, const FbBufs &b,
                           cudaStream_t s) {
@@ -896,20 +997,30 @@ cudaError_t fb_fwd_launch(const ::jd_problem *p, const jd_feedback_desc &fb, boo
   fb_make_params<R>(p, fb, fp);
   const unsigned grid = (unsigned)ceil_div(p->desc.M, FB_TPB);
   const R *mu = static_cast<const R *>(b.mu), *xd = static_cast<const R *>(p->xdk);
-  R *traj = static_cast<R *>(b.traj);
-  if (fb.particles) {
-    if (store)
-      fb_fwd_kernel<R, NX, NV, true, true><<<grid, FB_TPB, 0, s>>>(kp, fp, mu, xd, traj, b.flags, b.partC);
-    else
-      fb_fwd_kernel<R, NX, NV, false, true><<<grid, FB_TPB, 0, s>>>(kp, fp, mu, xd, nullptr, nullptr, b.partC);
-  } else {
-    if (store)
-      fb_fwd_kernel<R, NX, NV, true, false><<<grid, FB_TPB, 0, s>>>(kp, fp, mu, xd, traj, b.flags, b.partC);
-    else
-      fb_fwd_kernel<R, NX, NV, false, false><<<grid, FB_TPB, 0, s>>>(kp, fp, mu, xd, nullptr, nullptr, b.partC);
+  R *traj = store ? static_cast<R *>(b.traj) : nullptr;
+  uint32_t *flags = store ? b.flags : nullptr;
+  switch (ring_kind(fb.particles) * 2 + (store ? 1 : 0)) {
+    case 0: return fb_fwd_ring<R, NX, NV, false, 0>(kp, fp, mu, xd, traj, flags, b.partC, grid, s);
+    case 1: return fb_fwd_ring<R, NX, NV, true, 0>(kp, fp, mu, xd, traj, flags, b.partC, grid, s);
+    case 2: return fb_fwd_ring<R, NX, NV, false, 1>(kp, fp, mu, xd, traj, flags, b.partC, grid, s);
+    case 3: return fb_fwd_ring<R, NX, NV, true, 1>(kp, fp, mu, xd, traj, flags, b.partC, grid, s);
+    case 4: return fb_fwd_ring<R, NX, NV, false, 2>(kp, fp, mu, xd, traj, flags, b.partC, grid, s);
+    case 5: return fb_fwd_ring<R, NX, NV, true, 2>(kp, fp, mu, xd, traj, flags, b.partC, grid, s);
+    case 6: return fb_fwd_ring<R, NX, NV, false, 3>(kp, fp, mu, xd, traj, flags, b.partC, grid, s);
+    default: return fb_fwd_ring<R, NX, NV, true, 3>(kp, fp, mu, xd, traj, flags, b.partC, grid, s);
   }
-  count_launch();
-  return cudaGetLastError();
+}
+
+template <typename R, int NX, int NV, int RING>
+cudaError_t fb_adj_ring(const KParams<R, 2, 1> &kp, const FbParams<R> &fp, const FbBufs &b, const R *xd,
+                        unsigned grid, cudaStream_t s) {
+  constexpr size_t smem = fb_adj_smem<R, NX, NV>();
+  static_assert(smem <= 232448, "fb_adj_kernel shared memory");
+  const cudaError_t e = ensure_dyn_smem((const void *)fb_adj_kernel<R, NX, NV, RING>, smem);
+  if (e != cudaSuccess) return e;
+  return fb_launch(fb_adj_kernel<R, NX, NV, RING>, RING, fp.S, grid, smem, s, kp, fp,
+                   static_cast<const R *>(b.mu), xd, static_cast<const R *>(b.traj),
+                   static_cast<const uint32_t *>(b.flags), static_cast<R *>(b.partW));
 }
 
 // The adjoint sweep (warp partials of the gradient).
@@ -919,16 +1030,14 @@ cudaError_t fb_adj_launch(const ::jd_problem *p, const jd_feedback_desc &fb, con
   fb_make_kparams<R>(p, fb, kp);
   FbParams<R> fp;
   fb_make_params<R>(p, fb, fp);
-  constexpr size_t smem = fb_adj_smem<R, NX, NV>();
-  static_assert(smem <= 232448, "fb_adj_kernel shared memory");
-  auto kern = fb.particles ? fb_adj_kernel<R, NX, NV, true> : fb_adj_kernel<R, NX, NV, false>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
   const unsigned grid = (unsigned)ceil_div(p->desc.M, FB_TPB);
-  kern<<<grid, FB_TPB, smem, s>>>(kp, fp, static_cast<const R *>(b.mu), static_cast<const R *>(p->xdk),
-                                  static_cast<const R *>(b.traj), b.flags, static_cast<R *>(b.partW));
-  count_launch();
-  return cudaGetLastError();
+  const R *xd = static_cast<const R *>(p->xdk);
+  switch (ring_kind(fb.particles)) {
+    case 0: return fb_adj_ring<R, NX, NV, 0>(kp, fp, b, xd, grid, s);
+    case 1: return fb_adj_ring<R, NX, NV, 1>(kp, fp, b, xd, grid, s);
+    case 2: return fb_adj_ring<R, NX, NV, 2>(kp, fp, b, xd, grid, s);
+    default: return fb_adj_ring<R, NX, NV, 3>(kp, fp, b, xd, grid, s);
+  }
 }
 
 // Surrogate gradient (Sec. 6.5): the surrogate adjoint writes bhat, then the forward
@@ -978,11 +1087,12 @@ template <typename R, int NX, int NV>
 size_t fb_stack_bytes() {
   static const size_t bytes = [] {   // the kernels' attributes do not change: ask once
     size_t need = 0;
-    const void *ks[] = {(const void *)fb_fwd_kernel<R, NX, NV, false, false>,
-                        (const void *)fb_fwd_kernel<R, NX, NV, true, false>,
-                        (const void *)fb_fwd_kernel<R, NX, NV, false, true>,
-                        (const void *)fb_fwd_kernel<R, NX, NV, true, true>,
-                        (const void *)fb_adj_kernel<R, NX, NV, false>, (const void *)fb_adj_kernel<R, NX, NV, true>,
+    const void *ks[] = {(const void *)fb_fwd_kernel<R, NX, NV, false, 0>, (const void *)fb_fwd_kernel<R, NX, NV, true, 0>,
+                        (const void *)fb_fwd_kernel<R, NX, NV, false, 1>, (const void *)fb_fwd_kernel<R, NX, NV, true, 1>,
+                        (const void *)fb_fwd_kernel<R, NX, NV, false, 2>, (const void *)fb_fwd_kernel<R, NX, NV, true, 2>,
+                        (const void *)fb_fwd_kernel<R, NX, NV, false, 3>, (const void *)fb_fwd_kernel<R, NX, NV, true, 3>,
+                        (const void *)fb_adj_kernel<R, NX, NV, 0>, (const void *)fb_adj_kernel<R, NX, NV, 1>,
+                        (const void *)fb_adj_kernel<R, NX, NV, 2>, (const void *)fb_adj_kernel<R, NX, NV, 3>,
                         (const void *)fb_sur_adj_kernel<R, NX, NV>, (const void *)fb_fwd_sur_kernel<R, NX, NV>};
     for (const void *k : ks) {
       cudaFuncAttributes a;

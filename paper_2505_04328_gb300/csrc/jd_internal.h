@@ -88,6 +88,21 @@ constexpr int FB_NB = 16;     // largest centre count per axis
 constexpr int FB_GROUP_WARPS = 128;   // warps per group of the first gradient reduction stage
 inline int64_t fb_groups(int64_t nwarp) { return (nwarp + FB_GROUP_WARPS - 1) / FB_GROUP_WARPS; }
 
+// Rings of interacting particles (Sec. 6.4): the exchange kind of a ring of N particles
+// (0: independent paths, 1: one warp, 2: lanes of one block, 3: a thread-block cluster)
+// and its lane count S (particle i of ring r is lane S r + i).
+inline int ring_kind(int N) { return N <= 0 ? 0 : N <= 32 ? 1 : N <= 256 ? 2 : 3; }
+inline int ring_lanes(int N) {
+  if (N <= 32) return 32;
+  if (N <= 256) {
+    int s = 64;
+    while (s < N) s *= 2;
+    return s;
+  }
+  return 256 * ((N + 255) / 256);
+}
+constexpr int RING_MAX = 2048;   // 8 blocks of 256 lanes: the largest portable cluster
+
 struct FbBufs {
   const void *mu = nullptr;     // [Nt][NX/2][NV][2] padded, interleaved weights, kernel precision
   void *traj = nullptr;         // [Nt+1][2][M] states (gradient only)
@@ -202,6 +217,7 @@ struct jd_problem {
   uint32_t *fb_flags = nullptr;
   double *fb_mu64 = nullptr, *fb_grad = nullptr, *fb_partC = nullptr, *fb_partG = nullptr;
   void *fb_partW = nullptr;
+  void *fb_z0 = nullptr;     // interacting particles: the ring's initial states [2][S], kernel precision
   double *fb_mut = nullptr;  // optimizer: trial weights (FP64)
   int fb_LP = 0;             // padded weights per step of fb_mu / fb_partW / fb_partG
   size_t fb_stack = 0;       // stack limit already ensured for the feedback kernels

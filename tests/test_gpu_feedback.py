@@ -176,12 +176,16 @@ def test_surrogate_gradient_parity(case, prec):
         assert eJ <= 1e-6 and eg <= 1e-5
 
 
-@pytest.mark.parametrize("N", [5, 32])
+@pytest.mark.parametrize("N", [5, 32, 33, 256, 2000])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_coupled_particles_parity(N, prec):
-    """Sec. 6.4: rings of N coupled particles (one warp per ring, neighbours by shuffles),
-    ellipse tracking cost, shared weights; against the oracle's ring."""
-    p, fb = workloads.feedback_coupled(M=32 * 37, Nt=30, particles=N)
+    """Sec. 6.4: rings of N coupled particles, ellipse tracking cost, shared weights;
+    against the oracle's rings.  N <= 32: one warp per ring (shuffles); N <= 256: rings
+    within a block (shared memory); N > 256: a ring per thread-block cluster (distributed
+    shared memory)."""
+    S = oracle.ring_lanes(N)
+    R = {32: 37, 64: 12, 256: 5, 2048: 3}[S]   # rings (whole blocks beyond one warp)
+    p, fb = workloads.feedback_coupled(M=S * R, Nt=30, particles=N)
     p = p.replace(lam=5.0)
     mu = workloads.random_mu(p, fb, seed=27, scale=0.6)
     Jo, go = oracle.fb_coupled_gradient(p, fb, mu)
@@ -197,10 +201,11 @@ def test_coupled_particles_parity(N, prec):
         assert eJ <= 1e-6 and eg <= 1e-5
 
 
-def test_coupled_optimizer_follows_the_oracle():
+@pytest.mark.parametrize("N,R", [(8, 12), (256, 2)])
+def test_coupled_optimizer_follows_the_oracle(N, R):
     """Algorithm 5.4 on the shared weights of the coupled rings (FP64): the oracle's iterate
     sequence, J history within 1e-10."""
-    p, fb = workloads.feedback_coupled(M=32 * 12, Nt=20, particles=8)
+    p, fb = workloads.feedback_coupled(M=oracle.ring_lanes(N) * R, Nt=20, particles=N)
     p = p.replace(lam=4.0)
     muo, ro, ho = oracle.fb_optimize(p, fb, max_iter=5)
     with JdProblem(p, prec="fp64") as jp:
