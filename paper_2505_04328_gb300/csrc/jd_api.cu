@@ -181,27 +181,41 @@ __global__ void unit_sums_kernel(const double *__restrict__ partC, int64_t nblk,
 
 // J = (1/M) sum_i units[i][0] + (nu dt / 2) sum_k |u_k|^2          (eq:discrete_functional)
 // grad[e-1] = nu dt u[e-1] + (1/M) sum_i units[i][e], e >= 1       (eq:definition_Gradient)
-// Sums in unit order with the operations of jd_combine_units (host) one for one, so the
-// device and the host combine give the same bits.
+// Sums over units in unit order; sum_k |u_k|^2 as consecutive chunks of 32 squares, each
+// added by the xor butterfly of one warp (offsets 16, 8, 4, 2, 1; the two lanes of a pair
+// add the same two values, so every lane holds the same sum), the chunk sums added in
+// order.  jd_combine_units (host) performs the same operations one for one, so the device
+// and the host combine give the same bits.
 __global__ void combine_units_kernel(const double *__restrict__ units, int64_t nunits, int ne,
                                      const double *__restrict__ u, int n, double nu_dt, double half_nu_dt,
                                      double invM, double *__restrict__ J, double *__restrict__ grad,
                                      double *__restrict__ bad) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= ne) return;
-  double s = 0.0;
-  for (int64_t i = 0; i < nunits; ++i) s = __dadd_rn(s, units[i * ne + e]);
-  double v;
-  if (e == 0) {
+  if (blockIdx.x == 0 && threadIdx.x < 32) {   // warp 0 of block 0: J
+    const int lane = threadIdx.x;
     double b = 0.0;
-    for (int k = 0; k < n; ++k) b = __dadd_rn(b, __dmul_rn(u[k], u[k]));
-    v = __fma_rn(half_nu_dt, b, __dmul_rn(s, invM));
-    *J = v;
-  } else {
-    v = __fma_rn(nu_dt, u[e - 1], __dmul_rn(s, invM));
-    grad[e - 1] = v;
+    for (int c0 = 0; c0 < n; c0 += 32) {
+      const double x = c0 + lane < n ? u[c0 + lane] : 0.0;
+      double v = __dmul_rn(x, x);
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+      b = __dadd_rn(b, v);
+    }
+    if (lane == 0) {
+      double s = 0.0;
+      for (int64_t i = 0; i < nunits; ++i) s = __dadd_rn(s, units[i * ne]);
+      const double v = __fma_rn(half_nu_dt, b, __dmul_rn(s, invM));
+      *J = v;
+      if (!isfinite(v)) *bad = 1.0;
+    }
   }
-  if (!isfinite(v)) *bad = 1.0;
+  if (e >= 1 && e < ne) {
+    double s = 0.0;
+    for (int64_t i = 0; i < nunits; ++i) s = __dadd_rn(s, units[i * ne + e]);
+    const double v = __fma_rn(nu_dt, u[e - 1], __dmul_rn(s, invM));
+    grad[e - 1] = v;
+    if (!isfinite(v)) *bad = 1.0;
+  }
 }
 
 // theta[t] = (1/M) sum_b partT[map(t) * nblk + b], map: [0, 1..d, d+1] -> [0, 1..d, D+1]
@@ -386,9 +400,26 @@ static PathBufs plan_bufs(const jd_problem *p) {
   return b;
 }
 
-static size_t recompute_bytes(const jd_problem *p) {
-  const int nseg = (int)ceil_div(p->desc.Nt, p->ops->S);
-  return (size_t)(nseg + 1) * p->D * p->desc.M * elem_size(p);
+// Checkpoint bytes of the recompute plan with segments of S steps.
+static size_t ckpt_bytes(const jd_problem_desc &q, int D, size_t es, int S) {
+  return (size_t)(ceil_div(q.Nt, S) + 1) * D * (size_t)q.M * es;
+}
+
+static size_t recompute_bytes(const jd_problem *p) { return ckpt_bytes(p->desc, p->D, elem_size(p), p->S); }
+
+// Checkpoint spacing of the recompute plan: 16 steps, or (when the budget does not hold
+// those checkpoints) the smallest of 32 and 64 whose checkpoints fit and whose segment
+// buffer fits a block's shared memory with the parameter gradients (S ~ sqrt(N_t) for
+// N_t near 4096).  0 when none fits.
+static int choose_spacing(const jd_problem *p, size_t avail) {
+  int smax = 0;
+  if (cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device) != cudaSuccess)
+    smax = 232448;
+  for (int S = 16; S <= 64; S *= 2) {
+    if (p->ops->rc_smem && p->ops->rc_smem(true, S) > (size_t)smax && S > 16) break;
+    if (ckpt_bytes(p->desc, p->D, elem_size(p), S) <= avail) return S;
+  }
+  return 0;
 }
 
 // Buffers jd_problem_create allocates (the ALLOC list there).
@@ -438,6 +469,10 @@ static jd_status ensure_plan(jd_problem *p) {
     s = dev_alloc(p, (void **)&p->jcnt, (size_t)M * 8, "jump log counts");
     if (s) return s;
   } else {
+    const size_t avail = p->budget > p->bytes ? p->budget - p->bytes : 0;
+    const int S = choose_spacing(p, avail);
+    if (!S) return fail(JD_ERR_OOM, "the memory budget does not hold the checkpoints of the recompute plan");
+    p->S = S;
     jd_status s = dev_alloc(p, &p->ckpt, recompute_bytes(p), "checkpoints");
     if (s) return s;
   }
@@ -1272,8 +1307,7 @@ size_t jd::pair_bytes(const jd_problem_desc &q, jd_adjoint_mode plan) {
     b += traj_values(q.Nt, D, (int)es, (int64_t)M) * es + capa * M * 2 * es + capa * M * D * es;
   } else {
     const jd::PathOps *ops = path_ops_dims(q.prec, D, DU);
-    const int S = ops ? ops->S : 16;
-    b += (size_t)(ceil_div(q.Nt, S) + 1) * D * M * es;
+    b += ckpt_bytes(q, D, es, ops ? ops->S : 16);
   }
   return b;
 }
@@ -1287,8 +1321,7 @@ size_t jd::problem_bytes(const jd_problem_desc &q, jd_adjoint_mode plan) {
     b += stored_plan_bytes(q, D, es, q.M);
   } else if (plan == JD_ADJ_RECOMPUTE) {
     const jd::PathOps *ops = path_ops_dims(q.prec, D, DU);
-    const int S = ops ? ops->S : 16;
-    b += (size_t)(ceil_div(q.Nt, S) + 1) * D * q.M * es;
+    b += ckpt_bytes(q, D, es, ops ? ops->S : 16);
   }
   return b;
 }
@@ -1390,10 +1423,21 @@ jd_status jd_combine_units(int64_t M_total, int Nt, int du, double T, double nu,
     for (int64_t i = 0; i < nunits; ++i) s = s + units[i * ne + e];
     double v;
     if (e == 0) {
+      // chunks of 32 squares, each by the xor butterfly of combine_units_kernel
+      const int n = Nt * du;
       double b = 0.0;
-      for (int k = 0; k < Nt * du; ++k) {
-        const double sq = u[k] * u[k];
-        b = b + sq;
+      for (int c0 = 0; c0 < n; c0 += 32) {
+        double w[32];
+        for (int l = 0; l < 32; ++l) {
+          const double x = c0 + l < n ? u[c0 + l] : 0.0;
+          w[l] = x * x;
+        }
+        for (int o = 16; o >= 1; o >>= 1) {
+          double t[32];
+          for (int l = 0; l < 32; ++l) t[l] = w[l] + w[l ^ o];
+          for (int l = 0; l < 32; ++l) w[l] = t[l];
+        }
+        b = b + w[0];
       }
       const double sm = s * invM;
       v = std::fma(half_nu_dt, b, sm);

@@ -78,6 +78,9 @@ struct PathOps {
   // theta partials [D+2][nblk]
   cudaError_t (*adj)(const struct ::jd_problem *p, int variant, bool theta, int64_t m_begin,
                      int64_t mloc, const void *uk, const PathBufs &b, cudaStream_t s);
+  // shared memory per block of the recompute adjoint for segments of S steps (null: no
+  // recompute plan)
+  size_t (*rc_smem)(bool theta, int S);
 };
 
 const PathOps *path_ops_dims(int prec, int D, int DU);
@@ -181,6 +184,7 @@ struct jd_problem {
   int device = 0;
   size_t budget = 0;
   jd_adjoint_mode plan = JD_ADJ_AUTO;
+  int S = 16;                // recompute plan: steps per checkpoint segment (16, 32 or 64)
   bool fwd_valid = false;   // stored states / checkpoints belong to u_in (jd_forward)
   // device buffers
   void *uk = nullptr;        // kernel-precision padded control, Nt*DU

@@ -245,7 +245,8 @@ struct LogReader2 {
 
 struct NoLog {};
 
-// Recompute variant: steps per checkpoint segment.
+// Recompute variant: the preferred steps per checkpoint segment (the plan widens it to
+// 32 or 64 when the memory budget does not hold the checkpoints; KParams::S).
 template <int D>
 __host__ __device__ constexpr int seg_len() {
   return D <= 8 ? 16 : 8;
@@ -998,11 +999,11 @@ fwd_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u
       if constexpr (PAIR) stage_state<R, D>(p2.traj, k, Nt, mloc, lm, active, x2, sb2);
     }
     if (k == Nt) break;
-    if (MODE == FWD_CKPT && active && (k % seg_len<D>()) == 0) {   // S is a power of two
+    if (MODE == FWD_CKPT && active && (k & (kp.S - 1)) == 0) {   // S is a power of two
 #pragma unroll
       for (int c = 0; c < D; ++c) {
-        ckpt[((size_t)(k / seg_len<D>()) * D + c) * mloc + lm] = x[c];
-        if constexpr (PAIR) p2.ckpt[((size_t)(k / seg_len<D>()) * D + c) * mloc + lm] = x2[c];
+        ckpt[((size_t)(k / kp.S) * D + c) * mloc + lm] = x[c];
+        if constexpr (PAIR) p2.ckpt[((size_t)(k / kp.S) * D + c) * mloc + lm] = x2[c];
       }
     }
     int nj;
@@ -1025,7 +1026,7 @@ fwd_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u
     }
   }
   if (MODE == FWD_CKPT && active) {
-    const int nseg = (Nt + seg_len<D>() - 1) / seg_len<D>();
+    const int nseg = (Nt + kp.S - 1) / kp.S;
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       ckpt[((size_t)nseg * D + c) * mloc + lm] = x[c];
@@ -1381,7 +1382,7 @@ adj_recompute_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__re
     R x[D];
 #pragma unroll
     for (int c = 0; c < D; ++c) x[c] = __ldg(ckpt + ((size_t)seg * D + c) * mloc + lmc);
-    uint32_t jm = 0;
+    uint64_t jm = 0;   // bit i: step k0 + i had a jump (S <= 64)
     LWR lw;
     if constexpr (!THETA) {
       lw.L = sl;
@@ -1393,7 +1394,7 @@ adj_recompute_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__re
       for (int c = 0; c < D; ++c) sbuf[(i * D + c) * TPB + tid] = x[c];
       if (forward_step<R, D, DU, LWR, ZBUF, !THETA>(kp, k0 + i, m, u, x, lw, zbuf + (size_t)i * D * TPB + tid,
                                                     TPB))
-        jm |= 1u << i;
+        jm |= 1ull << i;
     }
     LogReader2<R, D> lr;
     int kovf = 0;
@@ -1522,7 +1523,7 @@ void make_kparams(const jd_problem *p, int64_t m_begin, int64_t mloc, KParams<R,
   kp.jump_law = (int)q.jump_law;
   kp.jumps_on = q.jump_law != JD_JUMP_NONE && q.lambda > 0.0;
   kp.has_dA = !p->dA.empty();
-  kp.S = seg_len<D>();
+  kp.S = p->S;   // checkpoint spacing of the recompute plan (a power of two, 16 .. 64)
   kp.nblk = (int)ceil_div(mloc, TPB);
   kp.m_begin = q.m_offset + m_begin;   // global path index (a shard starts at m_offset)
   kp.npart = grad_parts(mloc);
@@ -1576,9 +1577,10 @@ cudaError_t op_fwd(const jd_problem *p, int mode, int64_t m_begin, int64_t mloc,
   return cudaGetLastError();
 }
 
+// Shared memory of the recompute adjoint for segments of S steps.
 template <typename R, int D, int DU>
-constexpr size_t recompute_smem(bool theta) {
-  return (size_t)seg_len<D>() * D * TPB * sizeof(R) * (theta && recompute_zbuf<R, D, true>() ? 2 : 1) +
+size_t recompute_smem(bool theta, int S) {
+  return (size_t)S * D * TPB * sizeof(R) * (theta && recompute_zbuf<R, D, true>() ? 2 : 1) +
          (theta ? 0 : (size_t)seg_log_cap<D>() * (2 + D) * TPB * sizeof(R)) + grad_rows_bytes<R, DU, 8>();
 }
 
@@ -1633,7 +1635,7 @@ cudaError_t op_adj(const jd_problem *p, int variant, bool theta, int64_t m_begin
                                                                    b.partT, nullptr, mloc);
     }
   } else {
-    const size_t smem = recompute_smem<R, D, DU>(theta);
+    const size_t smem = recompute_smem<R, D, DU>(theta, kp.S);
     const R *ck = static_cast<const R *>(b.ckpt);
     if (theta) {
       err = ensure_dyn_smem((const void *)adj_recompute_kernel<R, D, DU, true>, smem);
@@ -1678,7 +1680,7 @@ size_t op_stack_bytes() {
 template <typename R, int D, int DU>
 constexpr PathOps make_ops() {
   return PathOps{D, DU, seg_len<D>(), (int)sizeof(R), 0, &op_stack_bytes<R, D, DU>, &op_fwd<R, D, DU>,
-                 &op_adj<R, D, DU>};
+                 &op_adj<R, D, DU>, &recompute_smem<R, D, DU>};
 }
 
 }  // namespace jd
