@@ -397,6 +397,8 @@ static PathBufs plan_bufs(const jd_problem *p) {
   b.partG = p->partG;
   b.partT = p->partT;
   b.status = reinterpret_cast<int *>(p->scal_d + S_STATUS);
+  b.pre_w = p->pre_w;
+  b.pre_z = p->pre_z;
   return b;
 }
 
@@ -428,6 +430,7 @@ static size_t base_bytes(const jd_problem_desc &q, int D, int DU, size_t es) {
   return (size_t)q.Nt * DU * es + (size_t)(q.Nt + 1) * D * es + 4 * nu * 8 + NSCAL * 8 + nblk * 8 +
          (size_t)q.Nt * DU * grad_parts(q.M) * 8 + (size_t)(D + 2) * nblk * 8 +
          (size_t)ceil_div(q.M, JD_UNIT_PATHS) * (1 + nu) * 8 +
+         (pre_pass(q.d, q.Nt, q.M, es) ? pre_bytes(q.Nt, D, q.M, es) : 0) +
          (D == 32 ? 16384 + (size_t)q.Nt * 32 * sizeof(float) : 0);
 }
 
@@ -1116,6 +1119,8 @@ jd_status jd_problem_destroy(jd_problem *p) {
   free_dev(p, p->partC);
   free_dev(p, p->partG);
   free_dev(p, p->units);
+  free_dev(p, p->pre_w);
+  free_dev(p, p->pre_z);
   free_dev(p, p->partT);
   free_dev(p, p->traj);
   free_dev(p, p->flags);
@@ -1255,6 +1260,10 @@ jd_status jd::create_problem(const jd_problem_desc &q, const jd::ProblemOpts &op
   ALLOC(p->partG, (size_t)q.Nt * p->DU * grad_parts(q.M) * 8, "gradient partials");
   ALLOC(p->partT, (size_t)(p->D + 2) * p->nblk * 8, "parameter partials");
   ALLOC(p->units, (size_t)n_units(q.M) * (1 + nu) * 8, "unit sums");
+  if (pre_pass(q.d, q.Nt, q.M, es)) {   // a small problem: the draws' pre-pass buffers
+    ALLOC(p->pre_w, (size_t)q.Nt * q.M * 4, "pre-drawn Poisson words");
+    ALLOC(p->pre_z, (size_t)q.Nt * (1 + 3 * p->D) * q.M * es, "pre-drawn normals and slot draws");
+  }
   ALLOC(p->opt_u, nu * 8, "optimizer iterate");
   ALLOC(p->opt_ut, nu * 8, "optimizer trial");
   if (p->D == 32) {

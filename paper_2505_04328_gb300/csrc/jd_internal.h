@@ -58,6 +58,12 @@ struct PathBufs {
   const void *uk2 = nullptr;
   void *traj2 = nullptr, *ckpt2 = nullptr, *log_kt2 = nullptr, *log_y2 = nullptr;
   double *partC2 = nullptr;
+  // main-stream draws of every (step, path) taken by a parallel pre-pass (small problems,
+  // whose sweeps are latency-bound): pre_w [Nt][mloc] Poisson words, pre_z [Nt][D][mloc]
+  // normals followed by [Nt][1 + 2D][mloc] slot-0 draws, in kernel precision; null = the
+  // sweep draws them itself
+  uint32_t *pre_w = nullptr;
+  void *pre_z = nullptr;
   // partial-stride override: a launch that covers one block of the paths (chunked
   // stored plan) writes its partials at their global positions (partG, partC offset
   // by the caller) with the stride of all M paths; 0 = this launch's own count
@@ -105,6 +111,20 @@ inline int ring_lanes(int N) {
   return 256 * ((N + 255) / 256);
 }
 constexpr int RING_MAX = 2048;   // 8 blocks of 256 lanes: the largest portable cluster
+
+// Draw pre-pass: a problem with d <= 2 whose paths fill at most 2 blocks per SM of a
+// GB300 (its sweeps are latency-bound: each thread's steps are a chain of dependent
+// operations, and the Philox and Box-Muller of every step sit on that chain) takes its
+// main-stream draws in one parallel kernel first, when their buffers stay small.
+constexpr int64_t PRE_MAX_PATHS = 152 * 2 * 128;
+constexpr size_t PRE_MAX_BYTES = (size_t)128 << 20;
+inline size_t pre_bytes(int Nt, int D, int64_t M, size_t es) {
+  return (size_t)Nt * (size_t)M * (4 + (1 + 3 * D) * es);   // words, normals, slot-0 draws
+}
+inline bool pre_pass(int d, int Nt, int64_t M, size_t es) {
+  const int D = d <= 1 ? 1 : 2;
+  return d <= 2 && M <= PRE_MAX_PATHS && pre_bytes(Nt, D, M, es) <= PRE_MAX_BYTES;
+}
 
 struct FbBufs {
   const void *mu = nullptr;     // [Nt][NX/2][NV][2] padded, interleaved weights, kernel precision
@@ -185,6 +205,8 @@ struct jd_problem {
   size_t budget = 0;
   jd_adjoint_mode plan = JD_ADJ_AUTO;
   int S = 16;                // recompute plan: steps per checkpoint segment (16, 32 or 64)
+  uint32_t *pre_w = nullptr; // draw pre-pass buffers of a small problem (PathBufs::pre_w, pre_z)
+  void *pre_z = nullptr;
   bool fwd_valid = false;   // stored states / checkpoints belong to u_in (jd_forward)
   // device buffers
   void *uk = nullptr;        // kernel-precision padded control, Nt*DU

@@ -425,10 +425,8 @@ __device__ __forceinline__ int forward_step(const KParams<R, D, DU> &kp, int k, 
 // the one of a sweep of its control alone.  Returns the number of jumps.
 template <typename R, int D, int DU, typename LW, typename KH>
 __device__ __forceinline__ int forward_step2(const KParams<R, D, DU> &kp, const KH &kh, int k, uint32_t m,
-                                             const R *__restrict__ u, R (&x)[D], LW &lw,
-                                             const R *__restrict__ u2, R (&x2)[D], LW &lw2) {
-  R z[D];
-  const uint32_t w0 = main_draws(kp, k, m, z);
+                                             uint32_t w0, const R (&z)[D], const R *__restrict__ u, R (&x)[D],
+                                             LW &lw, const R *__restrict__ u2, R (&x2)[D], LW &lw2) {
   R uk[DU], uk2[DU];
 #pragma unroll
   for (int l = 0; l < DU; ++l) {
@@ -949,12 +947,65 @@ __device__ __forceinline__ void stage_state(R *__restrict__ traj, int k, int Nt,
   }
 }
 
-template <typename R, int D, int DU, int MODE, bool PAIR = false>
+// Main-stream draws of every step of every path of a launch, taken in parallel (one thread
+// per (step, path)): the Poisson word w[k][lm] and the normals z[k][c][lm] of main_draws,
+// and for a step with exactly one jump its slot-0 draws s[k][.][lm] (slot0_draws).
+template <typename R, int D, int DU>
+__global__ void __launch_bounds__(256)
+draws_kernel(const __grid_constant__ KParams<R, D, DU> kp, int64_t mloc, uint32_t *__restrict__ w,
+             R *__restrict__ z, R *__restrict__ s) {
+  const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  if (i >= (int64_t)kp.Nt * mloc) return;
+  const int k = (int)(i / mloc);
+  const int64_t lm = i - (int64_t)k * mloc;
+  const uint32_t m = (uint32_t)(kp.m_begin + lm);
+  R zz[D];
+  const uint32_t w0 = main_draws(kp, k, m, zz);
+  w[i] = w0;
+#pragma unroll
+  for (int c = 0; c < D; ++c) z[((int64_t)k * D + c) * mloc + lm] = zz[c];
+  if (has_jump(kp, w0) && one_jump(kp, w0)) {
+    R xih[D], z1[D];
+    R *sk = s + (int64_t)k * (1 + 2 * D) * mloc + lm;
+    sk[0] = slot0_draws(kp, k, m, xih, z1);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      sk[(1 + c) * mloc] = xih[c];
+      sk[(1 + D + c) * mloc] = z1[c];
+    }
+  }
+}
+
+template <typename R, int D>
+struct PreDraws {
+  const uint32_t *w;   // [Nt][mloc] Poisson words
+  const R *z;          // [Nt][D][mloc] sub-step 0 normals
+  const R *s;          // [Nt][1 + 2D][mloc] a step with exactly one (additive) jump: its
+                       // slot-0 draws (time fraction, unit size, next normals); else unset
+};
+
+// A step with one jump, its slot draws pre-drawn: sub-step to the jump, jump, sub-step.
+template <typename R, int D, int DU, typename LW>
+__device__ __forceinline__ void one_jump_pre(const KParams<R, D, DU> &kp, int k, const R *__restrict__ sk,
+                                             int64_t mloc, const R (&z)[D], const R (&uk)[DU], R (&x)[D], LW &lw) {
+  R xih[D], z1[D];
+  const R th = sk[0];
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    xih[c] = sk[(1 + c) * mloc];
+    z1[c] = sk[(1 + D + c) * mloc];
+  }
+  one_jump_inline(kp, k, th, xih, z, z1, uk, x, lw);
+}
+
+// PRE: the main-stream draws come from draws_kernel (PreDraws) instead of the step's own
+// Philox and Box-Muller; the same values, so the same bits.
+template <typename R, int D, int DU, int MODE, bool PAIR = false, bool PRE = false>
 __global__ void __launch_bounds__(TPB)
 fwd_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u,
            const R *__restrict__ xd, double *__restrict__ partC, R *__restrict__ traj,
            uint32_t *__restrict__ flags, R *__restrict__ ckpt, R *__restrict__ pcost,
-           JLog<R, D> jl, int *__restrict__ jcnt, int64_t mloc, PairOut<R, D> p2) {
+           JLog<R, D> jl, int *__restrict__ jcnt, int64_t mloc, PairOut<R, D> p2, PreDraws<R, D> pd = {}) {
   __shared__ Pair<R> red[TPB / 32];
   const int64_t lm = (int64_t)blockIdx.x * TPB + threadIdx.x;
   const bool active = lm < mloc;
@@ -1007,10 +1058,37 @@ fwd_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u
       }
     }
     int nj;
-    if constexpr (PAIR)
-      nj = forward_step2(kp, kh, k, m, u, x, lw, p2.u, x2, lw2);
-    else
+    if constexpr (PRE) {   // inactive threads read path 0's draws
+      const int64_t lmc = active ? lm : 0, ik = (int64_t)k * mloc + lmc;
+      const uint32_t w0 = pd.w[ik];
+      R z[D];
+#pragma unroll
+      for (int c = 0; c < D; ++c) z[c] = pd.z[((int64_t)k * D + c) * mloc + lmc];
+      const R *sk = pd.s + (int64_t)k * (1 + 2 * D) * mloc + lmc;
+      R uk[DU];
+#pragma unroll
+      for (int l = 0; l < DU; ++l) uk[l] = __ldg(u + (size_t)k * DU + l);
+      if (has_jump(kp, w0) && one_jump(kp, w0)) {   // the common jump step, pre-drawn
+        one_jump_pre(kp, k, sk, mloc, z, uk, x, lw);
+        if constexpr (PAIR) {
+          R uk2[DU];
+#pragma unroll
+          for (int l = 0; l < DU; ++l) uk2[l] = __ldg(p2.u + (size_t)k * DU + l);
+          one_jump_pre(kp, k, sk, mloc, z, uk2, x2, lw2);
+        }
+        nj = 1;
+      } else if constexpr (PAIR) {
+        nj = forward_step2(kp, kh, k, m, w0, z, u, x, lw, p2.u, x2, lw2);
+      } else {
+        nj = step_from_draws<R, D, DU, LW, true, KH>(kp, kh, k, m, w0, z, uk, x, lw);
+      }
+    } else if constexpr (PAIR) {
+      R z[D];
+      const uint32_t w0 = main_draws(kp, k, m, z);
+      nj = forward_step2(kp, kh, k, m, w0, z, u, x, lw, p2.u, x2, lw2);
+    } else {
       nj = forward_step_h<R, D, DU, LW, false, true, KH>(kp, kh, k, m, u, x, lw);
+    }
     if (nj) fw |= 1u << (k & 31);
     cost.add(cost_term(kh, x, xd + (size_t)(k + 1) * D));
     if constexpr (PAIR) cost2.add(cost_term(kh, x2, xd + (size_t)(k + 1) * D));
@@ -1545,6 +1623,39 @@ cudaError_t op_fwd(const jd_problem *p, int mode, int64_t m_begin, int64_t mloc,
     p2 = PairOut<R, D>{static_cast<const R *>(b.uk2), b.partC2, static_cast<R *>(b.traj2), static_cast<R *>(b.ckpt2),
                        JLog<R, D>{static_cast<typename V2<R>::T *>(b.log_kt2), static_cast<R *>(b.log_y2), mloc,
                                   b.log_cap}};
+  if constexpr (D <= 2) {
+    if (b.pre_w) {   // a small problem: all main-stream draws in one parallel pass first
+      R *pz = static_cast<R *>(b.pre_z), *ps = pz + (size_t)kp.Nt * D * mloc;
+      draws_kernel<R, D, DU><<<(unsigned)ceil_div((int64_t)kp.Nt * mloc, 256), 256, 0, s>>>(kp, mloc, b.pre_w,
+                                                                                             pz, ps);
+      count_launch();
+      const PreDraws<R, D> pd{b.pre_w, pz, ps};
+      switch (mode) {
+        case FWD_COST:
+          fwd_kernel<R, D, DU, FWD_COST, false, true><<<grid, TPB, 0, s>>>(
+              kp, u, xd, b.partC, nullptr, nullptr, nullptr, pc, jl, nullptr, mloc, p2, pd);
+          break;
+        case FWD_STORE:
+          fwd_kernel<R, D, DU, FWD_STORE, false, true><<<grid, TPB, 0, s>>>(
+              kp, u, xd, b.partC, static_cast<R *>(b.traj), b.flags, nullptr, pc, jl, b.jcnt, mloc, p2, pd);
+          break;
+        case FWD_STORE | FWD_PAIR:
+          fwd_kernel<R, D, DU, FWD_STORE, true, true><<<grid, TPB, 0, s>>>(
+              kp, u, xd, b.partC, static_cast<R *>(b.traj), b.flags, nullptr, nullptr, jl, b.jcnt, mloc, p2, pd);
+          break;
+        case FWD_CKPT | FWD_PAIR:
+          fwd_kernel<R, D, DU, FWD_CKPT, true, true><<<grid, TPB, 0, s>>>(
+              kp, u, xd, b.partC, nullptr, nullptr, static_cast<R *>(b.ckpt), nullptr, jl, nullptr, mloc, p2, pd);
+          break;
+        default:
+          fwd_kernel<R, D, DU, FWD_CKPT, false, true><<<grid, TPB, 0, s>>>(
+              kp, u, xd, b.partC, nullptr, nullptr, static_cast<R *>(b.ckpt), pc, jl, nullptr, mloc, p2, pd);
+          break;
+      }
+      count_launch();
+      return cudaGetLastError();
+    }
+  }
   switch (mode) {
     case FWD_COST:
       fwd_kernel<R, D, DU, FWD_COST><<<grid, TPB, 0, s>>>(kp, u, xd, b.partC, nullptr, nullptr, nullptr, pc,
