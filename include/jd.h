@@ -268,9 +268,15 @@ jd_status jd_problem_footprint(const jd_problem_desc *desc, jd_adjoint_mode plan
  *   a quarter of the budget, else RECOMPUTE (d <= 8).  A request that cannot fit even
  *   an empty server finishes with status OOM; later requests may overtake one that is
  *   waiting for memory.
- * Execution: each request runs jd_optimize's kernels and host decisions on its own
- *   buffers and stream, so its result is bitwise the same as a solo jd_optimize with
- *   u0 = 0, whatever else runs; the kernels of all active requests overlap.
+ * Execution: each request runs jd_optimize's arithmetic and host decisions on its own
+ *   buffers, so its result is bitwise the same as a solo jd_optimize with u0 = 0,
+ *   whatever else runs; the kernels of all active requests overlap.  Large requests run
+ *   on their own stream.  Small ones (d <= 2, du = 1, the stored plan, M at most the
+ *   batching limit) share launches (the paper's Algorithm 5.4 per request, its gradient
+ *   evaluations batched): each optimizer phase of up to 16 such requests with the same
+ *   phase kind, precision and dimension is one launch sequence -- one forward and one
+ *   adjoint sweep over all their paths, one launch per reduction and per optimizer
+ *   step -- in which every problem's blocks compute what its own launches would.
  * jd_server_poll: JD_ERR_BUSY while the request runs; then JD_OK with r (the request's
  *   own status in r->status) and, if u_out is not NULL, the final control (Nt*du host
  *   doubles), which is handed out once (a second poll with u_out fails with INVALID_ARG).
@@ -281,8 +287,14 @@ jd_status jd_problem_footprint(const jd_problem_desc *desc, jd_adjoint_mode plan
  *   path-steps (M*Nt per sweep over the paths actually run: forward sweeps of gradients
  *   and line-search trials, a paired trial counting one, plus the adjoint sweeps).  A request's footprint includes the second buffer set of paired
  *   trials when that keeps it within a quarter of the budget and what is free.
+ * jd_server_set_batching: the batching limit, in paths, for requests admitted after the
+ *   call (default JD_SERVER_BATCH_PATHS; 0 = every request runs its own launches).
+ *   INVALID_ARG for a negative limit.
+ * jd_server_batch_stats: batched launch sequences so far, and the request phases they
+ *   ran (phases / launches = the mean batch size).  Either pointer may be NULL.
  * jd_server_destroy: cancels requests not yet admitted (status INVALID_ARG), waits for
  *   the running ones, frees everything. */
+#define JD_SERVER_BATCH_PATHS 65536
 typedef struct jd_server jd_server;
 typedef struct {
   double submit_s, admit_s, done_s;
@@ -296,6 +308,8 @@ jd_status jd_server_submit(jd_server *s, const jd_problem_desc *d, const jd_opt_
 jd_status jd_server_poll(jd_server *s, uint64_t ticket, double *u_out, jd_opt_result *r);
 jd_status jd_server_wait(jd_server *s, uint64_t ticket, double timeout_s);
 jd_status jd_server_info(jd_server *s, uint64_t ticket, jd_request_info *info);
+jd_status jd_server_set_batching(jd_server *s, int64_t max_paths);
+jd_status jd_server_batch_stats(jd_server *s, int64_t *launches, int64_t *phases);
 jd_status jd_server_destroy(jd_server *s);
 
 /* Number of kernels this library has launched in this process (monotone counter). */

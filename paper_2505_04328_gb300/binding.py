@@ -33,7 +33,8 @@ ABI_SYMBOLS = (
     "jd_profile_read", "jd_cost_noalloc", "jd_problem_footprint", "jd_server_create",
     "jd_server_submit", "jd_server_poll", "jd_server_wait", "jd_server_info", "jd_server_destroy",
     "jd_status_string", "jd_last_error", "jd_fb_cost", "jd_fb_gradient", "jd_fb_optimize",
-    "jd_gradient_units", "jd_cost_units", "jd_combine_units",
+    "jd_gradient_units", "jd_cost_units", "jd_combine_units", "jd_server_set_batching",
+    "jd_server_batch_stats",
 )
 
 UNIT_PATHS = 16384   # JD_UNIT_PATHS: paths per unit of the path reduction (path sharding)
@@ -143,6 +144,8 @@ def lib():
         L.jd_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_double]
         L.jd_server_info.argtypes = [vp, ctypes.c_uint64, P(RequestInfo)]
         L.jd_server_destroy.argtypes = [vp]
+        L.jd_server_set_batching.argtypes = [vp, ctypes.c_int64]
+        L.jd_server_batch_stats.argtypes = [vp, P(ctypes.c_int64), P(ctypes.c_int64)]
         L.jd_kernel_launch_count.restype = ctypes.c_uint64
         L.jd_profile_enable.argtypes = [ctypes.c_int]
         L.jd_profile_enable.restype = None
@@ -492,13 +495,23 @@ class JdServer:
     """The serving loop (jd_server_*): submit problems, poll results.
 
     ``budget``: device bytes for admitted requests (0 = 80% of free memory);
-    ``max_slots``: requests in flight at most."""
+    ``max_slots``: requests in flight at most; ``batch_paths``: small requests (d <= 2,
+    du = 1, stored plan) with at most this many paths share batched launches (None = the
+    library's default, 0 = off)."""
 
-    def __init__(self, budget: int = 0, max_slots: int = 16):
+    def __init__(self, budget: int = 0, max_slots: int = 16, batch_paths=None):
         h = ctypes.c_void_p()
         _check(lib().jd_server_create(int(budget), int(max_slots), ctypes.byref(h)), "jd_server_create")
         self.h = h
         self._shapes = {}
+        if batch_paths is not None:
+            _check(lib().jd_server_set_batching(self.h, int(batch_paths)), "jd_server_set_batching")
+
+    def batch_stats(self):
+        """(batched launch sequences, request phases they ran)."""
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().jd_server_batch_stats(self.h, ctypes.byref(a), ctypes.byref(b)), "jd_server_batch_stats")
+        return a.value, b.value
 
     def submit(self, problem, prec="fp32", mode="auto", use_tensor_cores=0, max_iter=200,
                tol_rel_grad=1e-4, tol_step=0.0, armijo_c=1e-4, zeta0=1.0, zeta_max=1e3,

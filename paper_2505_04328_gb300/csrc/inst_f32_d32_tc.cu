@@ -85,6 +85,7 @@ static size_t op32_stack() {
   return (need + 255) & ~(size_t)255;
 }
 
-extern const PathOps ops_f32_d32_u4 = PathOps{D32, DU32, 8, 4, 1, &op32_stack, &op32_fwd, &op32_adj, nullptr};
+extern const PathOps ops_f32_d32_u4 = PathOps{D32, DU32, 8, 4, 1, &op32_stack, &op32_fwd, &op32_adj, nullptr,
+                                                    nullptr, nullptr};
 
 }  // namespace jd

@@ -158,9 +158,11 @@ inline int64_t n_units(int64_t M) { return ceil_div(M, UNIT_PATHS); }
 // units[i][e], e < ne: e = 0 the sum of unit i's cost partials (its blocks), e = 1 + k du + l
 // the sum of its gradient partials of entry (k, l) (its warps).  One warp per (unit,
 // entry): lane j adds partials j, j + 32, ... in order, then the warp's fixed tree.
-__global__ void unit_sums_kernel(const double *__restrict__ partC, int64_t nblk, const double *__restrict__ partG,
-                                 int64_t npart, int du, int DU, int64_t nunits, int ne, double *__restrict__ units) {
-  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// bid: the block's index within this reduction (a batched launch runs several).
+__device__ __forceinline__ void unit_sums_body(int64_t bid, const double *__restrict__ partC, int64_t nblk,
+                                               const double *__restrict__ partG, int64_t npart, int du, int DU,
+                                               int64_t nunits, int ne, double *__restrict__ units) {
+  const int64_t gw = (bid * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (gw >= nunits * ne) return;   // whole warps (blockDim is a multiple of 32)
   const int64_t i = gw / ne;
@@ -179,6 +181,11 @@ __global__ void unit_sums_kernel(const double *__restrict__ partC, int64_t nblk,
   if (lane == 0) units[gw] = s;
 }
 
+__global__ void unit_sums_kernel(const double *__restrict__ partC, int64_t nblk, const double *__restrict__ partG,
+                                 int64_t npart, int du, int DU, int64_t nunits, int ne, double *__restrict__ units) {
+  unit_sums_body(blockIdx.x, partC, nblk, partG, npart, du, DU, nunits, ne, units);
+}
+
 // J = (1/M) sum_i units[i][0] + (nu dt / 2) sum_k |u_k|^2          (eq:discrete_functional)
 // grad[e-1] = nu dt u[e-1] + (1/M) sum_i units[i][e], e >= 1       (eq:definition_Gradient)
 // Sums over units in unit order; sum_k |u_k|^2 as consecutive chunks of 32 squares, each
@@ -186,12 +193,12 @@ __global__ void unit_sums_kernel(const double *__restrict__ partC, int64_t nblk,
 // add the same two values, so every lane holds the same sum), the chunk sums added in
 // order.  jd_combine_units (host) performs the same operations one for one, so the device
 // and the host combine give the same bits.
-__global__ void combine_units_kernel(const double *__restrict__ units, int64_t nunits, int ne,
-                                     const double *__restrict__ u, int n, double nu_dt, double half_nu_dt,
-                                     double invM, double *__restrict__ J, double *__restrict__ grad,
-                                     double *__restrict__ bad) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (blockIdx.x == 0 && threadIdx.x < 32) {   // warp 0 of block 0: J
+__device__ __forceinline__ void combine_units_body(int bid, const double *__restrict__ units, int64_t nunits, int ne,
+                                                   const double *__restrict__ u, int n, double nu_dt,
+                                                   double half_nu_dt, double invM, double *__restrict__ J,
+                                                   double *__restrict__ grad, double *__restrict__ bad) {
+  const int e = bid * blockDim.x + threadIdx.x;
+  if (bid == 0 && threadIdx.x < 32) {   // warp 0 of block 0: J
     const int lane = threadIdx.x;
     double b = 0.0;
     for (int c0 = 0; c0 < n; c0 += 32) {
@@ -218,6 +225,13 @@ __global__ void combine_units_kernel(const double *__restrict__ units, int64_t n
   }
 }
 
+__global__ void combine_units_kernel(const double *__restrict__ units, int64_t nunits, int ne,
+                                     const double *__restrict__ u, int n, double nu_dt, double half_nu_dt,
+                                     double invM, double *__restrict__ J, double *__restrict__ grad,
+                                     double *__restrict__ bad) {
+  combine_units_body(blockIdx.x, units, nunits, ne, u, n, nu_dt, half_nu_dt, invM, J, grad, bad);
+}
+
 // theta[t] = (1/M) sum_b partT[map(t) * nblk + b], map: [0, 1..d, d+1] -> [0, 1..d, D+1]
 __global__ void finalize_theta_kernel(const double *__restrict__ partT, int64_t nblk, int d, int D,
                                       double invM, double *__restrict__ out) {
@@ -238,10 +252,23 @@ __global__ void prep_u_kernel(const double *__restrict__ u, int Nt, int du, int 
   uk[i] = l < du ? (R)u[(int64_t)k * du + l] : R(0);
 }
 
+// The optimizer's one-block kernels below are bodies (blockDim.x == 256, sm: 32 doubles
+// of shared memory) run by their own launch or, one block per problem, by a batched one.
+
+// Control in kernel precision, one block: the elements of prep_u_kernel in a loop.
+template <typename R>
+__device__ __forceinline__ void prep_u_block(const double *__restrict__ u, int Nt, int du, int DU,
+                                             R *__restrict__ uk) {
+  for (int64_t i = threadIdx.x; i < (int64_t)Nt * DU; i += blockDim.x) {
+    const int k = (int)(i / DU), l = (int)(i % DU);
+    uk[i] = l < du ? (R)u[(int64_t)k * du + l] : R(0);
+  }
+}
+
 // |P(u - g) - u|_{L2} with g = grad / dt; out = value.
-__global__ void opt_pgnorm_kernel(int n, const double *__restrict__ u, const double *__restrict__ grad,
-                                  double dt, double lo, double hi, double *__restrict__ out) {
-  __shared__ double sm[32];
+__device__ __forceinline__ void opt_pgnorm_body(int n, const double *__restrict__ u, const double *__restrict__ grad,
+                                                double dt, double lo, double hi, double *__restrict__ out,
+                                                double *sm) {
   double a = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const double g = grad[i] / dt;
@@ -252,14 +279,18 @@ __global__ void opt_pgnorm_kernel(int n, const double *__restrict__ u, const dou
   if (threadIdx.x == 0) *out = sqrt(a);
 }
 
+__global__ void opt_pgnorm_kernel(int n, const double *__restrict__ u, const double *__restrict__ grad,
+                                  double dt, double lo, double hi, double *__restrict__ out) {
+  __shared__ double sm[32];
+  opt_pgnorm_body(n, u, grad, dt, lo, hi, out, sm);
+}
+
 // Trial point ut = clip(u - zeta g) and <g, ut - u>_{L2} = sum grad (ut - u); with ut2
 // also the point at zeta / 2 (the second trial of a pair) and its product in dot2.
-__global__ void opt_trial_kernel(int n, const double *__restrict__ u, const double *__restrict__ grad,
-                                 const double *__restrict__ zeta_p, double dt, double lo, double hi,
-                                 double *__restrict__ ut, double *__restrict__ dot, double *__restrict__ ut2,
-                                 double *__restrict__ dot2) {
-  __shared__ double sm[32];
-  const double zeta = *zeta_p;
+__device__ __forceinline__ void opt_trial_body(int n, const double *__restrict__ u, const double *__restrict__ grad,
+                                               double zeta, double dt, double lo, double hi,
+                                               double *__restrict__ ut, double *__restrict__ dot,
+                                               double *__restrict__ ut2, double *__restrict__ dot2, double *sm) {
   for (int h = 0; h < (ut2 ? 2 : 1); ++h) {
     const double z = h ? 0.5 * zeta : zeta;
     double *w = h ? ut2 : ut;
@@ -275,15 +306,23 @@ __global__ void opt_trial_kernel(int n, const double *__restrict__ u, const doub
   }
 }
 
+__global__ void opt_trial_kernel(int n, const double *__restrict__ u, const double *__restrict__ grad,
+                                 const double *__restrict__ zeta_p, double dt, double lo, double hi,
+                                 double *__restrict__ ut, double *__restrict__ dot, double *__restrict__ ut2,
+                                 double *__restrict__ dot2) {
+  __shared__ double sm[32];
+  opt_trial_body(n, u, grad, *zeta_p, dt, lo, hi, ut, dot, ut2, dot2, sm);
+}
+
 // Armijo test J(ut) <= J(u) + c <g, ut - u>; on acceptance u <- ut and J <- J(ut).
 // s: [0] J(u), [1] J(ut), [2] dot, [4] accepted (out), [5] |ut - u|^2_{L2} (out).
 // With ut2 (a pair of trials, ut2 at half the step, J(ut2) and its product in
 // s[S_JT2], s[S_DOT2]) the points are tested in the order of backtracking and the first
 // that passes is taken: s[4] = 1 (ut), 2 (ut2) or 0, s[5] the squared step of the taken
 // point (of ut2 when neither passes).
-__global__ void opt_accept_kernel(int n, double *__restrict__ u, const double *__restrict__ ut,
-                                  const double *__restrict__ ut2, double c, double dt, double *__restrict__ s) {
-  __shared__ double sm[32];
+__device__ __forceinline__ void opt_accept_body(int n, double *__restrict__ u, const double *__restrict__ ut,
+                                                const double *__restrict__ ut2, double c, double dt,
+                                                double *__restrict__ s, double *sm) {
   const bool acc1 = s[1] <= s[0] + c * s[2];
   const bool acc2 = ut2 && !acc1 && s[S_JT2] <= s[0] + c * s[S_DOT2];
   const double *w = (ut2 && !acc1) ? ut2 : ut;
@@ -302,6 +341,108 @@ __global__ void opt_accept_kernel(int n, double *__restrict__ u, const double *_
     if (acc1) s[0] = s[1];
     if (acc2) s[0] = s[1] = s[S_JT2];
   }
+}
+
+__global__ void opt_accept_kernel(int n, double *__restrict__ u, const double *__restrict__ ut,
+                                  const double *__restrict__ ut2, double c, double dt, double *__restrict__ s) {
+  __shared__ double sm[32];
+  opt_accept_body(n, u, ut, ut2, c, dt, s, sm);
+}
+
+// ---------------------------------------------------------------------------
+// Batched optimizer phases: several problems' phase work in shared launches, one block
+// (small kernels) or one range of blocks (reductions, sweeps) per problem.  Each block
+// runs the body of the single-problem kernel with its index within its problem, so every
+// problem gets the bits of its own launches.
+// ---------------------------------------------------------------------------
+struct OptBatchItem {
+  int n, Nt, du, DU;
+  int fwd;                        // gradient phase with its forward sweep: the control into uk
+  double dt, lo, hi, c, zeta;
+  double *u, *grad, *ut, *ut2;    // ut2: the second point of a paired trial (else null)
+  double *scal;
+  void *uk, *uk2;
+};
+struct OptBatch {
+  int n;
+  OptBatchItem it[kBatchMax];
+};
+
+// Gradient phase, before the sweeps: clear the status word and the non-finite flag (the
+// bytes of clear_bad's memset); with the forward sweep, the control in kernel precision.
+template <typename R>
+__global__ void opt_grad_pre_batch_kernel(const __grid_constant__ OptBatch t) {
+  const OptBatchItem &b = t.it[blockIdx.x];
+  if (threadIdx.x < 2) b.scal[S_STATUS + threadIdx.x] = 0.0;
+  if (b.fwd) prep_u_block<R>(b.u, b.Nt, b.du, b.DU, static_cast<R *>(b.uk));
+}
+
+// Trial phase, before the sweep: the trial point(s) and their products (opt_trial at the
+// machine's zeta), then the point(s) in kernel precision.
+template <typename R>
+__global__ void opt_trial_pre_batch_kernel(const __grid_constant__ OptBatch t) {
+  __shared__ double sm[32];
+  const OptBatchItem &b = t.it[blockIdx.x];
+  if (threadIdx.x == 0) b.scal[S_ZETA] = b.zeta;
+  opt_trial_body(b.n, b.u, b.grad, b.zeta, b.dt, b.lo, b.hi, b.ut, b.scal + S_DOT, b.ut2, b.scal + S_DOT2, sm);
+  __syncthreads();
+  prep_u_block<R>(b.ut, b.Nt, b.du, b.DU, static_cast<R *>(b.uk));
+  if (b.ut2) prep_u_block<R>(b.ut2, b.Nt, b.du, b.DU, static_cast<R *>(b.uk2));
+}
+
+__global__ void opt_grad_post_batch_kernel(const __grid_constant__ OptBatch t) {
+  __shared__ double sm[32];
+  const OptBatchItem &b = t.it[blockIdx.x];
+  opt_pgnorm_body(b.n, b.u, b.grad, b.dt, b.lo, b.hi, b.scal + S_PG, sm);
+}
+
+__global__ void opt_trial_post_batch_kernel(const __grid_constant__ OptBatch t) {
+  __shared__ double sm[32];
+  const OptBatchItem &b = t.it[blockIdx.x];
+  opt_accept_body(b.n, b.u, b.ut, b.ut2, b.c, b.dt, b.scal, sm);
+}
+
+// The job of a block of a batched reduction: first[i] <= blockIdx.x < first[i + 1].
+__device__ __forceinline__ int batch_job(const int *first, int n) {
+  int i = 0;
+  while (i + 1 < n && (int)blockIdx.x >= first[i + 1]) ++i;
+  return i;
+}
+
+struct UnitJob {
+  const double *partC, *partG;
+  int64_t nblk, npart, nunits;
+  int du, DU, ne;
+  double *units;
+};
+struct UnitBatch {
+  int n;
+  int first[2 * kBatchMax + 1];
+  UnitJob j[2 * kBatchMax];
+};
+__global__ void unit_sums_batch_kernel(const __grid_constant__ UnitBatch t) {
+  const int i = batch_job(t.first, t.n);
+  const UnitJob &j = t.j[i];
+  unit_sums_body(blockIdx.x - t.first[i], j.partC, j.nblk, j.partG, j.npart, j.du, j.DU, j.nunits, j.ne, j.units);
+}
+
+struct CombineJob {
+  const double *units, *u;
+  int64_t nunits;
+  int ne, n;
+  double nu_dt, half_nu_dt, invM;
+  double *J, *grad, *bad;
+};
+struct CombineBatch {
+  int n;
+  int first[2 * kBatchMax + 1];
+  CombineJob j[2 * kBatchMax];
+};
+__global__ void combine_units_batch_kernel(const __grid_constant__ CombineBatch t) {
+  const int i = batch_job(t.first, t.n);
+  const CombineJob &j = t.j[i];
+  combine_units_body(blockIdx.x - t.first[i], j.units, j.nunits, j.ne, j.u, j.n, j.nu_dt, j.half_nu_dt, j.invM,
+                     j.J, j.grad, j.bad);
 }
 
 }  // namespace jd
@@ -899,9 +1040,14 @@ static jd_status launch_grad(jd::OptMachine &m) {
   const int v = m.forward_done ? 1 : 0;
   jd_problem *p = m.p;
   if (m.o.resample) p->desc.epoch = m.epoch0 + (uint32_t)m.it;   // fresh sample per iteration
-  const jd_status s =
-      run_phase(m, &m.g_grad[m.bank][v], &m.n_grad[m.bank][v], [&]() { return enqueue_grad(p, v == 1); });
-  if (s) return s;
+  if (m.defer) {   // opt_launch_batch runs the work
+    m.want = jd::OptMachine::GRAD;
+    m.want_fwd = v == 0;
+  } else {
+    const jd_status s =
+        run_phase(m, &m.g_grad[m.bank][v], &m.n_grad[m.bank][v], [&]() { return enqueue_grad(p, v == 1); });
+    if (s) return s;
+  }
   m.forward_done = false;
   m.r.evals++;
   if (v == 0) m.r.sweeps++;
@@ -924,9 +1070,14 @@ static jd_status launch_trial(jd::OptMachine &m) {
   m.pair = m.pairs && want && m.backtracks + 1 <= m.o.max_backtracks && ensure_pair(p);
   const bool pair = m.pair;
   const int v = pair ? 1 : 0;
-  const jd_status s =
-      run_phase(m, &m.g_trial[m.bank][v], &m.n_trial[m.bank][v], [&]() { return enqueue_trial(p, c, pair); });
-  if (s) return s;
+  if (m.defer) {   // opt_launch_batch runs the work
+    m.want = jd::OptMachine::TRIAL;
+    m.want_pair = pair;
+  } else {
+    const jd_status s =
+        run_phase(m, &m.g_trial[m.bank][v], &m.n_trial[m.bank][v], [&]() { return enqueue_trial(p, c, pair); });
+    if (s) return s;
+  }
   m.r.evals++;
   m.r.sweeps++;
   m.phase = jd::OptMachine::TRIAL;
@@ -1048,6 +1199,149 @@ jd_status jd::opt_advance(OptMachine &m) {
     default:
       return fail(JD_ERR_INVALID_ARG, "optimizer machine is not running");
   }
+}
+
+bool jd::opt_batchable(jd_problem *p) {
+  if (ensure_plan(p)) return false;
+  return p->ops->fwd_batch && p->ops->adj_batch && p->desc.du == 1 && p->D <= 2 && p->plan == JD_ADJ_STORED &&
+         !p->chunk;
+}
+
+int jd::opt_batch_key(const OptMachine &m) {
+  if (m.want == OptMachine::IDLE) return -1;
+  const int kind = m.want == OptMachine::GRAD ? (m.want_fwd ? 0 : 1) : (m.want_pair ? 3 : 2);
+  return kind + 4 * (m.p->D + 4 * (m.p->desc.prec == JD_FP64 ? 1 : 0));
+}
+
+// The deferred phases of machines with one batch key: the work of enqueue_grad or
+// enqueue_trial for each, in shared launches (optimizer bodies one block per problem,
+// sweeps and reductions over the blocks of all problems), then each machine's scalars to
+// its pinned buffer and its event.
+jd_status jd::opt_launch_batch(OptMachine *const *ms, int n, cudaStream_t st) {
+  if (n < 1 || n > kBatchMax) return fail(JD_ERR_INVALID_ARG, "batch size");
+  const int key = opt_batch_key(*ms[0]);
+  const OptMachine::Phase kind = ms[0]->want;
+  const bool fwd = ms[0]->want_fwd, pair = ms[0]->want_pair;
+  const PathOps *ops = ms[0]->p->ops;
+  for (int i = 0; i < n; ++i) {
+    OptMachine &m = *ms[i];
+    jd_problem *p = m.p;
+    if (opt_batch_key(m) != key || p->ops != ops) return fail(JD_ERR_INVALID_ARG, "mixed batch");
+    jd_status s = ensure_plan(p);
+    if (s) return s;
+    if (!opt_batchable(p)) return fail(JD_ERR_UNSUPPORTED, "problem cannot run batched");
+    // the batch follows everything queued on the problem's own stream (allocations,
+    // copies of the control)
+    JD_CUDA(cudaEventRecord(m.ev, p->stream));
+    JD_CUDA(cudaStreamWaitEvent(st, m.ev, 0));
+  }
+  const bool f64 = ops->elem == 8;
+  OptBatch ob;
+  ob.n = n;
+  BatchSweep sw[kBatchMax];
+  UnitBatch ub;
+  CombineBatch cb;
+  ub.n = cb.n = 0;
+  int ubl = 0, cbl = 0;
+  auto add_unit = [&](jd_problem *p, const double *partC, int ne, double *units) {
+    const jd_problem_desc &q = p->desc;
+    const int64_t nun = n_units(q.M);
+    ub.first[ub.n] = ubl;
+    ub.j[ub.n++] = UnitJob{partC, p->partG, p->nblk, grad_parts(q.M), nun, q.du, p->DU, ne, units};
+    ubl += (int)ceil_div(nun * ne * 32, 256);
+  };
+  auto add_combine = [&](jd_problem *p, const double *units, int ne, const double *u, int slot) {
+    const jd_problem_desc &q = p->desc;
+    const double dt = q.T / q.Nt;
+    cb.first[cb.n] = cbl;
+    cb.j[cb.n++] = CombineJob{units, u, n_units(q.M), ne, q.Nt * q.du, q.nu * dt, 0.5 * q.nu * dt,
+                              1.0 / (double)q.M, p->scal_d + slot, p->grad_d, p->scal_d + S_BAD};
+    cbl += (int)ceil_div(ne, 128);
+  };
+  for (int i = 0; i < n; ++i) {
+    OptMachine &m = *ms[i];
+    jd_problem *p = m.p;
+    const jd_problem_desc &q = p->desc;
+    OptBatchItem &b = ob.it[i];
+    b.n = q.Nt * q.du;
+    b.Nt = q.Nt;
+    b.du = q.du;
+    b.DU = p->DU;
+    b.fwd = kind == OptMachine::GRAD && fwd;
+    b.dt = q.T / q.Nt;
+    b.lo = q.u_min;
+    b.hi = q.u_max;
+    b.c = m.o.armijo_c;
+    b.zeta = m.zeta;
+    b.u = p->opt_u;
+    b.grad = p->grad_d;
+    b.ut = p->opt_ut;
+    b.ut2 = kind == OptMachine::TRIAL && pair ? p->opt_ut2 : nullptr;
+    b.scal = p->scal_d;
+    b.uk = p->uk;
+    b.uk2 = p->uk2;
+    sw[i].p = p;
+    sw[i].uk = p->uk;
+    sw[i].b = plan_bufs(p);
+    if (kind == OptMachine::TRIAL && pair) {
+      PathBufs &pb = sw[i].b;
+      pb.uk2 = p->uk2;
+      pb.traj2 = p->traj2;
+      pb.log_kt2 = p->log_kt2;
+      pb.log_y2 = p->log_y2;
+      pb.partC2 = p->partC2;
+    }
+    const int64_t nun = n_units(q.M);
+    if (kind == OptMachine::GRAD) {
+      const int ne = 1 + q.Nt * q.du;
+      add_unit(p, p->partC, ne, p->units);
+      add_combine(p, p->units, ne, p->opt_u, S_J);
+    } else {   // the second point's cost units after the first's (the cost needs nun of them)
+      add_unit(p, p->partC, 1, p->units);
+      add_combine(p, p->units, 1, p->opt_ut, S_JT);
+      if (pair) {
+        add_unit(p, p->partC2, 1, p->units + nun);
+        add_combine(p, p->units + nun, 1, p->opt_ut2, S_JT2);
+      }
+    }
+  }
+  ub.first[ub.n] = ubl;
+  cb.first[cb.n] = cbl;
+  cudaError_t e = cudaSuccess;
+  if (kind == OptMachine::GRAD) {
+    if (f64)
+      opt_grad_pre_batch_kernel<double><<<n, 256, 0, st>>>(ob);
+    else
+      opt_grad_pre_batch_kernel<float><<<n, 256, 0, st>>>(ob);
+    count_launch();
+    JD_CUDA(cudaGetLastError());
+    if (fwd) e = ops->fwd_batch(sw, n, FWD_STORE, st);
+    if (e == cudaSuccess) e = ops->adj_batch(sw, n, st);
+  } else {
+    if (f64)
+      opt_trial_pre_batch_kernel<double><<<n, 256, 0, st>>>(ob);
+    else
+      opt_trial_pre_batch_kernel<float><<<n, 256, 0, st>>>(ob);
+    count_launch();
+    JD_CUDA(cudaGetLastError());
+    e = ops->fwd_batch(sw, n, pair ? FWD_STORE | FWD_PAIR : FWD_STORE, st);
+  }
+  JD_CUDA(e);
+  unit_sums_batch_kernel<<<ubl, 256, 0, st>>>(ub);
+  combine_units_batch_kernel<<<cbl, 128, 0, st>>>(cb);
+  if (kind == OptMachine::GRAD)
+    opt_grad_post_batch_kernel<<<n, 256, 0, st>>>(ob);
+  else
+    opt_trial_post_batch_kernel<<<n, 256, 0, st>>>(ob);
+  count_launch(3);
+  JD_CUDA(cudaGetLastError());
+  for (int i = 0; i < n; ++i) {
+    OptMachine &m = *ms[i];
+    JD_CUDA(cudaMemcpyAsync(m.p->host_pinned, m.p->scal_d, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    JD_CUDA(cudaEventRecord(m.ev, st));
+    m.want = OptMachine::IDLE;
+  }
+  return JD_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -1260,7 +1554,7 @@ jd_status jd::create_problem(const jd_problem_desc &q, const jd::ProblemOpts &op
   ALLOC(p->partG, (size_t)q.Nt * p->DU * grad_parts(q.M) * 8, "gradient partials");
   ALLOC(p->partT, (size_t)(p->D + 2) * p->nblk * 8, "parameter partials");
   ALLOC(p->units, (size_t)n_units(q.M) * (1 + nu) * 8, "unit sums");
-  if (pre_pass(q.d, q.Nt, q.M, es)) {   // a small problem: the draws' pre-pass buffers
+  if (!opts.no_pre && pre_pass(q.d, q.Nt, q.M, es)) {   // a small problem: the draws' pre-pass buffers
     ALLOC(p->pre_w, (size_t)q.Nt * q.M * 4, "pre-drawn Poisson words");
     ALLOC(p->pre_z, (size_t)q.Nt * (1 + 3 * p->D) * q.M * es, "pre-drawn normals and slot draws");
   }

@@ -336,11 +336,13 @@ struct GradRows {
 #pragma unroll
     for (int l = 0; l < DU; ++l) w[(l * NR + j) * RowGeom<R>::LD + c] = active ? g[l] : R(0);
   }
-  // rows of steps kbase .. kbase + NR - 1 (those < Nt) -> FP64 warp partials
-  __device__ __forceinline__ void flush(int kbase, int Nt, double *__restrict__ partG, int64_t npart) {
+  // rows of steps kbase .. kbase + NR - 1 (those < Nt) -> FP64 warp partials; bid: the
+  // block's index within its problem's launch
+  __device__ __forceinline__ void flush(int kbase, int Nt, double *__restrict__ partG, int64_t npart,
+                                        int64_t bid) {
     __syncwarp();
     const int lane = threadIdx.x & 31;
-    const int64_t wid = (int64_t)blockIdx.x * (TPB / 32) + (threadIdx.x >> 5);
+    const int64_t wid = bid * (TPB / 32) + (threadIdx.x >> 5);
     constexpr int SPAN = 32 / (32 / NR);   // lanes summed by one reader: 16 or 8
     const int r = lane / (32 / NR), part = lane % (32 / NR);
 #pragma unroll

@@ -70,6 +70,15 @@ struct PathBufs {
   int64_t npart = 0;
 };
 
+// Batched sweeps (serving): the problems of one launch, each with its control in kernel
+// precision and its plan's buffers.
+constexpr int kBatchMax = 16;   // problems per batched launch
+struct BatchSweep {
+  const struct ::jd_problem *p;
+  const void *uk;
+  PathBufs b;
+};
+
 // Per-instantiation launch table (one entry per precision x compiled dimension).
 struct PathOps {
   int D, DU, S, elem;
@@ -87,6 +96,11 @@ struct PathOps {
   // shared memory per block of the recompute adjoint for segments of S steps (null: no
   // recompute plan)
   size_t (*rc_smem)(bool theta, int S);
+  // batched stored-plan sweeps over all paths of up to kBatchMax problems of this
+  // instantiation (forward in mode FWD_STORE or FWD_STORE | FWD_PAIR; adjoint without
+  // parameter gradients); null where not built (built for D <= 2, DU = 1)
+  cudaError_t (*fwd_batch)(const BatchSweep *items, int n, int mode, cudaStream_t s);
+  cudaError_t (*adj_batch)(const BatchSweep *items, int n, cudaStream_t s);
 };
 
 const PathOps *path_ops_dims(int prec, int D, int DU);
@@ -257,6 +271,7 @@ struct ProblemOpts {
   cudaStream_t stream = nullptr;     // null: own stream (or desc.cuda_stream)
   double *pinned = nullptr;          // null: own pinned scalar buffer (kScalars doubles)
   bool async_alloc = false;
+  bool no_pre = false;               // no draw pre-pass buffers (the problem runs batched sweeps)
 };
 constexpr int kScalars = 8 + 34 + 4;   // FP64 scalar slots per problem (device and pinned)
 
@@ -305,11 +320,25 @@ struct OptMachine {
   cudaGraphExec_t g_grad[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   cudaGraphExec_t g_trial[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   int n_grad[2][2] = {{0, 0}, {0, 0}}, n_trial[2][2] = {{0, 0}, {0, 0}};
+  // deferred launches (batched serving): the machine decides its next phase and leaves
+  // the phase's work to opt_launch_batch; want = the phase to launch (GRAD or TRIAL, IDLE
+  // when none), want_fwd = a gradient with its forward sweep, want_pair = a paired trial
+  bool defer = false;
+  Phase want = IDLE;
+  bool want_fwd = false, want_pair = false;
 };
 // p->u_in holds u^0.  u_dst (space us) receives the final iterate.
 jd_status opt_begin(OptMachine &m, ::jd_problem *p, const jd_opt_params &o, double *u_dst,
                     jd_memspace us, double *J_hist);
 jd_status opt_advance(OptMachine &m);
 void opt_release(OptMachine &m);   // frees the machine's graphs
+// Batched phases: whether a problem's phases can share launches (d <= 2, du = 1, the
+// stored plan over all paths at once; the plan's buffers are allocated here); the key of a deferred launch (machines with the
+// same key may share one; -1: nothing deferred); and the deferred phases of n <=
+// kBatchMax machines with one key, launched together on stream s.  Each machine's event
+// is recorded on s after its scalars were copied to its pinned buffer.
+bool opt_batchable(::jd_problem *p);
+int opt_batch_key(const OptMachine &m);
+jd_status opt_launch_batch(OptMachine *const *ms, int n, cudaStream_t s);
 
 }  // namespace jd

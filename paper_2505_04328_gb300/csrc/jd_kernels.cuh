@@ -1000,14 +1000,15 @@ __device__ __forceinline__ void one_jump_pre(const KParams<R, D, DU> &kp, int k,
 
 // PRE: the main-stream draws come from draws_kernel (PreDraws) instead of the step's own
 // Philox and Box-Muller; the same values, so the same bits.
+// fwd_body: the sweep of block bid of a launch over mloc paths (fwd_kernel: bid =
+// blockIdx.x; fwd_batch_kernel: the block's index within its problem).
 template <typename R, int D, int DU, int MODE, bool PAIR = false, bool PRE = false>
-__global__ void __launch_bounds__(TPB)
-fwd_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u,
-           const R *__restrict__ xd, double *__restrict__ partC, R *__restrict__ traj,
-           uint32_t *__restrict__ flags, R *__restrict__ ckpt, R *__restrict__ pcost,
-           JLog<R, D> jl, int *__restrict__ jcnt, int64_t mloc, PairOut<R, D> p2, PreDraws<R, D> pd = {}) {
-  __shared__ Pair<R> red[TPB / 32];
-  const int64_t lm = (int64_t)blockIdx.x * TPB + threadIdx.x;
+__device__ __forceinline__ void fwd_body(const KParams<R, D, DU> &kp, int64_t bid, const R *__restrict__ u,
+                                         const R *__restrict__ xd, double *__restrict__ partC, R *__restrict__ traj,
+                                         uint32_t *__restrict__ flags, R *__restrict__ ckpt, R *__restrict__ pcost,
+                                         const JLog<R, D> &jl, int *__restrict__ jcnt, int64_t mloc,
+                                         const PairOut<R, D> &p2, const PreDraws<R, D> &pd, Pair<R> *red) {
+  const int64_t lm = bid * TPB + threadIdx.x;
   const bool active = lm < mloc;
   const uint32_t m = (uint32_t)(kp.m_begin + lm);
   const int Nt = kp.Nt;
@@ -1115,13 +1116,24 @@ fwd_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u
   if (!active) v = {R(0), R(0)};
   if (pcost && active) pcost[lm] = Ar<R>::add(v.s, v.e);
   const double s = block_sum_to_double(v, red);
-  if (threadIdx.x == 0) partC[blockIdx.x] = s;
+  if (threadIdx.x == 0) partC[bid] = s;
   if constexpr (PAIR) {
     Pair<R> v2 = cost2.pair();
     if (!active) v2 = {R(0), R(0)};
     const double s2 = block_sum_to_double(v2, red);
-    if (threadIdx.x == 0) p2.partC[blockIdx.x] = s2;
+    if (threadIdx.x == 0) p2.partC[bid] = s2;
   }
+}
+
+template <typename R, int D, int DU, int MODE, bool PAIR = false, bool PRE = false>
+__global__ void __launch_bounds__(TPB)
+fwd_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u,
+           const R *__restrict__ xd, double *__restrict__ partC, R *__restrict__ traj,
+           uint32_t *__restrict__ flags, R *__restrict__ ckpt, R *__restrict__ pcost,
+           JLog<R, D> jl, int *__restrict__ jcnt, int64_t mloc, PairOut<R, D> p2, PreDraws<R, D> pd = {}) {
+  __shared__ Pair<R> red[TPB / 32];
+  fwd_body<R, D, DU, MODE, PAIR, PRE>(kp, blockIdx.x, u, xd, partC, traj, flags, ckpt, pcost, jl, jcnt, mloc, p2,
+                                      pd, red);
 }
 
 // X_k of one path from the stored trajectory.
@@ -1227,14 +1239,14 @@ __device__ __forceinline__ const R *staged_rows(const unsigned char *stage, int 
 
 template <typename R, int D, int DU, bool THETA>
 __device__ __forceinline__ void finish_theta(const KParams<R, D, DU> &kp, R (&th)[D + 2], bool active,
-                                             double *__restrict__ partT, Pair<R> *red) {
+                                             double *__restrict__ partT, Pair<R> *red, int64_t bid) {
   if constexpr (THETA) {
     // unrolled: a runtime index into th would keep the accumulators in local memory
 #pragma unroll
   for (int t = 0; t < D + 2; ++t) {
     Pair<R> v = {active ? th[t] : R(0), R(0)};
     const double s = block_sum_to_double(v, red);
-    if (threadIdx.x == 0) partT[(size_t)t * kp.nblk + blockIdx.x] = s;
+    if (threadIdx.x == 0) partT[(size_t)t * kp.nblk + bid] = s;
   }
   }
 }
@@ -1259,7 +1271,7 @@ __device__ __forceinline__ void stored_sweep(const KParams<R, D, DU> &kp, const 
                                              const uint32_t *__restrict__ flags, const JLog<R, D> &jl,
                                              const int *__restrict__ jcnt, double *__restrict__ partG,
                                              double *__restrict__ partT, R *__restrict__ lam_out, int64_t mloc,
-                                             unsigned char *dsm, Pair<R> *red1) {
+                                             unsigned char *dsm, Pair<R> *red1, int64_t bid) {
   using M = Ar<R>;
   constexpr int CH = AdjChunk<R, D>::CH, SV = TS<R, D>::SV, NR = 16, LD = RowGeom<R>::LD;
   constexpr bool FAST = !THETA && !LAM, PIN = pin_coef<D>();
@@ -1267,7 +1279,7 @@ __device__ __forceinline__ void stored_sweep(const KParams<R, D, DU> &kp, const 
   rows.init(reinterpret_cast<R *>(dsm));
   unsigned char *stage = dsm + grad_rows_bytes<R, DU, NR>();
   const int64_t npart = kp.npart;
-  const int64_t lm = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  const int64_t lm = bid * TPB + threadIdx.x;
   const bool active = lm < mloc;
   // inactive threads of the last block replay path 0 (its stored data and its random
   // streams must belong to the same path) and discard the result
@@ -1366,9 +1378,9 @@ __device__ __forceinline__ void stored_sweep(const KParams<R, D, DU> &kp, const 
         rows.put(k & (NR - 1), g, active);
       }
     }
-    if ((k0 & (NR - 1)) == 0) rows.flush(k0, Nt, partG, npart);
+    if ((k0 & (NR - 1)) == 0) rows.flush(k0, Nt, partG, npart, bid);
   }
-  finish_theta<R, D, DU, THETA>(kp, th, active, partT, red1);
+  finish_theta<R, D, DU, THETA>(kp, th, active, partT, red1, bid);
 }
 
 template <typename R, int D, int DU, bool THETA, bool LAM = false>
@@ -1382,11 +1394,14 @@ adj_stored_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restr
   __shared__ Pair<R> red1[TPB / 32];
   if constexpr (pin_coef<D>() && !THETA && !LAM) {   // the drift family decided once
     if (kp.cubic)
-      stored_sweep<R, D, DU, THETA, LAM, 1>(kp, u, xd, traj, flags, jl, jcnt, partG, partT, lam_out, mloc, dsm, red1);
+      stored_sweep<R, D, DU, THETA, LAM, 1>(kp, u, xd, traj, flags, jl, jcnt, partG, partT, lam_out, mloc, dsm, red1,
+                                            blockIdx.x);
     else
-      stored_sweep<R, D, DU, THETA, LAM, 0>(kp, u, xd, traj, flags, jl, jcnt, partG, partT, lam_out, mloc, dsm, red1);
+      stored_sweep<R, D, DU, THETA, LAM, 0>(kp, u, xd, traj, flags, jl, jcnt, partG, partT, lam_out, mloc, dsm, red1,
+                                            blockIdx.x);
   } else {
-    stored_sweep<R, D, DU, THETA, LAM, -1>(kp, u, xd, traj, flags, jl, jcnt, partG, partT, lam_out, mloc, dsm, red1);
+    stored_sweep<R, D, DU, THETA, LAM, -1>(kp, u, xd, traj, flags, jl, jcnt, partG, partT, lam_out, mloc, dsm, red1,
+                                           blockIdx.x);
   }
 }
 
@@ -1536,10 +1551,10 @@ adj_recompute_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__re
           rows.put(k & (NR - 1), g, active);
         }
       }
-      if (((k0 + i0) & (NR - 1)) == 0) rows.flush(k0 + i0, Nt, partG, npart);
+      if (((k0 + i0) & (NR - 1)) == 0) rows.flush(k0 + i0, Nt, partG, npart, blockIdx.x);
     }
   }
-  finish_theta<R, D, DU, THETA>(kp, th, active, partT, red1);
+  finish_theta<R, D, DU, THETA>(kp, th, active, partT, red1, blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -1763,6 +1778,136 @@ cudaError_t op_adj(const jd_problem *p, int variant, bool theta, int64_t m_begin
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Batched stored-plan sweeps (serving): up to kBatchMax problems of one instantiation in
+// one launch.  The table of the problems is the kernel's parameter; problem i owns the
+// launch's blocks first[i] .. first[i + 1] - 1, and each block runs the single-problem
+// body with its index within its problem, so a problem's states, logs and partials are
+// those of its own launch bit for bit.
+// ---------------------------------------------------------------------------
+template <typename R, int D, int DU>
+struct SweepItem {
+  KParams<R, D, DU> kp;
+  const R *u, *xd;
+  double *partC, *partG;
+  R *traj;
+  uint32_t *flags;
+  JLog<R, D> jl;
+  int *jcnt;
+  int64_t mloc;
+  PairOut<R, D> p2;
+};
+template <typename R, int D, int DU>
+struct SweepBatch {
+  int n;
+  int first[kBatchMax + 1];
+  SweepItem<R, D, DU> it[kBatchMax];
+};
+
+__device__ __forceinline__ int sweep_item(const int *first, int n) {
+  int i = 0;
+  while (i + 1 < n && (int)blockIdx.x >= first[i + 1]) ++i;
+  return i;
+}
+
+template <typename R, int D, int DU, bool PAIR>
+__global__ void __launch_bounds__(TPB) fwd_batch_kernel(const __grid_constant__ SweepBatch<R, D, DU> t) {
+  __shared__ Pair<R> red[TPB / 32];
+  const int i = sweep_item(t.first, t.n);
+  const SweepItem<R, D, DU> &f = t.it[i];
+  fwd_body<R, D, DU, FWD_STORE, PAIR, false>(f.kp, blockIdx.x - t.first[i], f.u, f.xd, f.partC, f.traj, f.flags,
+                                             nullptr, nullptr, f.jl, f.jcnt, f.mloc, f.p2, PreDraws<R, D>{}, red);
+}
+
+template <typename R, int D, int DU>
+__global__ void __launch_bounds__(TPB) adj_batch_kernel(const __grid_constant__ SweepBatch<R, D, DU> t) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ Pair<R> red1[TPB / 32];
+  const int i = sweep_item(t.first, t.n);
+  const SweepItem<R, D, DU> &f = t.it[i];
+  const int64_t bid = blockIdx.x - t.first[i];
+  if constexpr (pin_coef<D>()) {   // as adj_stored_kernel: the drift family decided once
+    if (f.kp.cubic)
+      stored_sweep<R, D, DU, false, false, 1>(f.kp, f.u, f.xd, f.traj, f.flags, f.jl, f.jcnt, f.partG, nullptr,
+                                              nullptr, f.mloc, dsm, red1, bid);
+    else
+      stored_sweep<R, D, DU, false, false, 0>(f.kp, f.u, f.xd, f.traj, f.flags, f.jl, f.jcnt, f.partG, nullptr,
+                                              nullptr, f.mloc, dsm, red1, bid);
+  } else {
+    stored_sweep<R, D, DU, false, false, -1>(f.kp, f.u, f.xd, f.traj, f.flags, f.jl, f.jcnt, f.partG, nullptr,
+                                             nullptr, f.mloc, dsm, red1, bid);
+  }
+}
+
+template <typename R, int D, int DU>
+int sweep_table(const BatchSweep *items, int n, bool pair, SweepBatch<R, D, DU> &t) {
+  static_assert(sizeof(SweepBatch<R, D, DU>) <= 32000, "the table is one kernel parameter (at most 32764 bytes)");
+  t.n = n;
+  int nb = 0;
+  for (int i = 0; i < n; ++i) {
+    const jd_problem *p = items[i].p;
+    const PathBufs &b = items[i].b;
+    const int64_t M = p->desc.M;
+    SweepItem<R, D, DU> &f = t.it[i];
+    make_kparams<R, D, DU>(p, 0, M, f.kp);
+    f.u = static_cast<const R *>(items[i].uk);
+    f.xd = static_cast<const R *>(p->xdk);
+    f.partC = b.partC;
+    f.partG = b.partG;
+    f.traj = static_cast<R *>(b.traj);
+    f.flags = b.flags;
+    f.jl = JLog<R, D>{static_cast<typename V2<R>::T *>(b.log_kt), static_cast<R *>(b.log_y), M, b.log_cap};
+    f.jcnt = b.jcnt;
+    f.mloc = M;
+    f.p2 = PairOut<R, D>{};
+    if (pair)
+      f.p2 = PairOut<R, D>{static_cast<const R *>(b.uk2), b.partC2, static_cast<R *>(b.traj2), nullptr,
+                           JLog<R, D>{static_cast<typename V2<R>::T *>(b.log_kt2), static_cast<R *>(b.log_y2), M,
+                                      b.log_cap}};
+    t.first[i] = nb;
+    nb += (int)ceil_div(M, TPB);
+  }
+  t.first[n] = nb;
+  return nb;
+}
+
+template <typename R, int D, int DU>
+cudaError_t op_fwd_batch(const BatchSweep *items, int n, int mode, cudaStream_t s) {
+  if (n < 1 || n > kBatchMax) return cudaErrorInvalidValue;
+  static thread_local SweepBatch<R, D, DU> t;   // a large table: kept off the stack
+  const bool pair = (mode & FWD_PAIR) != 0;
+  const int nb = sweep_table<R, D, DU>(items, n, pair, t);
+  if constexpr (PAIR_SWEEPS<D>) {
+    if (pair)
+      fwd_batch_kernel<R, D, DU, true><<<nb, TPB, 0, s>>>(t);
+    else
+      fwd_batch_kernel<R, D, DU, false><<<nb, TPB, 0, s>>>(t);
+  } else {
+    if (pair) return cudaErrorNotSupported;
+    fwd_batch_kernel<R, D, DU, false><<<nb, TPB, 0, s>>>(t);
+  }
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <typename R, int D, int DU>
+cudaError_t op_adj_batch(const BatchSweep *items, int n, cudaStream_t s) {
+  if (n < 1 || n > kBatchMax) return cudaErrorInvalidValue;
+  static thread_local SweepBatch<R, D, DU> t;
+  const int nb = sweep_table<R, D, DU>(items, n, false, t);
+  const size_t smem = grad_rows_bytes<R, DU, 16>() + adj_stage_bytes<R, D>();
+  cudaError_t err = ensure_dyn_smem((const void *)adj_batch_kernel<R, D, DU>, smem);
+  if (err == cudaSuccess) adj_batch_kernel<R, D, DU><<<nb, TPB, smem, s>>>(t);
+  count_launch();
+  if (err != cudaSuccess) return err;
+  return cudaGetLastError();
+}
+
+template <typename R, int D, int DU>
+constexpr bool batch_built() {
+  return D <= 2 && DU == 1;
+}
+
 template <typename R, int D, int DU>
 size_t op_stack_bytes() {
   size_t need = 2 * sizeof(JumpStep<R, D>) + 2048;
@@ -1785,13 +1930,25 @@ size_t op_stack_bytes() {
         need = a.localSizeBytes + 1024;
     }
   }
+  if constexpr (batch_built<R, D, DU>()) {
+    for (const void *k : {(const void *)fwd_batch_kernel<R, D, DU, false>, (const void *)fwd_batch_kernel<R, D, DU, true>,
+                          (const void *)adj_batch_kernel<R, D, DU>}) {
+      cudaFuncAttributes a;
+      if (cudaFuncGetAttributes(&a, k) == cudaSuccess && a.localSizeBytes + 1024 > need)
+        need = a.localSizeBytes + 1024;
+    }
+  }
   return (need + 255) & ~(size_t)255;
 }
 
 template <typename R, int D, int DU>
 constexpr PathOps make_ops() {
-  return PathOps{D, DU, seg_len<D>(), (int)sizeof(R), 0, &op_stack_bytes<R, D, DU>, &op_fwd<R, D, DU>,
-                 &op_adj<R, D, DU>, &recompute_smem<R, D, DU>};
+  if constexpr (batch_built<R, D, DU>())
+    return PathOps{D, DU, seg_len<D>(), (int)sizeof(R), 0, &op_stack_bytes<R, D, DU>, &op_fwd<R, D, DU>,
+                   &op_adj<R, D, DU>, &recompute_smem<R, D, DU>, &op_fwd_batch<R, D, DU>, &op_adj_batch<R, D, DU>};
+  else
+    return PathOps{D, DU, seg_len<D>(), (int)sizeof(R), 0, &op_stack_bytes<R, D, DU>, &op_fwd<R, D, DU>,
+                   &op_adj<R, D, DU>, &recompute_smem<R, D, DU>, nullptr, nullptr};
 }
 
 }  // namespace jd

@@ -13,9 +13,16 @@
 //     polls each slot's event and advances the machines whose phase has finished, so
 //     the kernels of all active requests overlap on the device while the host takes
 //     one request's line-search decision;
+//   * small requests (d <= 2, du = 1, the stored plan, at most batch_paths paths) share
+//     launches: their machines defer each phase, and the worker launches the deferred
+//     phases of up to kBatchMax requests with the same phase kind, precision and
+//     dimension as one batched sequence (jd::opt_launch_batch) on one of a few batch
+//     streams -- one forward and one adjoint sweep over all their paths, one launch per
+//     reduction and per optimizer step, instead of a launch sequence per request;
 //   * a finished request frees its slot and memory, and the next ones are admitted.
-// Each request runs exactly the kernels and the host decisions of jd_optimize on its
-// own buffers, so its result does not depend on what else is running.
+// Each request runs the arithmetic and the host decisions of jd_optimize on its own
+// buffers (a batched launch gives every problem the bits of its own launches), so its
+// result does not depend on what else is running.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -58,7 +65,10 @@ struct Slot {
   jd_problem *p = nullptr;
   Request *req = nullptr;
   jd::OptMachine m;
+  bool batch = false;   // the request's phases run in batched launches
 };
+
+constexpr int kBatchStreams = 4;
 
 }  // namespace
 
@@ -72,6 +82,10 @@ struct jd_server {
   std::unordered_map<uint64_t, Request *> all;
   uint64_t next_ticket = 1;
   std::atomic<bool> stop{false};
+  std::atomic<int64_t> batch_paths{JD_SERVER_BATCH_PATHS};
+  std::atomic<int64_t> batch_launches{0}, batch_phases{0};
+  cudaStream_t bstream[kBatchStreams] = {};
+  int next_bstream = 0;
   std::thread worker;
   Clock::time_point t0;
   double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
@@ -188,7 +202,10 @@ bool admit_one(jd_server *s) {
   Slot &sl = *free_slot;
   sl.m = jd::OptMachine();
   sl.m.ev = sl.ev;
-  sl.m.use_graphs = true;   // every phase of a request replays a captured graph
+  sl.m.use_graphs = true;   // every phase of a solo request replays a captured graph
+  const jd_problem_desc &rd = rq->desc;
+  sl.batch = rd.d <= 2 && rd.du == 1 && plan == JD_ADJ_STORED && !rd.use_tensor_cores &&
+             rd.M <= s->batch_paths.load();
   rq->t_admit = s->now();
   rq->plan = plan;
   rq->bytes = bytes;
@@ -213,11 +230,17 @@ bool admit_one(jd_server *s) {
   opts.stream = sl.stream;
   opts.pinned = sl.pinned_scal;
   opts.async_alloc = true;
+  opts.no_pre = sl.batch;   // batched sweeps draw in the sweep
   jd_status st = jd::create_problem(q, opts, &sl.p);
   if (st != JD_OK) {
     sl.p = nullptr;
     finish_request(s, sl, st);
     return true;
+  }
+  if (sl.batch && !jd::opt_batchable(sl.p)) sl.batch = false;
+  if (sl.batch) {   // phases deferred to batched launches; no graphs
+    sl.m.defer = true;
+    sl.m.use_graphs = false;
   }
   // u^0 = 0 projected into the bounds
   const double u0 = std::min(std::max(0.0, q.u_min), q.u_max);
@@ -231,15 +254,45 @@ bool admit_one(jd_server *s) {
   return true;
 }
 
+// Launch the deferred phases of batched requests: grouped by batch key, up to
+// kBatchMax per launch, on the batch streams in turn.
+void launch_batches(jd_server *s) {
+  std::vector<Slot *> w;
+  for (auto &sl : s->slots)
+    if (sl.req && sl.batch && jd::opt_batch_key(sl.m) >= 0) w.push_back(&sl);
+  std::stable_sort(w.begin(), w.end(),
+                   [](const Slot *a, const Slot *b) { return jd::opt_batch_key(a->m) < jd::opt_batch_key(b->m); });
+  for (size_t i = 0; i < w.size();) {
+    const int key = jd::opt_batch_key(w[i]->m);
+    size_t j = i;
+    jd::OptMachine *ms[jd::kBatchMax];
+    int n = 0;
+    while (j < w.size() && n < jd::kBatchMax && jd::opt_batch_key(w[j]->m) == key) ms[n++] = &w[j++]->m;
+    cudaStream_t st = s->bstream[s->next_bstream];
+    s->next_bstream = (s->next_bstream + 1) % kBatchStreams;
+    const jd_status e = jd::opt_launch_batch(ms, n, st);
+    if (e != JD_OK) {
+      cudaStreamSynchronize(st);   // nothing of the group may still run when its buffers go
+      for (size_t k = i; k < j; ++k) finish_request(s, *w[k], e);
+    } else {
+      s->batch_launches.fetch_add(1);
+      s->batch_phases.fetch_add(n);
+    }
+    i = j;
+  }
+}
+
 void worker_main(jd_server *s) {
   cudaSetDevice(s->device);
   for (;;) {
     while (admit_one(s)) {
     }
+    launch_batches(s);   // the first phases of the requests just admitted
     bool progress = false, active = false;
     for (auto &sl : s->slots) {
       if (!sl.req) continue;
       active = true;
+      if (sl.batch && sl.m.want != jd::OptMachine::IDLE) continue;   // not launched yet
       const cudaError_t q = cudaEventQuery(sl.ev);
       if (q == cudaErrorNotReady) continue;
       progress = true;
@@ -253,6 +306,7 @@ void worker_main(jd_server *s) {
       else if (sl.m.phase == jd::OptMachine::DONE)
         finish_request(s, sl, JD_OK);
     }
+    launch_batches(s);   // the phases decided in this pass
     if (progress) continue;
     std::unique_lock<std::mutex> g(s->mu);
     if (!active) {
@@ -326,6 +380,11 @@ jd_status jd_server_create(size_t hbm_budget, int max_slots, jd_server **out) {
   size_t cur = 0;
   if (cudaDeviceGetLimit(&cur, cudaLimitStackSize) == cudaSuccess && cur < need)
     cudaDeviceSetLimit(cudaLimitStackSize, need);
+  for (auto &b : s->bstream)
+    if (cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking) != cudaSuccess) {
+      jd_server_destroy(s);
+      return JD_ERR_CUDA;
+    }
   s->slots.resize(max_slots);
   for (auto &sl : s->slots) {
     if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -415,6 +474,19 @@ jd_status jd_server_info(jd_server *s, uint64_t ticket, jd_request_info *info) {
   return JD_OK;
 }
 
+jd_status jd_server_set_batching(jd_server *s, int64_t max_paths) {
+  if (!s || max_paths < 0) return JD_ERR_INVALID_ARG;
+  s->batch_paths.store(max_paths);
+  return JD_OK;
+}
+
+jd_status jd_server_batch_stats(jd_server *s, int64_t *launches, int64_t *phases) {
+  if (!s) return JD_ERR_INVALID_ARG;
+  if (launches) *launches = s->batch_launches.load();
+  if (phases) *phases = s->batch_phases.load();
+  return JD_OK;
+}
+
 jd_status jd_server_destroy(jd_server *s) {
   if (!s) return JD_OK;
   {
@@ -437,6 +509,11 @@ jd_status jd_server_destroy(jd_server *s) {
     if (sl.pinned_scal) cudaFreeHost(sl.pinned_scal);
     if (sl.pinned_u) cudaFreeHost(sl.pinned_u);
   }
+  for (auto &b : s->bstream)
+    if (b) {
+      cudaStreamSynchronize(b);
+      cudaStreamDestroy(b);
+    }
   cudaMemPool_t pool;
   if (cudaDeviceGetDefaultMemPool(&pool, s->device) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
   for (auto &kv : s->all) delete kv.second;

@@ -7,12 +7,16 @@
   request (FP32 only) within the FP32 bars (J 1e-5, control 1e-4 relative).
 * Admission: a request larger than the whole budget finishes with status OOM; a small
   budget serializes requests without changing their results.
+* Batched launches: many small requests (d <= 2) share launch sequences, and each still
+  gets the bits of its solo jd_optimize; the batched server launches fewer kernels than
+  the same stream served one request per launch sequence.
 """
 import numpy as np
 import pytest
 
 import oracle
 import workloads
+import paper_2505_04328_gb300 as jd
 from paper_2505_04328_gb300 import JdProblem, JdServer, build, footprint
 
 pytestmark = pytest.mark.gpu
@@ -121,3 +125,61 @@ def test_parity_with_oracle(idx):
     else:
         assert abs(r["J"] - ro["J"]) <= 1e-5 * abs(ro["J"])
         assert np.linalg.norm(u - uo) <= 1e-4 * np.linalg.norm(uo)
+
+
+def _small_requests(n=24):
+    """Small requests of the serving families: d in {1, 2}, M from 700 to 40000 (ragged),
+    N_t from 30 to 400, lambda from 0.5 to 9; FP32 and FP64."""
+    rng = np.random.default_rng(11)
+    out = []
+    for i in range(n):
+        d = 1 + i % 2
+        M = int(rng.integers(700, 40001))
+        Nt = int(rng.integers(30, 401))
+        p = workloads.lq_scalar(M=M, Nt=Nt) if d == 1 else workloads.double_well(M=M, Nt=Nt)
+        p.lam = float(rng.uniform(0.5, 9.0))
+        p.seed = 900 + i
+        out.append((p, "fp64" if i % 3 == 2 else "fp32"))
+    return out
+
+
+def _serve(reqs, batch_paths, slots=32):
+    l0 = jd.launch_count()
+    with JdServer(max_slots=slots, batch_paths=batch_paths) as srv:
+        tickets = [srv.submit(p, prec=prec, **OPT) for p, prec in reqs]
+        for t in tickets:
+            assert srv.wait(t, timeout=600)
+        res = [srv.poll(t) for t in tickets]
+        stats = srv.batch_stats()
+    return res, stats, jd.launch_count() - l0
+
+
+def test_batched_small_requests_equal_solo():
+    reqs = _small_requests()
+    solo = [_solo(p, prec) for p, prec in reqs]
+    res, (launches, phases), nk = _serve(reqs, batch_paths=1 << 16)
+    assert launches > 0 and phases > launches, (launches, phases)   # phases shared launches
+    for (p, prec), (us, rs), (um, rm) in zip(reqs, solo, res):
+        assert rm["status"] == 0 and rs["status"] == 0, p.name
+        assert rm["J"] == rs["J"] and rm["iters"] == rs["iters"] and rm["evals"] == rs["evals"], p.name
+        assert rm["sweeps"] == rs["sweeps"], p.name
+        assert np.array_equal(um, us), (p.name, prec)
+    # the same stream without batching: the same bits, more kernels
+    res0, (l0, ph0), nk0 = _serve(reqs, batch_paths=0)
+    assert l0 == 0 and ph0 == 0
+    for (um, rm), (u0, r0) in zip(res, res0):
+        assert rm["J"] == r0["J"] and np.array_equal(um, u0)
+    print("kernels batched", nk, "unbatched", nk0, "mean batch", phases / launches)
+    assert nk < nk0
+
+
+def test_batching_limit_excludes_large_requests():
+    """Requests above the limit run their own launches (no batched phase)."""
+    reqs = [(workloads.double_well(M=5000, Nt=40), "fp32"), (workloads.lq_scalar(M=3000, Nt=40), "fp32")]
+    res, (launches, phases), _ = _serve(reqs, batch_paths=2000, slots=4)
+    assert launches == 0 and phases == 0
+    assert all(r["status"] == 0 for _, r in res)
+    with JdServer(max_slots=2) as srv:
+        import ctypes
+        from paper_2505_04328_gb300 import binding
+        assert binding.lib().jd_server_set_batching(srv.h, ctypes.c_int64(-1)) == binding.JD_ERR_INVALID_ARG
