@@ -696,11 +696,12 @@ def run_autograd(args, p, stream, dist, ws, rank, local):
     return 0
 
 
-def serve(jd, reqs, opt, slots):
+def serve(jd, reqs, opt, slots, batch_paths=None):
     """Submit (arrival_time, problem) pairs at their arrival times to one jd_server and
-    wait for all; returns (infos, results, wall seconds, kernels launched)."""
+    wait for all; returns (infos, results, wall seconds, kernels launched, (batched
+    launch sequences, request phases in them))."""
     import threading as th
-    srv = jd.JdServer(max_slots=slots)
+    srv = jd.JdServer(max_slots=slots, batch_paths=batch_paths)
     tickets = [None] * len(reqs)
 
     def submitter():
@@ -722,8 +723,128 @@ def serve(jd, reqs, opt, slots):
     launches = jd.launch_count() - l0
     infos = [srv.info(t) for t in tickets]
     results = [srv.poll(t)[1] for t in tickets]
+    bstats = srv.batch_stats()
     srv.close()
-    return infos, results, wall, launches
+    return infos, results, wall, launches, bstats
+
+
+def small_stream(n, rate, seed=5):
+    """The small requests of the serving stream (d <= 2, M <= 2^16: the ones that share
+    batched launches), n of them, re-timed as Poisson arrivals at rate."""
+    reqs, k = [], 0
+    while len(reqs) < n:
+        k += 5 * n
+        reqs = [(t, p) for t, p in workloads.serving_requests(n=k, rate=rate, seed=seed)
+                if p.d <= 2 and p.M <= (1 << 16)][:n]
+    t = np.cumsum(np.random.default_rng(seed + 1000).exponential(1.0 / rate, size=n))
+    return [(float(ti), p) for ti, (_, p) in zip(t, reqs)]
+
+
+def plain_rate(jd, torch, reqs, prec, iters=3):
+    """Path-steps per second of requests solved one at a time (jd_optimize, iters
+    iterations each, no tolerance stop), gradient path-steps as in the served value."""
+    steps, t = 0, 0.0
+    for _, p in reqs:
+        with jd.JdProblem(p, prec=prec) as jp:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, r, _ = jp.optimize(np.zeros((p.Nt, p.du)), max_iter=iters, tol_rel_grad=0.0)
+            t += time.perf_counter() - t0
+            steps += (r["iters"] + (0 if r["iters"] == iters else 1)) * p.M * p.Nt
+    return steps / t if t > 0 else None
+
+
+def run_serving_small(args, jd, clocks, ws, rank):
+    """The small requests of the stream, served with batched launches and with one launch
+    sequence per request (batching off): throughput, latency, kernels, mean batch."""
+    reqs = small_stream(args.requests, args.rate, seed=5 + rank)
+    opt = dict(max_iter=args.max_iter, tol_rel_grad=1e-4)
+    out = {}
+    for name, bp in (("batched", None), ("unbatched", 0)):
+        infos, results, wall, launches, (bl, bph) = serve(jd, reqs, opt, args.slots, batch_paths=bp)
+        st = serve_stats(infos, results)
+        st.update(kernels=launches, batched_launches=bl, batched_phases=bph,
+                  mean_batch=(bph / bl) if bl else None)
+        out[name] = st
+    clk = clocks.stop()
+    value = out["batched"]["path_steps_per_s"]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": len(reqs), "warmup": 0,
+            "ms_per_step": out["batched"]["makespan_s"] * 1e3 / len(reqs), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"serving: the small requests of the stream (d <= 2, M <= 2^16), "
+                                   f"{len(reqs)} requests, Poisson arrivals {args.rate}/s",
+                       "slots": args.slots, "max_iter": args.max_iter, "tol_rel_grad": 1e-4,
+                       "step": "one request; value = gradient path-steps / makespan (batched)"},
+            "batched": out["batched"], "unbatched": out["unbatched"],
+            "batched_vs_unbatched": value / out["unbatched"]["path_steps_per_s"],
+            "latency_s": out["batched"]["latency_s"], "gpu_launches": out["batched"]["kernels"],
+            "roofline": None, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def serving_sample(jd, torch, reqs, slots):
+    """The same requests three ways, 3 optimizer iterations each: served together (FP32),
+    and one at a time through jd_optimize in FP32 (what serving itself adds) and in FP64
+    (the plain per-problem GPU form)."""
+    si, sr, _, _, _ = serve(jd, [(0.0, p) for _, p in reqs], dict(max_iter=3, tol_rel_grad=0.0), slots)
+    served = serve_stats(si, sr)["path_steps_per_s"]
+    plain64 = plain_rate(jd, torch, reqs, "fp64")
+    plain32 = plain_rate(jd, torch, reqs, "fp32")
+    return {"requests": len(reqs), "iterations": 3, "served_fp32": served, "one_at_a_time_fp32": plain32,
+            "one_at_a_time_fp64": plain64, "unit": UNIT,
+            "served_vs_one_at_a_time_fp32": (served / plain32) if plain32 else None,
+            "served_vs_one_at_a_time_fp64": (served / plain64) if plain64 else None}
+
+
+def run_serving_sample(args, jd, torch, clocks, ws, rank):
+    """Only the served / one-at-a-time comparison on the first --plain-sample d <= 8
+    requests of the stream."""
+    reqs = workloads.serving_requests(n=args.requests, rate=args.rate, seed=5 + rank)
+    sample = [(t, p) for t, p in reqs if p.d <= 8][: args.plain_sample]
+    res = serving_sample(jd, torch, sample, args.slots)
+    clk = clocks.stop()
+    line = {"metric": METRIC, "value": res["served_fp32"], "unit": UNIT, "n_gpus": ws, "steps": len(sample),
+            "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"serving: the first {len(sample)} d <= 8 requests of the stream, served "
+                                   "together vs one at a time", "slots": args.slots},
+            "sample": res, "roofline": None, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serving_sweep(args, jd, clocks, ws, rank):
+    """Rate sweep over the whole stream: --requests requests at each rate of --rates;
+    per rate the completion rate (requests / makespan), latency p50/p99 and whether the
+    server kept up (completion rate at least 0.9 of the arrival rate)."""
+    opt = dict(max_iter=args.max_iter, tol_rel_grad=1e-4)
+    rows = []
+    for rate in [float(r) for r in args.rates.split(",")]:
+        reqs = workloads.serving_requests(n=args.requests, rate=rate, seed=5 + rank)
+        infos, results, wall, launches, (bl, bph) = serve(jd, reqs, opt, args.slots)
+        st = serve_stats(infos, results)
+        span = reqs[-1][0] - reqs[0][0]
+        done_rate = len(reqs) / st["makespan_s"]
+        rows.append({"rate": rate, "arrival_span_s": span, "completed_per_s": done_rate,
+                     "kept_up": done_rate >= 0.9 * rate, "latency_s": st["latency_s"],
+                     "path_steps_per_s": st["path_steps_per_s"], "kernels": launches,
+                     "batched_phases": bph, "requests_ok": st["requests_ok"]})
+    clk = clocks.stop()
+    ok = [r["rate"] for r in rows if r["kept_up"]]
+    best = max(rows, key=lambda r: r["path_steps_per_s"])
+    line = {"metric": METRIC, "value": best["path_steps_per_s"], "unit": UNIT, "n_gpus": ws,
+            "steps": args.requests * len(rows), "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"serving rate sweep, {args.requests} requests of the stream per rate",
+                       "slots": args.slots, "max_iter": args.max_iter, "tol_rel_grad": 1e-4},
+            "sweep": rows, "highest_rate_kept_up": max(ok) if ok else None,
+            "gpu_launches": sum(r["kernels"] for r in rows), "roofline": None, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
 
 
 def serve_stats(infos, results):
@@ -753,11 +874,17 @@ def run_serving(args):
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     jd.build()
-    reqs = workloads.serving_requests(n=args.requests, rate=args.rate, seed=5 + rank)
-    opt = dict(max_iter=args.max_iter, tol_rel_grad=1e-4)
     clocks = ClockSampler(local)
     clocks.start()
-    infos, results, wall, launches = serve(jd, reqs, opt, args.slots)
+    if args.small:
+        return run_serving_small(args, jd, clocks, ws, rank)
+    if args.rates:
+        return run_serving_sweep(args, jd, clocks, ws, rank)
+    if args.sample_only:
+        return run_serving_sample(args, jd, torch, clocks, ws, rank)
+    reqs = workloads.serving_requests(n=args.requests, rate=args.rate, seed=5 + rank)
+    opt = dict(max_iter=args.max_iter, tol_rel_grad=1e-4)
+    infos, results, wall, launches, (bl, bph) = serve(jd, reqs, opt, args.slots)
     clk = clocks.stop()
     mix = serve_stats(infos, results)
     if args.mix_only:   # e.g. a rate below capacity: latency of the mix alone
@@ -768,24 +895,18 @@ def run_serving(args):
                 "config": {"workload": f"serving {len(reqs)} requests, Poisson arrivals {args.rate}/s",
                            "slots": args.slots, "max_iter": args.max_iter, "tol_rel_grad": 1e-4},
                 "mix": mix, "latency_s": mix["latency_s"], "gpu_launches": launches, "roofline": None,
-                "clocks": clk}
+                "batched": {"launches": bl, "phases": bph}, "clocks": clk}
         if rank == 0:
             print(json.dumps(line), flush=True)
         return 0
 
     small = [(t, p) for t, p in reqs if p.d <= 8]
-    i8, r8, _, _ = serve(jd, small, opt, args.slots)
+    i8, r8, _, _, _ = serve(jd, small, opt, args.slots)
     sub = serve_stats(i8, r8)
-    # plain per-problem FP64 GPU form: one request at a time, 3 optimizer iterations each
-    plain_steps, plain_t = 0, 0.0
-    for _, p in small[: args.plain_sample]:
-        with jd.JdProblem(p, prec="fp64") as jp:
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            _, r, _ = jp.optimize(np.zeros((p.Nt, p.du)), max_iter=3, tol_rel_grad=0.0)
-            plain_t += time.perf_counter() - t0
-            plain_steps += (r["iters"] + (0 if r["iters"] == 3 else 1)) * p.M * p.Nt
-    plain = plain_steps / plain_t if plain_t > 0 else None
+    # the same sample of these requests three ways, 3 optimizer iterations each: served
+    # (all submitted at once), and one at a time through jd_optimize in FP32 (what
+    # serving itself adds) and in FP64 (the plain per-problem GPU form)
+    sample = serving_sample(jd, torch, small[: args.plain_sample], args.slots)
     value = mix["path_steps_per_s"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": len(reqs),
@@ -798,10 +919,8 @@ def run_serving(args):
                            "path-steps / makespan",
                    "l2": "inputs larger than L2 for most requests; no flush"},
         "mix": mix,
-        "d_le_8": {**sub, "plain_fp64_gpu": {"value": plain, "unit": UNIT,
-                                            "sample": f"first {min(len(small), args.plain_sample)} of "
-                                                      "these requests, one at a time, 3 iterations each"},
-                   "ratio_vs_plain_fp64": (sub["path_steps_per_s"] / plain) if plain else None},
+        "d_le_8": {**sub, "sample": sample},
+        "batched": {"launches": bl, "phases": bph},
         "latency_s": mix["latency_s"],
         "gpu_launches": launches, "roofline": None, "clocks": clk,
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
@@ -946,9 +1065,16 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0, help="serving: Poisson arrival rate (1/s)")
     ap.add_argument("--slots", type=int, default=16, help="serving: requests in flight at most")
     ap.add_argument("--max-iter", type=int, default=50, help="serving: optimizer updates at most")
-    ap.add_argument("--plain-sample", type=int, default=6, help="serving: requests timed in plain FP64")
+    ap.add_argument("--plain-sample", type=int, default=32,
+                    help="serving: requests of the d <= 8 subset served together and timed one at a time")
     ap.add_argument("--mix-only", action="store_true",
                     help="serving: the whole stream only (no d <= 8 pass, no plain FP64 sample)")
+    ap.add_argument("--small", action="store_true",
+                    help="serving: the stream's small requests (d <= 2, M <= 2^16), batched vs unbatched")
+    ap.add_argument("--sample-only", action="store_true",
+                    help="serving: only the served vs one-at-a-time comparison on --plain-sample requests")
+    ap.add_argument("--rates", default=None,
+                    help="serving: comma-separated arrival rates (1/s) for a rate sweep of the stream")
     ap.add_argument("--tc", type=int, default=0, choices=[0, 1, 2, 3],
                     help="tensor cores for the d=32 workload: 0 off, 1 BF16, 2 BF16x3, "
                          "3 BF16x3 in the adjoint only")
