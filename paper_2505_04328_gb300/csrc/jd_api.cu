@@ -1556,7 +1556,7 @@ jd_status jd::create_problem(const jd_problem_desc &q, const jd::ProblemOpts &op
   ALLOC(p->units, (size_t)n_units(q.M) * (1 + nu) * 8, "unit sums");
   if (!opts.no_pre && pre_pass(q.d, q.Nt, q.M, es)) {   // a small problem: the draws' pre-pass buffers
     ALLOC(p->pre_w, (size_t)q.Nt * q.M * 4, "pre-drawn Poisson words");
-    ALLOC(p->pre_z, (size_t)q.Nt * (1 + 3 * p->D) * q.M * es, "pre-drawn normals and slot draws");
+    ALLOC(p->pre_z, pre_z_values(q.Nt, p->D, q.M) * es, "pre-drawn normals and slot draws");
   }
   ALLOC(p->opt_u, nu * 8, "optimizer iterate");
   ALLOC(p->opt_ut, nu * 8, "optimizer trial");

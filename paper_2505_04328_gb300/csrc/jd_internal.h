@@ -13,6 +13,8 @@ namespace jd {
 
 constexpr int NMAX = 16;   // jumps per uniform step are capped at this count
 constexpr int TPB = 128;   // threads (one path each) per block of the path kernels
+constexpr int SPREAD_TPB = 32;     // a small problem's pre-drawn sweeps: one warp per block ...
+constexpr int SPREAD_LANES = 4;    // ... with this many paths (lanes) active (measured: 4 beat 1, 8, 32)
 constexpr int BATCH = 8;   // steps per transposed warp reduction
 
 // FWD_PAIR (with FWD_STORE or FWD_CKPT): a second control on the same random data in the
@@ -60,8 +62,8 @@ struct PathBufs {
   double *partC2 = nullptr;
   // main-stream draws of every (step, path) taken by a parallel pre-pass (small problems,
   // whose sweeps are latency-bound): pre_w [Nt][mloc] Poisson words, pre_z [Nt][D][mloc]
-  // normals followed by [Nt][1 + 2D][mloc] slot-0 draws, in kernel precision; null = the
-  // sweep draws them itself
+  // normals followed by [Nt][1 + 2D][mloc] slot-0 draws, in kernel precision, then the
+  // sweeps' per-path cost pairs [2][mloc]; null = the sweep draws them itself
   uint32_t *pre_w = nullptr;
   void *pre_z = nullptr;
   // partial-stride override: a launch that covers one block of the paths (chunked
@@ -132,8 +134,13 @@ constexpr int RING_MAX = 2048;   // 8 blocks of 256 lanes: the largest portable 
 // main-stream draws in one parallel kernel first, when their buffers stay small.
 constexpr int64_t PRE_MAX_PATHS = 152 * 2 * 128;
 constexpr size_t PRE_MAX_BYTES = (size_t)128 << 20;
+// pre_z holds the normals, the slot-0 draws and then the paths' cost pairs of the sweeps
+// (2 controls x M pairs of 2 values)
+inline size_t pre_z_values(int Nt, int D, int64_t M) {
+  return (size_t)Nt * (1 + 3 * D) * (size_t)M + 4 * (size_t)M;
+}
 inline size_t pre_bytes(int Nt, int D, int64_t M, size_t es) {
-  return (size_t)Nt * (size_t)M * (4 + (1 + 3 * D) * es);   // words, normals, slot-0 draws
+  return (size_t)Nt * (size_t)M * 4 + pre_z_values(Nt, D, M) * es;   // words, normals, slot-0 draws
 }
 inline bool pre_pass(int d, int Nt, int64_t M, size_t es) {
   const int D = d <= 1 ? 1 : 2;

@@ -982,6 +982,7 @@ struct PreDraws {
   const R *z;          // [Nt][D][mloc] sub-step 0 normals
   const R *s;          // [Nt][1 + 2D][mloc] a step with exactly one (additive) jump: its
                        // slot-0 draws (time fraction, unit size, next normals); else unset
+  Pair<R> *cw, *cw2;   // [mloc] each path's cost pair (first, second control)
 };
 
 // A step with one jump, its slot draws pre-drawn: sub-step to the jump, jump, sub-step.
@@ -1002,13 +1003,20 @@ __device__ __forceinline__ void one_jump_pre(const KParams<R, D, DU> &kp, int k,
 // Philox and Box-Muller; the same values, so the same bits.
 // fwd_body: the sweep of block bid of a launch over mloc paths (fwd_kernel: bid =
 // blockIdx.x; fwd_batch_kernel: the block's index within its problem).
+// With PRE the launch has one warp per block with SPREAD_LANES paths (the other lanes
+// leave at once): a small problem's few paths spread over many SMs and warp schedulers,
+// each warp carrying few lanes (an FP64 warp instruction of this part occupies its
+// scheduler's FP64 pipe for many cycles).  Each path leaves its cost pair in pd.cw, and
+// spread_combine_kernel forms every 128-path block's cost partial from them exactly as
+// block_sum_to_double does in the one-path-per-thread launch.
 template <typename R, int D, int DU, int MODE, bool PAIR = false, bool PRE = false>
 __device__ __forceinline__ void fwd_body(const KParams<R, D, DU> &kp, int64_t bid, const R *__restrict__ u,
                                          const R *__restrict__ xd, double *__restrict__ partC, R *__restrict__ traj,
                                          uint32_t *__restrict__ flags, R *__restrict__ ckpt, R *__restrict__ pcost,
                                          const JLog<R, D> &jl, int *__restrict__ jcnt, int64_t mloc,
                                          const PairOut<R, D> &p2, const PreDraws<R, D> &pd, Pair<R> *red) {
-  const int64_t lm = bid * TPB + threadIdx.x;
+  if (PRE && threadIdx.x >= SPREAD_LANES) return;   // no warp-wide operation follows in this mode
+  const int64_t lm = PRE ? bid * SPREAD_LANES + threadIdx.x : bid * TPB + threadIdx.x;
   const bool active = lm < mloc;
   const uint32_t m = (uint32_t)(kp.m_begin + lm);
   const int Nt = kp.Nt;
@@ -1094,12 +1102,12 @@ __device__ __forceinline__ void fwd_body(const KParams<R, D, DU> &kp, int64_t bi
     cost.add(cost_term(kh, x, xd + (size_t)(k + 1) * D));
     if constexpr (PAIR) cost2.add(cost_term(kh, x2, xd + (size_t)(k + 1) * D));
     if (MODE == FWD_STORE && ((k & 31) == 31 || k == Nt - 1)) {
-      if (active) flags[(size_t)(k >> 5) * mloc + lm] = fw;
+      if (active && (!PRE || flags)) flags[(size_t)(k >> 5) * mloc + lm] = fw;
       fw = 0;
     }
   }
   if constexpr (MODE == FWD_STORE) {
-    if (active) {   // the same count and closing step for the second control
+    if (active && (!PRE || jcnt)) {   // the same count and closing step for the second control
       jcnt[lm] = lw.r;
       jcnt[mloc + lm] = min(lw.kovf, Nt);
     }
@@ -1115,13 +1123,38 @@ __device__ __forceinline__ void fwd_body(const KParams<R, D, DU> &kp, int64_t bi
   Pair<R> v = cost.pair();
   if (!active) v = {R(0), R(0)};
   if (pcost && active) pcost[lm] = Ar<R>::add(v.s, v.e);
-  const double s = block_sum_to_double(v, red);
-  if (threadIdx.x == 0) partC[bid] = s;
-  if constexpr (PAIR) {
-    Pair<R> v2 = cost2.pair();
-    if (!active) v2 = {R(0), R(0)};
-    const double s2 = block_sum_to_double(v2, red);
-    if (threadIdx.x == 0) p2.partC[bid] = s2;
+  if constexpr (PRE) {   // the path's pair; spread_combine_kernel sums them
+    if (active) pd.cw[lm] = v;
+    if constexpr (PAIR) {
+      if (active) pd.cw2[lm] = cost2.pair();
+    }
+  } else {
+    const double s = block_sum_to_double(v, red);
+    if (threadIdx.x == 0) partC[bid] = s;
+    if constexpr (PAIR) {
+      Pair<R> v2 = cost2.pair();
+      if (!active) v2 = {R(0), R(0)};
+      const double s2 = block_sum_to_double(v2, red);
+      if (threadIdx.x == 0) p2.partC[bid] = s2;
+    }
+  }
+}
+
+// The cost partials of a spread sweep: block b of TPB threads takes the pairs of paths
+// b TPB .. b TPB + TPB - 1 (the zero pair past mloc, as an idle thread of the sweep has) and
+// sums them with block_sum_to_double, so partC[b] is the one-path-per-thread sweep's.
+template <typename R>
+__global__ void __launch_bounds__(TPB) spread_combine_kernel(const Pair<R> *__restrict__ cw,
+                                                             const Pair<R> *__restrict__ cw2, int64_t mloc,
+                                                             double *__restrict__ partC,
+                                                             double *__restrict__ partC2) {
+  __shared__ Pair<R> red[TPB / 32];
+  const int64_t lm = (int64_t)blockIdx.x * TPB + threadIdx.x;
+  for (int h = 0; h < (cw2 ? 2 : 1); ++h) {
+    const Pair<R> *w = h ? cw2 : cw;
+    const Pair<R> v = lm < mloc ? w[lm] : Pair<R>{R(0), R(0)};
+    const double s = block_sum_to_double(v, red);
+    if (threadIdx.x == 0) (h ? partC2 : partC)[blockIdx.x] = s;
   }
 }
 
@@ -1132,8 +1165,22 @@ fwd_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u
            uint32_t *__restrict__ flags, R *__restrict__ ckpt, R *__restrict__ pcost,
            JLog<R, D> jl, int *__restrict__ jcnt, int64_t mloc, PairOut<R, D> p2, PreDraws<R, D> pd = {}) {
   __shared__ Pair<R> red[TPB / 32];
-  fwd_body<R, D, DU, MODE, PAIR, PRE>(kp, blockIdx.x, u, xd, partC, traj, flags, ckpt, pcost, jl, jcnt, mloc, p2,
-                                      pd, red);
+  if constexpr (PAIR && PRE) {
+    // a pre-drawn pair: each control on its own warps (the first half of the blocks, then
+    // the second), each a single sweep -- the pair sweep's per-control arithmetic; the
+    // flags and log counts (the same for both) from the first control
+    const unsigned nb = gridDim.x / 2;
+    const bool second = blockIdx.x >= nb;
+    PreDraws<R, D> pd1 = pd;
+    if (second) pd1.cw = pd.cw2;
+    fwd_body<R, D, DU, MODE, false, true>(kp, second ? blockIdx.x - nb : blockIdx.x, second ? p2.u : u, xd, partC,
+                                          second ? p2.traj : traj, second ? nullptr : flags,
+                                          second ? p2.ckpt : ckpt, nullptr, second ? p2.jl : jl,
+                                          second ? nullptr : jcnt, mloc, PairOut<R, D>{}, pd1, red);
+  } else {
+    fwd_body<R, D, DU, MODE, PAIR, PRE>(kp, blockIdx.x, u, xd, partC, traj, flags, ckpt, pcost, jl, jcnt, mloc, p2,
+                                        pd, red);
+  }
 }
 
 // X_k of one path from the stored trajectory.
@@ -1641,33 +1688,39 @@ cudaError_t op_fwd(const jd_problem *p, int mode, int64_t m_begin, int64_t mloc,
   if constexpr (D <= 2) {
     if (b.pre_w) {   // a small problem: all main-stream draws in one parallel pass first
       R *pz = static_cast<R *>(b.pre_z), *ps = pz + (size_t)kp.Nt * D * mloc;
+      Pair<R> *cw = reinterpret_cast<Pair<R> *>(ps + (size_t)kp.Nt * (1 + 2 * D) * mloc);
       draws_kernel<R, D, DU><<<(unsigned)ceil_div((int64_t)kp.Nt * mloc, 256), 256, 0, s>>>(kp, mloc, b.pre_w,
                                                                                              pz, ps);
       count_launch();
-      const PreDraws<R, D> pd{b.pre_w, pz, ps};
+      const PreDraws<R, D> pd{b.pre_w, pz, ps, cw, cw + mloc};
+      // blocks of one warp with SPREAD_LANES paths; a pair's controls on separate blocks
+      const dim3 sgrid((unsigned)(ceil_div(mloc, SPREAD_LANES) * ((mode & FWD_PAIR) ? 2 : 1)));
       switch (mode) {
         case FWD_COST:
-          fwd_kernel<R, D, DU, FWD_COST, false, true><<<grid, TPB, 0, s>>>(
+          fwd_kernel<R, D, DU, FWD_COST, false, true><<<sgrid, SPREAD_TPB, 0, s>>>(
               kp, u, xd, b.partC, nullptr, nullptr, nullptr, pc, jl, nullptr, mloc, p2, pd);
           break;
         case FWD_STORE:
-          fwd_kernel<R, D, DU, FWD_STORE, false, true><<<grid, TPB, 0, s>>>(
+          fwd_kernel<R, D, DU, FWD_STORE, false, true><<<sgrid, SPREAD_TPB, 0, s>>>(
               kp, u, xd, b.partC, static_cast<R *>(b.traj), b.flags, nullptr, pc, jl, b.jcnt, mloc, p2, pd);
           break;
         case FWD_STORE | FWD_PAIR:
-          fwd_kernel<R, D, DU, FWD_STORE, true, true><<<grid, TPB, 0, s>>>(
+          fwd_kernel<R, D, DU, FWD_STORE, true, true><<<sgrid, SPREAD_TPB, 0, s>>>(
               kp, u, xd, b.partC, static_cast<R *>(b.traj), b.flags, nullptr, nullptr, jl, b.jcnt, mloc, p2, pd);
           break;
         case FWD_CKPT | FWD_PAIR:
-          fwd_kernel<R, D, DU, FWD_CKPT, true, true><<<grid, TPB, 0, s>>>(
+          fwd_kernel<R, D, DU, FWD_CKPT, true, true><<<sgrid, SPREAD_TPB, 0, s>>>(
               kp, u, xd, b.partC, nullptr, nullptr, static_cast<R *>(b.ckpt), nullptr, jl, nullptr, mloc, p2, pd);
           break;
         default:
-          fwd_kernel<R, D, DU, FWD_CKPT, false, true><<<grid, TPB, 0, s>>>(
+          fwd_kernel<R, D, DU, FWD_CKPT, false, true><<<sgrid, SPREAD_TPB, 0, s>>>(
               kp, u, xd, b.partC, nullptr, nullptr, static_cast<R *>(b.ckpt), pc, jl, nullptr, mloc, p2, pd);
           break;
       }
-      count_launch();
+      const bool pair = (mode & FWD_PAIR) != 0;
+      spread_combine_kernel<R><<<grid, TPB, 0, s>>>(cw, pair ? cw + mloc : nullptr, mloc, b.partC,
+                                                    pair ? b.partC2 : nullptr);
+      count_launch(2);
       return cudaGetLastError();
     }
   }
