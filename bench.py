@@ -153,12 +153,15 @@ FB_WORKLOADS = {"feedback_centering": workloads.feedback_centering,
                 "feedback_coupled": workloads.feedback_coupled}
 
 
-def bench_workload(M=None, Nt=None, name="double_well"):
+def bench_workload(M=None, Nt=None, name="double_well", keep_dt=False):
+    """The named workload, with M and N_t overridden when given; keep_dt shortens the
+    horizon with N_t so that the step length (and with it the jump rate per step, which
+    sets the kernels' instruction mix) stays the full workload's."""
     p = WORKLOADS[name]()
     if M is not None:
         p = p.replace(M=M)
     if Nt is not None:
-        p = p.replace(Nt=Nt)
+        p = p.replace(Nt=Nt, T=p.T * Nt / p.Nt) if keep_dt else p.replace(Nt=Nt)
     return p
 
 
@@ -310,9 +313,9 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     if args.shard:   # every rank works on the same sample
-        return run_shard(args, bench_workload(args.paths, args.steps_t, args.workload), stream, dist, ws, rank,
+        return run_shard(args, bench_workload(args.paths, args.steps_t, args.workload, args.keep_dt), stream, dist, ws, rank,
                          local)
-    p = replica_problem(bench_workload(args.paths, args.steps_t, args.workload), rank)
+    p = replica_problem(bench_workload(args.paths, args.steps_t, args.workload, args.keep_dt), rank)
     if args.workload == "double_well_autograd":
         return run_autograd(args, p, stream, dist, ws, rank, local)
     if args.workload in FB_WORKLOADS:
@@ -977,7 +980,14 @@ def adjoint_ops(p):
 # fingerprint of the kernel sources it was counted on; when the sources have changed
 # since, the entry is stale and the figures derived from it are reported as null.
 COUNTERS = {
-    # (workload, kernel): (fingerprint, DRAM bytes per path-step or None, warp-inst per warp-step)
+    # (workload, kernel): (fingerprint of the kernel sources, DRAM bytes per path-step or
+    # None, warp-instructions per warp-step), from single ncu captures of each kernel at
+    # full occupancy (M = 2^20, 8192 blocks) over N_t = 100 steps of the workload's own step
+    # length (--steps-t 100 --keep-dt): profiles/*_double_well_d2_M2p20_Nt100_dt2e-3.md
+    ("double_well", "fwd_pair"): ("3a5a235f26ef", 17.90, 358.7),
+    ("double_well", "fwd_store"): ("3a5a235f26ef", 8.59, 288.7),
+    ("double_well", "adj_stored"): ("3a5a235f26ef", 9.26, 72.7),
+    ("double_well", "adj_recompute"): ("3a5a235f26ef", 0.75, 354.6),
 }
 
 
@@ -1080,6 +1090,8 @@ def main():
                          "3 BF16x3 in the adjoint only")
     ap.add_argument("--paths", type=int, default=None, help="override M (paths per GPU)")
     ap.add_argument("--steps-t", type=int, default=None, help="override N_t")
+    ap.add_argument("--keep-dt", action="store_true",
+                    help="with --steps-t: shorten the horizon so that the step length stays the workload's")
     ap.add_argument("--reference-paths", type=int, default=1 << 14)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--particles", type=int, default=None,

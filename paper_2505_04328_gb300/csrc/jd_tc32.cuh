@@ -276,67 +276,6 @@ __device__ __forceinline__ uint32_t main_noise_or_jump(const KP32 &kp, int k, ui
 // Steps with jumps at d = 32 (linear drift)
 // ---------------------------------------------------------------------------
 
-// y_c += scale_c * Z_c for the main-stream normals of step k (words 1..32), where
-// scale_c = sigma_c * s (s = sqrt of the sub-step length).
-__device__ __forceinline__ void add_main_noise_scaled(const KP32 &kp, int k, uint32_t m, float s, float (&y)[32]) {
-  uint32_t carry = 0;
-#pragma unroll
-  for (int b = 0; b < 9; ++b) {
-    const uint4 o = philox10((uint32_t)k, m, (uint32_t)b, kp.epoch, kp.key0, kp.key1);
-    const uint32_t w[4] = {o.x, o.y, o.z, o.w};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int j = 4 * b + q;
-      if (j == 0 || j > 32) continue;
-      if (j & 1) {
-        carry = w[q];
-      } else {
-        float z0, z1;
-        normal_pair<float>(carry, w[q], z0, z1);
-        const int c = j - 2;
-        y[c] = __fmaf_rn(__fmul_rn(kp.sigma[c], s), z0, y[c]);
-        y[c + 1] = __fmaf_rn(__fmul_rn(kp.sigma[c + 1], s), z1, y[c + 1]);
-      }
-    }
-  }
-}
-
-// Words [first, first + 32) of jump slot 0 of step k decoded into 32 values added to y:
-// sizes (first = 1): y_c += jump_scale * xi_c; post-jump normals (first = 33):
-// y_c += sigma_c * s * Z_c.  Valid for d >= 31 (16 normal pairs per slot).
-template <bool SIZES>
-__device__ __forceinline__ void add_slot0_words(const KP32 &kp, int k, uint32_t m, float s, float (&y)[32]) {
-  constexpr int first = SIZES ? 1 : 33;
-  const uint32_t tag = (1u << 24) | (1u << 16);
-  uint32_t carry = 0;
-#pragma unroll
-  for (int b = first / 4; b <= (first + 31) / 4; ++b) {
-    const uint4 o = philox10((uint32_t)k, m, tag | (uint32_t)b, kp.epoch, kp.key0, kp.key1);
-    const uint32_t w[4] = {o.x, o.y, o.z, o.w};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int j = 4 * b + q;
-      if (j < first || j >= first + 32) continue;
-      const int i = j - first;   // value index 0..31
-      if (SIZES && kp.jump_law == JD_JUMP_UNIFORM) {
-        y[i] = __fadd_rn(y[i], __fmul_rn(kp.jump_scale, __fsub_rn(__fmul_rn(2.f, Ar<float>::u01(w[q])), 1.f)));
-      } else if ((i & 1) == 0) {
-        carry = w[q];
-      } else {
-        float z0, z1;
-        normal_pair<float>(carry, w[q], z0, z1);
-        if (SIZES) {
-          y[i - 1] = __fadd_rn(y[i - 1], __fmul_rn(kp.jump_scale, z0));
-          y[i] = __fadd_rn(y[i], __fmul_rn(kp.jump_scale, z1));
-        } else {
-          y[i - 1] = __fmaf_rn(__fmul_rn(kp.sigma[i - 1], s), z0, y[i - 1]);
-          y[i] = __fmaf_rn(__fmul_rn(kp.sigma[i], s), z1, y[i]);
-        }
-      }
-    }
-  }
-}
-
 // y += de * (f + B u_k)
 __device__ __forceinline__ void add_drift(const KP32 &kp, const float *__restrict__ u, int k, float de,
                                           const float (&f)[32], float (&y)[32]) {
@@ -370,33 +309,113 @@ __device__ __forceinline__ void regen_jump_times(const KP32 &kp, int k, uint32_t
   }
 }
 
-// One-jump step of the forward, out of line (its streamed draws would crowd the
-// instruction cache of the main loop): sub-step 0 with this step's A x (f), the jump,
-// sub-step 1 with A Y_1 on the CUDA cores.  x holds X_k on entry and X_{k+1} on exit;
-// y1 receives the post-jump state for the jump log.
-__device__ __noinline__ float fwd32_one_jump(const KP32 &kp, const float *at, float *vcol, int k, uint32_t m,
-                                             const float *__restrict__ u, float *xio, const float *fin,
-                                             float *y1) {
-  float x[32], f[32];
+// One-jump steps of a warp (linear drift, d = 32), done by the whole warp.  The step of
+// a lane with one jump at fraction th (word 0 of jump slot 0): sub-step 0 of length
+// d0 = dt th from X_k with the step's main-stream normals (words 1..32, pair p of
+// components (2p, 2p + 1) from words (2p + 1, 2p + 2)) scaled by sigma_c sqrt(d0) and the
+// drift f = A X_k + B u_k; the jump Y_1 = Y + jump_scale xi (sizes xi from slot-0 words
+// 1..32: normal pairs, or 2 u - 1 per word for the uniform law); sub-step 1 of length
+// d1 = dt (1 - th) from Y_1 with the post-jump normals (slot-0 words 33..64) and the drift
+// A Y_1 + B u_k.  For each such lane the 32 lanes draw its Philox blocks (the 9 of its
+// main stream and the 17 of its slot) in one round and its 48 Box-Muller pairs in two,
+// and then carry one component each through the step's arithmetic (A Y_1 in k order from
+// zero, as cc_matvec); every component gets the operations of the one-lane routine in the
+// same order, so the same bits.  A lane alone drew 27 blocks and 48 pairs and did all 32
+// components while its warp (and, with the tensor cores, its CTA at the next step's
+// barrier) waited; here it only hands over X_k and A X_k and takes X_{k+1} and Y_1 back.
+// ws: the warp's 32 x TPB floats of vbuf, free at this point of the step (rows: 0-1 main
+// words, 2-4 slot words, 5 main normals, 6 jump sizes, 7 post-jump normals, 8 Y_1, 9 X,
+// 10 A X_k).  Called by every lane of the warp; returns th in the jump lanes.
+__device__ __forceinline__ float coop_one_jumps(const KP32 &kp, const float *at, float *ws, int k, uint32_t m,
+                                                const float *__restrict__ u, unsigned om, float (&x)[32],
+                                                const float (&f)[32], float (&y1)[32]) {
+  const int lane = threadIdx.x & 31;
+  uint32_t *wu = reinterpret_cast<uint32_t *>(ws);
+  auto mword = [&](int w) -> uint32_t & { return wu[(w >> 5) * TPB + (w & 31)]; };
+  auto sword = [&](int w) -> uint32_t & { return wu[(2 + (w >> 5)) * TPB + (w & 31)]; };
+  float *zm = ws + 5 * TPB, *zs = ws + 6 * TPB, *zp = ws + 7 * TPB, *yv = ws + 8 * TPB, *xv = ws + 9 * TPB,
+        *fv = ws + 10 * TPB;
+  const uint32_t tag = (1u << 24) | (1u << 16);   // jump slot 0
+  const bool sizes_normal = kp.jump_law != JD_JUMP_UNIFORM;
+  float th_out = 0.f;
+  while (om) {
+    const int j = __ffs(om) - 1;
+    om &= om - 1;
+    const uint32_t mj = __shfl_sync(0xffffffffu, m, j);
+    if (lane < 26) {   // lanes 0..8: main blocks 0..8; lanes 9..25: slot blocks 0..16
+      const bool slot = lane >= 9;
+      const uint32_t b = slot ? (uint32_t)(lane - 9) : (uint32_t)lane;
+      const uint4 o = philox10((uint32_t)k, mj, slot ? (tag | b) : b, kp.epoch, kp.key0, kp.key1);
+      const int w = 4 * (int)b;
+      if (slot) {
+        sword(w) = o.x;
+        sword(w + 1) = o.y;
+        sword(w + 2) = o.z;
+        sword(w + 3) = o.w;
+      } else {
+        mword(w) = o.x;
+        mword(w + 1) = o.y;
+        mword(w + 2) = o.z;
+        mword(w + 3) = o.w;
+      }
+    }
+    if (lane == j) {   // X_k and A X_k of the jump lane
 #pragma unroll
-  for (int c = 0; c < 32; ++c) {
-    x[c] = xio[c];
-    f[c] = fin[c];
+      for (int c = 0; c < 32; ++c) {
+        xv[c] = x[c];
+        fv[c] = f[c];
+      }
+    }
+    __syncwarp();
+    {   // pair p of components (2p, 2p + 1) takes words (2p + 1, 2p + 2) of its set
+      float z0, z1;
+      if (lane < 16) {
+        normal_pair<float>(mword(2 * lane + 1), mword(2 * lane + 2), z0, z1);
+        zm[2 * lane] = z0;
+        zm[2 * lane + 1] = z1;
+        normal_pair<float>(sword(2 * lane + 33), sword(2 * lane + 34), z0, z1);
+        zp[2 * lane] = z0;
+        zp[2 * lane + 1] = z1;
+      } else if (sizes_normal) {
+        const int q = lane - 16;
+        normal_pair<float>(sword(2 * q + 1), sword(2 * q + 2), z0, z1);
+        zs[2 * q] = z0;
+        zs[2 * q + 1] = z1;
+      }
+    }
+    __syncwarp();
+    // component c = lane of the jump lane's step
+    const int c = lane;
+    const float th = Ar<float>::u01(sword(0));
+    const float d0 = __fmul_rn(kp.dt, th), d1 = __fmul_rn(kp.dt, __fsub_rn(1.f, th));
+    float bc = 0.f;
+#pragma unroll
+    for (int l = 0; l < DU32; ++l) bc = __fmaf_rn(kp.B[c * DU32 + l], __ldg(u + (size_t)k * DU32 + l), bc);
+    float xc = __fmaf_rn(__fmul_rn(kp.sigma[c], __fsqrt_rn(d0)), zm[c], xv[c]);
+    xc = __fmaf_rn(d0, __fadd_rn(fv[c], bc), xc);
+    if (sizes_normal)
+      xc = __fadd_rn(xc, __fmul_rn(kp.jump_scale, zs[c]));
+    else
+      xc = __fadd_rn(xc, __fmul_rn(kp.jump_scale, __fsub_rn(__fmul_rn(2.f, Ar<float>::u01(sword(1 + c))), 1.f)));
+    yv[c] = xc;
+    __syncwarp();
+    float acc = 0.f;   // (A Y_1)_c
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) acc = __fmaf_rn(at[kk * 32 + c], yv[kk], acc);
+    xc = __fmaf_rn(__fmul_rn(kp.sigma[c], __fsqrt_rn(d1)), zp[c], xc);
+    xv[c] = __fmaf_rn(d1, __fadd_rn(acc, bc), xc);
+    __syncwarp();
+    if (lane == j) {
+#pragma unroll
+      for (int cc = 0; cc < 32; ++cc) {
+        x[cc] = xv[cc];
+        y1[cc] = yv[cc];
+      }
+      th_out = th;
+    }
+    __syncwarp();   // the scratch is the next jump lane's
   }
-  const float th =
-      Ar<float>::u01(philox10((uint32_t)k, m, (1u << 24) | (1u << 16), kp.epoch, kp.key0, kp.key1).x);
-  const float d0 = __fmul_rn(kp.dt, th), d1 = __fmul_rn(kp.dt, __fsub_rn(1.f, th));
-  add_main_noise_scaled(kp, k, m, __fsqrt_rn(d0), x);
-  add_drift(kp, u, k, d0, f, x);
-  add_slot0_words<true>(kp, k, m, 0.f, x);
-#pragma unroll
-  for (int c = 0; c < 32; ++c) y1[c] = x[c];
-  cc_matvec(at, vcol, x, f);
-  add_slot0_words<false>(kp, k, m, __fsqrt_rn(d1), x);
-  add_drift(kp, u, k, d1, f, x);
-#pragma unroll
-  for (int c = 0; c < 32; ++c) xio[c] = x[c];
-  return th;
+  return th_out;
 }
 
 // bu[k][c] = sum_l B[c][l] u_k[l] (FP32, multiply-adds in the order l = 0..3 from zero):
@@ -422,8 +441,7 @@ fwd32_kernel(const KP32 *__restrict__ kpg, const float *__restrict__ u, const fl
   constexpr bool SPLIT = TC == 2;
   __shared__ __align__(1024) TcShared sh;
   __shared__ __align__(16) CcShared cs;
-  __shared__ __align__(16) float vbuf[32 * TPB];   // product staging (CUDA cores, jump sub-steps)
-  float *const vbuf_j = vbuf;
+  __shared__ __align__(16) float vbuf[32 * TPB];   // product staging (CUDA cores, jump steps)
   __shared__ Pair<float> red[TPB / 32];
   stage_params(cs, kpg);
   const KP32 &kp = cs.kp;
@@ -464,6 +482,7 @@ fwd32_kernel(const KP32 *__restrict__ kpg, const float *__restrict__ u, const fl
     bool jump;
     const uint32_t w0 = main_noise_or_jump(kp, k, m, x, vbuf + threadIdx.x, jump);   // x += noise unless jump
     if (TC) tc_collect(sh, (uint32_t)(k & 1), f, status);
+    const bool one = jump && kp.npair == 16 && (unsigned long long)w0 < kp.thr[1];
     if (!jump) {
       const float4 *b4 = reinterpret_cast<const float4 *>(bu + (size_t)k * 32);
 #pragma unroll
@@ -474,24 +493,17 @@ fwd32_kernel(const KP32 *__restrict__ kpg, const float *__restrict__ u, const fl
         Pr<float>::fma(kp.dt, kp.dt, s01.x, s01.y, x[4 * q], x[4 * q + 1]);
         Pr<float>::fma(kp.dt, kp.dt, s23.x, s23.y, x[4 * q + 2], x[4 * q + 3]);
       }
-    } else if (kp.npair == 16 && (unsigned long long)w0 < kp.thr[1]) {
-      fw |= 1u << (k & 31);
-      float xl[32], fl[32], yl[32];
-#pragma unroll
-      for (int c = 0; c < 32; ++c) {
-        xl[c] = x[c];
-        fl[c] = f[c];
+    }
+    const unsigned om = __ballot_sync(0xffffffffu, one);   // every lane of the warp is in the loop
+    if (__builtin_expect(om != 0u, 0)) {
+      float y1[32];
+      const float th = coop_one_jumps(kp, cs.at, vbuf + (threadIdx.x & ~31u), k, m, u, om, x, f, y1);
+      if (one) {
+        fw |= 1u << (k & 31);
+        if (lw.fits(1)) lw.put(k, 0, th, y1);
       }
-      const float th = fwd32_one_jump(kp, cs.at, vbuf_j + threadIdx.x, k, m, u, xl, fl, yl);
-      if (lw.fits(1)) {
-        float y[32];
-#pragma unroll
-        for (int c = 0; c < 32; ++c) y[c] = yl[c];
-        lw.put(k, 0, th, y);
-      }
-#pragma unroll
-      for (int c = 0; c < 32; ++c) x[c] = xl[c];
-    } else {
+    }
+    if (jump && !one) {
       // two or more jumps (rare): the generic routine on the CUDA cores (x is X_k)
       fw |= 1u << (k & 31);
       JumpStep<float, D32> S;
