@@ -586,6 +586,33 @@ __device__ __noinline__ void adj32_jump_substeps(const KP32 &kp, float *vcol, in
   for (int l = 0; l < DU32; ++l) gout[l] = g[l];
 }
 
+// mu <- mu + de (A^T mu) for every lane of om, the product formed by the whole warp: the
+// lane's costate goes to the warp's scratch (row 0 of ws, its 32 x TPB floats of vbuf)
+// and lane c forms component c in cc_matvec's order (k from 0, from zero), into row 1.
+__device__ __forceinline__ void coop_adj_product(const float *A, float *ws, unsigned om, float de, float (&mu)[32]) {
+  const int lane = threadIdx.x & 31;
+  float *mv = ws, *tv = ws + TPB;
+  while (om) {
+    const int j = __ffs(om) - 1;
+    om &= om - 1;
+    if (lane == j) {
+#pragma unroll
+      for (int c = 0; c < 32; ++c) mv[c] = mu[c];
+    }
+    __syncwarp();
+    float acc = 0.f;
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) acc = __fmaf_rn(A[kk * 32 + lane], mv[kk], acc);
+    tv[lane] = acc;
+    __syncwarp();
+    if (lane == j) {
+#pragma unroll
+      for (int c = 0; c < 32; ++c) mu[c] = __fmaf_rn(de, tv[c], mu[c]);
+    }
+    __syncwarp();   // the scratch is the next lane's
+  }
+}
+
 template <int TC>
 __global__ void __launch_bounds__(TPB, 4)
 adj32_kernel(const KP32 *__restrict__ kpg, const float *__restrict__ u, const float *__restrict__ xd,
@@ -654,18 +681,50 @@ adj32_kernel(const KP32 *__restrict__ kpg, const float *__restrict__ u, const fl
       control_sensitivity(kp, mu, kp.dt, g);
 #pragma unroll
       for (int c = 0; c < 32; c += 2) Pr<float>::fma(kp.dt, kp.dt, t[c], t[c + 1], mu[c], mu[c + 1]);
-    } else {
-      float ml[32], tl[32], gl[DU32];
+    }
+    // CUDA cores: a step with one jump at fraction th takes sub-step 1 (length dt (1 - th))
+    // with this step's product, then sub-step 0 (length dt th) with A^T of the updated
+    // costate, formed by the whole warp one component per lane (cc_matvec's order: the same
+    // bits); a step with more jumps, and every jump step with the tensor cores, takes the
+    // one-lane routine (measured: the warp-wide form there slowed the jump-free steps more,
+    // 5.8 -> 6.9 ms per sweep, than it saved on the jump steps)
+    bool one = false;
+    float de0 = 0.f;
+    if (jumped) {
+      const uint32_t w0 = TC == 0 ? philox10((uint32_t)k, m, 0u, kp.epoch, kp.key0, kp.key1).x : 0xffffffffu;
+      one = TC == 0 && (unsigned long long)w0 < kp.thr[1];
+      if (one) {
+        float th;
+        if (lr.has(k)) {
+          float ylog[32];
+          lr.pop(th, ylog);
+        } else {
+          th = Ar<float>::u01(
+              philox10((uint32_t)k, m, (1u << 24) | (1u << 16), kp.epoch, kp.key0, kp.key1).x);
+        }
+        const float de1 = __fmul_rn(kp.dt, __fsub_rn(1.f, th));
+        control_sensitivity(kp, mu, de1, g);
 #pragma unroll
-      for (int c = 0; c < 32; ++c) {
-        ml[c] = mu[c];
-        tl[c] = t[c];
+        for (int c = 0; c < 32; ++c) mu[c] = __fmaf_rn(de1, t[c], mu[c]);
+        de0 = __fmul_rn(kp.dt, th);
+        control_sensitivity(kp, mu, de0, g);
+      } else {
+        float ml[32], tl[32], gl[DU32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          ml[c] = mu[c];
+          tl[c] = t[c];
+        }
+        adj32_jump_substeps(kp, vbuf + threadIdx.x, k, m, &lr, ml, tl, gl);
+#pragma unroll
+        for (int c = 0; c < 32; ++c) mu[c] = ml[c];
+#pragma unroll
+        for (int l = 0; l < DU32; ++l) g[l] = gl[l];
       }
-      adj32_jump_substeps(kp, vbuf + threadIdx.x, k, m, &lr, ml, tl, gl);
-#pragma unroll
-      for (int c = 0; c < 32; ++c) mu[c] = ml[c];
-#pragma unroll
-      for (int l = 0; l < DU32; ++l) g[l] = gl[l];
+    }
+    if constexpr (TC == 0) {
+      const unsigned om = __ballot_sync(0xffffffffu, one);   // every lane of the warp is in the loop
+      if (__builtin_expect(om != 0u, 0)) coop_adj_product(kp.A, vbuf + (threadIdx.x & ~31u), om, de0, mu);
     }
     if (k >= 1) {
       // cost gradient dt q (X_k - xd_k), the stored state streamed 4 components at a time
