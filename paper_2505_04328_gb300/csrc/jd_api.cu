@@ -540,6 +540,7 @@ static PathBufs plan_bufs(const jd_problem *p) {
   b.status = reinterpret_cast<int *>(p->scal_d + S_STATUS);
   b.pre_w = p->pre_w;
   b.pre_z = p->pre_z;
+  b.pre_key = p->pre_key;
   return b;
 }
 
@@ -1415,6 +1416,7 @@ jd_status jd_problem_destroy(jd_problem *p) {
   free_dev(p, p->units);
   free_dev(p, p->pre_w);
   free_dev(p, p->pre_z);
+  free_dev(p, p->pre_key);
   free_dev(p, p->partT);
   free_dev(p, p->traj);
   free_dev(p, p->flags);
@@ -1557,6 +1559,11 @@ jd_status jd::create_problem(const jd_problem_desc &q, const jd::ProblemOpts &op
   if (!opts.no_pre && pre_pass(q.d, q.Nt, q.M, es)) {   // a small problem: the draws' pre-pass buffers
     ALLOC(p->pre_w, (size_t)q.Nt * q.M * 4, "pre-drawn Poisson words");
     ALLOC(p->pre_z, pre_z_values(q.Nt, p->D, q.M) * es, "pre-drawn normals and slot draws");
+    ALLOC(p->pre_key, sizeof(unsigned long long), "pre-drawn key");
+    if (cudaMemsetAsync(p->pre_key, 0, sizeof(unsigned long long), p->stream) != cudaSuccess) {
+      jd_problem_destroy(p);
+      return cuda_fail(cudaGetLastError(), "clearing the pre-drawn key");
+    }
   }
   ALLOC(p->opt_u, nu * 8, "optimizer iterate");
   ALLOC(p->opt_ut, nu * 8, "optimizer trial");

@@ -66,6 +66,10 @@ struct PathBufs {
   // sweeps' per-path cost pairs [2][mloc]; null = the sweep draws them itself
   uint32_t *pre_w = nullptr;
   void *pre_z = nullptr;
+  // key of the draws the pre-pass buffers hold (0: none): the draws depend on the generator's
+  // key, epoch and path range and on the jump thresholds only, not on the control, so a sweep
+  // with the same key reuses them (the draws kernel returns at once)
+  unsigned long long *pre_key = nullptr;
   // partial-stride override: a launch that covers one block of the paths (chunked
   // stored plan) writes its partials at their global positions (partG, partC offset
   // by the caller) with the stride of all M paths; 0 = this launch's own count
@@ -140,7 +144,8 @@ inline size_t pre_z_values(int Nt, int D, int64_t M) {
   return (size_t)Nt * (1 + 3 * D) * (size_t)M + 4 * (size_t)M;
 }
 inline size_t pre_bytes(int Nt, int D, int64_t M, size_t es) {
-  return (size_t)Nt * (size_t)M * 4 + pre_z_values(Nt, D, M) * es;   // words, normals, slot-0 draws
+  // words; normals, slot-0 draws and cost pairs; the key of the draws held
+  return (size_t)Nt * (size_t)M * 4 + pre_z_values(Nt, D, M) * es + sizeof(unsigned long long);
 }
 inline bool pre_pass(int d, int Nt, int64_t M, size_t es) {
   const int D = d <= 1 ? 1 : 2;
@@ -226,8 +231,9 @@ struct jd_problem {
   size_t budget = 0;
   jd_adjoint_mode plan = JD_ADJ_AUTO;
   int S = 16;                // recompute plan: steps per checkpoint segment (16, 32 or 64)
-  uint32_t *pre_w = nullptr; // draw pre-pass buffers of a small problem (PathBufs::pre_w, pre_z)
-  void *pre_z = nullptr;
+  uint32_t *pre_w = nullptr; // draw pre-pass buffers of a small problem (PathBufs::pre_w, pre_z,
+  void *pre_z = nullptr;     // pre_key)
+  unsigned long long *pre_key = nullptr;
   bool fwd_valid = false;   // stored states / checkpoints belong to u_in (jd_forward)
   // device buffers
   void *uk = nullptr;        // kernel-precision padded control, Nt*DU

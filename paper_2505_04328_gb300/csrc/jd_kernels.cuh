@@ -953,7 +953,9 @@ __device__ __forceinline__ void stage_state(R *__restrict__ traj, int k, int Nt,
 template <typename R, int D, int DU>
 __global__ void __launch_bounds__(256)
 draws_kernel(const __grid_constant__ KParams<R, D, DU> kp, int64_t mloc, uint32_t *__restrict__ w,
-             R *__restrict__ z, R *__restrict__ s) {
+             R *__restrict__ z, R *__restrict__ s, const unsigned long long *__restrict__ held,
+             unsigned long long key) {
+  if (*held == key) return;   // the buffers hold these draws already
   const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
   if (i >= (int64_t)kp.Nt * mloc) return;
   const int k = (int)(i / mloc);
@@ -983,6 +985,7 @@ struct PreDraws {
   const R *s;          // [Nt][1 + 2D][mloc] a step with exactly one (additive) jump: its
                        // slot-0 draws (time fraction, unit size, next normals); else unset
   Pair<R> *cw, *cw2;   // [mloc] each path's cost pair (first, second control)
+  unsigned long long *held, key;   // the sweep records that the buffers hold the draws of key
 };
 
 // A step with one jump, its slot draws pre-drawn: sub-step to the jump, jump, sub-step.
@@ -1124,6 +1127,7 @@ __device__ __forceinline__ void fwd_body(const KParams<R, D, DU> &kp, int64_t bi
   if (!active) v = {R(0), R(0)};
   if (pcost && active) pcost[lm] = Ar<R>::add(v.s, v.e);
   if constexpr (PRE) {   // the path's pair; spread_combine_kernel sums them
+    if (bid == 0 && threadIdx.x == 0) *pd.held = pd.key;   // the draws kernel has completed
     if (active) pd.cw[lm] = v;
     if constexpr (PAIR) {
       if (active) pd.cw2[lm] = cost2.pair();
@@ -1669,6 +1673,30 @@ void make_kparams(const jd_problem *p, int64_t m_begin, int64_t mloc, KParams<R,
   kp.npart = grad_parts(mloc);
 }
 
+// Key of the pre-drawn draws of a launch: everything they depend on (the generator's key
+// and epoch, the first path and the path count, N_t, d, the jump law and its Poisson
+// thresholds), mixed into 64 bits; never 0 (the key of empty buffers).
+template <typename R, int D, int DU>
+unsigned long long draws_key(const KParams<R, D, DU> &kp, int64_t mloc) {
+  unsigned long long h = 0x9e3779b97f4a7c15ull;
+  auto mix = [&h](unsigned long long v) {
+    h ^= v + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+    h *= 0xff51afd7ed558ccdull;
+    h ^= h >> 33;
+  };
+  mix(kp.key0);
+  mix(kp.key1);
+  mix(kp.epoch);
+  mix((unsigned long long)kp.m_begin);
+  mix((unsigned long long)mloc);
+  mix((unsigned long long)kp.Nt);
+  mix((unsigned long long)kp.d);
+  mix((unsigned long long)kp.jump_law);
+  mix((unsigned long long)kp.jumps_on);
+  for (int n = 0; n < NMAX; ++n) mix(kp.thr[n]);
+  return h | 1ull;
+}
+
 template <typename R, int D, int DU>
 cudaError_t op_fwd(const jd_problem *p, int mode, int64_t m_begin, int64_t mloc, const void *uk,
                    const PathBufs &b, cudaStream_t s) {
@@ -1689,10 +1717,11 @@ cudaError_t op_fwd(const jd_problem *p, int mode, int64_t m_begin, int64_t mloc,
     if (b.pre_w) {   // a small problem: all main-stream draws in one parallel pass first
       R *pz = static_cast<R *>(b.pre_z), *ps = pz + (size_t)kp.Nt * D * mloc;
       Pair<R> *cw = reinterpret_cast<Pair<R> *>(ps + (size_t)kp.Nt * (1 + 2 * D) * mloc);
-      draws_kernel<R, D, DU><<<(unsigned)ceil_div((int64_t)kp.Nt * mloc, 256), 256, 0, s>>>(kp, mloc, b.pre_w,
-                                                                                             pz, ps);
+      const unsigned long long key = draws_key(kp, mloc);
+      draws_kernel<R, D, DU><<<(unsigned)ceil_div((int64_t)kp.Nt * mloc, 256), 256, 0, s>>>(
+          kp, mloc, b.pre_w, pz, ps, b.pre_key, key);
       count_launch();
-      const PreDraws<R, D> pd{b.pre_w, pz, ps, cw, cw + mloc};
+      const PreDraws<R, D> pd{b.pre_w, pz, ps, cw, cw + mloc, b.pre_key, key};
       // blocks of one warp with SPREAD_LANES paths; a pair's controls on separate blocks
       const dim3 sgrid((unsigned)(ceil_div(mloc, SPREAD_LANES) * ((mode & FWD_PAIR) ? 2 : 1)));
       switch (mode) {
