@@ -273,10 +273,11 @@ jd_status jd_problem_footprint(const jd_problem_desc *desc, jd_adjoint_mode plan
  *   whatever else runs; the kernels of all active requests overlap.  Large requests run
  *   on their own stream.  Small ones (d <= 2, du = 1, the stored plan, M at most the
  *   batching limit) share launches (the paper's Algorithm 5.4 per request, its gradient
- *   evaluations batched): each optimizer phase of up to 16 such requests with the same
- *   phase kind, precision and dimension is one launch sequence -- one forward and one
- *   adjoint sweep over all their paths, one launch per reduction and per optimizer
- *   step -- in which every problem's blocks compute what its own launches would.
+ *   evaluations batched): the pending optimizer phases (gradient or line-search trial)
+ *   of up to 16 such requests with the same precision and dimension are one launch
+ *   sequence -- forward sweeps (single and paired) and one adjoint sweep over all their
+ *   paths, one launch per reduction and per optimizer step -- in which every problem's
+ *   blocks compute what its own launches would.
  * jd_server_poll: JD_ERR_BUSY while the request runs; then JD_OK with r (the request's
  *   own status in r->status) and, if u_out is not NULL, the final control (Nt*du host
  *   doubles), which is handed out once (a second poll with u_out fails with INVALID_ARG).

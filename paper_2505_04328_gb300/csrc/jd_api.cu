@@ -357,6 +357,7 @@ __global__ void opt_accept_kernel(int n, double *__restrict__ u, const double *_
 // ---------------------------------------------------------------------------
 struct OptBatchItem {
   int n, Nt, du, DU;
+  int trial;                      // a trial phase (else a gradient phase)
   int fwd;                        // gradient phase with its forward sweep: the control into uk
   double dt, lo, hi, c, zeta;
   double *u, *grad, *ut, *ut2;    // ut2: the second point of a paired trial (else null)
@@ -368,21 +369,19 @@ struct OptBatch {
   OptBatchItem it[kBatchMax];
 };
 
-// Gradient phase, before the sweeps: clear the status word and the non-finite flag (the
-// bytes of clear_bad's memset); with the forward sweep, the control in kernel precision.
+// Before the sweeps, one block per problem.  Gradient phase: clear the status word and
+// the non-finite flag (the bytes of clear_bad's memset); with the forward sweep, the
+// control in kernel precision.  Trial phase: the trial point(s) and their products
+// (opt_trial at the machine's zeta), then the point(s) in kernel precision.
 template <typename R>
-__global__ void opt_grad_pre_batch_kernel(const __grid_constant__ OptBatch t) {
-  const OptBatchItem &b = t.it[blockIdx.x];
-  if (threadIdx.x < 2) b.scal[S_STATUS + threadIdx.x] = 0.0;
-  if (b.fwd) prep_u_block<R>(b.u, b.Nt, b.du, b.DU, static_cast<R *>(b.uk));
-}
-
-// Trial phase, before the sweep: the trial point(s) and their products (opt_trial at the
-// machine's zeta), then the point(s) in kernel precision.
-template <typename R>
-__global__ void opt_trial_pre_batch_kernel(const __grid_constant__ OptBatch t) {
+__global__ void opt_pre_batch_kernel(const __grid_constant__ OptBatch t) {
   __shared__ double sm[32];
   const OptBatchItem &b = t.it[blockIdx.x];
+  if (!b.trial) {
+    if (threadIdx.x < 2) b.scal[S_STATUS + threadIdx.x] = 0.0;
+    if (b.fwd) prep_u_block<R>(b.u, b.Nt, b.du, b.DU, static_cast<R *>(b.uk));
+    return;
+  }
   if (threadIdx.x == 0) b.scal[S_ZETA] = b.zeta;
   opt_trial_body(b.n, b.u, b.grad, b.zeta, b.dt, b.lo, b.hi, b.ut, b.scal + S_DOT, b.ut2, b.scal + S_DOT2, sm);
   __syncthreads();
@@ -390,16 +389,15 @@ __global__ void opt_trial_pre_batch_kernel(const __grid_constant__ OptBatch t) {
   if (b.ut2) prep_u_block<R>(b.ut2, b.Nt, b.du, b.DU, static_cast<R *>(b.uk2));
 }
 
-__global__ void opt_grad_post_batch_kernel(const __grid_constant__ OptBatch t) {
+// After the reductions, one block per problem: the projected-gradient norm (gradient
+// phase) or the Armijo test (trial phase).
+__global__ void opt_post_batch_kernel(const __grid_constant__ OptBatch t) {
   __shared__ double sm[32];
   const OptBatchItem &b = t.it[blockIdx.x];
-  opt_pgnorm_body(b.n, b.u, b.grad, b.dt, b.lo, b.hi, b.scal + S_PG, sm);
-}
-
-__global__ void opt_trial_post_batch_kernel(const __grid_constant__ OptBatch t) {
-  __shared__ double sm[32];
-  const OptBatchItem &b = t.it[blockIdx.x];
-  opt_accept_body(b.n, b.u, b.ut, b.ut2, b.c, b.dt, b.scal, sm);
+  if (b.trial)
+    opt_accept_body(b.n, b.u, b.ut, b.ut2, b.c, b.dt, b.scal, sm);
+  else
+    opt_pgnorm_body(b.n, b.u, b.grad, b.dt, b.lo, b.hi, b.scal + S_PG, sm);
 }
 
 // The job of a block of a batched reduction: first[i] <= blockIdx.x < first[i + 1].
@@ -1208,21 +1206,23 @@ bool jd::opt_batchable(jd_problem *p) {
          !p->chunk;
 }
 
+// Machines with the same key (precision and compiled dimension) share launches whatever
+// their phases.
 int jd::opt_batch_key(const OptMachine &m) {
   if (m.want == OptMachine::IDLE) return -1;
-  const int kind = m.want == OptMachine::GRAD ? (m.want_fwd ? 0 : 1) : (m.want_pair ? 3 : 2);
-  return kind + 4 * (m.p->D + 4 * (m.p->desc.prec == JD_FP64 ? 1 : 0));
+  return m.p->D + 4 * (m.p->desc.prec == JD_FP64 ? 1 : 0);
 }
 
 // The deferred phases of machines with one batch key: the work of enqueue_grad or
-// enqueue_trial for each, in shared launches (optimizer bodies one block per problem,
-// sweeps and reductions over the blocks of all problems), then each machine's scalars to
-// its pinned buffer and its event.
+// enqueue_trial for each, in shared launches -- one optimizer block per problem before
+// and after, one forward sweep over the blocks of the problems whose phase has a single
+// forward (a trial, or a gradient without a kept forward), one over those with a paired
+// trial, one adjoint sweep over the gradient phases' problems (after their forward, in
+// stream order), one launch for all unit sums and one for all combines -- then each
+// machine's scalars to its pinned buffer and its event.
 jd_status jd::opt_launch_batch(OptMachine *const *ms, int n, cudaStream_t st) {
   if (n < 1 || n > kBatchMax) return fail(JD_ERR_INVALID_ARG, "batch size");
   const int key = opt_batch_key(*ms[0]);
-  const OptMachine::Phase kind = ms[0]->want;
-  const bool fwd = ms[0]->want_fwd, pair = ms[0]->want_pair;
   const PathOps *ops = ms[0]->p->ops;
   for (int i = 0; i < n; ++i) {
     OptMachine &m = *ms[i];
@@ -1239,7 +1239,8 @@ jd_status jd::opt_launch_batch(OptMachine *const *ms, int n, cudaStream_t st) {
   const bool f64 = ops->elem == 8;
   OptBatch ob;
   ob.n = n;
-  BatchSweep sw[kBatchMax];
+  BatchSweep fs[kBatchMax], fp[kBatchMax], ad[kBatchMax];   // single forward, paired forward, adjoint
+  int nfs = 0, nfp = 0, nad = 0;
   UnitBatch ub;
   CombineBatch cb;
   ub.n = cb.n = 0;
@@ -1263,7 +1264,10 @@ jd_status jd::opt_launch_batch(OptMachine *const *ms, int n, cudaStream_t st) {
     OptMachine &m = *ms[i];
     jd_problem *p = m.p;
     const jd_problem_desc &q = p->desc;
+    const OptMachine::Phase kind = m.want;
+    const bool fwd = m.want_fwd, pair = m.want_pair;
     OptBatchItem &b = ob.it[i];
+    b.trial = kind == OptMachine::TRIAL;
     b.n = q.Nt * q.du;
     b.Nt = q.Nt;
     b.du = q.du;
@@ -1281,17 +1285,19 @@ jd_status jd::opt_launch_batch(OptMachine *const *ms, int n, cudaStream_t st) {
     b.scal = p->scal_d;
     b.uk = p->uk;
     b.uk2 = p->uk2;
-    sw[i].p = p;
-    sw[i].uk = p->uk;
-    sw[i].b = plan_bufs(p);
+    const BatchSweep sw{p, p->uk, plan_bufs(p)};
     if (kind == OptMachine::TRIAL && pair) {
-      PathBufs &pb = sw[i].b;
-      pb.uk2 = p->uk2;
-      pb.traj2 = p->traj2;
-      pb.log_kt2 = p->log_kt2;
-      pb.log_y2 = p->log_y2;
-      pb.partC2 = p->partC2;
+      BatchSweep &x = fp[nfp++];
+      x = sw;
+      x.b.uk2 = p->uk2;
+      x.b.traj2 = p->traj2;
+      x.b.log_kt2 = p->log_kt2;
+      x.b.log_y2 = p->log_y2;
+      x.b.partC2 = p->partC2;
+    } else if (kind == OptMachine::TRIAL || fwd) {
+      fs[nfs++] = sw;
     }
+    if (kind == OptMachine::GRAD) ad[nad++] = sw;
     const int64_t nun = n_units(q.M);
     if (kind == OptMachine::GRAD) {
       const int ne = 1 + q.Nt * q.du;
@@ -1308,32 +1314,20 @@ jd_status jd::opt_launch_batch(OptMachine *const *ms, int n, cudaStream_t st) {
   }
   ub.first[ub.n] = ubl;
   cb.first[cb.n] = cbl;
+  if (f64)
+    opt_pre_batch_kernel<double><<<n, 256, 0, st>>>(ob);
+  else
+    opt_pre_batch_kernel<float><<<n, 256, 0, st>>>(ob);
+  count_launch();
+  JD_CUDA(cudaGetLastError());
   cudaError_t e = cudaSuccess;
-  if (kind == OptMachine::GRAD) {
-    if (f64)
-      opt_grad_pre_batch_kernel<double><<<n, 256, 0, st>>>(ob);
-    else
-      opt_grad_pre_batch_kernel<float><<<n, 256, 0, st>>>(ob);
-    count_launch();
-    JD_CUDA(cudaGetLastError());
-    if (fwd) e = ops->fwd_batch(sw, n, FWD_STORE, st);
-    if (e == cudaSuccess) e = ops->adj_batch(sw, n, st);
-  } else {
-    if (f64)
-      opt_trial_pre_batch_kernel<double><<<n, 256, 0, st>>>(ob);
-    else
-      opt_trial_pre_batch_kernel<float><<<n, 256, 0, st>>>(ob);
-    count_launch();
-    JD_CUDA(cudaGetLastError());
-    e = ops->fwd_batch(sw, n, pair ? FWD_STORE | FWD_PAIR : FWD_STORE, st);
-  }
+  if (nfs) e = ops->fwd_batch(fs, nfs, FWD_STORE, st);
+  if (e == cudaSuccess && nfp) e = ops->fwd_batch(fp, nfp, FWD_STORE | FWD_PAIR, st);
+  if (e == cudaSuccess && nad) e = ops->adj_batch(ad, nad, st);
   JD_CUDA(e);
   unit_sums_batch_kernel<<<ubl, 256, 0, st>>>(ub);
   combine_units_batch_kernel<<<cbl, 128, 0, st>>>(cb);
-  if (kind == OptMachine::GRAD)
-    opt_grad_post_batch_kernel<<<n, 256, 0, st>>>(ob);
-  else
-    opt_trial_post_batch_kernel<<<n, 256, 0, st>>>(ob);
+  opt_post_batch_kernel<<<n, 256, 0, st>>>(ob);
   count_launch(3);
   JD_CUDA(cudaGetLastError());
   for (int i = 0; i < n; ++i) {

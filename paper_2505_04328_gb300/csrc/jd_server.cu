@@ -15,9 +15,9 @@
 //     one request's line-search decision;
 //   * small requests (d <= 2, du = 1, the stored plan, at most batch_paths paths) share
 //     launches: their machines defer each phase, and the worker launches the deferred
-//     phases of up to kBatchMax requests with the same phase kind, precision and
-//     dimension as one batched sequence (jd::opt_launch_batch) on one of a few batch
-//     streams -- one forward and one adjoint sweep over all their paths, one launch per
+//     phases of up to kBatchMax requests with the same precision and dimension, whatever
+//     their phases, as one batched sequence (jd::opt_launch_batch) on one of a few batch
+//     streams -- forward and adjoint sweeps over all their paths, one launch per
 //     reduction and per optimizer step, instead of a launch sequence per request;
 //   * a finished request frees its slot and memory, and the next ones are admitted.
 // Each request runs the arithmetic and the host decisions of jd_optimize on its own
