@@ -402,8 +402,13 @@ def run_ours(args):
                        "sweeps_per_step": r["sweeps"] / args.steps,
                        "step": "one projected-gradient Armijo iteration (gradient, line search, "
                                "update) inside one jd_optimize call",
-                       "l2": "inputs larger than L2: the %s buffers (%.2f GB) exceed the 129 MB "
-                             "L2; no flush" % (prob.info()["mode"], prob.info()["device_bytes"] / 1e9)},
+                       "l2": ("inputs larger than L2: the %s buffers (%.2f GB) exceed the 129 MB "
+                              "L2; no flush" % (prob.info()["mode"], prob.info()["device_bytes"] / 1e9))
+                       if prob.info()["device_bytes"] > 129e6 else
+                       ("inputs fit in L2 (%.3f GB of %s buffers) and no flush: the K iterations run "
+                        "inside one jd_optimize call; the problem is latency-bound (per-step chains of "
+                        "few paths), not memory-bound" % (prob.info()["device_bytes"] / 1e9,
+                                                          prob.info()["mode"]))},
             "gpu_launches": launches,
             "kernels_ms_per_step": {k: v[1] / args.steps for k, v in kstats.items()},
             "roofline": rl.get(dom),
@@ -417,8 +422,7 @@ def run_ours(args):
             rate, sec, threads = oracle_step_rate(ps, 1, 0)
             line["cpu_baseline"] = {
                 "value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-                "sample": f"{args.reference_paths} of {M} paths, all {Nt} steps, one optimizer "
-                          "iteration"}
+                "sample": f"{ps.M} of {M} paths, all {Nt} steps, one optimizer iteration"}
             # the same path sample in this path's precision against the oracle (FP64)
             import oracle
             with jd.JdProblem(ps, prec=prec, stream=stream, use_tensor_cores=args.tc) as q:
