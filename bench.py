@@ -331,6 +331,7 @@ def run_ours(args):
     # device-resident control (the optimizer state zeta carries over)
     r = optimize_device(prob, u, args.warmup, 1.0)
     zeta = min(2 * r["zeta"], 1e3)
+    u_start, zeta_start = u.detach().cpu().numpy().reshape(Nt, du).copy(), zeta   # e2e replays this window
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
@@ -356,19 +357,19 @@ def run_ours(args):
     ms_per_step = ms / args.steps
     value = ws * M * Nt / (ms_per_step * 1e-3)
 
-    # end to end through the public API with host buffers: the control goes host ->
-    # device, K iterations run (each reads its cost and Armijo decision back to the
-    # host), and the new control comes back
-    u_host = u.cpu().numpy().reshape(Nt, du).copy()
-    zeta = min(2 * r["zeta"], 1e3)
+    # end to end through the public API with host buffers, over the same K iterations: the
+    # control at the start of the timed window goes host -> device, the K iterations run
+    # (each reads its cost and Armijo decision back to the host; the fixed sample makes
+    # them the timed iterations bit for bit), and the new control comes back
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    u_host, r2, _ = prob.optimize(u_host, max_iter=args.steps, tol_rel_grad=0.0, zeta0=zeta)
+    u_host, r2, _ = prob.optimize(u_start, max_iter=args.steps, tol_rel_grad=0.0, zeta0=zeta_start)
     e2e_sec = (time.perf_counter() - t0) / args.steps
     trials = (r2["sweeps"] - 1) / args.steps   # trial phases (a pair is one); the first gradient's sweep
     e2e = {"value": ws * M * Nt / e2e_sec, "unit": UNIT,
            "h2d_bytes_per_step": n * 8 / args.steps,
-           "d2h_bytes_per_step": n * 8 / args.steps + 64 * (1 + trials)}
+           "d2h_bytes_per_step": n * 8 / args.steps + 64 * (1 + trials),
+           "same_iterations": bool(r2["evals"] == evals and r2["J"] == r["J"])}
 
     # gradient error of the FP32 path against FP64 at the final control: the FP64 GPU path
     # on all paths (it equals the oracle within 1e-12 pathwise in the parity tests); the
