@@ -432,6 +432,20 @@ def run_ours(args):
             line["grad_error_vs_oracle"] = {
                 "paths": ps.M, "J_rel": abs(Js - Jo) / abs(Jo),
                 "grad_rel_l2": float(np.linalg.norm(gs - go) / np.linalg.norm(go))}
+        if args.oracle_paths:
+            # this path's gradient at the final control against the FP64 oracle on the first
+            # oracle_paths paths (all of them for a full-size FP64 reference where no FP64
+            # GPU form is built, d = 32)
+            import oracle
+            pf = p.replace(M=min(M, args.oracle_paths))
+            with jd.JdProblem(pf, prec=prec, stream=stream, use_tensor_cores=args.tc) as q:
+                Jf, gf, _ = q.gradient(u_fin)
+            t0 = time.perf_counter()
+            Jo, go, _ = oracle.gradient(pf, u_fin)
+            line["grad_error_vs_oracle_paths"] = {
+                "paths": pf.M, "J_rel": abs(Jf - Jo) / abs(Jo),
+                "grad_rel_l2": float(np.linalg.norm(gf - go) / np.linalg.norm(go)),
+                "oracle_seconds": time.perf_counter() - t0, "oracle_threads": oracle.default_threads()}
         print(json.dumps(line), flush=True)
     prob.close()
     if dist is not None:
@@ -1098,6 +1112,9 @@ def main():
     ap.add_argument("--keep-dt", action="store_true",
                     help="with --steps-t: shorten the horizon so that the step length stays the workload's")
     ap.add_argument("--reference-paths", type=int, default=1 << 14)
+    ap.add_argument("--oracle-paths", type=int, default=0,
+                    help="also compare the gradient at the final control with the FP64 oracle on "
+                         "this many paths (0 = no)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--particles", type=int, default=None,
                     help="feedback_coupled: particles per ring (3..2048; the paper's Sec. 6 uses 2000)")
