@@ -744,11 +744,31 @@ adj32_kernel(const KP32 *__restrict__ kpg, const float *__restrict__ u, const fl
     if (lam_out && active)
 #pragma unroll
       for (int c = 0; c < 32; ++c) lam_out[((size_t)k * D32 + c) * mloc + lm] = mu[c];
-    // per-step, per-warp compensated sums of the control sensitivities
+    // per-step, per-warp compensated sums of the four control sensitivities, transposed:
+    // at offset 16 a lane keeps two components and sends the other two, at offset 8 one,
+    // then one pair per lane through offsets 4, 2, 1 (12 shuffles and 6 TwoSums instead of
+    // 40 and 20 for four separate butterflies); lane 8 c then holds component c's sum
+    static_assert(DU32 == 4, "the transposed reduction takes four components");
+    {
+      Pair<float> v[4];
 #pragma unroll
-    for (int l = 0; l < DU32; ++l) {
-      const Pair<float> r = warp_sum(Pair<float>{active ? g[l] : 0.f, 0.f});
-      if (lane == 0) partG[((int64_t)k * DU32 + l) * npart + wid] = (double)r.s + (double)r.e;
+      for (int l = 0; l < 4; ++l) v[l] = Pair<float>{active ? g[l] : 0.f, 0.f};
+      const bool up16 = (lane & 16) != 0, up8 = (lane & 8) != 0;
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const Pair<float> send = up16 ? v[i] : v[i + 2];
+        const Pair<float> keep = up16 ? v[i + 2] : v[i];
+        v[i] = padd(keep, shfl_xor(send, 16));
+      }
+      {
+        const Pair<float> send = up8 ? v[0] : v[1];
+        const Pair<float> keep = up8 ? v[1] : v[0];
+        v[0] = padd(keep, shfl_xor(send, 8));
+      }
+#pragma unroll
+      for (int o = 4; o >= 1; o >>= 1) v[0] = padd(v[0], shfl_xor(v[0], o));
+      if ((lane & 7) == 0)
+        partG[((int64_t)k * DU32 + (lane >> 3)) * npart + wid] = (double)v[0].s + (double)v[0].e;
     }
   }
   if (TC) tc_teardown(sh);
