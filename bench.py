@@ -1003,10 +1003,10 @@ COUNTERS = {
     # None, warp-instructions per warp-step), from single ncu captures of each kernel at
     # full occupancy (M = 2^20, 8192 blocks) over N_t = 100 steps of the workload's own step
     # length (--steps-t 100 --keep-dt): profiles/*_double_well_d2_M2p20_Nt100_dt2e-3.md
-    ("double_well", "fwd_pair"): ("610815f8e2f9", 17.90, 358.7),
-    ("double_well", "fwd_store"): ("610815f8e2f9", 8.59, 288.7),
-    ("double_well", "adj_stored"): ("610815f8e2f9", 9.26, 72.7),
-    ("double_well", "adj_recompute"): ("610815f8e2f9", 0.75, 354.6),
+    ("double_well", "fwd_pair"): ("467756828abb", 17.90, 358.7),
+    ("double_well", "fwd_store"): ("467756828abb", 8.59, 288.7),
+    ("double_well", "adj_stored"): ("467756828abb", 9.26, 72.7),
+    ("double_well", "adj_recompute"): ("467756828abb", 0.75, 354.6),
 }
 
 
