@@ -43,6 +43,9 @@ CASES = {
     "linear32": lambda: workloads.linear_family(32, M=300, Nt=61, lam=1.0),
     "linear16": lambda: workloads.linear_family(16, M=200, Nt=40, lam=2.0),
     "linear32_jumpy": lambda: workloads.linear_family(32, M=130, Nt=20, lam=60.0),
+    # uniform jump sizes (2 u - 1 per word) through the warp-wide one-jump steps
+    "linear32_uniform": lambda: workloads.linear_family(32, M=160, Nt=30, lam=20.0).replace(
+        jump_law=workloads.JUMP_UNIFORM, jump_scale=0.2),
 }
 
 
