@@ -1069,6 +1069,9 @@ def kernel_roofline(name, stat, p, peaks, peak_kind, tc=0, plan="stored"):
     achieved = ops * units / per_launch_s / 1e9
     out = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "Glane-op/s",
            "frac": achieved / peak, "traffic": traffic,
+           "frac_kind": "algorithmic only: the method's lane-operations per path-step (a Box-Muller pair "
+                        "counted as 7, though the library log and sincospi take about 76 instructions) "
+                        "against the issue peak; the instructions actually issued are in 'issue'",
            "peak_source": f"derived: {nsm} SMs x 4 schedulers x 32 lanes x 1 instruction/clock x "
                           f"{sm_mhz:.0f} MHz (max SM clock)",
            "algorithmic_ops_per_path_step": ops}
