@@ -5,11 +5,17 @@ namespace jd {
 
 // Coefficients go to the problem's device buffer (stream ordered) for the kernels to stage.
 static cudaError_t upload_kp(const jd_problem *p, int64_t m_begin, int64_t mloc, const PathBufs &b,
-                             cudaStream_t s, KP32 **dev) {
+                             cudaStream_t s, KP32 **dev, RoundKeys *rk = nullptr) {
   if (!p->kp_dev) return cudaErrorInvalidValue;
   thread_local KP32 kp;   // 13 KB: not on the stack, and not allocated per launch
   make_kparams<float, D32, DU32>(p, m_begin, mloc, kp);
   if (b.npart) kp.npart = b.npart;
+  if (rk) {
+    for (int r = 0; r < 10; ++r) {
+      rk->k0[r] = kp.rk0[r];
+      rk->k1[r] = kp.rk1[r];
+    }
+  }
   // pageable source: the copy is staged before cudaMemcpyAsync returns
   const cudaError_t e = cudaMemcpyAsync(p->kp_dev, &kp, sizeof(KP32), cudaMemcpyHostToDevice, s);
   *dev = static_cast<KP32 *>(p->kp_dev);
@@ -20,7 +26,8 @@ static cudaError_t op32_fwd(const jd_problem *p, int mode, int64_t m_begin, int6
                             const PathBufs &b, cudaStream_t s) {
   if (mode == FWD_CKPT) return cudaErrorNotSupported;
   KP32 *kp = nullptr;
-  const cudaError_t ue = upload_kp(p, m_begin, mloc, b, s, &kp);
+  RoundKeys rk;
+  const cudaError_t ue = upload_kp(p, m_begin, mloc, b, s, &kp, &rk);
   if (ue != cudaSuccess) return ue;
   const dim3 grid((unsigned)ceil_div(mloc, TPB));
   const float *u = static_cast<const float *>(uk);
@@ -33,13 +40,13 @@ static cudaError_t op32_fwd(const jd_problem *p, int mode, int64_t m_begin, int6
   const float *bu = p->bu_dev;
   switch (p->desc.use_tensor_cores) {
     case 1:
-      fwd32_kernel<1><<<grid, TPB, 0, s>>>(kp, u, bu, xd, b.partC, traj, b.flags, pc, jl, b.jcnt, b.status, mloc);
+      fwd32_kernel<1><<<grid, TPB, 0, s>>>(kp, u, bu, xd, b.partC, traj, b.flags, pc, jl, b.jcnt, b.status, mloc, rk);
       break;
     case 2:
-      fwd32_kernel<2><<<grid, TPB, 0, s>>>(kp, u, bu, xd, b.partC, traj, b.flags, pc, jl, b.jcnt, b.status, mloc);
+      fwd32_kernel<2><<<grid, TPB, 0, s>>>(kp, u, bu, xd, b.partC, traj, b.flags, pc, jl, b.jcnt, b.status, mloc, rk);
       break;
     default:   // 0, and 3 (tensor cores in the adjoint only)
-      fwd32_kernel<0><<<grid, TPB, 0, s>>>(kp, u, bu, xd, b.partC, traj, b.flags, pc, jl, b.jcnt, b.status, mloc);
+      fwd32_kernel<0><<<grid, TPB, 0, s>>>(kp, u, bu, xd, b.partC, traj, b.flags, pc, jl, b.jcnt, b.status, mloc, rk);
       break;
   }
   count_launch(2);

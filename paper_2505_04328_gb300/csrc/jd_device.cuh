@@ -40,6 +40,24 @@ __device__ __forceinline__ uint4 philox10(uint32_t c0, uint32_t c1, uint32_t c2,
   return make_uint4(c0, c1, c2, c3);
 }
 
+// The same generator with the ten round keys given (rk0[r] = k0 + r 0x9E3779B9, rk1[r] =
+// k1 + r 0xBB67AE85): from a kernel's parameter block each XOR takes its key as a
+// constant operand, and no key is bumped per block.
+__device__ __forceinline__ uint4 philox10_rk(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                             const uint32_t (&rk0)[10], const uint32_t (&rk1)[10]) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c0;
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c2;
+    const uint32_t y0 = (uint32_t)(p1 >> 32) ^ c1 ^ rk0[r], y2 = (uint32_t)(p0 >> 32) ^ c3 ^ rk1[r];
+    c0 = y0;
+    c1 = (uint32_t)p1;
+    c2 = y2;
+    c3 = (uint32_t)p0;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
 // ---------------------------------------------------------------------------
 // Precision-generic arithmetic with fixed rounding
 // ---------------------------------------------------------------------------
@@ -500,14 +518,25 @@ struct MainWords {
 
 // Main stream of step k, path m: word 0 decides the Poisson count, words 1..2P the
 // sub-step-0 normals.
-template <typename R, int D, int DU>
+// Block (c0, c1, c2, epoch) of the problem's generator; RK: with the round keys of the
+// parameter block (kernels whose kp is a __grid_constant__ parameter), else the keys are
+// bumped round by round.  The same words either way.
+template <bool RK, typename R, int D, int DU>
+__device__ __forceinline__ uint4 philox_kp(const KParams<R, D, DU> &kp, uint32_t c0, uint32_t c1, uint32_t c2) {
+  if constexpr (RK)
+    return philox10_rk(c0, c1, c2, kp.epoch, kp.rk0, kp.rk1);
+  else
+    return philox10(c0, c1, c2, kp.epoch, kp.key0, kp.key1);
+}
+
+template <bool RK = false, typename R, int D, int DU>
 __device__ __forceinline__ uint32_t main_draws(const KParams<R, D, DU> &kp, int k, uint32_t m,
                                                R (&z)[D]) {
   constexpr int NB = MainWords<D>::NB, PD = MainWords<D>::PD;
   uint32_t w[4 * NB];
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
-    const uint4 o = philox10((uint32_t)k, m, (uint32_t)b, kp.epoch, kp.key0, kp.key1);
+    const uint4 o = philox_kp<RK>(kp, (uint32_t)k, m, (uint32_t)b);
     w[4 * b] = o.x;
     w[4 * b + 1] = o.y;
     w[4 * b + 2] = o.z;
@@ -590,7 +619,7 @@ __device__ __forceinline__ void slot_draws(const KParams<R, D, DU> &kp, int k, u
 // Draws of jump slot 0 for a step with exactly one jump, with the word layout known at
 // compile time (valid when kp.npair == ceil(D/2)): time fraction, unit size, and the
 // normals of the sub-step after the jump.  Same values as slot_draws(kp, k, m, 0, ..).
-template <typename R, int D, int DU>
+template <bool RK = false, typename R, int D, int DU>
 __device__ __forceinline__ R slot0_draws(const KParams<R, D, DU> &kp, int k, uint32_t m, R (&xih)[D],
                                          R (&z)[D]) {
   using M = Ar<R>;
@@ -599,7 +628,7 @@ __device__ __forceinline__ R slot0_draws(const KParams<R, D, DU> &kp, int k, uin
   uint32_t w[4 * NB];
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
-    const uint4 o = philox10((uint32_t)k, m, (1u << 24) | (1u << 16) | (uint32_t)b, kp.epoch, kp.key0, kp.key1);
+    const uint4 o = philox_kp<RK>(kp, (uint32_t)k, m, (1u << 24) | (1u << 16) | (uint32_t)b);
     w[4 * b] = o.x;
     w[4 * b + 1] = o.y;
     w[4 * b + 2] = o.z;

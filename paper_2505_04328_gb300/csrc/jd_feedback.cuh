@@ -444,7 +444,7 @@ fb_fwd_kernel(const __grid_constant__ KParams<R, 2, 1> kp, const __grid_constant
       }
       const R *mk = mu + (size_t)k * LP;
       R zs[2];
-      const uint32_t w0 = main_draws(kp, k, mg, zs);
+      const uint32_t w0 = main_draws<true>(kp, k, mg, zs);   // round keys of the parameter block
       int n = 0;
       FbPlan<R> P;
       if (has_jump(kp, w0)) {
@@ -640,7 +640,7 @@ fb_adj_kernel(const __grid_constant__ KParams<R, 2, 1> kp, const __grid_constant
       if ((fk >> (k & 31)) & 1u) {
         // regenerate the step's sub-states from X_k with the forward's arithmetic
         R zs[2], y[2] = {zk[0], zk[1]};
-        const uint32_t w0 = main_draws(kp, k, mg, zs);
+        const uint32_t w0 = main_draws<true>(kp, k, mg, zs);   // round keys of the parameter block
         n = fb_plan(kp, k, mg, w0, P);
 #pragma unroll 1
         for (int i = 0; i < n; ++i) {
@@ -799,7 +799,7 @@ fb_fwd_sur_kernel(const __grid_constant__ KParams<R, 2, 1> kp, const __grid_cons
     FbPlan<R> P;
     R bk = R(0);
     if (active) {
-      const uint32_t w0 = main_draws(kp, k, mg, zs);
+      const uint32_t w0 = main_draws<true>(kp, k, mg, zs);   // round keys of the parameter block
       if (has_jump(kp, w0)) n = fb_plan(kp, k, mg, w0, P);
       bk = bhat[(size_t)k * mloc + m];
     }

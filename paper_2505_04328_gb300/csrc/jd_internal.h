@@ -41,6 +41,10 @@ struct KParams {
   int kvel;                       // first component a jump moves (d/2 for Keilson-Storer, else 0)
   int64_t m_begin;                // global index of path 0 of this launch
   int64_t npart;                  // stride of the per-warp gradient partials (all launches)
+  // Philox round keys (key0 + r W0, key1 + r W1 mod 2^32, r = 0..9), read by the forward
+  // sweeps as constant operands of the rounds' XORs instead of bumping the key in every
+  // block; last in the struct, so kernels that do not read them see the same layout
+  uint32_t rk0[10], rk1[10];
 };
 
 // Device buffers of one launch (unused ones are null).

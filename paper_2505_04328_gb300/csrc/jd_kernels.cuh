@@ -328,8 +328,10 @@ __device__ __forceinline__ void plain_update(const KP &kp, const R (&f)[D], cons
 // gradient recompute adjoint, whose loop must stay small for the instruction cache, and
 // the paired sweep of two controls).
 // kh: the source of the drift, noise and step coefficients of the step without jumps
-// (kp itself or a HotFwd); the jump paths read kp.
-template <typename R, int D, int DU, typename LW, bool INLINE_JUMP = true, typename KH = KParams<R, D, DU>>
+// (kp itself or a HotFwd); the jump paths read kp.  RK: the inline slot draws take the
+// round keys of kp (a __grid_constant__ parameter).
+template <typename R, int D, int DU, typename LW, bool INLINE_JUMP = true, typename KH = KParams<R, D, DU>,
+          bool RK = false>
 __device__ __forceinline__ int step_from_draws(const KParams<R, D, DU> &kp, const KH &kh, int k, uint32_t m,
                                                uint32_t w0, const R (&z)[D], const R (&uk)[DU], R (&x)[D],
                                                LW &lw) {
@@ -361,7 +363,7 @@ __device__ __forceinline__ int step_from_draws(const KParams<R, D, DU> &kp, cons
   }
   if (INLINE_JUMP && one_jump(kp, w0)) {
     R xih[D], z1[D];
-    const R th = slot0_draws(kp, k, m, xih, z1);
+    const R th = slot0_draws<RK>(kp, k, m, xih, z1);
     one_jump_inline(kp, k, th, xih, z, z1, uk, x, lw);
     return 1;
   }
@@ -396,12 +398,12 @@ __device__ __forceinline__ int step_from_draws(const KParams<R, D, DU> &kp, cons
 // the post-jump states of the step are recorded.  zo (optional, stride zs) receives the
 // step's main-stream normals Z_{k,0}.
 template <typename R, int D, int DU, typename LW, bool ZOUT = false, bool INLINE_JUMP = true,
-          typename KH = KParams<R, D, DU>>
+          typename KH = KParams<R, D, DU>, bool RK = false>
 __device__ __forceinline__ int forward_step_h(const KParams<R, D, DU> &kp, const KH &kh, int k, uint32_t m,
                                               const R *__restrict__ u, R (&x)[D], LW &lw,
                                               R *zo = nullptr, int zs = 0) {
   R z[D];
-  const uint32_t w0 = main_draws(kp, k, m, z);
+  const uint32_t w0 = main_draws<RK>(kp, k, m, z);
   if constexpr (ZOUT) {
 #pragma unroll
     for (int c = 0; c < D; ++c) zo[c * zs] = z[c];
@@ -409,7 +411,7 @@ __device__ __forceinline__ int forward_step_h(const KParams<R, D, DU> &kp, const
   R uk[DU];
 #pragma unroll
   for (int l = 0; l < DU; ++l) uk[l] = __ldg(u + (size_t)k * DU + l);
-  return step_from_draws<R, D, DU, LW, INLINE_JUMP, KH>(kp, kh, k, m, w0, z, uk, x, lw);
+  return step_from_draws<R, D, DU, LW, INLINE_JUMP, KH, RK>(kp, kh, k, m, w0, z, uk, x, lw);
 }
 
 template <typename R, int D, int DU, typename LW, bool ZOUT = false, bool INLINE_JUMP = true>
@@ -423,7 +425,7 @@ __device__ __forceinline__ int forward_step(const KParams<R, D, DU> &kp, int k, 
 // sweep): one draw of the main stream, and on a jump step the same jump times and sizes
 // for both states.  Each state's arithmetic is forward_step's, so each result is bitwise
 // the one of a sweep of its control alone.  Returns the number of jumps.
-template <typename R, int D, int DU, typename LW, typename KH>
+template <typename R, int D, int DU, typename LW, typename KH, bool RK = false>
 __device__ __forceinline__ int forward_step2(const KParams<R, D, DU> &kp, const KH &kh, int k, uint32_t m,
                                              uint32_t w0, const R (&z)[D], const R *__restrict__ u, R (&x)[D],
                                              LW &lw, const R *__restrict__ u2, R (&x2)[D], LW &lw2) {
@@ -443,7 +445,7 @@ __device__ __forceinline__ int forward_step2(const KParams<R, D, DU> &kp, const 
   }
   if (one_jump(kp, w0)) {   // one slot draw for both states
     R xih[D], z1[D];
-    const R th = slot0_draws(kp, k, m, xih, z1);
+    const R th = slot0_draws<RK>(kp, k, m, xih, z1);
     one_jump_inline(kp, k, th, xih, z, z1, uk, x, lw);
     one_jump_inline(kp, k, th, xih, z, z1, uk2, x2, lw2);
     return 1;
@@ -1012,7 +1014,9 @@ __device__ __forceinline__ void one_jump_pre(const KParams<R, D, DU> &kp, int k,
 // scheduler's FP64 pipe for many cycles).  Each path leaves its cost pair in pd.cw, and
 // spread_combine_kernel forms every 128-path block's cost partial from them exactly as
 // block_sum_to_double does in the one-path-per-thread launch.
-template <typename R, int D, int DU, int MODE, bool PAIR = false, bool PRE = false>
+// RK: kp is the launch's __grid_constant__ parameter, whose Philox round keys the draws
+// take as constant operands (fwd_kernel); the batched sweeps' kp lies in a table.
+template <typename R, int D, int DU, int MODE, bool PAIR = false, bool PRE = false, bool RK = false>
 __device__ __forceinline__ void fwd_body(const KParams<R, D, DU> &kp, int64_t bid, const R *__restrict__ u,
                                          const R *__restrict__ xd, double *__restrict__ partC, R *__restrict__ traj,
                                          uint32_t *__restrict__ flags, R *__restrict__ ckpt, R *__restrict__ pcost,
@@ -1090,16 +1094,16 @@ __device__ __forceinline__ void fwd_body(const KParams<R, D, DU> &kp, int64_t bi
         }
         nj = 1;
       } else if constexpr (PAIR) {
-        nj = forward_step2(kp, kh, k, m, w0, z, u, x, lw, p2.u, x2, lw2);
+        nj = forward_step2<R, D, DU, LW, KH, RK>(kp, kh, k, m, w0, z, u, x, lw, p2.u, x2, lw2);
       } else {
-        nj = step_from_draws<R, D, DU, LW, true, KH>(kp, kh, k, m, w0, z, uk, x, lw);
+        nj = step_from_draws<R, D, DU, LW, true, KH, RK>(kp, kh, k, m, w0, z, uk, x, lw);
       }
     } else if constexpr (PAIR) {
       R z[D];
-      const uint32_t w0 = main_draws(kp, k, m, z);
-      nj = forward_step2(kp, kh, k, m, w0, z, u, x, lw, p2.u, x2, lw2);
+      const uint32_t w0 = main_draws<RK>(kp, k, m, z);
+      nj = forward_step2<R, D, DU, LW, KH, RK>(kp, kh, k, m, w0, z, u, x, lw, p2.u, x2, lw2);
     } else {
-      nj = forward_step_h<R, D, DU, LW, false, true, KH>(kp, kh, k, m, u, x, lw);
+      nj = forward_step_h<R, D, DU, LW, false, true, KH, RK>(kp, kh, k, m, u, x, lw);
     }
     if (nj) fw |= 1u << (k & 31);
     cost.add(cost_term(kh, x, xd + (size_t)(k + 1) * D));
@@ -1177,13 +1181,13 @@ fwd_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u
     const bool second = blockIdx.x >= nb;
     PreDraws<R, D> pd1 = pd;
     if (second) pd1.cw = pd.cw2;
-    fwd_body<R, D, DU, MODE, false, true>(kp, second ? blockIdx.x - nb : blockIdx.x, second ? p2.u : u, xd, partC,
+    fwd_body<R, D, DU, MODE, false, true, true>(kp, second ? blockIdx.x - nb : blockIdx.x, second ? p2.u : u, xd, partC,
                                           second ? p2.traj : traj, second ? nullptr : flags,
                                           second ? p2.ckpt : ckpt, nullptr, second ? p2.jl : jl,
                                           second ? nullptr : jcnt, mloc, PairOut<R, D>{}, pd1, red);
   } else {
-    fwd_body<R, D, DU, MODE, PAIR, PRE>(kp, blockIdx.x, u, xd, partC, traj, flags, ckpt, pcost, jl, jcnt, mloc, p2,
-                                        pd, red);
+    fwd_body<R, D, DU, MODE, PAIR, PRE, true>(kp, blockIdx.x, u, xd, partC, traj, flags, ckpt, pcost, jl, jcnt, mloc,
+                                              p2, pd, red);
   }
 }
 
@@ -1659,6 +1663,17 @@ inline void poisson_thresholds(double mu, unsigned long long *thr) {
   }
 }
 
+// The generator's key (seed mod 2^32, seed >> 32) and its ten round keys.
+template <typename R, int D, int DU>
+void set_philox_key(KParams<R, D, DU> &kp, unsigned long long seed) {
+  kp.key0 = (uint32_t)(seed & 0xffffffffull);
+  kp.key1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    kp.rk0[r] = kp.key0 + (uint32_t)r * 0x9E3779B9u;
+    kp.rk1[r] = kp.key1 + (uint32_t)r * 0xBB67AE85u;
+  }
+}
+
 template <typename R, int D, int DU>
 void make_kparams(const jd_problem *p, int64_t m_begin, int64_t mloc, KParams<R, D, DU> &kp) {
   const jd_problem_desc &q = p->desc;
@@ -1690,8 +1705,7 @@ void make_kparams(const jd_problem *p, int64_t m_begin, int64_t mloc, KParams<R,
   kp.jump_scale = (R)q.jump_scale;
   kp.kvel = q.jump_law == JD_JUMP_KS ? d / 2 : 0;
   poisson_thresholds(q.lambda * dt, kp.thr);
-  kp.key0 = (uint32_t)(q.seed & 0xffffffffull);
-  kp.key1 = (uint32_t)(q.seed >> 32);
+  set_philox_key(kp, q.seed);
   kp.epoch = q.epoch;
   kp.d = d;
   kp.npair = (d + 1) / 2;

@@ -101,8 +101,7 @@ static void noalloc_kparams(const jd_problem_desc &q, KParams<R, D, DU> &kp) {
   kp.jump_scale = (R)q.jump_scale;
   kp.kvel = 0;
   poisson_thresholds(q.lambda * dt, kp.thr);
-  kp.key0 = (uint32_t)(q.seed & 0xffffffffull);
-  kp.key1 = (uint32_t)(q.seed >> 32);
+  set_philox_key(kp, q.seed);
   kp.epoch = q.epoch;
   kp.d = d;
   kp.npair = (d + 1) / 2;

@@ -238,9 +238,15 @@ __device__ __forceinline__ void cc_matvec(const float *M, float *vcol, const flo
 // loop that parks the 30 normals in the thread's shared-memory column zcol[c * TPB]
 // (the unrolled form is 9 Philox blocks and 16 Box-Muller pairs of straight-line code,
 // which overflowed the instruction cache).  Returns word 0.
-__device__ __forceinline__ uint32_t main_noise_or_jump(const KP32 &kp, int k, uint32_t m, float (&x)[32],
-                                                        float *zcol, bool &jump) {
-  const uint4 o0 = philox10((uint32_t)k, m, 0u, kp.epoch, kp.key0, kp.key1);
+// rk: the Philox round keys as a kernel parameter (constant operands of the rounds' XORs;
+// the staged copy in shared memory would cost a load per key).
+struct RoundKeys {
+  uint32_t k0[10], k1[10];
+};
+
+__device__ __forceinline__ uint32_t main_noise_or_jump(const KP32 &kp, const RoundKeys &rk, int k, uint32_t m,
+                                                        float (&x)[32], float *zcol, bool &jump) {
+  const uint4 o0 = philox10_rk((uint32_t)k, m, 0u, kp.epoch, rk.k0, rk.k1);
   jump = has_jump(kp, o0.x);
   if (jump) return o0.x;
   uint32_t carry = o0.w;
@@ -252,7 +258,7 @@ __device__ __forceinline__ uint32_t main_noise_or_jump(const KP32 &kp, int k, ui
   }
 #pragma unroll 1
   for (int b = 1; b < 9; ++b) {
-    const uint4 o = philox10((uint32_t)k, m, (uint32_t)b, kp.epoch, kp.key0, kp.key1);
+    const uint4 o = philox10_rk((uint32_t)k, m, (uint32_t)b, kp.epoch, rk.k0, rk.k1);
     // words 4b..4b+3: pairs (4b-1, 4b) and (4b+1, 4b+2); word 4b+3 carries over
     const int c = 4 * b - 2;   // components of pair (4b-1, 4b)
     float z0, z1;
@@ -437,7 +443,7 @@ fwd32_kernel(const KP32 *__restrict__ kpg, const float *__restrict__ u, const fl
              const float *__restrict__ xd,
              double *__restrict__ partC, float *__restrict__ traj, uint32_t *__restrict__ flags,
              float *__restrict__ pcost, JLog<float, D32> jl, int *__restrict__ jcnt, int *status,
-             int64_t mloc) {
+             int64_t mloc, const __grid_constant__ RoundKeys rk) {
   constexpr bool SPLIT = TC == 2;
   __shared__ __align__(1024) TcShared sh;
   __shared__ __align__(16) CcShared cs;
@@ -480,7 +486,7 @@ fwd32_kernel(const KP32 *__restrict__ kpg, const float *__restrict__ u, const fl
       cc_matvec(cs.at, vbuf + threadIdx.x, x, f);
     }
     bool jump;
-    const uint32_t w0 = main_noise_or_jump(kp, k, m, x, vbuf + threadIdx.x, jump);   // x += noise unless jump
+    const uint32_t w0 = main_noise_or_jump(kp, rk, k, m, x, vbuf + threadIdx.x, jump);   // x += noise unless jump
     if (TC) tc_collect(sh, (uint32_t)(k & 1), f, status);
     const bool one = jump && kp.npair == 16 && (unsigned long long)w0 < kp.thr[1];
     if (!jump) {
