@@ -828,7 +828,7 @@ __device__ __forceinline__ void backward_logged(const KH &kh, const R (&xk)[D], 
   using M = Ar<R>;
 #pragma unroll
   for (int l = 0; l < DU; ++l) g[l] = R(0);
-  R thn = R(1);
+  R thn = R(1), de0 = kh.dt;
   if (maybe) {
     // every lane of the warp runs one sub-step: the lanes that jumped at step k take
     // their step's last logged jump (its sub-step, then back across the jump); the others
@@ -862,8 +862,8 @@ __device__ __forceinline__ void backward_logged(const KH &kh, const R (&xk)[D], 
       thn = tl;
       lr = ll;
     }
+    de0 = M::mul(kh.dt, thn);
   }
-  const R de0 = M::mul(kh.dt, thn);
   control_sensitivity(kh, mu, de0, g);
   adjoint_update(kh, xk, de0, mu);
 }

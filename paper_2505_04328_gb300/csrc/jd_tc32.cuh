@@ -256,7 +256,7 @@ __device__ __forceinline__ uint32_t main_noise_or_jump(const KP32 &kp, const Rou
     x[0] = __fmaf_rn(kp.sig_sqdt[0], z0, x[0]);
     x[1] = __fmaf_rn(kp.sig_sqdt[1], z1, x[1]);
   }
-#pragma unroll 1
+#pragma unroll 4
   for (int b = 1; b < 9; ++b) {
     const uint4 o = philox10_rk((uint32_t)k, m, (uint32_t)b, kp.epoch, rk.k0, rk.k1);
     // words 4b..4b+3: pairs (4b-1, 4b) and (4b+1, 4b+2); word 4b+3 carries over
