@@ -1173,6 +1173,10 @@ fwd_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u
            uint32_t *__restrict__ flags, R *__restrict__ ckpt, R *__restrict__ pcost,
            JLog<R, D> jl, int *__restrict__ jcnt, int64_t mloc, PairOut<R, D> p2, PreDraws<R, D> pd = {}) {
   __shared__ Pair<R> red[TPB / 32];
+  // the round keys of kp in the draws: the paired, checkpoint and cost sweeps run faster
+  // with them; the single store sweep's register allocation did not (288.7 -> 298.4
+  // warp-instructions per warp-step, 9.75 -> 9.97 ms per launch at M = 2^20, N_t = 1000)
+  constexpr bool RK = !(MODE == FWD_STORE && !PAIR);
   if constexpr (PAIR && PRE) {
     // a pre-drawn pair: each control on its own warps (the first half of the blocks, then
     // the second), each a single sweep -- the pair sweep's per-control arithmetic; the
@@ -1181,13 +1185,13 @@ fwd_kernel(const __grid_constant__ KParams<R, D, DU> kp, const R *__restrict__ u
     const bool second = blockIdx.x >= nb;
     PreDraws<R, D> pd1 = pd;
     if (second) pd1.cw = pd.cw2;
-    fwd_body<R, D, DU, MODE, false, true, true>(kp, second ? blockIdx.x - nb : blockIdx.x, second ? p2.u : u, xd, partC,
+    fwd_body<R, D, DU, MODE, false, true, RK>(kp, second ? blockIdx.x - nb : blockIdx.x, second ? p2.u : u, xd, partC,
                                           second ? p2.traj : traj, second ? nullptr : flags,
                                           second ? p2.ckpt : ckpt, nullptr, second ? p2.jl : jl,
                                           second ? nullptr : jcnt, mloc, PairOut<R, D>{}, pd1, red);
   } else {
-    fwd_body<R, D, DU, MODE, PAIR, PRE, true>(kp, blockIdx.x, u, xd, partC, traj, flags, ckpt, pcost, jl, jcnt, mloc,
-                                              p2, pd, red);
+    fwd_body<R, D, DU, MODE, PAIR, PRE, RK>(kp, blockIdx.x, u, xd, partC, traj, flags, ckpt, pcost, jl, jcnt, mloc,
+                                            p2, pd, red);
   }
 }
 
