@@ -1003,10 +1003,14 @@ COUNTERS = {
     # None, warp-instructions per warp-step), from single ncu captures of each kernel at
     # full occupancy (M = 2^20, 8192 blocks) over N_t = 100 steps of the workload's own step
     # length (--steps-t 100 --keep-dt): profiles/*_double_well_d2_M2p20_Nt100_dt2e-3.md
-    ("double_well", "fwd_pair"): ("467756828abb", 17.90, 358.7),
-    ("double_well", "fwd_store"): ("467756828abb", 8.59, 288.7),
-    ("double_well", "adj_stored"): ("467756828abb", 9.26, 72.7),
-    ("double_well", "adj_recompute"): ("467756828abb", 0.75, 354.6),
+    ("double_well", "fwd_pair"): ("d441ee0bde60", 17.91, 345.0),
+    ("double_well", "fwd_store"): ("d441ee0bde60", 8.59, 288.7),
+    ("double_well", "adj_stored"): ("d441ee0bde60", 9.25, 70.0),
+    ("double_well", "adj_recompute"): ("d441ee0bde60", 0.74, 351.4),
+    # the d = 32 kernels in BF16 tensor-core mode, M = 2^16 (512 tiles), N_t = 100 at the
+    # workload's step length: profiles/fwd32_adj32_linear32_d32_M2p16_Nt100_dt2e-3_bf16.md
+    ("linear32/tc1", "fwd_store"): ("d441ee0bde60", 127.7, 2145.7),
+    ("linear32/tc1", "adj_stored"): ("d441ee0bde60", 143.0, 662.2),
 }
 
 
@@ -1014,7 +1018,7 @@ def _kernel_fingerprint() -> str:
     import hashlib
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2505_04328_gb300", "csrc")
-    for f in ("jd_kernels.cuh", "jd_device.cuh", "jd_feedback.cuh", "jd_internal.h"):
+    for f in ("jd_kernels.cuh", "jd_device.cuh", "jd_feedback.cuh", "jd_internal.h", "jd_tc32.cuh"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
@@ -1045,8 +1049,11 @@ def kernel_roofline(name, stat, p, peaks, peak_kind, tc=0, plan="stored"):
     launches, total_ms = stat
     per_launch_s = total_ms / launches * 1e-3
     units = p.M * p.Nt
-    captured = p.d == 2 and p.name == "double_well" and (name != "fwd_pair" or plan == "stored")
-    tr = _counter(p.name, name, "traffic") if captured else None
+    # counters exist for the headline's kernels and for the d = 32 kernels in BF16 mode
+    wl = p.name if p.name != "linear32" else f"linear32/tc{tc}"
+    captured = ((p.d == 2 and p.name == "double_well" and (name != "fwd_pair" or plan == "stored"))
+                or (p.name == "linear32" and tc == 1))
+    tr = _counter(wl, name, "traffic") if captured else None
     traffic = None if tr is None else tr * units
     if KERNEL_BOUND[name] == "hbm":
         bytes_per = 4 * p.d + 0.125 + p.lam * p.dt * (2 + p.d) * 4
@@ -1057,7 +1064,7 @@ def kernel_roofline(name, stat, p, peaks, peak_kind, tc=0, plan="stored"):
                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                else "fallback 6.8 TB/s",
                "algorithmic_bytes_per_path_step": bytes_per}
-        iss = issue_fraction(p.name, name, units, per_launch_s, peaks)
+        iss = issue_fraction(wl, name, units, per_launch_s, peaks) if captured else None
         if iss:
             out["issue"] = iss
         return out
@@ -1078,7 +1085,7 @@ def kernel_roofline(name, stat, p, peaks, peak_kind, tc=0, plan="stored"):
     if tc:
         flops = 2.0 * p.d * p.d * (3 if tc == 2 else 1) * units
         out["tensor_tflops"] = flops / per_launch_s / 1e12
-    iss = issue_fraction(p.name, name, units, per_launch_s, peaks) if captured or name != "fwd_pair" else None
+    iss = issue_fraction(wl, name, units, per_launch_s, peaks) if captured else None
     if iss:
         out["issue"] = iss
     return out
