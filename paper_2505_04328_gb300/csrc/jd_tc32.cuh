@@ -234,10 +234,11 @@ __device__ __forceinline__ void cc_matvec(const float *M, float *vcol, const flo
 }
 
 // Main-stream noise of step k: block 0 first (its word 0 decides the Poisson count);
-// when the step has no jump, x_c += sigma_c sqrt(dt) Z_c.  Blocks 1..8 run in a rolled
-// loop that parks the 30 normals in the thread's shared-memory column zcol[c * TPB]
-// (the unrolled form is 9 Philox blocks and 16 Box-Muller pairs of straight-line code,
-// which overflowed the instruction cache).  Returns word 0.
+// when the step has no jump, x_c += sigma_c sqrt(dt) Z_c.  Blocks 1..8 run in a loop
+// unrolled four times (four independent Philox chains for the scheduler) that parks the
+// 30 normals in the thread's shared-memory column zcol[c * TPB]; the fully unrolled form,
+// 9 Philox blocks and 16 Box-Muller pairs of straight-line code, overflowed the
+// instruction cache.  Returns word 0.
 // rk: the Philox round keys as a kernel parameter (constant operands of the rounds' XORs;
 // the staged copy in shared memory would cost a load per key).
 struct RoundKeys {
