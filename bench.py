@@ -1003,14 +1003,14 @@ COUNTERS = {
     # None, warp-instructions per warp-step), from single ncu captures of each kernel at
     # full occupancy (M = 2^20, 8192 blocks) over N_t = 100 steps of the workload's own step
     # length (--steps-t 100 --keep-dt): profiles/*_double_well_d2_M2p20_Nt100_dt2e-3.md
-    ("double_well", "fwd_pair"): ("65ef00204d60", 17.91, 345.0),
-    ("double_well", "fwd_store"): ("65ef00204d60", 8.59, 288.7),
-    ("double_well", "adj_stored"): ("65ef00204d60", 9.25, 70.0),
-    ("double_well", "adj_recompute"): ("65ef00204d60", 0.74, 351.4),
+    ("double_well", "fwd_pair"): ("999d9a9c5bfe", 17.74, 319.0),
+    ("double_well", "fwd_store"): ("999d9a9c5bfe", 8.58, 295.9),
+    ("double_well", "adj_stored"): ("999d9a9c5bfe", 9.20, 67.2),
+    ("double_well", "adj_recompute"): ("999d9a9c5bfe", 0.79, 338.5),
     # the d = 32 kernels in BF16 tensor-core mode, M = 2^16 (512 tiles), N_t = 100 at the
     # workload's step length: profiles/fwd32_adj32_linear32_d32_M2p16_Nt100_dt2e-3_bf16.md
-    ("linear32/tc1", "fwd_store"): ("65ef00204d60", 127.7, 2145.7),
-    ("linear32/tc1", "adj_stored"): ("65ef00204d60", 143.0, 662.2),
+    ("linear32/tc1", "fwd_store"): ("999d9a9c5bfe", 127.7, 2145.7),
+    ("linear32/tc1", "adj_stored"): ("999d9a9c5bfe", 143.0, 662.2),
 }
 
 

@@ -144,11 +144,11 @@ struct LogWriter {
   __device__ __forceinline__ bool fits(int n) const { return r + n <= L.cap; }
   // Whether the n records of step k fit.  A step that does not fit closes the log, so
   // the logged steps are exactly the jump steps before kovf: a backward sweep that has
-  // not reached kovf regenerates nothing.  A step with three or more jumps (probability
-  // about (lambda dt)^3 / 6) closes it too, so a logged step holds one or two records and
-  // the readers take them without a loop.
+  // not reached kovf regenerates nothing.  In FP32 a step with three or more jumps
+  // (probability about (lambda dt)^3 / 6) closes it too, so a logged step holds one or two
+  // records and the FP32 readers take them without a loop or a call.
   __device__ __forceinline__ bool take(int n, int k) {
-    if (n <= 2 && r + n <= L.cap) return true;
+    if ((sizeof(R) == 8 || n <= 2) && r + n <= L.cap) return true;
     kovf = min(kovf, k);
     L.cap = r;
     return false;
@@ -805,6 +805,27 @@ __device__ __forceinline__ int logged_substep(const KH &kh, R (&mu)[D], R (&g)[D
   return i;
 }
 
+// The records of a step's second and later jumps, out of line, on copies: the FP64 form
+// (with it the scalar FP64 problem's stored adjoint took 0.085 ms per launch, with the FP32
+// form and its log closed at three jumps 0.135 ms).
+template <typename R, int D, int DU, typename KH>
+__device__ __noinline__ void logged_more(const KH kh, R *mu_io, R *g_io, R *thn_io, LogReader2<R, D> *lr) {
+  R mu[D], g[DU], thn = *thn_io;
+#pragma unroll
+  for (int c = 0; c < D; ++c) mu[c] = mu_io[c];
+#pragma unroll
+  for (int l = 0; l < DU; ++l) g[l] = g_io[l];
+  int i;
+  do {
+    i = logged_substep(kh, mu, g, thn, *lr);
+  } while (i > 0);
+#pragma unroll
+  for (int c = 0; c < D; ++c) mu_io[c] = mu[c];
+#pragma unroll
+  for (int l = 0; l < DU; ++l) g_io[l] = g[l];
+  *thn_io = thn;
+}
+
 template <typename R, int D, int DU, typename KH>
 __device__ __forceinline__ void backward_logged(const KH &kh, const R (&xk)[D], R (&mu)[D], R (&g)[DU],
                                                 LogReader2<R, D> &lr, bool maybe, bool jumped) {
@@ -830,9 +851,27 @@ __device__ __forceinline__ void backward_logged(const KH &kh, const R (&xk)[D], 
       for (int c = 0; c < D; ++c) mu[c] = jumped ? mj[c] : mu[c];
     }
     thn = the;
-    // a step with two jumps (rare): its first jump's record follows (a logged step holds at
-    // most two, LogWriter::take)
-    if (i > 0) logged_substep(kh, mu, g, thn, lr);
+    // a step with two or more jumps (rare): the records of its earlier jumps follow; in
+    // FP32 a logged step holds at most two (LogWriter::take), taken inline
+    if (i > 0) {
+      if constexpr (sizeof(R) == 4) {
+        logged_substep(kh, mu, g, thn, lr);
+      } else {
+        R ml[D], gl[DU], tl = thn;
+        LogReader2<R, D> ll = lr;
+#pragma unroll
+        for (int c = 0; c < D; ++c) ml[c] = mu[c];
+#pragma unroll
+        for (int l = 0; l < DU; ++l) gl[l] = g[l];
+        logged_more<R, D, DU, KH>(kh, ml, gl, &tl, &ll);
+#pragma unroll
+        for (int c = 0; c < D; ++c) mu[c] = ml[c];
+#pragma unroll
+        for (int l = 0; l < DU; ++l) g[l] = gl[l];
+        thn = tl;
+        lr = ll;
+      }
+    }
     de0 = M::mul(kh.dt, thn);
   }
   control_sensitivity(kh, mu, de0, g);
