@@ -1000,12 +1000,15 @@ def adjoint_ops(p):
 # since, the entry is stale and the figures derived from it are reported as null.
 COUNTERS = {
     # (workload, kernel): (fingerprint of the kernel sources, DRAM bytes per path-step or
-    # None, warp-instructions per warp-step), from single ncu captures of each kernel at
-    # full occupancy (M = 2^20, 8192 blocks) over N_t = 100 steps of the workload's own step
-    # length (--steps-t 100 --keep-dt): profiles/*_double_well_d2_M2p20_Nt100_dt2e-3.md
-    ("double_well", "fwd_pair"): ("999d9a9c5bfe", 17.74, 319.0),
-    ("double_well", "fwd_store"): ("999d9a9c5bfe", 8.58, 295.9),
-    ("double_well", "adj_stored"): ("999d9a9c5bfe", 9.20, 67.2),
+    # None, warp-instructions per warp-step).  The headline's stored-plan kernels: one
+    # launch each over the headline's N_t = 1000 steps on M = 2^18 paths (2048 blocks; the
+    # counts per warp-step and the bytes per path-step do not depend on M), from
+    # smsp__inst_executed.sum and dram__bytes_{read,write}.sum; the recompute adjoint: a
+    # full capture at M = 2^20 over N_t = 100 steps of the workload's step length.  Both
+    # in profiles/*_double_well_d2_*.md
+    ("double_well", "fwd_pair"): ("999d9a9c5bfe", 18.06, 316.4),
+    ("double_well", "fwd_store"): ("999d9a9c5bfe", 8.64, 293.9),
+    ("double_well", "adj_stored"): ("999d9a9c5bfe", 8.79, 60.2),
     ("double_well", "adj_recompute"): ("999d9a9c5bfe", 0.79, 338.5),
     # the d = 32 kernels in BF16 tensor-core mode, M = 2^16 (512 tiles), N_t = 100 at the
     # workload's step length: profiles/fwd32_adj32_linear32_d32_M2p16_Nt100_dt2e-3_bf16.md
